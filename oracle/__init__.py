@@ -1,0 +1,353 @@
+"""CPU FP64 oracle for polyharmonic-spline (PHS) interpolation (Geoga & O'Neil).
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA path and never calls it; the two meet only through the seeded
+input generators in ``synth.py``.
+
+What it computes, each function citing the passage it follows:
+
+* ``normalize``           -- the affine map to a square domain (Sec. 2, Eq. 2.1
+                             and the domain choices of Sec. 2.2).
+* ``poly_basis``          -- the polynomial block B of Eq. (1.3).
+* ``dense_*``             -- the kernel matrix M, M t and the interpolant,
+                             Eqs. (1.1)-(1.3), by their O(n^2) definitions.
+* ``solve_augmented``     -- the augmented system (1.3) by LU with partial
+                             pivoting (a library primitive).
+* ``solve_qperp``         -- the same system by the sequence (2.5) with an
+                             explicit complete QR and a Cholesky factor.
+* ``random_order``, ``maxmin_order``, ``knn_prev``, ``vecchia_factor``,
+  ``vecchia_apply``       -- the Vecchia preconditioner of Sec. 2.2 (Eq. 2.19,
+                             Fig. 1) with brute-force neighbour search.
+* ``pcg``                 -- preconditioned CG on Q_perp^T M Q_perp (Sec. 2,
+                             after Eq. 2.5; Sec. 2.2) with a dense matvec.
+
+The FMM of Sec. 2.1 is not restated here: it approximates M t, whose plain
+definition ``dense_matvec`` is the oracle for it.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        d, i64, u64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+        P = ctypes.c_void_p
+        L.or_phi.restype = d
+        L.or_phi.argtypes = [i32, d]
+        L.or_dense_matrix.argtypes = [i64, P, i32, P]
+        L.or_dense_matvec.argtypes = [i64, P, i32, P, P]
+        L.or_dense_eval.argtypes = [i64, P, P, i32, i64, P, P]
+        L.or_splitmix64.restype = u64
+        L.or_splitmix64.argtypes = [u64, u64]
+        L.or_random_order.argtypes = [i64, u64, P]
+        L.or_maxmin_order.argtypes = [i64, P, P, P]
+        L.or_knn_prev.argtypes = [i64, P, P, i32, P]
+        L.or_bessel_k1.restype = d
+        L.or_bessel_k1.argtypes = [d]
+        L.or_matern.restype = d
+        L.or_matern.argtypes = [d, d, d]
+        L.or_vecchia_factor.restype = i64
+        L.or_vecchia_factor.argtypes = [i64, P, P, P, i32, d, d, d, P, P]
+        L.or_vecchia_apply.argtypes = [i64, P, i32, P, P, P, P]
+        _LIB = L
+    return _LIB
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# frame and polynomial block
+def normalize(points, halfwidth: float = 0.25):
+    """Map points into [-halfwidth, halfwidth]^2 (Sec. 2: scale invariance, Eq. 2.1;
+    Sec. 2.2: [-1/4,1/4]^2 for k = 2, [-1,1]^2 for k = 4).
+
+    centre c = (min + max)/2 per axis, rho = halfwidth / (max(extent_x, extent_y)/2),
+    x' = (x - c) * rho.  Returns (x', c, rho)."""
+    x = _f64(points).reshape(-1, 2)
+    lo = x.min(axis=0)
+    hi = x.max(axis=0)
+    c = (lo + hi) * 0.5
+    h = max(hi[0] - lo[0], hi[1] - lo[1]) * 0.5
+    if not h > 0:
+        raise ValueError("all points coincide")
+    rho = halfwidth / h
+    return (x - c) * rho, c, rho
+
+
+def min_poly_degree(k: int) -> int:
+    """Smallest polynomial degree that makes phi conditionally positive definite:
+    k/2 for even k, (k-1)/2 for odd k (Sec. 1, Eq. 1.3)."""
+    return k // 2 if k % 2 == 0 else (k - 1) // 2
+
+
+def cpd_sign(k: int) -> int:
+    """Sign s with s * Q_perp^T M Q_perp positive definite.  The paper states
+    Q_perp^T M Q_perp > 0 for the thin-plate case (Sec. 1); for general k the
+    classical result is that (-1)^ceil(k/2) r^k (odd k) and (-1)^(k/2+1) r^k log r
+    (even k) are conditionally positive definite of the minimal order."""
+    return (-1) ** ((k + 1) // 2) if k % 2 == 1 else (-1) ** (k // 2 + 1)
+
+
+def n_poly(deg: int) -> int:
+    return (deg + 1) * (deg + 2) // 2
+
+
+def poly_basis(x, deg: int) -> np.ndarray:
+    """B_{j,s} = P_s(x_j): the total-degree monomials up to `deg`, graded
+    lexicographic order 1, x, y, x^2, xy, y^2, ... (Eq. 1.3)."""
+    x = _f64(x).reshape(-1, 2)
+    cols = []
+    for d in range(deg + 1):
+        for b in range(d + 1):
+            a = d - b
+            cols.append(x[:, 0] ** a * x[:, 1] ** b)
+    return np.stack(cols, axis=1)
+
+
+# --------------------------------------------------------------------------
+# dense kernel matrix, Eqs. (1.1)-(1.3)
+def phi(k: int, r: float) -> float:
+    return lib().or_phi(int(k), float(r))
+
+
+def dense_matrix(x, k: int) -> np.ndarray:
+    x = _f64(x).reshape(-1, 2)
+    n = x.shape[0]
+    out = np.empty((n, n), dtype=np.float64)
+    lib().or_dense_matrix(n, _p(x), int(k), _p(out))
+    return out
+
+
+def dense_matvec(x, k: int, t) -> np.ndarray:
+    x = _f64(x).reshape(-1, 2)
+    t = _f64(t)
+    out = np.empty(x.shape[0], dtype=np.float64)
+    lib().or_dense_matvec(x.shape[0], _p(x), int(k), _p(t), _p(out))
+    return out
+
+
+def dense_eval(x, w, k: int, y) -> np.ndarray:
+    x = _f64(x).reshape(-1, 2)
+    y = _f64(y).reshape(-1, 2)
+    w = _f64(w)
+    out = np.empty(y.shape[0], dtype=np.float64)
+    lib().or_dense_eval(x.shape[0], _p(x), _p(w), int(k), y.shape[0], _p(y), _p(out))
+    return out
+
+
+def interpolant(x, w, beta, k: int, deg: int, y) -> np.ndarray:
+    """f^(y) = sum_s beta_s P_s(y) + sum_j w_j phi(|x_j - y|), Eq. (1.1)."""
+    return poly_basis(y, deg) @ _f64(beta) + dense_eval(x, w, k, y)
+
+
+# --------------------------------------------------------------------------
+# direct solves of the augmented system
+def solve_augmented(x, f, k: int, deg: int):
+    """[M B; B^T 0][w; beta] = [f; 0], Eq. (1.3), by LU with partial pivoting."""
+    x = _f64(x).reshape(-1, 2)
+    n = x.shape[0]
+    M = dense_matrix(x, k)
+    B = poly_basis(x, deg)
+    S = B.shape[1]
+    A = np.zeros((n + S, n + S))
+    A[:n, :n] = M
+    A[:n, n:] = B
+    A[n:, :n] = B.T
+    rhs = np.concatenate([_f64(f), np.zeros(S)])
+    sol = np.linalg.solve(A, rhs)
+    return sol[:n], sol[n:]
+
+
+def solve_qperp(x, f, k: int, deg: int):
+    """The sequence (2.5): Q_perp^T M Q_perp u = Q_perp^T f, w = Q_perp u,
+    R beta = Q^T (f - M w), with B = QR and [Q Q_perp] orthogonal."""
+    x = _f64(x).reshape(-1, 2)
+    f = _f64(f)
+    M = dense_matrix(x, k)
+    B = poly_basis(x, deg)
+    S = B.shape[1]
+    Qc, Rc = np.linalg.qr(B, mode="complete")
+    Q, Qp, R = Qc[:, :S], Qc[:, S:], Rc[:S, :]
+    sg = cpd_sign(k)
+    Mp = sg * (Qp.T @ M @ Qp)
+    L = np.linalg.cholesky(Mp)
+    u = np.linalg.solve(L.T, np.linalg.solve(L, sg * (Qp.T @ f)))
+    w = Qp @ u
+    beta = np.linalg.solve(R, Q.T @ (f - M @ w))
+    return w, beta
+
+
+# --------------------------------------------------------------------------
+# Vecchia preconditioner, Sec. 2.2
+def splitmix64(seed: int, i: int) -> int:
+    return int(lib().or_splitmix64(ctypes.c_uint64(seed), ctypes.c_uint64(i)))
+
+
+def random_order(n: int, seed: int) -> np.ndarray:
+    """order[r] = point of rank r; ranks sorted by (splitmix64(seed, i), i)."""
+    out = np.empty(n, dtype=np.int64)
+    lib().or_random_order(n, ctypes.c_uint64(seed), _p(out))
+    return out
+
+
+def maxmin_order(x):
+    """Exact greedy maxmin enumeration; returns (order, squared selection distances)."""
+    x = _f64(x).reshape(-1, 2)
+    n = x.shape[0]
+    out = np.empty(n, dtype=np.int64)
+    dm = np.empty(n, dtype=np.float64)
+    lib().or_maxmin_order(n, _p(x), _p(out), _p(dm))
+    return out, dm
+
+
+def knn_prev(x, order, m: int) -> np.ndarray:
+    """nbr[i, :] = the min(m, rank(i)) nearest points of smaller rank, by
+    (squared distance, rank); -1 padded.  Brute force."""
+    x = _f64(x).reshape(-1, 2)
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    n = x.shape[0]
+    out = np.empty((n, m), dtype=np.int64)
+    lib().or_knn_prev(n, _p(x), _p(order), int(m), _p(out))
+    return out
+
+
+def bessel_k1(x: float) -> float:
+    return lib().or_bessel_k1(float(x))
+
+
+def matern(nu: float, alpha: float, r) -> np.ndarray:
+    r = np.atleast_1d(_f64(r))
+    L = lib()
+    return np.array([L.or_matern(float(nu), float(alpha), float(v)) for v in r.ravel()]).reshape(r.shape)
+
+
+def vecchia_factor(x, order, nbr, m: int, nu: float, alpha: float, jitter_base: float = 1e-12):
+    """Columns of U~ (Sigma^{-1} ~= U~ U~^T), Eq. (2.19) and Fig. 1.
+    Returns (diag, offd, n_jittered)."""
+    x = _f64(x).reshape(-1, 2)
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    nbr = np.ascontiguousarray(nbr, dtype=np.int64)
+    n = x.shape[0]
+    diag = np.zeros(n)
+    offd = np.zeros((n, m))
+    nj = lib().or_vecchia_factor(n, _p(x), _p(order), _p(nbr), int(m), float(nu), float(alpha),
+                                 float(jitter_base), _p(diag), _p(offd))
+    if nj < 0:
+        raise RuntimeError("local Cholesky failed")
+    return diag, offd, int(nj)
+
+
+def vecchia_apply(nbr, diag, offd, r) -> np.ndarray:
+    """z = U~ (U~^T r)."""
+    nbr = np.ascontiguousarray(nbr, dtype=np.int64)
+    n, m = nbr.shape
+    r = _f64(r)
+    z = np.empty(n)
+    lib().or_vecchia_apply(n, _p(nbr), int(m), _p(_f64(diag)), _p(_f64(offd)), _p(r), _p(z))
+    return z
+
+
+def vecchia_dense(nbr, diag, offd) -> np.ndarray:
+    """The dense n x n matrix U~ of Fig. 1 (column i: 1/c at i, -lambda/c at sigma(i))."""
+    n, m = nbr.shape
+    U = np.zeros((n, n))
+    for i in range(n):
+        U[i, i] = diag[i]
+        for q in range(m):
+            if nbr[i, q] >= 0:
+                U[nbr[i, q], i] = offd[i, q]
+    return U
+
+
+# --------------------------------------------------------------------------
+# preconditioned CG, Sec. 2 (after Eq. 2.5) and Sec. 2.2
+def pcg(x, f, k: int, deg: int, precond=None, tol: float = 1e-10, maxiter: int = 500, atol: float = 0.0):
+    """PCG for Q_perp^T M Q_perp u = Q_perp^T f with preconditioner
+    Q_perp^T U~ U~^T Q_perp, run on the iterates w = Q_perp u in R^n using
+    Q_perp Q_perp^T = I - Q Q^T (Q from the thin QR of B).  x_0 = 0; stops when
+    the recursive residual satisfies ||r_k|| <= max(tol ||Q_perp^T f||, atol).
+    The system is multiplied by cpd_sign(k) so that CG sees a positive definite
+    operator.  precond = (nbr, diag, offd) or None.  Returns (w, beta, iters, history)."""
+    sg = cpd_sign(k)
+    x = _f64(x).reshape(-1, 2)
+    f = _f64(f)
+    B = poly_basis(x, deg)
+    Q, R = np.linalg.qr(B)
+
+    def proj(v):
+        return v - Q @ (Q.T @ v)
+
+    def mv(v):
+        return sg * proj(dense_matvec(x, k, v))
+
+    def prec(v):
+        if precond is None:
+            return v.copy()
+        return proj(vecchia_apply(precond[0], precond[1], precond[2], v))
+
+    w = np.zeros_like(f)
+    r = sg * proj(f)
+    stop = max(tol * np.linalg.norm(r), atol)
+    hist = [np.linalg.norm(r)]
+    z = prec(r)
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    while hist[-1] > stop and it < maxiter:
+        q = mv(p)
+        a = rz / (p @ q)
+        w = w + a * p
+        r = r - a * q
+        it += 1
+        hist.append(np.linalg.norm(r))
+        if hist[-1] <= stop:
+            break
+        z = prec(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    beta = np.linalg.solve(R, Q.T @ (f - dense_matvec(x, k, w)))
+    return w, beta, it, np.array(hist)
+
+
+# --------------------------------------------------------------------------
+# user-frame wrappers
+def fit_dense(points, f, k: int, deg: int | None = None, halfwidth: float = 0.25):
+    """Exact fit in the normalised frame, weights returned in the caller's frame:
+    w_user = rho^k w_norm (Eq. 2.1 generalised to phi = r^k (log r)); beta is
+    the coefficient vector of the monomials in the normalised frame."""
+    if deg is None:
+        deg = min_poly_degree(k)
+    xn, c, rho = normalize(points, halfwidth)
+    w, beta = solve_augmented(xn, f, k, deg)
+    return {"w_norm": w, "w": w * rho ** k, "beta": beta, "center": c, "rho": rho, "xn": xn,
+            "k": k, "deg": deg}
+
+
+def predict(fit: dict, targets) -> np.ndarray:
+    yn = (_f64(targets).reshape(-1, 2) - fit["center"]) * fit["rho"]
+    return interpolant(fit["xn"], fit["w_norm"], fit["beta"], fit["k"], fit["deg"], yn)
+
+
+def nu_alpha_default(k: int):
+    """Paper's preconditioner parameters (Sec. 2.2): nu = 1; alpha ~= 0.35 in
+    [-1/4,1/4]^2 for k = 2, alpha ~= 2 in [-1,1]^2 for k = 4."""
+    return (1.0, 0.35) if k <= 3 else (1.0, 2.0)
+

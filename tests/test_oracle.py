@@ -1,0 +1,331 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- closed forms, published vectors, identities the paper states,
+library routines for special cases, and brute force on tiny inputs."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.special
+from scipy.spatial.distance import cdist
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as fh:
+        return json.load(fh)
+
+
+def _pts(n, seed=0):
+    return np.random.default_rng(seed).random((n, 2))
+
+
+# ---------------------------------------------------------------- phi and M
+def test_phi_closed_forms_345_triangle():
+    g = _gold("phi_345.json")
+    x = np.array(g["points"], dtype=float)
+    for k_s, ent in g["entries"].items():
+        k = int(k_s)
+        M = oracle.dense_matrix(x, k)
+        assert np.all(np.diag(M) == 0.0)
+        for ij, expr in ent.items():
+            i, j = int(ij[0]), int(ij[1])
+            want = eval(expr, {"log": math.log})
+            assert M[i, j] == pytest.approx(want, rel=1e-15, abs=0)
+            assert M[j, i] == M[i, j]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_dense_matvec_is_symmetric_form(k):
+    x = _pts(300, 1)
+    rng = np.random.default_rng(2)
+    t, s = rng.standard_normal(300), rng.standard_normal(300)
+    a = s @ oracle.dense_matvec(x, k, t)
+    b = t @ oracle.dense_matvec(x, k, s)
+    assert a == pytest.approx(b, rel=1e-12)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_scale_law_eq21(k):
+    """Eq. (2.1), generalised: M(rho) = rho^k M + rho^k log(rho) [r^k]."""
+    x = _pts(120, 3)
+    rho = 0.37
+    Mr = oracle.dense_matrix(rho * x, k)
+    M = oracle.dense_matrix(x, k)
+    Dk = cdist(x, x) ** k
+    want = rho ** k * M + rho ** k * math.log(rho) * Dk
+    assert np.max(np.abs(Mr - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def _hadamard_factors(x, power):
+    """Low-rank factors of [|x_i - x_j|^power] (Sec. 2, after Eq. 2.4), power 2 or 4."""
+    a = (x ** 2).sum(1)
+    x1, x2 = x[:, 0], x[:, 1]
+    one = np.ones_like(a)
+    if power == 2:
+        U = np.stack([a, one, -2 * x1, -2 * x2], 1)
+        V = np.stack([one, a, x1, x2], 1)
+    else:
+        U = np.stack([a * a, one, 2 * a, -4 * a * x1, -4 * a * x2, -4 * x1, -4 * x2, 4 * x1 * x1, 8 * x1 * x2, 4 * x2 * x2], 1)
+        V = np.stack([one, a * a, a, x1, x2, a * x1, a * x2, x1 * x1, x1 * x2, x2 * x2], 1)
+    return U, V
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_hadamard_identity_eq26(k):
+    """Eq. (2.6): M t = sum_l D_{u_l} M_core D_{v_l} t with M_core = log r (even k)
+    or r (odd k) and U V^T = [r^{2m}]."""
+    x = _pts(250, 4) - 0.5
+    t = np.random.default_rng(5).standard_normal(250)
+    R = cdist(x, x)
+    np.fill_diagonal(R, 1.0)
+    core = np.log(R) if k % 2 == 0 else R.copy()
+    np.fill_diagonal(core, 0.0)
+    power = k if k % 2 == 0 else k - 1
+    U, V = _hadamard_factors(x, power)
+    assert np.allclose(U @ V.T, cdist(x, x) ** power, rtol=0, atol=1e-14)
+    got = sum(U[:, l] * (core @ (V[:, l] * t)) for l in range(U.shape[1]))
+    want = oracle.dense_matvec(x, k, t)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------- Matern
+def test_bessel_k1_against_scipy():
+    xs = np.concatenate([np.logspace(-8, 2, 400), [1.999999, 2.0, 2.000001]])
+    for v in xs:
+        assert oracle.bessel_k1(v) == pytest.approx(scipy.special.k1(v), rel=2e-14)
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.0, 1.5, 2.5])
+def test_matern_against_general_formula(nu):
+    alpha = 3.0
+    r = np.linspace(1e-3, 4.0, 200)
+    a = alpha * r
+    want = 2 ** (1 - nu) / scipy.special.gamma(nu) * a ** nu * scipy.special.kv(nu, a)
+    got = oracle.matern(nu, alpha, r)
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+    assert oracle.matern(nu, alpha, 0.0)[0] == 1.0
+
+
+def test_matern_small_r_tps_link_eq217():
+    """Eq. (2.17): a K_1(a) = 1 + c a^2 + (a^2/2) log(a/2) + O(a^4 log a): the
+    remainder after removing the log term, divided by a^2, tends to a constant."""
+    a = np.array([1e-2, 5e-3, 2.5e-3, 1.25e-3])
+    g = (oracle.matern(1.0, 1.0, a) - 1.0 - a ** 2 / 2 * np.log(a / 2)) / a ** 2
+    d = np.abs(np.diff(g))
+    assert np.all(d[1:] < d[:-1])
+    assert d[-1] < 1e-5
+    # with the wrong log coefficient the quotient diverges like log a
+    g_bad = (oracle.matern(1.0, 1.0, a) - 1.0 - a ** 2 / 4 * np.log(a / 2)) / a ** 2
+    assert abs(g_bad[-1] - g_bad[0]) > 0.5
+
+
+# ---------------------------------------------------------------- augmented system
+def _system(n=160, seed=6, k=2):
+    x, _, _ = oracle.normalize(_pts(n, seed), 0.25)
+    f = np.sin(7 * x[:, 0]) + np.cos(5 * x[:, 1]) + x[:, 0] * x[:, 1]
+    return x, f
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_augmented_solvers_agree(k):
+    deg = oracle.min_poly_degree(k)
+    x, f = _system(k=k)
+    w1, b1 = oracle.solve_augmented(x, f, k, deg)
+    w2, b2 = oracle.solve_qperp(x, f, k, deg)
+    M = oracle.dense_matrix(x, k)
+    B = oracle.poly_basis(x, deg)
+    S = B.shape[1]
+    A = np.block([[M, B], [B.T, np.zeros((S, S))]])
+    sol = scipy.linalg.solve(A, np.concatenate([f, np.zeros(S)]), assume_a="sym")
+    w3, b3 = sol[: len(f)], sol[len(f):]
+    kappa = np.linalg.cond(A)
+    tol = max(kappa, 1.0) * 1e-15 * 10
+    for w, b in [(w2, b2), (w3, b3)]:
+        assert np.linalg.norm(w - w1) <= tol * np.linalg.norm(w1)
+        assert np.linalg.norm(b - b1) <= tol * max(np.linalg.norm(b1), 1.0)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_interpolation_invariants(k):
+    deg = oracle.min_poly_degree(k)
+    x, f = _system(k=k)
+    w, beta = oracle.solve_augmented(x, f, k, deg)
+    B = oracle.poly_basis(x, deg)
+    fhat = oracle.interpolant(x, w, beta, k, deg, x)
+    assert np.max(np.abs(fhat - f)) <= 1e-9 * np.max(np.abs(f))
+    assert np.linalg.norm(B.T @ w) <= 1e-10 * np.linalg.norm(w) * np.linalg.norm(B)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_polynomial_reproduction(k):
+    deg = oracle.min_poly_degree(k)
+    x, _ = _system(k=k)
+    B = oracle.poly_basis(x, deg)
+    coef = np.arange(1, B.shape[1] + 1, dtype=float) * np.array([1, -1] * 5)[: B.shape[1]]
+    f = B @ coef
+    w, beta = oracle.solve_augmented(x, f, k, deg)
+    M = oracle.dense_matrix(x, k)
+    S = B.shape[1]
+    kappa = np.linalg.cond(np.block([[M, B], [B.T, np.zeros((S, S))]]))
+    # exact answer: w = 0, beta = coef; the LU solve reaches it to kappa * eps
+    assert np.max(np.abs(w)) <= 10 * kappa * 2.2e-16 * np.max(np.abs(f))
+    assert np.allclose(beta, coef, rtol=0, atol=10 * kappa * 2.2e-16 * np.max(np.abs(coef)))
+    y = np.random.default_rng(1).random((50, 2)) * 0.5 - 0.25
+    assert np.allclose(oracle.interpolant(x, w, beta, k, deg, y), oracle.poly_basis(y, deg) @ coef, atol=1e-9)
+
+
+def test_n_equals_S_gives_zero_weights():
+    x = np.array([[0.0, 0.0], [0.2, 0.05], [-0.1, 0.2]])
+    f = np.array([1.0, -2.0, 0.5])
+    w, beta = oracle.solve_augmented(x, f, 2, 1)
+    assert np.max(np.abs(w)) < 1e-14
+    assert np.allclose(oracle.poly_basis(x, 1) @ beta, f, atol=1e-14)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_qperp_projection_is_positive_definite(k):
+    deg = oracle.min_poly_degree(k)
+    x, _ = _system(n=120, k=k)
+    M = oracle.dense_matrix(x, k)
+    B = oracle.poly_basis(x, deg)
+    Qc, _ = np.linalg.qr(B, mode="complete")
+    Qp = Qc[:, B.shape[1]:]
+    ev = np.linalg.eigvalsh(Qp.T @ M @ Qp)
+    # Sec. 1: Q_perp^T M Q_perp is definite; positive for the thin-plate spline
+    assert np.all(oracle.cpd_sign(k) * ev > 0)
+    if k == 2:
+        assert oracle.cpd_sign(k) == 1
+
+
+def test_fit_is_scale_invariant():
+    """Sec. 2, Eq. (2.1): rescaling the points changes neither the interpolant nor
+    the caller-frame weights."""
+    w_ = synth.workload("uniform_tps", n=200, n_targets=50)
+    a = oracle.fit_dense(w_["points"], w_["f"], 2, halfwidth=0.25)
+    b = oracle.fit_dense(w_["points"], w_["f"], 2, halfwidth=1.0)
+    assert np.allclose(a["w"], b["w"], rtol=1e-8, atol=1e-8 * np.abs(a["w"]).max())
+    fa, fb = oracle.predict(a, w_["targets"]), oracle.predict(b, w_["targets"])
+    assert np.max(np.abs(fa - fb)) <= 1e-9 * np.max(np.abs(fa))
+
+
+# ---------------------------------------------------------------- ordering and neighbours
+def test_splitmix64_published_vectors():
+    g = _gold("splitmix64.json")
+    for i, h in enumerate(g["outputs_hex"]):
+        assert oracle.splitmix64(g["seed"], i) == int(h, 16)
+
+
+def test_random_order_sorted_by_key():
+    order = oracle.random_order(1000, 77)
+    assert sorted(order.tolist()) == list(range(1000))
+    keys = [oracle.splitmix64(77, int(i)) for i in order]
+    assert all(keys[i] < keys[i + 1] for i in range(999))
+
+
+def test_knn_golden_lattice():
+    g = _gold("knn_lattice.json")
+    x = np.array(g["points"], dtype=float)
+    for case in g["cases"]:
+        got = oracle.knn_prev(x, np.array(case["order"]), g["m"])
+        assert got.tolist() == case["nbr"]
+
+
+def test_knn_against_independent_brute_force():
+    rng = np.random.default_rng(8)
+    x = np.round(rng.random((300, 2)) * 16) / 16  # lattice: many exact ties
+    order = oracle.random_order(300, 3)
+    m = 7
+    got = oracle.knn_prev(x, order, m)
+    rank = np.empty(300, dtype=np.int64)
+    rank[order] = np.arange(300)
+    for i in range(300):
+        prev = order[: rank[i]]
+        d = ((x[prev] - x[i]) ** 2).sum(1)
+        sel = prev[np.lexsort((rank[prev], d))][:m]
+        want = np.full(m, -1)
+        want[: len(sel)] = sel
+        assert got[i].tolist() == want.tolist()
+
+
+def test_maxmin_golden_line():
+    g = _gold("maxmin_line.json")
+    order, dm = oracle.maxmin_order(np.array(g["points"], dtype=float))
+    assert order.tolist() == g["order"]
+    assert np.isinf(dm[0]) and dm[1:].tolist() == g["dmin2"][1:]
+
+
+def test_maxmin_properties():
+    x = _pts(400, 9)
+    order, dm = oracle.maxmin_order(x)
+    assert sorted(order.tolist()) == list(range(400))
+    assert np.all(np.diff(dm[1:]) <= 0)
+    for r in [1, 7, 50, 399]:
+        d = ((x[order[:r]] - x[order[r]]) ** 2).sum(1).min()
+        assert d == dm[r]
+        rest = order[r:]
+        dd = ((x[rest][:, None, :] - x[order[:r]][None, :, :]) ** 2).sum(2).min(1)
+        assert dd.max() == dm[r]
+    c = (x.min(0) + x.max(0)) / 2
+    assert order[0] == np.argmin(((x - c) ** 2).sum(1))
+
+
+# ---------------------------------------------------------------- Vecchia factor
+@pytest.mark.parametrize("nu,alpha", [(1.5, 6.0), (1.0, 4.0)])
+def test_vecchia_full_conditioning_is_exact_inverse(nu, alpha):
+    """Fig. 1: with sigma(j) = all previous points, U U^T = Sigma^{-1} exactly."""
+    n = 120
+    x = _pts(n, 10) * 0.5
+    order = oracle.random_order(n, 5)
+    nbr = oracle.knn_prev(x, order, n - 1)
+    diag, offd, nj = oracle.vecchia_factor(x, order, nbr, n - 1, nu, alpha)
+    assert nj == 0
+    U = oracle.vecchia_dense(nbr, diag, offd)
+    Sigma = 2 ** (1 - nu) / scipy.special.gamma(nu) * (alpha * cdist(x, x)) ** nu * scipy.special.kv(nu, alpha * cdist(x, x) + 1e-300)
+    np.fill_diagonal(Sigma, 1.0)
+    Sinv = np.linalg.inv(Sigma)
+    assert np.linalg.norm(U @ U.T - Sinv) <= 1e-8 * np.linalg.norm(Sinv)
+    # and U is triangular in the enumeration order
+    Up = U[np.ix_(order, order)]
+    assert np.allclose(Up, np.triu(Up))
+
+
+def test_vecchia_apply_matches_dense_factor():
+    n, m = 200, 10
+    x = _pts(n, 11)
+    order = oracle.random_order(n, 1)
+    nbr = oracle.knn_prev(x, order, m)
+    diag, offd, _ = oracle.vecchia_factor(x, order, nbr, m, 1.5, 10.0)
+    U = oracle.vecchia_dense(nbr, diag, offd)
+    r = np.random.default_rng(0).standard_normal(n)
+    assert np.allclose(oracle.vecchia_apply(nbr, diag, offd, r), U @ (U.T @ r), rtol=1e-13, atol=1e-12)
+
+
+# ---------------------------------------------------------------- PCG
+def test_pcg_converges_to_direct_solution():
+    """Sec. 2.2 / Sec. 3: the Vecchia-preconditioned CG (nu = 1, alpha = 0.35,
+    points in [-1/4,1/4]^2, m = 30, random order) converges in few iterations to
+    the direct solution; plain CG needs far more."""
+    w_ = synth.workload("uniform_tps", n=600, n_targets=10)
+    x, c, rho = oracle.normalize(w_["points"], 0.25)
+    f = w_["f"]
+    order = oracle.random_order(len(f), 1)
+    nbr = oracle.knn_prev(x, order, 30)
+    d, o, _ = oracle.vecchia_factor(x, order, nbr, 30, 1.0, 0.35)
+    w, beta, it, hist = oracle.pcg(x, f, 2, 1, (nbr, d, o), tol=1e-12, maxiter=200)
+    w0, b0 = oracle.solve_augmented(x, f, 2, 1)
+    assert hist[-1] <= 1e-12 * hist[0]
+    assert it < 25
+    y = (w_["targets"] - c) * rho
+    a = oracle.interpolant(x, w, beta, 2, 1, y)
+    b = oracle.interpolant(x, w0, b0, 2, 1, y)
+    assert np.max(np.abs(a - b)) <= 1e-8 * np.max(np.abs(b))
+    _, _, it_plain, _ = oracle.pcg(x, f, 2, 1, None, tol=1e-6, maxiter=2000)
+    _, _, it_pre, _ = oracle.pcg(x, f, 2, 1, (nbr, d, o), tol=1e-6, maxiter=2000)
+    assert it_plain > 5 * it_pre
