@@ -1,0 +1,196 @@
+/*
+ * phs.h -- C ABI of a B300 (sm_103a) implementation of linear-cost
+ * polyharmonic-spline (PHS) interpolation after Geoga & O'Neil,
+ * "Linear-cost Polyharmonic Spline Interpolation of Arbitrary Degree".
+ *
+ * Problem (Sec. 1, Eqs. 1.1-1.3): given points x_j in R^2 and values f_j, find
+ * weights w and polynomial coefficients beta with
+ *     [ M  B ] [ w    ]   [ f ]
+ *     [ B' 0 ] [ beta ] = [ 0 ],   M_ij = phi(|x_i - x_j|),  B_js = P_s(x_j),
+ * phi(r) = r^k (k odd) or r^k log r (k even), so that
+ *     f^(y) = sum_s beta_s P_s(y) + sum_j w_j phi(|x_j - y|).
+ * The solve follows Sec. 2: points are mapped to a square domain (Eq. 2.1),
+ * PCG runs on Q_perp' M Q_perp (Eq. 2.5) with M applied by a 2D fast multipole
+ * method through the Hadamard/low-rank identity (Eq. 2.6) and the Vecchia
+ * sparse inverse-Cholesky preconditioner of a Matern covariance (Sec. 2.2,
+ * Eq. 2.19, Fig. 1).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library never frees or retains them past the call.  Pointers named *_host
+ *    are host pointers (pinned memory gives asynchronous copies).
+ *  - Points are row-major n x 2 arrays of double (x0, y0, x1, y1, ...).
+ *  - Vectors are double, indexed in the caller's point order.
+ *  - All work is enqueued on `stream` (0 = legacy default stream).  Calls that
+ *    return host-visible results (info structs, host outputs) synchronise it.
+ *  - Errors are returned as phs_status; no exception crosses the ABI.  A
+ *    human-readable message for the most recent failing call on the calling
+ *    host thread is available from phs_last_error().
+ *  - A plan may be used from one stream at a time.
+ */
+#ifndef PHS_B300_H
+#define PHS_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *phs_stream_t; /* == cudaStream_t */
+typedef struct phs_plan *phs_plan_t;
+
+typedef enum {
+    PHS_OK = 0,
+    PHS_ERR_INVALID_ARG = 1,      /* bad size, k, degree, option, or non-finite input */
+    PHS_ERR_DUPLICATE_POINTS = 2, /* two input points coincide exactly */
+    PHS_ERR_OOM = 3,              /* device allocation failed */
+    PHS_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed */
+    PHS_ERR_NOT_CONVERGED = 5,    /* PCG reached maxiter above tolerance (results still written) */
+    PHS_ERR_CHOLESKY = 6,         /* a local Vecchia factor failed even after jitter */
+    PHS_ERR_TIMEOUT = 7           /* reserved for bounded device waits */
+} phs_status;
+
+/* Solver options (defaults from phs_options_default). */
+typedef struct {
+    int precision;          /* 0: FP64 throughout.  1: FP32 FMM inside an FP64
+                               iterative-refinement loop (residuals, inner products,
+                               projection and preconditioner stay FP64). */
+    double tol;             /* stop when ||r_k|| <= max(tol*||Q_perp' f||, atol); default 1e-8 */
+    double atol;            /* default 0 */
+    int maxiter;            /* PCG iterations (precision 0) or total inner iterations; default 200 */
+    int leaf_cap;           /* quadtree leaf capacity s; default 64 */
+    int ordering;           /* Vecchia enumeration: 0 random (Sec. 3), 1 exact maxmin */
+    double nu;              /* Matern smoothness: 0.5, 1, 1.5 or 2.5; default 1 (Sec. 2.2) */
+    double alpha;           /* Matern inverse range in the NORMALISED frame; default 0.35 (k<=3), 2 (k>=4) */
+    double domain_halfwidth;/* points are mapped into [-h, h]^2; default 0.25 (k<=3), 1 (k>=4) */
+    uint64_t seed;          /* random enumeration seed */
+    double fmm_eps;         /* FMM truncation target used when fmm_order <= 0; default 1e-13 */
+    double inner_tol;       /* precision 1: relative tolerance of each inner FP32 solve; default 1e-4 */
+    int max_refine;         /* precision 1: maximum refinement steps; default 8 */
+} phs_options;
+
+typedef struct {
+    int iters;              /* PCG iterations (all inner iterations for precision 1) */
+    int outer_iters;        /* refinement steps (precision 1), else 0 */
+    int converged;          /* 1 if the stopping rule was met */
+    int jittered;           /* Vecchia local factors that needed diagonal jitter */
+    double rel_res_recursive; /* final recursive residual / ||Q_perp' f|| */
+    double rel_res_true;      /* ||Q_perp'(f - M w)|| / ||Q_perp' f|| with an FP64 FMM matvec */
+    float ms_plan;          /* plan creation wall time (set by phs_plan_create) */
+    float ms_fit;           /* phs_fit wall time */
+    float ms_matvec_avg;    /* average FMM matvec time inside the fit */
+} phs_fit_info;
+
+/* Fill *opt with the defaults for spline order k. */
+void phs_options_default(phs_options *opt, int k);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *phs_last_error(void);
+
+/*
+ * Build a plan for n points (Sec. 2, setup phase):
+ *   normalisation to [-h,h]^2 (Eq. 2.1), Morton sort and adaptive quadtree with
+ *   FMM interaction lists (Sec. 2.1), thin QR of B (Eq. 2.4), Vecchia
+ *   enumeration, conditioning sets and local factors (Sec. 2.2, Eq. 2.19).
+ * pts_dev:     n x 2 device array, caller order.  Must be finite and distinct.
+ * k:           spline order, 1..5 (Eq. 1.2).
+ * poly_degree: total degree of the polynomial block; >= k/2 (even k) or (k-1)/2
+ *              (odd k), <= 3.  -1 selects the minimum.
+ * fmm_order:   number of expansion terms p (Sec. 2.1, Eqs. 2.12-2.15); <= 0 picks
+ *              p from opt->fmm_eps.  At most 60.
+ * vecchia_m:   conditioning-set size m (Sec. 2.2), 1..64.
+ * opt:         NULL for phs_options_default(k).
+ * On success *out receives the plan (free with phs_plan_destroy).  The call
+ * synchronises `stream`.
+ */
+phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_degree,
+                           int fmm_order, int vecchia_m, const phs_options *opt,
+                           phs_stream_t stream, phs_plan_t *out);
+
+/* out = M t in the caller's frame and order, M_ij = phi(|x_i - x_j|) (Eq. 1.3),
+ * by the FMM of Sec. 2.1 applied through Eq. (2.6).  precision 0 = FP64 FMM,
+ * 1 = FP32 FMM.  t_dev, out_dev: n doubles on the device (may not alias). */
+phs_status phs_matvec(phs_plan_t plan, const double *t_dev, double *out_dev, int precision,
+                      phs_stream_t stream);
+
+/* Solve the augmented system (Eq. 1.3) by the sequence of Eq. (2.5) with
+ * Vecchia-preconditioned CG.  f_dev: n values (caller order).  w_dev: n weights
+ * in the caller's frame.  beta_dev: S coefficients of the monomials
+ * 1, x, y, x^2, xy, y^2, ... evaluated in the plan's NORMALISED frame
+ * (x' = (x - c) * rho, see phs_plan_frame).  info may be NULL.  Synchronises. */
+phs_status phs_fit(phs_plan_t plan, const double *f_dev, double *w_dev, double *beta_dev,
+                   phs_fit_info *info, phs_stream_t stream);
+
+/* Evaluate the interpolant (Eq. 1.1) at m targets (m x 2 device array, caller
+ * frame) with the FMM for the kernel part; w_dev/beta_dev as returned by
+ * phs_fit.  out_dev: m values. */
+phs_status phs_eval(phs_plan_t plan, const double *w_dev, const double *beta_dev,
+                    const double *tgt_dev, int64_t m, double *out_dev, phs_stream_t stream);
+
+/* End-to-end fit and prediction from HOST buffers: copies points/values in,
+ * builds a plan, fits, evaluates at the targets and copies w, beta and the
+ * predictions out.  Any output pointer may be NULL.  Synchronises. */
+phs_status phs_fit_predict_host(const double *pts_host, const double *f_host, int64_t n,
+                                const double *tgt_host, int64_t m, int k, int poly_degree,
+                                int fmm_order, int vecchia_m, const phs_options *opt,
+                                double *w_host, double *beta_host, double *pred_host,
+                                phs_fit_info *info, phs_stream_t stream);
+
+phs_status phs_plan_destroy(phs_plan_t plan);
+
+/* ---- inspection (small host copies; synchronise) --------------------------- */
+/* frame[0..3] = (centre_x, centre_y, rho, halfwidth); sizes[0..7] = (n, k, S, p,
+ * nd, n_boxes, n_leaves, depth). */
+phs_status phs_plan_frame(phs_plan_t plan, double *frame_host, int64_t *sizes_host);
+/* Enumeration and conditioning sets built by the plan: order_host[r] = caller
+ * index of rank r (n entries); nbr_host: n x m caller indices, -1 padded, by
+ * increasing (squared distance, rank).  Either pointer may be NULL. */
+phs_status phs_plan_vecchia(phs_plan_t plan, int64_t *order_host, int64_t *nbr_host);
+/* Vecchia factor columns (Fig. 1): diag_host[i] = 1/c_i, offd_host[i*m+q] = -lambda_q/c_i
+ * (caller order, slots aligned with phs_plan_vecchia's nbr). */
+phs_status phs_plan_vecchia_factor(phs_plan_t plan, double *diag_host, double *offd_host);
+/* z = Q_perp-projected preconditioner P U~ U~' P r (Sec. 2.2); caller order. */
+phs_status phs_plan_precond(phs_plan_t plan, const double *r_dev, double *z_dev,
+                            phs_stream_t stream);
+/* Direct-interaction pair count of the tree (P2P work per matvec) and V-list
+ * translation count (M2L work per matvec): counts_host[0..1]. */
+phs_status phs_plan_work(phs_plan_t plan, int64_t *counts_host);
+/* Per-phase device timing of the most recent phs_fit / phs_matvec calls, in ms,
+ * measured with CUDA events on the plan's stream when enabled (0/1).
+ * ms_host[0..7] = (p2p, m2l, upward, downward, precond, vector, eval, total);
+ * calls_host[0..7] = launches timed per phase. */
+phs_status phs_plan_set_timing(phs_plan_t plan, int enabled);
+phs_status phs_plan_timing(phs_plan_t plan, double *ms_host, int64_t *calls_host);
+
+/* ---- stand-alone building blocks (device pointers, caller order) ----------- */
+/* out = M t with an exact O(n^2) all-pairs sum in FP64 (Eq. 1.3). */
+phs_status phs_dense_matvec(const double *pts_dev, int64_t n, int k, const double *t_dev,
+                            double *out_dev, phs_stream_t stream);
+/* Random enumeration (Sec. 3): order_dev[r] = index of rank r, ranks sorted by
+ * (SplitMix64(seed, i), i), SplitMix64 output i = mix(seed + (i+1)*0x9E3779B97F4A7C15). */
+phs_status phs_random_order(int64_t n, uint64_t seed, int64_t *order_dev, phs_stream_t stream);
+/* Exact maxmin enumeration of the given points: first the point nearest the
+ * bounding-box centre, then repeatedly the point farthest from the selected
+ * set; ties to the smaller index.  Squared distances dx*dx+dy*dy, no FMA. */
+phs_status phs_maxmin_order(const double *pts_dev, int64_t n, int64_t *order_dev,
+                            phs_stream_t stream);
+/* Conditioning sets (Sec. 2.2): for the point of rank r (order_dev as above) the
+ * min(m, r) points of smaller rank nearest to it, by (squared distance
+ * dx*dx+dy*dy without FMA, rank); nbr_dev is n x m int64, -1 padded. */
+phs_status phs_knn_prev(const double *pts_dev, int64_t n, const int64_t *order_dev, int m,
+                        int64_t *nbr_dev, phs_stream_t stream);
+/* Vecchia factor columns (Eq. 2.19, Fig. 1) for conditioning sets nbr_dev
+ * (n x m, -1 padded) of a Matern(nu, alpha) covariance with K(0) = 1:
+ * diag_dev[i] = 1/c_i, offd_dev[i*m+q] = -lambda_q / c_i.  A failed local
+ * Cholesky is retried with diagonal jitter 1e-12 * 10^t, t = 0..4;
+ * *jittered_host (may be NULL) receives how many points needed it. */
+phs_status phs_vecchia_factor(const double *pts_dev, int64_t n, const int64_t *order_dev,
+                              const int64_t *nbr_dev, int m, double nu, double alpha,
+                              double *diag_dev, double *offd_dev, int64_t *jittered_host,
+                              phs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHS_B300_H */

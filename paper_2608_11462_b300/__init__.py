@@ -1,0 +1,212 @@
+"""B300 (sm_103a) polyharmonic-spline interpolation after Geoga & O'Neil,
+"Linear-cost Polyharmonic Spline Interpolation of Arbitrary Degree".
+
+Thin PyTorch-facing binding of the C ABI in include/phs.h: tensors supply
+device memory and streams, every step runs in the CUDA library.  Function names
+mirror the C entry points; ``Plan`` wraps a plan handle.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native
+from ._native import PhsError, PhsFitInfo, PhsOptions, check, lib
+
+__all__ = ["Plan", "PhsError", "PhsOptions", "PhsFitInfo", "options", "phs_dense_matvec", "phs_random_order",
+           "phs_maxmin_order", "phs_knn_prev", "phs_vecchia_factor", "phs_fit_predict_host", "lib"]
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype=torch.float64, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return t.contiguous()
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def options(k: int, **kw) -> PhsOptions:
+    """Defaults of phs_options_default(k), overridden by keyword."""
+    o = PhsOptions()
+    lib().phs_options_default(ctypes.byref(o), int(k))
+    for key, v in kw.items():
+        if not hasattr(o, key):
+            raise KeyError(key)
+        setattr(o, key, v)
+    return o
+
+
+class Plan:
+    """phs_plan_create / phs_matvec / phs_fit / phs_eval on one point set."""
+
+    def __init__(self, points: torch.Tensor, k: int, poly_degree: int = -1, fmm_order: int = 0,
+                 vecchia_m: int = 30, opts: PhsOptions | None = None, stream=None):
+        pts = _dev(points, name="points")
+        if pts.dim() != 2 or pts.shape[1] != 2:
+            raise ValueError("points must be n x 2")
+        self.n = pts.shape[0]
+        self.k = int(k)
+        self.device = pts.device
+        self._opts = opts if opts is not None else options(k)
+        h = ctypes.c_void_p()
+        check(lib().phs_plan_create(_ptr(pts), self.n, self.k, int(poly_degree), int(fmm_order), int(vecchia_m),
+                                    ctypes.byref(self._opts), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.m = int(vecchia_m)
+        fr, sz = self.frame()
+        self.S = int(sz[2])
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().phs_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- hot path
+    def matvec(self, t: torch.Tensor, precision: int = 0, stream=None) -> torch.Tensor:
+        t = _dev(t, name="t")
+        out = torch.empty_like(t)
+        check(lib().phs_matvec(self._h, _ptr(t), _ptr(out), int(precision), _stream(stream)))
+        return out
+
+    def fit(self, f: torch.Tensor, stream=None, allow_not_converged: bool = False):
+        f = _dev(f, name="f")
+        w = torch.empty_like(f)
+        beta = torch.empty(self.S, dtype=torch.float64, device=f.device)
+        info = PhsFitInfo()
+        check(lib().phs_fit(self._h, _ptr(f), _ptr(w), _ptr(beta), ctypes.byref(info), _stream(stream)),
+              allow=(5,) if allow_not_converged else ())
+        return w, beta, info.as_dict()
+
+    def eval(self, w: torch.Tensor, beta: torch.Tensor, targets: torch.Tensor, stream=None) -> torch.Tensor:
+        w = _dev(w, name="w")
+        beta = _dev(beta, name="beta")
+        tg = _dev(targets, name="targets")
+        out = torch.empty(tg.shape[0], dtype=torch.float64, device=tg.device)
+        check(lib().phs_eval(self._h, _ptr(w), _ptr(beta), _ptr(tg), tg.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    # ---- inspection
+    def frame(self):
+        fr = (ctypes.c_double * 4)()
+        sz = (ctypes.c_int64 * 8)()
+        check(lib().phs_plan_frame(self._h, fr, sz))
+        return list(fr), list(sz)
+
+    def vecchia(self):
+        import numpy as np
+        order = np.empty(self.n, dtype=np.int64)
+        nbr = np.empty((self.n, self.m), dtype=np.int64)
+        check(lib().phs_plan_vecchia(self._h, order.ctypes.data_as(ctypes.c_void_p),
+                                     nbr.ctypes.data_as(ctypes.c_void_p)))
+        return order, nbr
+
+    def vecchia_factor(self):
+        import numpy as np
+        diag = np.empty(self.n)
+        offd = np.empty((self.n, self.m))
+        check(lib().phs_plan_vecchia_factor(self._h, diag.ctypes.data_as(ctypes.c_void_p),
+                                            offd.ctypes.data_as(ctypes.c_void_p)))
+        return diag, offd
+
+    def precond(self, r: torch.Tensor, stream=None) -> torch.Tensor:
+        r = _dev(r, name="r")
+        z = torch.empty_like(r)
+        check(lib().phs_plan_precond(self._h, _ptr(r), _ptr(z), _stream(stream)))
+        return z
+
+    def work(self):
+        c = (ctypes.c_int64 * 2)()
+        check(lib().phs_plan_work(self._h, c))
+        return {"near_pairs": c[0], "m2l_translations": c[1]}
+
+    def set_timing(self, enabled: bool):
+        check(lib().phs_plan_set_timing(self._h, int(bool(enabled))))
+
+    def timing(self):
+        ms = (ctypes.c_double * 8)()
+        calls = (ctypes.c_int64 * 8)()
+        check(lib().phs_plan_timing(self._h, ms, calls))
+        names = ["p2p", "m2l", "upward", "downward", "precond", "vector", "eval", "total"]
+        return {nm: (ms[i], calls[i]) for i, nm in enumerate(names)}
+
+
+# ---- stand-alone building blocks
+def phs_dense_matvec(points: torch.Tensor, k: int, t: torch.Tensor, stream=None) -> torch.Tensor:
+    pts = _dev(points, name="points")
+    t = _dev(t, name="t")
+    out = torch.empty_like(t)
+    check(lib().phs_dense_matvec(_ptr(pts), pts.shape[0], int(k), _ptr(t), _ptr(out), _stream(stream)))
+    return out
+
+
+def phs_random_order(n: int, seed: int, device="cuda", stream=None) -> torch.Tensor:
+    out = torch.empty(int(n), dtype=torch.int64, device=device)
+    check(lib().phs_random_order(int(n), ctypes.c_uint64(seed), _ptr(out), _stream(stream)))
+    return out
+
+
+def phs_maxmin_order(points: torch.Tensor, stream=None) -> torch.Tensor:
+    pts = _dev(points, name="points")
+    out = torch.empty(pts.shape[0], dtype=torch.int64, device=pts.device)
+    check(lib().phs_maxmin_order(_ptr(pts), pts.shape[0], _ptr(out), _stream(stream)))
+    return out
+
+
+def phs_knn_prev(points: torch.Tensor, order: torch.Tensor, m: int, stream=None) -> torch.Tensor:
+    pts = _dev(points, name="points")
+    order = _dev(order, torch.int64, name="order")
+    out = torch.empty((pts.shape[0], int(m)), dtype=torch.int64, device=pts.device)
+    check(lib().phs_knn_prev(_ptr(pts), pts.shape[0], _ptr(order), int(m), _ptr(out), _stream(stream)))
+    return out
+
+
+def phs_vecchia_factor(points, order, nbr, m: int, nu: float, alpha: float, stream=None):
+    pts = _dev(points, name="points")
+    order = _dev(order, torch.int64, name="order")
+    nbr = _dev(nbr, torch.int64, name="nbr")
+    n = pts.shape[0]
+    diag = torch.empty(n, dtype=torch.float64, device=pts.device)
+    offd = torch.empty((n, int(m)), dtype=torch.float64, device=pts.device)
+    nj = ctypes.c_int64()
+    check(lib().phs_vecchia_factor(_ptr(pts), n, _ptr(order), _ptr(nbr), int(m), float(nu), float(alpha),
+                                   _ptr(diag), _ptr(offd), ctypes.byref(nj), _stream(stream)))
+    return diag, offd, nj.value
+
+
+def phs_fit_predict_host(points, f, targets, k: int, poly_degree: int = -1, fmm_order: int = 0,
+                         vecchia_m: int = 30, opts: PhsOptions | None = None, stream=None):
+    """End-to-end from host (numpy float64) arrays: returns (w, beta, predictions, info)."""
+    import numpy as np
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    tg = np.ascontiguousarray(targets, dtype=np.float64)
+    n, m = pts.shape[0], tg.shape[0]
+    w = np.empty(n)
+    beta = np.empty(10)
+    pred = np.empty(m)
+    info = PhsFitInfo()
+    o = opts if opts is not None else options(k)
+    P = ctypes.c_void_p
+    code = lib().phs_fit_predict_host(pts.ctypes.data_as(P), f.ctypes.data_as(P), n, tg.ctypes.data_as(P), m,
+                                      int(k), int(poly_degree), int(fmm_order), int(vecchia_m), ctypes.byref(o),
+                                      w.ctypes.data_as(P), beta.ctypes.data_as(P), pred.ctypes.data_as(P),
+                                      ctypes.byref(info), _stream(stream))
+    check(code)
+    S = {0: 1, 1: 3, 2: 6, 3: 10}[poly_degree if poly_degree >= 0 else (k // 2 if k % 2 == 0 else (k - 1) // 2)]
+    return w, beta[:S], pred, info.as_dict()

@@ -1,0 +1,1028 @@
+// abi.cu -- the C ABI (include/phs.h): plans, the preconditioned CG solve of
+// Eq. (2.5) on the Q_perp complement, evaluation, and stand-alone building blocks.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "phs_internal.cuh"
+
+namespace phs {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+const char *last_error() { return g_err.c_str(); }
+
+// ---------------------------------------------------------------- timers
+static thread_local std::vector<cudaEvent_t> g_pool;
+static cudaEvent_t ev_get() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    PHS_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+}  // namespace phs
+
+struct phs_plan {
+    int k = 2, S = 3, deg = 1, m = 30, p = 20;
+    phs_options opt{};
+    phs::PointSet ps;
+    phs::Tree tree;
+    phs::Fmm fmm;
+    phs::Vecchia vec;
+    phs::DBuf<double> Q;      // [S][n] sorted order
+    phs::DBuf<double> R;      // S x S upper triangular, row-major
+    phs::DBuf<double> work;   // 12 work vectors of n
+    phs::DBuf<double> part;   // reduction partials
+    phs::DBuf<double> scal;   // device scalars
+    double *hscal = nullptr;  // pinned host mirror
+    phs::Timers tm;
+    float ms_plan = 0;
+    int sign = 1;             // sign * Q_perp' M Q_perp is positive definite
+    ~phs_plan() {
+        if (hscal) cudaFreeHost(hscal);
+    }
+};
+
+namespace phs {
+
+void Timers::begin(cudaStream_t s) {
+    if (!enabled) return;
+    cudaEvent_t a = ev_get();
+    cudaEventRecord(a, s);
+    stack.push_back(a);
+}
+void Timers::end(int phase, cudaStream_t s) {
+    if (!enabled || stack.empty()) return;
+    cudaEvent_t a = stack.back();
+    stack.pop_back();
+    cudaEvent_t b = ev_get();
+    cudaEventRecord(b, s);
+    pending.push_back(EvRec{a, b, phase});
+    if (pending.size() > 8192) resolve();
+}
+void Timers::resolve() {
+    for (auto &p : pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        this->ms[p.phase] += ms;
+        calls[p.phase] += 1;
+        g_pool.push_back(p.a);
+        g_pool.push_back(p.b);
+    }
+    pending.clear();
+}
+Timers::~Timers() {
+    for (auto &p : pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+}
+
+namespace {
+
+constexpr int RED_T = 256;
+constexpr int RED_B = 592;  // 4 blocks per SM on 148 SMs
+constexpr int MAXS = 10;
+
+// partial dot products: out[b*cnt + i] = sum over this block's stride of a_i . b_i
+struct DotSet {
+    const double *a[12];
+    const double *b[12];
+    int cnt;
+};
+__global__ void dots_partial(DotSet ds, int64_t n, double *part) {
+    double acc[12];
+    for (int i = 0; i < ds.cnt; ++i) acc[i] = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * RED_T + threadIdx.x; j < n; j += (int64_t)gridDim.x * RED_T)
+        for (int i = 0; i < ds.cnt; ++i) acc[i] += ds.a[i][j] * ds.b[i][j];
+    __shared__ double sh[RED_T];
+    for (int i = 0; i < ds.cnt; ++i) {
+        sh[threadIdx.x] = acc[i];
+        __syncthreads();
+        for (int o = RED_T / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * 12 + i] = sh[0];
+        __syncthreads();
+    }
+}
+// fixed-order final sum of the partials: out[i] = sum_b part[b][i]
+__global__ void dots_final(const double *part, int nblk, int cnt, double *out) {
+    const int i = threadIdx.x;
+    if (i >= cnt) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[b * 12 + i];
+    out[i] = s;
+}
+
+// monomials 1, x, y, x^2, xy, y^2, ... (graded lexicographic), Eq. (1.3)
+__device__ __forceinline__ void monomials(int deg, double x, double y, double *v) {
+    int s = 0;
+    for (int d = 0; d <= deg; ++d)
+        for (int b = 0; b <= d; ++b) {
+            const int a = d - b;
+            double t = 1.0;
+            for (int i = 0; i < a; ++i) t *= x;
+            for (int i = 0; i < b; ++i) t *= y;
+            v[s++] = t;
+        }
+}
+__global__ void build_B(const double2 *xs, int64_t n, int deg, int S, double *B) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double v[MAXS];
+    monomials(deg, xs[j].x, xs[j].y, v);
+    for (int s = 0; s < S; ++s) B[(int64_t)s * n + j] = v[s];
+}
+// Gram partials G_ab = sum_j B_a B_b (upper triangle, packed)
+__global__ void gram_partial(const double *B, int64_t n, int S, double *part) {
+    double acc[MAXS * (MAXS + 1) / 2];
+    const int np = S * (S + 1) / 2;
+    for (int i = 0; i < np; ++i) acc[i] = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * RED_T + threadIdx.x; j < n; j += (int64_t)gridDim.x * RED_T) {
+        double v[MAXS];
+        for (int s = 0; s < S; ++s) v[s] = B[(int64_t)s * n + j];
+        int t = 0;
+        for (int a = 0; a < S; ++a)
+            for (int b = a; b < S; ++b) acc[t++] += v[a] * v[b];
+    }
+    __shared__ double sh[RED_T];
+    for (int i = 0; i < np; ++i) {
+        sh[threadIdx.x] = acc[i];
+        __syncthreads();
+        for (int o = RED_T / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * 64 + i] = sh[0];
+        __syncthreads();
+    }
+}
+// one thread: G = R'R (Cholesky, R upper), status[0] = 0 on success
+__global__ void gram_chol(const double *part, int nblk, int S, double *Rout, int *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double G[MAXS][MAXS];
+    int t = 0;
+    for (int a = 0; a < S; ++a)
+        for (int b = a; b < S; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < nblk; ++k) s += part[k * 64 + t];
+            G[a][b] = G[b][a] = s;
+            ++t;
+        }
+    double Rm[MAXS][MAXS] = {};
+    for (int j = 0; j < S; ++j) {
+        double d = G[j][j];
+        for (int k = 0; k < j; ++k) d -= Rm[k][j] * Rm[k][j];
+        if (!(d > 0.0)) { status[0] = 1; return; }
+        Rm[j][j] = sqrt(d);
+        for (int i = j + 1; i < S; ++i) {
+            double v = G[j][i];
+            for (int k = 0; k < j; ++k) v -= Rm[k][j] * Rm[k][i];
+            Rm[j][i] = v / Rm[j][j];
+        }
+    }
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) Rout[a * S + b] = Rm[a][b];
+    status[0] = 0;
+}
+// rows q = b R^{-1} (in place on B, column-major [S][n])
+__global__ void apply_rinv(double *B, int64_t n, int S, const double *Rm) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double q[MAXS];
+    for (int c = 0; c < S; ++c) {
+        double v = B[(int64_t)c * n + j];
+        for (int i = 0; i < c; ++i) v -= q[i] * Rm[i * S + c];
+        q[c] = v / Rm[c * S + c];
+    }
+    for (int c = 0; c < S; ++c) B[(int64_t)c * n + j] = q[c];
+}
+// R = R2 R1 (both upper triangular)
+__global__ void mul_upper(const double *R2, const double *R1, int S, double *Rout) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < S; ++k) s += R2[a * S + k] * R1[k * S + b];
+            Rout[a * S + b] = s;
+        }
+}
+// Q-coefficient partials: part[b][s] = sum Q_s . v
+__global__ void qt_partial(const double *Q, int S, int64_t n, const double *v, double *part) {
+    double acc[MAXS];
+    for (int s = 0; s < S; ++s) acc[s] = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * RED_T + threadIdx.x; j < n; j += (int64_t)gridDim.x * RED_T) {
+        const double vj = v[j];
+        for (int s = 0; s < S; ++s) acc[s] += Q[(int64_t)s * n + j] * vj;
+    }
+    __shared__ double sh[RED_T];
+    for (int s = 0; s < S; ++s) {
+        sh[threadIdx.x] = acc[s];
+        __syncthreads();
+        for (int o = RED_T / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * 12 + s] = sh[0];
+        __syncthreads();
+    }
+}
+// out = sign * (v - Q c); optional partial of dot(other, out)
+__global__ void proj_apply(const double *Q, int S, int64_t n, const double *c, const double *v, double sign,
+                           double *out, const double *other, double *part) {
+    double acc = 0.0;
+    double cc[MAXS];
+    for (int s = 0; s < S; ++s) cc[s] = c[s];
+    for (int64_t j = (int64_t)blockIdx.x * RED_T + threadIdx.x; j < n; j += (int64_t)gridDim.x * RED_T) {
+        double x = v[j];
+        for (int s = 0; s < S; ++s) x -= Q[(int64_t)s * n + j] * cc[s];
+        x *= sign;
+        out[j] = x;
+        if (other) acc += other[j] * x;
+    }
+    if (!part) return;
+    __shared__ double sh[RED_T];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = RED_T / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x * 12] = sh[0];
+}
+// x += alpha p, r -= alpha q, partial r.r ; alpha = sc[0] / sc[1]
+__global__ void cg_update(double *x, double *r, const double *p, const double *q, int64_t n, const double *num,
+                          const double *den, double *part) {
+    const double alpha = num[0] / den[0];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * RED_T + threadIdx.x; j < n; j += (int64_t)gridDim.x * RED_T) {
+        x[j] += alpha * p[j];
+        const double rj = r[j] - alpha * q[j];
+        r[j] = rj;
+        acc += rj * rj;
+    }
+    __shared__ double sh[RED_T];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = RED_T / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x * 12] = sh[0];
+}
+// p = z + (num/den) p
+__global__ void p_update(double *p, const double *z, int64_t n, const double *num, const double *den) {
+    const double beta = num[0] / den[0];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        p[j] = z[j] + beta * p[j];
+}
+__global__ void copy_scalar(const double *src, double *dst) { dst[0] = src[0]; }
+
+__global__ void gather_vec(const double *src, const int *idx, int64_t n, double *dst) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = src[idx[j]];
+}
+__global__ void gather_scaled(const double *src, const int *idx, int64_t n, double scale, double *dst) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = src[idx[j]] * scale;
+}
+__global__ void scatter_scaled(const double *src, const int *idx, int64_t n, double scale, double *dst) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[idx[j]] = src[j] * scale;
+}
+__global__ void axpy_k(double *y, const double *x, int64_t n, double a) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) y[j] += a * x[j];
+}
+__global__ void zero_k(double *y, int64_t n) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) y[j] = 0.0;
+}
+__global__ void sub_k(double *out, const double *a, const double *b, int64_t n) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = a[j] - b[j];
+}
+// R beta = c  (upper triangular, one thread)
+__global__ void tri_solve(const double *Rm, int S, const double *c, double *beta) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double b[MAXS];
+    for (int i = S - 1; i >= 0; --i) {
+        double v = c[i];
+        for (int j = i + 1; j < S; ++j) v -= Rm[i * S + j] * b[j];
+        b[i] = v / Rm[i * S + i];
+    }
+    for (int i = 0; i < S; ++i) beta[i] = b[i];
+}
+// normalise targets and add the polynomial part: out += sum_s beta_s P_s(y')
+__global__ void norm_targets(const double *tgt, int64_t m, double cx, double cy, double rho, double2 *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    out[i] = make_double2(__dmul_rn(__dsub_rn(tgt[2 * i], cx), rho), __dmul_rn(__dsub_rn(tgt[2 * i + 1], cy), rho));
+}
+__global__ void add_poly(const double2 *y, int64_t m, int deg, int S, const double *beta, double *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double v[MAXS];
+    monomials(deg, y[i].x, y[i].y, v);
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += beta[q] * v[q];
+    out[i] += s;
+}
+// low-rank correction of the frame change, Eq. (2.1): partials of v_l . t and y -= log(rho) * u . c
+__global__ void had_dots(const double2 *xs, const double *t, int64_t n, int power, double *part) {
+    const int nd = power == 2 ? 4 : 10;
+    double acc[10] = {};
+    for (int64_t j = (int64_t)blockIdx.x * RED_T + threadIdx.x; j < n; j += (int64_t)gridDim.x * RED_T) {
+        const double x = xs[j].x, y = xs[j].y, a = x * x + y * y, tj = t[j];
+        double v[10];
+        if (power == 2) { v[0] = 1; v[1] = a; v[2] = x; v[3] = y; }
+        else { v[0] = 1; v[1] = a * a; v[2] = a; v[3] = x; v[4] = y; v[5] = a * x; v[6] = a * y; v[7] = x * x; v[8] = x * y; v[9] = y * y; }
+        for (int d = 0; d < nd; ++d) acc[d] += v[d] * tj;
+    }
+    __shared__ double sh[RED_T];
+    for (int d = 0; d < nd; ++d) {
+        sh[threadIdx.x] = acc[d];
+        __syncthreads();
+        for (int o = RED_T / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * 12 + d] = sh[0];
+        __syncthreads();
+    }
+}
+__global__ void had_correct(const double2 *xs, int64_t n, int power, const double *c, double lr, double *y) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double x = xs[j].x, yy = xs[j].y, a = x * x + yy * yy;
+    double u[10];
+    int nd;
+    if (power == 2) { nd = 4; u[0] = a; u[1] = 1; u[2] = -2 * x; u[3] = -2 * yy; }
+    else { nd = 10; u[0] = a * a; u[1] = 1; u[2] = 2 * a; u[3] = -4 * a * x; u[4] = -4 * a * yy; u[5] = -4 * x; u[6] = -4 * yy; u[7] = 4 * x * x; u[8] = 8 * x * yy; u[9] = 4 * yy * yy; }
+    double s = 0.0;
+    for (int d = 0; d < nd; ++d) s += u[d] * c[d];
+    y[j] -= lr * s;
+}
+__global__ void to_i64(const int *src, int64_t n, int64_t *dst) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = src[j];
+}
+__global__ void from_i64(const int64_t *src, int64_t n, int *dst) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = (int)src[j];
+}
+__global__ void ell_to_rows_i64(const int *ell, int64_t n, int m, int64_t *rows) {
+    // rows[i*m + q] = ell[q*n + i]
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * m) return;
+    const int64_t i = t / m, q = t - i * m;
+    rows[t] = ell[q * n + i];
+}
+__global__ void rows_to_ell_i32(const int64_t *rows, int64_t n, int m, int *ell) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * m) return;
+    const int64_t i = t / m, q = t - i * m;
+    ell[q * n + i] = (int)rows[t];
+}
+__global__ void ell_to_rows_d(const double *ell, int64_t n, int m, int slot0, double *rows) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * m) return;
+    const int64_t i = t / m, q = t - i * m;
+    rows[t] = ell[(q + slot0) * n + i];
+}
+__global__ void pts_to_d2(const double *p, int64_t n, double2 *out) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = make_double2(p[2 * j], p[2 * j + 1]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- plan helpers
+static double *W(phs_plan *pl, int i) { return pl->work.get() + (size_t)i * pl->ps.n; }
+
+static void dots(phs_plan *pl, std::initializer_list<std::pair<const double *, const double *>> prs, double *out,
+                 cudaStream_t s) {
+    DotSet ds;
+    ds.cnt = 0;
+    for (auto &pr : prs) {
+        ds.a[ds.cnt] = pr.first;
+        ds.b[ds.cnt] = pr.second;
+        ++ds.cnt;
+    }
+    dots_partial<<<RED_B, RED_T, 0, s>>>(ds, pl->ps.n, pl->part.get());
+    PHS_LAUNCH_CHECK();
+    dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, ds.cnt, out);
+    PHS_LAUNCH_CHECK();
+}
+
+// out = sign * P v  (P = I - Q Q'); if other != null, dot(other, out) -> *dot_out
+static void project(phs_plan *pl, const double *v, double sign, double *out, const double *other, double *dot_out,
+                    cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    double *coef = pl->scal.get() + 16;
+    qt_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, v, pl->part.get());
+    PHS_LAUNCH_CHECK();
+    dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, pl->S, coef);
+    PHS_LAUNCH_CHECK();
+    proj_apply<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, coef, v, sign, out, other,
+                                        other ? pl->part.get() + 8 * 0 : nullptr);
+    PHS_LAUNCH_CHECK();
+    if (other) {
+        dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, 1, dot_out);
+        PHS_LAUNCH_CHECK();
+    }
+}
+
+static void matvec_norm(phs_plan *pl, const double *t, double *y, int precision, cudaStream_t s) {
+    if (precision == 0) fmm_apply64(pl->fmm, pl->tree, pl->ps, t, y, s, &pl->tm);
+    else fmm_apply32(pl->fmm, pl->tree, pl->ps, t, y, s, &pl->tm);
+}
+
+static double read_scalar(phs_plan *pl, const double *dev, cudaStream_t s) {
+    PHS_CUDA(cudaMemcpyAsync(pl->hscal, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    return pl->hscal[0];
+}
+
+// z = P U~ U~' r
+static void precond(phs_plan *pl, const double *r, double *z, double *tmp, double *tmp2, cudaStream_t s) {
+    pl->tm.begin(s);
+    vecchia_apply(pl->vec, r, tmp, tmp2, s);
+    pl->tm.end(T_PRECOND, s);
+    project(pl, tmp2, 1.0, z, nullptr, nullptr, s);
+}
+
+// PCG on sign * P M' P x = rhs (rhs in range(P)), x0 = 0.  Returns iterations; *relres = ||r||/||rhs||.
+// Work vectors used: 0..6.
+static int pcg(phs_plan *pl, const double *rhs, double *x, double tol_abs, int maxiter, int precision,
+               double *rr_final, cudaStream_t s, double *ms_mv, int *n_mv) {
+    const int64_t n = pl->ps.n;
+    double *r = W(pl, 0), *z = W(pl, 1), *p = W(pl, 2), *q = W(pl, 3), *y = W(pl, 4), *t1 = W(pl, 5),
+           *t2 = W(pl, 6);
+    double *sc = pl->scal.get();  // 0 rz, 1 pq, 2 rr, 3 rz_new
+    zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
+    PHS_CUDA(cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    precond(pl, r, z, t1, t2, s);
+    PHS_CUDA(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    dots(pl, {{r, z}, {r, r}}, sc + 4, s);
+    copy_scalar<<<1, 1, 0, s>>>(sc + 4, sc + 0);
+    double rr = read_scalar(pl, sc + 5, s);
+    int it = 0;
+    while (std::sqrt(rr) > tol_abs && it < maxiter) {
+        auto t0 = std::chrono::steady_clock::now();
+        matvec_norm(pl, p, y, precision, s);
+        if (ms_mv) {
+            PHS_CUDA(cudaStreamSynchronize(s));
+            *ms_mv += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            ++*n_mv;
+        }
+        pl->tm.begin(s);
+        project(pl, y, (double)pl->sign, q, p, sc + 1, s);
+        cg_update<<<RED_B, RED_T, 0, s>>>(x, r, p, q, n, sc + 0, sc + 1, pl->part.get());
+        PHS_LAUNCH_CHECK();
+        dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, 1, sc + 2);
+        PHS_LAUNCH_CHECK();
+        pl->tm.end(T_VEC, s);
+        rr = read_scalar(pl, sc + 2, s);
+        ++it;
+        if (std::sqrt(rr) <= tol_abs) break;
+        precond(pl, r, z, t1, t2, s);
+        pl->tm.begin(s);
+        dots(pl, {{r, z}}, sc + 3, s);
+        p_update<<<RED_B, RED_T, 0, s>>>(p, z, n, sc + 3, sc + 0);
+        PHS_LAUNCH_CHECK();
+        copy_scalar<<<1, 1, 0, s>>>(sc + 3, sc + 0);
+        PHS_LAUNCH_CHECK();
+        pl->tm.end(T_VEC, s);
+    }
+    *rr_final = rr;
+    return it;
+}
+
+}  // namespace phs
+
+using namespace phs;
+
+#define PHS_TRY try {
+#define PHS_CATCH                                                        \
+    }                                                                    \
+    catch (const phs::Error &e) {                                        \
+        phs::set_error(e.msg);                                           \
+        return e.code;                                                   \
+    }                                                                    \
+    catch (const std::bad_alloc &) {                                     \
+        phs::set_error("host allocation failed");                        \
+        return PHS_ERR_OOM;                                              \
+    }                                                                    \
+    catch (const std::exception &e) {                                    \
+        phs::set_error(e.what());                                        \
+        return PHS_ERR_CUDA;                                             \
+    }                                                                    \
+    phs::set_error("");                                                  \
+    return PHS_OK;
+
+static int min_degree(int k) { return k % 2 == 0 ? k / 2 : (k - 1) / 2; }
+static int cpd_sign(int k) {
+    if (k % 2 == 1) return ((k + 1) / 2) % 2 ? -1 : 1;
+    return (k / 2 + 1) % 2 ? -1 : 1;
+}
+
+extern "C" {
+
+void phs_options_default(phs_options *o, int k) {
+    std::memset(o, 0, sizeof(*o));
+    o->precision = 0;
+    o->tol = 1e-8;
+    o->atol = 0.0;
+    o->maxiter = 200;
+    o->leaf_cap = 64;
+    o->ordering = 0;
+    o->nu = 1.0;
+    o->alpha = k >= 4 ? 2.0 : 0.35;
+    o->domain_halfwidth = k >= 4 ? 1.0 : 0.25;
+    o->seed = 1;
+    o->fmm_eps = 1e-13;
+    o->inner_tol = 1e-4;
+    o->max_refine = 8;
+}
+
+const char *phs_last_error(void) { return phs::last_error(); }
+
+phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_degree, int fmm_order, int vecchia_m,
+                           const phs_options *opt, phs_stream_t stream, phs_plan_t *out) {
+    PHS_TRY
+    PHS_REQUIRE(out != nullptr && pts_dev != nullptr, PHS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    PHS_REQUIRE(k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "k must be in 1..5");
+    const int deg = poly_degree < 0 ? min_degree(k) : poly_degree;
+    PHS_REQUIRE(deg >= min_degree(k) && deg <= 3, PHS_ERR_INVALID_ARG, "poly_degree below the minimum for k, or > 3");
+    const int S = (deg + 1) * (deg + 2) / 2;
+    PHS_REQUIRE(n > S, PHS_ERR_INVALID_ARG, "need more points than polynomial terms");
+    PHS_REQUIRE(vecchia_m >= 1 && vecchia_m <= 64, PHS_ERR_INVALID_ARG, "vecchia_m must be in 1..64");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    phs_plan *pl = new phs_plan();
+    try {
+        pl->k = k;
+        pl->deg = deg;
+        pl->S = S;
+        pl->m = vecchia_m;
+        if (opt) pl->opt = *opt;
+        else phs_options_default(&pl->opt, k);
+        const phs_options &o = pl->opt;
+        PHS_REQUIRE(o.tol > 0 && o.maxiter >= 1 && o.precision >= 0 && o.precision <= 1, PHS_ERR_INVALID_ARG,
+                    "bad solver options");
+        PHS_REQUIRE(o.ordering == 0 || o.ordering == 1, PHS_ERR_INVALID_ARG, "ordering must be 0 or 1");
+        int p = fmm_order;
+        if (p <= 0) {
+            PHS_REQUIRE(o.fmm_eps > 0 && o.fmm_eps < 1, PHS_ERR_INVALID_ARG, "fmm_eps must be in (0,1)");
+            p = (int)std::ceil(std::log(o.fmm_eps) / std::log(0.55));
+            p = std::max(4, std::min(p, 60));
+        }
+        pl->p = p;
+        pl->sign = cpd_sign(k);
+        PHS_CUDA(cudaMallocHost((void **)&pl->hscal, 64 * sizeof(double)));
+        build_points_and_tree(pts_dev, n, o.domain_halfwidth, o.leaf_cap, pl->ps, pl->tree, s);
+        fmm_setup(pl->fmm, k, p, std::min(p, 24), pl->tree, s);
+        // thin QR of B by two rounds of Cholesky QR (Q has orthonormal columns, R upper)
+        pl->Q.alloc((size_t)S * n);
+        pl->R.alloc((size_t)S * S * 3);
+        pl->part.alloc((size_t)RED_B * 64);
+        pl->scal.alloc(64);
+        build_B<<<blocks_for(n, 256), 256, 0, s>>>(pl->ps.xs.get(), n, deg, S, pl->Q.get());
+        PHS_LAUNCH_CHECK();
+        DBuf<int> st(1);
+        for (int round = 0; round < 2; ++round) {
+            gram_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), n, S, pl->part.get());
+            PHS_LAUNCH_CHECK();
+            gram_chol<<<1, 1, 0, s>>>(pl->part.get(), RED_B, S, pl->R.get() + (size_t)(round + 1) * S * S, st.get());
+            PHS_LAUNCH_CHECK();
+            int hs = 0;
+            PHS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+            PHS_CUDA(cudaStreamSynchronize(s));
+            PHS_REQUIRE(hs == 0, PHS_ERR_INVALID_ARG, "polynomial block is rank deficient for these points");
+            apply_rinv<<<blocks_for(n, 256), 256, 0, s>>>(pl->Q.get(), n, S, pl->R.get() + (size_t)(round + 1) * S * S);
+            PHS_LAUNCH_CHECK();
+        }
+        mul_upper<<<1, 1, 0, s>>>(pl->R.get() + 2 * S * S, pl->R.get() + S * S, S, pl->R.get());
+        PHS_LAUNCH_CHECK();
+        // Vecchia preconditioner
+        vecchia_build(pl->vec, pl->ps, vecchia_m, o.ordering, o.seed, o.nu, o.alpha, s);
+        pl->work.alloc((size_t)12 * n);
+        PHS_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        delete pl;
+        throw;
+    }
+    pl->ms_plan = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = pl;
+    PHS_CATCH
+}
+
+phs_status phs_plan_destroy(phs_plan_t plan) {
+    PHS_TRY
+    if (plan) {
+        cudaDeviceSynchronize();
+        delete plan;
+    }
+    PHS_CATCH
+}
+
+phs_status phs_matvec(phs_plan_t pl, const double *t_dev, double *out_dev, int precision, phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pl && t_dev && out_dev && t_dev != out_dev, PHS_ERR_INVALID_ARG, "bad arguments");
+    PHS_REQUIRE(precision == 0 || precision == 1, PHS_ERR_INVALID_ARG, "precision must be 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = pl->ps.n;
+    double *ts = W(pl, 8), *y = W(pl, 9);
+    gather_vec<<<blocks_for(n, 256), 256, 0, s>>>(t_dev, pl->ps.perm.get(), n, ts);
+    PHS_LAUNCH_CHECK();
+    pl->tm.begin(s);
+    matvec_norm(pl, ts, y, precision, s);
+    pl->tm.end(T_TOTAL, s);
+    const double rho = pl->ps.frame.rho;
+    if (pl->k % 2 == 0) {
+        // M' = rho^k M + log(rho) [r'^k]  =>  M t = rho^-k (M' t - log(rho) U'(V'^T t))
+        const int power = pl->k;
+        had_dots<<<RED_B, RED_T, 0, s>>>(pl->ps.xs.get(), ts, n, power, pl->part.get());
+        PHS_LAUNCH_CHECK();
+        dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, power == 2 ? 4 : 10, pl->scal.get() + 32);
+        PHS_LAUNCH_CHECK();
+        had_correct<<<blocks_for(n, 256), 256, 0, s>>>(pl->ps.xs.get(), n, power, pl->scal.get() + 32, std::log(rho), y);
+        PHS_LAUNCH_CHECK();
+    }
+    scatter_scaled<<<blocks_for(n, 256), 256, 0, s>>>(y, pl->ps.perm.get(), n, std::pow(rho, -(double)pl->k), out_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CATCH
+}
+
+phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *beta_dev, phs_fit_info *info,
+                   phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pl && f_dev && w_dev && beta_dev, PHS_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t n = pl->ps.n;
+    const phs_options &o = pl->opt;
+    double *fs = W(pl, 7), *rhs = W(pl, 8), *x = W(pl, 9), *y = W(pl, 10), *d = W(pl, 11);
+    double *sc = pl->scal.get();
+    gather_vec<<<blocks_for(n, 256), 256, 0, s>>>(f_dev, pl->ps.perm.get(), n, fs);
+    PHS_LAUNCH_CHECK();
+    // rhs = sign * P f
+    project(pl, fs, (double)pl->sign, rhs, rhs, sc + 6, s);
+    const double rr0 = read_scalar(pl, sc + 6, s);
+    const double nrm0 = std::sqrt(rr0);
+    const double stop = std::max(o.tol * nrm0, o.atol);
+    double ms_mv = 0;
+    int n_mv = 0;
+    int iters = 0, outer = 0;
+    double rr = rr0;
+    bool converged = false;
+    if (nrm0 == 0.0) {
+        zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
+        converged = true;
+    } else if (o.precision == 0) {
+        iters = pcg(pl, rhs, x, stop, o.maxiter, 0, &rr, s, &ms_mv, &n_mv);
+        converged = std::sqrt(rr) <= stop;
+    } else {
+        // FP64 iterative refinement around FP32-FMM inner PCG solves
+        zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
+        PHS_CUDA(cudaMemcpyAsync(d, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));  // residual
+        double res = nrm0;
+        while (outer < o.max_refine && iters < o.maxiter) {
+            double rri = 0;
+            double *dx = W(pl, 8);  // rhs no longer needed
+            int it = pcg(pl, d, dx, std::max(o.inner_tol * res, 0.5 * stop), o.maxiter - iters, 1, &rri, s, &ms_mv,
+                         &n_mv);
+            iters += it;
+            ++outer;
+            axpy_k<<<blocks_for(n, 256), 256, 0, s>>>(x, dx, n, 1.0);
+            PHS_LAUNCH_CHECK();
+            // true residual in FP64: d = sign * P (f - M' x)
+            matvec_norm(pl, x, y, 0, s);
+            sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, fs, y, n);
+            PHS_LAUNCH_CHECK();
+            project(pl, y, (double)pl->sign, d, d, sc + 7, s);
+            res = std::sqrt(read_scalar(pl, sc + 7, s));
+            rr = res * res;
+            if (res <= stop) { converged = true; break; }
+            if (it == 0) break;
+        }
+    }
+    // beta: R beta = Q' (f - M' w)
+    matvec_norm(pl, x, y, 0, s);
+    sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, fs, y, n);
+    PHS_LAUNCH_CHECK();
+    qt_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, y, pl->part.get());
+    PHS_LAUNCH_CHECK();
+    dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, pl->S, sc + 40);
+    PHS_LAUNCH_CHECK();
+    tri_solve<<<1, 1, 0, s>>>(pl->R.get(), pl->S, sc + 40, beta_dev);
+    PHS_LAUNCH_CHECK();
+    // true relative residual ||P (f - M' w)|| / ||P f||
+    project(pl, y, 1.0, d, d, sc + 8, s);
+    const double rr_true = read_scalar(pl, sc + 8, s);
+    // caller frame and order: w_user = rho^k w'
+    scatter_scaled<<<blocks_for(n, 256), 256, 0, s>>>(x, pl->ps.perm.get(), n, std::pow(pl->ps.frame.rho, (double)pl->k),
+                                                       w_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        info->iters = iters;
+        info->outer_iters = outer;
+        info->converged = converged ? 1 : 0;
+        info->jittered = (int)pl->vec.jittered;
+        info->rel_res_recursive = nrm0 > 0 ? std::sqrt(rr) / nrm0 : 0.0;
+        info->rel_res_true = nrm0 > 0 ? std::sqrt(rr_true) / nrm0 : 0.0;
+        info->ms_plan = pl->ms_plan;
+        info->ms_fit = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        info->ms_matvec_avg = n_mv ? (float)(ms_mv / n_mv) : 0.0f;
+    }
+    if (!converged) throw phs::Error{PHS_ERR_NOT_CONVERGED, "PCG did not reach the tolerance"};
+    PHS_CATCH
+}
+
+phs_status phs_eval(phs_plan_t pl, const double *w_dev, const double *beta_dev, const double *tgt_dev, int64_t m,
+                    double *out_dev, phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pl && w_dev && beta_dev && out_dev && (tgt_dev || m == 0) && m >= 0, PHS_ERR_INVALID_ARG,
+                "bad arguments");
+    if (m == 0) return PHS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = pl->ps.n;
+    double *ws = W(pl, 8);
+    // w' = rho^-k w_user in sorted order
+    gather_scaled<<<blocks_for(n, 256), 256, 0, s>>>(w_dev, pl->ps.perm.get(), n, std::pow(pl->ps.frame.rho, -(double)pl->k),
+                                                      ws);
+    PHS_LAUNCH_CHECK();
+    DBuf<double2> yn(m);
+    const Frame &fr = pl->ps.frame;
+    norm_targets<<<blocks_for(m, 256), 256, 0, s>>>(tgt_dev, m, fr.cx, fr.cy, fr.rho, yn.get());
+    PHS_LAUNCH_CHECK();
+    fmm_eval64(pl->fmm, pl->tree, pl->ps, ws, yn.get(), m, out_dev, s, &pl->tm);
+    add_poly<<<blocks_for(m, 256), 256, 0, s>>>(yn.get(), m, pl->deg, pl->S, beta_dev, out_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_CATCH
+}
+
+phs_status phs_fit_predict_host(const double *pts_host, const double *f_host, int64_t n, const double *tgt_host,
+                                int64_t m, int k, int poly_degree, int fmm_order, int vecchia_m, const phs_options *opt,
+                                double *w_host, double *beta_host, double *pred_host, phs_fit_info *info,
+                                phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pts_host && f_host && n > 0 && m >= 0 && (tgt_host || m == 0), PHS_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<double> pts(2 * n), f(n), w(n), beta(16), tgt(std::max<int64_t>(2 * m, 1)), pred(std::max<int64_t>(m, 1));
+    PHS_CUDA(cudaMemcpyAsync(pts.get(), pts_host, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.get(), f_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (m) PHS_CUDA(cudaMemcpyAsync(tgt.get(), tgt_host, 2 * m * sizeof(double), cudaMemcpyHostToDevice, s));
+    phs_plan_t pl = nullptr;
+    phs_status st = phs_plan_create(pts.get(), n, k, poly_degree, fmm_order, vecchia_m, opt, stream, &pl);
+    if (st != PHS_OK) return st;
+    phs_fit_info inf{};
+    st = phs_fit(pl, f.get(), w.get(), beta.get(), &inf, stream);
+    if (st != PHS_OK && st != PHS_ERR_NOT_CONVERGED) {
+        std::string msg = phs_last_error();
+        phs_plan_destroy(pl);
+        phs::set_error(msg);
+        return st;
+    }
+    const phs_status fit_st = st;
+    if (m) {
+        st = phs_eval(pl, w.get(), beta.get(), tgt.get(), m, pred.get(), stream);
+        if (st != PHS_OK) {
+            std::string msg = phs_last_error();
+            phs_plan_destroy(pl);
+            phs::set_error(msg);
+            return st;
+        }
+    }
+    if (w_host) PHS_CUDA(cudaMemcpyAsync(w_host, w.get(), n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (beta_host) PHS_CUDA(cudaMemcpyAsync(beta_host, beta.get(), pl->S * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (pred_host && m) PHS_CUDA(cudaMemcpyAsync(pred_host, pred.get(), m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    if (info) *info = inf;
+    phs_plan_destroy(pl);
+    if (fit_st != PHS_OK) {
+        phs::set_error("PCG did not reach the tolerance");
+        return fit_st;
+    }
+    PHS_CATCH
+}
+
+phs_status phs_plan_frame(phs_plan_t pl, double *frame_host, int64_t *sizes_host) {
+    PHS_TRY
+    PHS_REQUIRE(pl, PHS_ERR_INVALID_ARG, "null plan");
+    if (frame_host) {
+        frame_host[0] = pl->ps.frame.cx;
+        frame_host[1] = pl->ps.frame.cy;
+        frame_host[2] = pl->ps.frame.rho;
+        frame_host[3] = pl->ps.frame.hw;
+    }
+    if (sizes_host) {
+        sizes_host[0] = pl->ps.n;
+        sizes_host[1] = pl->k;
+        sizes_host[2] = pl->S;
+        sizes_host[3] = pl->p;
+        sizes_host[4] = pl->fmm.nd;
+        sizes_host[5] = pl->tree.nbox;
+        sizes_host[6] = pl->tree.nleaf;
+        sizes_host[7] = pl->tree.depth;
+    }
+    PHS_CATCH
+}
+
+phs_status phs_plan_vecchia(phs_plan_t pl, int64_t *order_host, int64_t *nbr_host) {
+    PHS_TRY
+    PHS_REQUIRE(pl, PHS_ERR_INVALID_ARG, "null plan");
+    const int64_t n = pl->ps.n;
+    const int m = pl->m;
+    if (order_host) {
+        // caller index of rank r = perm[order_pos[r]]
+        std::vector<int> ho(n), hp(n);
+        PHS_CUDA(cudaMemcpy(ho.data(), pl->vec.order.get(), n * sizeof(int), cudaMemcpyDeviceToHost));
+        PHS_CUDA(cudaMemcpy(hp.data(), pl->ps.perm.get(), n * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int64_t r = 0; r < n; ++r) order_host[r] = hp[ho[r]];
+    }
+    if (nbr_host) {
+        std::vector<int> ell((size_t)m * n), hp(n);
+        PHS_CUDA(cudaMemcpy(ell.data(), pl->vec.nbr.get(), ell.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        PHS_CUDA(cudaMemcpy(hp.data(), pl->ps.perm.get(), n * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int64_t p = 0; p < n; ++p)
+            for (int q = 0; q < m; ++q) {
+                const int v = ell[(size_t)q * n + p];
+                nbr_host[(int64_t)hp[p] * m + q] = v >= 0 ? hp[v] : -1;
+            }
+    }
+    PHS_CATCH
+}
+
+phs_status phs_plan_vecchia_factor(phs_plan_t pl, double *diag_host, double *offd_host) {
+    PHS_TRY
+    PHS_REQUIRE(pl, PHS_ERR_INVALID_ARG, "null plan");
+    const int64_t n = pl->ps.n;
+    const int m = pl->m;
+    std::vector<double> val((size_t)(m + 1) * n);
+    std::vector<int> hp(n);
+    PHS_CUDA(cudaMemcpy(val.data(), pl->vec.val.get(), val.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    PHS_CUDA(cudaMemcpy(hp.data(), pl->ps.perm.get(), n * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t p = 0; p < n; ++p) {
+        if (diag_host) diag_host[hp[p]] = val[p];
+        if (offd_host)
+            for (int q = 0; q < m; ++q) offd_host[(int64_t)hp[p] * m + q] = val[(size_t)(1 + q) * n + p];
+    }
+    PHS_CATCH
+}
+
+phs_status phs_plan_precond(phs_plan_t pl, const double *r_dev, double *z_dev, phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pl && r_dev && z_dev, PHS_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = pl->ps.n;
+    double *rs = W(pl, 8), *zs = W(pl, 9);
+    gather_vec<<<blocks_for(n, 256), 256, 0, s>>>(r_dev, pl->ps.perm.get(), n, rs);
+    PHS_LAUNCH_CHECK();
+    double *t1 = W(pl, 10), *t2 = W(pl, 11);
+    project(pl, rs, 1.0, t1, nullptr, nullptr, s);
+    precond(pl, t1, zs, rs, t2, s);
+    scatter_scaled<<<blocks_for(n, 256), 256, 0, s>>>(zs, pl->ps.perm.get(), n, 1.0, z_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CATCH
+}
+
+phs_status phs_plan_work(phs_plan_t pl, int64_t *counts_host) {
+    PHS_TRY
+    PHS_REQUIRE(pl && counts_host, PHS_ERR_INVALID_ARG, "bad arguments");
+    counts_host[0] = pl->tree.near_pairs;
+    counts_host[1] = pl->tree.m2l_pairs;
+    PHS_CATCH
+}
+
+phs_status phs_plan_set_timing(phs_plan_t pl, int enabled) {
+    PHS_TRY
+    PHS_REQUIRE(pl, PHS_ERR_INVALID_ARG, "null plan");
+    pl->tm.resolve();
+    pl->tm.enabled = enabled != 0;
+    pl->tm.reset();
+    PHS_CATCH
+}
+
+phs_status phs_plan_timing(phs_plan_t pl, double *ms_host, int64_t *calls_host) {
+    PHS_TRY
+    PHS_REQUIRE(pl, PHS_ERR_INVALID_ARG, "null plan");
+    pl->tm.resolve();
+    for (int i = 0; i < 8; ++i) {
+        if (ms_host) ms_host[i] = pl->tm.ms[i];
+        if (calls_host) calls_host[i] = pl->tm.calls[i];
+    }
+    PHS_CATCH
+}
+
+phs_status phs_dense_matvec(const double *pts_dev, int64_t n, int k, const double *t_dev, double *out_dev,
+                            phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pts_dev && t_dev && out_dev && n >= 0 && k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return PHS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<double2> x(n);
+    pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
+    PHS_LAUNCH_CHECK();
+    dense_matvec64(x.get(), n, k, t_dev, out_dev, s);
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_CATCH
+}
+
+phs_status phs_random_order(int64_t n, uint64_t seed, int64_t *order_dev, phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(order_dev && n >= 0 && n < (1ll << 31), PHS_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return PHS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<int> o(n);
+    random_order_dev(n, seed, o.get(), s);
+    to_i64<<<blocks_for(n, 256), 256, 0, s>>>(o.get(), n, order_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_CATCH
+}
+
+phs_status phs_maxmin_order(const double *pts_dev, int64_t n, int64_t *order_dev, phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pts_dev && order_dev && n >= 0 && n < (1ll << 31), PHS_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return PHS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<double2> x(n);
+    pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<int> o(n);
+    maxmin_order_dev(x.get(), n, o.get(), s);
+    to_i64<<<blocks_for(n, 256), 256, 0, s>>>(o.get(), n, order_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_CATCH
+}
+
+phs_status phs_knn_prev(const double *pts_dev, int64_t n, const int64_t *order_dev, int m, int64_t *nbr_dev,
+                        phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pts_dev && order_dev && nbr_dev && n >= 0 && n < (1ll << 31) && m >= 1 && m <= 64,
+                PHS_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return PHS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<double2> x(n);
+    pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<int> o(n), ell((size_t)m * n);
+    from_i64<<<blocks_for(n, 256), 256, 0, s>>>(order_dev, n, o.get());
+    PHS_LAUNCH_CHECK();
+    knn_prev_dev(x.get(), n, o.get(), m, ell.get(), s);
+    ell_to_rows_i64<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>(ell.get(), n, m, nbr_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_CATCH
+}
+
+phs_status phs_vecchia_factor(const double *pts_dev, int64_t n, const int64_t *order_dev, const int64_t *nbr_dev, int m,
+                              double nu, double alpha, double *diag_dev, double *offd_dev, int64_t *jittered_host,
+                              phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pts_dev && order_dev && nbr_dev && diag_dev && offd_dev && n >= 0 && m >= 1 && m <= 64,
+                PHS_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return PHS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<double2> x(n);
+    pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<int> o(n), rank(n), ell((size_t)m * n);
+    from_i64<<<blocks_for(n, 256), 256, 0, s>>>(order_dev, n, o.get());
+    PHS_LAUNCH_CHECK();
+    {
+        std::vector<int> ho(n), hr(n);
+        PHS_CUDA(cudaMemcpyAsync(ho.data(), o.get(), n * sizeof(int), cudaMemcpyDeviceToHost, s));
+        PHS_CUDA(cudaStreamSynchronize(s));
+        for (int64_t r = 0; r < n; ++r) hr[ho[r]] = (int)r;
+        PHS_CUDA(cudaMemcpyAsync(rank.get(), hr.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    rows_to_ell_i32<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>(nbr_dev, n, m, ell.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<double> val((size_t)(m + 1) * n);
+    int64_t nj = vecchia_factor_dev(x.get(), n, rank.get(), ell.get(), m, nu, alpha, val.get(), s);
+    PHS_CUDA(cudaMemcpyAsync(diag_dev, val.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    ell_to_rows_d<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>(val.get(), n, m, 1, offd_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+    if (jittered_host) *jittered_host = nj;
+    PHS_CATCH
+}
+
+}  // extern "C"

@@ -1,0 +1,688 @@
+// fmm.cu -- 2D fast multipole method for the PHS matvec (Sec. 2.1) through the
+// Hadamard/low-rank identity (Eq. 2.6):  M t = sum_l D_{u_l} M_core D_{v_l} t.
+//
+// Log core (even k): complex outgoing/incoming expansions (Eqs. 2.13-2.15) with
+// box-width scaled coefficients, so the translation operators are level
+// invariant:  a~_k = a_k / w^k,  b~_l = b_l w^l  (w = box width at the level).
+//   P2M  a_0 = sum q,  a~_k = -sum q zeta^k / k,           zeta = (z - c)/w
+//   M2M  a~'_l = -a_0 d^l / l + sum_{k<=l} a~_k 2^-k d^(l-k) C(l-1,k-1)   (d = child offset / w_parent)
+//   M2L  b~_0 = a_0 (log w + log(-o)) + sum_k a~_k (-1)^k o^-k
+//        b~_l = -a_0 / (l o^l) + o^-l sum_k a~_k (-1)^k C(l+k-1,k-1) o^-k (o = source offset / w)
+//   L2L  b~'_m = sum_{l>=m} b~_l C(l,m) d^(l-m) 2^-m
+//   L2P  Re sum_l b~_l v^l,  v = (z - c)/w
+// The near field (U, W and folded X lists) is summed directly with the full phi,
+// which equals the Hadamard sum restricted to those pairs.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "geom.cuh"
+#include "phs_internal.cuh"
+
+namespace phs {
+
+// ---------------------------------------------------------------- complex helpers
+template <typename T> struct C2T;
+template <> struct C2T<double> { using type = double2; };
+template <> struct C2T<float> { using type = float2; };
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C>
+__device__ __forceinline__ void cfma(C &acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// Hadamard factors of [|x_i - x_j|^power] (Sec. 2): u_l(x_i) v_l(x_j) summed over l.
+__device__ __forceinline__ void had_v(int power, double x, double y, double *v) {
+    const double a = x * x + y * y;
+    if (power == 0) {
+        v[0] = 1.0;
+    } else if (power == 2) {
+        v[0] = 1.0; v[1] = a; v[2] = x; v[3] = y;
+    } else {
+        v[0] = 1.0; v[1] = a * a; v[2] = a; v[3] = x; v[4] = y;
+        v[5] = a * x; v[6] = a * y; v[7] = x * x; v[8] = x * y; v[9] = y * y;
+    }
+}
+__device__ __forceinline__ void had_u(int power, double x, double y, double *u) {
+    const double a = x * x + y * y;
+    if (power == 0) {
+        u[0] = 1.0;
+    } else if (power == 2) {
+        u[0] = a; u[1] = 1.0; u[2] = -2.0 * x; u[3] = -2.0 * y;
+    } else {
+        u[0] = a * a; u[1] = 1.0; u[2] = 2.0 * a; u[3] = -4.0 * a * x; u[4] = -4.0 * a * y;
+        u[5] = -4.0 * x; u[6] = -4.0 * y; u[7] = 4.0 * x * x; u[8] = 8.0 * x * y; u[9] = 4.0 * y * y;
+    }
+}
+constexpr int kMaxNd = 10;
+constexpr int kMaxP = 61;
+
+__device__ __forceinline__ void box_geom(const TreeView &tv, int b, double &cx, double &cy, double &w) {
+    int ix, iy;
+    demorton(tv.key[b], ix, iy);
+    w = box_width(tv.R, tv.level[b]);
+    cx = -tv.R + (ix + 0.5) * w;
+    cy = -tv.R + (iy + 0.5) * w;
+}
+
+// ---------------------------------------------------------------- operators (host)
+// layout: slot s in [0,4) M2M quadrant, [4,8) L2L quadrant, [8,57) M2L class (dx+3)*7+(dy+3)
+constexpr int kSlots = 57;
+static std::vector<std::complex<long double>> build_ops(int P) {
+    using cx = std::complex<long double>;
+    std::vector<cx> ops((size_t)kSlots * P * P, cx(0, 0));
+    auto at = [&](int s, int r, int c) -> cx & { return ops[((size_t)s * P + r) * P + c]; };
+    // binomials up to 2P
+    std::vector<std::vector<long double>> C(2 * P + 1, std::vector<long double>(2 * P + 1, 0));
+    for (int a = 0; a <= 2 * P; ++a) {
+        C[a][0] = 1;
+        for (int b = 1; b <= a; ++b) C[a][b] = C[a - 1][b - 1] + (b <= a - 1 ? C[a - 1][b] : 0);
+    }
+    for (int q = 0; q < 4; ++q) {
+        cx d((q & 1) ? 0.25L : -0.25L, (q & 2) ? 0.25L : -0.25L);
+        // M2M
+        at(q, 0, 0) = 1;
+        for (int l = 1; l < P; ++l) {
+            at(q, l, 0) = -std::pow(d, l) / (long double)l;
+            for (int k = 1; k <= l; ++k)
+                at(q, l, k) = std::pow(0.5L, (long double)k) * std::pow(d, l - k) * C[l - 1][k - 1];
+        }
+        // L2L
+        for (int m = 0; m < P; ++m)
+            for (int l = m; l < P; ++l) at(4 + q, m, l) = C[l][m] * std::pow(d, l - m) * std::pow(0.5L, (long double)m);
+    }
+    for (int dx = -3; dx <= 3; ++dx)
+        for (int dy = -3; dy <= 3; ++dy) {
+            if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+            const int s = 8 + (dx + 3) * 7 + (dy + 3);
+            cx o((long double)dx, (long double)dy);
+            cx io = 1.0L / o;
+            at(s, 0, 0) = std::log(-o);
+            for (int l = 1; l < P; ++l) at(s, l, 0) = -std::pow(io, l) / (long double)l;
+            for (int l = 0; l < P; ++l)
+                for (int k = 1; k < P; ++k) {
+                    long double sg = (k % 2) ? -1.0L : 1.0L;
+                    at(s, l, k) = sg * C[l + k - 1][k - 1] * std::pow(io, l + k);
+                }
+        }
+    return ops;
+}
+
+// ---------------------------------------------------------------- kernels
+constexpr int FMM_T = 256;
+constexpr int OUT_PER_T = 3;  // nd * P <= 768
+
+template <typename T>
+__global__ void p2m_kernel(TreeView tv, const int *leaf_box, const double2 *xs, const double *t, int power, int nd,
+                           int P, typename C2T<T>::type *mp) {
+    using C = typename C2T<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *pw = reinterpret_cast<C *>(smem_raw);        // [32][P]
+    T *qs = reinterpret_cast<T *>(pw + 32 * P);     // [32][nd]
+    const int b = leaf_box[blockIdx.x];
+    double cx, cy, w;
+    box_geom(tv, b, cx, cy, w);
+    const double iw = 1.0 / w;
+    const int s = tv.start[b], e = tv.end[b];
+    C acc[OUT_PER_T];
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) acc[i].x = acc[i].y = T(0);
+    const int nout = nd * P;
+    for (int j0 = s; j0 < e; j0 += 32) {
+        if (threadIdx.x < 32) {
+            const int j = j0 + threadIdx.x;
+            C z1;
+            C zk;
+            zk.x = T(1); zk.y = T(0);
+            double v[kMaxNd];
+            if (j < e) {
+                const double2 xj = xs[j];
+                z1.x = T((xj.x - cx) * iw);
+                z1.y = T((xj.y - cy) * iw);
+                had_v(power, xj.x, xj.y, v);
+                const double tj = t[j];
+                for (int d = 0; d < nd; ++d) qs[threadIdx.x * nd + d] = T(v[d] * tj);
+            } else {
+                z1.x = z1.y = T(0);
+                for (int d = 0; d < nd; ++d) qs[threadIdx.x * nd + d] = T(0);
+            }
+            for (int k = 0; k < P; ++k) {
+                pw[threadIdx.x * P + k] = zk;
+                zk = cmul(zk, z1);
+            }
+        }
+        __syncthreads();
+        const int jn = min(32, e - j0);
+#pragma unroll
+        for (int i = 0; i < OUT_PER_T; ++i) {
+            const int o = threadIdx.x + i * FMM_T;
+            if (o < nout) {
+                const int d = o / P, k = o - d * P;
+                C a = acc[i];
+                for (int jj = 0; jj < jn; ++jj) {
+                    const T q = qs[jj * nd + d];
+                    const C z = pw[jj * P + k];
+                    a.x += q * z.x;
+                    a.y += q * z.y;
+                }
+                acc[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) {
+        const int o = threadIdx.x + i * FMM_T;
+        if (o < nout) {
+            const int d = o / P, k = o - d * P;
+            C a = acc[i];
+            if (k > 0) {
+                const T sc = T(-1) / T(k);
+                a.x *= sc;
+                a.y *= sc;
+            }
+            mp[((size_t)b * nd + d) * P + k] = a;
+        }
+    }
+}
+
+// M2M: parents of level l (all non-leaf boxes of that level)
+template <typename T>
+__global__ void m2m_kernel(TreeView tv, int b0, int nd, int P, const typename C2T<T>::type *ops,
+                           typename C2T<T>::type *mp) {
+    using C = typename C2T<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);  // [nd][P]
+    const int b = b0 + blockIdx.x;
+    const int nc = tv.nchild[b];
+    if (nc == 0) return;
+    const int nout = nd * P;
+    C acc[OUT_PER_T];
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) acc[i].x = acc[i].y = T(0);
+    for (int c = tv.child[b]; c < tv.child[b] + nc; ++c) {
+        for (int i = threadIdx.x; i < nout; i += blockDim.x) sm[i] = mp[(size_t)c * nout + i];
+        __syncthreads();
+        const int q = (int)(tv.key[c] & 3);
+        const C *A = ops + (size_t)q * P * P;
+#pragma unroll
+        for (int i = 0; i < OUT_PER_T; ++i) {
+            const int o = threadIdx.x + i * FMM_T;
+            if (o < nout) {
+                const int d = o / P, l = o - d * P;
+                C a = acc[i];
+                for (int k = 0; k <= l; ++k) cfma(a, A[l * P + k], sm[d * P + k]);
+                acc[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) {
+        const int o = threadIdx.x + i * FMM_T;
+        if (o < nout) mp[(size_t)b * nout + o] = acc[i];
+    }
+}
+
+// M2L over V lists for boxes [b0, b0 + gridDim.x)
+template <typename T>
+__global__ void m2l_kernel(TreeView tv, int b0, const int *v_off, const int *v_src, const unsigned char *v_cls, int nd,
+                           int P, const typename C2T<T>::type *ops, const typename C2T<T>::type *mp,
+                           typename C2T<T>::type *lc) {
+    using C = typename C2T<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);  // [nd][P]
+    const int b = b0 + blockIdx.x;
+    const int nout = nd * P;
+    const T logw = T(log(box_width(tv.R, tv.level[b])));
+    C acc[OUT_PER_T];
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) acc[i].x = acc[i].y = T(0);
+    for (int v = v_off[b]; v < v_off[b + 1]; ++v) {
+        const int src = v_src[v];
+        for (int i = threadIdx.x; i < nout; i += blockDim.x) sm[i] = mp[(size_t)src * nout + i];
+        __syncthreads();
+        const C *A = ops + (size_t)(8 + v_cls[v]) * P * P;
+#pragma unroll
+        for (int i = 0; i < OUT_PER_T; ++i) {
+            const int o = threadIdx.x + i * FMM_T;
+            if (o < nout) {
+                const int d = o / P, l = o - d * P;
+                C a = acc[i];
+                const C *Ar = A + l * P;
+                const C *mv = sm + d * P;
+                for (int k = 0; k < P; ++k) cfma(a, Ar[k], mv[k]);
+                if (l == 0) a.x += mv[0].x * logw;
+                acc[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) {
+        const int o = threadIdx.x + i * FMM_T;
+        if (o < nout) lc[(size_t)b * nout + o] = acc[i];
+    }
+}
+
+// L2L: boxes of one level receive their parent's local expansion
+template <typename T>
+__global__ void l2l_kernel(TreeView tv, int b0, int nd, int P, const typename C2T<T>::type *ops,
+                           typename C2T<T>::type *lc) {
+    using C = typename C2T<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int b = b0 + blockIdx.x;
+    const int par = tv.parent[b];
+    const int nout = nd * P;
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) sm[i] = lc[(size_t)par * nout + i];
+    __syncthreads();
+    const int q = (int)(tv.key[b] & 3);
+    const C *A = ops + (size_t)(4 + q) * P * P;
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) {
+        const int o = threadIdx.x + i * FMM_T;
+        if (o < nout) {
+            const int d = o / P, m = o - d * P;
+            C a = lc[(size_t)b * nout + o];
+            for (int l = m; l < P; ++l) cfma(a, A[m * P + l], sm[d * P + l]);
+            lc[(size_t)b * nout + o] = a;
+        }
+    }
+}
+
+// L2P + Hadamard combination: y_i += sum_d u_d(x_i) Re L_d(x_i)
+template <typename T>
+__global__ void l2p_kernel(TreeView tv, const int *leaf_box, const double2 *xs, int power, int nd, int P,
+                           const typename C2T<T>::type *lc, double *y) {
+    using C = typename C2T<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int b = leaf_box[blockIdx.x];
+    const int nout = nd * P;
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) sm[i] = lc[(size_t)b * nout + i];
+    __syncthreads();
+    double cx, cy, w;
+    box_geom(tv, b, cx, cy, w);
+    const double iw = 1.0 / w;
+    for (int j = tv.start[b] + threadIdx.x; j < tv.end[b]; j += blockDim.x) {
+        const double2 xj = xs[j];
+        C v;
+        v.x = T((xj.x - cx) * iw);
+        v.y = T((xj.y - cy) * iw);
+        double u[kMaxNd];
+        had_u(power, xj.x, xj.y, u);
+        double sum = 0.0;
+        for (int d = 0; d < nd; ++d) {
+            const C *L = sm + d * P;
+            C h = L[P - 1];
+            for (int l = P - 2; l >= 0; --l) {
+                C t2 = cmul(h, v);
+                h.x = t2.x + L[l].x;
+                h.y = t2.y + L[l].y;
+            }
+            sum += u[d] * (double)h.x;
+        }
+        y[j] += sum;
+    }
+}
+
+// near field: y_i = sum_{j in near(leaf(i)), j != i} phi(|x_i - x_j|) t_j  (full phi, Eq. 1.2)
+template <typename T, int K>
+__device__ __forceinline__ T phi_r2(T r2) {
+    if (K == 1) return sqrt(r2);
+    if (K == 2) return T(0.5) * r2 * log(r2);
+    if (K == 3) return r2 * sqrt(r2);
+    if (K == 4) return T(0.5) * r2 * r2 * log(r2);
+    return r2 * r2 * sqrt(r2);
+}
+template <>
+__device__ __forceinline__ float phi_r2<float, 2>(float r2) { return 0.5f * r2 * __logf(r2); }
+template <>
+__device__ __forceinline__ float phi_r2<float, 4>(float r2) { return 0.5f * r2 * r2 * __logf(r2); }
+
+constexpr int P2P_T = 128;
+template <typename T, int K>
+__global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, const int *leaf_box, const int *near_off,
+                                                   const int2 *near_rng, const double2 *xs, const double *t,
+                                                   double *y) {
+    __shared__ T sx[P2P_T], sy[P2P_T], st[P2P_T];
+    const int li = blockIdx.x;
+    const int b = leaf_box[li];
+    double cx, cy, w;
+    box_geom(tv, b, cx, cy, w);
+    const int s = tv.start[b], e = tv.end[b];
+    for (int i0 = s; i0 < e; i0 += P2P_T) {
+        const int i = i0 + threadIdx.x;
+        T xi = 0, yi = 0;
+        if (i < e) {
+            const double2 p = xs[i];
+            xi = T(p.x - cx);
+            yi = T(p.y - cy);
+        }
+        T acc = 0;
+        for (int r = near_off[li]; r < near_off[li + 1]; ++r) {
+            const int2 rg = near_rng[r];
+            for (int j0 = rg.x; j0 < rg.y; j0 += P2P_T) {
+                const int j = j0 + threadIdx.x;
+                __syncthreads();
+                if (j < rg.y) {
+                    const double2 p = xs[j];
+                    sx[threadIdx.x] = T(p.x - cx);
+                    sy[threadIdx.x] = T(p.y - cy);
+                    st[threadIdx.x] = T(t[j]);
+                }
+                __syncthreads();
+                const int jn = min(P2P_T, rg.y - j0);
+                for (int jj = 0; jj < jn; ++jj) {
+                    const T dx = xi - sx[jj], dy = yi - sy[jj];
+                    const T r2 = dx * dx + dy * dy;
+                    if (r2 > T(0)) acc += phi_r2<T, K>(r2) * st[jj];
+                }
+            }
+        }
+        if (i < e) y[i] = (double)acc;
+    }
+}
+
+// exact O(n^2) product, FP64
+template <int K>
+__global__ void dense_kernel(const double2 *x, int64_t n, const double *t, double *out) {
+    __shared__ double sx[256], sy[256], st[256];
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    double xi = 0, yi = 0;
+    if (i < n) { xi = x[i].x; yi = x[i].y; }
+    double acc = 0;
+    for (int64_t j0 = 0; j0 < n; j0 += 256) {
+        __syncthreads();
+        if (j0 + threadIdx.x < n) {
+            sx[threadIdx.x] = x[j0 + threadIdx.x].x;
+            sy[threadIdx.x] = x[j0 + threadIdx.x].y;
+            st[threadIdx.x] = t[j0 + threadIdx.x];
+        }
+        __syncthreads();
+        const int jn = (int)min((int64_t)256, n - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            const double dx = xi - sx[jj], dy = yi - sy[jj];
+            const double r2 = dx * dx + dy * dy;
+            if (r2 > 0) acc += phi_r2<double, K>(r2) * st[jj];
+        }
+    }
+    if (i < n) out[i] = acc;
+}
+
+template <typename T>
+typename C2T<T>::type *mp_buf(Fmm &f);
+template <>
+double2 *mp_buf<double>(Fmm &f) { return f.mp64.get(); }
+template <>
+float2 *mp_buf<float>(Fmm &f) { return f.mp32.get(); }
+template <typename T>
+typename C2T<T>::type *lc_buf(Fmm &f);
+template <>
+double2 *lc_buf<double>(Fmm &f) { return f.lc64.get(); }
+template <>
+float2 *lc_buf<float>(Fmm &f) { return f.lc32.get(); }
+template <typename T>
+const typename C2T<T>::type *ops_buf(const Fmm &f);
+template <>
+const double2 *ops_buf<double>(const Fmm &f) { return f.ops64.get(); }
+template <>
+const float2 *ops_buf<float>(const Fmm &f) { return f.ops32.get(); }
+
+template <typename T>
+static int P_of(const Fmm &f) { return sizeof(T) == 8 ? f.P : f.P32; }
+
+template <typename T>
+static void ensure_bufs(Fmm &f, const Tree &t) {
+    const size_t sz = (size_t)t.nbox * f.nd * P_of<T>(f);
+    if (sizeof(T) == 8) {
+        if (f.mp64.n != sz) { f.mp64.alloc(sz); f.lc64.alloc(sz); }
+    } else {
+        if (f.mp32.n != sz) { f.mp32.alloc(sz); f.lc32.alloc(sz); }
+    }
+}
+
+// upward pass, M2L and downward pass (local expansions of every box)
+template <typename T>
+static void far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, cudaStream_t s,
+                      Timers *tm) {
+    using C = typename C2T<T>::type;
+    ensure_bufs<T>(f, t);
+    C *mp = mp_buf<T>(f);
+    C *lc = lc_buf<T>(f);
+    const C *ops = ops_buf<T>(f);
+    TreeView tv = tree_view(t);
+    const int nd = f.nd, P = P_of<T>(f);
+    const size_t esz = (size_t)nd * P * sizeof(C);
+    if (tm) tm->begin(s);
+    const size_t p2m_smem = 32 * P * sizeof(C) + 32 * nd * sizeof(T);
+    p2m_kernel<T><<<t.nleaf, FMM_T, p2m_smem, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, nd, P, mp);
+    PHS_LAUNCH_CHECK();
+    for (int l = t.depth - 1; l >= 0; --l) {
+        const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
+        if (nb > 0) m2m_kernel<T><<<nb, FMM_T, esz, s>>>(tv, b0, nd, P, ops, mp);
+        PHS_LAUNCH_CHECK();
+    }
+    if (tm) tm->end(T_UP, s);
+    if (tm) tm->begin(s);
+    PHS_CUDA(cudaMemsetAsync(lc, 0, (size_t)t.nbox * esz, s));
+    if (t.depth >= 2) {
+        const int b0 = t.lvl_off[2], nb = t.nbox - b0;
+        if (nb > 0)
+            m2l_kernel<T><<<nb, FMM_T, esz, s>>>(tv, b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), nd, P, ops, mp,
+                                                 lc);
+        PHS_LAUNCH_CHECK();
+    }
+    if (tm) tm->end(T_M2L, s);
+    if (tm) tm->begin(s);
+    for (int l = 3; l <= t.depth; ++l) {
+        const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
+        if (nb > 0) l2l_kernel<T><<<nb, FMM_T, esz, s>>>(tv, b0, nd, P, ops, lc);
+        PHS_LAUNCH_CHECK();
+    }
+    if (tm) tm->end(T_DOWN, s);
+}
+
+template <typename T, int K>
+static void p2p_launch(const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s) {
+    p2p_kernel<T, K><<<t.nleaf, P2P_T, 0, s>>>(tree_view(t), t.leaf_box.get(), t.near_off.get(), t.near_rng.get(),
+                                               ps.xs.get(), tv_sorted, y);
+    PHS_LAUNCH_CHECK();
+}
+template <typename T>
+static void p2p_dispatch(int k, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s) {
+    switch (k) {
+        case 1: p2p_launch<T, 1>(t, ps, tv_sorted, y, s); break;
+        case 2: p2p_launch<T, 2>(t, ps, tv_sorted, y, s); break;
+        case 3: p2p_launch<T, 3>(t, ps, tv_sorted, y, s); break;
+        case 4: p2p_launch<T, 4>(t, ps, tv_sorted, y, s); break;
+        default: p2p_launch<T, 5>(t, ps, tv_sorted, y, s); break;
+    }
+}
+
+template <typename T>
+static void apply_t(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s,
+                    Timers *tm) {
+    PHS_REQUIRE(f.log_core, PHS_ERR_INVALID_ARG, "odd spline orders need the distance-kernel FMM");
+    if (tm) tm->begin(s);
+    p2p_dispatch<T>(f.k, t, ps, tv_sorted, y, s);
+    if (tm) tm->end(T_P2P, s);
+    far_field<T>(f, t, ps, tv_sorted, s, tm);
+    using C = typename C2T<T>::type;
+    if (tm) tm->begin(s);
+    l2p_kernel<T><<<t.nleaf, 128, (size_t)f.nd * P_of<T>(f) * sizeof(C), s>>>(
+        tree_view(t), t.leaf_box.get(), ps.xs.get(), f.power, f.nd, P_of<T>(f), lc_buf<T>(f), y);
+    PHS_LAUNCH_CHECK();
+    if (tm) tm->end(T_DOWN, s);
+}
+
+void fmm_setup(Fmm &f, int k, int p, int p32, const Tree &t, cudaStream_t s) {
+    PHS_REQUIRE(k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "k must be in 1..5");
+    PHS_REQUIRE(p >= 2 && p + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "fmm_order must be in 2..60");
+    PHS_REQUIRE(p32 >= 2 && p32 + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "FP32 fmm order must be in 2..60");
+    f.k = k;
+    f.p = p;
+    f.P = p + 1;
+    f.p32 = p32;
+    f.P32 = p32 + 1;
+    f.log_core = (k % 2 == 0);
+    f.power = f.log_core ? k : k - 1;
+    f.nd = f.power == 0 ? 1 : (f.power == 2 ? 4 : 10);
+    PHS_REQUIRE(f.nd * f.P <= FMM_T * OUT_PER_T, PHS_ERR_INVALID_ARG, "fmm_order too large for this spline order");
+    auto ops = build_ops(f.P);
+    auto opsf = build_ops(f.P32);
+    std::vector<double2> o64(ops.size());
+    std::vector<float2> o32(opsf.size());
+    for (size_t i = 0; i < ops.size(); ++i) o64[i] = make_double2((double)ops[i].real(), (double)ops[i].imag());
+    for (size_t i = 0; i < opsf.size(); ++i) o32[i] = make_float2((float)opsf[i].real(), (float)opsf[i].imag());
+    f.ops64.alloc(o64.size());
+    f.ops32.alloc(o32.size());
+    PHS_CUDA(cudaMemcpyAsync(f.ops64.get(), o64.data(), o64.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.ops32.get(), o32.data(), o32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    (void)t;
+}
+
+void fmm_apply64(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, cudaStream_t s,
+                 Timers *tm) {
+    apply_t<double>(f, t, ps, t_sorted, y, s, tm);
+}
+void fmm_apply32(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, cudaStream_t s,
+                 Timers *tm) {
+    apply_t<float>(f, t, ps, t_sorted, y, s, tm);
+}
+
+// ---------------------------------------------------------------- evaluation at targets
+// One thread per target: deepest box containing it, L2P of that box's local
+// expansion, direct sum over its near set (same construction as the leaf lists).
+template <int K>
+__global__ void eval_kernel(TreeView tv, const double2 *xs, const double *w, const double2 *tgt, int64_t m, int power,
+                            int nd, int P, const double2 *lc, double *out, int *outside) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double2 y = tgt[i];
+    const double R = tv.R;
+    if (!(y.x >= -R && y.x <= R && y.y >= -R && y.y <= R)) {
+        outside[i] = 1;
+        out[i] = 0.0;
+        return;
+    }
+    outside[i] = 0;
+    const int L = tv.depth;
+    const double wl = box_width(R, L);
+    long long ix = (long long)floor((y.x + R) / wl), iy = (long long)floor((y.y + R) / wl);
+    const long long lim = (1ll << L) - 1;
+    ix = ix < 0 ? 0 : (ix > lim ? lim : ix);
+    iy = iy < 0 ? 0 : (iy > lim ? lim : iy);
+    const int b = find_deepest(tv, L, (int)ix, (int)iy);
+    double acc = 0.0;
+    enumerate_near(tv, b, [&](int s, int e) {
+        for (int j = s; j < e; ++j) {
+            const double dx = y.x - xs[j].x, dy = y.y - xs[j].y;
+            const double r2 = dx * dx + dy * dy;
+            if (r2 > 0) acc += phi_r2<double, K>(r2) * w[j];
+        }
+    });
+    if (tv.level[b] >= 2) {
+        double cx, cy, bw;
+        box_geom(tv, b, cx, cy, bw);
+        double2 v = make_double2((y.x - cx) / bw, (y.y - cy) / bw);
+        double u[kMaxNd];
+        had_u(power, y.x, y.y, u);
+        const double2 *Lb = lc + (size_t)b * nd * P;
+        for (int d = 0; d < nd; ++d) {
+            const double2 *Ld = Lb + d * P;
+            double2 h = Ld[P - 1];
+            for (int l = P - 2; l >= 0; --l) {
+                double2 t2 = cmul(h, v);
+                h.x = t2.x + Ld[l].x;
+                h.y = t2.y + Ld[l].y;
+            }
+            acc += u[d] * h.x;
+        }
+    }
+    out[i] = acc;
+}
+
+// direct sum over all sources for targets outside the root box (block per target)
+template <int K>
+__global__ void eval_outside_kernel(const double2 *xs, int64_t n, const double *w, const double2 *tgt, int64_t m,
+                                    const int *outside, double *out) {
+    const int64_t i = blockIdx.x;
+    if (i >= m || !outside[i]) return;
+    const double2 y = tgt[i];
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double dx = y.x - xs[j].x, dy = y.y - xs[j].y;
+        const double r2 = dx * dx + dy * dy;
+        if (r2 > 0) acc += phi_r2<double, K>(r2) * w[j];
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = red[0];
+}
+
+template <int K>
+static void eval_launch(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted, const double2 *tgt, int64_t m,
+                        double *out, cudaStream_t s) {
+    DBuf<int> outside(std::max<int64_t>(m, 1));
+    eval_kernel<K><<<blocks_for(m, 128), 128, 0, s>>>(tree_view(t), ps.xs.get(), w_sorted, tgt, m, f.power, f.nd, f.P,
+                                                      f.lc64.get(), out, outside.get());
+    PHS_LAUNCH_CHECK();
+    eval_outside_kernel<K><<<(unsigned)std::max<int64_t>(m, 1), 256, 0, s>>>(ps.xs.get(), ps.n, w_sorted, tgt, m,
+                                                                              outside.get(), out);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+}
+
+void fmm_eval64(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted, const double2 *tgt, int64_t m,
+                double *out, cudaStream_t s, Timers *tm) {
+    PHS_REQUIRE(f.log_core, PHS_ERR_INVALID_ARG, "odd spline orders need the distance-kernel FMM");
+    far_field<double>(f, t, ps, w_sorted, s, nullptr);
+    if (tm) tm->begin(s);
+    switch (f.k) {
+        case 1: eval_launch<1>(f, t, ps, w_sorted, tgt, m, out, s); break;
+        case 2: eval_launch<2>(f, t, ps, w_sorted, tgt, m, out, s); break;
+        case 3: eval_launch<3>(f, t, ps, w_sorted, tgt, m, out, s); break;
+        case 4: eval_launch<4>(f, t, ps, w_sorted, tgt, m, out, s); break;
+        default: eval_launch<5>(f, t, ps, w_sorted, tgt, m, out, s); break;
+    }
+    if (tm) tm->end(T_EVAL, s);
+}
+
+void dense_matvec64(const double2 *x, int64_t n, int k, const double *t, double *out, cudaStream_t s) {
+    const unsigned nb = blocks_for(n, 256);
+    switch (k) {
+        case 1: dense_kernel<1><<<nb, 256, 0, s>>>(x, n, t, out); break;
+        case 2: dense_kernel<2><<<nb, 256, 0, s>>>(x, n, t, out); break;
+        case 3: dense_kernel<3><<<nb, 256, 0, s>>>(x, n, t, out); break;
+        case 4: dense_kernel<4><<<nb, 256, 0, s>>>(x, n, t, out); break;
+        default: dense_kernel<5><<<nb, 256, 0, s>>>(x, n, t, out); break;
+    }
+    PHS_LAUNCH_CHECK();
+}
+
+}  // namespace phs

@@ -1,0 +1,196 @@
+// phs_internal.cuh -- shared declarations of the CUDA implementation (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/phs.h"
+
+namespace phs {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    phs_status code;
+    std::string msg;
+};
+void set_error(const std::string &msg);
+const char *last_error();
+
+#define PHS_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            throw ::phs::Error{e_ == cudaErrorMemoryAllocation ? PHS_ERR_OOM : PHS_ERR_CUDA, \
+                               std::string(#call) + ": " + cudaGetErrorString(e_)};    \
+        }                                                                               \
+    } while (0)
+#define PHS_LAUNCH_CHECK() PHS_CUDA(cudaGetLastError())
+#define PHS_REQUIRE(cond, code, msg)                                                    \
+    do {                                                                                \
+        if (!(cond)) throw ::phs::Error{code, msg};                                     \
+    } while (0)
+
+inline unsigned blocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------- device buffers
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    explicit DBuf(size_t count) { alloc(count); }
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        if (count) PHS_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+        n = count;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    T *get() const { return p; }
+};
+
+// ---------------------------------------------------------------- primitives (sort_scan.cu)
+// exclusive scan of int32 counts; returns total (synchronises stream)
+int64_t exclusive_scan_i32(const int *in, int *out, int64_t n, cudaStream_t s);
+// stable LSD radix sort of (key, value) pairs on the low `bits` bits of key
+void radix_sort_pairs(uint64_t *keys, int *vals, int64_t n, int bits, cudaStream_t s);
+
+// ---------------------------------------------------------------- tree (tree.cu)
+constexpr int kMaxLevel = 20;  // quadtree levels 0..kMaxLevel
+
+struct Frame {
+    double cx = 0, cy = 0, rho = 1, hw = 0.25;  // x' = (x - c) * rho in [-hw, hw]^2
+};
+
+struct Tree {
+    int64_t n = 0;
+    int leaf_cap = 64;
+    int depth = 0;                   // deepest level present
+    int nbox = 0, nleaf = 0;
+    double R = 0.25;                 // root box [-R, R]^2
+    std::vector<int> lvl_off;        // boxes of level l: [lvl_off[l], lvl_off[l+1])
+    DBuf<int> lvl_dev;               // device copy of lvl_off
+    DBuf<int> start, end, parent, child, nchild, level;
+    DBuf<uint64_t> key;              // Morton key of the box at its own level
+    DBuf<int> leaf_box;              // leaf list
+    DBuf<int> point_leaf;            // leaf index of each (sorted) point
+    DBuf<int> v_off, v_src;          // V (M2L) lists per box (CSR)
+    DBuf<unsigned char> v_cls;       // offset class (dx+3)*7 + (dy+3)
+    DBuf<int> near_off;              // near (direct) ranges per leaf (CSR)
+    DBuf<int2> near_rng;
+    int64_t near_pairs = 0, m2l_pairs = 0;
+};
+
+struct PointSet {
+    int64_t n = 0;
+    Frame frame;
+    DBuf<double2> xs;  // normalised coordinates, Morton order
+    DBuf<int> perm;    // perm[p] = caller index of sorted position p
+    DBuf<int> iperm;   // iperm[i] = sorted position of caller index i
+};
+
+// normalise caller points, Morton-sort them and build the adaptive quadtree + lists
+void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, int leaf_cap,
+                           PointSet &ps, Tree &tree, cudaStream_t s);
+// device view of the tree for kernels
+struct TreeView {
+    const int *start, *end, *parent, *child, *nchild, *level;
+    const uint64_t *key;
+    const int *lvl_off;  // device copy
+    int depth;
+    double R;
+};
+TreeView tree_view(const Tree &t);
+
+// ---------------------------------------------------------------- FMM (fmm.cu)
+struct FmmOps;  // translation operators for one precision
+struct Fmm {
+    int k = 2, p = 20, P = 21, nd = 4;  // P = p + 1 coefficients (FP64 expansions)
+    int p32 = 20, P32 = 21;             // FP32 expansions
+    int power = 2;                      // r^{power} Hadamard factor, 0 for k = 1
+    bool log_core = true;               // log kernel (even k) or distance kernel (odd k)
+    // expansions (complex, [box][nd][P]); double and float variants allocated on demand
+    DBuf<double2> mp64, lc64;
+    DBuf<float2> mp32, lc32;
+    DBuf<double2> ops64;  // M2M[4], L2L[4], M2L[49] (P x P each)
+    DBuf<float2> ops32;
+    DBuf<int> lvl_off_dev;
+    // Chebyshev (distance kernel) data
+    int cheb_q = 0;                      // nodes per dimension
+    DBuf<double> cheb64;                 // operators
+    DBuf<float> cheb32;
+    DBuf<double> cw64, cl64;             // weights/potentials at nodes [box][nd][q*q]
+    DBuf<float> cw32, cl32;
+};
+void fmm_setup(Fmm &f, int k, int p, int p32, const Tree &t, cudaStream_t s);
+// y = M' t for sorted-order vectors in the normalised frame (M' of the normalised points)
+void fmm_apply64(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted,
+                 cudaStream_t s, struct Timers *tm);
+void fmm_apply32(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted,
+                 cudaStream_t s, struct Timers *tm);
+// evaluate sum_j w_j phi(|x_j - y|) at normalised targets (after an FMM upward/downward
+// pass on w), out written (overwritten) for m targets
+void fmm_eval64(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted,
+                const double2 *tgt_norm, int64_t m, double *out, cudaStream_t s, struct Timers *tm);
+// exact all-pairs product out = M t (points in any order, FP64)
+void dense_matvec64(const double2 *x, int64_t n, int k, const double *t, double *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- timers
+// Per-phase device time from CUDA events recorded on the launching stream; events
+// are resolved lazily (resolve()) so timing adds no host synchronisation.
+struct EvRec {
+    cudaEvent_t a, b;
+    int phase;
+};
+struct Timers {
+    bool enabled = false;
+    double ms[8] = {0};
+    int64_t calls[8] = {0};
+    std::vector<cudaEvent_t> stack;
+    std::vector<EvRec> pending;
+    void begin(cudaStream_t s);
+    void end(int phase, cudaStream_t s);
+    void resolve();
+    void reset() { for (int i = 0; i < 8; ++i) { ms[i] = 0; calls[i] = 0; } }
+    ~Timers();
+};
+enum { T_P2P = 0, T_M2L = 1, T_UP = 2, T_DOWN = 3, T_PRECOND = 4, T_VEC = 5, T_EVAL = 6, T_TOTAL = 7 };
+
+// ---------------------------------------------------------------- Vecchia (vecchia.cu)
+struct Vecchia {
+    int m = 0;
+    int64_t n = 0;
+    DBuf<int> rank;       // rank of sorted position p
+    DBuf<int> order;      // order[r] = sorted position of rank r
+    DBuf<int> nbr;        // ELL [m][n] sorted positions of neighbours (-1 pad)
+    DBuf<double> val;     // ELL [m+1][n]: slot 0 = 1/c, slot 1+q = -lambda_q/c
+    DBuf<int> t_off, t_col;  // transpose (CSR by row) of U~
+    DBuf<double> t_val;
+    int64_t jittered = 0;
+};
+void random_order_dev(int64_t n, uint64_t seed, int *order_out, cudaStream_t s);
+void maxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t s);
+void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr_ell, cudaStream_t s);
+int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m,
+                           double nu, double alpha, double *val_ell, cudaStream_t s);
+void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t seed, double nu,
+                   double alpha, cudaStream_t s);
+// z = U~ (U~' r) (sorted order)
+void vecchia_apply(const Vecchia &v, const double *r, double *tmp, double *z, cudaStream_t s);
+
+}  // namespace phs

@@ -1,0 +1,603 @@
+// vecchia.cu -- Vecchia sparse inverse-Cholesky preconditioner (Sec. 2.2, Eq. 2.19, Fig. 1):
+// enumeration, previous-point neighbour search, per-point local Cholesky factors,
+// the transposed factor and the apply z = U~ (U~' r).
+#include <algorithm>
+#include <cmath>
+
+#include "phs_internal.cuh"
+
+namespace phs {
+namespace {
+
+// SplitMix64 output i for a seed (Steele, Lea & Flood 2014)
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void rand_keys(int64_t n, uint64_t seed, uint64_t *keys, int *vals) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = splitmix64(seed, (uint64_t)i);
+    vals[i] = (int)i;
+}
+
+// squared distance with two roundings per product and one for the sum (no FMA)
+__device__ __forceinline__ double sqd(double2 a, double2 b) {
+    const double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+__global__ void ranks_from_order(const int *order, int64_t n, int *rank) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) rank[order[r]] = (int)r;
+}
+
+__global__ void gather_xy(const double2 *x, const int *idx, int64_t n, double2 *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = x[idx[i]];
+}
+
+// ---------------------------------------------------------------- neighbour grid
+struct Grid {
+    double x0, y0, cw;
+    int G;
+};
+
+__global__ void grid_keys(const double2 *x, const int *rank, int64_t n, Grid g, uint64_t *keys, int *vals) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cx = (int)floor((x[i].x - g.x0) / g.cw), cy = (int)floor((x[i].y - g.y0) / g.cw);
+    cx = min(max(cx, 0), g.G - 1);
+    cy = min(max(cy, 0), g.G - 1);
+    keys[i] = ((uint64_t)(cy * g.G + cx) << 32) | (uint64_t)(uint32_t)rank[i];
+    vals[i] = (int)i;
+}
+
+__global__ void cell_starts(const uint64_t *keys, int64_t n, int ncell, int *start) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncell) return;
+    const uint64_t v = (uint64_t)c << 32;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    start[c] = (int)lo;
+}
+
+__global__ void cell_payload(const uint64_t *keys, const int *vals, const double2 *x, int64_t n, double2 *xc, int *rc) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    xc[s] = x[vals[s]];
+    rc[s] = (int)(keys[s] & 0xffffffffu);
+}
+
+constexpr int KNN_MAXM = 64;
+
+struct TopM {
+    double d[KNN_MAXM];
+    int r[KNN_MAXM];
+    int cnt;
+    int cap;
+    __device__ void consider(double dv, int q) {
+        if (cnt == cap && !(dv < d[cap - 1] || (dv == d[cap - 1] && q < r[cap - 1]))) return;
+        int pos = cnt < cap ? cnt : cap - 1;
+        while (pos > 0 && (dv < d[pos - 1] || (dv == d[pos - 1] && q < r[pos - 1]))) {
+            d[pos] = d[pos - 1];
+            r[pos] = r[pos - 1];
+            --pos;
+        }
+        d[pos] = dv;
+        r[pos] = q;
+        if (cnt < cap) ++cnt;
+    }
+};
+
+// thread per rank r: the min(m, r) nearest points of smaller rank, by (d2, rank)
+__global__ void knn_kernel(const double2 *x_by_rank, int64_t n, int m, int brute, Grid g, const int *cstart,
+                           const double2 *xc, const int *rc, const int *order, int *nbr_ell) {
+    const int64_t r64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r64 >= n) return;
+    const int r = (int)r64;
+    const double2 p = x_by_rank[r];
+    TopM top;
+    top.cnt = 0;
+    top.cap = m;
+    const int need = min(m, r);
+    if (need > 0) {
+        if (r <= brute) {
+            for (int q = 0; q < r; ++q) top.consider(sqd(p, x_by_rank[q]), q);
+        } else {
+            int cx0 = (int)floor((p.x - g.x0) / g.cw), cy0 = (int)floor((p.y - g.y0) / g.cw);
+            cx0 = min(max(cx0, 0), g.G - 1);
+            cy0 = min(max(cy0, 0), g.G - 1);
+            for (int k = 0;; ++k) {
+                const int xa = cx0 - k, xb = cx0 + k, ya = cy0 - k, yb = cy0 + k;
+                for (int cy = max(ya, 0); cy <= min(yb, g.G - 1); ++cy) {
+                    const bool edge_row = (cy == ya || cy == yb);
+                    for (int cx = max(xa, 0); cx <= min(xb, g.G - 1); ++cx) {
+                        if (!edge_row && cx != xa && cx != xb) continue;
+                        const int c = cy * g.G + cx;
+                        for (int s2 = cstart[c]; s2 < cstart[c + 1]; ++s2) {
+                            const int q = rc[s2];
+                            if (q >= r) break;
+                            top.consider(sqd(p, xc[s2]), q);
+                        }
+                    }
+                }
+                const bool all = xa <= 0 && ya <= 0 && xb >= g.G - 1 && yb >= g.G - 1;
+                if (all) break;
+                if (top.cnt >= need) {
+                    double dm = INFINITY;
+                    if (xa > 0) dm = fmin(dm, p.x - (g.x0 + xa * g.cw));
+                    if (xb < g.G - 1) dm = fmin(dm, (g.x0 + (xb + 1) * g.cw) - p.x);
+                    if (ya > 0) dm = fmin(dm, p.y - (g.y0 + ya * g.cw));
+                    if (yb < g.G - 1) dm = fmin(dm, (g.y0 + (yb + 1) * g.cw) - p.y);
+                    if (dm > 0 && dm * dm * (1.0 - 1e-12) > top.d[need - 1]) break;
+                }
+            }
+        }
+    }
+    const int i = order[r];
+    for (int s2 = 0; s2 < m; ++s2) nbr_ell[(int64_t)s2 * n + i] = s2 < top.cnt ? order[top.r[s2]] : -1;
+}
+
+// ---------------------------------------------------------------- Matern covariance, K(0) = 1
+// K_1 by the ascending series (DLMF 10.31.1) for x <= 2 and the trapezoidal rule on
+// K_1(x) = int_0^inf exp(-x cosh t) cosh t dt (DLMF 10.32.9) for x > 2.
+__device__ double bessel_k1(double x) {
+    if (x <= 2.0) {
+        const double eg = 0.57721566490153286061;
+        const double q = 0.25 * x * x;
+        double term = 1.0, hk = 0.0, si = 0.0, sp = 0.0;
+        for (int k = 0; k < 40; ++k) {
+            if (k > 0) {
+                term *= q / ((double)k * (double)(k + 1));
+                hk += 1.0 / k;
+            }
+            const double p1 = -eg + hk, p2 = p1 + 1.0 / (k + 1);
+            si += term;
+            sp += (p1 + p2) * term;
+            if (term < 1e-20 * si) break;
+        }
+        return 1.0 / x + log(0.5 * x) * (0.5 * x * si) - 0.25 * x * sp;
+    }
+    const double h = 0.25;
+    double s = 0.5 * exp(-x);
+    for (int j = 1; j < 200; ++j) {
+        const double t = j * h, ch = cosh(t);
+        const double f = exp(-x * ch) * ch;
+        s += f;
+        if (f < 1e-19 * s) break;
+    }
+    return h * s;
+}
+
+__device__ __forceinline__ double matern(double nu, double alpha, double r) {
+    const double a = alpha * r;
+    if (a == 0.0) return 1.0;
+    if (nu == 0.5) return exp(-a);
+    if (nu == 1.5) return (1.0 + a) * exp(-a);
+    if (nu == 2.5) return (1.0 + a + a * a / 3.0) * exp(-a);
+    return a * bessel_k1(a);  // nu == 1
+}
+
+// warp per point: local Cholesky of K(X_sigma, X_sigma), lambda, c (Eq. 2.19)
+__global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, double nu,
+                              double alpha, double *val_ell, unsigned long long *njit, unsigned long long *nfail) {
+    extern __shared__ double fsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int per = m * m + 3 * m + 1;
+    double *A = fsm + (size_t)wib * per;
+    double *kv = A + m * m;
+    double *X = kv + m;
+    double *Y = X + m;
+    volatile double *flag = Y + m;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (i >= n) return;
+    const int s = min(m, rank[i]);
+    const double2 xi = x[i];
+    for (int a = lane; a < s; a += 32) {
+        const int j = nbr_ell[(int64_t)a * n + i];
+        X[a] = x[j].x;
+        Y[a] = x[j].y;
+    }
+    __syncwarp();
+    bool ok = false;
+    int tries = 0;
+    for (int t = 0; t <= 5 && !ok; ++t) {
+        const double jit = t == 0 ? 0.0 : 1e-12 * pow(10.0, (double)(t - 1));
+        for (int idx = lane; idx < s * s; idx += 32) {
+            const int a = idx / s, b = idx - a * s;
+            if (b <= a) {
+                const double dx = X[a] - X[b], dy = Y[a] - Y[b];
+                A[a * m + b] = matern(nu, alpha, sqrt(dx * dx + dy * dy)) + (a == b ? jit : 0.0);
+            }
+        }
+        __syncwarp();
+        ok = true;
+        for (int j = 0; j < s; ++j) {
+            if (lane == 0) {
+                const double d = A[j * m + j];
+                flag[0] = d > 0.0 ? 1.0 : 0.0;
+                if (d > 0.0) A[j * m + j] = sqrt(d);
+            }
+            __syncwarp();
+            if (flag[0] == 0.0) { ok = false; break; }
+            const double djj = A[j * m + j];
+            for (int a = j + 1 + lane; a < s; a += 32) A[a * m + j] /= djj;
+            __syncwarp();
+            for (int a = j + 1 + lane; a < s; a += 32) {
+                const double laj = A[a * m + j];
+                for (int c = j + 1; c <= a; ++c) A[a * m + c] -= laj * A[c * m + j];
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+        if (!ok) ++tries;
+    }
+    if (!ok) {
+        if (lane == 0) atomicAdd(nfail, 1ull);
+        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = 0.0;
+        return;
+    }
+    if (tries > 0 && lane == 0) atomicAdd(njit, 1ull);
+    for (int a = lane; a < s; a += 32) {
+        const double dx = X[a] - xi.x, dy = Y[a] - xi.y;
+        kv[a] = matern(nu, alpha, sqrt(dx * dx + dy * dy));
+    }
+    __syncwarp();
+    for (int c = 0; c < s; ++c) {  // L y = k
+        const double yc = kv[c] / A[c * m + c];
+        __syncwarp();
+        if (lane == 0) kv[c] = yc;
+        for (int a = c + 1 + lane; a < s; a += 32) kv[a] -= A[a * m + c] * yc;
+        __syncwarp();
+    }
+    double part = 0.0;
+    for (int a = lane; a < s; a += 32) part += kv[a] * kv[a];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const double c2 = 1.0 - part;
+    for (int c = s - 1; c >= 0; --c) {  // L' lambda = y
+        const double lc = kv[c] / A[c * m + c];
+        __syncwarp();
+        if (lane == 0) kv[c] = lc;
+        for (int a = lane; a < c; a += 32) kv[a] -= A[c * m + a] * lc;
+        __syncwarp();
+    }
+    if (!(c2 > 0.0)) {
+        if (lane == 0) atomicAdd(nfail, 1ull);
+        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = 0.0;
+        return;
+    }
+    const double ic = 1.0 / sqrt(c2);
+    if (lane == 0) val_ell[i] = ic;
+    for (int q = lane; q < m; q += 32) val_ell[(int64_t)(1 + q) * n + i] = q < s ? -kv[q] * ic : 0.0;
+}
+
+// ---------------------------------------------------------------- transpose of U~ (rows of U~)
+__global__ void t_count(const int *nbr_ell, int64_t n, int m, int *cnt) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    atomicAdd(&cnt[j], 1);
+    for (int q = 0; q < m; ++q) {
+        const int r = nbr_ell[(int64_t)q * n + j];
+        if (r >= 0) atomicAdd(&cnt[r], 1);
+    }
+}
+__global__ void t_fill(const int *nbr_ell, const double *val_ell, int64_t n, int m, const int *off, int *cur, int *col,
+                       double *val) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int pos = off[j] + atomicAdd(&cur[j], 1);
+    col[pos] = (int)j;
+    val[pos] = val_ell[j];
+    for (int q = 0; q < m; ++q) {
+        const int r = nbr_ell[(int64_t)q * n + j];
+        if (r >= 0) {
+            pos = off[r] + atomicAdd(&cur[r], 1);
+            col[pos] = (int)j;
+            val[pos] = val_ell[(int64_t)(1 + q) * n + j];
+        }
+    }
+}
+// deterministic order within each row (by column)
+__global__ void t_sort_rows(const int *off, int64_t n, int *col, double *val) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = off[i] + 1; a < off[i + 1]; ++a) {
+        const int c = col[a];
+        const double v = val[a];
+        int b = a - 1;
+        while (b >= off[i] && col[b] > c) {
+            col[b + 1] = col[b];
+            val[b + 1] = val[b];
+            --b;
+        }
+        col[b + 1] = c;
+        val[b + 1] = v;
+    }
+}
+
+// y = U~' r  (column j of U~ dotted with r)
+__global__ void apply_ut(const int *nbr_ell, const double *val_ell, int64_t n, int m, const double *r, double *y) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double acc = val_ell[j] * r[j];
+    for (int q = 0; q < m; ++q) {
+        const int c = nbr_ell[(int64_t)q * n + j];
+        if (c >= 0) acc += val_ell[(int64_t)(1 + q) * n + j] * r[c];
+    }
+    y[j] = acc;
+}
+// z = U~ y, warp per row of the transposed (CSR) factor
+__global__ void apply_u(const int *off, const int *col, const double *val, int64_t n, const double *y, double *z) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int e = off[i] + lane; e < off[i + 1]; e += 32) acc += val[e] * y[col[e]];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) z[i] = acc;
+}
+
+__global__ void ell_to_positions(int *nbr_ell, int64_t total, const int *iperm) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int v = nbr_ell[t];
+    if (v >= 0) nbr_ell[t] = iperm[v];
+}
+__global__ void permute_ell(const int *src, int64_t n, int slots, const int *perm, int *dst) {
+    // dst[s][p] = src[s][perm[p]]  (caller index -> sorted position columns)
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * slots) return;
+    const int64_t s2 = t / n, p = t - s2 * n;
+    dst[t] = src[s2 * n + perm[p]];
+}
+__global__ void permute_ell_d(const double *src, int64_t n, int slots, const int *perm, double *dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * slots) return;
+    const int64_t s2 = t / n, p = t - s2 * n;
+    dst[t] = src[s2 * n + perm[p]];
+}
+
+// Exact greedy maxmin in one block: first the point nearest the bounding-box centre,
+// then repeatedly argmax over unselected points of the squared distance to the
+// selected set; ties to the smaller index.  O(n^2 / blockDim) work.
+constexpr int MM_T = 1024;
+__global__ void __launch_bounds__(MM_T) maxmin_block(const double2 *x, int64_t n, double *dmin, unsigned char *sel,
+                                                     int *order) {
+    __shared__ double sv[MM_T];
+    __shared__ long long si[MM_T];
+    __shared__ double bb[4];
+    // bounding box
+    double a0 = INFINITY, a1 = -INFINITY, a2 = INFINITY, a3 = -INFINITY;
+    for (int64_t i = threadIdx.x; i < n; i += MM_T) {
+        a0 = fmin(a0, x[i].x); a1 = fmax(a1, x[i].x);
+        a2 = fmin(a2, x[i].y); a3 = fmax(a3, x[i].y);
+    }
+    for (int c = 0; c < 4; ++c) {
+        double v = c == 0 ? a0 : c == 1 ? a1 : c == 2 ? a2 : a3;
+        sv[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = MM_T / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                double u = sv[threadIdx.x + o];
+                sv[threadIdx.x] = (c & 1) ? fmax(sv[threadIdx.x], u) : fmin(sv[threadIdx.x], u);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) bb[c] = sv[0];
+        __syncthreads();
+    }
+    const double2 ctr = make_double2(__dmul_rn(__dadd_rn(bb[0], bb[1]), 0.5), __dmul_rn(__dadd_rn(bb[2], bb[3]), 0.5));
+    // first point: smallest (distance to centre, index)
+    double bv = INFINITY;
+    long long bi = -1;
+    for (int64_t i = threadIdx.x; i < n; i += MM_T) {
+        double d = sqd(x[i], ctr);
+        if (d < bv) { bv = d; bi = i; }
+        sel[i] = 0;
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = MM_T / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            double u = sv[threadIdx.x + o];
+            long long ui = si[threadIdx.x + o];
+            if (ui >= 0 && (u < sv[threadIdx.x] || (u == sv[threadIdx.x] && (si[threadIdx.x] < 0 || ui < si[threadIdx.x])))) {
+                sv[threadIdx.x] = u;
+                si[threadIdx.x] = ui;
+            }
+        }
+        __syncthreads();
+    }
+    long long last = si[0];
+    __syncthreads();
+    if (threadIdx.x == 0) { order[0] = (int)last; sel[last] = 1; }
+    for (int64_t i = threadIdx.x; i < n; i += MM_T) dmin[i] = INFINITY;
+    __syncthreads();
+    for (int64_t r = 1; r < n; ++r) {
+        const double2 pl = x[last];
+        bv = -1.0;
+        bi = -1;
+        for (int64_t i = threadIdx.x; i < n; i += MM_T) {
+            if (sel[i]) continue;
+            double d = fmin(dmin[i], sqd(x[i], pl));
+            dmin[i] = d;
+            if (d > bv) { bv = d; bi = i; }
+        }
+        sv[threadIdx.x] = bv;
+        si[threadIdx.x] = bi;
+        __syncthreads();
+        for (int o = MM_T / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                double u = sv[threadIdx.x + o];
+                long long ui = si[threadIdx.x + o];
+                if (ui >= 0 && (si[threadIdx.x] < 0 || u > sv[threadIdx.x] || (u == sv[threadIdx.x] && ui < si[threadIdx.x]))) {
+                    sv[threadIdx.x] = u;
+                    si[threadIdx.x] = ui;
+                }
+            }
+            __syncthreads();
+        }
+        last = si[0];
+        __syncthreads();
+        if (threadIdx.x == 0) { order[r] = (int)last; sel[last] = 1; }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+void maxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t s) {
+    DBuf<double> dmin(n);
+    DBuf<unsigned char> sel(n);
+    maxmin_block<<<1, MM_T, 0, s>>>(x, n, dmin.get(), sel.get(), order_out);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+}
+
+void random_order_dev(int64_t n, uint64_t seed, int *order_out, cudaStream_t s) {
+    DBuf<uint64_t> keys(n);
+    rand_keys<<<blocks_for(n, 256), 256, 0, s>>>(n, seed, keys.get(), order_out);
+    PHS_LAUNCH_CHECK();
+    radix_sort_pairs(keys.get(), order_out, n, 64, s);
+}
+
+void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr_ell, cudaStream_t s) {
+    PHS_REQUIRE(m >= 1 && m <= KNN_MAXM, PHS_ERR_INVALID_ARG, "conditioning-set size m must be in 1..64");
+    DBuf<int> rank(n);
+    ranks_from_order<<<blocks_for(n, 256), 256, 0, s>>>(order, n, rank.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<double2> xr(n);
+    gather_xy<<<blocks_for(n, 256), 256, 0, s>>>(x, order, n, xr.get());
+    PHS_LAUNCH_CHECK();
+    // grid over the bounding box, about 2 points per cell
+    std::vector<double2> hx(n);
+    PHS_CUDA(cudaMemcpyAsync(hx.data(), x, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    double xmin = hx[0].x, xmax = hx[0].x, ymin = hx[0].y, ymax = hx[0].y;
+    for (auto &v : hx) {
+        xmin = std::min(xmin, v.x); xmax = std::max(xmax, v.x);
+        ymin = std::min(ymin, v.y); ymax = std::max(ymax, v.y);
+    }
+    Grid g;
+    g.G = (int)std::max<double>(1.0, std::min<double>(8192.0, std::floor(std::sqrt((double)n / 2.0))));
+    const double ext = std::max(xmax - xmin, ymax - ymin);
+    g.cw = ext > 0 ? ext / g.G * (1.0 + 1e-12) : 1.0;
+    g.x0 = xmin;
+    g.y0 = ymin;
+    const int ncell = g.G * g.G;
+    DBuf<uint64_t> keys(n);
+    DBuf<int> vals(n);
+    grid_keys<<<blocks_for(n, 256), 256, 0, s>>>(x, rank.get(), n, g, keys.get(), vals.get());
+    PHS_LAUNCH_CHECK();
+    int cbits = 1;
+    while ((1ll << cbits) < ncell) ++cbits;
+    radix_sort_pairs(keys.get(), vals.get(), n, 32 + cbits, s);
+    DBuf<int> cst(ncell + 1);
+    cell_starts<<<blocks_for(ncell + 1, 256), 256, 0, s>>>(keys.get(), n, ncell, cst.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<double2> xc(n);
+    DBuf<int> rc(n);
+    cell_payload<<<blocks_for(n, 256), 256, 0, s>>>(keys.get(), vals.get(), x, n, xc.get(), rc.get());
+    PHS_LAUNCH_CHECK();
+    const int brute = (int)std::min<int64_t>(n, 2048);
+    knn_kernel<<<blocks_for(n, 128), 128, 0, s>>>(xr.get(), n, m, brute, g, cst.get(), xc.get(), rc.get(), order,
+                                                  nbr_ell);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+}
+
+int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, double nu,
+                           double alpha, double *val_ell, cudaStream_t s) {
+    PHS_REQUIRE(m >= 1 && m <= KNN_MAXM, PHS_ERR_INVALID_ARG, "conditioning-set size m must be in 1..64");
+    PHS_REQUIRE(nu == 0.5 || nu == 1.0 || nu == 1.5 || nu == 2.5, PHS_ERR_INVALID_ARG, "nu must be 0.5, 1, 1.5 or 2.5");
+    PHS_REQUIRE(alpha > 0 && std::isfinite(alpha), PHS_ERR_INVALID_ARG, "alpha must be positive");
+    const size_t per = (size_t)(m * m + 3 * m + 1) * sizeof(double);
+    int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
+    const size_t smem = per * wpb;
+    PHS_CUDA(cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DBuf<unsigned long long> cnt(2);
+    PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, 2 * sizeof(unsigned long long), s));
+    factor_kernel<<<blocks_for(n, wpb), 32 * wpb, smem, s>>>(x, n, rank, nbr_ell, m, nu, alpha, val_ell, cnt.get(),
+                                                             cnt.get() + 1);
+    PHS_LAUNCH_CHECK();
+    unsigned long long h[2];
+    PHS_CUDA(cudaMemcpyAsync(h, cnt.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_REQUIRE(h[1] == 0, PHS_ERR_CHOLESKY, "a local Vecchia factor failed even with jitter");
+    return (int64_t)h[0];
+}
+
+void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t seed, double nu, double alpha,
+                   cudaStream_t s) {
+    const int64_t n = ps.n;
+    v.n = n;
+    v.m = m;
+    // caller-order coordinates (normalised frame): ties in orderings and neighbour lists
+    // resolve by caller index, the definition the interface documents
+    DBuf<double2> xcal(n);
+    gather_xy<<<blocks_for(n, 256), 256, 0, s>>>(ps.xs.get(), ps.iperm.get(), n, xcal.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<int> order_c(n);
+    if (ordering == 0) random_order_dev(n, seed, order_c.get(), s);
+    else maxmin_order_dev(xcal.get(), n, order_c.get(), s);
+    DBuf<int> nbr_c((size_t)m * n);
+    knn_prev_dev(xcal.get(), n, order_c.get(), m, nbr_c.get(), s);
+    DBuf<int> rank_c(n);
+    ranks_from_order<<<blocks_for(n, 256), 256, 0, s>>>(order_c.get(), n, rank_c.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<double> val_c((size_t)(m + 1) * n);
+    v.jittered = vecchia_factor_dev(xcal.get(), n, rank_c.get(), nbr_c.get(), m, nu, alpha, val_c.get(), s);
+    // move to sorted positions: columns permuted by perm, entries mapped by iperm
+    v.nbr.alloc((size_t)m * n);
+    v.val.alloc((size_t)(m + 1) * n);
+    v.rank.alloc(n);
+    v.order.alloc(n);
+    permute_ell<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>(nbr_c.get(), n, m, ps.perm.get(), v.nbr.get());
+    PHS_LAUNCH_CHECK();
+    ell_to_positions<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>(v.nbr.get(), (int64_t)m * n, ps.iperm.get());
+    PHS_LAUNCH_CHECK();
+    permute_ell_d<<<blocks_for((int64_t)(m + 1) * n, 256), 256, 0, s>>>(val_c.get(), n, m + 1, ps.perm.get(),
+                                                                          v.val.get());
+    PHS_LAUNCH_CHECK();
+    permute_ell<<<blocks_for(n, 256), 256, 0, s>>>(rank_c.get(), n, 1, ps.perm.get(), v.rank.get());
+    PHS_LAUNCH_CHECK();
+    // order (ranks -> sorted positions) = iperm[order_c]
+    permute_ell<<<blocks_for(n, 256), 256, 0, s>>>(ps.iperm.get(), n, 1, order_c.get(), v.order.get());
+    PHS_LAUNCH_CHECK();
+    // transpose
+    DBuf<int> cnt(n), cur(n);
+    PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, n * sizeof(int), s));
+    PHS_CUDA(cudaMemsetAsync(cur.get(), 0, n * sizeof(int), s));
+    t_count<<<blocks_for(n, 256), 256, 0, s>>>(v.nbr.get(), n, m, cnt.get());
+    PHS_LAUNCH_CHECK();
+    v.t_off.alloc(n + 1);
+    int64_t nnz = exclusive_scan_i32(cnt.get(), v.t_off.get(), n, s);
+    int nz32 = (int)nnz;
+    PHS_CUDA(cudaMemcpyAsync(v.t_off.get() + n, &nz32, sizeof(int), cudaMemcpyHostToDevice, s));
+    v.t_col.alloc(nnz);
+    v.t_val.alloc(nnz);
+    t_fill<<<blocks_for(n, 256), 256, 0, s>>>(v.nbr.get(), v.val.get(), n, m, v.t_off.get(), cur.get(), v.t_col.get(),
+                                              v.t_val.get());
+    PHS_LAUNCH_CHECK();
+    t_sort_rows<<<blocks_for(n, 256), 256, 0, s>>>(v.t_off.get(), n, v.t_col.get(), v.t_val.get());
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+}
+
+void vecchia_apply(const Vecchia &v, const double *r, double *tmp, double *z, cudaStream_t s) {
+    apply_ut<<<blocks_for(v.n, 256), 256, 0, s>>>(v.nbr.get(), v.val.get(), v.n, v.m, r, tmp);
+    PHS_LAUNCH_CHECK();
+    apply_u<<<blocks_for(v.n * 32, 256), 256, 0, s>>>(v.t_off.get(), v.t_col.get(), v.t_val.get(), v.n, tmp, z);
+    PHS_LAUNCH_CHECK();
+}
+
+}  // namespace phs

@@ -1,0 +1,50 @@
+"""CPU checks of the native boundary: the library builds for sm_103a, loads, and
+exports every entry point that include/phs.h declares (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "phs.h")) as fh:
+        txt = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:phs_status|void|const char \*)\s*(phs_\w+)\s*\(", txt, re.M)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2608_11462_b300 import build
+    build.build()
+    from paper_2608_11462_b300 import _native
+    return _native
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ["phs_plan_create", "phs_matvec", "phs_fit", "phs_eval", "phs_plan_destroy", "phs_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(native):
+    L = ctypes.CDLL(native.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+    assert sorted(native.EXPORTS) == _declared()
+
+
+def test_options_default_host_only(native):
+    o = native.PhsOptions()
+    native.lib().phs_options_default(ctypes.byref(o), 2)
+    assert o.tol == 1e-8 and o.domain_halfwidth == 0.25 and abs(o.alpha - 0.35) < 1e-15 and o.nu == 1.0
+    native.lib().phs_options_default(ctypes.byref(o), 4)
+    assert o.domain_halfwidth == 1.0 and o.alpha == 2.0
+    assert native.lib().phs_last_error() is not None
+
+
+def test_build_targets_sm103a_only():
+    from paper_2608_11462_b300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances: orderings and neighbour lists bit-exact; FP64 matvec within 1e-10
+relative (2-norm, random t); the fitted interpolant within 1e-8 relative (inf
+norm) of the dense solve at held-out points; Vecchia factors within 1e-10
+relative.  The FP32 FMM is checked at 2e-5 relative (its expansion order and
+float arithmetic bound it near 1e-6)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def phs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_11462_b300 import build
+    build.build()
+    import paper_2608_11462_b300 as mod
+    return mod
+
+
+DEV = "cuda"
+
+
+def _t(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+def _clustered(n, seed, frac=0.5, sigma=0.003):
+    rng = np.random.default_rng(seed)
+    nc = int(frac * n)
+    pts = np.concatenate([rng.random((n - nc, 2)), synth.gaussian_mixture(nc, 5, sigma, 0.2, 0.8, rng)])
+    return pts
+
+
+# ---------------------------------------------------------------- exact dense matvec
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_dense_matvec_matches_oracle(phs, k):
+    pts = np.random.default_rng(k).random((777, 2))
+    t = np.random.default_rng(10 + k).standard_normal(777)
+    got = phs.phs_dense_matvec(_t(pts), k, _t(t)).cpu().numpy()
+    want = oracle.dense_matvec(pts, k, t)
+    assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------- FMM matvec
+@pytest.mark.parametrize("k", [2, 4])
+@pytest.mark.parametrize("geom", ["uniform", "clustered"])
+@pytest.mark.parametrize("leaf_cap", [8, 64])
+def test_fmm_matvec_fp64(phs, k, geom, leaf_cap):
+    n = 3001
+    pts = np.random.default_rng(1).random((n, 2)) if geom == "uniform" else _clustered(n, 2)
+    t = np.random.default_rng(3).standard_normal(n)
+    plan = phs.Plan(_t(pts), k, fmm_order=0, vecchia_m=8, opts=phs.options(k, leaf_cap=leaf_cap))
+    got = plan.matvec(_t(t), precision=0).cpu().numpy()
+    want = oracle.dense_matvec(pts, k, t)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= 1e-10, err
+    assert plan.frame()[1][7] >= (2 if leaf_cap == 8 else 1)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_fmm_matvec_fp32(phs, k):
+    n = 4000
+    pts = _clustered(n, 4)
+    t = np.random.default_rng(5).standard_normal(n)
+    plan = phs.Plan(_t(pts), k, vecchia_m=8, opts=phs.options(k, leaf_cap=32))
+    got = plan.matvec(_t(t), precision=1).cpu().numpy()
+    want = oracle.dense_matvec(pts, k, t)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= 2e-5, err
+
+
+def test_fmm_matvec_p20_reports_error(phs):
+    """Config-1 order p = 20: expansion error ~0.55^20; stated, not gated at 1e-10."""
+    w_ = synth.workload("uniform_tps")
+    t = np.random.default_rng(6).standard_normal(len(w_["f"]))
+    plan = phs.Plan(_t(w_["points"]), 2, fmm_order=20, vecchia_m=10)
+    got = plan.matvec(_t(t)).cpu().numpy()
+    want = oracle.dense_matvec(w_["points"], 2, t)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= 1e-5, err
+
+
+def test_fmm_ragged_and_tiny(phs):
+    for n in [4, 5, 17, 65, 129]:
+        pts = np.random.default_rng(n).random((n, 2))
+        t = np.random.default_rng(n + 1).standard_normal(n)
+        plan = phs.Plan(_t(pts), 2, vecchia_m=3, opts=phs.options(2, leaf_cap=4))
+        got = plan.matvec(_t(t)).cpu().numpy()
+        want = oracle.dense_matvec(pts, 2, t)
+        assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------- ordering and neighbours
+def test_random_order_bit_exact(phs):
+    for n in [1, 2, 1000, 70001]:
+        got = phs.phs_random_order(n, 12345).cpu().numpy()
+        assert np.array_equal(got, oracle.random_order(n, 12345))
+
+
+@pytest.mark.parametrize("lattice", [False, True])
+def test_knn_prev_bit_exact(phs, lattice):
+    n, m = 6000, 30
+    rng = np.random.default_rng(7)
+    pts = rng.random((n, 2))
+    if lattice:
+        pts = np.round(pts * 40) / 40 + rng.random((n, 2)) * 1e-9 * (rng.random((n, 1)) < 0.1)
+        pts = np.unique(pts, axis=0)
+        n = pts.shape[0]
+    order = oracle.random_order(n, 9)
+    got = phs.phs_knn_prev(_t(pts), _t(order, torch.int64), m).cpu().numpy()
+    want = oracle.knn_prev(pts, order, m)
+    assert np.array_equal(got, want)
+
+
+def test_maxmin_order_bit_exact(phs):
+    pts = np.random.default_rng(8).random((1500, 2))
+    got = phs.phs_maxmin_order(_t(pts)).cpu().numpy()
+    want, _ = oracle.maxmin_order(pts)
+    assert np.array_equal(got, want)
+    g = np.array([[0, 0], [1, 0], [2, 0], [3, 0], [10, 0]], dtype=float)
+    assert phs.phs_maxmin_order(_t(g)).cpu().numpy().tolist() == [3, 4, 0, 1, 2]
+
+
+@pytest.mark.parametrize("nu,alpha", [(1.5, 20.0), (1.0, 0.35 * 4)])
+def test_vecchia_factor_matches_oracle(phs, nu, alpha):
+    n, m = 2500, 30
+    pts = np.random.default_rng(11).random((n, 2)) * 0.5
+    order = oracle.random_order(n, 2)
+    nbr = oracle.knn_prev(pts, order, m)
+    d_w, o_w, _ = oracle.vecchia_factor(pts, order, nbr, m, nu, alpha)
+    d_g, o_g, _ = phs.phs_vecchia_factor(_t(pts), _t(order, torch.int64), _t(nbr, torch.int64), m, nu, alpha)
+    d_g, o_g = d_g.cpu().numpy(), o_g.cpu().numpy()
+    assert np.max(np.abs(d_g - d_w) / np.abs(d_w)) <= 1e-10
+    assert np.max(np.abs(o_g - o_w)) <= 1e-10 * np.max(np.abs(o_w))
+
+
+def test_plan_vecchia_matches_oracle(phs):
+    w_ = synth.workload("uniform_tps", n=3000)
+    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=30, opts=phs.options(2, seed=42))
+    order, nbr = plan.vecchia()
+    xn, _, _ = oracle.normalize(w_["points"], 0.25)
+    assert np.array_equal(order, oracle.random_order(3000, 42))
+    assert np.array_equal(nbr, oracle.knn_prev(xn, order, 30))
+    d_g, o_g = plan.vecchia_factor()
+    d_w, o_w, _ = oracle.vecchia_factor(xn, order, nbr, 30, 1.0, 0.35)
+    assert np.max(np.abs(d_g - d_w) / np.abs(d_w)) <= 1e-9
+    assert np.max(np.abs(o_g - o_w)) <= 1e-9 * np.max(np.abs(o_w))
+
+
+def test_plan_precond_matches_oracle(phs):
+    w_ = synth.workload("uniform_tps", n=2000)
+    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=20)
+    xn, _, _ = oracle.normalize(w_["points"], 0.25)
+    order, nbr = plan.vecchia()
+    d, o, _ = oracle.vecchia_factor(xn, order, nbr, 20, 1.0, 0.35)
+    r = np.random.default_rng(0).standard_normal(2000)
+    B = oracle.poly_basis(xn, 1)
+    Q, _ = np.linalg.qr(B)
+    P = lambda v: v - Q @ (Q.T @ v)  # noqa: E731
+    want = P(oracle.vecchia_apply(nbr, d, o, P(r)))
+    got = plan.precond(_t(r)).cpu().numpy()
+    assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------- fit and eval
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fit_uniform_tps_matches_dense_solve(phs, precision):
+    """Workload uniform_tps (n = 1,500, k = 2, S = 3): interpolant within 1e-8
+    relative of the dense augmented solve at 500 held-out targets."""
+    w_ = synth.workload("uniform_tps")
+    opts = phs.options(2, tol=1e-10, precision=precision)
+    plan = phs.Plan(_t(w_["points"]), 2, fmm_order=0, vecchia_m=10, opts=opts)
+    w, beta, info = plan.fit(_t(w_["f"]))
+    pred = plan.eval(w, beta, _t(w_["targets"])).cpu().numpy()
+    ref = oracle.fit_dense(w_["points"], w_["f"], 2)
+    want = oracle.predict(ref, w_["targets"])
+    err = np.max(np.abs(pred - want)) / np.max(np.abs(want))
+    assert info["converged"] == 1
+    assert err <= 1e-8, err
+    assert np.allclose(beta.cpu().numpy(), ref["beta"], rtol=0, atol=1e-6 * np.abs(ref["beta"]).max())
+    wg = w.cpu().numpy()
+    assert np.linalg.norm(wg - ref["w"]) <= 1e-5 * np.linalg.norm(ref["w"])
+    # nodes are interpolated
+    at_nodes = plan.eval(w, beta, _t(w_["points"])).cpu().numpy()
+    assert np.max(np.abs(at_nodes - w_["f"])) <= 1e-8 * np.max(np.abs(w_["f"]))
+
+
+@pytest.mark.parametrize("k", [4])
+def test_fit_even_k_higher_order(phs, k):
+    pts = np.random.default_rng(21).random((900, 2))
+    f = synth.f_uniform_tps(pts)
+    tg = np.random.default_rng(22).random((200, 2))
+    plan = phs.Plan(_t(pts), k, vecchia_m=30, opts=phs.options(k, tol=1e-11, maxiter=400))
+    w, beta, info = plan.fit(_t(f), allow_not_converged=True)
+    pred = plan.eval(w, beta, _t(tg)).cpu().numpy()
+    ref = oracle.fit_dense(pts, f, k, halfwidth=1.0)
+    want = oracle.predict(ref, tg)
+    assert np.max(np.abs(pred - want)) <= 1e-6 * np.max(np.abs(want))
+
+
+def test_polynomial_reproduction_gpu(phs):
+    pts = np.random.default_rng(30).random((1200, 2))
+    f = 1.0 + 2.0 * pts[:, 0] - 3.0 * pts[:, 1]
+    plan = phs.Plan(_t(pts), 2, vecchia_m=10)
+    w, beta, info = plan.fit(_t(f))
+    assert np.max(np.abs(w.cpu().numpy())) < 1e-10
+    tg = np.random.default_rng(31).random((50, 2))
+    pred = plan.eval(w, beta, _t(tg)).cpu().numpy()
+    assert np.allclose(pred, 1.0 + 2.0 * tg[:, 0] - 3.0 * tg[:, 1], atol=1e-10)
+
+
+def test_eval_outside_root_box(phs):
+    w_ = synth.workload("uniform_tps", n=800)
+    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=10, opts=phs.options(2, tol=1e-10))
+    w, beta, _ = plan.fit(_t(w_["f"]))
+    tg = np.array([[-0.5, 0.5], [1.7, 1.2], [0.5, 0.5], [w_["points"][:, 0].max() + 1e-3, 0.3]])
+    pred = plan.eval(w, beta, _t(tg)).cpu().numpy()
+    ref = oracle.fit_dense(w_["points"], w_["f"], 2)
+    want = oracle.predict(ref, tg)
+    assert np.max(np.abs(pred - want)) <= 1e-8 * np.max(np.abs(want))
+
+
+def test_host_end_to_end(phs):
+    w_ = synth.workload("uniform_tps", n=600, n_targets=80)
+    w, beta, pred, info = phs.phs_fit_predict_host(w_["points"], w_["f"], w_["targets"], 2, vecchia_m=10,
+                                                   opts=phs.options(2, tol=1e-10))
+    ref = oracle.fit_dense(w_["points"], w_["f"], 2)
+    want = oracle.predict(ref, w_["targets"])
+    assert np.max(np.abs(pred - want)) <= 1e-8 * np.max(np.abs(want))
+
+
+# ---------------------------------------------------------------- errors and edge cases
+def test_errors_are_reported(phs):
+    pts = np.random.default_rng(0).random((50, 2))
+    dup = pts.copy()
+    dup[7] = dup[3]
+    with pytest.raises(phs.PhsError, match="DUPLICATE"):
+        phs.Plan(_t(dup), 2, vecchia_m=5)
+    bad = pts.copy()
+    bad[2, 1] = np.nan
+    with pytest.raises(phs.PhsError, match="INVALID"):
+        phs.Plan(_t(bad), 2, vecchia_m=5)
+    with pytest.raises(phs.PhsError, match="INVALID"):
+        phs.Plan(_t(pts[:3]), 2, vecchia_m=5)
+    with pytest.raises(phs.PhsError, match="INVALID"):
+        phs.Plan(_t(pts), 7, vecchia_m=5)
+    with pytest.raises(phs.PhsError, match="INVALID"):
+        phs.Plan(_t(pts), 2, vecchia_m=65)
+    # the context stays usable after the errors
+    plan = phs.Plan(_t(pts), 2, vecchia_m=5)
+    t = np.ones(50)
+    assert np.allclose(plan.matvec(_t(t)).cpu().numpy(), oracle.dense_matvec(pts, 2, t), rtol=1e-10)
