@@ -1,0 +1,325 @@
+"""Benchmark: one step = the whole PHS hot path on the tps_1m workload
+(n = 1,048,576 points, 90% uniform + 10% in 50 tight clusters, k = 2, linear
+block, Vecchia m = 30), i.e. plan creation (normalisation, Morton sort,
+quadtree and lists, QR of B, Vecchia enumeration, neighbours and local factors),
+the preconditioned CG fit to a 1e-8 relative residual, and evaluation of the
+interpolant at 10,000 held-out targets.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl native|reference]
+
+Prints one JSON line.  `value` is the device-timed wall time of one step (inputs
+resident in HBM, CUDA events on the library's stream, L2 flushed between
+steps); `e2e` is the same step through phs_fit_predict_host from host buffers.
+For N > 1 (torchrun) every rank runs an independent replica on its own GPU;
+`value` is the max over ranks and `fits_per_s` the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG fit time to 1e-8 at n=1M TPS"
+WORKLOAD = "tps_1m"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--n", type=int, default=None, help="override the point count (smaller parity runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        import statistics
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+def oracle_step(points, f, targets, n_sample, seed=0):
+    """The oracle as it stands on a bounded random subsample: normalisation, random
+    order, brute-force neighbours, Vecchia factor, dense-matvec PCG to 1e-8, dense
+    evaluation at the targets.  Returns (seconds, n_sample, iterations)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(f), n_sample, replace=False))
+    p, fs = points[idx], f[idx]
+    t0 = time.perf_counter()
+    xn, c, rho = oracle.normalize(p, 0.25)
+    order = oracle.random_order(n_sample, 1)
+    nbr = oracle.knn_prev(xn, order, 30)
+    d, o, _ = oracle.vecchia_factor(xn, order, nbr, 30, 1.5, 0.35)
+    w, beta, it, _ = oracle.pcg(xn, fs, 2, 1, (nbr, d, o), tol=1e-8, maxiter=300)
+    yn = (targets - c) * rho
+    oracle.interpolant(xn, w, beta, 2, 1, yn)
+    return time.perf_counter() - t0, n_sample, it
+
+
+def cpu_baseline(points, f, targets, n_full, budget_s=20.0):
+    """Time the oracle on a subsample sized for ~budget_s of CPU work and scale the
+    O(n^2) dense path to the full n (labelled as an extrapolation)."""
+    n_s = 2048
+    dt, _, it = oracle_step(points, f, targets[:1000], n_s)
+    while dt < budget_s / 5 and n_s * 2 <= 16384:
+        n_s *= 2
+        dt, _, it = oracle_step(points, f, targets[:1000], n_s)
+    scale = (n_full / n_s) ** 2
+    return {"value": dt * scale, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle fit (brute-force neighbours, Vecchia m=30, dense-matvec PCG to 1e-8, {it} iters) "
+                      f"on a {n_s}-point random subsample of {WORKLOAD} plus 1000 targets, measured {dt:.2f} s, "
+                      f"extrapolated by (n/{n_s})^2 to n={n_full}",
+            "measured_s": dt, "n_sample": n_s, "extrapolated": True}
+
+
+# --------------------------------------------------------------------------- native leg
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    import numpy as np
+
+    import synth
+
+    wl = synth.workload(WORKLOAD, n=args.n)
+    points, f, targets = wl["points"], wl["f"], wl["targets"]
+    n, m_t = len(f), len(targets)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        for i in range(args.warmup + args.steps):
+            dt, ns, it = oracle_step(points, f, targets[:1000], 4096, seed=i)
+            if i >= args.warmup:
+                steps.append(dt * (n / ns) ** 2)
+        v = float(np.mean(steps))
+        cb = {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+              "sample": f"oracle fit on a 4096-point subsample of {WORKLOAD} + 1000 targets, O(n^2) dense path "
+                        f"extrapolated by (n/4096)^2 to n={n}"}
+        print(json.dumps({"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "impl": "reference", "config": {"workload": WORKLOAD, "n": n, "k": 2, "vecchia_m": 30},
+                          "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2608_11462_b300 as phs
+
+    L = phs.lib()
+    opts = phs.options(2, precision=args.precision, tol=1e-8, nu=1.5, alpha=0.35, leaf_cap=64)
+    pts_d = torch.tensor(points, device=dev)
+    f_d = torch.tensor(f, device=dev)
+    tg_d = torch.tensor(targets, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step(timing=False):
+        plan = phs.Plan(pts_d, 2, fmm_order=0, vecchia_m=30, opts=opts)
+        if timing:
+            plan.set_timing(True)
+        w, beta, info = plan.fit(f_d)
+        pred = plan.eval(w, beta, tg_d)
+        tim = plan.timing() if timing else None
+        work = plan.work()
+        sizes = plan.frame()[1]
+        plan.close()
+        return info, tim, work, sizes, pred
+
+    for _ in range(args.warmup):
+        step()
+    times, infos, tims = [], [], []
+    clocks = ClockSampler(local)
+    launches0 = L.phs_kernel_launches()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info, tim, work, sizes, pred = step(timing=True)
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        infos.append(info)
+        tims.append(tim)
+    clk = clocks.stop()
+    launches = (L.phs_kernel_launches() - launches0) // args.steps
+    t_step = float(np.mean(times))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+
+    # ---- end to end from host buffers through the C ABI
+    e2e_times = []
+    for i in range(max(1, min(args.steps, 2))):
+        barrier()
+        t0 = time.perf_counter()
+        phs.phs_fit_predict_host(points, f, targets, 2, vecchia_m=30, opts=opts)
+        torch.cuda.synchronize(dev)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = float(np.mean(e2e_times))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = float(tt.item())
+
+    # ---- roofline of the dominant kernel (per-launch algorithmic work / event-timed duration)
+    peaks, peak_kind = load_peaks()
+    agg = {}
+    for tim in tims:
+        for k_, (ms, calls) in tim.items():
+            a = agg.setdefault(k_, [0.0, 0])
+            a[0] += ms
+            a[1] += calls
+    phases = {k_: v for k_, v in agg.items() if k_ in ("p2p", "m2l", "upward", "downward", "precond", "vector")}
+    dom = max(phases, key=lambda k_: phases[k_][0])
+    P = sizes[3] + 1
+    nd = sizes[4]
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2032.0))
+    fp64_peak_tflops = 148 * 2 * 2 * sm_mhz_max * 1e6 / 1e12   # 2 FP64 FMA / clk / SM
+    if dom == "m2l":
+        ms_launch = phases["m2l"][0] / phases["m2l"][1]
+        flops = 8.0 * nd * P * P * work["m2l_translations"]
+        prec_m2l = "f64" if args.precision in (0, 1) else "f32"
+        peak = fp64_peak_tflops if prec_m2l == "f64" else 148 * 128 * 2 * sm_mhz_max * 1e6 / 1e12
+        ach = flops / (ms_launch / 1e3) / 1e12
+        roof = {"kernel": f"m2l_kernel<{ 'double' if prec_m2l == 'f64' else 'float'}>", "bound": "alu",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": f"derived: 148 SMs x {'2 FP64' if prec_m2l == 'f64' else '128 FP32'} FMA/clk x "
+                               f"{sm_mhz_max:.0f} MHz",
+                "work_per_launch": f"8*nd*P^2 flops x {work['m2l_translations']} V-list translations",
+                "traffic": None}
+    elif dom == "p2p":
+        ms_launch = phases["p2p"][0] / phases["p2p"][1]
+        pairs = work["near_pairs"]
+        ach = pairs / (ms_launch / 1e3) / 1e9
+        roof = {"kernel": "p2p_kernel", "bound": "alu", "achieved": ach, "peak": None, "unit": "Gpairs/s",
+                "frac": None, "work_per_launch": f"{pairs} near-field pairs", "traffic": None}
+    else:
+        ms_launch = phases[dom][0] / max(phases[dom][1], 1)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": None, "traffic": None}
+    roof["ms_per_launch"] = ms_launch
+    roof["peak_kind"] = peak_kind
+    # the preconditioner apply (HBM-bound) alongside: 2 passes over the factor + vectors
+    pre_ms = phases["precond"][0] / max(phases["precond"][1], 1)
+    nnz = n * 31
+    pre_bytes = 2 * nnz * 12 + 4 * n * 8
+    pre = {"bound": "hbm", "achieved": pre_bytes / (pre_ms / 1e3) / 1e9, "peak": float(peaks["hbm_gbs"]),
+           "unit": "GB/s", "ms_per_launch": pre_ms, "bytes_per_launch": pre_bytes}
+    pre["frac"] = pre["achieved"] / pre["peak"]
+
+    info = infos[-1]
+    out = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
+        "fits_per_s": world / t_step,
+        "config": {"workload": WORKLOAD, "n": n, "targets": m_t, "k": 2, "poly_degree": 1, "vecchia_m": 30,
+                   "nu": 1.5, "alpha": 0.35, "ordering": "random", "leaf_cap": 64, "fmm_order": sizes[3],
+                   "precision_mode": args.precision, "tol": 1e-8, "parallelism": f"replicas{world}",
+                   "l2": "flushed (256 MB write) between timed steps"},
+        "pcg": {"iters": info["iters"], "outer_iters": info["outer_iters"], "converged": info["converged"],
+                "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"], "ms_fit": info["ms_fit"],
+                "ms_matvec_avg": info["ms_matvec_avg"]},
+        "phases_ms_per_step": {k_: v[0] / args.steps for k_, v in agg.items()},
+        "roofline": roof, "roofline_precond": pre, "clocks": clk, "gpu_launches": int(launches),
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(16 * n + 8 * n + 16 * m_t),
+                "d2h_bytes_per_step": int(8 * n + 8 * 3 + 8 * m_t)},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(points, f, targets, n)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

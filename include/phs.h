@@ -53,9 +53,14 @@ typedef enum {
 
 /* Solver options (defaults from phs_options_default). */
 typedef struct {
-    int precision;          /* 0: FP64 throughout.  1: FP32 FMM inside an FP64
-                               iterative-refinement loop (residuals, inner products,
-                               projection and preconditioner stay FP64). */
+    int precision;          /* FMM arithmetic inside the CG iterations:
+                               0: FP64 throughout (plain PCG);
+                               1: FP32 near field, FP64 far field;
+                               2: FP32 near field and FP32 M2L, FP64 elsewhere;
+                               3: FP32 throughout (order min(p, 24)).
+                               Modes 1-3 run inside FP64 iterative refinement: the
+                               outer residual uses the FP64 FMM; residuals, inner
+                               products, projection and preconditioner stay FP64. */
     double tol;             /* stop when ||r_k|| <= max(tol*||Q_perp' f||, atol); default 1e-8 */
     double atol;            /* default 0 */
     int maxiter;            /* PCG iterations (precision 0) or total inner iterations; default 200 */
@@ -88,6 +93,11 @@ void phs_options_default(phs_options *opt, int k);
 /* Thread-local message of the last failing call ("" if none). */
 const char *phs_last_error(void);
 
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all threads, all plans); differences of two readings count the launches of
+ * the calls between them. */
+int64_t phs_kernel_launches(void);
+
 /*
  * Build a plan for n points (Sec. 2, setup phase):
  *   normalisation to [-h,h]^2 (Eq. 2.1), Morton sort and adaptive quadtree with
@@ -109,8 +119,9 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
                            phs_stream_t stream, phs_plan_t *out);
 
 /* out = M t in the caller's frame and order, M_ij = phi(|x_i - x_j|) (Eq. 1.3),
- * by the FMM of Sec. 2.1 applied through Eq. (2.6).  precision 0 = FP64 FMM,
- * 1 = FP32 FMM.  t_dev, out_dev: n doubles on the device (may not alias). */
+ * by the FMM of Sec. 2.1 applied through Eq. (2.6).  precision selects the
+ * arithmetic as in phs_options.precision (0 = FP64 FMM).  t_dev, out_dev: n
+ * doubles on the device (may not alias). */
 phs_status phs_matvec(phs_plan_t plan, const double *t_dev, double *out_dev, int precision,
                       phs_stream_t stream);
 

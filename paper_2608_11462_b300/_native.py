@@ -30,7 +30,7 @@ class PhsFitInfo(ctypes.Structure):
 
 
 EXPORTS = [
-    "phs_options_default", "phs_last_error", "phs_plan_create", "phs_matvec", "phs_fit", "phs_eval",
+    "phs_options_default", "phs_last_error", "phs_kernel_launches", "phs_plan_create", "phs_matvec", "phs_fit", "phs_eval",
     "phs_fit_predict_host", "phs_plan_destroy", "phs_plan_frame", "phs_plan_vecchia", "phs_plan_vecchia_factor",
     "phs_plan_precond", "phs_plan_work", "phs_plan_set_timing", "phs_plan_timing", "phs_dense_matvec",
     "phs_random_order", "phs_maxmin_order", "phs_knn_prev", "phs_vecchia_factor",
@@ -51,6 +51,7 @@ def lib():
     sig = {
         "phs_options_default": (None, [ctypes.POINTER(PhsOptions), i32]),
         "phs_last_error": (ctypes.c_char_p, []),
+        "phs_kernel_launches": (i64, []),
         "phs_plan_create": (st, [P, i64, i32, i32, i32, i32, ctypes.POINTER(PhsOptions), P, ctypes.POINTER(P)]),
         "phs_matvec": (st, [P, P, P, i32, P]),
         "phs_fit": (st, [P, P, P, P, ctypes.POINTER(PhsFitInfo), P]),

@@ -1,6 +1,7 @@
 // abi.cu -- the C ABI (include/phs.h): plans, the preconditioned CG solve of
 // Eq. (2.5) on the Q_perp complement, evaluation, and stand-alone building blocks.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -13,6 +14,8 @@ namespace phs {
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
 const char *last_error() { return g_err.c_str(); }
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- timers
 static thread_local std::vector<cudaEvent_t> g_pool;
@@ -444,8 +447,7 @@ static void project(phs_plan *pl, const double *v, double sign, double *out, con
 }
 
 static void matvec_norm(phs_plan *pl, const double *t, double *y, int precision, cudaStream_t s) {
-    if (precision == 0) fmm_apply64(pl->fmm, pl->tree, pl->ps, t, y, s, &pl->tm);
-    else fmm_apply32(pl->fmm, pl->tree, pl->ps, t, y, s, &pl->tm);
+    fmm_apply(pl->fmm, pl->tree, pl->ps, t, y, precision, s, &pl->tm);
 }
 
 static double read_scalar(phs_plan *pl, const double *dev, cudaStream_t s) {
@@ -558,6 +560,8 @@ void phs_options_default(phs_options *o, int k) {
 
 const char *phs_last_error(void) { return phs::last_error(); }
 
+int64_t phs_kernel_launches(void) { return (int64_t)phs::g_launches.load(); }
+
 phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_degree, int fmm_order, int vecchia_m,
                            const phs_options *opt, phs_stream_t stream, phs_plan_t *out) {
     PHS_TRY
@@ -580,7 +584,7 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         if (opt) pl->opt = *opt;
         else phs_options_default(&pl->opt, k);
         const phs_options &o = pl->opt;
-        PHS_REQUIRE(o.tol > 0 && o.maxiter >= 1 && o.precision >= 0 && o.precision <= 1, PHS_ERR_INVALID_ARG,
+        PHS_REQUIRE(o.tol > 0 && o.maxiter >= 1 && o.precision >= 0 && o.precision <= 3, PHS_ERR_INVALID_ARG,
                     "bad solver options");
         PHS_REQUIRE(o.ordering == 0 || o.ordering == 1, PHS_ERR_INVALID_ARG, "ordering must be 0 or 1");
         int p = fmm_order;
@@ -641,7 +645,7 @@ phs_status phs_plan_destroy(phs_plan_t plan) {
 phs_status phs_matvec(phs_plan_t pl, const double *t_dev, double *out_dev, int precision, phs_stream_t stream) {
     PHS_TRY
     PHS_REQUIRE(pl && t_dev && out_dev && t_dev != out_dev, PHS_ERR_INVALID_ARG, "bad arguments");
-    PHS_REQUIRE(precision == 0 || precision == 1, PHS_ERR_INVALID_ARG, "precision must be 0 or 1");
+    PHS_REQUIRE(precision >= 0 && precision <= 3, PHS_ERR_INVALID_ARG, "precision must be 0..3");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = pl->ps.n;
     double *ts = W(pl, 8), *y = W(pl, 9);
@@ -681,6 +685,8 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
     // rhs = sign * P f
     project(pl, fs, (double)pl->sign, rhs, rhs, sc + 6, s);
     const double rr0 = read_scalar(pl, sc + 6, s);
+    dots(pl, {{fs, fs}}, sc + 9, s);
+    const double fnrm = std::sqrt(read_scalar(pl, sc + 9, s));
     const double nrm0 = std::sqrt(rr0);
     const double stop = std::max(o.tol * nrm0, o.atol);
     double ms_mv = 0;
@@ -688,7 +694,8 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
     int iters = 0, outer = 0;
     double rr = rr0;
     bool converged = false;
-    if (nrm0 == 0.0) {
+    // f in span(B) up to rounding: the projected right-hand side is noise, w = 0
+    if (nrm0 <= 1e-14 * fnrm || nrm0 == 0.0) {
         zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
         converged = true;
     } else if (o.precision == 0) {
@@ -702,8 +709,8 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
         while (outer < o.max_refine && iters < o.maxiter) {
             double rri = 0;
             double *dx = W(pl, 8);  // rhs no longer needed
-            int it = pcg(pl, d, dx, std::max(o.inner_tol * res, 0.5 * stop), o.maxiter - iters, 1, &rri, s, &ms_mv,
-                         &n_mv);
+            int it = pcg(pl, d, dx, std::max(o.inner_tol * res, 0.5 * stop), std::min(o.maxiter - iters, 100),
+                         o.precision, &rri, s, &ms_mv, &n_mv);
             iters += it;
             ++outer;
             axpy_k<<<blocks_for(n, 256), 256, 0, s>>>(x, dx, n, 1.0);

@@ -369,8 +369,14 @@ __global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, const int *leaf
     double cx, cy, w;
     box_geom(tv, b, cx, cy, w);
     const int s = tv.start[b], e = tv.end[b];
-    for (int i0 = s; i0 < e; i0 += P2P_T) {
-        const int i = i0 + threadIdx.x;
+    // G threads share a target (power of two <= 32) so small leaves keep the block busy
+    const int nt = e - s;
+    int G = 1;
+    while (G < 32 && nt * G * 2 <= P2P_T) G <<= 1;
+    const int tpp = P2P_T / G;
+    const int sub = threadIdx.x & (G - 1);
+    for (int i0 = s; i0 < e; i0 += tpp) {
+        const int i = i0 + threadIdx.x / G;
         T xi = 0, yi = 0;
         if (i < e) {
             const double2 p = xs[i];
@@ -391,14 +397,15 @@ __global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, const int *leaf
                 }
                 __syncthreads();
                 const int jn = min(P2P_T, rg.y - j0);
-                for (int jj = 0; jj < jn; ++jj) {
+                for (int jj = sub; jj < jn; jj += G) {
                     const T dx = xi - sx[jj], dy = yi - sy[jj];
                     const T r2 = dx * dx + dy * dy;
                     if (r2 > T(0)) acc += phi_r2<T, K>(r2) * st[jj];
                 }
             }
         }
-        if (i < e) y[i] = (double)acc;
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (sub == 0 && i < e) y[i] = (double)acc;
     }
 }
 
@@ -460,19 +467,13 @@ static void ensure_bufs(Fmm &f, const Tree &t) {
     }
 }
 
-// upward pass, M2L and downward pass (local expansions of every box)
 template <typename T>
-static void far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, cudaStream_t s,
-                      Timers *tm) {
+static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, typename C2T<T>::type *mp,
+                   const typename C2T<T>::type *ops, int P, cudaStream_t s) {
     using C = typename C2T<T>::type;
-    ensure_bufs<T>(f, t);
-    C *mp = mp_buf<T>(f);
-    C *lc = lc_buf<T>(f);
-    const C *ops = ops_buf<T>(f);
     TreeView tv = tree_view(t);
-    const int nd = f.nd, P = P_of<T>(f);
+    const int nd = f.nd;
     const size_t esz = (size_t)nd * P * sizeof(C);
-    if (tm) tm->begin(s);
     const size_t p2m_smem = 32 * P * sizeof(C) + 32 * nd * sizeof(T);
     p2m_kernel<T><<<t.nleaf, FMM_T, p2m_smem, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, nd, P, mp);
     PHS_LAUNCH_CHECK();
@@ -481,23 +482,77 @@ static void far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *t
         if (nb > 0) m2m_kernel<T><<<nb, FMM_T, esz, s>>>(tv, b0, nd, P, ops, mp);
         PHS_LAUNCH_CHECK();
     }
-    if (tm) tm->end(T_UP, s);
-    if (tm) tm->begin(s);
+}
+template <typename T>
+static void m2l_pass(Fmm &f, const Tree &t, const typename C2T<T>::type *mp, typename C2T<T>::type *lc,
+                     const typename C2T<T>::type *ops, int P, cudaStream_t s) {
+    using C = typename C2T<T>::type;
+    const size_t esz = (size_t)f.nd * P * sizeof(C);
     PHS_CUDA(cudaMemsetAsync(lc, 0, (size_t)t.nbox * esz, s));
     if (t.depth >= 2) {
         const int b0 = t.lvl_off[2], nb = t.nbox - b0;
         if (nb > 0)
-            m2l_kernel<T><<<nb, FMM_T, esz, s>>>(tv, b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), nd, P, ops, mp,
-                                                 lc);
+            m2l_kernel<T><<<nb, FMM_T, esz, s>>>(tree_view(t), b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), f.nd,
+                                                 P, ops, mp, lc);
         PHS_LAUNCH_CHECK();
     }
-    if (tm) tm->end(T_M2L, s);
-    if (tm) tm->begin(s);
+}
+template <typename T>
+static void downward(Fmm &f, const Tree &t, typename C2T<T>::type *lc, const typename C2T<T>::type *ops, int P,
+                     cudaStream_t s) {
+    using C = typename C2T<T>::type;
+    const size_t esz = (size_t)f.nd * P * sizeof(C);
     for (int l = 3; l <= t.depth; ++l) {
         const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-        if (nb > 0) l2l_kernel<T><<<nb, FMM_T, esz, s>>>(tv, b0, nd, P, ops, lc);
+        if (nb > 0) l2l_kernel<T><<<nb, FMM_T, esz, s>>>(tree_view(t), b0, f.nd, P, ops, lc);
         PHS_LAUNCH_CHECK();
     }
+}
+
+__global__ void d2f_kernel(const double2 *in, float2 *out, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+__global__ void f2d_kernel(const float2 *in, double2 *out, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+// upward pass, M2L and downward pass (local expansions of every box) in one precision
+template <typename T>
+static void far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, cudaStream_t s,
+                      Timers *tm) {
+    ensure_bufs<T>(f, t);
+    const int P = P_of<T>(f);
+    if (tm) tm->begin(s);
+    upward<T>(f, t, ps, tv_sorted, mp_buf<T>(f), ops_buf<T>(f), P, s);
+    if (tm) tm->end(T_UP, s);
+    if (tm) tm->begin(s);
+    m2l_pass<T>(f, t, mp_buf<T>(f), lc_buf<T>(f), ops_buf<T>(f), P, s);
+    if (tm) tm->end(T_M2L, s);
+    if (tm) tm->begin(s);
+    downward<T>(f, t, lc_buf<T>(f), ops_buf<T>(f), P, s);
+    if (tm) tm->end(T_DOWN, s);
+}
+
+// FP64 upward/downward passes around an FP32 M2L of the same order
+static void far_field_m2l32(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, cudaStream_t s,
+                            Timers *tm) {
+    ensure_bufs<double>(f, t);
+    const size_t sz = (size_t)t.nbox * f.nd * f.P;
+    if (f.mpx32.n != sz) { f.mpx32.alloc(sz); f.lcx32.alloc(sz); }
+    if (tm) tm->begin(s);
+    upward<double>(f, t, ps, tv_sorted, f.mp64.get(), f.ops64.get(), f.P, s);
+    d2f_kernel<<<blocks_for((int64_t)sz, 256), 256, 0, s>>>(f.mp64.get(), f.mpx32.get(), sz);
+    PHS_LAUNCH_CHECK();
+    if (tm) tm->end(T_UP, s);
+    if (tm) tm->begin(s);
+    m2l_pass<float>(f, t, f.mpx32.get(), f.lcx32.get(), f.ops32p.get(), f.P, s);
+    if (tm) tm->end(T_M2L, s);
+    if (tm) tm->begin(s);
+    f2d_kernel<<<blocks_for((int64_t)sz, 256), 256, 0, s>>>(f.lcx32.get(), f.lc64.get(), sz);
+    PHS_LAUNCH_CHECK();
+    downward<double>(f, t, f.lc64.get(), f.ops64.get(), f.P, s);
     if (tm) tm->end(T_DOWN, s);
 }
 
@@ -519,18 +574,27 @@ static void p2p_dispatch(int k, const Tree &t, const PointSet &ps, const double 
 }
 
 template <typename T>
-static void apply_t(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s,
-                    Timers *tm) {
-    PHS_REQUIRE(f.log_core, PHS_ERR_INVALID_ARG, "odd spline orders need the distance-kernel FMM");
-    if (tm) tm->begin(s);
-    p2p_dispatch<T>(f.k, t, ps, tv_sorted, y, s);
-    if (tm) tm->end(T_P2P, s);
-    far_field<T>(f, t, ps, tv_sorted, s, tm);
+static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s) {
     using C = typename C2T<T>::type;
-    if (tm) tm->begin(s);
     l2p_kernel<T><<<t.nleaf, 128, (size_t)f.nd * P_of<T>(f) * sizeof(C), s>>>(
         tree_view(t), t.leaf_box.get(), ps.xs.get(), f.power, f.nd, P_of<T>(f), lc_buf<T>(f), y);
     PHS_LAUNCH_CHECK();
+}
+
+void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, int mode, cudaStream_t s,
+               Timers *tm) {
+    PHS_REQUIRE(f.log_core, PHS_ERR_INVALID_ARG, "odd spline orders need the distance-kernel FMM");
+    PHS_REQUIRE(mode >= 0 && mode <= 3, PHS_ERR_INVALID_ARG, "precision mode must be 0..3");
+    if (tm) tm->begin(s);
+    if (mode == 0) p2p_dispatch<double>(f.k, t, ps, t_sorted, y, s);
+    else p2p_dispatch<float>(f.k, t, ps, t_sorted, y, s);
+    if (tm) tm->end(T_P2P, s);
+    if (mode <= 1) far_field<double>(f, t, ps, t_sorted, s, tm);
+    else if (mode == 2) far_field_m2l32(f, t, ps, t_sorted, s, tm);
+    else far_field<float>(f, t, ps, t_sorted, s, tm);
+    if (tm) tm->begin(s);
+    if (mode == 3) l2p_pass<float>(f, t, ps, y, s);
+    else l2p_pass<double>(f, t, ps, y, s);
     if (tm) tm->end(T_DOWN, s);
 }
 
@@ -550,24 +614,20 @@ void fmm_setup(Fmm &f, int k, int p, int p32, const Tree &t, cudaStream_t s) {
     auto ops = build_ops(f.P);
     auto opsf = build_ops(f.P32);
     std::vector<double2> o64(ops.size());
-    std::vector<float2> o32(opsf.size());
-    for (size_t i = 0; i < ops.size(); ++i) o64[i] = make_double2((double)ops[i].real(), (double)ops[i].imag());
+    std::vector<float2> o32(opsf.size()), o32p(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+        o64[i] = make_double2((double)ops[i].real(), (double)ops[i].imag());
+        o32p[i] = make_float2((float)ops[i].real(), (float)ops[i].imag());
+    }
     for (size_t i = 0; i < opsf.size(); ++i) o32[i] = make_float2((float)opsf[i].real(), (float)opsf[i].imag());
     f.ops64.alloc(o64.size());
     f.ops32.alloc(o32.size());
+    f.ops32p.alloc(o32p.size());
     PHS_CUDA(cudaMemcpyAsync(f.ops64.get(), o64.data(), o64.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32.get(), o32.data(), o32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.ops32p.get(), o32p.data(), o32p.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaStreamSynchronize(s));
     (void)t;
-}
-
-void fmm_apply64(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, cudaStream_t s,
-                 Timers *tm) {
-    apply_t<double>(f, t, ps, t_sorted, y, s, tm);
-}
-void fmm_apply32(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, cudaStream_t s,
-                 Timers *tm) {
-    apply_t<float>(f, t, ps, t_sorted, y, s, tm);
 }
 
 // ---------------------------------------------------------------- evaluation at targets

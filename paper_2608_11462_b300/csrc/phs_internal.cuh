@@ -25,7 +25,14 @@ const char *last_error();
                                std::string(#call) + ": " + cudaGetErrorString(e_)};    \
         }                                                                               \
     } while (0)
-#define PHS_LAUNCH_CHECK() PHS_CUDA(cudaGetLastError())
+// every kernel launch in the library is followed by PHS_LAUNCH_CHECK(), which also
+// counts it (phs_kernel_launches)
+void count_launch();
+#define PHS_LAUNCH_CHECK()        \
+    do {                          \
+        ::phs::count_launch();    \
+        PHS_CUDA(cudaGetLastError()); \
+    } while (0)
 #define PHS_REQUIRE(cond, code, msg)                                                    \
     do {                                                                                \
         if (!(cond)) throw ::phs::Error{code, msg};                                     \
@@ -128,7 +135,8 @@ struct Fmm {
     DBuf<double2> mp64, lc64;
     DBuf<float2> mp32, lc32;
     DBuf<double2> ops64;  // M2M[4], L2L[4], M2L[49] (P x P each)
-    DBuf<float2> ops32;
+    DBuf<float2> ops32;   // same for the FP32 order P32
+    DBuf<float2> ops32p, mpx32, lcx32;  // FP32 copies at the FP64 order (FP32 M2L mode)
     DBuf<int> lvl_off_dev;
     // Chebyshev (distance kernel) data
     int cheb_q = 0;                      // nodes per dimension
@@ -139,10 +147,10 @@ struct Fmm {
 };
 void fmm_setup(Fmm &f, int k, int p, int p32, const Tree &t, cudaStream_t s);
 // y = M' t for sorted-order vectors in the normalised frame (M' of the normalised points)
-void fmm_apply64(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted,
-                 cudaStream_t s, struct Timers *tm);
-void fmm_apply32(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted,
-                 cudaStream_t s, struct Timers *tm);
+// mode 0: FP64 throughout; 1: FP32 near field + FP64 far field; 2: FP32 near field and
+// FP32 M2L inside FP64 upward/downward passes; 3: FP32 throughout (order p32)
+void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted, int mode,
+               cudaStream_t s, struct Timers *tm);
 // evaluate sum_j w_j phi(|x_j - y|) at normalised targets (after an FMM upward/downward
 // pass on w), out written (overwritten) for m targets
 void fmm_eval64(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted,

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     with open(os.path.join(ROOT, "include", "phs.h")) as fh:
         txt = fh.read()
-    return sorted(set(re.findall(r"^\s*(?:phs_status|void|const char \*)\s*(phs_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:phs_status|void|int64_t|const char \*)\s*(phs_\w+)\s*\(", txt, re.M)))
 
 
 @pytest.fixture(scope="module")
