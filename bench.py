@@ -27,6 +27,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PCG fit time to 1e-8 at n=1M TPS"
 WORKLOAD = "tps_1m"
+# Matern nu = 1.5 with range 0.1 in the caller frame ([0,1]^2): alpha = 1/0.1, i.e. 20 in the
+# normalised frame [-1/4,1/4]^2 (rho = 0.5)
+NU, ALPHA = 1.5, 20.0
 
 
 def parse():
@@ -35,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--n", type=int, default=None, help="override the point count (smaller parity runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -117,7 +120,7 @@ def oracle_step(points, f, targets, n_sample, seed=0):
     xn, c, rho = oracle.normalize(p, 0.25)
     order = oracle.random_order(n_sample, 1)
     nbr = oracle.knn_prev(xn, order, 30)
-    d, o, _ = oracle.vecchia_factor(xn, order, nbr, 30, 1.5, 0.35)
+    d, o, _ = oracle.vecchia_factor(xn, order, nbr, 30, NU, ALPHA)
     w, beta, it, _ = oracle.pcg(xn, fs, 2, 1, (nbr, d, o), tol=1e-8, maxiter=300)
     yn = (targets - c) * rho
     oracle.interpolant(xn, w, beta, 2, 1, yn)
@@ -182,7 +185,7 @@ def main():
     import paper_2608_11462_b300 as phs
 
     L = phs.lib()
-    opts = phs.options(2, precision=args.precision, tol=1e-8, nu=1.5, alpha=0.35, leaf_cap=64)
+    opts = phs.options(2, precision=args.precision, tol=1e-8, nu=NU, alpha=ALPHA, leaf_cap=64)
     pts_d = torch.tensor(points, device=dev)
     f_d = torch.tensor(f, device=dev)
     tg_d = torch.tensor(targets, device=dev)
@@ -301,7 +304,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
         "fits_per_s": world / t_step,
         "config": {"workload": WORKLOAD, "n": n, "targets": m_t, "k": 2, "poly_degree": 1, "vecchia_m": 30,
-                   "nu": 1.5, "alpha": 0.35, "ordering": "random", "leaf_cap": 64, "fmm_order": sizes[3],
+                   "nu": NU, "alpha_normalised": ALPHA, "range_user": 0.1, "ordering": "random", "leaf_cap": 64, "fmm_order": sizes[3],
                    "precision_mode": args.precision, "tol": 1e-8, "parallelism": f"replicas{world}",
                    "l2": "flushed (256 MB write) between timed steps"},
         "pcg": {"iters": info["iters"], "outer_iters": info["outer_iters"], "converged": info["converged"],

@@ -70,7 +70,7 @@ typedef struct {
     double alpha;           /* Matern inverse range in the NORMALISED frame; default 0.35 (k<=3), 2 (k>=4) */
     double domain_halfwidth;/* points are mapped into [-h, h]^2; default 0.25 (k<=3), 1 (k>=4) */
     uint64_t seed;          /* random enumeration seed */
-    double fmm_eps;         /* FMM truncation target used when fmm_order <= 0; default 1e-13 */
+    double fmm_eps;         /* FMM truncation target used when fmm_order <= 0; default 1e-11 */
     double inner_tol;       /* precision 1: relative tolerance of each inner FP32 solve; default 1e-4 */
     int max_refine;         /* precision 1: maximum refinement steps; default 8 */
 } phs_options;

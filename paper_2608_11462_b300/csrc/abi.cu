@@ -553,7 +553,7 @@ void phs_options_default(phs_options *o, int k) {
     o->alpha = k >= 4 ? 2.0 : 0.35;
     o->domain_halfwidth = k >= 4 ? 1.0 : 0.25;
     o->seed = 1;
-    o->fmm_eps = 1e-13;
+    o->fmm_eps = 1e-11;
     o->inner_tol = 1e-4;
     o->max_refine = 8;
 }
