@@ -358,12 +358,57 @@ __device__ __forceinline__ float phi_r2<float, 2>(float r2) { return 0.5f * r2 *
 template <>
 __device__ __forceinline__ float phi_r2<float, 4>(float r2) { return 0.5f * r2 * r2 * __logf(r2); }
 
+// Table-driven natural logarithm in FP64, after P. T. P. Tang, "Table-driven
+// implementation of the logarithm function in IEEE floating-point arithmetic"
+// (ACM TOMS 16(4), 1990):  x = 2^e m with m in [1, 2);  F = 1 + j/1024 is the
+// grid point nearest m;  log x = e log 2 + log F + log(1 + r),  r = (m - F)/F,
+// |r| <= 2^-11, with log(1 + r) from its degree-4 Taylor polynomial (truncation
+// below 6e-18).  log F and 1/F come from 1025-entry tables in shared memory.
+// Valid for positive normal x.  FP64 work: 1 DADD + 1 DMUL + 3 DFMA + 1 DMUL + 1 DFMA.
+constexpr int kLogTab = 1025;
+__device__ double g_logtab[kLogTab];
+__device__ double g_invtab[kLogTab];
+
+__device__ __forceinline__ double tab_log(double x, const double *lf, const double *inv) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int e = (hi >> 20) - 1023;
+    const int j = (((hi >> 9) & 0x7ff) + 1) >> 1;
+    const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
+    const double F = j < 1024 ? __hiloint2double(0x3ff00000 | (j << 10), 0) : 2.0;
+    const double r = (m - F) * inv[j];
+    double c = fma(-0.25, r, 0.33333333333333333);
+    c = fma(c, r, -0.5);
+    c = fma(c, r, 1.0);
+    return fma((double)e, 0.69314718055994530942, fma(c, r, lf[j]));
+}
+
 constexpr int P2P_T = 128;
+
+// even-K FP64 near field with the table-driven logarithm
+template <int K>
+__device__ __forceinline__ double phi_r2_tab(double r2, const double *lf, const double *inv) {
+    const double L = tab_log(r2, lf, inv);
+    return K == 2 ? 0.5 * r2 * L : 0.5 * r2 * r2 * L;
+}
+
+template <typename T, int K>
+struct UsesLogTab {
+    static constexpr bool value = sizeof(T) == 8 && (K % 2 == 0);
+};
+
 template <typename T, int K>
 __global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, const int *leaf_box, const int *near_off,
                                                    const int2 *near_rng, const double2 *xs, const double *t,
                                                    double *y) {
     __shared__ T sx[P2P_T], sy[P2P_T], st[P2P_T];
+    extern __shared__ double logtab_sm[];  // [2][kLogTab] when the table log is used
+    const double *lf = logtab_sm, *inv = logtab_sm + kLogTab;
+    if (UsesLogTab<T, K>::value) {
+        for (int i = threadIdx.x; i < kLogTab; i += P2P_T) {
+            logtab_sm[i] = g_logtab[i];
+            logtab_sm[kLogTab + i] = g_invtab[i];
+        }
+    }
     const int li = blockIdx.x;
     const int b = leaf_box[li];
     double cx, cy, w;
@@ -400,7 +445,11 @@ __global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, const int *leaf
                 for (int jj = sub; jj < jn; jj += G) {
                     const T dx = xi - sx[jj], dy = yi - sy[jj];
                     const T r2 = dx * dx + dy * dy;
-                    if (r2 > T(0)) acc += phi_r2<T, K>(r2) * st[jj];
+                    if (UsesLogTab<T, K>::value) {
+                        if (r2 > T(0)) acc += (T)phi_r2_tab<K>((double)r2, lf, inv) * st[jj];
+                    } else {
+                        if (r2 > T(0)) acc += phi_r2<T, K>(r2) * st[jj];
+                    }
                 }
             }
         }
@@ -558,9 +607,22 @@ static void far_field_m2l32(Fmm &f, const Tree &t, const PointSet &ps, const dou
 
 template <typename T, int K>
 static void p2p_launch(const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s) {
-    p2p_kernel<T, K><<<t.nleaf, P2P_T, 0, s>>>(tree_view(t), t.leaf_box.get(), t.near_off.get(), t.near_rng.get(),
-                                               ps.xs.get(), tv_sorted, y);
+    const size_t smem = UsesLogTab<T, K>::value ? 2 * kLogTab * sizeof(double) : 0;
+    p2p_kernel<T, K><<<t.nleaf, P2P_T, smem, s>>>(tree_view(t), t.leaf_box.get(), t.near_off.get(),
+                                                  t.near_rng.get(), ps.xs.get(), tv_sorted, y);
     PHS_LAUNCH_CHECK();
+}
+
+// log F_j and 1/F_j, F_j = 1 + j/1024, for the table-driven logarithm
+static void upload_log_tables() {
+    std::vector<double> lf(kLogTab), inv(kLogTab);
+    for (int j = 0; j < kLogTab; ++j) {
+        const long double F = 1.0L + (long double)j / 1024.0L;
+        lf[j] = (double)std::log(F);
+        inv[j] = (double)(1.0L / F);
+    }
+    PHS_CUDA(cudaMemcpyToSymbol(g_logtab, lf.data(), kLogTab * sizeof(double)));
+    PHS_CUDA(cudaMemcpyToSymbol(g_invtab, inv.data(), kLogTab * sizeof(double)));
 }
 template <typename T>
 static void p2p_dispatch(int k, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s) {
@@ -627,6 +689,7 @@ void fmm_setup(Fmm &f, int k, int p, int p32, const Tree &t, cudaStream_t s) {
     PHS_CUDA(cudaMemcpyAsync(f.ops32.get(), o32.data(), o32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32p.get(), o32p.data(), o32p.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaStreamSynchronize(s));
+    upload_log_tables();
     (void)t;
 }
 
