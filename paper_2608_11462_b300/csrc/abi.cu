@@ -597,7 +597,11 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         pl->sign = cpd_sign(k);
         PHS_CUDA(cudaMallocHost((void **)&pl->hscal, 64 * sizeof(double)));
         build_points_and_tree(pts_dev, n, o.domain_halfwidth, o.leaf_cap, pl->ps, pl->tree, s);
-        fmm_setup(pl->fmm, k, p, std::min(p, 24), pl->tree, s);
+        // Chebyshev order for the distance kernel: interpolation error ~ 5.83^-q at the
+        // V-list separation (Bernstein ellipse of a unit gap), q in [6, 16]
+        const double eps_q = fmm_order > 0 ? std::pow(0.55, fmm_order) : o.fmm_eps;
+        const int cq = std::max(6, std::min(16, (int)std::ceil(std::log(eps_q) / std::log(1.0 / 5.83)) + 1));
+        fmm_setup(pl->fmm, k, p, std::min(p, 24), cq, pl->tree, s);
         // thin QR of B by two rounds of Cholesky QR (Q has orthonormal columns, R upper)
         pl->Q.alloc((size_t)S * n);
         pl->R.alloc((size_t)S * S * 3);

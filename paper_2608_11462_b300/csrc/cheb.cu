@@ -1,0 +1,380 @@
+// cheb.cu -- far field of the distance kernel |x - y| (odd k: r^k = r * r^{k-1}, Eq. 2.6
+// with the distance core kernel of Sec. 4) by Chebyshev interpolation on every box.
+//
+// The paper names the distance-kernel FMM as future work and gives no expansions; this
+// file uses tensor-product Chebyshev interpolation (kernel-independent FMM):
+//   nodes       xb_m = cos((2m+1) pi / (2q)), m = 0..q-1, per axis; box node (m1, m2)
+//   basis       S(xb, t) = 1/q + (2/q) sum_{k=1}^{q-1} T_k(xb) T_k(t)  (= Lagrange basis)
+//   P2M         W[m] = sum_j q_j S(xb_m1, s_j1) S(xb_m2, s_j2),  s_j = (x_j - c)/h
+//   M2M / L2L   child nodes sit at +-1/2 + xb/2 in the parent frame
+//   M2L         L_t[m] += h * sum_n |xb_m - xb_n - 2 o| W_s[n]  (o = source offset in
+//               box widths; |x - y| is homogeneous, so one matrix per offset class
+//               serves every level after scaling by the half-width h)
+//   L2P         pot(x) = sum_m S(xb_m1, s1) S(xb_m2, s2) L[m]
+#include <cmath>
+#include <vector>
+
+#include "geom.cuh"
+#include "phs_internal.cuh"
+
+namespace phs {
+
+constexpr int kChebMaxQ = 16;
+constexpr int CHEB_T = 256;
+
+namespace {
+
+__device__ __forceinline__ void box_center_h(const TreeView &tv, int b, double &cx, double &cy, double &h) {
+    int ix, iy;
+    demorton(tv.key[b], ix, iy);
+    const double w = box_width(tv.R, tv.level[b]);
+    cx = -tv.R + (ix + 0.5) * w;
+    cy = -tv.R + (iy + 0.5) * w;
+    h = 0.5 * w;
+}
+
+// S(xb_m, t) for m = 0..q-1 (Tn[k*q + m] = T_k(xb_m))
+__device__ __forceinline__ void cheb_basis(double t, int q, const double *Tn, double *S) {
+    double Tk[kChebMaxQ];
+    Tk[0] = 1.0;
+    if (q > 1) Tk[1] = t;
+    for (int k = 2; k < q; ++k) Tk[k] = 2.0 * t * Tk[k - 1] - Tk[k - 2];
+    const double iq = 1.0 / q;
+    for (int m = 0; m < q; ++m) {
+        double s = 0.0;
+        for (int k = 1; k < q; ++k) s += Tn[k * q + m] * Tk[k];
+        S[m] = iq + 2.0 * iq * s;
+    }
+}
+
+__device__ __forceinline__ void had_v_cheb(int power, double x, double y, double *v) {
+    const double a = x * x + y * y;
+    if (power == 0) {
+        v[0] = 1.0;
+    } else if (power == 2) {
+        v[0] = 1.0; v[1] = a; v[2] = x; v[3] = y;
+    } else {
+        v[0] = 1.0; v[1] = a * a; v[2] = a; v[3] = x; v[4] = y;
+        v[5] = a * x; v[6] = a * y; v[7] = x * x; v[8] = x * y; v[9] = y * y;
+    }
+}
+__device__ __forceinline__ void had_u_cheb(int power, double x, double y, double *u) {
+    const double a = x * x + y * y;
+    if (power == 0) {
+        u[0] = 1.0;
+    } else if (power == 2) {
+        u[0] = a; u[1] = 1.0; u[2] = -2.0 * x; u[3] = -2.0 * y;
+    } else {
+        u[0] = a * a; u[1] = 1.0; u[2] = 2.0 * a; u[3] = -4.0 * a * x; u[4] = -4.0 * a * y;
+        u[5] = -4.0 * x; u[6] = -4.0 * y; u[7] = 4.0 * x * x; u[8] = 8.0 * x * y; u[9] = 4.0 * y * y;
+    }
+}
+
+// P2M on leaves: W[b][d][m1*q+m2]
+__global__ void cheb_p2m(TreeView tv, const int *leaf_box, const double2 *xs, const double *t, int power, int nd, int q,
+                         const double *Tn_g, double *W) {
+    __shared__ double Tn[kChebMaxQ * kChebMaxQ];
+    __shared__ double S1[32][kChebMaxQ], S2[32][kChebMaxQ], qd[32][10];
+    for (int i = threadIdx.x; i < q * q; i += blockDim.x) Tn[i] = Tn_g[i];
+    const int b = leaf_box[blockIdx.x];
+    double cx, cy, h;
+    box_center_h(tv, b, cx, cy, h);
+    const double ih = 1.0 / h;
+    const int s = tv.start[b], e = tv.end[b];
+    const int qq = q * q;
+    const int m = threadIdx.x;  // node index (q*q <= 256)
+    const int m1 = m / q, m2 = m - (m / q) * q;
+    double acc[10];
+    for (int d = 0; d < nd; ++d) acc[d] = 0.0;
+    __syncthreads();
+    for (int j0 = s; j0 < e; j0 += 32) {
+        if (threadIdx.x < 32) {
+            const int j = j0 + threadIdx.x;
+            if (j < e) {
+                const double2 p = xs[j];
+                cheb_basis(fmin(1.0, fmax(-1.0, (p.x - cx) * ih)), q, Tn, S1[threadIdx.x]);
+                cheb_basis(fmin(1.0, fmax(-1.0, (p.y - cy) * ih)), q, Tn, S2[threadIdx.x]);
+                double v[10];
+                had_v_cheb(power, p.x, p.y, v);
+                const double tj = t[j];
+                for (int d = 0; d < nd; ++d) qd[threadIdx.x][d] = v[d] * tj;
+            } else {
+                for (int d = 0; d < nd; ++d) qd[threadIdx.x][d] = 0.0;
+                for (int k = 0; k < q; ++k) S1[threadIdx.x][k] = S2[threadIdx.x][k] = 0.0;
+            }
+        }
+        __syncthreads();
+        if (m < qq) {
+            const int jn = min(32, e - j0);
+            for (int jj = 0; jj < jn; ++jj) {
+                const double sv = S1[jj][m1] * S2[jj][m2];
+                for (int d = 0; d < nd; ++d) acc[d] += qd[jj][d] * sv;
+            }
+        }
+        __syncthreads();
+    }
+    if (m < qq)
+        for (int d = 0; d < nd; ++d) W[((size_t)b * nd + d) * qq + m] = acc[d];
+}
+
+// separable 2D application of the 1D child-node matrices A[sx], A[sy]:
+// out[m1][m2] (+)= sum_{a,c} Ax(m1,a) Ay(m2,c) in[a][c], with TRANS selecting A' (L2L)
+template <bool TRANS>
+__device__ __forceinline__ double sep_apply(const double *Ax, const double *Ay, const double *in, double *tmp, int q,
+                                            int m1, int m2, bool active) {
+    // tmp[a][m2] = sum_c Ay(m2, c) in[a][c]
+    const int qq = q * q;
+    for (int idx = threadIdx.x; idx < qq; idx += blockDim.x) {
+        const int a = idx / q, mm2 = idx - a * q;
+        double s = 0.0;
+        for (int c = 0; c < q; ++c) s += (TRANS ? Ay[c * q + mm2] : Ay[mm2 * q + c]) * in[a * q + c];
+        tmp[idx] = s;
+    }
+    __syncthreads();
+    double r = 0.0;
+    if (active)
+        for (int a = 0; a < q; ++a) r += (TRANS ? Ax[a * q + m1] : Ax[m1 * q + a]) * tmp[a * q + m2];
+    __syncthreads();
+    return r;
+}
+
+// M2M for the non-leaf boxes of one level; A holds [2][q][q]: A[s][m][m'] = S(xb_m, s*1 - 1/2 + xb_m'/2)
+__global__ void cheb_m2m(TreeView tv, int b0, int nd, int q, const double *A, double *W) {
+    __shared__ double in[kChebMaxQ * kChebMaxQ], tmp[kChebMaxQ * kChebMaxQ];
+    const int b = b0 + blockIdx.x;
+    const int nc = tv.nchild[b];
+    if (nc == 0) return;
+    const int qq = q * q;
+    const int m = threadIdx.x, m1 = m / q, m2 = m % q;
+    const bool active = m < qq;
+    for (int d = 0; d < nd; ++d) {
+        double acc = 0.0;
+        for (int c = tv.child[b]; c < tv.child[b] + nc; ++c) {
+            for (int i = threadIdx.x; i < qq; i += blockDim.x) in[i] = W[((size_t)c * nd + d) * qq + i];
+            __syncthreads();
+            const int quad = (int)(tv.key[c] & 3);
+            const double *Ax = A + (size_t)(quad & 1) * qq, *Ay = A + (size_t)((quad >> 1) & 1) * qq;
+            acc += sep_apply<false>(Ax, Ay, in, tmp, q, m1, m2, active);
+        }
+        if (active) W[((size_t)b * nd + d) * qq + m] = acc;
+        __syncthreads();
+    }
+}
+
+// M2L over V lists: L_t[d][m] = h * sum_v sum_n K[cls][n][m] W_src[d][n]
+__global__ void cheb_m2l(TreeView tv, int b0, const int *v_off, const int *v_src, const unsigned char *v_cls, int nd,
+                         int q, const double *K, const double *W, double *L) {
+    extern __shared__ double wsm[];  // [nd][q*q]
+    const int b = b0 + blockIdx.x;
+    const int qq = q * q;
+    const int m = threadIdx.x;
+    double acc[10];
+    for (int d = 0; d < nd; ++d) acc[d] = 0.0;
+    for (int v = v_off[b]; v < v_off[b + 1]; ++v) {
+        const int src = v_src[v];
+        for (int i = threadIdx.x; i < nd * qq; i += blockDim.x) wsm[i] = W[(size_t)src * nd * qq + i];
+        __syncthreads();
+        if (m < qq) {
+            const double *Kc = K + (size_t)v_cls[v] * qq * qq;
+            for (int n = 0; n < qq; ++n) {
+                const double kv = Kc[(size_t)n * qq + m];
+                for (int d = 0; d < nd; ++d) acc[d] = fma(kv, wsm[d * qq + n], acc[d]);
+            }
+        }
+        __syncthreads();
+    }
+    if (m < qq) {
+        const double h = 0.5 * box_width(tv.R, tv.level[b]);
+        for (int d = 0; d < nd; ++d) L[((size_t)b * nd + d) * qq + m] = h * acc[d];
+    }
+}
+
+// L2L for one level: L_c += A' L_parent
+__global__ void cheb_l2l(TreeView tv, int b0, int nd, int q, const double *A, double *L) {
+    __shared__ double in[kChebMaxQ * kChebMaxQ], tmp[kChebMaxQ * kChebMaxQ];
+    const int b = b0 + blockIdx.x;
+    const int par = tv.parent[b];
+    const int qq = q * q;
+    const int m = threadIdx.x, m1 = m / q, m2 = m % q;
+    const bool active = m < qq;
+    const int quad = (int)(tv.key[b] & 3);
+    const double *Ax = A + (size_t)(quad & 1) * qq, *Ay = A + (size_t)((quad >> 1) & 1) * qq;
+    for (int d = 0; d < nd; ++d) {
+        for (int i = threadIdx.x; i < qq; i += blockDim.x) in[i] = L[((size_t)par * nd + d) * qq + i];
+        __syncthreads();
+        const double r = sep_apply<true>(Ax, Ay, in, tmp, q, m1, m2, active);
+        if (active) L[((size_t)b * nd + d) * qq + m] += r;
+        __syncthreads();
+    }
+}
+
+// local potential of box b at point (x, y) for density d
+__device__ __forceinline__ double cheb_l2p_point(const double *Lb, int q, const double *Tn, double sx, double sy) {
+    double S1[kChebMaxQ], S2[kChebMaxQ];
+    cheb_basis(sx, q, Tn, S1);
+    cheb_basis(sy, q, Tn, S2);
+    double r = 0.0;
+    for (int a = 0; a < q; ++a) {
+        double s = 0.0;
+        for (int c = 0; c < q; ++c) s += S2[c] * Lb[a * q + c];
+        r += S1[a] * s;
+    }
+    return r;
+}
+
+__global__ void cheb_l2p(TreeView tv, const int *leaf_box, const double2 *xs, int power, int nd, int q,
+                         const double *Tn_g, const double *L, double *y) {
+    extern __shared__ double lsm[];  // [nd][q*q] then Tn
+    const int b = leaf_box[blockIdx.x];
+    const int qq = q * q;
+    double *Tn = lsm + nd * qq;
+    for (int i = threadIdx.x; i < nd * qq; i += blockDim.x) lsm[i] = L[(size_t)b * nd * qq + i];
+    for (int i = threadIdx.x; i < qq; i += blockDim.x) Tn[i] = Tn_g[i];
+    __syncthreads();
+    double cx, cy, h;
+    box_center_h(tv, b, cx, cy, h);
+    const double ih = 1.0 / h;
+    for (int j = tv.start[b] + threadIdx.x; j < tv.end[b]; j += blockDim.x) {
+        const double2 p = xs[j];
+        const double sx = fmin(1.0, fmax(-1.0, (p.x - cx) * ih)), sy = fmin(1.0, fmax(-1.0, (p.y - cy) * ih));
+        double S1[kChebMaxQ], S2[kChebMaxQ];
+        cheb_basis(sx, q, Tn, S1);
+        cheb_basis(sy, q, Tn, S2);
+        double u[10];
+        had_u_cheb(power, p.x, p.y, u);
+        double sum = 0.0;
+        for (int d = 0; d < nd; ++d) {
+            const double *Lb = lsm + d * qq;
+            double r = 0.0;
+            for (int a = 0; a < q; ++a) {
+                double s = 0.0;
+                for (int c = 0; c < q; ++c) s += S2[c] * Lb[a * q + c];
+                r += S1[a] * s;
+            }
+            sum += u[d] * r;
+        }
+        y[j] += sum;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+void cheb_setup(Fmm &f, int q, cudaStream_t s) {
+    PHS_REQUIRE(q >= 3 && q <= kChebMaxQ, PHS_ERR_INVALID_ARG, "Chebyshev order must be in 3..16");
+    f.cheb_q = q;
+    const int qq = q * q;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<long double> xb(q);
+    for (int m = 0; m < q; ++m) xb[m] = std::cos((2 * m + 1) * pi / (2.0L * q));
+    auto S = [&](int m, long double t) {
+        long double Tk0 = 1, Tk1 = t, s = 0;
+        for (int k = 1; k < q; ++k) {
+            long double Tm = std::cos(k * (2 * m + 1) * pi / (2.0L * q));
+            s += Tm * Tk1;
+            long double Tk2 = 2 * t * Tk1 - Tk0;
+            Tk0 = Tk1;
+            Tk1 = Tk2;
+        }
+        return 1.0L / q + 2.0L / q * s;
+    };
+    // layout of cheb64: Tn [q*q] | A [2][q][q] | K [49][qq][qq] (K[cls][n][m])
+    const size_t nK = (size_t)49 * qq * qq;
+    std::vector<double> buf((size_t)qq + 2 * qq + nK, 0.0);
+    for (int k = 0; k < q; ++k)
+        for (int m = 0; m < q; ++m) buf[k * q + m] = (double)std::cos(k * (2 * m + 1) * pi / (2.0L * q));
+    for (int sgn = 0; sgn < 2; ++sgn)
+        for (int m = 0; m < q; ++m)
+            for (int mp = 0; mp < q; ++mp)
+                buf[qq + (size_t)sgn * qq + m * q + mp] = (double)S(m, (sgn ? 0.5L : -0.5L) + 0.5L * xb[mp]);
+    for (int dx = -3; dx <= 3; ++dx)
+        for (int dy = -3; dy <= 3; ++dy) {
+            if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+            const int cls = (dx + 3) * 7 + (dy + 3);
+            double *K = buf.data() + 3 * qq + (size_t)cls * qq * qq;
+            for (int n = 0; n < qq; ++n)
+                for (int m = 0; m < qq; ++m) {
+                    const long double ex = xb[m / q] - xb[n / q] - 2.0L * dx;
+                    const long double ey = xb[m % q] - xb[n % q] - 2.0L * dy;
+                    K[(size_t)n * qq + m] = (double)std::sqrt(ex * ex + ey * ey);
+                }
+        }
+    f.cheb64.alloc(buf.size());
+    PHS_CUDA(cudaMemcpyAsync(f.cheb64.get(), buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+}
+
+void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, cudaStream_t s, Timers *tm) {
+    const int q = f.cheb_q, qq = q * q, nd = f.nd;
+    const size_t sz = (size_t)t.nbox * nd * qq;
+    if (f.cw64.n != sz) {
+        f.cw64.alloc(sz);
+        f.cl64.alloc(sz);
+    }
+    const double *Tn = f.cheb64.get(), *A = Tn + qq, *K = Tn + 3 * qq;
+    TreeView tv = tree_view(t);
+    if (tm) tm->begin(s);
+    cheb_p2m<<<t.nleaf, CHEB_T, 0, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, nd, q, Tn,
+                                        f.cw64.get());
+    PHS_LAUNCH_CHECK();
+    for (int l = t.depth - 1; l >= 0; --l) {
+        const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
+        if (nb > 0) cheb_m2m<<<nb, CHEB_T, 0, s>>>(tv, b0, nd, q, A, f.cw64.get());
+        PHS_LAUNCH_CHECK();
+    }
+    if (tm) tm->end(T_UP, s);
+    if (tm) tm->begin(s);
+    PHS_CUDA(cudaMemsetAsync(f.cl64.get(), 0, sz * sizeof(double), s));
+    if (t.depth >= 2) {
+        const int b0 = t.lvl_off[2], nb = t.nbox - b0;
+        if (nb > 0)
+            cheb_m2l<<<nb, CHEB_T, (size_t)nd * qq * sizeof(double), s>>>(tv, b0, t.v_off.get(), t.v_src.get(),
+                                                                          t.v_cls.get(), nd, q, K, f.cw64.get(),
+                                                                          f.cl64.get());
+        PHS_LAUNCH_CHECK();
+    }
+    if (tm) tm->end(T_M2L, s);
+    if (tm) tm->begin(s);
+    for (int l = 3; l <= t.depth; ++l) {
+        const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
+        if (nb > 0) cheb_l2l<<<nb, CHEB_T, 0, s>>>(tv, b0, nd, q, A, f.cl64.get());
+        PHS_LAUNCH_CHECK();
+    }
+    if (tm) tm->end(T_DOWN, s);
+}
+
+void cheb_l2p_apply(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s) {
+    const int q = f.cheb_q, qq = q * q;
+    cheb_l2p<<<t.nleaf, 128, (size_t)(f.nd * qq + qq) * sizeof(double), s>>>(
+        tree_view(t), t.leaf_box.get(), ps.xs.get(), f.power, f.nd, q, f.cheb64.get(), f.cl64.get(), y);
+    PHS_LAUNCH_CHECK();
+}
+
+// far-field part of the interpolant at normalised targets (distance kernel):
+// out[i] += sum_d u_d(y_i) pot_d(y_i) from the local expansion of box_of[i] (if level >= 2)
+__global__ void cheb_eval_far(TreeView tv, const double2 *tgt, const int *box_of, int64_t m, int power, int nd, int q,
+                              const double *Tn, const double *L, double *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int b = box_of[i];
+    if (b < 0 || tv.level[b] < 2) return;
+    double cx, cy, h;
+    box_center_h(tv, b, cx, cy, h);
+    const double2 y = tgt[i];
+    const double sx = fmin(1.0, fmax(-1.0, (y.x - cx) / h)), sy = fmin(1.0, fmax(-1.0, (y.y - cy) / h));
+    double u[10];
+    had_u_cheb(power, y.x, y.y, u);
+    const int qq = q * q;
+    double acc = 0.0;
+    for (int d = 0; d < nd; ++d) acc += u[d] * cheb_l2p_point(L + ((size_t)b * nd + d) * qq, q, Tn, sx, sy);
+    out[i] += acc;
+}
+
+void cheb_eval_far_launch(Fmm &f, const Tree &t, const double2 *tgt, const int *box_of, int64_t m, double *out,
+                          cudaStream_t s) {
+    cheb_eval_far<<<blocks_for(m, 128), 128, 0, s>>>(tree_view(t), tgt, box_of, m, f.power, f.nd, f.cheb_q,
+                                                      f.cheb64.get(), f.cl64.get(), out);
+    PHS_LAUNCH_CHECK();
+}
+
+}  // namespace phs

@@ -645,8 +645,19 @@ static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaS
 
 void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, int mode, cudaStream_t s,
                Timers *tm) {
-    PHS_REQUIRE(f.log_core, PHS_ERR_INVALID_ARG, "odd spline orders need the distance-kernel FMM");
     PHS_REQUIRE(mode >= 0 && mode <= 3, PHS_ERR_INVALID_ARG, "precision mode must be 0..3");
+    if (!f.log_core) {
+        // odd k: distance-kernel far field by Chebyshev interpolation, FP64 only
+        PHS_REQUIRE(mode == 0, PHS_ERR_INVALID_ARG, "odd spline orders run in FP64 (precision 0)");
+        if (tm) tm->begin(s);
+        p2p_dispatch<double>(f.k, t, ps, t_sorted, y, s);
+        if (tm) tm->end(T_P2P, s);
+        cheb_far_field(f, t, ps, t_sorted, s, tm);
+        if (tm) tm->begin(s);
+        cheb_l2p_apply(f, t, ps, y, s);
+        if (tm) tm->end(T_DOWN, s);
+        return;
+    }
     if (tm) tm->begin(s);
     if (mode == 0) p2p_dispatch<double>(f.k, t, ps, t_sorted, y, s);
     else p2p_dispatch<float>(f.k, t, ps, t_sorted, y, s);
@@ -660,7 +671,7 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
     if (tm) tm->end(T_DOWN, s);
 }
 
-void fmm_setup(Fmm &f, int k, int p, int p32, const Tree &t, cudaStream_t s) {
+void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, const Tree &t, cudaStream_t s) {
     PHS_REQUIRE(k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "k must be in 1..5");
     PHS_REQUIRE(p >= 2 && p + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "fmm_order must be in 2..60");
     PHS_REQUIRE(p32 >= 2 && p32 + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "FP32 fmm order must be in 2..60");
@@ -690,32 +701,44 @@ void fmm_setup(Fmm &f, int k, int p, int p32, const Tree &t, cudaStream_t s) {
     PHS_CUDA(cudaMemcpyAsync(f.ops32p.get(), o32p.data(), o32p.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaStreamSynchronize(s));
     upload_log_tables();
+    if (!f.log_core) cheb_setup(f, cheb_q, s);
     (void)t;
 }
 
 // ---------------------------------------------------------------- evaluation at targets
-// One thread per target: deepest box containing it, L2P of that box's local
-// expansion, direct sum over its near set (same construction as the leaf lists).
-template <int K>
-__global__ void eval_kernel(TreeView tv, const double2 *xs, const double *w, const double2 *tgt, int64_t m, int power,
-                            int nd, int P, const double2 *lc, double *out, int *outside) {
+// Per target: the deepest box containing it, the direct sum over that box's near set
+// (the same construction as the leaf lists), and the far field from that box's local
+// expansion (complex log expansion or Chebyshev interpolant).  Targets outside the
+// root box are summed directly over all sources.
+__global__ void eval_box_kernel(TreeView tv, const double2 *tgt, int64_t m, int *box_of) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const double2 y = tgt[i];
     const double R = tv.R;
     if (!(y.x >= -R && y.x <= R && y.y >= -R && y.y <= R)) {
-        outside[i] = 1;
-        out[i] = 0.0;
+        box_of[i] = -1;
         return;
     }
-    outside[i] = 0;
     const int L = tv.depth;
     const double wl = box_width(R, L);
     long long ix = (long long)floor((y.x + R) / wl), iy = (long long)floor((y.y + R) / wl);
     const long long lim = (1ll << L) - 1;
     ix = ix < 0 ? 0 : (ix > lim ? lim : ix);
     iy = iy < 0 ? 0 : (iy > lim ? lim : iy);
-    const int b = find_deepest(tv, L, (int)ix, (int)iy);
+    box_of[i] = find_deepest(tv, L, (int)ix, (int)iy);
+}
+
+template <int K>
+__global__ void eval_near_kernel(TreeView tv, const double2 *xs, const double *w, const double2 *tgt, int64_t m,
+                                 const int *box_of, double *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int b = box_of[i];
+    if (b < 0) {
+        out[i] = 0.0;
+        return;
+    }
+    const double2 y = tgt[i];
     double acc = 0.0;
     enumerate_near(tv, b, [&](int s, int e) {
         for (int j = s; j < e; ++j) {
@@ -724,33 +747,41 @@ __global__ void eval_kernel(TreeView tv, const double2 *xs, const double *w, con
             if (r2 > 0) acc += phi_r2<double, K>(r2) * w[j];
         }
     });
-    if (tv.level[b] >= 2) {
-        double cx, cy, bw;
-        box_geom(tv, b, cx, cy, bw);
-        double2 v = make_double2((y.x - cx) / bw, (y.y - cy) / bw);
-        double u[kMaxNd];
-        had_u(power, y.x, y.y, u);
-        const double2 *Lb = lc + (size_t)b * nd * P;
-        for (int d = 0; d < nd; ++d) {
-            const double2 *Ld = Lb + d * P;
-            double2 h = Ld[P - 1];
-            for (int l = P - 2; l >= 0; --l) {
-                double2 t2 = cmul(h, v);
-                h.x = t2.x + Ld[l].x;
-                h.y = t2.y + Ld[l].y;
-            }
-            acc += u[d] * h.x;
-        }
-    }
     out[i] = acc;
+}
+
+__global__ void eval_far_log_kernel(TreeView tv, const double2 *tgt, int64_t m, const int *box_of, int power, int nd,
+                                    int P, const double2 *lc, double *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int b = box_of[i];
+    if (b < 0 || tv.level[b] < 2) return;
+    const double2 y = tgt[i];
+    double cx, cy, bw;
+    box_geom(tv, b, cx, cy, bw);
+    double2 v = make_double2((y.x - cx) / bw, (y.y - cy) / bw);
+    double u[kMaxNd];
+    had_u(power, y.x, y.y, u);
+    const double2 *Lb = lc + (size_t)b * nd * P;
+    double acc = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        const double2 *Ld = Lb + d * P;
+        double2 h = Ld[P - 1];
+        for (int l = P - 2; l >= 0; --l) {
+            double2 t2 = cmul(h, v);
+            h.x = t2.x + Ld[l].x;
+            h.y = t2.y + Ld[l].y;
+        }
+        acc += u[d] * h.x;
+    }
+    out[i] += acc;
 }
 
 // direct sum over all sources for targets outside the root box (block per target)
 template <int K>
-__global__ void eval_outside_kernel(const double2 *xs, int64_t n, const double *w, const double2 *tgt, int64_t m,
-                                    const int *outside, double *out) {
-    const int64_t i = blockIdx.x;
-    if (i >= m || !outside[i]) return;
+__global__ void eval_outside_kernel(const double2 *xs, int64_t n, const double *w, const double2 *tgt,
+                                    const int *out_idx, double *out) {
+    const int64_t i = out_idx[blockIdx.x];
     const double2 y = tgt[i];
     double acc = 0.0;
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
@@ -771,20 +802,40 @@ __global__ void eval_outside_kernel(const double2 *xs, int64_t n, const double *
 template <int K>
 static void eval_launch(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted, const double2 *tgt, int64_t m,
                         double *out, cudaStream_t s) {
-    DBuf<int> outside(std::max<int64_t>(m, 1));
-    eval_kernel<K><<<blocks_for(m, 128), 128, 0, s>>>(tree_view(t), ps.xs.get(), w_sorted, tgt, m, f.power, f.nd, f.P,
-                                                      f.lc64.get(), out, outside.get());
+    DBuf<int> box_of(std::max<int64_t>(m, 1));
+    TreeView tv = tree_view(t);
+    eval_box_kernel<<<blocks_for(m, 128), 128, 0, s>>>(tv, tgt, m, box_of.get());
     PHS_LAUNCH_CHECK();
-    eval_outside_kernel<K><<<(unsigned)std::max<int64_t>(m, 1), 256, 0, s>>>(ps.xs.get(), ps.n, w_sorted, tgt, m,
-                                                                              outside.get(), out);
+    eval_near_kernel<K><<<blocks_for(m, 128), 128, 0, s>>>(tv, ps.xs.get(), w_sorted, tgt, m, box_of.get(), out);
     PHS_LAUNCH_CHECK();
+    if (f.log_core) {
+        eval_far_log_kernel<<<blocks_for(m, 128), 128, 0, s>>>(tv, tgt, m, box_of.get(), f.power, f.nd, f.P,
+                                                               f.lc64.get(), out);
+        PHS_LAUNCH_CHECK();
+    } else {
+        cheb_eval_far_launch(f, t, tgt, box_of.get(), m, out, s);
+    }
+    // targets outside the root box
+    std::vector<int> hb(m);
+    PHS_CUDA(cudaMemcpyAsync(hb.data(), box_of.get(), m * sizeof(int), cudaMemcpyDeviceToHost, s));
     PHS_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> outside;
+    for (int64_t i = 0; i < m; ++i)
+        if (hb[i] < 0) outside.push_back((int)i);
+    if (!outside.empty()) {
+        DBuf<int> oi(outside.size());
+        PHS_CUDA(cudaMemcpyAsync(oi.get(), outside.data(), outside.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        eval_outside_kernel<K><<<(unsigned)outside.size(), 256, 0, s>>>(ps.xs.get(), ps.n, w_sorted, tgt, oi.get(),
+                                                                        out);
+        PHS_LAUNCH_CHECK();
+        PHS_CUDA(cudaStreamSynchronize(s));
+    }
 }
 
 void fmm_eval64(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted, const double2 *tgt, int64_t m,
                 double *out, cudaStream_t s, Timers *tm) {
-    PHS_REQUIRE(f.log_core, PHS_ERR_INVALID_ARG, "odd spline orders need the distance-kernel FMM");
-    far_field<double>(f, t, ps, w_sorted, s, nullptr);
+    if (f.log_core) far_field<double>(f, t, ps, w_sorted, s, nullptr);
+    else cheb_far_field(f, t, ps, w_sorted, s, nullptr);
     if (tm) tm->begin(s);
     switch (f.k) {
         case 1: eval_launch<1>(f, t, ps, w_sorted, tgt, m, out, s); break;

@@ -145,7 +145,14 @@ struct Fmm {
     DBuf<double> cw64, cl64;             // weights/potentials at nodes [box][nd][q*q]
     DBuf<float> cw32, cl32;
 };
-void fmm_setup(Fmm &f, int k, int p, int p32, const Tree &t, cudaStream_t s);
+void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, const Tree &t, cudaStream_t s);
+// distance-kernel far field (cheb.cu)
+void cheb_setup(Fmm &f, int q, cudaStream_t s);
+void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, cudaStream_t s,
+                    struct Timers *tm);
+void cheb_l2p_apply(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s);
+void cheb_eval_far_launch(Fmm &f, const Tree &t, const double2 *tgt, const int *box_of, int64_t m, double *out,
+                          cudaStream_t s);
 // y = M' t for sorted-order vectors in the normalised frame (M' of the normalised points)
 // mode 0: FP64 throughout; 1: FP32 near field + FP64 far field; 2: FP32 near field and
 // FP32 M2L inside FP64 upward/downward passes; 3: FP32 throughout (order p32)

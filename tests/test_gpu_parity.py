@@ -79,6 +79,32 @@ def test_fmm_matvec_mixed_precision(phs, k, mode, tol):
     assert err <= tol, err
 
 
+@pytest.mark.parametrize("k", [1, 3, 5])
+@pytest.mark.parametrize("geom", ["uniform", "clustered"])
+def test_fmm_matvec_odd_k_distance_kernel(phs, k, geom):
+    """Odd k: r^k = r * r^(k-1) through the distance-kernel (Chebyshev) far field."""
+    n = 3001
+    pts = np.random.default_rng(12).random((n, 2)) if geom == "uniform" else _clustered(n, 13)
+    t = np.random.default_rng(14).standard_normal(n)
+    plan = phs.Plan(_t(pts), k, fmm_order=0, vecchia_m=8, opts=phs.options(k, leaf_cap=16))
+    got = plan.matvec(_t(t), precision=0).cpu().numpy()
+    want = oracle.dense_matvec(pts, k, t)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= 1e-10, err
+
+
+def test_fit_cubic_mix_matches_dense_solve(phs):
+    """Workload cubic_mix scaled to n = 2,000 (k = 3, S = 3, Vecchia m = 20)."""
+    w_ = synth.workload("cubic_mix", n=2000, n_targets=300)
+    plan = phs.Plan(_t(w_["points"]), 3, vecchia_m=20, opts=phs.options(3, tol=1e-11, maxiter=400))
+    w, beta, info = plan.fit(_t(w_["f"]), allow_not_converged=True)
+    pred = plan.eval(w, beta, _t(w_["targets"])).cpu().numpy()
+    ref = oracle.fit_dense(w_["points"], w_["f"], 3)
+    want = oracle.predict(ref, w_["targets"])
+    err = np.max(np.abs(pred - want)) / np.max(np.abs(want))
+    assert err <= 1e-8, (err, info)
+
+
 def test_fmm_matvec_p20_reports_error(phs):
     """Config-1 order p = 20: expansion error ~0.55^20; stated, not gated at 1e-10."""
     w_ = synth.workload("uniform_tps")
