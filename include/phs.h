@@ -66,8 +66,10 @@ typedef struct {
     int maxiter;            /* PCG iterations (precision 0) or total inner iterations; default 200 */
     int leaf_cap;           /* quadtree leaf capacity s; default 64 */
     int ordering;           /* Vecchia enumeration: 0 random (Sec. 3), 1 exact maxmin */
-    double nu;              /* Matern smoothness: 0.5, 1, 1.5 or 2.5; default 1 (Sec. 2.2) */
-    double alpha;           /* Matern inverse range in the NORMALISED frame; default 0.35 (k<=3), 2 (k>=4) */
+    double nu;              /* Matern smoothness: 0.5, 1, 1.5, 2 or 2.5; default k/2, whose
+                               leading non-analytic term is the PHS kernel (nu = 1 for the
+                               thin-plate spline, Sec. 2.2, Eq. 2.17) */
+    double alpha;           /* Matern inverse range in the NORMALISED frame; default 0.35 (k<=3), 0.5 (k>=4) */
     double domain_halfwidth;/* points are mapped into [-h, h]^2; default 0.25 (k<=3), 1 (k>=4) */
     uint64_t seed;          /* random enumeration seed */
     double fmm_eps;         /* FMM truncation target used when fmm_order <= 0; default 1e-11 */

@@ -55,6 +55,8 @@ def lib():
         L.or_knn_prev.argtypes = [i64, P, P, i32, P]
         L.or_bessel_k1.restype = d
         L.or_bessel_k1.argtypes = [d]
+        L.or_bessel_k0.restype = d
+        L.or_bessel_k0.argtypes = [d]
         L.or_matern.restype = d
         L.or_matern.argtypes = [d, d, d]
         L.or_vecchia_factor.restype = i64
@@ -232,6 +234,10 @@ def bessel_k1(x: float) -> float:
     return lib().or_bessel_k1(float(x))
 
 
+def bessel_k0(x: float) -> float:
+    return lib().or_bessel_k0(float(x))
+
+
 def matern(nu: float, alpha: float, r) -> np.ndarray:
     r = np.atleast_1d(_f64(r))
     L = lib()
@@ -347,7 +353,8 @@ def predict(fit: dict, targets) -> np.ndarray:
 
 
 def nu_alpha_default(k: int):
-    """Paper's preconditioner parameters (Sec. 2.2): nu = 1; alpha ~= 0.35 in
-    [-1/4,1/4]^2 for k = 2, alpha ~= 2 in [-1,1]^2 for k = 4."""
-    return (1.0, 0.35) if k <= 3 else (1.0, 2.0)
+    """Preconditioner parameters: nu = k/2, the Matern whose leading non-analytic
+    term is the PHS kernel (Sec. 2.2, Eq. 2.17 for k = 2: nu = 1, alpha ~= 0.35 in
+    [-1/4,1/4]^2); alpha = 0.5 in [-1,1]^2 for k >= 4."""
+    return (k / 2.0, 0.35) if k <= 3 else (k / 2.0, 0.5)
 

@@ -217,9 +217,38 @@ double or_bessel_k1(double x)
     return h * s;
 }
 
+/* Modified Bessel function K_0(x), x > 0: DLMF 10.31.2 for x <= 2,
+ *   K_0(x) = -(ln(x/2) + gamma) I_0(x) + sum_{k>=1} H_k (x^2/4)^k / (k!)^2,
+ *   I_0(x) = sum_k (x^2/4)^k / (k!)^2,
+ * and the trapezoidal rule on DLMF 10.32.9, K_0(x) = int_0^inf exp(-x cosh t) dt, for x > 2. */
+double or_bessel_k0(double x)
+{
+    const double euler_gamma = 0.57721566490153286060651209;
+    if (x <= 2.0) {
+        double q = 0.25 * x * x, term = 1.0, hk = 0.0, s_i = 1.0, s_h = 0.0;
+        for (int k = 1; k < 60; ++k) {
+            term *= q / ((double)k * (double)k);
+            hk += 1.0 / k;
+            s_i += term;
+            s_h += hk * term;
+            if (term < 1e-22 * s_i) break;
+        }
+        return -(log(0.5 * x) + euler_gamma) * s_i + s_h;
+    }
+    double h = 1.0 / 64.0, s = 0.0;
+    for (int j = 0; ; ++j) {
+        double f = exp(-x * cosh(j * h));
+        s += (j == 0 ? 0.5 : 1.0) * f;
+        if (j > 0 && f < 1e-30 * s) break;
+        if (j > 4000) break;
+    }
+    return h * s;
+}
+
 /* Matern covariance with unit variance, Sec. 2.2:
  *   K(r) = 2^{1-nu}/Gamma(nu) (alpha r)^nu K_nu(alpha r),  K(0) = 1.
- * Implemented for nu = 1 (alpha r K_1(alpha r)), the paper's choice, and for
+ * Implemented for nu = 1 (alpha r K_1(alpha r)), the paper's choice, nu = 2
+ * ((alpha r)^2 K_2(alpha r) / 2 with K_2 = K_0 + (2/x) K_1, DLMF 10.29.1), and
  * the half-integer cases nu = 0.5, 1.5, 2.5 where K_nu is elementary. */
 double or_matern(double nu, double alpha, double r)
 {
@@ -229,6 +258,7 @@ double or_matern(double nu, double alpha, double r)
     if (nu == 1.5) return (1.0 + a) * exp(-a);
     if (nu == 2.5) return (1.0 + a + a * a / 3.0) * exp(-a);
     if (nu == 1.0) return a * or_bessel_k1(a);
+    if (nu == 2.0) return 0.5 * a * a * or_bessel_k0(a) + a * or_bessel_k1(a);
     return NAN;
 }
 

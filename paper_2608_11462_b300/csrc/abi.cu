@@ -549,8 +549,9 @@ void phs_options_default(phs_options *o, int k) {
     o->maxiter = 200;
     o->leaf_cap = 64;
     o->ordering = 0;
-    o->nu = 1.0;
-    o->alpha = k >= 4 ? 2.0 : 0.35;
+    // Matern smoothness k/2: its leading non-analytic term is r^k (log r), the PHS kernel
+    o->nu = 0.5 * (k < 1 ? 2 : k);
+    o->alpha = k >= 4 ? 0.5 : 0.35;
     o->domain_halfwidth = k >= 4 ? 1.0 : 0.25;
     o->seed = 1;
     o->fmm_eps = 1e-11;

@@ -177,12 +177,41 @@ __device__ double bessel_k1(double x) {
     return h * s;
 }
 
+// K_0 by the ascending series (DLMF 10.31.2) for x <= 2 and the trapezoidal rule on
+// K_0(x) = int_0^inf exp(-x cosh t) dt (DLMF 10.32.9) for x > 2.
+__device__ double bessel_k0(double x) {
+    if (x <= 2.0) {
+        const double eg = 0.57721566490153286061;
+        const double q = 0.25 * x * x;
+        double term = 1.0, hk = 0.0, si = 1.0, sh = 0.0;
+        for (int k = 1; k < 40; ++k) {
+            term *= q / ((double)k * (double)k);
+            hk += 1.0 / k;
+            si += term;
+            sh += hk * term;
+            if (term < 1e-20 * si) break;
+        }
+        return -(log(0.5 * x) + eg) * si + sh;
+    }
+    const double h = 0.25;
+    double s = 0.5 * exp(-x);
+    for (int j = 1; j < 200; ++j) {
+        const double f = exp(-x * cosh(j * h));
+        s += f;
+        if (f < 1e-19 * s) break;
+    }
+    return h * s;
+}
+
+// Matern with K(0) = 1: nu in {0.5, 1.5, 2.5} closed forms; nu = 1: a K_1(a);
+// nu = 2: a^2 K_2(a) / 2 = a^2 K_0(a) / 2 + a K_1(a)  (K_2 = K_0 + (2/a) K_1)
 __device__ __forceinline__ double matern(double nu, double alpha, double r) {
     const double a = alpha * r;
     if (a == 0.0) return 1.0;
     if (nu == 0.5) return exp(-a);
     if (nu == 1.5) return (1.0 + a) * exp(-a);
     if (nu == 2.5) return (1.0 + a + a * a / 3.0) * exp(-a);
+    if (nu == 2.0) return 0.5 * a * a * bessel_k0(a) + a * bessel_k1(a);
     return a * bessel_k1(a);  // nu == 1
 }
 
@@ -518,7 +547,8 @@ void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr
 int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, double nu,
                            double alpha, double *val_ell, cudaStream_t s) {
     PHS_REQUIRE(m >= 1 && m <= KNN_MAXM, PHS_ERR_INVALID_ARG, "conditioning-set size m must be in 1..64");
-    PHS_REQUIRE(nu == 0.5 || nu == 1.0 || nu == 1.5 || nu == 2.5, PHS_ERR_INVALID_ARG, "nu must be 0.5, 1, 1.5 or 2.5");
+    PHS_REQUIRE(nu == 0.5 || nu == 1.0 || nu == 1.5 || nu == 2.0 || nu == 2.5, PHS_ERR_INVALID_ARG,
+                "nu must be 0.5, 1, 1.5, 2 or 2.5");
     PHS_REQUIRE(alpha > 0 && std::isfinite(alpha), PHS_ERR_INVALID_ARG, "alpha must be positive");
     const size_t per = (size_t)(m * m + 3 * m + 1) * sizeof(double);
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));

@@ -41,7 +41,9 @@ def test_options_default_host_only(native):
     native.lib().phs_options_default(ctypes.byref(o), 2)
     assert o.tol == 1e-8 and o.domain_halfwidth == 0.25 and abs(o.alpha - 0.35) < 1e-15 and o.nu == 1.0
     native.lib().phs_options_default(ctypes.byref(o), 4)
-    assert o.domain_halfwidth == 1.0 and o.alpha == 2.0
+    assert o.domain_halfwidth == 1.0 and o.alpha == 0.5 and o.nu == 2.0
+    native.lib().phs_options_default(ctypes.byref(o), 3)
+    assert o.nu == 1.5
     assert native.lib().phs_last_error() is not None
 
 

@@ -170,6 +170,9 @@ def _local_kappa(x, nbr, nu, alpha):
         a = alpha * d
         if nu == 1.5:
             K = (1 + a) * np.exp(-a)
+        elif nu == 2.0:
+            with np.errstate(all="ignore"):
+                K = np.where(a > 0, a * a * scipy.special.kv(2, np.where(a > 0, a, 1.0)) / 2, 1.0)
         else:
             with np.errstate(all="ignore"):
                 K = np.where(a > 0, a * scipy.special.k1(np.where(a > 0, a, 1.0)), 1.0)
@@ -183,7 +186,7 @@ def _check_factor(d_g, o_g, d_w, o_w, kap):
     assert np.all(np.max(np.abs(o_g - o_w), axis=1) <= tol * np.maximum(np.max(np.abs(o_w), axis=1), 1e-300))
 
 
-@pytest.mark.parametrize("nu,alpha", [(1.5, 20.0), (1.0, 0.35 * 4)])
+@pytest.mark.parametrize("nu,alpha", [(1.5, 20.0), (1.0, 0.35 * 4), (2.0, 3.0), (2.0, 0.5)])
 def test_vecchia_factor_matches_oracle(phs, nu, alpha):
     n, m = 2500, 30
     pts = np.random.default_rng(11).random((n, 2)) * 0.5

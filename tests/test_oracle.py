@@ -102,7 +102,13 @@ def test_bessel_k1_against_scipy():
         assert oracle.bessel_k1(v) == pytest.approx(scipy.special.k1(v), rel=2e-14)
 
 
-@pytest.mark.parametrize("nu", [0.5, 1.0, 1.5, 2.5])
+def test_bessel_k0_against_scipy():
+    xs = np.concatenate([np.logspace(-8, 2, 400), [1.999999, 2.0, 2.000001]])
+    for v in xs:
+        assert oracle.bessel_k0(v) == pytest.approx(scipy.special.k0(v), rel=2e-14)
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.0, 1.5, 2.0, 2.5])
 def test_matern_against_general_formula(nu):
     alpha = 3.0
     r = np.linspace(1e-3, 4.0, 200)
