@@ -288,8 +288,10 @@ static int chol_inplace(int s, double *A)
  * (Sigma^{-1} ~= U~ U~^T) holds 1/c at row i and -lambda/c at rows sigma.
  * diag[i] = 1/c, offd[i*m + q] = -lambda_q / c (0 for unused slots).
  * If a local Cholesky fails, the diagonal of K_sigma,sigma is raised by
- * jitter_base * 10^t, t = 0..4, until it succeeds.  Returns the number of
- * points that needed jitter, or -1 if one still failed. */
+ * jitter_base * 10^t, t = 0..6, until it succeeds; if it still fails (or the
+ * conditional variance is not positive) the point keeps an empty conditioning
+ * set (column 1/sqrt(K(0)) e_i).  Returns the number of points that needed
+ * jitter or the fallback. */
 int64_t or_vecchia_factor(int64_t n, const double *x, const int64_t *order, const int64_t *nbr,
                           int m, double nu, double alpha, double jitter_base,
                           double *diag, double *offd)
@@ -307,7 +309,8 @@ int64_t or_vecchia_factor(int64_t n, const double *x, const int64_t *order, cons
             int s = (int)(rank[i] < m ? rank[i] : m);
             const int64_t *sg = nbr + i * m;
             int ok = -1;
-            for (int t = 0; t <= 5 && ok != 0; ++t) {
+            const double k0 = or_matern(nu, alpha, 0.0);
+            for (int t = 0; t <= 7 && ok != 0; ++t) {
                 double jit = t == 0 ? 0.0 : jitter_base * pow(10.0, t - 1);
                 for (int a = 0; a < s; ++a)
                     for (int b = 0; b < s; ++b)
@@ -316,7 +319,12 @@ int64_t or_vecchia_factor(int64_t n, const double *x, const int64_t *order, cons
                 ok = chol_inplace(s, A);
                 if (ok == 0 && t > 0) ++njit;
             }
-            if (ok != 0) { ++fail; continue; }
+            if (ok != 0) {
+                ++njit;
+                diag[i] = 1.0 / sqrt(k0);
+                for (int q = 0; q < m; ++q) offd[i * m + q] = 0.0;
+                continue;
+            }
             for (int a = 0; a < s; ++a) kv[a] = or_matern(nu, alpha, sqrt(sqdist(x + 2 * sg[a], x + 2 * i)));
             /* forward solve L y = k */
             for (int a = 0; a < s; ++a) {
@@ -332,7 +340,12 @@ int64_t or_vecchia_factor(int64_t n, const double *x, const int64_t *order, cons
                 for (int b = a + 1; b < s; ++b) v -= A[b * s + a] * y[b];
                 y[a] = v / A[a * s + a];
             }
-            if (!(c2 > 0.0)) { ++fail; continue; }
+            if (!(c2 > 0.0)) {
+                ++njit;
+                diag[i] = 1.0 / sqrt(k0);
+                for (int q = 0; q < m; ++q) offd[i * m + q] = 0.0;
+                continue;
+            }
             double c = sqrt(c2);
             diag[i] = 1.0 / c;
             for (int q = 0; q < m; ++q) offd[i * m + q] = q < s ? -y[q] / c : 0.0;

@@ -238,7 +238,7 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
     __syncwarp();
     bool ok = false;
     int tries = 0;
-    for (int t = 0; t <= 5 && !ok; ++t) {
+    for (int t = 0; t <= 7 && !ok; ++t) {
         const double jit = t == 0 ? 0.0 : 1e-12 * pow(10.0, (double)(t - 1));
         for (int idx = lane; idx < s * s; idx += 32) {
             const int a = idx / s, b = idx - a * s;
@@ -270,8 +270,9 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
         if (!ok) ++tries;
     }
     if (!ok) {
-        if (lane == 0) atomicAdd(nfail, 1ull);
-        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = 0.0;
+        // still indefinite after the largest jitter: empty conditioning set for this point
+        if (lane == 0) atomicAdd(njit, 1ull);
+        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = q == 0 ? 1.0 : 0.0;
         return;
     }
     if (tries > 0 && lane == 0) atomicAdd(njit, 1ull);
@@ -299,8 +300,8 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
         __syncwarp();
     }
     if (!(c2 > 0.0)) {
-        if (lane == 0) atomicAdd(nfail, 1ull);
-        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = 0.0;
+        if (lane == 0 && tries == 0) atomicAdd(njit, 1ull);
+        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = q == 0 ? 1.0 : 0.0;
         return;
     }
     const double ic = 1.0 / sqrt(c2);

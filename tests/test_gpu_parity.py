@@ -93,6 +93,26 @@ def test_fmm_matvec_odd_k_distance_kernel(phs, k, geom):
     assert err <= 1e-10, err
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_eval_matches_dense_interpolant(phs, k):
+    """phs_eval alone: given w, beta, the interpolant (Eq. 1.1) at targets inside and
+    outside the root box equals the dense sum."""
+    pts = _clustered(2500, 40 + k)
+    rng = np.random.default_rng(50 + k)
+    plan = phs.Plan(_t(pts), k, vecchia_m=5, opts=phs.options(k, leaf_cap=16))
+    fr, sz = plan.frame()
+    S = sz[2]
+    w = rng.standard_normal(2500)
+    beta = rng.standard_normal(S)
+    tg = np.concatenate([rng.random((400, 2)), pts[:50] + 1e-4, [[-0.3, 0.4], [1.2, 1.1]]])
+    got = plan.eval(_t(w), _t(beta), _t(tg)).cpu().numpy()
+    c, rho = np.array(fr[:2]), fr[2]
+    xn = (pts - c) * rho
+    yn = (tg - c) * rho
+    want = oracle.interpolant(xn, w / rho ** k, beta, k, oracle.min_poly_degree(k), yn)
+    assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
+
+
 def test_fit_cubic_mix_matches_dense_solve(phs):
     """Workload cubic_mix scaled to n = 2,000 (k = 3, S = 3, Vecchia m = 20)."""
     w_ = synth.workload("cubic_mix", n=2000, n_targets=300)
