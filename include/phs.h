@@ -180,6 +180,20 @@ phs_status phs_plan_timing(phs_plan_t plan, double *ms_host, int64_t *calls_host
 /* out = M t with an exact O(n^2) all-pairs sum in FP64 (Eq. 1.3). */
 phs_status phs_dense_matvec(const double *pts_dev, int64_t n, int k, const double *t_dev,
                             double *out_dev, phs_stream_t stream);
+/* The same exact product as phs_dense_matvec without allocating device memory.  The
+ * paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code issuing work while a stream is being captured, real-time loops
+ * that must not hit the implicit device synchronisation of cudaMalloc/cudaFree, and
+ * applications that hand all device memory to their own pool.  The points are staged
+ * in a fixed device array inside the library (65,536 points, 1 MiB, kept by every GPU
+ * that loads the library until the process exits); n > 65536 returns
+ * PHS_ERR_INVALID_ARG.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress); make it before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Asynchronous on `stream`. */
+phs_status phs_dense_matvec_noalloc(const double *pts_dev, int64_t n, int k, const double *t_dev,
+                                    double *out_dev, phs_stream_t stream);
+
 /* Random enumeration (Sec. 3): order_dev[r] = index of rank r, ranks sorted by
  * (SplitMix64(seed, i), i), SplitMix64 output i = mix(seed + (i+1)*0x9E3779B97F4A7C15). */
 phs_status phs_random_order(int64_t n, uint64_t seed, int64_t *order_dev, phs_stream_t stream);
