@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libphs_b300.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "-diag-suppress", "177"]
+         "-diag-suppress", "177"] + os.environ.get("PHS_NVCC_EXTRA", "").split()
 
 
 def _sources():

@@ -54,8 +54,8 @@ __device__ __forceinline__ void had_v_cheb(int power, double x, double y, double
     } else if (power == 2) {
         v[0] = 1.0; v[1] = a; v[2] = x; v[3] = y;
     } else {
-        v[0] = 1.0; v[1] = a * a; v[2] = a; v[3] = x; v[4] = y;
-        v[5] = a * x; v[6] = a * y; v[7] = x * x; v[8] = x * y; v[9] = y * y;
+        v[0] = 1.0; v[1] = a * a; v[2] = x; v[3] = y; v[4] = a * x; v[5] = a * y;
+        v[6] = x * x; v[7] = x * y; v[8] = y * y;
     }
 }
 __device__ __forceinline__ void had_u_cheb(int power, double x, double y, double *u) {
@@ -65,8 +65,8 @@ __device__ __forceinline__ void had_u_cheb(int power, double x, double y, double
     } else if (power == 2) {
         u[0] = a; u[1] = 1.0; u[2] = -2.0 * x; u[3] = -2.0 * y;
     } else {
-        u[0] = a * a; u[1] = 1.0; u[2] = 2.0 * a; u[3] = -4.0 * a * x; u[4] = -4.0 * a * y;
-        u[5] = -4.0 * x; u[6] = -4.0 * y; u[7] = 4.0 * x * x; u[8] = 8.0 * x * y; u[9] = 4.0 * y * y;
+        u[0] = a * a; u[1] = 1.0; u[2] = -4.0 * a * x; u[3] = -4.0 * a * y; u[4] = -4.0 * x; u[5] = -4.0 * y;
+        u[6] = 4.0 * x * x + 2.0 * a; u[7] = 8.0 * x * y; u[8] = 4.0 * y * y + 2.0 * a;
     }
 }
 
@@ -95,7 +95,7 @@ __global__ void cheb_p2m(TreeView tv, const int *leaf_box, const double2 *xs, co
                 cheb_basis(fmin(1.0, fmax(-1.0, (p.x - cx) * ih)), q, Tn, S1[threadIdx.x]);
                 cheb_basis(fmin(1.0, fmax(-1.0, (p.y - cy) * ih)), q, Tn, S2[threadIdx.x]);
                 double v[10];
-                had_v_cheb(power, p.x, p.y, v);
+                had_v_cheb(power, 0.5 * (p.x - cx) * ih, 0.5 * (p.y - cy) * ih, v);  // box-local densities
                 const double tj = t[j];
                 for (int d = 0; d < nd; ++d) qd[threadIdx.x][d] = v[d] * tj;
             } else {
@@ -138,35 +138,46 @@ __device__ __forceinline__ double sep_apply(const double *Ax, const double *Ay, 
     return r;
 }
 
-// M2M for the non-leaf boxes of one level; A holds [2][q][q]: A[s][m][m'] = S(xb_m, s*1 - 1/2 + xb_m'/2)
-__global__ void cheb_m2m(TreeView tv, int b0, int nd, int q, const double *A, double *W) {
+// M2M for the non-leaf boxes of one level; A holds [2][q][q]: A[s][m][m'] = S(xb_m, s*1 - 1/2 + xb_m'/2).
+// Densities are box-local: each interpolated child density is mixed into the parent's
+// through Rv (mix slot 49 + quadrant, see fmm.cu).
+__global__ void cheb_m2m(TreeView tv, int b0, int nd, int q, const double *A, const double *mix, double *W) {
     __shared__ double in[kChebMaxQ * kChebMaxQ], tmp[kChebMaxQ * kChebMaxQ];
+    extern __shared__ double ich[];  // [nd][q*q] interpolated child densities
     const int b = b0 + blockIdx.x;
     const int nc = tv.nchild[b];
     if (nc == 0) return;
     const int qq = q * q;
     const int m = threadIdx.x, m1 = m / q, m2 = m % q;
     const bool active = m < qq;
-    for (int d = 0; d < nd; ++d) {
-        double acc = 0.0;
-        for (int c = tv.child[b]; c < tv.child[b] + nc; ++c) {
+    double acc[10];
+    for (int d = 0; d < nd; ++d) acc[d] = 0.0;
+    for (int c = tv.child[b]; c < tv.child[b] + nc; ++c) {
+        const int quad = (int)(tv.key[c] & 3);
+        const double *Ax = A + (size_t)(quad & 1) * qq, *Ay = A + (size_t)((quad >> 1) & 1) * qq;
+        for (int d = 0; d < nd; ++d) {
             for (int i = threadIdx.x; i < qq; i += blockDim.x) in[i] = W[((size_t)c * nd + d) * qq + i];
             __syncthreads();
-            const int quad = (int)(tv.key[c] & 3);
-            const double *Ax = A + (size_t)(quad & 1) * qq, *Ay = A + (size_t)((quad >> 1) & 1) * qq;
-            acc += sep_apply<false>(Ax, Ay, in, tmp, q, m1, m2, active);
+            const double r = sep_apply<false>(Ax, Ay, in, tmp, q, m1, m2, active);
+            if (active) ich[d * qq + m] = r;
         }
-        if (active) W[((size_t)b * nd + d) * qq + m] = acc;
+        const double *Rv = mix + (size_t)(49 + quad) * nd * nd;
+        if (active)
+            for (int l = 0; l < nd; ++l)
+                for (int bb = 0; bb < nd; ++bb) acc[l] += Rv[l * nd + bb] * ich[bb * qq + m];
         __syncthreads();
     }
+    if (active)
+        for (int l = 0; l < nd; ++l) W[((size_t)b * nd + l) * qq + m] = acc[l];
 }
 
-// M2L over V lists: L_t[d][m] = h * sum_v sum_n K[cls][n][m] W_src[d][n]
+// M2L over V lists: L_t[l][m] = w^{2m'} h sum_v sum_n K[cls][n][m] (S[cls] W_src)[l][n]
 __global__ void cheb_m2l(TreeView tv, int b0, const int *v_off, const int *v_src, const unsigned char *v_cls, int nd,
-                         int q, const double *K, const double *W, double *L) {
-    extern __shared__ double wsm[];  // [nd][q*q]
+                         int q, int power, const double *K, const double *mix, const double *W, double *L) {
+    extern __shared__ double wsm[];  // [nd][q*q] source weights, then [nd][q*q] mixed
     const int b = b0 + blockIdx.x;
     const int qq = q * q;
+    double *wmx = wsm + nd * qq;
     const int m = threadIdx.x;
     double acc[10];
     for (int d = 0; d < nd; ++d) acc[d] = 0.0;
@@ -174,24 +185,36 @@ __global__ void cheb_m2l(TreeView tv, int b0, const int *v_off, const int *v_src
         const int src = v_src[v];
         for (int i = threadIdx.x; i < nd * qq; i += blockDim.x) wsm[i] = W[(size_t)src * nd * qq + i];
         __syncthreads();
+        const double *S = mix + (size_t)v_cls[v] * nd * nd;
+        for (int i = threadIdx.x; i < nd * qq; i += blockDim.x) {
+            const int l = i / qq, n = i - l * qq;
+            double s = 0.0;
+            for (int bb = 0; bb < nd; ++bb) s += S[l * nd + bb] * wsm[bb * qq + n];
+            wmx[i] = s;
+        }
+        __syncthreads();
         if (m < qq) {
             const double *Kc = K + (size_t)v_cls[v] * qq * qq;
             for (int n = 0; n < qq; ++n) {
                 const double kv = Kc[(size_t)n * qq + m];
-                for (int d = 0; d < nd; ++d) acc[d] = fma(kv, wsm[d * qq + n], acc[d]);
+                for (int d = 0; d < nd; ++d) acc[d] = fma(kv, wmx[d * qq + n], acc[d]);
             }
         }
         __syncthreads();
     }
     if (m < qq) {
-        const double h = 0.5 * box_width(tv.R, tv.level[b]);
-        for (int d = 0; d < nd; ++d) L[((size_t)b * nd + d) * qq + m] = h * acc[d];
+        const double w = box_width(tv.R, tv.level[b]);
+        double sc = 0.5 * w;
+        for (int i = 0; i < power; ++i) sc *= w;
+        for (int d = 0; d < nd; ++d) L[((size_t)b * nd + d) * qq + m] = sc * acc[d];
     }
 }
 
-// L2L for one level: L_c += A' L_parent
-__global__ void cheb_l2l(TreeView tv, int b0, int nd, int q, const double *A, double *L) {
+// L2L for one level: interpolate each parent factor's potential to the child nodes,
+// then mix into the child's factors through Ru (mix slot 53 + quadrant)
+__global__ void cheb_l2l(TreeView tv, int b0, int nd, int q, const double *A, const double *mix, double *L) {
     __shared__ double in[kChebMaxQ * kChebMaxQ], tmp[kChebMaxQ * kChebMaxQ];
+    extern __shared__ double ipar[];  // [nd][q*q]
     const int b = b0 + blockIdx.x;
     const int par = tv.parent[b];
     const int qq = q * q;
@@ -203,9 +226,15 @@ __global__ void cheb_l2l(TreeView tv, int b0, int nd, int q, const double *A, do
         for (int i = threadIdx.x; i < qq; i += blockDim.x) in[i] = L[((size_t)par * nd + d) * qq + i];
         __syncthreads();
         const double r = sep_apply<true>(Ax, Ay, in, tmp, q, m1, m2, active);
-        if (active) L[((size_t)b * nd + d) * qq + m] += r;
-        __syncthreads();
+        if (active) ipar[d * qq + m] = r;
     }
+    const double *Ru = mix + (size_t)(53 + quad) * nd * nd;
+    if (active)
+        for (int a = 0; a < nd; ++a) {
+            double s = 0.0;
+            for (int l = 0; l < nd; ++l) s += Ru[l * nd + a] * ipar[l * qq + m];
+            L[((size_t)b * nd + a) * qq + m] += s;
+        }
 }
 
 // local potential of box b at point (x, y) for density d
@@ -241,7 +270,7 @@ __global__ void cheb_l2p(TreeView tv, const int *leaf_box, const double2 *xs, in
         cheb_basis(sx, q, Tn, S1);
         cheb_basis(sy, q, Tn, S2);
         double u[10];
-        had_u_cheb(power, p.x, p.y, u);
+        had_u_cheb(power, 0.5 * sx, 0.5 * sy, u);  // box-local factors
         double sum = 0.0;
         for (int d = 0; d < nd; ++d) {
             const double *Lb = lsm + d * qq;
@@ -319,7 +348,9 @@ void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_
     PHS_LAUNCH_CHECK();
     for (int l = t.depth - 1; l >= 0; --l) {
         const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-        if (nb > 0) cheb_m2m<<<nb, CHEB_T, 0, s>>>(tv, b0, nd, q, A, f.cw64.get());
+        if (nb > 0)
+            cheb_m2m<<<nb, CHEB_T, (size_t)nd * qq * sizeof(double), s>>>(tv, b0, nd, q, A, f.mix64.get(),
+                                                                          f.cw64.get());
         PHS_LAUNCH_CHECK();
     }
     if (tm) tm->end(T_UP, s);
@@ -328,16 +359,18 @@ void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_
     if (t.depth >= 2) {
         const int b0 = t.lvl_off[2], nb = t.nbox - b0;
         if (nb > 0)
-            cheb_m2l<<<nb, CHEB_T, (size_t)nd * qq * sizeof(double), s>>>(tv, b0, t.v_off.get(), t.v_src.get(),
-                                                                          t.v_cls.get(), nd, q, K, f.cw64.get(),
-                                                                          f.cl64.get());
+            cheb_m2l<<<nb, CHEB_T, 2 * (size_t)nd * qq * sizeof(double), s>>>(
+                tv, b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), nd, q, f.power, K, f.mix64.get(), f.cw64.get(),
+                f.cl64.get());
         PHS_LAUNCH_CHECK();
     }
     if (tm) tm->end(T_M2L, s);
     if (tm) tm->begin(s);
     for (int l = 3; l <= t.depth; ++l) {
         const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-        if (nb > 0) cheb_l2l<<<nb, CHEB_T, 0, s>>>(tv, b0, nd, q, A, f.cl64.get());
+        if (nb > 0)
+            cheb_l2l<<<nb, CHEB_T, (size_t)nd * qq * sizeof(double), s>>>(tv, b0, nd, q, A, f.mix64.get(),
+                                                                          f.cl64.get());
         PHS_LAUNCH_CHECK();
     }
     if (tm) tm->end(T_DOWN, s);
@@ -363,7 +396,7 @@ __global__ void cheb_eval_far(TreeView tv, const double2 *tgt, const int *box_of
     const double2 y = tgt[i];
     const double sx = fmin(1.0, fmax(-1.0, (y.x - cx) / h)), sy = fmin(1.0, fmax(-1.0, (y.y - cy) / h));
     double u[10];
-    had_u_cheb(power, y.x, y.y, u);
+    had_u_cheb(power, 0.5 * (y.x - cx) / h, 0.5 * (y.y - cy) / h, u);  // box-local factors
     const int qq = q * q;
     double acc = 0.0;
     for (int d = 0; d < nd; ++d) acc += u[d] * cheb_l2p_point(L + ((size_t)b * nd + d) * qq, q, Tn, sx, sy);

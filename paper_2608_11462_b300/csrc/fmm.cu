@@ -49,6 +49,8 @@ __device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
 }
 
 // Hadamard factors of [|x_i - x_j|^power] (Sec. 2): u_l(x_i) v_l(x_j) summed over l.
+// power 2: rank 4.  power 4: rank 9 (|x|^2 |y|^2 folds into the quadratic monomials,
+// so the separable rank is 9 rather than the 10 terms of the plain expansion).
 __device__ __forceinline__ void had_v(int power, double x, double y, double *v) {
     const double a = x * x + y * y;
     if (power == 0) {
@@ -56,8 +58,8 @@ __device__ __forceinline__ void had_v(int power, double x, double y, double *v) 
     } else if (power == 2) {
         v[0] = 1.0; v[1] = a; v[2] = x; v[3] = y;
     } else {
-        v[0] = 1.0; v[1] = a * a; v[2] = a; v[3] = x; v[4] = y;
-        v[5] = a * x; v[6] = a * y; v[7] = x * x; v[8] = x * y; v[9] = y * y;
+        v[0] = 1.0; v[1] = a * a; v[2] = x; v[3] = y; v[4] = a * x; v[5] = a * y;
+        v[6] = x * x; v[7] = x * y; v[8] = y * y;
     }
 }
 __device__ __forceinline__ void had_u(int power, double x, double y, double *u) {
@@ -67,8 +69,8 @@ __device__ __forceinline__ void had_u(int power, double x, double y, double *u) 
     } else if (power == 2) {
         u[0] = a; u[1] = 1.0; u[2] = -2.0 * x; u[3] = -2.0 * y;
     } else {
-        u[0] = a * a; u[1] = 1.0; u[2] = 2.0 * a; u[3] = -4.0 * a * x; u[4] = -4.0 * a * y;
-        u[5] = -4.0 * x; u[6] = -4.0 * y; u[7] = 4.0 * x * x; u[8] = 8.0 * x * y; u[9] = 4.0 * y * y;
+        u[0] = a * a; u[1] = 1.0; u[2] = -4.0 * a * x; u[3] = -4.0 * a * y; u[4] = -4.0 * x; u[5] = -4.0 * y;
+        u[6] = 4.0 * x * x + 2.0 * a; u[7] = 8.0 * x * y; u[8] = 4.0 * y * y + 2.0 * a;
     }
 }
 constexpr int kMaxNd = 10;
@@ -156,7 +158,7 @@ __global__ void p2m_kernel(TreeView tv, const int *leaf_box, const double2 *xs, 
                 const double2 xj = xs[j];
                 z1.x = T((xj.x - cx) * iw);
                 z1.y = T((xj.y - cy) * iw);
-                had_v(power, xj.x, xj.y, v);
+                had_v(power, (xj.x - cx) * iw, (xj.y - cy) * iw, v);  // leaf-local densities
                 const double tj = t[j];
                 for (int d = 0; d < nd; ++d) qs[threadIdx.x * nd + d] = T(v[d] * tj);
             } else {
@@ -203,13 +205,23 @@ __global__ void p2m_kernel(TreeView tv, const int *leaf_box, const double2 *xs, 
     }
 }
 
+// Box-local Hadamard factors: densities v_b and factors u_a are evaluated in the
+// coordinates of the box they belong to, (z - c)/w.  Moving between frames mixes them
+// with small level-invariant matrices (rows = new index, columns = old index):
+//   slot cls (0..48):  v_l(z + o)       = sum_b S[l][b] v_b(z)    (M2L, o = source offset)
+//   slot 49 + q:       v_l(z/2 + d_q)   = sum_b Rv[l][b] v_b(z)   (M2M, child quadrant q)
+//   slot 53 + q:       u_l(z/2 + d_q)   = sum_a Ru[l][a] u_a(z)   (L2L)
+// With these, every far-field term is O(1) in box units instead of |x|^2 / |x - y|^2.
+constexpr int kMixSlots = 57;
+
 // M2M: parents of level l (all non-leaf boxes of that level)
 template <typename T>
-__global__ void m2m_kernel(TreeView tv, int b0, int nd, int P, const typename C2T<T>::type *ops,
+__global__ void m2m_kernel(TreeView tv, int b0, int nd, int P, const typename C2T<T>::type *ops, const T *mix,
                            typename C2T<T>::type *mp) {
     using C = typename C2T<T>::type;
     extern __shared__ unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);  // [nd][P]
+    C *sm = reinterpret_cast<C *>(smem_raw);  // [nd][P] child multipole
+    C *sh = sm + nd * P;                       // [nd][P] shifted to the parent centre
     const int b = b0 + blockIdx.x;
     const int nc = tv.nchild[b];
     if (nc == 0) return;
@@ -222,13 +234,30 @@ __global__ void m2m_kernel(TreeView tv, int b0, int nd, int P, const typename C2
         __syncthreads();
         const int q = (int)(tv.key[c] & 3);
         const C *A = ops + (size_t)q * P * P;
+        const T *Rv = mix + (size_t)(49 + q) * nd * nd;
+#pragma unroll
+        for (int i = 0; i < OUT_PER_T; ++i) {
+            const int o = threadIdx.x + i * FMM_T;
+            if (o < nout) {
+                const int d = o / P, l = o - d * P;
+                C a;
+                a.x = a.y = T(0);
+                for (int k = 0; k <= l; ++k) cfma(a, A[l * P + k], sm[d * P + k]);
+                sh[o] = a;
+            }
+        }
+        __syncthreads();
 #pragma unroll
         for (int i = 0; i < OUT_PER_T; ++i) {
             const int o = threadIdx.x + i * FMM_T;
             if (o < nout) {
                 const int d = o / P, l = o - d * P;
                 C a = acc[i];
-                for (int k = 0; k <= l; ++k) cfma(a, A[l * P + k], sm[d * P + k]);
+                for (int bb = 0; bb < nd; ++bb) {
+                    const T r = Rv[d * nd + bb];
+                    a.x += r * sh[bb * P + l].x;
+                    a.y += r * sh[bb * P + l].y;
+                }
                 acc[i] = a;
             }
         }
@@ -244,20 +273,35 @@ __global__ void m2m_kernel(TreeView tv, int b0, int nd, int P, const typename C2
 // M2L over V lists for boxes [b0, b0 + gridDim.x)
 template <typename T>
 __global__ void m2l_kernel(TreeView tv, int b0, const int *v_off, const int *v_src, const unsigned char *v_cls, int nd,
-                           int P, const typename C2T<T>::type *ops, const typename C2T<T>::type *mp,
-                           typename C2T<T>::type *lc) {
+                           int P, int power, const typename C2T<T>::type *ops, const T *mix,
+                           const typename C2T<T>::type *mp, typename C2T<T>::type *lc) {
     using C = typename C2T<T>::type;
     extern __shared__ unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);  // [nd][P]
+    C *src_m = reinterpret_cast<C *>(smem_raw);  // [nd][P] source multipole (source-local densities)
+    C *sm = src_m + nd * P;                      // [nd][P] densities re-expressed about the target centre
     const int b = b0 + blockIdx.x;
     const int nout = nd * P;
-    const T logw = T(log(box_width(tv.R, tv.level[b])));
+    const double wb = box_width(tv.R, tv.level[b]);
+    const T logw = T(log(wb));
     C acc[OUT_PER_T];
 #pragma unroll
     for (int i = 0; i < OUT_PER_T; ++i) acc[i].x = acc[i].y = T(0);
     for (int v = v_off[b]; v < v_off[b + 1]; ++v) {
         const int src = v_src[v];
-        for (int i = threadIdx.x; i < nout; i += blockDim.x) sm[i] = mp[(size_t)src * nout + i];
+        for (int i = threadIdx.x; i < nout; i += blockDim.x) src_m[i] = mp[(size_t)src * nout + i];
+        __syncthreads();
+        const T *S = mix + (size_t)v_cls[v] * nd * nd;
+        for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+            const int d = o / P, k = o - d * P;
+            C a;
+            a.x = a.y = T(0);
+            for (int bb = 0; bb < nd; ++bb) {
+                const T s = S[d * nd + bb];
+                a.x += s * src_m[bb * P + k].x;
+                a.y += s * src_m[bb * P + k].y;
+            }
+            sm[o] = a;
+        }
         __syncthreads();
         const C *A = ops + (size_t)(8 + v_cls[v]) * P * P;
 #pragma unroll
@@ -275,20 +319,29 @@ __global__ void m2l_kernel(TreeView tv, int b0, const int *v_off, const int *v_s
         }
         __syncthreads();
     }
+    // |x - y|^{2m} = w^{2m} |x~ - y~|^{2m} in box units
+    T wpow = T(1);
+    for (int i = 0; i < power; ++i) wpow *= T(wb);
 #pragma unroll
     for (int i = 0; i < OUT_PER_T; ++i) {
         const int o = threadIdx.x + i * FMM_T;
-        if (o < nout) lc[(size_t)b * nout + o] = acc[i];
+        if (o < nout) {
+            C a = acc[i];
+            a.x *= wpow;
+            a.y *= wpow;
+            lc[(size_t)b * nout + o] = a;
+        }
     }
 }
 
 // L2L: boxes of one level receive their parent's local expansion
 template <typename T>
-__global__ void l2l_kernel(TreeView tv, int b0, int nd, int P, const typename C2T<T>::type *ops,
+__global__ void l2l_kernel(TreeView tv, int b0, int nd, int P, const typename C2T<T>::type *ops, const T *mix,
                            typename C2T<T>::type *lc) {
     using C = typename C2T<T>::type;
     extern __shared__ unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);
+    C *sm = reinterpret_cast<C *>(smem_raw);  // [nd][P] parent local expansions
+    C *sh = sm + nd * P;                       // [nd][P] shifted to the child centre
     const int b = b0 + blockIdx.x;
     const int par = tv.parent[b];
     const int nout = nd * P;
@@ -296,15 +349,25 @@ __global__ void l2l_kernel(TreeView tv, int b0, int nd, int P, const typename C2
     __syncthreads();
     const int q = (int)(tv.key[b] & 3);
     const C *A = ops + (size_t)(4 + q) * P * P;
-#pragma unroll
-    for (int i = 0; i < OUT_PER_T; ++i) {
-        const int o = threadIdx.x + i * FMM_T;
-        if (o < nout) {
-            const int d = o / P, m = o - d * P;
-            C a = lc[(size_t)b * nout + o];
-            for (int l = m; l < P; ++l) cfma(a, A[m * P + l], sm[d * P + l]);
-            lc[(size_t)b * nout + o] = a;
+    const T *Ru = mix + (size_t)(53 + q) * nd * nd;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int d = o / P, m = o - d * P;
+        C a;
+        a.x = a.y = T(0);
+        for (int l = m; l < P; ++l) cfma(a, A[m * P + l], sm[d * P + l]);
+        sh[o] = a;
+    }
+    __syncthreads();
+    // child factor a collects parent factor l through u_l(z/2 + d_q) = sum_a Ru[l][a] u_a(z)
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int a_ = o / P, m = o - a_ * P;
+        C a = lc[(size_t)b * nout + o];
+        for (int l = 0; l < nd; ++l) {
+            const T r = Ru[l * nd + a_];
+            a.x += r * sh[l * P + m].x;
+            a.y += r * sh[l * P + m].y;
         }
+        lc[(size_t)b * nout + o] = a;
     }
 }
 
@@ -328,7 +391,7 @@ __global__ void l2p_kernel(TreeView tv, const int *leaf_box, const double2 *xs, 
         v.x = T((xj.x - cx) * iw);
         v.y = T((xj.y - cy) * iw);
         double u[kMaxNd];
-        had_u(power, xj.x, xj.y, u);
+        had_u(power, (xj.x - cx) * iw, (xj.y - cy) * iw, u);  // leaf-local factors
         double sum = 0.0;
         for (int d = 0; d < nd; ++d) {
             const C *L = sm + d * P;
@@ -429,7 +492,7 @@ __global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, const int *leaf
             yi = T(p.y - cy);
         }
         T acc = 0;
-        for (int r = near_off[li]; r < near_off[li + 1]; ++r) {
+        for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
             const int2 rg = near_rng[r];
             for (int j0 = rg.x; j0 < rg.y; j0 += P2P_T) {
                 const int j = j0 + threadIdx.x;
@@ -504,7 +567,94 @@ template <>
 const float2 *ops_buf<float>(const Fmm &f) { return f.ops32.get(); }
 
 template <typename T>
+const T *mix_buf(const Fmm &f);
+template <>
+const double *mix_buf<double>(const Fmm &f) { return f.mix64.get(); }
+template <>
+const float *mix_buf<float>(const Fmm &f) { return f.mix32.get(); }
+
+template <typename T>
 static int P_of(const Fmm &f) { return sizeof(T) == 8 ? f.P : f.P32; }
+
+// host copies of the Hadamard factor lists (same definitions as had_u / had_v)
+static void host_had(int power, long double x, long double y, long double *u, long double *v) {
+    const long double a = x * x + y * y;
+    if (power == 0) {
+        u[0] = v[0] = 1;
+    } else if (power == 2) {
+        v[0] = 1; v[1] = a; v[2] = x; v[3] = y;
+        u[0] = a; u[1] = 1; u[2] = -2 * x; u[3] = -2 * y;
+    } else {
+        v[0] = 1; v[1] = a * a; v[2] = x; v[3] = y; v[4] = a * x; v[5] = a * y; v[6] = x * x; v[7] = x * y;
+        v[8] = y * y;
+        u[0] = a * a; u[1] = 1; u[2] = -4 * a * x; u[3] = -4 * a * y; u[4] = -4 * x; u[5] = -4 * y;
+        u[6] = 4 * x * x + 2 * a; u[7] = 8 * x * y; u[8] = 4 * y * y + 2 * a;
+    }
+}
+
+// Frame-change matrices of the factor lists (see kMixSlots): G with f_l(alpha z + beta) =
+// sum_b G[l][b] f_b(z), solved exactly (the lists span affinely closed polynomial spaces)
+// by least squares on a 7 x 7 grid in long double.
+static std::vector<long double> build_mix(int power, int nd) {
+    std::vector<long double> out((size_t)kMixSlots * nd * nd, 0.0L);
+    auto solve = [&](bool use_u, long double alpha, long double bx, long double by, long double *dst) {
+        const int N = 49;
+        std::vector<long double> F0((size_t)N * nd), F1((size_t)N * nd);
+        long double u[10], v[10];
+        for (int i = 0; i < N; ++i) {
+            const long double zx = -0.6L + 0.2L * (i % 7), zy = -0.6L + 0.2L * (i / 7);
+            host_had(power, zx, zy, u, v);
+            for (int b = 0; b < nd; ++b) F0[(size_t)i * nd + b] = use_u ? u[b] : v[b];
+            host_had(power, alpha * zx + bx, alpha * zy + by, u, v);
+            for (int b = 0; b < nd; ++b) F1[(size_t)i * nd + b] = use_u ? u[b] : v[b];
+        }
+        // normal equations (F0' F0) X = F0' F1, X[b][l] = G[l][b]
+        std::vector<long double> A((size_t)nd * nd, 0), Bm((size_t)nd * nd, 0);
+        for (int i = 0; i < N; ++i)
+            for (int r = 0; r < nd; ++r)
+                for (int c = 0; c < nd; ++c) {
+                    A[(size_t)r * nd + c] += F0[(size_t)i * nd + r] * F0[(size_t)i * nd + c];
+                    Bm[(size_t)r * nd + c] += F0[(size_t)i * nd + r] * F1[(size_t)i * nd + c];
+                }
+        for (int c = 0; c < nd; ++c) {  // Gauss-Jordan with partial pivoting
+            int piv = c;
+            for (int r = c + 1; r < nd; ++r)
+                if (std::fabs(A[(size_t)r * nd + c]) > std::fabs(A[(size_t)piv * nd + c])) piv = r;
+            for (int j = 0; j < nd; ++j) {
+                std::swap(A[(size_t)c * nd + j], A[(size_t)piv * nd + j]);
+                std::swap(Bm[(size_t)c * nd + j], Bm[(size_t)piv * nd + j]);
+            }
+            const long double d = A[(size_t)c * nd + c];
+            for (int j = 0; j < nd; ++j) {
+                A[(size_t)c * nd + j] /= d;
+                Bm[(size_t)c * nd + j] /= d;
+            }
+            for (int r = 0; r < nd; ++r) {
+                if (r == c) continue;
+                const long double fct = A[(size_t)r * nd + c];
+                if (fct == 0) continue;
+                for (int j = 0; j < nd; ++j) {
+                    A[(size_t)r * nd + j] -= fct * A[(size_t)c * nd + j];
+                    Bm[(size_t)r * nd + j] -= fct * Bm[(size_t)c * nd + j];
+                }
+            }
+        }
+        for (int l = 0; l < nd; ++l)
+            for (int b = 0; b < nd; ++b) {
+                long double g = Bm[(size_t)b * nd + l];
+                dst[(size_t)l * nd + b] = std::fabs(g) < 1e-15L ? 0.0L : g;
+            }
+    };
+    for (int dx = -3; dx <= 3; ++dx)
+        for (int dy = -3; dy <= 3; ++dy)
+            solve(false, 1.0L, (long double)dx, (long double)dy, out.data() + (size_t)((dx + 3) * 7 + (dy + 3)) * nd * nd);
+    for (int q = 0; q < 4; ++q) {
+        const long double bx = (q & 1) ? 0.25L : -0.25L, by = (q & 2) ? 0.25L : -0.25L;
+        solve(false, 0.5L, bx, by, out.data() + (size_t)(49 + q) * nd * nd);
+        solve(true, 0.5L, bx, by, out.data() + (size_t)(53 + q) * nd * nd);
+    }
+    return out;
+}
 
 template <typename T>
 static void ensure_bufs(Fmm &f, const Tree &t) {
@@ -528,7 +678,7 @@ static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_s
     PHS_LAUNCH_CHECK();
     for (int l = t.depth - 1; l >= 0; --l) {
         const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-        if (nb > 0) m2m_kernel<T><<<nb, FMM_T, esz, s>>>(tv, b0, nd, P, ops, mp);
+        if (nb > 0) m2m_kernel<T><<<nb, FMM_T, 2 * esz, s>>>(tv, b0, nd, P, ops, mix_buf<T>(f), mp);
         PHS_LAUNCH_CHECK();
     }
 }
@@ -541,8 +691,8 @@ static void m2l_pass(Fmm &f, const Tree &t, const typename C2T<T>::type *mp, typ
     if (t.depth >= 2) {
         const int b0 = t.lvl_off[2], nb = t.nbox - b0;
         if (nb > 0)
-            m2l_kernel<T><<<nb, FMM_T, esz, s>>>(tree_view(t), b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), f.nd,
-                                                 P, ops, mp, lc);
+            m2l_kernel<T><<<nb, FMM_T, 2 * esz, s>>>(tree_view(t), b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), f.nd,
+                                                 P, f.power, ops, mix_buf<T>(f), mp, lc);
         PHS_LAUNCH_CHECK();
     }
 }
@@ -553,7 +703,7 @@ static void downward(Fmm &f, const Tree &t, typename C2T<T>::type *lc, const typ
     const size_t esz = (size_t)f.nd * P * sizeof(C);
     for (int l = 3; l <= t.depth; ++l) {
         const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-        if (nb > 0) l2l_kernel<T><<<nb, FMM_T, esz, s>>>(tree_view(t), b0, f.nd, P, ops, lc);
+        if (nb > 0) l2l_kernel<T><<<nb, FMM_T, 2 * esz, s>>>(tree_view(t), b0, f.nd, P, ops, mix_buf<T>(f), lc);
         PHS_LAUNCH_CHECK();
     }
 }
@@ -682,7 +832,7 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, const Tree &t, cudaStr
     f.P32 = p32 + 1;
     f.log_core = (k % 2 == 0);
     f.power = f.log_core ? k : k - 1;
-    f.nd = f.power == 0 ? 1 : (f.power == 2 ? 4 : 10);
+    f.nd = f.power == 0 ? 1 : (f.power == 2 ? 4 : 9);
     PHS_REQUIRE(f.nd * f.P <= FMM_T * OUT_PER_T, PHS_ERR_INVALID_ARG, "fmm_order too large for this spline order");
     auto ops = build_ops(f.P);
     auto opsf = build_ops(f.P32);
@@ -699,6 +849,19 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, const Tree &t, cudaStr
     PHS_CUDA(cudaMemcpyAsync(f.ops64.get(), o64.data(), o64.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32.get(), o32.data(), o32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32p.get(), o32p.data(), o32p.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    {
+        auto mx = build_mix(f.power, f.nd);
+        std::vector<double> m64(mx.size());
+        std::vector<float> m32(mx.size());
+        for (size_t i = 0; i < mx.size(); ++i) {
+            m64[i] = (double)mx[i];
+            m32[i] = (float)mx[i];
+        }
+        f.mix64.alloc(m64.size());
+        f.mix32.alloc(m32.size());
+        PHS_CUDA(cudaMemcpyAsync(f.mix64.get(), m64.data(), m64.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        PHS_CUDA(cudaMemcpyAsync(f.mix32.get(), m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
     PHS_CUDA(cudaStreamSynchronize(s));
     upload_log_tables();
     if (!f.log_core) cheb_setup(f, cheb_q, s);
@@ -728,9 +891,10 @@ __global__ void eval_box_kernel(TreeView tv, const double2 *tgt, int64_t m, int 
     box_of[i] = find_deepest(tv, L, (int)ix, (int)iy);
 }
 
+// direct part from the precomputed near list of the target's box
 template <int K>
-__global__ void eval_near_kernel(TreeView tv, const double2 *xs, const double *w, const double2 *tgt, int64_t m,
-                                 const int *box_of, double *out) {
+__global__ void eval_near_kernel(const double2 *xs, const double *w, const double2 *tgt, int64_t m, const int *box_of,
+                                 const int *near_off, const int2 *near_rng, double *out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const int b = box_of[i];
@@ -740,13 +904,14 @@ __global__ void eval_near_kernel(TreeView tv, const double2 *xs, const double *w
     }
     const double2 y = tgt[i];
     double acc = 0.0;
-    enumerate_near(tv, b, [&](int s, int e) {
-        for (int j = s; j < e; ++j) {
+    for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
+        const int2 rg = near_rng[r];
+        for (int j = rg.x; j < rg.y; ++j) {
             const double dx = y.x - xs[j].x, dy = y.y - xs[j].y;
             const double r2 = dx * dx + dy * dy;
             if (r2 > 0) acc += phi_r2<double, K>(r2) * w[j];
         }
-    });
+    }
     out[i] = acc;
 }
 
@@ -761,7 +926,7 @@ __global__ void eval_far_log_kernel(TreeView tv, const double2 *tgt, int64_t m, 
     box_geom(tv, b, cx, cy, bw);
     double2 v = make_double2((y.x - cx) / bw, (y.y - cy) / bw);
     double u[kMaxNd];
-    had_u(power, y.x, y.y, u);
+    had_u(power, v.x, v.y, u);  // factors local to the box
     const double2 *Lb = lc + (size_t)b * nd * P;
     double acc = 0.0;
     for (int d = 0; d < nd; ++d) {
@@ -806,7 +971,8 @@ static void eval_launch(Fmm &f, const Tree &t, const PointSet &ps, const double 
     TreeView tv = tree_view(t);
     eval_box_kernel<<<blocks_for(m, 128), 128, 0, s>>>(tv, tgt, m, box_of.get());
     PHS_LAUNCH_CHECK();
-    eval_near_kernel<K><<<blocks_for(m, 128), 128, 0, s>>>(tv, ps.xs.get(), w_sorted, tgt, m, box_of.get(), out);
+    eval_near_kernel<K><<<blocks_for(m, 128), 128, 0, s>>>(ps.xs.get(), w_sorted, tgt, m, box_of.get(),
+                                                           t.near_off.get(), t.near_rng.get(), out);
     PHS_LAUNCH_CHECK();
     if (f.log_core) {
         eval_far_log_kernel<<<blocks_for(m, 128), 128, 0, s>>>(tv, tgt, m, box_of.get(), f.power, f.nd, f.P,

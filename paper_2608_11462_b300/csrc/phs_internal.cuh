@@ -98,7 +98,7 @@ struct Tree {
     DBuf<int> point_leaf;            // leaf index of each (sorted) point
     DBuf<int> v_off, v_src;          // V (M2L) lists per box (CSR)
     DBuf<unsigned char> v_cls;       // offset class (dx+3)*7 + (dy+3)
-    DBuf<int> near_off;              // near (direct) ranges per leaf (CSR)
+    DBuf<int> near_off;              // near (direct) ranges per box (CSR)
     DBuf<int2> near_rng;
     int64_t near_pairs = 0, m2l_pairs = 0;
 };
@@ -137,6 +137,8 @@ struct Fmm {
     DBuf<double2> ops64;  // M2M[4], L2L[4], M2L[49] (P x P each)
     DBuf<float2> ops32;   // same for the FP32 order P32
     DBuf<float2> ops32p, mpx32, lcx32;  // FP32 copies at the FP64 order (FP32 M2L mode)
+    DBuf<double> mix64;                 // box-local Hadamard frame changes [57][nd][nd]
+    DBuf<float> mix32;
     DBuf<int> lvl_off_dev;
     // Chebyshev (distance kernel) data
     int cheb_q = 0;                      // nodes per dimension

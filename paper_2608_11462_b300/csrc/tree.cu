@@ -183,14 +183,15 @@ __global__ void vlist_kernel(TreeView tv, int nbox, int *cnt, const int *off, in
     if (!FILL) cnt[b] = c;
 }
 
+// near lists of every box (leaves: the P2P lists; all boxes: direct parts of target
+// evaluation); the pair count covers leaves only
 template <bool FILL>
-__global__ void nearlist_kernel(TreeView tv, const int *leaf_box, int nleaf, int *cnt, const int *off, int2 *rng,
+__global__ void nearlist_kernel(TreeView tv, int nbox, int *cnt, const int *off, int2 *rng,
                                 unsigned long long *pairs) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nleaf) return;
-    const int b = leaf_box[i];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
     int c = 0;
-    int o = FILL ? off[i] : 0;
+    const int o = FILL ? off[b] : 0;
     long long np = 0;
     const int nt = tv.end[b] - tv.start[b];
     enumerate_near(tv, b, [&](int s, int e) {
@@ -198,8 +199,8 @@ __global__ void nearlist_kernel(TreeView tv, const int *leaf_box, int nleaf, int
         np += (long long)nt * (e - s);
         ++c;
     });
-    if (!FILL) cnt[i] = c;
-    else atomicAdd(pairs, (unsigned long long)np);
+    if (!FILL) cnt[b] = c;
+    else if (tv.nchild[b] == 0) atomicAdd(pairs, (unsigned long long)np);
 }
 
 __global__ void count_sum(const int *cnt, int n, unsigned long long *out) {
@@ -351,19 +352,19 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
         tree.m2l_pairs = tot;
     }
     {
-        DBuf<int> cnt(tree.nleaf);
+        DBuf<int> cnt(tree.nbox);
         DBuf<unsigned long long> pairs(1);
         PHS_CUDA(cudaMemsetAsync(pairs.get(), 0, sizeof(unsigned long long), s));
-        tree.near_off.alloc(tree.nleaf + 1);
-        nearlist_kernel<false><<<blocks_for(tree.nleaf, 128), 128, 0, s>>>(tv, tree.leaf_box.get(), tree.nleaf,
-                                                                           cnt.get(), nullptr, nullptr, nullptr);
+        tree.near_off.alloc(tree.nbox + 1);
+        nearlist_kernel<false><<<blocks_for(tree.nbox, 128), 128, 0, s>>>(tv, tree.nbox, cnt.get(), nullptr, nullptr,
+                                                                          nullptr);
         PHS_LAUNCH_CHECK();
-        int64_t tot = exclusive_scan_i32(cnt.get(), tree.near_off.get(), tree.nleaf, s);
+        int64_t tot = exclusive_scan_i32(cnt.get(), tree.near_off.get(), tree.nbox, s);
         int t32 = (int)tot;
-        PHS_CUDA(cudaMemcpyAsync(tree.near_off.get() + tree.nleaf, &t32, sizeof(int), cudaMemcpyHostToDevice, s));
+        PHS_CUDA(cudaMemcpyAsync(tree.near_off.get() + tree.nbox, &t32, sizeof(int), cudaMemcpyHostToDevice, s));
         tree.near_rng.alloc(std::max<int64_t>(tot, 1));
-        nearlist_kernel<true><<<blocks_for(tree.nleaf, 128), 128, 0, s>>>(
-            tv, tree.leaf_box.get(), tree.nleaf, nullptr, tree.near_off.get(), tree.near_rng.get(), pairs.get());
+        nearlist_kernel<true><<<blocks_for(tree.nbox, 128), 128, 0, s>>>(tv, tree.nbox, nullptr, tree.near_off.get(),
+                                                                         tree.near_rng.get(), pairs.get());
         PHS_LAUNCH_CHECK();
         unsigned long long hp2 = 0;
         PHS_CUDA(cudaMemcpyAsync(&hp2, pairs.get(), sizeof(hp2), cudaMemcpyDeviceToHost, s));
