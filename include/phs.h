@@ -75,6 +75,12 @@ typedef struct {
     double fmm_eps;         /* FMM truncation target used when fmm_order <= 0; default 1e-11 */
     double inner_tol;       /* precision 1: relative tolerance of each inner FP32 solve; default 1e-4 */
     int max_refine;         /* precision 1: maximum refinement steps; default 8 */
+    int m2l_tensor;         /* even k, FP64 far field: 1 (default) runs the multipole-to-local
+                               translations (Sec. 2.1, Eq. 2.14) on the tensor cores in exact
+                               fixed point (bf16 digit planes, about 1e-12 relative); 0 runs
+                               them in FP64 on the CUDA cores.  A bounded device wait of the
+                               tensor-core path that expires is reported as PHS_ERR_TIMEOUT by
+                               the next phs_fit or phs_eval (phs_matvec is asynchronous). */
 } phs_options;
 
 typedef struct {

@@ -557,6 +557,7 @@ void phs_options_default(phs_options *o, int k) {
     o->fmm_eps = 1e-11;
     o->inner_tol = 1e-4;
     o->max_refine = 8;
+    o->m2l_tensor = 1;
 }
 
 const char *phs_last_error(void) { return phs::last_error(); }
@@ -602,7 +603,7 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         // V-list separation (Bernstein ellipse of a unit gap), q in [6, 16]
         const double eps_q = fmm_order > 0 ? std::pow(0.55, fmm_order) : o.fmm_eps;
         const int cq = std::max(6, std::min(16, (int)std::ceil(std::log(eps_q) / std::log(1.0 / 5.83)) + 1));
-        fmm_setup(pl->fmm, k, p, std::min(p, 24), cq, pl->tree, s);
+        fmm_setup(pl->fmm, k, p, std::min(p, 24), cq, o.m2l_tensor != 0, pl->tree, s);
         // thin QR of B by two rounds of Cholesky QR (Q has orthonormal columns, R upper)
         pl->Q.alloc((size_t)S * n);
         pl->R.alloc((size_t)S * S * 3);
@@ -749,6 +750,7 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
                                                        w_dev);
     PHS_LAUNCH_CHECK();
     PHS_CUDA(cudaStreamSynchronize(s));
+    m2l_tc_check(pl->fmm, s);
     if (info) {
         info->iters = iters;
         info->outer_iters = outer;
@@ -785,6 +787,7 @@ phs_status phs_eval(phs_plan_t pl, const double *w_dev, const double *beta_dev, 
     add_poly<<<blocks_for(m, 256), 256, 0, s>>>(yn.get(), m, pl->deg, pl->S, beta_dev, out_dev);
     PHS_LAUNCH_CHECK();
     PHS_CUDA(cudaStreamSynchronize(s));
+    m2l_tc_check(pl->fmm, s);
     PHS_CATCH
 }
 

@@ -686,6 +686,12 @@ template <typename T>
 static void m2l_pass(Fmm &f, const Tree &t, const typename C2T<T>::type *mp, typename C2T<T>::type *lc,
                      const typename C2T<T>::type *ops, int P, cudaStream_t s) {
     using C = typename C2T<T>::type;
+    if constexpr (sizeof(T) == 8) {
+        if (f.tc && P == f.P) {
+            m2l_tc_pass(f, t, mp, lc, s);
+            return;
+        }
+    }
     const size_t esz = (size_t)f.nd * P * sizeof(C);
     PHS_CUDA(cudaMemsetAsync(lc, 0, (size_t)t.nbox * esz, s));
     if (t.depth >= 2) {
@@ -821,7 +827,7 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
     if (tm) tm->end(T_DOWN, s);
 }
 
-void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, const Tree &t, cudaStream_t s) {
+void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s) {
     PHS_REQUIRE(k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "k must be in 1..5");
     PHS_REQUIRE(p >= 2 && p + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "fmm_order must be in 2..60");
     PHS_REQUIRE(p32 >= 2 && p32 + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "FP32 fmm order must be in 2..60");
@@ -861,6 +867,15 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, const Tree &t, cudaStr
         f.mix32.alloc(m32.size());
         PHS_CUDA(cudaMemcpyAsync(f.mix64.get(), m64.data(), m64.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         PHS_CUDA(cudaMemcpyAsync(f.mix32.get(), m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        f.tc = false;
+        if (tensor_m2l && f.log_core && m2l_tc_supported(f.nd, f.P)) {
+            std::vector<long double> ore(ops.size()), oim(ops.size());
+            for (size_t i = 0; i < ops.size(); ++i) {
+                ore[i] = ops[i].real();
+                oim[i] = ops[i].imag();
+            }
+            m2l_tc_setup(f, ore, oim, mx, s);
+        }
     }
     PHS_CUDA(cudaStreamSynchronize(s));
     upload_log_tables();

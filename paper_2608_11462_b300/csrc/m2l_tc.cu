@@ -1,0 +1,536 @@
+// m2l_tc.cu -- multipole-to-local translations of the log-kernel FMM (Sec. 2.1,
+// Eqs. 2.13-2.15) on the 5th-generation tensor cores.
+//
+// For a target box t the M2L is a sum over its interaction (V) list, one source per
+// offset class c:
+//     b_t[d][l] = sum_c sum_k T_c[l][k] * (S_c a_src(c))[d][k]  (+ log w * sum_c (S_c a)[d][0] at l = 0)
+// with T_c the level-invariant class operator (box units) and S_c the integer frame
+// change of the box-local Hadamard densities.  Written over all classes this is one
+// dense contraction per tile of targets:  D[rows][l] = sum_(c,k') A_c[rows][k'] B_c[k'][l],
+// rows = (density d, re/im, target), k' = (coefficient k, re/im), which runs on the
+// tensor cores exactly in fixed point:
+//   * every input is an integer X (|X| <= 2^47) times a power of two: A rows share the
+//     per-target exponent E_t, B columns the per-column exponent F_l; the factor 2^floor(k/2)
+//     moves from B to A so both operands are flat in k;
+//   * X is split into six balanced base-256 digits (each in [-128, 128], exact in bf16);
+//   * digit planes i of A and j of B with i + j <= 5 are multiplied by tcgen05.mma and
+//     accumulated per diagonal g = i + j in FP32 in tensor memory.  All products are
+//     integers and every diagonal sum stays far below 2^24 for the digit statistics of
+//     this operator, so the accumulation is exact; the dropped planes i + j >= 6 weigh
+//     below 2^-48 of the operands;
+//   * the epilogue recombines sum_g D_g 256^(5-g) in integer arithmetic and scales it
+//     once per output in FP64.
+// Complex products use the real form: row (re) = [Re a_k, -Im a_k], row (im) =
+// [Im a_k, Re a_k] against column l = [Re T_lk, Im T_lk].
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <cuda_bf16.h>
+#include <vector>
+
+#include "geom.cuh"
+#include "phs_internal.cuh"
+#include "tc.cuh"
+
+namespace phs {
+
+constexpr int TC_DB = 8;                     // bits per digit
+constexpr int TC_NPL = 6;                    // digit planes per operand
+constexpr int TC_QB = TC_DB * TC_NPL - 1;    // fixed point: |X| <= 2^47
+constexpr int TC_GB = 6;                     // guard bits kept through the frame change
+constexpr int TC_M = 128;                    // rows per tile (one TMEM lane each)
+constexpr int TC_KC = 48;                    // K columns per step
+constexpr int TC_KCC = TC_KC / 2;            // complex coefficients per step
+constexpr int TC_T = 384;                    // threads per CTA
+constexpr int TC_A_PLANE = TC_M * TC_KC * 2; // bytes of one A digit plane
+constexpr int TC_NCLS = 49;
+constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
+
+bool m2l_tc_supported(int nd, int P) { return (nd == 4 || nd == 9) && P <= 64; }
+
+struct TcArgs {
+    TreeView tv;
+    int b0, nbox;
+    const int *v_off, *v_src;
+    const unsigned char *v_cls;
+    int P, npad, nch, power;
+    const double2 *mp;
+    double2 *lc;
+    const int *mexp, *gexp, *S, *F;
+    const uint16_t *bplanes;  // [49][nch][NPL][npad x 48], core-matrix order
+    int *err;
+};
+
+// round(x * 2^sh) for |x| * 2^sh < 2^62, from the bit pattern (no FP64 arithmetic);
+// the caller guarantees a right shift (sh small enough).  Zero and subnormals give 0.
+__device__ __forceinline__ long long to_fixed(double x, int sh) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    if (e == 0) return 0;
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int r = 1075 - e - sh;
+    long long v;
+    if (r >= 64) v = 0;
+    else if (r <= 0) v = (long long)(m << (-r));
+    else v = (long long)((m + (1ull << (r - 1))) >> r);
+    return (long long)bits < 0 ? -v : v;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(int lo, int hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn((float)lo, (float)hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// max over (b, k, re/im) of the exponent bound of |a_b[k]| 2^floor(k/2): one warp per box
+__global__ void tc_mexp_kernel(const double2 *mp, int nbox, int nd, int P, int *mexp) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= nbox) return;
+    const int lane = threadIdx.x & 31;
+    int m = -100000;
+    for (int i = lane; i < nd * P; i += 32) {
+        const int k = i % P;
+        const double2 v = mp[(size_t)b * nd * P + i];
+        const unsigned long long bx = (unsigned long long)__double_as_longlong(v.x);
+        const unsigned long long by = (unsigned long long)__double_as_longlong(v.y);
+        const int ex = (int)((bx >> 52) & 0x7FF), ey = (int)((by >> 52) & 0x7FF);
+        if (ex) m = max(m, ex - 1023 + 1 + (k >> 1));
+        if (ey) m = max(m, ey - 1023 + 1 + (k >> 1));
+    }
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) mexp[b] = m;
+}
+
+template <int ND>
+struct TcLayout {
+    static constexpr int TPB = TC_M / (2 * ND);  // targets per tile
+    int bplane, bstep;
+    size_t off_B, off_vsrc, off_cflag, off_clist, off_E, off_lsum, off_mbar, off_misc, total;
+    __host__ __device__ TcLayout(int npad) {
+        bplane = npad * TC_KC * 2;
+        bstep = TC_NPL * bplane;
+        off_B = (size_t)2 * TC_NPL * TC_A_PLANE;
+        off_vsrc = off_B + (size_t)2 * bstep;
+        off_cflag = off_vsrc + (size_t)TPB * TC_NCLS * 4;
+        off_clist = off_cflag + TC_NCLS * 4;
+        off_E = off_clist + TC_NCLS * 4;                 // [TPB][ND] row exponents, then [TPB] minimum
+        off_lsum = (off_E + (size_t)TPB * (ND + 1) * 4 + 7) & ~(size_t)7;
+        off_mbar = off_lsum + (size_t)TPB * ND * 8;
+        off_misc = off_mbar + 5 * 8;
+        total = off_misc + 16;
+    }
+};
+
+template <int ND>
+__global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
+    using L = TcLayout<ND>;
+    constexpr int TPB = L::TPB;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const L lay(a.npad);
+    unsigned char *Abuf = sm;
+    unsigned char *Bbuf = sm + lay.off_B;
+    int *vsrc = reinterpret_cast<int *>(sm + lay.off_vsrc);
+    int *cflag = reinterpret_cast<int *>(sm + lay.off_cflag);
+    int *clist = reinterpret_cast<int *>(sm + lay.off_clist);
+    int *Et = reinterpret_cast<int *>(sm + lay.off_E);
+    long long *lsum = reinterpret_cast<long long *>(sm + lay.off_lsum);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + lay.off_mbar);  // mma[2], bload[2], done
+    uint32_t *misc = reinterpret_cast<uint32_t *>(sm + lay.off_misc);  // tmem base, ncls, abort
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tb0 = a.b0 + blockIdx.x * TPB;
+    const int nt = min(TPB, a.nbox - tb0);
+
+    // ---- prologue: interaction lists of the tile, exponents, zeroed operand buffers
+    for (int i = tid; i < TPB * TC_NCLS; i += TC_T) vsrc[i] = -1;
+    for (int i = tid; i < TC_NCLS; i += TC_T) cflag[i] = 0;
+    for (int i = tid; i < TPB * ND; i += TC_T) lsum[i] = 0;
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(Abuf);
+        const int n16 = 2 * TC_NPL * TC_A_PLANE / 16;
+        for (int i = tid; i < n16; i += TC_T) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 5; ++i) tc::mbar_init(&mbar[i], 1);
+        tc::fence_mbar_init();
+        misc[2] = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&misc[0], 512);
+        tc::tmem_relinquish();
+    }
+    __syncthreads();
+    // row exponents: |(S_c a)_d[k] 2^floor(k/2)| < 2^(E[t][d] - 1) over the interaction list
+    for (int ti = tid; ti < nt; ti += TC_T) {
+        const int b = tb0 + ti;
+        int e[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) e[d] = -100000;
+        for (int v = a.v_off[b]; v < a.v_off[b + 1]; ++v) {
+            const int c = a.v_cls[v], src = a.v_src[v];
+            vsrc[ti * TC_NCLS + c] = src;
+            const int me = a.mexp[src];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) e[d] = max(e[d], me + a.gexp[c * ND + d]);
+            cflag[c] = 1;
+        }
+        int emin = 1 << 30;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            Et[ti * ND + d] = e[d] + 1;
+            emin = min(emin, e[d] + 1);
+        }
+        Et[TPB * ND + ti] = emin;
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+        int n = 0;
+        for (int c = 0; c < TC_NCLS; ++c)
+            if (cflag[c]) clist[n++] = c;
+        misc[1] = (uint32_t)n;
+    }
+    __syncthreads();
+    const uint32_t tmem = misc[0];
+    const int nsteps = (int)misc[1] * a.nch;
+    const uint32_t idesc = tc::idesc_bf16_f32(TC_M, a.npad);
+    const uint32_t a_base = tc::smem_u32(Abuf), b_base = tc::smem_u32(Bbuf);
+    uint32_t inited = 0;               // accumulators written at least once (thread 0)
+    int bpend[2] = {-1, -1};           // parity of an operator copy not yet waited for (thread 0)
+
+    // ---- main loop: one step = (class, K chunk)
+    for (int s = 0; s < nsteps; ++s) {
+        const int u = s & 1;
+        const int c = clist[s / a.nch], h = s % a.nch;
+        if (s >= 2 && !tc::mbar_wait(&mbar[u], (uint32_t)(((s >> 1) - 1) & 1), TC_TIMEOUT_NS)) misc[2] = 1;
+        if (tid == 0 && !misc[2]) {
+            bpend[u] = (s >> 1) & 1;
+            tc::mbar_arrive_expect_tx(&mbar[2 + u], (uint32_t)lay.bstep);
+            tc::bulk_g2s(Bbuf + (size_t)u * lay.bstep,
+                         reinterpret_cast<const unsigned char *>(a.bplanes) + ((size_t)c * a.nch + h) * lay.bstep,
+                         (uint32_t)lay.bstep, &mbar[2 + u]);
+        }
+        // stage A: item = (coefficient kk, target ti); rows (2d + part) * TPB + ti
+        unsigned char *Au = Abuf + (size_t)u * TC_NPL * TC_A_PLANE;
+        const int *Sc = a.S + c * ND * ND;
+        for (int it = tid; it < TPB * TC_KCC; it += TC_T) {
+            const int ti = it % TPB, kk = it / TPB;
+            const int k = h * TC_KCC + kk;
+            const int src = (ti < nt && k < a.P) ? vsrc[ti * TC_NCLS + c] : -1;
+            const uint32_t colb = (uint32_t)((kk >> 2) * 128 + (kk & 3) * 4);  // byte offset of column 2kk in a row
+            if (src < 0) {
+                for (int g2 = 0; g2 < 2 * ND; ++g2) {
+                    const int row = g2 * TPB + ti;
+                    const uint32_t off = (uint32_t)((row >> 3) * (TC_KC / 8) * 128 + (row & 7) * 16) + colb;
+#pragma unroll
+                    for (int i = 0; i < TC_NPL; ++i) *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off) = 0u;
+                }
+                continue;
+            }
+            // sources convert once at the finest row scale of the target; each row then
+            // shifts down to its own exponent (|y| < 2^62 before the shift)
+            const int emin = Et[TPB * ND + ti];
+            const int sh = TC_QB + TC_GB - emin + (k >> 1);
+            long long xr[ND], xi[ND];
+#pragma unroll
+            for (int b = 0; b < ND; ++b) {
+                const double2 m = a.mp[((size_t)src * ND + b) * a.P + k];
+                xr[b] = to_fixed(m.x, sh);
+                xi[b] = to_fixed(m.y, sh);
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                long long yr = 0, yi = 0;
+#pragma unroll
+                for (int b = 0; b < ND; ++b) {
+                    const int sv = Sc[d * ND + b];
+                    if (sv) {
+                        yr += (long long)sv * xr[b];
+                        yi += (long long)sv * xi[b];
+                    }
+                }
+                const int dsh = Et[ti * ND + d] - emin;
+                if (dsh > 0) {
+                    yr = (yr + (1ll << (dsh - 1))) >> dsh;
+                    yi = (yi + (1ll << (dsh - 1))) >> dsh;
+                }
+                if (k == 0) lsum[ti * ND + d] += yr;
+                yr = (yr + (1ll << (TC_GB - 1))) >> TC_GB;
+                yi = (yi + (1ll << (TC_GB - 1))) >> TC_GB;
+                int dr[TC_NPL], di[TC_NPL];
+#pragma unroll
+                for (int i = TC_NPL - 1; i >= 1; --i) {
+                    const int qr = (int)((yr + 128) & 255) - 128, qi = (int)((yi + 128) & 255) - 128;
+                    dr[i] = qr;
+                    di[i] = qi;
+                    yr = (yr - qr) >> TC_DB;
+                    yi = (yi - qi) >> TC_DB;
+                }
+                dr[0] = (int)yr;
+                di[0] = (int)yi;
+                const int row_re = (2 * d) * TPB + ti, row_im = row_re + TPB;
+                const uint32_t off_re = (uint32_t)((row_re >> 3) * (TC_KC / 8) * 128 + (row_re & 7) * 16) + colb;
+                const uint32_t off_im = (uint32_t)((row_im >> 3) * (TC_KC / 8) * 128 + (row_im & 7) * 16) + colb;
+#pragma unroll
+                for (int i = 0; i < TC_NPL; ++i) {
+                    *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off_re) = pack_bf16(dr[i], -di[i]);
+                    *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off_im) = pack_bf16(di[i], dr[i]);
+                }
+            }
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (misc[2]) break;
+        if (tid == 0) {
+            if (!tc::mbar_wait(&mbar[2 + u], (uint32_t)((s >> 1) & 1), TC_TIMEOUT_NS)) {
+                misc[2] = 1;
+            } else {
+                bpend[u] = -1;
+                tc::fence_after_sync();
+                const uint32_t au = a_base + (uint32_t)(u * TC_NPL * TC_A_PLANE);
+                const uint32_t bu = b_base + (uint32_t)(u * lay.bstep);
+#pragma unroll 1
+                for (int ks = 0; ks < TC_KC / 16; ++ks) {
+#pragma unroll
+                    for (int i = 0; i < TC_NPL; ++i) {
+                        const uint64_t ad = tc::make_desc_kmajor(au + i * TC_A_PLANE + ks * 256, 128, (TC_KC / 8) * 128);
+#pragma unroll
+                        for (int j = 0; j < TC_NPL - i; ++j) {
+                            const int g = i + j;
+                            const uint64_t bd =
+                                tc::make_desc_kmajor(bu + j * lay.bplane + ks * 256, 128, (TC_KC / 8) * 128);
+                            tc::mma_bf16(tmem + (uint32_t)(g * a.npad), ad, bd, idesc, (inited >> g) & 1);
+                            inited |= 1u << g;
+                        }
+                    }
+                }
+                tc::mma_commit(&mbar[u]);
+            }
+        }
+    }
+    __syncthreads();
+    const bool aborted = misc[2] != 0;
+    bool ok = !aborted;
+    if (nsteps > 0) {
+        if (tid == 0) tc::mma_commit(&mbar[4]);
+        ok = tc::mbar_wait(&mbar[4], 0, TC_TIMEOUT_NS) && ok;
+    }
+    if (tid == 0) {  // operator copies still in flight after an abort land before the CTA exits
+        for (int u = 0; u < 2; ++u)
+            if (bpend[u] >= 0 && !tc::mbar_wait(&mbar[2 + u], (uint32_t)bpend[u], TC_TIMEOUT_NS)) ok = false;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && lane == 0) atomicExch(a.err, 1);
+    tc::fence_after_sync();
+
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, 16-column chunks w / 4, +3, ...
+    if (ok) {
+        const int q = warp & 3, cg = warp >> 2;
+        const int r = 32 * q + lane;
+        const int grp = r / TPB, ti = r - grp * TPB;
+        const bool valid = grp < 2 * ND && ti < nt;
+        const int d = grp >> 1, part = grp & 1;
+        int E = 0;
+        double logw = 0, wpow = 1, l0 = 0;
+        double2 *dst = nullptr;
+        if (valid) {
+            const int b = tb0 + ti;
+            const double w = box_width(a.tv.R, a.tv.level[b]);
+            logw = log(w);
+            for (int i = 0; i < a.power; ++i) wpow *= w;
+            E = Et[ti * ND + d];
+            l0 = ldexp((double)lsum[ti * ND + d], E - TC_QB - TC_GB);
+            dst = a.lc + ((size_t)b * ND + d) * a.P;
+        }
+        for (int chk = cg; chk < a.npad / 16; chk += 3) {
+            uint32_t v[TC_NPL][16];
+            if (nsteps > 0) {
+#pragma unroll
+                for (int g = 0; g < TC_NPL; ++g)
+                    tc::tmem_ld16_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * a.npad + chk * 16), v[g]);
+                tc::tmem_wait_ld();
+            }
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int l = chk * 16 + j;
+                    if (l < a.P) {
+                        double val = 0;
+                        if (nsteps > 0) {
+                            long long dg[TC_NPL];
+#pragma unroll
+                            for (int g = 0; g < TC_NPL; ++g)
+                                dg[g] = (long long)__float2int_rn(__uint_as_float(v[g][j]));
+                            const long long hi = (dg[0] << 16) + (dg[1] << 8) + dg[2];
+                            const long long lo = (dg[3] << 16) + (dg[4] << 8) + dg[5];
+                            val = ldexp(fma((double)hi, 16777216.0, (double)lo),
+                                        E + a.F[l] - (2 * TC_QB - TC_DB * (TC_NPL - 1)));
+                            if (l == 0 && part == 0) val += logw * l0;
+                        }
+                        val *= wpow;
+                        if (part == 0) dst[l].x = val;
+                        else dst[l].y = val;
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------- host side
+static inline uint16_t bf16_bits_of_int(int v) {
+    const float f = (float)v;  // |v| <= 128: exact in bf16
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+}
+
+void m2l_tc_setup(Fmm &f, const std::vector<long double> &ops_re, const std::vector<long double> &ops_im,
+                  const std::vector<long double> &mix, cudaStream_t s) {
+    const int P = f.P, nd = f.nd;
+    PHS_REQUIRE(m2l_tc_supported(nd, P), PHS_ERR_INVALID_ARG, "tensor-core M2L needs nd in {4, 9} and P <= 64");
+    f.tc_npad = (P + 15) / 16 * 16;
+    f.tc_nch = (2 * P + TC_KC - 1) / TC_KC;
+    const int npad = f.tc_npad, nch = f.tc_nch;
+    auto opv = [&](const std::vector<long double> &o, int c, int l, int k) -> long double {
+        return o[((size_t)(8 + c) * P + l) * P + k];
+    };
+    auto valid_cls = [](int c) {
+        const int dx = c / 7 - 3, dy = c % 7 - 3;
+        return std::abs(dx) > 1 || std::abs(dy) > 1;
+    };
+    // column exponents: |T_c[l][k] 2^-floor(k/2)| < 2^F_l over all classes
+    std::vector<int> F(P, -100000);
+    for (int c = 0; c < TC_NCLS; ++c) {
+        if (!valid_cls(c)) continue;
+        for (int l = 0; l < P; ++l)
+            for (int k = 0; k < P; ++k)
+                for (int part = 0; part < 2; ++part) {
+                    const long double v = (part ? opv(ops_im, c, l, k) : opv(ops_re, c, l, k)) / std::ldexp(1.0L, k >> 1);
+                    if (v == 0) continue;
+                    int e;
+                    std::frexp(v, &e);
+                    F[l] = std::max(F[l], e);
+                }
+    }
+    const size_t plane = (size_t)npad * TC_KC;
+    std::vector<uint16_t> B((size_t)TC_NCLS * nch * TC_NPL * plane, 0);
+    for (int c = 0; c < TC_NCLS; ++c) {
+        if (!valid_cls(c)) continue;
+        for (int h = 0; h < nch; ++h)
+            for (int l = 0; l < P; ++l)
+                for (int kc = 0; kc < TC_KC; ++kc) {
+                    const int kp = h * TC_KC + kc, k = kp >> 1, part = kp & 1;
+                    if (k >= P) continue;
+                    const long double v = (part ? opv(ops_im, c, l, k) : opv(ops_re, c, l, k)) / std::ldexp(1.0L, k >> 1);
+                    long long X = std::llround(std::ldexp(v, TC_QB - F[l]));
+                    int dig[TC_NPL];
+                    for (int i = TC_NPL - 1; i >= 1; --i) {
+                        const int q = (int)((X + 128) & 255) - 128;
+                        dig[i] = q;
+                        X = (X - q) >> TC_DB;
+                    }
+                    dig[0] = (int)X;
+                    PHS_REQUIRE(std::abs(dig[0]) <= 128, PHS_ERR_INVALID_ARG, "tensor-core M2L: operator digit overflow");
+                    const size_t boff = (size_t)l / 8 * (TC_KC / 8) * 64 + (size_t)kc / 8 * 64 + (l % 8) * 8 + kc % 8;
+                    for (int j = 0; j < TC_NPL; ++j)
+                        B[(((size_t)c * nch + h) * TC_NPL + j) * plane + boff] = bf16_bits_of_int(dig[j]);
+                }
+    }
+    // integer frame changes (slots 0..48 of the mix table) and their growth bound
+    // (the rows of a target convert at the finest row scale, so the largest growth may
+    // add at most 10 bits to the 52-bit converted sources: |y| < 2^62)
+    std::vector<int> S((size_t)TC_NCLS * nd * nd, 0), gexp((size_t)TC_NCLS * nd, 0);
+    for (int c = 0; c < TC_NCLS; ++c) {
+        for (int d = 0; d < nd; ++d) {
+            long long rs = 0;
+            for (int b = 0; b < nd; ++b) {
+                const long double v = mix[((size_t)c * nd + d) * nd + b];
+                const long long iv = std::llround(v);
+                PHS_REQUIRE(std::fabs(v - (long double)iv) < 1e-6L, PHS_ERR_INVALID_ARG,
+                            "tensor-core M2L: frame change is not integral");
+                S[((size_t)c * nd + d) * nd + b] = (int)iv;
+                rs += std::llabs(iv);
+            }
+            int g = 0;
+            while ((1ll << g) < std::max(rs, 1ll)) ++g;
+            PHS_REQUIRE(g <= 10, PHS_ERR_INVALID_ARG, "tensor-core M2L: frame-change growth above 2^10");
+            gexp[(size_t)c * nd + d] = g;
+        }
+    }
+    f.tc_b.alloc(B.size());
+    f.tc_F.alloc(P);
+    f.tc_S.alloc(S.size());
+    f.tc_gexp.alloc(gexp.size());
+    f.tc_err.alloc(1);
+    PHS_CUDA(cudaMemcpyAsync(f.tc_b.get(), B.data(), B.size() * 2, cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.tc_F.get(), F.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.tc_S.get(), S.data(), S.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.tc_gexp.get(), gexp.data(), gexp.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemsetAsync(f.tc_err.get(), 0, sizeof(int), s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    f.tc = true;
+}
+
+template <int ND>
+static void launch_tc(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, int b0, cudaStream_t s) {
+    const TcLayout<ND> lay(f.tc_npad);
+    static bool attr_set = false;
+    if (!attr_set) {
+        PHS_CUDA(cudaFuncSetAttribute(m2l_tc_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+        attr_set = true;
+    }
+    PHS_REQUIRE(lay.total <= 232448, PHS_ERR_INVALID_ARG, "tensor-core M2L: shared memory layout too large");
+    TcArgs a;
+    a.tv = tree_view(t);
+    a.b0 = b0;
+    a.nbox = t.nbox;
+    a.v_off = t.v_off.get();
+    a.v_src = t.v_src.get();
+    a.v_cls = t.v_cls.get();
+    a.P = f.P;
+    a.npad = f.tc_npad;
+    a.nch = f.tc_nch;
+    a.power = f.power;
+    a.mp = mp;
+    a.lc = lc;
+    a.mexp = f.tc_mexp.get();
+    a.gexp = f.tc_gexp.get();
+    a.S = f.tc_S.get();
+    a.F = f.tc_F.get();
+    a.bplanes = f.tc_b.get();
+    a.err = f.tc_err.get();
+    const int nb = t.nbox - b0;
+    const unsigned grid = (unsigned)((nb + TcLayout<ND>::TPB - 1) / TcLayout<ND>::TPB);
+    m2l_tc_kernel<ND><<<grid, TC_T, lay.total, s>>>(a);
+    PHS_LAUNCH_CHECK();
+}
+
+void m2l_tc_pass(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, cudaStream_t s) {
+    const int b0 = t.depth >= 2 ? t.lvl_off[2] : t.nbox;
+    const size_t esz = (size_t)f.nd * f.P * sizeof(double2);
+    if (b0 > 0) PHS_CUDA(cudaMemsetAsync(lc, 0, (size_t)b0 * esz, s));
+    if (b0 >= t.nbox) return;
+    if (f.tc_mexp.n < (size_t)t.nbox) f.tc_mexp.alloc(t.nbox);
+    tc_mexp_kernel<<<blocks_for(t.nbox, 8), 256, 0, s>>>(mp, t.nbox, f.nd, f.P, f.tc_mexp.get());
+    PHS_LAUNCH_CHECK();
+    if (f.nd == 4) launch_tc<4>(f, t, mp, lc, b0, s);
+    else launch_tc<9>(f, t, mp, lc, b0, s);
+}
+
+void m2l_tc_check(Fmm &f, cudaStream_t s) {
+    if (!f.tc || !f.tc_err.get()) return;
+    int h = 0;
+    PHS_CUDA(cudaMemcpyAsync(&h, f.tc_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        PHS_CUDA(cudaMemsetAsync(f.tc_err.get(), 0, sizeof(int), s));
+        throw Error{PHS_ERR_TIMEOUT, "tensor-core M2L: a bounded wait expired"};
+    }
+}
+
+}  // namespace phs

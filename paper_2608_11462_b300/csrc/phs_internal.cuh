@@ -146,8 +146,27 @@ struct Fmm {
     DBuf<float> cheb32;
     DBuf<double> cw64, cl64;             // weights/potentials at nodes [box][nd][q*q]
     DBuf<float> cw32, cl32;
+    // tensor-core M2L of the log kernel (m2l_tc.cu)
+    bool tc = false;                     // use it for the FP64 far field
+    int tc_npad = 0, tc_nch = 0;         // output columns (P rounded up to 16), K chunks
+    DBuf<uint16_t> tc_b;                 // operator digit planes (bf16 bits)
+    DBuf<int> tc_F;                      // column exponents [P]
+    DBuf<int> tc_S;                      // integer frame changes [49][nd][nd]
+    DBuf<int> tc_gexp;                   // log2 bound of the frame-change row growth [49][nd]
+    DBuf<int> tc_mexp;                   // per-box exponent bound of the multipoles
+    DBuf<int> tc_err;                    // device status (nonzero: a bounded wait expired)
 };
-void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, const Tree &t, cudaStream_t s);
+// tensor_m2l: run the FP64 M2L of the log kernel on the tensor cores (m2l_tc.cu)
+void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s);
+// tensor-core M2L (m2l_tc.cu): setup from the class operators (slots 8 + cls of the
+// level-invariant operator table, [57][P][P] complex) and the frame changes ([57][nd][nd]);
+// the pass writes lc for every box (zero where the interaction list is empty)
+bool m2l_tc_supported(int nd, int P);
+void m2l_tc_setup(Fmm &f, const std::vector<long double> &ops_re, const std::vector<long double> &ops_im,
+                  const std::vector<long double> &mix, cudaStream_t s);
+void m2l_tc_pass(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, cudaStream_t s);
+// throws PHS_ERR_TIMEOUT if a tensor-core wait expired since the last check (synchronises s)
+void m2l_tc_check(Fmm &f, cudaStream_t s);
 // distance-kernel far field (cheb.cu)
 void cheb_setup(Fmm &f, int q, cudaStream_t s);
 void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, cudaStream_t s,

@@ -53,16 +53,38 @@ def test_dense_matvec_matches_oracle(phs, k):
 @pytest.mark.parametrize("k", [2, 4])
 @pytest.mark.parametrize("geom", ["uniform", "clustered"])
 @pytest.mark.parametrize("leaf_cap", [8, 64])
-def test_fmm_matvec_fp64(phs, k, geom, leaf_cap):
+@pytest.mark.parametrize("m2l_tensor", [0, 1])
+def test_fmm_matvec_fp64(phs, k, geom, leaf_cap, m2l_tensor):
+    """FP64 FMM (M2L on the FP64 CUDA cores or on the tensor cores) against the
+    oracle's dense product."""
     n = 3001
     pts = np.random.default_rng(1).random((n, 2)) if geom == "uniform" else _clustered(n, 2)
     t = np.random.default_rng(3).standard_normal(n)
-    plan = phs.Plan(_t(pts), k, fmm_order=0, vecchia_m=8, opts=phs.options(k, leaf_cap=leaf_cap))
+    plan = phs.Plan(_t(pts), k, fmm_order=0, vecchia_m=8,
+                    opts=phs.options(k, leaf_cap=leaf_cap, m2l_tensor=m2l_tensor))
     got = plan.matvec(_t(t), precision=0).cpu().numpy()
     want = oracle.dense_matvec(pts, k, t)
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err <= 1e-10, err
     assert plan.frame()[1][7] >= (2 if leaf_cap == 8 else 1)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+@pytest.mark.parametrize("fmm_order", [12, 30, 43, 60])
+def test_m2l_tensor_matches_fp64_m2l(phs, k, fmm_order):
+    """The tensor-core M2L (exact fixed point on bf16 digit planes) against the FP64
+    M2L on the same tree: one to three K chunks, 16 to 64 output columns, many
+    16-box tiles with a ragged last one."""
+    n = 5000
+    pts = _clustered(n, 7)
+    t = np.random.default_rng(8).standard_normal(n)
+    out = []
+    for tc in (0, 1):
+        plan = phs.Plan(_t(pts), k, fmm_order=fmm_order, vecchia_m=4,
+                        opts=phs.options(k, leaf_cap=16, m2l_tensor=tc))
+        out.append(plan.matvec(_t(t), precision=0).cpu().numpy())
+    err = np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0])
+    assert err <= 1e-11, err
 
 
 @pytest.mark.parametrize("k", [2, 4])
