@@ -147,87 +147,108 @@ __global__ void knn_kernel(const double2 *x_by_rank, int64_t n, int m, int brute
 }
 
 // ---------------------------------------------------------------- Matern covariance, K(0) = 1
-// K_1 by the ascending series (DLMF 10.31.1) for x <= 2 and the trapezoidal rule on
-// K_1(x) = int_0^inf exp(-x cosh t) cosh t dt (DLMF 10.32.9) for x > 2.
-__device__ double bessel_k1(double x) {
-    if (x <= 2.0) {
-        const double eg = 0.57721566490153286061;
-        const double q = 0.25 * x * x;
-        double term = 1.0, hk = 0.0, si = 0.0, sp = 0.0;
-        for (int k = 0; k < 40; ++k) {
-            if (k > 0) {
-                term *= q / ((double)k * (double)(k + 1));
-                hk += 1.0 / k;
-            }
-            const double p1 = -eg + hk, p2 = p1 + 1.0 / (k + 1);
-            si += term;
-            sp += (p1 + p2) * term;
-            if (term < 1e-20 * si) break;
+// In terms of q = (alpha r)^2 / 4 the ascending series of K_0 and K_1 (DLMF 10.31.1-2)
+// need neither a square root nor a division:
+//   a K_1(a) = 1 + q (log(q) S_1(q) - P_1(q)),   K_0(a) = -(log(q)/2 + gamma) S_0(q) + H_0(q),
+//   S_1 = sum q^k / (k!(k+1)!),  P_1 = sum (psi(k+1) + psi(k+2)) q^k / (k!(k+1)!),
+//   S_0 = sum q^k / (k!)^2,      H_0 = sum H_k q^k / (k!)^2.
+// The coefficients are tabulated (host, long double) and the sums run in Horner form
+// with as many terms as q needs (relative truncation below 1e-16 for q <= 1, a <= 2).
+// For a > 2 the trapezoidal rule with step 1/4 on K_nu(a) = int_0^inf exp(-a cosh t)
+// cosh(nu t) dt (DLMF 10.32.9) uses tabulated cosh(j/4).
+constexpr int kSerTerms = 14;
+constexpr int kCoshTab = 64;
+__constant__ double c_s1[kSerTerms], c_p1[kSerTerms], c_s0[kSerTerms], c_h0[kSerTerms], c_cosh[kCoshTab];
+
+__device__ __forceinline__ int ser_terms(double q) { return q <= 0.015625 ? 6 : (q <= 0.125 ? 9 : kSerTerms); }
+
+__device__ __forceinline__ double horner(const double *c, int nt, double q) {
+    double v = c[nt - 1];
+    for (int k = nt - 2; k >= 0; --k) v = fma(v, q, c[k]);
+    return v;
+}
+
+// (K_0(a), a K_1(a)) by quadrature for a > 2
+__device__ __forceinline__ void bessel_quad(double a, double &k0, double &ak1) {
+    double s0 = 0.5 * exp(-a), s1 = s0;
+    for (int j = 1; j < kCoshTab; ++j) {
+        const double ch = c_cosh[j];
+        const double e = exp(-a * ch);
+        s0 += e;
+        s1 += e * ch;
+        if (e * ch < 1e-19 * s0) break;
+    }
+    k0 = 0.25 * s0;
+    ak1 = a * 0.25 * s1;
+}
+
+// Matern with K(0) = 1 as a function of q = (alpha r)^2 / 4 (q > 0)
+__device__ __forceinline__ double matern_q(double nu, double q) {
+    if (nu == 0.5 || nu == 1.5 || nu == 2.5) {
+        const double a = 2.0 * sqrt(q), e = exp(-a);
+        if (nu == 0.5) return e;
+        if (nu == 1.5) return (1.0 + a) * e;
+        return (1.0 + a + a * a / 3.0) * e;
+    }
+    double k0, ak1;
+    if (q <= 1.0) {
+        const int nt = ser_terms(q);
+        const double lq = log(q);
+        ak1 = 1.0 + q * (lq * horner(c_s1, nt, q) - horner(c_p1, nt, q));
+        if (nu == 1.0) return ak1;
+        k0 = -(0.5 * lq + 0.57721566490153286061) * horner(c_s0, nt, q) + horner(c_h0, nt, q);
+    } else {
+        bessel_quad(2.0 * sqrt(q), k0, ak1);
+        if (nu == 1.0) return ak1;
+    }
+    return 2.0 * q * k0 + ak1;  // nu = 2: a^2 K_2(a) / 2 = a^2 K_0(a) / 2 + a K_1(a)
+}
+
+static void upload_bessel_tables() {
+    long double s1[kSerTerms], p1[kSerTerms], s0[kSerTerms], h0[kSerTerms];
+    const long double eg = 0.57721566490153286060651209008240243L;
+    long double fk = 1, fk1 = 1, H = 0;  // k!, (k+1)!, H_k
+    for (int k = 0; k < kSerTerms; ++k) {
+        if (k > 0) {
+            fk *= k;
+            H += 1.0L / k;
         }
-        return 1.0 / x + log(0.5 * x) * (0.5 * x * si) - 0.25 * x * sp;
+        fk1 = fk * (k + 1);
+        s1[k] = 1.0L / (fk * fk1);
+        p1[k] = (-2 * eg + 2 * H + 1.0L / (k + 1)) * s1[k];
+        s0[k] = 1.0L / (fk * fk);
+        h0[k] = H * s0[k];
     }
-    const double h = 0.25;
-    double s = 0.5 * exp(-x);
-    for (int j = 1; j < 200; ++j) {
-        const double t = j * h, ch = cosh(t);
-        const double f = exp(-x * ch) * ch;
-        s += f;
-        if (f < 1e-19 * s) break;
+    double d[4][kSerTerms], ch[kCoshTab];
+    for (int k = 0; k < kSerTerms; ++k) {
+        d[0][k] = (double)s1[k];
+        d[1][k] = (double)p1[k];
+        d[2][k] = (double)s0[k];
+        d[3][k] = (double)h0[k];
     }
-    return h * s;
+    for (int j = 0; j < kCoshTab; ++j) ch[j] = (double)std::cosh(0.25L * j);
+    PHS_CUDA(cudaMemcpyToSymbol(c_s1, d[0], sizeof(d[0])));
+    PHS_CUDA(cudaMemcpyToSymbol(c_p1, d[1], sizeof(d[1])));
+    PHS_CUDA(cudaMemcpyToSymbol(c_s0, d[2], sizeof(d[2])));
+    PHS_CUDA(cudaMemcpyToSymbol(c_h0, d[3], sizeof(d[3])));
+    PHS_CUDA(cudaMemcpyToSymbol(c_cosh, ch, sizeof(ch)));
 }
 
-// K_0 by the ascending series (DLMF 10.31.2) for x <= 2 and the trapezoidal rule on
-// K_0(x) = int_0^inf exp(-x cosh t) dt (DLMF 10.32.9) for x > 2.
-__device__ double bessel_k0(double x) {
-    if (x <= 2.0) {
-        const double eg = 0.57721566490153286061;
-        const double q = 0.25 * x * x;
-        double term = 1.0, hk = 0.0, si = 1.0, sh = 0.0;
-        for (int k = 1; k < 40; ++k) {
-            term *= q / ((double)k * (double)k);
-            hk += 1.0 / k;
-            si += term;
-            sh += hk * term;
-            if (term < 1e-20 * si) break;
-        }
-        return -(log(0.5 * x) + eg) * si + sh;
-    }
-    const double h = 0.25;
-    double s = 0.5 * exp(-x);
-    for (int j = 1; j < 200; ++j) {
-        const double f = exp(-x * cosh(j * h));
-        s += f;
-        if (f < 1e-19 * s) break;
-    }
-    return h * s;
-}
-
-// Matern with K(0) = 1: nu in {0.5, 1.5, 2.5} closed forms; nu = 1: a K_1(a);
-// nu = 2: a^2 K_2(a) / 2 = a^2 K_0(a) / 2 + a K_1(a)  (K_2 = K_0 + (2/a) K_1)
-__device__ __forceinline__ double matern(double nu, double alpha, double r) {
-    const double a = alpha * r;
-    if (a == 0.0) return 1.0;
-    if (nu == 0.5) return exp(-a);
-    if (nu == 1.5) return (1.0 + a) * exp(-a);
-    if (nu == 2.5) return (1.0 + a + a * a / 3.0) * exp(-a);
-    if (nu == 2.0) return 0.5 * a * a * bessel_k0(a) + a * bessel_k1(a);
-    return a * bessel_k1(a);  // nu == 1
-}
-
-// warp per point: local Cholesky of K(X_sigma, X_sigma), lambda, c (Eq. 2.19)
-__global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, double nu,
-                              double alpha, double *val_ell, unsigned long long *njit, unsigned long long *nfail) {
+// Warp per point: local Cholesky of K(X_sigma, X_sigma), lambda and c (Eq. 2.19).
+// The lower triangle (row stride ld, odd) lives in shared memory; lane a owns row a
+// of the right-looking updates and entries a, a + 32 of the triangular solves.
+__global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, int ld,
+                              double nu, double alpha, double *val_ell, unsigned long long *njit) {
     extern __shared__ double fsm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int per = m * m + 3 * m + 1;
+    const int per = m * ld + 3 * m;
     double *A = fsm + (size_t)wib * per;
-    double *kv = A + m * m;
-    double *X = kv + m;
+    double *rd = A + m * ld;  // reciprocal pivots
+    double *X = rd + m;
     double *Y = X + m;
-    volatile double *flag = Y + m;
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (i >= n) return;
+    const unsigned full = 0xffffffffu;
     const int s = min(m, rank[i]);
     const double2 xi = x[i];
     for (int a = lane; a < s; a += 32) {
@@ -236,33 +257,45 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
         Y[a] = x[j].y;
     }
     __syncwarp();
+    const double c2 = 0.25 * alpha * alpha;  // q = c2 r^2
+    const int ntri = s * (s + 1) / 2;
     bool ok = false;
     int tries = 0;
     for (int t = 0; t <= 7 && !ok; ++t) {
         const double jit = t == 0 ? 0.0 : 1e-12 * pow(10.0, (double)(t - 1));
-        for (int idx = lane; idx < s * s; idx += 32) {
-            const int a = idx / s, b = idx - a * s;
-            if (b <= a) {
+        for (int idx = lane; idx < ntri; idx += 32) {
+            int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+            while (a * (a + 1) / 2 > idx) --a;
+            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+            const int b = idx - a * (a + 1) / 2;
+            double v = 1.0 + jit;
+            if (b != a) {
                 const double dx = X[a] - X[b], dy = Y[a] - Y[b];
-                A[a * m + b] = matern(nu, alpha, sqrt(dx * dx + dy * dy)) + (a == b ? jit : 0.0);
+                const double q = c2 * (dx * dx + dy * dy);
+                v = q > 0.0 ? matern_q(nu, q) : 1.0;
             }
+            A[a * ld + b] = v;
         }
         __syncwarp();
         ok = true;
         for (int j = 0; j < s; ++j) {
+            double dj = 0.0, rj = 0.0;
             if (lane == 0) {
-                const double d = A[j * m + j];
-                flag[0] = d > 0.0 ? 1.0 : 0.0;
-                if (d > 0.0) A[j * m + j] = sqrt(d);
+                const double d = A[j * ld + j];
+                if (d > 0.0) {
+                    dj = sqrt(d);
+                    rj = 1.0 / dj;
+                    A[j * ld + j] = dj;
+                    rd[j] = rj;
+                }
             }
-            __syncwarp();
-            if (flag[0] == 0.0) { ok = false; break; }
-            const double djj = A[j * m + j];
-            for (int a = j + 1 + lane; a < s; a += 32) A[a * m + j] /= djj;
+            rj = __shfl_sync(full, rj, 0);
+            if (!(rj > 0.0)) { ok = false; break; }
+            for (int a = j + 1 + lane; a < s; a += 32) A[a * ld + j] *= rj;
             __syncwarp();
             for (int a = j + 1 + lane; a < s; a += 32) {
-                const double laj = A[a * m + j];
-                for (int c = j + 1; c <= a; ++c) A[a * m + c] -= laj * A[c * m + j];
+                const double laj = A[a * ld + j];
+                for (int c = j + 1; c <= a; ++c) A[a * ld + c] = fma(-laj, A[c * ld + j], A[a * ld + c]);
             }
             __syncwarp();
         }
@@ -276,37 +309,50 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
         return;
     }
     if (tries > 0 && lane == 0) atomicAdd(njit, 1ull);
-    for (int a = lane; a < s; a += 32) {
-        const double dx = X[a] - xi.x, dy = Y[a] - xi.y;
-        kv[a] = matern(nu, alpha, sqrt(dx * dx + dy * dy));
+    // k = K(X_sigma, x_i); forward solve L y = k, then L' lambda = y (entries a, a + 32 per lane)
+    double kv[2] = {0.0, 0.0};
+    for (int h = 0; h < 2; ++h) {
+        const int a = lane + 32 * h;
+        if (a < s) {
+            const double dx = X[a] - xi.x, dy = Y[a] - xi.y;
+            const double q = c2 * (dx * dx + dy * dy);
+            kv[h] = q > 0.0 ? matern_q(nu, q) : 1.0;
+        }
     }
-    __syncwarp();
-    for (int c = 0; c < s; ++c) {  // L y = k
-        const double yc = kv[c] / A[c * m + c];
-        __syncwarp();
-        if (lane == 0) kv[c] = yc;
-        for (int a = c + 1 + lane; a < s; a += 32) kv[a] -= A[a * m + c] * yc;
-        __syncwarp();
+    for (int c = 0; c < s; ++c) {
+        const int hc = c >> 5;
+        double yc = __shfl_sync(full, hc ? kv[1] : kv[0], c & 31);
+        yc *= rd[c];
+        if (lane == (c & 31)) kv[hc] = yc;
+        for (int h = 0; h < 2; ++h) {
+            const int a = lane + 32 * h;
+            if (a > c && a < s) kv[h] = fma(-A[a * ld + c], yc, kv[h]);
+        }
     }
-    double part = 0.0;
-    for (int a = lane; a < s; a += 32) part += kv[a] * kv[a];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    const double c2 = 1.0 - part;
-    for (int c = s - 1; c >= 0; --c) {  // L' lambda = y
-        const double lc = kv[c] / A[c * m + c];
-        __syncwarp();
-        if (lane == 0) kv[c] = lc;
-        for (int a = lane; a < c; a += 32) kv[a] -= A[c * m + a] * lc;
-        __syncwarp();
+    double part = kv[0] * kv[0] + kv[1] * kv[1];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(full, part, o);
+    const double cc = 1.0 - part;
+    for (int c = s - 1; c >= 0; --c) {
+        const int hc = c >> 5;
+        double lc = __shfl_sync(full, hc ? kv[1] : kv[0], c & 31);
+        lc *= rd[c];
+        if (lane == (c & 31)) kv[hc] = lc;
+        for (int h = 0; h < 2; ++h) {
+            const int a = lane + 32 * h;
+            if (a < c) kv[h] = fma(-A[c * ld + a], lc, kv[h]);
+        }
     }
-    if (!(c2 > 0.0)) {
+    if (!(cc > 0.0)) {
         if (lane == 0 && tries == 0) atomicAdd(njit, 1ull);
         for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = q == 0 ? 1.0 : 0.0;
         return;
     }
-    const double ic = 1.0 / sqrt(c2);
+    const double ic = 1.0 / sqrt(cc);
     if (lane == 0) val_ell[i] = ic;
-    for (int q = lane; q < m; q += 32) val_ell[(int64_t)(1 + q) * n + i] = q < s ? -kv[q] * ic : 0.0;
+    for (int h = 0; h < 2; ++h) {
+        const int q = lane + 32 * h;
+        if (q < m) val_ell[(int64_t)(1 + q) * n + i] = q < s ? -kv[h] * ic : 0.0;
+    }
 }
 
 // ---------------------------------------------------------------- transpose of U~ (rows of U~)
@@ -551,14 +597,16 @@ int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const i
     PHS_REQUIRE(nu == 0.5 || nu == 1.0 || nu == 1.5 || nu == 2.0 || nu == 2.5, PHS_ERR_INVALID_ARG,
                 "nu must be 0.5, 1, 1.5, 2 or 2.5");
     PHS_REQUIRE(alpha > 0 && std::isfinite(alpha), PHS_ERR_INVALID_ARG, "alpha must be positive");
-    const size_t per = (size_t)(m * m + 3 * m + 1) * sizeof(double);
+    upload_bessel_tables();
+    const int ld = m | 1;  // odd row stride: rows of consecutive lanes fall in different banks
+    const size_t per = (size_t)(m * ld + 3 * m) * sizeof(double);
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
     const size_t smem = per * wpb;
     PHS_CUDA(cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     DBuf<unsigned long long> cnt(2);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, 2 * sizeof(unsigned long long), s));
-    factor_kernel<<<blocks_for(n, wpb), 32 * wpb, smem, s>>>(x, n, rank, nbr_ell, m, nu, alpha, val_ell, cnt.get(),
-                                                             cnt.get() + 1);
+    factor_kernel<<<blocks_for(n, wpb), 32 * wpb, smem, s>>>(x, n, rank, nbr_ell, m, ld, nu, alpha, val_ell,
+                                                             cnt.get());
     PHS_LAUNCH_CHECK();
     unsigned long long h[2];
     PHS_CUDA(cudaMemcpyAsync(h, cnt.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
