@@ -423,101 +423,102 @@ __device__ __forceinline__ float phi_r2<float, 4>(float r2) { return 0.5f * r2 *
 
 // Table-driven natural logarithm in FP64, after P. T. P. Tang, "Table-driven
 // implementation of the logarithm function in IEEE floating-point arithmetic"
-// (ACM TOMS 16(4), 1990):  x = 2^e m with m in [1, 2);  F = 1 + j/1024 is the
-// grid point nearest m;  log x = e log 2 + log F + log(1 + r),  r = (m - F)/F,
-// |r| <= 2^-11, with log(1 + r) from its degree-4 Taylor polynomial (truncation
-// below 6e-18).  log F and 1/F come from 1025-entry tables in shared memory.
-// Valid for positive normal x.  FP64 work: 1 DADD + 1 DMUL + 3 DFMA + 1 DMUL + 1 DFMA.
-constexpr int kLogTab = 1025;
-__device__ double g_logtab[kLogTab];
-__device__ double g_invtab[kLogTab];
+// (ACM TOMS 16(4), 1990):  x = 2^e m with m in [1, 2);  F_j = 1 + j/2048 is the grid
+// point nearest m;  log x = e log 2 + log F_j + log(1 + r),  r = m/F_j - 1 (one FMA
+// with the tabulated 1/F_j), |r| < 2^-12, log(1 + r) ~ r - r^2/2 + r^3/3 (truncation
+// below 2^-50).  e log 2 comes from a table over biased exponents 768..1026 (smaller
+// exponents clamp: there x < 2^-255 and x log x vanishes to 1e-74).  x = 0 returns a
+// finite value, so x log x is 0 there.  FP64 work: 4 DFMA + 1 DADD.
+constexpr int kLogTab = 2049;
+constexpr int kExpLo = 768, kExpTab = 259;
+__device__ double2 g_logtab[kLogTab];  // (log F_j, 1/F_j)
+__device__ double g_eln2[kExpTab];     // (e - 1023) log 2 for biased e = kExpLo + i
 
-__device__ __forceinline__ double tab_log(double x, const double *lf, const double *inv) {
+__device__ __forceinline__ double tab_log(double x, const double2 *tab, const double *eln2) {
     const int hi = __double2hiint(x), lo = __double2loint(x);
-    const int e = (hi >> 20) - 1023;
-    const int j = (((hi >> 9) & 0x7ff) + 1) >> 1;
+    const int j = (((hi >> 8) & 0xfff) + 1) >> 1;
+    const int ei = min(max((hi >> 20) - kExpLo, 0), kExpTab - 1);
     const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
-    const double F = j < 1024 ? __hiloint2double(0x3ff00000 | (j << 10), 0) : 2.0;
-    const double r = (m - F) * inv[j];
-    double c = fma(-0.25, r, 0.33333333333333333);
-    c = fma(c, r, -0.5);
+    const double2 fj = tab[j];
+    const double r = fma(m, fj.y, -1.0);
+    double c = fma(r, 0.33333333333333333, -0.5);
     c = fma(c, r, 1.0);
-    return fma((double)e, 0.69314718055994530942, fma(c, r, lf[j]));
+    return fma(c, r, fj.x + eln2[ei]);
 }
 
 constexpr int P2P_T = 128;
-
-// even-K FP64 near field with the table-driven logarithm
-template <int K>
-__device__ __forceinline__ double phi_r2_tab(double r2, const double *lf, const double *inv) {
-    const double L = tab_log(r2, lf, inv);
-    return K == 2 ? 0.5 * r2 * L : 0.5 * r2 * r2 * L;
-}
 
 template <typename T, int K>
 struct UsesLogTab {
     static constexpr bool value = sizeof(T) == 8 && (K % 2 == 0);
 };
 
+// Near field of one leaf per block iteration (persistent blocks: the logarithm tables
+// load once per block).  G threads share a target (power of two <= 32) so small
+// leaves keep the block busy.  For the FP64 log kernel the sum is sum_j r^2 log(r^2) t_j,
+// halved once at the end (phi = r^2 log r = r^2 log(r^2) / 2, r^k log r likewise).
 template <typename T, int K>
-__global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, const int *leaf_box, const int *near_off,
+__global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, int nleaf, const int *leaf_box, const int *near_off,
                                                    const int2 *near_rng, const double2 *xs, const double *t,
                                                    double *y) {
     __shared__ T sx[P2P_T], sy[P2P_T], st[P2P_T];
-    extern __shared__ double logtab_sm[];  // [2][kLogTab] when the table log is used
-    const double *lf = logtab_sm, *inv = logtab_sm + kLogTab;
-    if (UsesLogTab<T, K>::value) {
-        for (int i = threadIdx.x; i < kLogTab; i += P2P_T) {
-            logtab_sm[i] = g_logtab[i];
-            logtab_sm[kLogTab + i] = g_invtab[i];
-        }
+    extern __shared__ double2 logtab_sm[];  // [kLogTab] (log F, 1/F), then [kExpTab] e log 2
+    constexpr bool kTab = UsesLogTab<T, K>::value;
+    const double *eln2 = reinterpret_cast<const double *>(logtab_sm + kLogTab);
+    if (kTab) {
+        for (int i = threadIdx.x; i < kLogTab; i += P2P_T) logtab_sm[i] = g_logtab[i];
+        for (int i = threadIdx.x; i < kExpTab; i += P2P_T)
+            reinterpret_cast<double *>(logtab_sm + kLogTab)[i] = g_eln2[i];
+        __syncthreads();
     }
-    const int li = blockIdx.x;
-    const int b = leaf_box[li];
-    double cx, cy, w;
-    box_geom(tv, b, cx, cy, w);
-    const int s = tv.start[b], e = tv.end[b];
-    // G threads share a target (power of two <= 32) so small leaves keep the block busy
-    const int nt = e - s;
-    int G = 1;
-    while (G < 32 && nt * G * 2 <= P2P_T) G <<= 1;
-    const int tpp = P2P_T / G;
-    const int sub = threadIdx.x & (G - 1);
-    for (int i0 = s; i0 < e; i0 += tpp) {
-        const int i = i0 + threadIdx.x / G;
-        T xi = 0, yi = 0;
-        if (i < e) {
-            const double2 p = xs[i];
-            xi = T(p.x - cx);
-            yi = T(p.y - cy);
-        }
-        T acc = 0;
-        for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
-            const int2 rg = near_rng[r];
-            for (int j0 = rg.x; j0 < rg.y; j0 += P2P_T) {
-                const int j = j0 + threadIdx.x;
-                __syncthreads();
-                if (j < rg.y) {
-                    const double2 p = xs[j];
-                    sx[threadIdx.x] = T(p.x - cx);
-                    sy[threadIdx.x] = T(p.y - cy);
-                    st[threadIdx.x] = T(t[j]);
-                }
-                __syncthreads();
-                const int jn = min(P2P_T, rg.y - j0);
-                for (int jj = sub; jj < jn; jj += G) {
-                    const T dx = xi - sx[jj], dy = yi - sy[jj];
-                    const T r2 = dx * dx + dy * dy;
-                    if (UsesLogTab<T, K>::value) {
-                        if (r2 > T(0)) acc += (T)phi_r2_tab<K>((double)r2, lf, inv) * st[jj];
-                    } else {
-                        if (r2 > T(0)) acc += phi_r2<T, K>(r2) * st[jj];
+    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+        const int b = leaf_box[li];
+        double cx, cy, w;
+        box_geom(tv, b, cx, cy, w);
+        const int s = tv.start[b], e = tv.end[b];
+        const int nt = e - s;
+        int G = 1;
+        while (G < 32 && nt * G * 2 <= P2P_T) G <<= 1;
+        const int tpp = P2P_T / G;
+        const int sub = threadIdx.x & (G - 1);
+        for (int i0 = s; i0 < e; i0 += tpp) {
+            const int i = i0 + threadIdx.x / G;
+            T xi = 0, yi = 0;
+            if (i < e) {
+                const double2 p = xs[i];
+                xi = T(p.x - cx);
+                yi = T(p.y - cy);
+            }
+            T acc = 0;
+            for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
+                const int2 rg = near_rng[r];
+                for (int j0 = rg.x; j0 < rg.y; j0 += P2P_T) {
+                    const int j = j0 + threadIdx.x;
+                    __syncthreads();
+                    if (j < rg.y) {
+                        const double2 p = xs[j];
+                        sx[threadIdx.x] = T(p.x - cx);
+                        sy[threadIdx.x] = T(p.y - cy);
+                        st[threadIdx.x] = T(t[j]);
+                    }
+                    __syncthreads();
+                    const int jn = min(P2P_T, rg.y - j0);
+                    for (int jj = sub; jj < jn; jj += G) {
+                        const T dx = xi - sx[jj], dy = yi - sy[jj];
+                        const T r2 = fma(dy, dy, dx * dx);
+                        if constexpr (kTab) {
+                            const double L = tab_log(r2, logtab_sm, eln2);
+                            const double f = K == 2 ? r2 * L : (r2 * r2) * L;
+                            acc = fma(f, st[jj], acc);
+                        } else {
+                            if (r2 > T(0)) acc += phi_r2<T, K>(r2) * st[jj];
+                        }
                     }
                 }
             }
+            for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (sub == 0 && i < e) y[i] = kTab ? 0.5 * (double)acc : (double)acc;
         }
-        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (sub == 0 && i < e) y[i] = (double)acc;
     }
 }
 
@@ -763,22 +764,32 @@ static void far_field_m2l32(Fmm &f, const Tree &t, const PointSet &ps, const dou
 
 template <typename T, int K>
 static void p2p_launch(const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s) {
-    const size_t smem = UsesLogTab<T, K>::value ? 2 * kLogTab * sizeof(double) : 0;
-    p2p_kernel<T, K><<<t.nleaf, P2P_T, smem, s>>>(tree_view(t), t.leaf_box.get(), t.near_off.get(),
-                                                  t.near_rng.get(), ps.xs.get(), tv_sorted, y);
+    const size_t smem = UsesLogTab<T, K>::value ? kLogTab * sizeof(double2) + kExpTab * sizeof(double) : 0;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        int dev = 0, nsm = 0, per = 0;
+        PHS_CUDA(cudaGetDevice(&dev));
+        PHS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        PHS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, p2p_kernel<T, K>, P2P_T, smem));
+        grid_cap = std::max(1, nsm * std::max(per, 1));
+    }
+    const int grid = std::min(t.nleaf, grid_cap);
+    p2p_kernel<T, K><<<grid, P2P_T, smem, s>>>(tree_view(t), t.nleaf, t.leaf_box.get(), t.near_off.get(),
+                                               t.near_rng.get(), ps.xs.get(), tv_sorted, y);
     PHS_LAUNCH_CHECK();
 }
 
-// log F_j and 1/F_j, F_j = 1 + j/1024, for the table-driven logarithm
+// (log F_j, 1/F_j), F_j = 1 + j/2048, and e log 2 for the table-driven logarithm
 static void upload_log_tables() {
-    std::vector<double> lf(kLogTab), inv(kLogTab);
+    std::vector<double2> tab(kLogTab);
     for (int j = 0; j < kLogTab; ++j) {
-        const long double F = 1.0L + (long double)j / 1024.0L;
-        lf[j] = (double)std::log(F);
-        inv[j] = (double)(1.0L / F);
+        const long double F = 1.0L + (long double)j / 2048.0L;
+        tab[j] = make_double2((double)std::log(F), (double)(1.0L / F));
     }
-    PHS_CUDA(cudaMemcpyToSymbol(g_logtab, lf.data(), kLogTab * sizeof(double)));
-    PHS_CUDA(cudaMemcpyToSymbol(g_invtab, inv.data(), kLogTab * sizeof(double)));
+    std::vector<double> el(kExpTab);
+    for (int i = 0; i < kExpTab; ++i) el[i] = (double)((long double)(kExpLo + i - 1023) * std::log(2.0L));
+    PHS_CUDA(cudaMemcpyToSymbol(g_logtab, tab.data(), kLogTab * sizeof(double2)));
+    PHS_CUDA(cudaMemcpyToSymbol(g_eln2, el.data(), kExpTab * sizeof(double)));
 }
 template <typename T>
 static void p2p_dispatch(int k, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s) {
