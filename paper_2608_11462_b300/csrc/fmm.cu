@@ -446,7 +446,7 @@ __device__ __forceinline__ double tab_log(double x, const double2 *tab, const do
     return fma(c, r, fj.x + eln2[ei]);
 }
 
-constexpr int P2P_T = 128;
+constexpr int P2P_T = kP2PThreads;
 
 template <typename T, int K>
 struct UsesLogTab {
@@ -520,6 +520,140 @@ __global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, int nleaf, cons
             if (sub == 0 && i < e) y[i] = kTab ? 0.5 * (double)acc : (double)acc;
         }
     }
+}
+
+// phi(r) up to the factor 1/2 of the log kernels (applied once per sum), from dx, dy
+template <int K, bool kTab>
+__device__ __forceinline__ double phi_sym(double dx, double dy, const double2 *tab, const double *eln2) {
+    const double r2 = fma(dy, dy, dx * dx);
+    if constexpr (kTab) {
+        const double L = tab_log(r2, tab, eln2);
+        return K == 2 ? r2 * L : (r2 * r2) * L;
+    } else {
+        return phi_r2<double, K>(r2);
+    }
+}
+
+// Symmetric FP64 near field: every pair of points in different leaves is evaluated once.
+// Leaf b sums its own box (rows only) and each near range R after it in Morton order:
+// rows into y, columns (sum_{i in b} phi_ij t_i, accumulated systolically across the
+// lanes that share a source, then summed over the warps in a fixed order) into the
+// scratch slot of (b, R).
+// Ranges before b arrive through p2p_gather from the slots of the earlier leaves, which
+// holds because the near relation is symmetric (its complement, the V-list relation,
+// is).  One pass per leaf: the plan enables this path only when every leaf has at most
+// P2P_T points.
+template <int K>
+__global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, const int *leaf_box,
+                                                       const int *near_off, const int2 *near_rng,
+                                                       const int *slot_off, const double2 *xs, const double *t,
+                                                       double *y, double *scratch) {
+    __shared__ double sx[P2P_T], sy[P2P_T], st[P2P_T];
+    __shared__ double colp[P2P_T / 32][P2P_T];
+    extern __shared__ double2 logtab_sm[];
+    constexpr bool kTab = (K % 2 == 0);
+    const double *eln2 = reinterpret_cast<const double *>(logtab_sm + kLogTab);
+    if (kTab) {
+        for (int i = threadIdx.x; i < kLogTab; i += P2P_T) logtab_sm[i] = g_logtab[i];
+        for (int i = threadIdx.x; i < kExpTab; i += P2P_T)
+            reinterpret_cast<double *>(logtab_sm + kLogTab)[i] = g_eln2[i];
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double scale = kTab ? 0.5 : 1.0;  // r^k log r = r^k log(r^2) / 2
+    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+        const int b = leaf_box[li];
+        double cx, cy, w;
+        box_geom(tv, b, cx, cy, w);
+        const int s = tv.start[b], e = tv.end[b];
+        const int nt = e - s;
+        int G = 1;
+        while (G < 32 && nt * G * 2 <= P2P_T) G <<= 1;
+        const int sub = threadIdx.x & (G - 1);
+        const int i = s + threadIdx.x / G;
+        const bool act = i < e;
+        double xi = 0, yi = 0, ti = 0;
+        if (act) {
+            const double2 p = xs[i];
+            xi = p.x - cx;
+            yi = p.y - cy;
+            ti = t[i];
+        }
+        double acc = 0;
+        int slot = slot_off[li];
+        for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
+            const int2 rg = near_rng[r];
+            const bool self = rg.x == s;
+            if (!self && rg.x < e) continue;
+            for (int j0 = rg.x; j0 < rg.y; j0 += P2P_T) {
+                const int j = j0 + threadIdx.x;
+                __syncthreads();
+                if (j < rg.y) {
+                    const double2 p = xs[j];
+                    sx[threadIdx.x] = p.x - cx;
+                    sy[threadIdx.x] = p.y - cy;
+                    st[threadIdx.x] = t[j];
+                }
+                __syncthreads();
+                const int jn = min(P2P_T, rg.y - j0);
+                if (self) {
+                    const int nk = (jn + G - 1) / G;
+                    for (int k = 0; k < nk; ++k) {
+                        const int jj = k * G + sub;
+                        const bool v = jj < jn;
+                        const int jc = v ? jj : 0;
+                        const double f = v ? phi_sym<K, kTab>(xi - sx[jc], yi - sy[jc], logtab_sm, eln2) : 0.0;
+                        acc = fma(f, st[jc], acc);
+                    }
+                } else {
+                    // systolic column sums: the S = 32/G lanes of a sub-group (same sub) take the
+                    // columns of a tile in rotation, step k: lane u on column (k + u) mod S, and
+                    // pass the running column sum to lane u - 1, so after S steps lane u holds
+                    // the sum of column u over the sub-group's targets (one FMA per pair)
+                    const int S = 32 / G, u = lane / G;
+                    for (int t0 = 0; t0 < jn; t0 += 32) {
+                        double cs = 0.0;
+                        for (int k = 0; k < S; ++k) {
+                            const int jj = t0 + ((k + u) & (S - 1)) * G + sub;
+                            const bool v = jj < jn;
+                            const int jc = v ? jj : 0;
+                            const double f = v ? phi_sym<K, kTab>(xi - sx[jc], yi - sy[jc], logtab_sm, eln2) : 0.0;
+                            acc = fma(f, st[jc], acc);
+                            cs = fma(f, ti, cs);
+                            cs = __shfl_sync(0xffffffffu, cs, (lane + G) & 31);
+                        }
+                        const int jo = t0 + u * G + sub;
+                        if (jo < jn) colp[warp][jo] = cs;
+                    }
+                }
+                if (!self) {
+                    __syncthreads();
+                    for (int q = threadIdx.x; q < jn; q += P2P_T) {
+                        double sum = 0;
+#pragma unroll
+                        for (int w2 = 0; w2 < P2P_T / 32; ++w2) sum += colp[w2][q];
+                        scratch[slot + (j0 - rg.x) + q] = scale * sum;
+                    }
+                }
+            }
+            if (!self) slot += rg.y - rg.x;
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (sub == 0 && act) y[i] = scale * acc;
+    }
+}
+
+// y_j += the column sums of the earlier leaves whose near ranges contain j's leaf
+// (ascending slot order: deterministic)
+__global__ void p2p_gather(TreeView tv, const int *leaf_box, const int *point_leaf, const int *goff,
+                           const int *gbase, int64_t n, const double *scratch, double *y) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int d = point_leaf[j];
+    const int o = (int)j - tv.start[leaf_box[d]];
+    double sum = 0;
+    for (int p = goff[d]; p < goff[d + 1]; ++p) sum += scratch[gbase[p] + o];
+    y[j] += sum;
 }
 
 // exact O(n^2) product, FP64
@@ -791,8 +925,40 @@ static void upload_log_tables() {
     PHS_CUDA(cudaMemcpyToSymbol(g_logtab, tab.data(), kLogTab * sizeof(double2)));
     PHS_CUDA(cudaMemcpyToSymbol(g_eln2, el.data(), kExpTab * sizeof(double)));
 }
+template <int K>
+static void p2p_sym_launch(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y,
+                           cudaStream_t s) {
+    const size_t smem = (K % 2 == 0) ? kLogTab * sizeof(double2) + kExpTab * sizeof(double) : 0;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        int dev = 0, nsm = 0, per = 0;
+        PHS_CUDA(cudaGetDevice(&dev));
+        PHS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        PHS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, p2p_sym_kernel<K>, P2P_T, smem));
+        grid_cap = std::max(1, nsm * std::max(per, 1));
+    }
+    if (f.sym_scratch.n < (size_t)std::max<int64_t>(t.sym_total, 1)) f.sym_scratch.alloc(std::max<int64_t>(t.sym_total, 1));
+    p2p_sym_kernel<K><<<std::min(t.nleaf, grid_cap), P2P_T, smem, s>>>(
+        tree_view(t), t.nleaf, t.leaf_box.get(), t.near_off.get(), t.near_rng.get(), t.sym_slot.get(), ps.xs.get(),
+        tv_sorted, y, f.sym_scratch.get());
+    PHS_LAUNCH_CHECK();
+    p2p_gather<<<blocks_for(ps.n, 256), 256, 0, s>>>(tree_view(t), t.leaf_box.get(), t.point_leaf.get(),
+                                                     t.sym_goff.get(), t.sym_gbase.get(), ps.n, f.sym_scratch.get(), y);
+    PHS_LAUNCH_CHECK();
+}
+
 template <typename T>
-static void p2p_dispatch(int k, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y, cudaStream_t s) {
+static void p2p_dispatch(Fmm &f, int k, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y,
+                         cudaStream_t s) {
+    if (sizeof(T) == 8 && t.sym_ok) {
+        switch (k) {
+            case 1: p2p_sym_launch<1>(f, t, ps, tv_sorted, y, s); return;
+            case 2: p2p_sym_launch<2>(f, t, ps, tv_sorted, y, s); return;
+            case 3: p2p_sym_launch<3>(f, t, ps, tv_sorted, y, s); return;
+            case 4: p2p_sym_launch<4>(f, t, ps, tv_sorted, y, s); return;
+            default: p2p_sym_launch<5>(f, t, ps, tv_sorted, y, s); return;
+        }
+    }
     switch (k) {
         case 1: p2p_launch<T, 1>(t, ps, tv_sorted, y, s); break;
         case 2: p2p_launch<T, 2>(t, ps, tv_sorted, y, s); break;
@@ -817,7 +983,7 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
         // odd k: distance-kernel far field by Chebyshev interpolation, FP64 only
         PHS_REQUIRE(mode == 0, PHS_ERR_INVALID_ARG, "odd spline orders run in FP64 (precision 0)");
         if (tm) tm->begin(s);
-        p2p_dispatch<double>(f.k, t, ps, t_sorted, y, s);
+        p2p_dispatch<double>(f, f.k, t, ps, t_sorted, y, s);
         if (tm) tm->end(T_P2P, s);
         cheb_far_field(f, t, ps, t_sorted, s, tm);
         if (tm) tm->begin(s);
@@ -826,8 +992,8 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
         return;
     }
     if (tm) tm->begin(s);
-    if (mode == 0) p2p_dispatch<double>(f.k, t, ps, t_sorted, y, s);
-    else p2p_dispatch<float>(f.k, t, ps, t_sorted, y, s);
+    if (mode == 0) p2p_dispatch<double>(f, f.k, t, ps, t_sorted, y, s);
+    else p2p_dispatch<float>(f, f.k, t, ps, t_sorted, y, s);
     if (tm) tm->end(T_P2P, s);
     if (mode <= 1) far_field<double>(f, t, ps, t_sorted, s, tm);
     else if (mode == 2) far_field_m2l32(f, t, ps, t_sorted, s, tm);

@@ -101,7 +101,15 @@ struct Tree {
     DBuf<int> near_off;              // near (direct) ranges per box (CSR)
     DBuf<int2> near_rng;
     int64_t near_pairs = 0, m2l_pairs = 0;
+    // symmetric near field: leaf li writes the column sums of its near ranges after it
+    // (Morton order) to scratch [sym_slot[li], ...); leaf d gathers its share from the
+    // slots of earlier leaves, starting at the offsets sym_gbase[sym_goff[d] .. sym_goff[d+1])
+    bool sym_ok = false;             // every leaf fits one P2P pass (<= kP2PThreads points)
+    int max_leaf = 0;
+    int64_t sym_total = 0;
+    DBuf<int> sym_slot, sym_goff, sym_gbase;
 };
+constexpr int kP2PThreads = 128;     // threads of a near-field block
 
 struct PointSet {
     int64_t n = 0;
@@ -155,6 +163,7 @@ struct Fmm {
     DBuf<int> tc_gexp;                   // log2 bound of the frame-change row growth [49][nd]
     DBuf<int> tc_mexp;                   // per-box exponent bound of the multipoles
     DBuf<int> tc_err;                    // device status (nonzero: a bounded wait expired)
+    DBuf<double> sym_scratch;            // column sums of the symmetric near field
 };
 // tensor_m2l: run the FP64 M2L of the log kernel on the tensor cores (m2l_tc.cu)
 void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s);

@@ -203,6 +203,63 @@ __global__ void nearlist_kernel(TreeView tv, int nbox, int *cnt, const int *off,
     else if (tv.nchild[b] == 0) atomicAdd(pairs, (unsigned long long)np);
 }
 
+// Symmetric near field (see Tree::sym_*): a near range of leaf b is either b itself, or
+// the points of a box disjoint from b, entirely before or after b in Morton order; each
+// leaf inside a range after b receives one gather offset.
+__global__ void sym_count(TreeView tv, const int *leaf_box, int nleaf, const int *near_off, const int2 *near_rng,
+                          const int *point_leaf, int *up_len, int *gcnt, int *maxleaf) {
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nleaf) return;
+    const int b = leaf_box[li];
+    const int e = tv.end[b];
+    atomicMax(maxleaf, e - tv.start[b]);
+    int len = 0;
+    for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
+        const int2 rg = near_rng[r];
+        if (rg.x < e) continue;  // b itself or before b
+        len += rg.y - rg.x;
+        for (int j = rg.x; j < rg.y;) {
+            const int d = point_leaf[j];
+            atomicAdd(&gcnt[d], 1);
+            j = tv.end[leaf_box[d]];
+        }
+    }
+    up_len[li] = len;
+}
+__global__ void sym_fill(TreeView tv, const int *leaf_box, int nleaf, const int *near_off, const int2 *near_rng,
+                         const int *point_leaf, const int *slot, const int *goff, int *gcur, int *gbase) {
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nleaf) return;
+    const int b = leaf_box[li];
+    const int e = tv.end[b];
+    int base = slot[li];
+    for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
+        const int2 rg = near_rng[r];
+        if (rg.x < e) continue;
+        for (int j = rg.x; j < rg.y;) {
+            const int d = point_leaf[j];
+            const int db = leaf_box[d];
+            gbase[goff[d] + atomicAdd(&gcur[d], 1)] = base + (tv.start[db] - rg.x);
+            j = tv.end[db];
+        }
+        base += rg.y - rg.x;
+    }
+}
+// ascending offsets per leaf: a fixed summation order in the gather
+__global__ void sym_sort(const int *goff, int nleaf, int *gbase) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nleaf) return;
+    for (int a = goff[d] + 1; a < goff[d + 1]; ++a) {
+        const int v = gbase[a];
+        int c = a - 1;
+        while (c >= goff[d] && gbase[c] > v) {
+            gbase[c + 1] = gbase[c];
+            --c;
+        }
+        gbase[c + 1] = v;
+    }
+}
+
 __global__ void count_sum(const int *cnt, int n, unsigned long long *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicAdd(out, (unsigned long long)cnt[i]);
@@ -370,6 +427,35 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
         PHS_CUDA(cudaMemcpyAsync(&hp2, pairs.get(), sizeof(hp2), cudaMemcpyDeviceToHost, s));
         PHS_CUDA(cudaStreamSynchronize(s));
         tree.near_pairs = (int64_t)hp2;
+    }
+    {
+        const int nl = tree.nleaf;
+        DBuf<int> up_len(nl), gcnt(nl), gcur(nl), mx(1);
+        PHS_CUDA(cudaMemsetAsync(gcnt.get(), 0, nl * sizeof(int), s));
+        PHS_CUDA(cudaMemsetAsync(gcur.get(), 0, nl * sizeof(int), s));
+        PHS_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
+        sym_count<<<blocks_for(nl, 128), 128, 0, s>>>(tv, tree.leaf_box.get(), nl, tree.near_off.get(),
+                                                      tree.near_rng.get(), tree.point_leaf.get(), up_len.get(),
+                                                      gcnt.get(), mx.get());
+        PHS_LAUNCH_CHECK();
+        tree.sym_slot.alloc(nl + 1);
+        tree.sym_goff.alloc(nl + 1);
+        tree.sym_total = exclusive_scan_i32(up_len.get(), tree.sym_slot.get(), nl, s);
+        const int64_t ng = exclusive_scan_i32(gcnt.get(), tree.sym_goff.get(), nl, s);
+        PHS_REQUIRE(tree.sym_total < (1ll << 31), PHS_ERR_INVALID_ARG, "near field too large for 32-bit slots");
+        const int tails[2] = {(int)tree.sym_total, (int)ng};
+        PHS_CUDA(cudaMemcpyAsync(tree.sym_slot.get() + nl, &tails[0], sizeof(int), cudaMemcpyHostToDevice, s));
+        PHS_CUDA(cudaMemcpyAsync(tree.sym_goff.get() + nl, &tails[1], sizeof(int), cudaMemcpyHostToDevice, s));
+        tree.sym_gbase.alloc(std::max<int64_t>(ng, 1));
+        sym_fill<<<blocks_for(nl, 128), 128, 0, s>>>(tv, tree.leaf_box.get(), nl, tree.near_off.get(),
+                                                     tree.near_rng.get(), tree.point_leaf.get(), tree.sym_slot.get(),
+                                                     tree.sym_goff.get(), gcur.get(), tree.sym_gbase.get());
+        PHS_LAUNCH_CHECK();
+        sym_sort<<<blocks_for(nl, 128), 128, 0, s>>>(tree.sym_goff.get(), nl, tree.sym_gbase.get());
+        PHS_LAUNCH_CHECK();
+        PHS_CUDA(cudaMemcpyAsync(&tree.max_leaf, mx.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        PHS_CUDA(cudaStreamSynchronize(s));
+        tree.sym_ok = tree.max_leaf <= kP2PThreads;
     }
 }
 
