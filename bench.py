@@ -31,6 +31,11 @@ WORKLOAD = "tps_1m"
 # [-1/4,1/4]^2 (Sec. 2.2: the nu = 1 kernel carries the thin-plate term, Eq. 2.17).
 # nu = 1.5 fails to converge within 200 iterations at this size for alpha in {5, 20, 60}.
 NU, ALPHA = 1.0, 0.35
+# DRAM bytes (read + write) per launch from ncu captures summarised under profiles/,
+# None while the current kernel has no capture.  The tensor-core M2L was captured on the
+# n = 262144 case of this workload (618 tiles) and is scaled by the tile count.
+M2L_DRAM_BYTES_PER_TILE = (29.627136e6 + 27.904e3) / 618
+P2P_DRAM_BYTES = None
 
 
 def parse():
@@ -207,9 +212,10 @@ def main():
         pred = plan.eval(w, beta, tg_d)
         tim = plan.timing() if timing else None
         work = plan.work()
+        kw = plan.kernel_work()
         sizes = plan.frame()[1]
         plan.close()
-        return info, tim, work, sizes, pred
+        return info, tim, (work, kw), sizes, pred
 
     for _ in range(args.warmup):
         step()
@@ -222,7 +228,7 @@ def main():
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        info, tim, work, sizes, pred = step(timing=True)
+        info, tim, (work, kwork), sizes, pred = step(timing=True)
         e1.record(stream)
         barrier()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -261,34 +267,36 @@ def main():
             a[0] += ms
             a[1] += calls
     phases = {k_: v for k_, v in agg.items() if k_ in ("p2p", "m2l", "upward", "downward", "precond", "vector")}
-    dom = max(phases, key=lambda k_: phases[k_][0])
-    P = sizes[3] + 1
-    nd = sizes[4]
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2032.0))
-    fp64_peak_tflops = 148 * 2 * 2 * sm_mhz_max * 1e6 / 1e12   # 2 FP64 FMA / clk / SM
-    if dom == "m2l":
-        ms_launch = phases["m2l"][0] / phases["m2l"][1]
-        flops = 8.0 * nd * P * P * work["m2l_translations"]
-        prec_m2l = "f64" if args.precision in (0, 1) else "f32"
-        peak = fp64_peak_tflops if prec_m2l == "f64" else 148 * 128 * 2 * sm_mhz_max * 1e6 / 1e12
-        ach = flops / (ms_launch / 1e3) / 1e12
-        roof = {"kernel": f"m2l_kernel<{ 'double' if prec_m2l == 'f64' else 'float'}>", "bound": "alu",
-                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "peak_source": f"derived: 148 SMs x {'2 FP64' if prec_m2l == 'f64' else '128 FP32'} FMA/clk x "
-                               f"{sm_mhz_max:.0f} MHz",
-                "work_per_launch": f"8*nd*P^2 flops x {work['m2l_translations']} V-list translations",
-                "traffic": None}
-    elif dom == "p2p":
-        ms_launch = phases["p2p"][0] / phases["p2p"][1]
-        pairs = work["near_pairs"]
-        ach = pairs / (ms_launch / 1e3) / 1e9
-        roof = {"kernel": "p2p_kernel", "bound": "alu", "achieved": ach, "peak": None, "unit": "Gpairs/s",
-                "frac": None, "work_per_launch": f"{pairs} near-field pairs", "traffic": None}
+    # FP64 pipe: 2 instructions (DFMA, DMUL or DADD) per clock per SM
+    fp64_peak_g = 148 * 2 * sm_mhz_max * 1e6 / 1e9
+    ms_p2p = phases["p2p"][0] / max(phases["p2p"][1], 1)
+    # per evaluated pair: 2 DADD + DMUL + DFMA (r^2), 4 DFMA + DADD (table log), DMUL
+    # (r^2 log r^2), DFMA (row sum) = 11; one more DFMA where the pair also feeds a column sum
+    p2p_ops = 11 * kwork["p2p_pairs"] + kwork["p2p_column_pairs"]
+    ach = p2p_ops / (ms_p2p / 1e3) / 1e9
+    roof_p2p = {"kernel": "p2p_sym_kernel<2> + p2p_gather", "bound": "alu", "achieved": ach, "peak": fp64_peak_g,
+                "unit": "G FP64-pipe instr/s", "frac": ach / fp64_peak_g,
+                "peak_source": f"derived: 148 SMs x 2 FP64 instr/clk x {sm_mhz_max:.0f} MHz",
+                "work_per_launch": f"{kwork['p2p_pairs']} pairs evaluated ({kwork['p2p_column_pairs']} with column "
+                                   f"sums) = {p2p_ops} FP64 instr; {work['near_pairs']} ordered near pairs",
+                "ms_per_launch": ms_p2p, "traffic": P2P_DRAM_BYTES}
+    ms_m2l = phases["m2l"][0] / max(phases["m2l"][1], 1)
+    roof_m2l = None
+    if kwork["tc_steps"] > 0:
+        flops = 2.0 * kwork["tc_steps"] * kwork["tc_mmas_per_step"] * kwork["tc_mma_macs"]
+        pk = float(peaks.get("bf16_tflops_sustained", 1371.7))
+        ach = flops / (ms_m2l / 1e3) / 1e12
+        roof_m2l = {"kernel": "m2l_tc_kernel<4>", "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                    "frac": ach / pk, "peak_source": "measured bf16 (sustained, kernel inside a long step)",
+                    "work_per_launch": f"{kwork['tc_steps']} steps x {kwork['tc_mmas_per_step']} tcgen05.mma x "
+                                       f"{kwork['tc_mma_macs']} MAC (bf16 digit planes, FP32 accumulate)",
+                    "ms_per_launch": ms_m2l,
+                    "traffic": M2L_DRAM_BYTES_PER_TILE * kwork["tc_tiles"]}
+    if roof_m2l is not None and ms_m2l > ms_p2p:
+        roof, roof_other = roof_m2l, {"roofline_p2p": roof_p2p}
     else:
-        ms_launch = phases[dom][0] / max(phases[dom][1], 1)
-        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": None, "traffic": None}
-    roof["ms_per_launch"] = ms_launch
+        roof, roof_other = roof_p2p, ({"roofline_m2l": roof_m2l} if roof_m2l else {})
     roof["peak_kind"] = peak_kind
     # the preconditioner apply (HBM-bound) alongside: 2 passes over the factor + vectors
     pre_ms = phases["precond"][0] / max(phases["precond"][1], 1)
@@ -312,7 +320,7 @@ def main():
                 "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"], "ms_fit": info["ms_fit"],
                 "ms_matvec_avg": info["ms_matvec_avg"]},
         "phases_ms_per_step": {k_: v[0] / args.steps for k_, v in agg.items()},
-        "roofline": roof, "roofline_precond": pre, "clocks": clk, "gpu_launches": int(launches),
+        "roofline": roof, **roof_other, "roofline_precond": pre, "clocks": clk, "gpu_launches": int(launches),
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(16 * n + 8 * n + 16 * m_t),
                 "d2h_bytes_per_step": int(8 * n + 8 * 3 + 8 * m_t)},
     }

@@ -175,6 +175,16 @@ phs_status phs_plan_precond(phs_plan_t plan, const double *r_dev, double *z_dev,
 /* Direct-interaction pair count of the tree (P2P work per matvec) and V-list
  * translation count (M2L work per matvec): counts_host[0..1]. */
 phs_status phs_plan_work(phs_plan_t plan, int64_t *counts_host);
+/* Work of one FP64 matvec per kernel, for roofline accounting (host array of 6):
+ *   [0] point pairs the near-field kernel evaluates (own leaf: all ordered pairs;
+ *       pairs across leaves once on the symmetric path, both orders otherwise),
+ *   [1] of those, pairs that also feed a column sum (symmetric path),
+ *   [2] tensor-core M2L steps (offset class x 48-column K chunk, summed over the
+ *       16-box tiles; 0 when the M2L runs on the CUDA cores),
+ *   [3] tensor-core M2L tiles,
+ *   [4] tcgen05.mma instructions per step,
+ *   [5] multiply-adds of one instruction (M * N * K). */
+phs_status phs_plan_kernel_work(phs_plan_t plan, int64_t *counts_host);
 /* Per-phase device timing of the most recent phs_fit / phs_matvec calls, in ms,
  * measured with CUDA events on the plan's stream when enabled (0/1).
  * ms_host[0..7] = (p2p, m2l, upward, downward, precond, vector, eval, total);

@@ -135,6 +135,12 @@ class Plan:
         check(lib().phs_plan_work(self._h, c))
         return {"near_pairs": c[0], "m2l_translations": c[1]}
 
+    def kernel_work(self):
+        c = (ctypes.c_int64 * 6)()
+        check(lib().phs_plan_kernel_work(self._h, c))
+        return {"p2p_pairs": c[0], "p2p_column_pairs": c[1], "tc_steps": c[2], "tc_tiles": c[3],
+                "tc_mmas_per_step": c[4], "tc_mma_macs": c[5]}
+
     def set_timing(self, enabled: bool):
         check(lib().phs_plan_set_timing(self._h, int(bool(enabled))))
 

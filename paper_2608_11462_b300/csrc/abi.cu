@@ -924,6 +924,20 @@ phs_status phs_plan_work(phs_plan_t pl, int64_t *counts_host) {
     PHS_CATCH
 }
 
+phs_status phs_plan_kernel_work(phs_plan_t pl, int64_t *counts_host) {
+    PHS_TRY
+    PHS_REQUIRE(pl && counts_host, PHS_ERR_INVALID_ARG, "bad arguments");
+    const Tree &t = pl->tree;
+    const bool sym = t.sym_ok;
+    counts_host[0] = sym ? t.p2p_self_pairs + t.p2p_upper_pairs : t.near_pairs;
+    counts_host[1] = sym ? t.p2p_upper_pairs : 0;
+    counts_host[2] = pl->fmm.tc_steps;
+    counts_host[3] = pl->fmm.tc_tiles;
+    counts_host[4] = pl->fmm.tc ? m2l_tc_mmas_per_step() : 0;
+    counts_host[5] = pl->fmm.tc ? (int64_t)128 * pl->fmm.tc_npad * 16 : 0;
+    PHS_CATCH
+}
+
 phs_status phs_plan_set_timing(phs_plan_t pl, int enabled) {
     PHS_TRY
     PHS_REQUIRE(pl, PHS_ERR_INVALID_ARG, "null plan");

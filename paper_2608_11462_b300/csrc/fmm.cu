@@ -1057,7 +1057,7 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     PHS_CUDA(cudaStreamSynchronize(s));
     upload_log_tables();
     if (!f.log_core) cheb_setup(f, cheb_q, s);
-    (void)t;
+    m2l_tc_count(f, t, s);
 }
 
 // ---------------------------------------------------------------- evaluation at targets

@@ -76,9 +76,26 @@ __device__ __forceinline__ long long to_fixed(double x, int sh) {
     return (long long)bits < 0 ? -v : v;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(int lo, int hi) {
-    __nv_bfloat162 h = __floats2bfloat162_rn((float)lo, (float)hi);
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Balanced base-256 digits of |y| < 2^47 as floats, d[0] the top digit: with
+// z = y + 0x808080 the three low digits are the bytes of z minus 128 and the rest
+// follow from z >> 24 the same way.  Each byte becomes a float exactly by the
+// magic number 2^23 (bits 0x4B000000 | byte), so no integer-to-float conversion.
+__device__ __forceinline__ void digits_f(long long y, float *d) {
+    const long long z = y + 0x808080ll;
+    const unsigned lo = (unsigned)z;
+    const unsigned z2 = (unsigned)((int)(z >> 24) + 0x8080);
+    constexpr float kBias = 8388736.0f;  // 2^23 + 128
+    d[5] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7540)) - kBias;
+    d[4] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7541)) - kBias;
+    d[3] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7542)) - kBias;
+    d[2] = __int_as_float(__byte_perm(z2, 0x4B000000u, 0x7540)) - kBias;
+    d[1] = __int_as_float(__byte_perm(z2, 0x4B000000u, 0x7541)) - kBias;
+    d[0] = (float)((int)z2 >> 16);
 }
 
 // max over (b, k, re/im) of the exponent bound of |a_b[k]| 2^floor(k/2): one warp per box
@@ -119,6 +136,19 @@ struct TcLayout {
         total = off_misc + 16;
     }
 };
+
+// staging item -> (target, coefficient); for 16-box tiles a warp spans 8 targets x 4
+// coefficients (bank-conflict-free shared stores), otherwise targets run fastest
+template <int TPB>
+__device__ __forceinline__ void item_of(int it, int &ti, int &kk) {
+    if constexpr (TPB == 16) {
+        ti = (it & 7) | (((it >> 3) / TC_KCC) << 3);
+        kk = (it >> 3) % TC_KCC;
+    } else {
+        ti = it % TPB;
+        kk = it / TPB;
+    }
+}
 
 template <int ND>
 __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
@@ -195,7 +225,24 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
     const uint32_t tmem = misc[0];
     const int nsteps = (int)misc[1] * a.nch;
     const uint32_t idesc = tc::idesc_bf16_f32(TC_M, a.npad);
-    const uint32_t a_base = tc::smem_u32(Abuf), b_base = tc::smem_u32(Bbuf);
+    const uint64_t adesc0 = tc::make_desc_kmajor(tc::smem_u32(Abuf), 128, (TC_KC / 8) * 128);
+    const uint64_t bdesc0 = tc::make_desc_kmajor(tc::smem_u32(Bbuf), 128, (TC_KC / 8) * 128);
+    // one staging item per thread and step when TPB x 24 == TC_T: its sources for the next
+    // step are prefetched into registers
+    constexpr bool kPrefetch = TPB * TC_KCC == TC_T;
+    double2 mpre[ND];
+    if constexpr (kPrefetch) {
+        int ti, kk;
+        item_of<TPB>(tid, ti, kk);
+        if (nsteps > 0) {
+            const int k0 = kk;  // step 0: first K chunk of the first class
+            const int src0 = (ti < nt && k0 < a.P) ? vsrc[ti * TC_NCLS + clist[0]] : -1;
+            if (src0 >= 0) {
+#pragma unroll
+                for (int b = 0; b < ND; ++b) mpre[b] = __ldg(&a.mp[((size_t)src0 * ND + b) * a.P + k0]);
+            }
+        }
+    }
     uint32_t inited = 0;               // accumulators written at least once (thread 0)
     int bpend[2] = {-1, -1};           // parity of an operator copy not yet waited for (thread 0)
 
@@ -211,14 +258,34 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
                          reinterpret_cast<const unsigned char *>(a.bplanes) + ((size_t)c * a.nch + h) * lay.bstep,
                          (uint32_t)lay.bstep, &mbar[2 + u]);
         }
-        // stage A: item = (coefficient kk, target ti); rows (2d + part) * TPB + ti
+        // stage A: item = (coefficient kk, target ti); rows (2d + part) * TPB + ti.  With
+        // TPB = 16 a warp covers 8 targets x 4 coefficients, so its 32 stores of a plane
+        // hit 32 different banks.
         unsigned char *Au = Abuf + (size_t)u * TC_NPL * TC_A_PLANE;
         const int *Sc = a.S + c * ND * ND;
         for (int it = tid; it < TPB * TC_KCC; it += TC_T) {
-            const int ti = it % TPB, kk = it / TPB;
+            int ti, kk;
+            item_of<TPB>(it, ti, kk);
             const int k = h * TC_KCC + kk;
             const int src = (ti < nt && k < a.P) ? vsrc[ti * TC_NCLS + c] : -1;
             const uint32_t colb = (uint32_t)((kk >> 2) * 128 + (kk & 3) * 4);  // byte offset of column 2kk in a row
+            double2 m[ND];
+            if constexpr (kPrefetch) {
+#pragma unroll
+                for (int b = 0; b < ND; ++b) m[b] = mpre[b];
+                // the next step's sources load while this step converts
+                if (s + 1 < nsteps) {
+                    const int c1 = clist[(s + 1) / a.nch], k1 = ((s + 1) % a.nch) * TC_KCC + kk;
+                    const int src1 = (ti < nt && k1 < a.P) ? vsrc[ti * TC_NCLS + c1] : -1;
+                    if (src1 >= 0) {
+#pragma unroll
+                        for (int b = 0; b < ND; ++b) mpre[b] = __ldg(&a.mp[((size_t)src1 * ND + b) * a.P + k1]);
+                    }
+                }
+            } else if (src >= 0) {
+#pragma unroll
+                for (int b = 0; b < ND; ++b) m[b] = __ldg(&a.mp[((size_t)src * ND + b) * a.P + k]);
+            }
             if (src < 0) {
                 for (int g2 = 0; g2 < 2 * ND; ++g2) {
                     const int row = g2 * TPB + ti;
@@ -235,9 +302,8 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
             long long xr[ND], xi[ND];
 #pragma unroll
             for (int b = 0; b < ND; ++b) {
-                const double2 m = a.mp[((size_t)src * ND + b) * a.P + k];
-                xr[b] = to_fixed(m.x, sh);
-                xi[b] = to_fixed(m.y, sh);
+                xr[b] = to_fixed(m[b].x, sh);
+                xi[b] = to_fixed(m[b].y, sh);
             }
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
@@ -258,17 +324,9 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
                 if (k == 0) lsum[ti * ND + d] += yr;
                 yr = (yr + (1ll << (TC_GB - 1))) >> TC_GB;
                 yi = (yi + (1ll << (TC_GB - 1))) >> TC_GB;
-                int dr[TC_NPL], di[TC_NPL];
-#pragma unroll
-                for (int i = TC_NPL - 1; i >= 1; --i) {
-                    const int qr = (int)((yr + 128) & 255) - 128, qi = (int)((yi + 128) & 255) - 128;
-                    dr[i] = qr;
-                    di[i] = qi;
-                    yr = (yr - qr) >> TC_DB;
-                    yi = (yi - qi) >> TC_DB;
-                }
-                dr[0] = (int)yr;
-                di[0] = (int)yi;
+                float dr[TC_NPL], di[TC_NPL];
+                digits_f(yr, dr);
+                digits_f(yi, di);
                 const int row_re = (2 * d) * TPB + ti, row_im = row_re + TPB;
                 const uint32_t off_re = (uint32_t)((row_re >> 3) * (TC_KC / 8) * 128 + (row_re & 7) * 16) + colb;
                 const uint32_t off_im = (uint32_t)((row_im >> 3) * (TC_KC / 8) * 128 + (row_im & 7) * 16) + colb;
@@ -288,18 +346,18 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
             } else {
                 bpend[u] = -1;
                 tc::fence_after_sync();
-                const uint32_t au = a_base + (uint32_t)(u * TC_NPL * TC_A_PLANE);
-                const uint32_t bu = b_base + (uint32_t)(u * lay.bstep);
+                // descriptor start addresses advance by (byte offset >> 4) in the low field
+                const uint64_t au = adesc0 + (uint64_t)((u * TC_NPL * TC_A_PLANE) >> 4);
+                const uint64_t bu = bdesc0 + (uint64_t)((u * lay.bstep) >> 4);
 #pragma unroll 1
                 for (int ks = 0; ks < TC_KC / 16; ++ks) {
 #pragma unroll
                     for (int i = 0; i < TC_NPL; ++i) {
-                        const uint64_t ad = tc::make_desc_kmajor(au + i * TC_A_PLANE + ks * 256, 128, (TC_KC / 8) * 128);
+                        const uint64_t ad = au + (uint64_t)((i * TC_A_PLANE + ks * 256) >> 4);
 #pragma unroll
                         for (int j = 0; j < TC_NPL - i; ++j) {
                             const int g = i + j;
-                            const uint64_t bd =
-                                tc::make_desc_kmajor(bu + j * lay.bplane + ks * 256, 128, (TC_KC / 8) * 128);
+                            const uint64_t bd = bu + (uint64_t)((j * lay.bplane + ks * 256) >> 4);
                             tc::mma_bf16(tmem + (uint32_t)(g * a.npad), ad, bd, idesc, (inited >> g) & 1);
                             inited |= 1u << g;
                         }
@@ -520,6 +578,38 @@ void m2l_tc_pass(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, cudaStre
     PHS_LAUNCH_CHECK();
     if (f.nd == 4) launch_tc<4>(f, t, mp, lc, b0, s);
     else launch_tc<9>(f, t, mp, lc, b0, s);
+}
+
+// classes present per tile of TPB consecutive boxes (the steps the pass will take)
+__global__ void tc_count_kernel(const int *v_off, const unsigned char *v_cls, int b0, int nbox, int tpb,
+                                unsigned long long *steps) {
+    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tb0 = b0 + tile * tpb;
+    if (tb0 >= nbox) return;
+    unsigned long long m = 0;
+    for (int b = tb0; b < min(tb0 + tpb, nbox); ++b)
+        for (int v = v_off[b]; v < v_off[b + 1]; ++v) m |= 1ull << v_cls[v];
+    atomicAdd(steps, (unsigned long long)__popcll(m));
+}
+
+int m2l_tc_mmas_per_step() { return (TC_KC / 16) * TC_NPL * (TC_NPL + 1) / 2; }
+
+void m2l_tc_count(Fmm &f, const Tree &t, cudaStream_t s) {
+    f.tc_steps = f.tc_tiles = 0;
+    if (!f.tc || t.depth < 2) return;
+    const int b0 = t.lvl_off[2];
+    const int tpb = f.nd == 4 ? TcLayout<4>::TPB : TcLayout<9>::TPB;
+    const int ntile = (t.nbox - b0 + tpb - 1) / tpb;
+    if (ntile <= 0) return;
+    DBuf<unsigned long long> cnt(1);
+    PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(unsigned long long), s));
+    tc_count_kernel<<<blocks_for(ntile, 128), 128, 0, s>>>(t.v_off.get(), t.v_cls.get(), b0, t.nbox, tpb, cnt.get());
+    PHS_LAUNCH_CHECK();
+    unsigned long long h = 0;
+    PHS_CUDA(cudaMemcpyAsync(&h, cnt.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    f.tc_steps = (int64_t)h * f.tc_nch;
+    f.tc_tiles = ntile;
 }
 
 void m2l_tc_check(Fmm &f, cudaStream_t s) {

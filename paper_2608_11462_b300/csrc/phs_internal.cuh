@@ -105,6 +105,7 @@ struct Tree {
     // (Morton order) to scratch [sym_slot[li], ...); leaf d gathers its share from the
     // slots of earlier leaves, starting at the offsets sym_gbase[sym_goff[d] .. sym_goff[d+1])
     bool sym_ok = false;             // every leaf fits one P2P pass (<= kP2PThreads points)
+    int64_t p2p_self_pairs = 0, p2p_upper_pairs = 0;  // pairs in own leaves / ranges after a leaf
     int max_leaf = 0;
     int64_t sym_total = 0;
     DBuf<int> sym_slot, sym_goff, sym_gbase;
@@ -163,6 +164,7 @@ struct Fmm {
     DBuf<int> tc_gexp;                   // log2 bound of the frame-change row growth [49][nd]
     DBuf<int> tc_mexp;                   // per-box exponent bound of the multipoles
     DBuf<int> tc_err;                    // device status (nonzero: a bounded wait expired)
+    int64_t tc_steps = 0, tc_tiles = 0;  // work of one pass (m2l_tc_count)
     DBuf<double> sym_scratch;            // column sums of the symmetric near field
 };
 // tensor_m2l: run the FP64 M2L of the log kernel on the tensor cores (m2l_tc.cu)
@@ -174,6 +176,9 @@ bool m2l_tc_supported(int nd, int P);
 void m2l_tc_setup(Fmm &f, const std::vector<long double> &ops_re, const std::vector<long double> &ops_im,
                   const std::vector<long double> &mix, cudaStream_t s);
 void m2l_tc_pass(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, cudaStream_t s);
+// steps and tiles of one pass over this tree (sets f.tc_steps, f.tc_tiles)
+void m2l_tc_count(Fmm &f, const Tree &t, cudaStream_t s);
+int m2l_tc_mmas_per_step();
 // throws PHS_ERR_TIMEOUT if a tensor-core wait expired since the last check (synchronises s)
 void m2l_tc_check(Fmm &f, cudaStream_t s);
 // distance-kernel far field (cheb.cu)

@@ -207,12 +207,13 @@ __global__ void nearlist_kernel(TreeView tv, int nbox, int *cnt, const int *off,
 // the points of a box disjoint from b, entirely before or after b in Morton order; each
 // leaf inside a range after b receives one gather offset.
 __global__ void sym_count(TreeView tv, const int *leaf_box, int nleaf, const int *near_off, const int2 *near_rng,
-                          const int *point_leaf, int *up_len, int *gcnt, int *maxleaf) {
+                          const int *point_leaf, int *up_len, int *gcnt, int *maxleaf, unsigned long long *pairs) {
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= nleaf) return;
     const int b = leaf_box[li];
     const int e = tv.end[b];
-    atomicMax(maxleaf, e - tv.start[b]);
+    const long long nt = e - tv.start[b];
+    atomicMax(maxleaf, (int)nt);
     int len = 0;
     for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
         const int2 rg = near_rng[r];
@@ -225,6 +226,8 @@ __global__ void sym_count(TreeView tv, const int *leaf_box, int nleaf, const int
         }
     }
     up_len[li] = len;
+    atomicAdd(&pairs[0], (unsigned long long)(nt * nt));
+    atomicAdd(&pairs[1], (unsigned long long)(nt * len));
 }
 __global__ void sym_fill(TreeView tv, const int *leaf_box, int nleaf, const int *near_off, const int2 *near_rng,
                          const int *point_leaf, const int *slot, const int *goff, int *gcur, int *gbase) {
@@ -431,12 +434,14 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     {
         const int nl = tree.nleaf;
         DBuf<int> up_len(nl), gcnt(nl), gcur(nl), mx(1);
+        DBuf<unsigned long long> prs(2);
+        PHS_CUDA(cudaMemsetAsync(prs.get(), 0, 2 * sizeof(unsigned long long), s));
         PHS_CUDA(cudaMemsetAsync(gcnt.get(), 0, nl * sizeof(int), s));
         PHS_CUDA(cudaMemsetAsync(gcur.get(), 0, nl * sizeof(int), s));
         PHS_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
         sym_count<<<blocks_for(nl, 128), 128, 0, s>>>(tv, tree.leaf_box.get(), nl, tree.near_off.get(),
                                                       tree.near_rng.get(), tree.point_leaf.get(), up_len.get(),
-                                                      gcnt.get(), mx.get());
+                                                      gcnt.get(), mx.get(), prs.get());
         PHS_LAUNCH_CHECK();
         tree.sym_slot.alloc(nl + 1);
         tree.sym_goff.alloc(nl + 1);
@@ -453,9 +458,13 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
         PHS_LAUNCH_CHECK();
         sym_sort<<<blocks_for(nl, 128), 128, 0, s>>>(tree.sym_goff.get(), nl, tree.sym_gbase.get());
         PHS_LAUNCH_CHECK();
+        unsigned long long hp[2];
         PHS_CUDA(cudaMemcpyAsync(&tree.max_leaf, mx.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        PHS_CUDA(cudaMemcpyAsync(hp, prs.get(), sizeof(hp), cudaMemcpyDeviceToHost, s));
         PHS_CUDA(cudaStreamSynchronize(s));
         tree.sym_ok = tree.max_leaf <= kP2PThreads;
+        tree.p2p_self_pairs = (int64_t)hp[0];
+        tree.p2p_upper_pairs = (int64_t)hp[1];
     }
 }
 
