@@ -41,7 +41,11 @@ constexpr int TC_GB = 6;                     // guard bits kept through the fram
 constexpr int TC_M = 128;                    // rows per tile (one TMEM lane each)
 constexpr int TC_KC = 48;                    // K columns per step
 constexpr int TC_KCC = TC_KC / 2;            // complex coefficients per step
-constexpr int TC_T = 384;                    // threads per CTA
+constexpr int TC_SW4 = 12, TC_SW9 = 11;      // staging warps (nd = 4, nd = 9); one more warp issues the MMAs
+template <int ND>
+__host__ __device__ constexpr int tc_staging_warps() { return ND == 4 ? TC_SW4 : TC_SW9; }
+template <int ND>
+__host__ __device__ constexpr int tc_threads() { return 32 * (tc_staging_warps<ND>() + 1); }
 constexpr int TC_A_PLANE = TC_M * TC_KC * 2; // bytes of one A digit plane
 constexpr int TC_NCLS = 49;
 constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
@@ -132,7 +136,7 @@ struct TcLayout {
         off_E = off_clist + TC_NCLS * 4;                 // [TPB][ND] row exponents, then [TPB] minimum
         off_lsum = (off_E + (size_t)TPB * (ND + 1) * 4 + 7) & ~(size_t)7;
         off_mbar = off_lsum + (size_t)TPB * ND * 8;
-        off_misc = off_mbar + 5 * 8;
+        off_misc = off_mbar + 7 * 8;
         total = off_misc + 16;
     }
 };
@@ -150,10 +154,17 @@ __device__ __forceinline__ void item_of(int it, int &ti, int &kk) {
     }
 }
 
+// Warp roles: warps 0 .. NSW-1 stage A (one mbarrier arrival per thread on full[u] when
+// buffer u is written), warp NSW (lane 0) copies B by TMA bulk copies and issues the MMAs,
+// committing to empty[u] when they have read buffer u.  No block-wide barrier inside the
+// loop; every wait is bounded and a timeout ends all roles through the abort flag.
 template <int ND>
-__global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
     using L = TcLayout<ND>;
     constexpr int TPB = L::TPB;
+    constexpr int NSW = tc_staging_warps<ND>();
+    constexpr int TC_T = tc_threads<ND>();
+    constexpr int NST = NSW * 32;  // staging threads
     extern __shared__ __align__(1024) unsigned char sm[];
     const L lay(a.npad);
     unsigned char *Abuf = sm;
@@ -163,7 +174,7 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
     int *clist = reinterpret_cast<int *>(sm + lay.off_clist);
     int *Et = reinterpret_cast<int *>(sm + lay.off_E);
     long long *lsum = reinterpret_cast<long long *>(sm + lay.off_lsum);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + lay.off_mbar);  // mma[2], bload[2], done
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + lay.off_mbar);  // empty[2], bfull[2], done, full[2]
     uint32_t *misc = reinterpret_cast<uint32_t *>(sm + lay.off_misc);  // tmem base, ncls, abort
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -181,6 +192,8 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
     }
     if (tid == 0) {
         for (int i = 0; i < 5; ++i) tc::mbar_init(&mbar[i], 1);
+        tc::mbar_init(&mbar[5], NST);
+        tc::mbar_init(&mbar[6], NST);
         tc::fence_mbar_init();
         misc[2] = 0;
     }
@@ -227,14 +240,14 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
     const uint32_t idesc = tc::idesc_bf16_f32(TC_M, a.npad);
     const uint64_t adesc0 = tc::make_desc_kmajor(tc::smem_u32(Abuf), 128, (TC_KC / 8) * 128);
     const uint64_t bdesc0 = tc::make_desc_kmajor(tc::smem_u32(Bbuf), 128, (TC_KC / 8) * 128);
-    // one staging item per thread and step when TPB x 24 == TC_T: its sources for the next
-    // step are prefetched into registers
-    constexpr bool kPrefetch = TPB * TC_KCC == TC_T;
+    // one staging item per staging thread and step when TPB x 24 == NST: its sources for
+    // the next step are prefetched into registers
+    constexpr bool kPrefetch = TPB * TC_KCC == NST;
     double2 mpre[ND];
     if constexpr (kPrefetch) {
         int ti, kk;
         item_of<TPB>(tid, ti, kk);
-        if (nsteps > 0) {
+        if (nsteps > 0 && tid < NST) {
             const int k0 = kk;  // step 0: first K chunk of the first class
             const int src0 = (ti < nt && k0 < a.P) ? vsrc[ti * TC_NCLS + clist[0]] : -1;
             if (src0 >= 0) {
@@ -243,127 +256,149 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
             }
         }
     }
-    uint32_t inited = 0;               // accumulators written at least once (thread 0)
-    int bpend[2] = {-1, -1};           // parity of an operator copy not yet waited for (thread 0)
+    uint32_t inited = 0;     // accumulators written at least once (issuer)
+    int bpend[2] = {-1, -1};  // parity of an operator copy not yet waited for (issuer)
+    const bool issuer = warp == NSW && lane == 0;
+    auto copy_b = [&](int s2) {
+        const int u2 = s2 & 1;
+        const int c2 = clist[s2 / a.nch], h2 = s2 % a.nch;
+        bpend[u2] = (s2 >> 1) & 1;
+        tc::mbar_arrive_expect_tx(&mbar[2 + u2], (uint32_t)lay.bstep);
+        tc::bulk_g2s(Bbuf + (size_t)u2 * lay.bstep,
+                     reinterpret_cast<const unsigned char *>(a.bplanes) + ((size_t)c2 * a.nch + h2) * lay.bstep,
+                     (uint32_t)lay.bstep, &mbar[2 + u2]);
+    };
 
     // ---- main loop: one step = (class, K chunk)
-    for (int s = 0; s < nsteps; ++s) {
-        const int u = s & 1;
-        const int c = clist[s / a.nch], h = s % a.nch;
-        if (s >= 2 && !tc::mbar_wait(&mbar[u], (uint32_t)(((s >> 1) - 1) & 1), TC_TIMEOUT_NS)) misc[2] = 1;
-        if (tid == 0 && !misc[2]) {
-            bpend[u] = (s >> 1) & 1;
-            tc::mbar_arrive_expect_tx(&mbar[2 + u], (uint32_t)lay.bstep);
-            tc::bulk_g2s(Bbuf + (size_t)u * lay.bstep,
-                         reinterpret_cast<const unsigned char *>(a.bplanes) + ((size_t)c * a.nch + h) * lay.bstep,
-                         (uint32_t)lay.bstep, &mbar[2 + u]);
-        }
-        // stage A: item = (coefficient kk, target ti); rows (2d + part) * TPB + ti.  With
-        // TPB = 16 a warp covers 8 targets x 4 coefficients, so its 32 stores of a plane
-        // hit 32 different banks.
-        unsigned char *Au = Abuf + (size_t)u * TC_NPL * TC_A_PLANE;
-        const int *Sc = a.S + c * ND * ND;
-        for (int it = tid; it < TPB * TC_KCC; it += TC_T) {
-            int ti, kk;
-            item_of<TPB>(it, ti, kk);
-            const int k = h * TC_KCC + kk;
-            const int src = (ti < nt && k < a.P) ? vsrc[ti * TC_NCLS + c] : -1;
-            const uint32_t colb = (uint32_t)((kk >> 2) * 128 + (kk & 3) * 4);  // byte offset of column 2kk in a row
-            double2 m[ND];
-            if constexpr (kPrefetch) {
-#pragma unroll
-                for (int b = 0; b < ND; ++b) m[b] = mpre[b];
-                // the next step's sources load while this step converts
-                if (s + 1 < nsteps) {
-                    const int c1 = clist[(s + 1) / a.nch], k1 = ((s + 1) % a.nch) * TC_KCC + kk;
-                    const int src1 = (ti < nt && k1 < a.P) ? vsrc[ti * TC_NCLS + c1] : -1;
-                    if (src1 >= 0) {
-#pragma unroll
-                        for (int b = 0; b < ND; ++b) mpre[b] = __ldg(&a.mp[((size_t)src1 * ND + b) * a.P + k1]);
-                    }
-                }
-            } else if (src >= 0) {
-#pragma unroll
-                for (int b = 0; b < ND; ++b) m[b] = __ldg(&a.mp[((size_t)src * ND + b) * a.P + k]);
-            }
-            if (src < 0) {
-                for (int g2 = 0; g2 < 2 * ND; ++g2) {
-                    const int row = g2 * TPB + ti;
-                    const uint32_t off = (uint32_t)((row >> 3) * (TC_KC / 8) * 128 + (row & 7) * 16) + colb;
-#pragma unroll
-                    for (int i = 0; i < TC_NPL; ++i) *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off) = 0u;
-                }
-                continue;
-            }
-            // sources convert once at the finest row scale of the target; each row then
-            // shifts down to its own exponent (|y| < 2^62 before the shift)
-            const int emin = Et[TPB * ND + ti];
-            const int sh = TC_QB + TC_GB - emin + (k >> 1);
-            long long xr[ND], xi[ND];
-#pragma unroll
-            for (int b = 0; b < ND; ++b) {
-                xr[b] = to_fixed(m[b].x, sh);
-                xi[b] = to_fixed(m[b].y, sh);
-            }
-#pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                long long yr = 0, yi = 0;
-#pragma unroll
-                for (int b = 0; b < ND; ++b) {
-                    const int sv = Sc[d * ND + b];
-                    if (sv) {
-                        yr += (long long)sv * xr[b];
-                        yi += (long long)sv * xi[b];
-                    }
-                }
-                const int dsh = Et[ti * ND + d] - emin;
-                if (dsh > 0) {
-                    yr = (yr + (1ll << (dsh - 1))) >> dsh;
-                    yi = (yi + (1ll << (dsh - 1))) >> dsh;
-                }
-                if (k == 0) lsum[ti * ND + d] += yr;
-                yr = (yr + (1ll << (TC_GB - 1))) >> TC_GB;
-                yi = (yi + (1ll << (TC_GB - 1))) >> TC_GB;
-                float dr[TC_NPL], di[TC_NPL];
-                digits_f(yr, dr);
-                digits_f(yi, di);
-                const int row_re = (2 * d) * TPB + ti, row_im = row_re + TPB;
-                const uint32_t off_re = (uint32_t)((row_re >> 3) * (TC_KC / 8) * 128 + (row_re & 7) * 16) + colb;
-                const uint32_t off_im = (uint32_t)((row_im >> 3) * (TC_KC / 8) * 128 + (row_im & 7) * 16) + colb;
-#pragma unroll
-                for (int i = 0; i < TC_NPL; ++i) {
-                    *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off_re) = pack_bf16(dr[i], -di[i]);
-                    *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off_im) = pack_bf16(di[i], dr[i]);
-                }
-            }
-        }
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (misc[2]) break;
-        if (tid == 0) {
-            if (!tc::mbar_wait(&mbar[2 + u], (uint32_t)((s >> 1) & 1), TC_TIMEOUT_NS)) {
+    if (warp < NSW) {
+        for (int s = 0; s < nsteps; ++s) {
+            const int u = s & 1;
+            const int c = clist[s / a.nch], h = s % a.nch;
+            if (misc[2]) break;
+            if (s >= 2 && !tc::mbar_wait(&mbar[u], (uint32_t)(((s >> 1) - 1) & 1), TC_TIMEOUT_NS)) {
                 misc[2] = 1;
-            } else {
-                bpend[u] = -1;
-                tc::fence_after_sync();
-                // descriptor start addresses advance by (byte offset >> 4) in the low field
-                const uint64_t au = adesc0 + (uint64_t)((u * TC_NPL * TC_A_PLANE) >> 4);
-                const uint64_t bu = bdesc0 + (uint64_t)((u * lay.bstep) >> 4);
-#pragma unroll 1
-                for (int ks = 0; ks < TC_KC / 16; ++ks) {
-#pragma unroll
-                    for (int i = 0; i < TC_NPL; ++i) {
-                        const uint64_t ad = au + (uint64_t)((i * TC_A_PLANE + ks * 256) >> 4);
-#pragma unroll
-                        for (int j = 0; j < TC_NPL - i; ++j) {
-                            const int g = i + j;
-                            const uint64_t bd = bu + (uint64_t)((j * lay.bplane + ks * 256) >> 4);
-                            tc::mma_bf16(tmem + (uint32_t)(g * a.npad), ad, bd, idesc, (inited >> g) & 1);
-                            inited |= 1u << g;
+                break;
+            }
+            // stage A: item = (coefficient kk, target ti); rows (2d + part) * TPB + ti.  With
+            // TPB = 16 a warp covers 8 targets x 4 coefficients, so its 32 stores of a plane
+            // hit 32 different banks.
+            unsigned char *Au = Abuf + (size_t)u * TC_NPL * TC_A_PLANE;
+            const int *Sc = a.S + c * ND * ND;
+            for (int it = tid; it < TPB * TC_KCC; it += NST) {
+                int ti, kk;
+                item_of<TPB>(it, ti, kk);
+                const int k = h * TC_KCC + kk;
+                const int src = (ti < nt && k < a.P) ? vsrc[ti * TC_NCLS + c] : -1;
+                const uint32_t colb = (uint32_t)((kk >> 2) * 128 + (kk & 3) * 4);  // byte offset of column 2kk in a row
+                double2 m[ND];
+                if constexpr (kPrefetch) {
+    #pragma unroll
+                    for (int b = 0; b < ND; ++b) m[b] = mpre[b];
+                    // the next step's sources load while this step converts
+                    if (s + 1 < nsteps) {
+                        const int c1 = clist[(s + 1) / a.nch], k1 = ((s + 1) % a.nch) * TC_KCC + kk;
+                        const int src1 = (ti < nt && k1 < a.P) ? vsrc[ti * TC_NCLS + c1] : -1;
+                        if (src1 >= 0) {
+    #pragma unroll
+                            for (int b = 0; b < ND; ++b) mpre[b] = __ldg(&a.mp[((size_t)src1 * ND + b) * a.P + k1]);
                         }
                     }
+                } else if (src >= 0) {
+    #pragma unroll
+                    for (int b = 0; b < ND; ++b) m[b] = __ldg(&a.mp[((size_t)src * ND + b) * a.P + k]);
                 }
-                tc::mma_commit(&mbar[u]);
+                if (src < 0) {
+                    for (int g2 = 0; g2 < 2 * ND; ++g2) {
+                        const int row = g2 * TPB + ti;
+                        const uint32_t off = (uint32_t)((row >> 3) * (TC_KC / 8) * 128 + (row & 7) * 16) + colb;
+    #pragma unroll
+                        for (int i = 0; i < TC_NPL; ++i) *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off) = 0u;
+                    }
+                    continue;
+                }
+                // sources convert once at the finest row scale of the target; each row then
+                // shifts down to its own exponent (|y| < 2^62 before the shift)
+                const int emin = Et[TPB * ND + ti];
+                const int sh = TC_QB + TC_GB - emin + (k >> 1);
+                long long xr[ND], xi[ND];
+    #pragma unroll
+                for (int b = 0; b < ND; ++b) {
+                    xr[b] = to_fixed(m[b].x, sh);
+                    xi[b] = to_fixed(m[b].y, sh);
+                }
+    #pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    long long yr = 0, yi = 0;
+    #pragma unroll
+                    for (int b = 0; b < ND; ++b) {
+                        const int sv = Sc[d * ND + b];
+                        if (sv) {
+                            yr += (long long)sv * xr[b];
+                            yi += (long long)sv * xi[b];
+                        }
+                    }
+                    const int dsh = Et[ti * ND + d] - emin;
+                    if (dsh > 0) {
+                        yr = (yr + (1ll << (dsh - 1))) >> dsh;
+                        yi = (yi + (1ll << (dsh - 1))) >> dsh;
+                    }
+                    if (k == 0) lsum[ti * ND + d] += yr;
+                    yr = (yr + (1ll << (TC_GB - 1))) >> TC_GB;
+                    yi = (yi + (1ll << (TC_GB - 1))) >> TC_GB;
+                    float dr[TC_NPL], di[TC_NPL];
+                    digits_f(yr, dr);
+                    digits_f(yi, di);
+                    const int row_re = (2 * d) * TPB + ti, row_im = row_re + TPB;
+                    const uint32_t off_re = (uint32_t)((row_re >> 3) * (TC_KC / 8) * 128 + (row_re & 7) * 16) + colb;
+                    const uint32_t off_im = (uint32_t)((row_im >> 3) * (TC_KC / 8) * 128 + (row_im & 7) * 16) + colb;
+    #pragma unroll
+                    for (int i = 0; i < TC_NPL; ++i) {
+                        *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off_re) = pack_bf16(dr[i], -di[i]);
+                        *reinterpret_cast<uint32_t *>(Au + i * TC_A_PLANE + off_im) = pack_bf16(di[i], dr[i]);
+                    }
+                }
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&mbar[5 + u]);
+        }
+    } else if (issuer && nsteps > 0) {
+        copy_b(0);
+        if (nsteps > 1) copy_b(1);
+        for (int s = 0; s < nsteps; ++s) {
+            const int u = s & 1;
+            if (misc[2]) break;
+            if (!tc::mbar_wait(&mbar[5 + u], (uint32_t)((s >> 1) & 1), TC_TIMEOUT_NS) ||
+                !tc::mbar_wait(&mbar[2 + u], (uint32_t)((s >> 1) & 1), TC_TIMEOUT_NS)) {
+                misc[2] = 1;
+                break;
+            }
+            bpend[u] = -1;
+            tc::fence_after_sync();
+            // descriptor start addresses advance by (byte offset >> 4) in the low field
+            const uint64_t au = adesc0 + (uint64_t)((u * TC_NPL * TC_A_PLANE) >> 4);
+            const uint64_t bu = bdesc0 + (uint64_t)((u * lay.bstep) >> 4);
+#pragma unroll 1
+            for (int ks = 0; ks < TC_KC / 16; ++ks) {
+#pragma unroll
+                for (int i = 0; i < TC_NPL; ++i) {
+                    const uint64_t ad = au + (uint64_t)((i * TC_A_PLANE + ks * 256) >> 4);
+#pragma unroll
+                    for (int j = 0; j < TC_NPL - i; ++j) {
+                        const int g = i + j;
+                        const uint64_t bd = bu + (uint64_t)((j * lay.bplane + ks * 256) >> 4);
+                        tc::mma_bf16(tmem + (uint32_t)(g * a.npad), ad, bd, idesc, (inited >> g) & 1);
+                        inited |= 1u << g;
+                    }
+                }
+            }
+            tc::mma_commit(&mbar[u]);
+            // the operator of step s + 1 goes into the buffer step s - 1 read
+            if (s >= 1 && s + 1 < nsteps) {
+                if (!tc::mbar_wait(&mbar[u ^ 1], (uint32_t)(((s - 1) >> 1) & 1), TC_TIMEOUT_NS)) {
+                    misc[2] = 1;
+                    break;
+                }
+                copy_b(s + 1);
             }
         }
     }
@@ -371,19 +406,22 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
     const bool aborted = misc[2] != 0;
     bool ok = !aborted;
     if (nsteps > 0) {
-        if (tid == 0) tc::mma_commit(&mbar[4]);
+        if (issuer) tc::mma_commit(&mbar[4]);
         ok = tc::mbar_wait(&mbar[4], 0, TC_TIMEOUT_NS) && ok;
     }
-    if (tid == 0) {  // operator copies still in flight after an abort land before the CTA exits
+    if (issuer) {  // operator copies still in flight after an abort land before the CTA exits
         for (int u = 0; u < 2; ++u)
             if (bpend[u] >= 0 && !tc::mbar_wait(&mbar[2 + u], (uint32_t)bpend[u], TC_TIMEOUT_NS)) ok = false;
     }
     ok = __all_sync(0xffffffffu, ok);
     if (!ok && lane == 0) atomicExch(a.err, 1);
+    __syncthreads();
+    ok = !misc[2] && ok;
     tc::fence_after_sync();
 
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, 16-column chunks w / 4, +3, ...
-    if (ok) {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, 16-column chunks w / 4, w / 4 + WQ, ...
+    constexpr int WQ = (TC_T / 32) / 4;  // epilogue warps per TMEM lane quadrant
+    if (ok && warp < 4 * WQ) {
         const int q = warp & 3, cg = warp >> 2;
         const int r = 32 * q + lane;
         const int grp = r / TPB, ti = r - grp * TPB;
@@ -401,7 +439,7 @@ __global__ void __launch_bounds__(TC_T, 1) m2l_tc_kernel(TcArgs a) {
             l0 = ldexp((double)lsum[ti * ND + d], E - TC_QB - TC_GB);
             dst = a.lc + ((size_t)b * ND + d) * a.P;
         }
-        for (int chk = cg; chk < a.npad / 16; chk += 3) {
+        for (int chk = cg; chk < a.npad / 16; chk += WQ) {
             uint32_t v[TC_NPL][16];
             if (nsteps > 0) {
 #pragma unroll
@@ -564,7 +602,7 @@ static void launch_tc(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, int
     a.err = f.tc_err.get();
     const int nb = t.nbox - b0;
     const unsigned grid = (unsigned)((nb + TcLayout<ND>::TPB - 1) / TcLayout<ND>::TPB);
-    m2l_tc_kernel<ND><<<grid, TC_T, lay.total, s>>>(a);
+    m2l_tc_kernel<ND><<<grid, tc_threads<ND>(), lay.total, s>>>(a);
     PHS_LAUNCH_CHECK();
 }
 
