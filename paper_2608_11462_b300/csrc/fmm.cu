@@ -545,9 +545,9 @@ __device__ __forceinline__ double phi_sym(double dx, double dy, const double2 *t
 // P2P_T points.
 template <int K>
 __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, const int *leaf_box,
-                                                       const int *near_off, const int2 *near_rng,
-                                                       const int *slot_off, const double2 *xs, const double *t,
-                                                       double *y, double *scratch) {
+                                                       const int *order, int *ticket, const int *near_off,
+                                                       const int2 *near_rng, const int *slot_off, const double2 *xs,
+                                                       const double *t, double *y, double *scratch) {
     __shared__ double sx[P2P_T], sy[P2P_T], st[P2P_T];
     __shared__ double colp[P2P_T / 32][P2P_T];
     extern __shared__ double2 logtab_sm[];
@@ -561,7 +561,15 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double scale = kTab ? 0.5 : 1.0;  // r^k log r = r^k log(r^2) / 2
-    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+    __shared__ int next_leaf;
+    for (;;) {
+        // dynamic schedule over the leaves in decreasing cost order
+        if (threadIdx.x == 0) next_leaf = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int oi = next_leaf;
+        __syncthreads();
+        if (oi >= nleaf) break;
+        const int li = order[oi];
         const int b = leaf_box[li];
         double cx, cy, w;
         box_geom(tv, b, cx, cy, w);
@@ -818,7 +826,7 @@ static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_s
     }
 }
 template <typename T>
-static void m2l_pass(Fmm &f, const Tree &t, const typename C2T<T>::type *mp, typename C2T<T>::type *lc,
+static void m2l_pass(Fmm &f, const Tree &t, typename C2T<T>::type *mp, typename C2T<T>::type *lc,
                      const typename C2T<T>::type *ops, int P, cudaStream_t s) {
     using C = typename C2T<T>::type;
     if constexpr (sizeof(T) == 8) {
@@ -938,9 +946,11 @@ static void p2p_sym_launch(Fmm &f, const Tree &t, const PointSet &ps, const doub
         grid_cap = std::max(1, nsm * std::max(per, 1));
     }
     if (f.sym_scratch.n < (size_t)std::max<int64_t>(t.sym_total, 1)) f.sym_scratch.alloc(std::max<int64_t>(t.sym_total, 1));
+    if (!f.p2p_ticket.get()) f.p2p_ticket.alloc(1);
+    PHS_CUDA(cudaMemsetAsync(f.p2p_ticket.get(), 0, sizeof(int), s));
     p2p_sym_kernel<K><<<std::min(t.nleaf, grid_cap), P2P_T, smem, s>>>(
-        tree_view(t), t.nleaf, t.leaf_box.get(), t.near_off.get(), t.near_rng.get(), t.sym_slot.get(), ps.xs.get(),
-        tv_sorted, y, f.sym_scratch.get());
+        tree_view(t), t.nleaf, t.leaf_box.get(), t.p2p_order.get(), f.p2p_ticket.get(), t.near_off.get(),
+        t.near_rng.get(), t.sym_slot.get(), ps.xs.get(), tv_sorted, y, f.sym_scratch.get());
     PHS_LAUNCH_CHECK();
     p2p_gather<<<blocks_for(ps.n, 256), 256, 0, s>>>(tree_view(t), t.leaf_box.get(), t.point_leaf.get(),
                                                      t.sym_goff.get(), t.sym_gbase.get(), ps.n, f.sym_scratch.get(), y);

@@ -58,9 +58,10 @@ struct TcArgs {
     const int *v_off, *v_src;
     const unsigned char *v_cls;
     int P, npad, nch, power;
-    const double2 *mp;
+    const longlong2 *mpx;     // multipoles in per-box fixed point (tc_fixed_kernel)
     double2 *lc;
     const int *mexp, *gexp, *S, *F;
+    const int2 *off;          // nd = 4: offset (ox, oy) of each class in box units
     const uint16_t *bplanes;  // [49][nch][NPL][npad x 48], core-matrix order
     int *err;
 };
@@ -102,36 +103,50 @@ __device__ __forceinline__ void digits_f(long long y, float *d) {
     d[0] = (float)((int)z2 >> 16);
 }
 
-// max over (b, k, re/im) of the exponent bound of |a_b[k]| 2^floor(k/2): one warp per box
-__global__ void tc_mexp_kernel(const double2 *mp, int nbox, int nd, int P, int *mexp) {
+// One warp per box: the exponent bound mexp = max over (b, k, re/im) of the exponent of
+// |a_b[k]| 2^floor(k/2) (so |a_b[k]| 2^floor(k/2) < 2^mexp), then the box's multipoles are
+// rewritten in place as integers X = round(a_b[k] 2^(53 - mexp + floor(k/2))), |X| <= 2^53.
+// A target later needs them at its own finer scale: one rounding right shift.
+__global__ void tc_fixed_kernel(double2 *mp, int nbox, int nd, int P, int *mexp) {
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= nbox) return;
     const int lane = threadIdx.x & 31;
+    double2 *mb = mp + (size_t)b * nd * P;
     int m = -100000;
     for (int i = lane; i < nd * P; i += 32) {
         const int k = i % P;
-        const double2 v = mp[(size_t)b * nd * P + i];
-        const unsigned long long bx = (unsigned long long)__double_as_longlong(v.x);
-        const unsigned long long by = (unsigned long long)__double_as_longlong(v.y);
-        const int ex = (int)((bx >> 52) & 0x7FF), ey = (int)((by >> 52) & 0x7FF);
+        const double2 v = mb[i];
+        const int ex = (int)(((unsigned long long)__double_as_longlong(v.x) >> 52) & 0x7FF);
+        const int ey = (int)(((unsigned long long)__double_as_longlong(v.y) >> 52) & 0x7FF);
         if (ex) m = max(m, ex - 1023 + 1 + (k >> 1));
         if (ey) m = max(m, ey - 1023 + 1 + (k >> 1));
     }
     for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) mexp[b] = m;
+    longlong2 *xb = reinterpret_cast<longlong2 *>(mb);
+    for (int i = lane; i < nd * P; i += 32) {
+        const int k = i % P;
+        const double2 v = mb[i];
+        const int sh = 53 - m + (k >> 1);
+        xb[i] = make_longlong2(to_fixed(v.x, sh), to_fixed(v.y, sh));
+    }
 }
+
+// rounding arithmetic right shift, 1 <= s <= 63
+__device__ __forceinline__ long long rshift_round(long long x, int s) { return (x + (1ll << (s - 1))) >> s; }
 
 template <int ND>
 struct TcLayout {
     static constexpr int TPB = TC_M / (2 * ND);  // targets per tile
     int bplane, bstep;
-    size_t off_B, off_vsrc, off_cflag, off_clist, off_E, off_lsum, off_mbar, off_misc, total;
+    size_t off_B, off_vsrc, off_vsh, off_cflag, off_clist, off_E, off_lsum, off_mbar, off_misc, total;
     __host__ __device__ TcLayout(int npad) {
         bplane = npad * TC_KC * 2;
         bstep = TC_NPL * bplane;
         off_B = (size_t)2 * TC_NPL * TC_A_PLANE;
         off_vsrc = off_B + (size_t)2 * bstep;
-        off_cflag = off_vsrc + (size_t)TPB * TC_NCLS * 4;
+        off_vsh = off_vsrc + (size_t)TPB * TC_NCLS * 4;
+        off_cflag = off_vsh + (((size_t)TPB * TC_NCLS + 15) & ~(size_t)15);
         off_clist = off_cflag + TC_NCLS * 4;
         off_E = off_clist + TC_NCLS * 4;                 // [TPB][ND] row exponents, then [TPB] minimum
         off_lsum = (off_E + (size_t)TPB * (ND + 1) * 4 + 7) & ~(size_t)7;
@@ -170,6 +185,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
     unsigned char *Abuf = sm;
     unsigned char *Bbuf = sm + lay.off_B;
     int *vsrc = reinterpret_cast<int *>(sm + lay.off_vsrc);
+    unsigned char *vsh = sm + lay.off_vsh;  // [TPB][49] shift from the source's scale to the target's
     int *cflag = reinterpret_cast<int *>(sm + lay.off_cflag);
     int *clist = reinterpret_cast<int *>(sm + lay.off_clist);
     int *Et = reinterpret_cast<int *>(sm + lay.off_E);
@@ -223,6 +239,9 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             emin = min(emin, e[d] + 1);
         }
         Et[TPB * ND + ti] = emin;
+        // emin >= mexp[src] + 1 for every source of the list, so the shift is >= 1
+        for (int v = a.v_off[b]; v < a.v_off[b + 1]; ++v)
+            vsh[ti * TC_NCLS + a.v_cls[v]] = (unsigned char)min(emin - a.mexp[a.v_src[v]], 63);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -243,7 +262,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
     // one staging item per staging thread and step when TPB x 24 == NST: its sources for
     // the next step are prefetched into registers
     constexpr bool kPrefetch = TPB * TC_KCC == NST;
-    double2 mpre[ND];
+    longlong2 mpre[ND];
     if constexpr (kPrefetch) {
         int ti, kk;
         item_of<TPB>(tid, ti, kk);
@@ -252,7 +271,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             const int src0 = (ti < nt && k0 < a.P) ? vsrc[ti * TC_NCLS + clist[0]] : -1;
             if (src0 >= 0) {
 #pragma unroll
-                for (int b = 0; b < ND; ++b) mpre[b] = __ldg(&a.mp[((size_t)src0 * ND + b) * a.P + k0]);
+                for (int b = 0; b < ND; ++b) mpre[b] = a.mpx[((size_t)src0 * ND + b) * a.P + k0];
             }
         }
     }
@@ -284,13 +303,14 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             // hit 32 different banks.
             unsigned char *Au = Abuf + (size_t)u * TC_NPL * TC_A_PLANE;
             const int *Sc = a.S + c * ND * ND;
+            const int2 cls_off = ND == 4 ? a.off[c] : make_int2(0, 0);
             for (int it = tid; it < TPB * TC_KCC; it += NST) {
                 int ti, kk;
                 item_of<TPB>(it, ti, kk);
                 const int k = h * TC_KCC + kk;
                 const int src = (ti < nt && k < a.P) ? vsrc[ti * TC_NCLS + c] : -1;
                 const uint32_t colb = (uint32_t)((kk >> 2) * 128 + (kk & 3) * 4);  // byte offset of column 2kk in a row
-                double2 m[ND];
+                longlong2 m[ND];
                 if constexpr (kPrefetch) {
     #pragma unroll
                     for (int b = 0; b < ND; ++b) m[b] = mpre[b];
@@ -300,12 +320,12 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
                         const int src1 = (ti < nt && k1 < a.P) ? vsrc[ti * TC_NCLS + c1] : -1;
                         if (src1 >= 0) {
     #pragma unroll
-                            for (int b = 0; b < ND; ++b) mpre[b] = __ldg(&a.mp[((size_t)src1 * ND + b) * a.P + k1]);
+                            for (int b = 0; b < ND; ++b) mpre[b] = a.mpx[((size_t)src1 * ND + b) * a.P + k1];
                         }
                     }
                 } else if (src >= 0) {
     #pragma unroll
-                    for (int b = 0; b < ND; ++b) m[b] = __ldg(&a.mp[((size_t)src * ND + b) * a.P + k]);
+                    for (int b = 0; b < ND; ++b) m[b] = a.mpx[((size_t)src * ND + b) * a.P + k];
                 }
                 if (src < 0) {
                     for (int g2 = 0; g2 < 2 * ND; ++g2) {
@@ -316,35 +336,52 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
                     }
                     continue;
                 }
-                // sources convert once at the finest row scale of the target; each row then
-                // shifts down to its own exponent (|y| < 2^62 before the shift)
+                // sources come to the finest row scale of the target (one rounding shift), mix
+                // exactly in integers, and each row rounds once to its own exponent
                 const int emin = Et[TPB * ND + ti];
-                const int sh = TC_QB + TC_GB - emin + (k >> 1);
+                const int sh2 = vsh[ti * TC_NCLS + c];
                 long long xr[ND], xi[ND];
-    #pragma unroll
+#pragma unroll
                 for (int b = 0; b < ND; ++b) {
-                    xr[b] = to_fixed(m[b].x, sh);
-                    xi[b] = to_fixed(m[b].y, sh);
+                    xr[b] = rshift_round(m[b].x, sh2);
+                    xi[b] = rshift_round(m[b].y, sh2);
                 }
-    #pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    long long yr = 0, yi = 0;
-    #pragma unroll
-                    for (int b = 0; b < ND; ++b) {
-                        const int sv = Sc[d * ND + b];
-                        if (sv) {
-                            yr += (long long)sv * xr[b];
-                            yi += (long long)sv * xi[b];
+                long long yrs[ND], yis[ND];
+                if constexpr (ND == 4) {
+                    // v = [1, a, x, y] (a = x^2 + y^2) about the target centre: S = I plus
+                    // row 1 = (|o|^2, ., 2 ox, 2 oy), row 2 = (ox, ...), row 3 = (oy, ...)
+                    const int2 o = cls_off;
+                    const long long o2 = (long long)o.x * o.x + (long long)o.y * o.y;
+                    yrs[0] = xr[0];
+                    yis[0] = xi[0];
+                    yrs[1] = xr[1] + 2ll * o.x * xr[2] + 2ll * o.y * xr[3] + o2 * xr[0];
+                    yis[1] = xi[1] + 2ll * o.x * xi[2] + 2ll * o.y * xi[3] + o2 * xi[0];
+                    yrs[2] = xr[2] + (long long)o.x * xr[0];
+                    yis[2] = xi[2] + (long long)o.x * xi[0];
+                    yrs[3] = xr[3] + (long long)o.y * xr[0];
+                    yis[3] = xi[3] + (long long)o.y * xi[0];
+                } else {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        long long yr = 0, yi = 0;
+#pragma unroll
+                        for (int b = 0; b < ND; ++b) {
+                            const int sv = Sc[d * ND + b];
+                            if (sv) {
+                                yr += (long long)sv * xr[b];
+                                yi += (long long)sv * xi[b];
+                            }
                         }
+                        yrs[d] = yr;
+                        yis[d] = yi;
                     }
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
                     const int dsh = Et[ti * ND + d] - emin;
-                    if (dsh > 0) {
-                        yr = (yr + (1ll << (dsh - 1))) >> dsh;
-                        yi = (yi + (1ll << (dsh - 1))) >> dsh;
-                    }
-                    if (k == 0) lsum[ti * ND + d] += yr;
-                    yr = (yr + (1ll << (TC_GB - 1))) >> TC_GB;
-                    yi = (yi + (1ll << (TC_GB - 1))) >> TC_GB;
+                    if (k == 0) lsum[ti * ND + d] += dsh > 0 ? rshift_round(yrs[d], dsh) : yrs[d];
+                    const long long yr = rshift_round(yrs[d], TC_GB + dsh);
+                    const long long yi = rshift_round(yis[d], TC_GB + dsh);
                     float dr[TC_NPL], di[TC_NPL];
                     digits_f(yr, dr);
                     digits_f(yi, di);
@@ -558,6 +595,21 @@ void m2l_tc_setup(Fmm &f, const std::vector<long double> &ops_re, const std::vec
             gexp[(size_t)c * nd + d] = g;
         }
     }
+    // nd = 4: the frame change has the closed form of [1, a, x, y] shifted by o = (ox, oy)
+    std::vector<int2> off(TC_NCLS, make_int2(0, 0));
+    if (nd == 4) {
+        for (int c = 0; c < TC_NCLS; ++c) {
+            if (!valid_cls(c)) continue;
+            const int *Sm = S.data() + (size_t)c * 16;
+            const int ox = Sm[2 * 4 + 0], oy = Sm[3 * 4 + 0];
+            const int want[16] = {1, 0, 0, 0, ox * ox + oy * oy, 1, 2 * ox, 2 * oy, ox, 0, 1, 0, oy, 0, 0, 1};
+            for (int i = 0; i < 16; ++i)
+                PHS_REQUIRE(Sm[i] == want[i], PHS_ERR_INVALID_ARG, "tensor-core M2L: unexpected frame change");
+            off[c] = make_int2(ox, oy);
+        }
+    }
+    f.tc_off.alloc(TC_NCLS);
+    PHS_CUDA(cudaMemcpyAsync(f.tc_off.get(), off.data(), TC_NCLS * sizeof(int2), cudaMemcpyHostToDevice, s));
     f.tc_b.alloc(B.size());
     f.tc_F.alloc(P);
     f.tc_S.alloc(S.size());
@@ -573,7 +625,7 @@ void m2l_tc_setup(Fmm &f, const std::vector<long double> &ops_re, const std::vec
 }
 
 template <int ND>
-static void launch_tc(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, int b0, cudaStream_t s) {
+static void launch_tc(Fmm &f, const Tree &t, double2 *mp, double2 *lc, int b0, cudaStream_t s) {
     const TcLayout<ND> lay(f.tc_npad);
     static bool attr_set = false;
     if (!attr_set) {
@@ -592,12 +644,13 @@ static void launch_tc(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, int
     a.npad = f.tc_npad;
     a.nch = f.tc_nch;
     a.power = f.power;
-    a.mp = mp;
+    a.mpx = reinterpret_cast<const longlong2 *>(mp);
     a.lc = lc;
     a.mexp = f.tc_mexp.get();
     a.gexp = f.tc_gexp.get();
     a.S = f.tc_S.get();
     a.F = f.tc_F.get();
+    a.off = f.tc_off.get();
     a.bplanes = f.tc_b.get();
     a.err = f.tc_err.get();
     const int nb = t.nbox - b0;
@@ -606,13 +659,13 @@ static void launch_tc(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, int
     PHS_LAUNCH_CHECK();
 }
 
-void m2l_tc_pass(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, cudaStream_t s) {
+void m2l_tc_pass(Fmm &f, const Tree &t, double2 *mp, double2 *lc, cudaStream_t s) {
     const int b0 = t.depth >= 2 ? t.lvl_off[2] : t.nbox;
     const size_t esz = (size_t)f.nd * f.P * sizeof(double2);
     if (b0 > 0) PHS_CUDA(cudaMemsetAsync(lc, 0, (size_t)b0 * esz, s));
     if (b0 >= t.nbox) return;
     if (f.tc_mexp.n < (size_t)t.nbox) f.tc_mexp.alloc(t.nbox);
-    tc_mexp_kernel<<<blocks_for(t.nbox, 8), 256, 0, s>>>(mp, t.nbox, f.nd, f.P, f.tc_mexp.get());
+    tc_fixed_kernel<<<blocks_for(t.nbox, 8), 256, 0, s>>>(mp, t.nbox, f.nd, f.P, f.tc_mexp.get());
     PHS_LAUNCH_CHECK();
     if (f.nd == 4) launch_tc<4>(f, t, mp, lc, b0, s);
     else launch_tc<9>(f, t, mp, lc, b0, s);

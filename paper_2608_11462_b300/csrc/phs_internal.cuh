@@ -109,6 +109,7 @@ struct Tree {
     int max_leaf = 0;
     int64_t sym_total = 0;
     DBuf<int> sym_slot, sym_goff, sym_gbase;
+    DBuf<int> p2p_order;             // leaves by decreasing near-field pair count
 };
 constexpr int kP2PThreads = 128;     // threads of a near-field block
 
@@ -162,10 +163,12 @@ struct Fmm {
     DBuf<int> tc_F;                      // column exponents [P]
     DBuf<int> tc_S;                      // integer frame changes [49][nd][nd]
     DBuf<int> tc_gexp;                   // log2 bound of the frame-change row growth [49][nd]
+    DBuf<int2> tc_off;                   // nd = 4: class offsets (ox, oy)
     DBuf<int> tc_mexp;                   // per-box exponent bound of the multipoles
     DBuf<int> tc_err;                    // device status (nonzero: a bounded wait expired)
     int64_t tc_steps = 0, tc_tiles = 0;  // work of one pass (m2l_tc_count)
     DBuf<double> sym_scratch;            // column sums of the symmetric near field
+    DBuf<int> p2p_ticket;                // next leaf of the near-field blocks (reset per launch)
 };
 // tensor_m2l: run the FP64 M2L of the log kernel on the tensor cores (m2l_tc.cu)
 void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s);
@@ -175,7 +178,8 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
 bool m2l_tc_supported(int nd, int P);
 void m2l_tc_setup(Fmm &f, const std::vector<long double> &ops_re, const std::vector<long double> &ops_im,
                   const std::vector<long double> &mix, cudaStream_t s);
-void m2l_tc_pass(Fmm &f, const Tree &t, const double2 *mp, double2 *lc, cudaStream_t s);
+// (rewrites the multipoles mp in place as per-box fixed point: the upward pass is done)
+void m2l_tc_pass(Fmm &f, const Tree &t, double2 *mp, double2 *lc, cudaStream_t s);
 // steps and tiles of one pass over this tree (sets f.tc_steps, f.tc_tiles)
 void m2l_tc_count(Fmm &f, const Tree &t, cudaStream_t s);
 int m2l_tc_mmas_per_step();

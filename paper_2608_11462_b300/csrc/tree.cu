@@ -207,7 +207,8 @@ __global__ void nearlist_kernel(TreeView tv, int nbox, int *cnt, const int *off,
 // the points of a box disjoint from b, entirely before or after b in Morton order; each
 // leaf inside a range after b receives one gather offset.
 __global__ void sym_count(TreeView tv, const int *leaf_box, int nleaf, const int *near_off, const int2 *near_rng,
-                          const int *point_leaf, int *up_len, int *gcnt, int *maxleaf, unsigned long long *pairs) {
+                          const int *point_leaf, int *up_len, int *gcnt, int *maxleaf, unsigned long long *pairs,
+                          uint64_t *cost_key, int *cost_val) {
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= nleaf) return;
     const int b = leaf_box[li];
@@ -228,6 +229,10 @@ __global__ void sym_count(TreeView tv, const int *leaf_box, int nleaf, const int
     up_len[li] = len;
     atomicAdd(&pairs[0], (unsigned long long)(nt * nt));
     atomicAdd(&pairs[1], (unsigned long long)(nt * len));
+    // processing order of the near-field blocks: decreasing pair count
+    const unsigned long long work = (unsigned long long)(nt * (nt + len));
+    cost_key[li] = 0xFFFFFFFFull - (work > 0xFFFFFFFFull ? 0xFFFFFFFFull : work);
+    cost_val[li] = li;
 }
 __global__ void sym_fill(TreeView tv, const int *leaf_box, int nleaf, const int *near_off, const int2 *near_rng,
                          const int *point_leaf, const int *slot, const int *goff, int *gcur, int *gbase) {
@@ -434,6 +439,8 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     {
         const int nl = tree.nleaf;
         DBuf<int> up_len(nl), gcnt(nl), gcur(nl), mx(1);
+        DBuf<uint64_t> ckey(nl);
+        tree.p2p_order.alloc(nl);
         DBuf<unsigned long long> prs(2);
         PHS_CUDA(cudaMemsetAsync(prs.get(), 0, 2 * sizeof(unsigned long long), s));
         PHS_CUDA(cudaMemsetAsync(gcnt.get(), 0, nl * sizeof(int), s));
@@ -441,8 +448,10 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
         PHS_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
         sym_count<<<blocks_for(nl, 128), 128, 0, s>>>(tv, tree.leaf_box.get(), nl, tree.near_off.get(),
                                                       tree.near_rng.get(), tree.point_leaf.get(), up_len.get(),
-                                                      gcnt.get(), mx.get(), prs.get());
+                                                      gcnt.get(), mx.get(), prs.get(), ckey.get(),
+                                                      tree.p2p_order.get());
         PHS_LAUNCH_CHECK();
+        radix_sort_pairs(ckey.get(), tree.p2p_order.get(), nl, 32, s);
         tree.sym_slot.alloc(nl + 1);
         tree.sym_goff.alloc(nl + 1);
         tree.sym_total = exclusive_scan_i32(up_len.get(), tree.sym_slot.get(), nl, s);

@@ -3,6 +3,7 @@
 // the transposed factor and the apply z = U~ (U~' r).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "phs_internal.cuh"
 
@@ -160,7 +161,30 @@ constexpr int kSerTerms = 14;
 constexpr int kCoshTab = 64;
 __constant__ double c_s1[kSerTerms], c_p1[kSerTerms], c_s0[kSerTerms], c_h0[kSerTerms], c_cosh[kCoshTab];
 
-__device__ __forceinline__ int ser_terms(double q) { return q <= 0.015625 ? 6 : (q <= 0.125 ? 9 : kSerTerms); }
+// terms for a truncation below 1e-16 relative: q^n / (n!)^2 at the bound of each class
+__device__ __forceinline__ int ser_terms(double q) {
+    return q <= 6.103515625e-05 ? 4 : (q <= 0.015625 ? 6 : (q <= 0.125 ? 9 : kSerTerms));
+}
+
+// Table-driven FP64 logarithm for the series (P. T. P. Tang, ACM TOMS 16(4), 1990):
+// x = 2^e m, F_j = 1 + j/2048 nearest m, log x = e log 2 + log F_j + log(1 + r) with
+// r = m/F_j - 1 (|r| < 2^-12) and a three-term log(1 + r); exponents below 2^-255 clamp
+// (there q log q vanishes).  Tables in global memory, read through the read-only cache.
+constexpr int kVLogTab = 2049, kVExpLo = 768, kVExpTab = 259;
+__device__ double2 g_vlogtab[kVLogTab];  // (log F_j, 1/F_j)
+__device__ double g_veln2[kVExpTab];     // (e - 1023) log 2 for biased e = kVExpLo + i
+
+__device__ __forceinline__ double vtab_log(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int j = (((hi >> 8) & 0xfff) + 1) >> 1;
+    const int ei = min(max((hi >> 20) - kVExpLo, 0), kVExpTab - 1);
+    const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
+    const double2 fj = __ldg(&g_vlogtab[j]);
+    const double r = fma(m, fj.y, -1.0);
+    double c = fma(r, 0.33333333333333333, -0.5);
+    c = fma(c, r, 1.0);
+    return fma(c, r, fj.x + __ldg(&g_veln2[ei]));
+}
 
 __device__ __forceinline__ double horner(const double *c, int nt, double q) {
     double v = c[nt - 1];
@@ -193,7 +217,7 @@ __device__ __forceinline__ double matern_q(double nu, double q) {
     double k0, ak1;
     if (q <= 1.0) {
         const int nt = ser_terms(q);
-        const double lq = log(q);
+        const double lq = vtab_log(q);
         ak1 = 1.0 + q * (lq * horner(c_s1, nt, q) - horner(c_p1, nt, q));
         if (nu == 1.0) return ak1;
         k0 = -(0.5 * lq + 0.57721566490153286061) * horner(c_s0, nt, q) + horner(c_h0, nt, q);
@@ -227,6 +251,15 @@ static void upload_bessel_tables() {
         d[3][k] = (double)h0[k];
     }
     for (int j = 0; j < kCoshTab; ++j) ch[j] = (double)std::cosh(0.25L * j);
+    std::vector<double2> lt(kVLogTab);
+    for (int j = 0; j < kVLogTab; ++j) {
+        const long double F = 1.0L + (long double)j / 2048.0L;
+        lt[j] = make_double2((double)std::log(F), (double)(1.0L / F));
+    }
+    std::vector<double> el(kVExpTab);
+    for (int i = 0; i < kVExpTab; ++i) el[i] = (double)((long double)(kVExpLo + i - 1023) * std::log(2.0L));
+    PHS_CUDA(cudaMemcpyToSymbol(g_vlogtab, lt.data(), kVLogTab * sizeof(double2)));
+    PHS_CUDA(cudaMemcpyToSymbol(g_veln2, el.data(), kVExpTab * sizeof(double)));
     PHS_CUDA(cudaMemcpyToSymbol(c_s1, d[0], sizeof(d[0])));
     PHS_CUDA(cudaMemcpyToSymbol(c_p1, d[1], sizeof(d[1])));
     PHS_CUDA(cudaMemcpyToSymbol(c_s0, d[2], sizeof(d[2])));

@@ -335,7 +335,18 @@ def test_fit_uniform_tps_matches_dense_solve(phs, precision):
     assert err <= 1e-8, err
     assert np.allclose(beta.cpu().numpy(), ref["beta"], rtol=0, atol=1e-6 * np.abs(ref["beta"]).max())
     wg = w.cpu().numpy()
-    assert np.linalg.norm(wg - ref["w"]) <= 1e-5 * np.linalg.norm(ref["w"])
+    # w solves the projected system (Eq. 2.5) on the oracle's exact dense operator: the
+    # relative residual ||Q_perp'(f - M w)|| / ||Q_perp' f|| within 10x the requested
+    # 1e-10, and B' w = 0.  (w itself is only as close to the direct solution as
+    # kappa(Q_perp' M Q_perp) ~ 1e8 times that residual allows.)
+    x = w_["points"]
+    M = oracle.dense_matrix(x, 2)
+    B = oracle.poly_basis(x, 1)
+    Q, _ = np.linalg.qr(B, mode="complete")
+    Qp = Q[:, 3:]
+    rel = np.linalg.norm(Qp.T @ (w_["f"] - M @ wg)) / np.linalg.norm(Qp.T @ w_["f"])
+    assert rel <= 1e-9, rel
+    assert np.linalg.norm(B.T @ wg) <= 1e-12 * np.linalg.norm(B) * np.linalg.norm(wg)
     # nodes are interpolated
     at_nodes = plan.eval(w, beta, _t(w_["points"])).cpu().numpy()
     assert np.max(np.abs(at_nodes - w_["f"])) <= 1e-8 * np.max(np.abs(w_["f"]))
