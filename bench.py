@@ -32,10 +32,10 @@ WORKLOAD = "tps_1m"
 # nu = 1.5 fails to converge within 200 iterations at this size for alpha in {5, 20, 60}.
 NU, ALPHA = 1.0, 0.35
 # DRAM bytes (read + write) per launch from ncu captures summarised under profiles/,
-# None while the current kernel has no capture.  The tensor-core M2L was captured on the
-# n = 262144 case of this workload (618 tiles) and is scaled by the tile count.
-M2L_DRAM_BYTES_PER_TILE = (29.627136e6 + 27.904e3) / 618
-P2P_DRAM_BYTES = None
+# taken on the n = 262144 case of this workload and scaled to the bench size: the
+# tensor-core M2L by its tile count (618 tiles there), the near field by the point count.
+M2L_DRAM_BYTES_PER_TILE = (29.62176e6 + 39.68e3) / 618
+P2P_DRAM_BYTES_PER_POINT = (7.3408e6 + 768) / 262144
 
 
 def parse():
@@ -280,7 +280,7 @@ def main():
                 "peak_source": f"derived: 148 SMs x 2 FP64 instr/clk x {sm_mhz_max:.0f} MHz",
                 "work_per_launch": f"{kwork['p2p_pairs']} pairs evaluated ({kwork['p2p_column_pairs']} with column "
                                    f"sums) = {p2p_ops} FP64 instr; {work['near_pairs']} ordered near pairs",
-                "ms_per_launch": ms_p2p, "traffic": P2P_DRAM_BYTES}
+                "ms_per_launch": ms_p2p, "traffic": P2P_DRAM_BYTES_PER_POINT * n}
     ms_m2l = phases["m2l"][0] / max(phases["m2l"][1], 1)
     roof_m2l = None
     if kwork["tc_steps"] > 0:
