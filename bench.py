@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--n", type=int, default=None, help="override the point count (smaller parity runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--leaf-cap", type=int, default=64, help="quadtree leaf capacity")
     return ap.parse_args()
 
 
@@ -191,7 +192,7 @@ def main():
     import paper_2608_11462_b300 as phs
 
     L = phs.lib()
-    opts = phs.options(2, precision=args.precision, tol=1e-8, nu=NU, alpha=ALPHA, leaf_cap=64)
+    opts = phs.options(2, precision=args.precision, tol=1e-8, nu=NU, alpha=ALPHA, leaf_cap=args.leaf_cap)
     pts_d = torch.tensor(points, device=dev)
     f_d = torch.tensor(f, device=dev)
     tg_d = torch.tensor(targets, device=dev)
@@ -313,7 +314,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
         "fits_per_s": world / t_step,
         "config": {"workload": WORKLOAD, "n": n, "targets": m_t, "k": 2, "poly_degree": 1, "vecchia_m": 30,
-                   "nu": NU, "alpha_normalised": ALPHA, "ordering": "random", "leaf_cap": 64, "fmm_order": sizes[3],
+                   "nu": NU, "alpha_normalised": ALPHA, "ordering": "random", "leaf_cap": args.leaf_cap, "fmm_order": sizes[3],
                    "precision_mode": args.precision, "tol": 1e-8, "parallelism": f"replicas{world}",
                    "l2": "flushed (256 MB write) between timed steps"},
         "pcg": {"iters": info["iters"], "outer_iters": info["outer_iters"], "converged": info["converged"],

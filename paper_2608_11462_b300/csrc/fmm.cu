@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "geom.cuh"
@@ -404,6 +406,225 @@ __global__ void l2p_kernel(TreeView tv, const int *leaf_box, const double2 *xs, 
             sum += u[d] * (double)h.x;
         }
         y[j] += sum;
+    }
+}
+
+// ---------------------------------------------------------------- FP64 upward / downward passes
+// The same arithmetic as the templated kernels above, arranged for the FP64 pipe: every
+// thread of a block has work, dependent chains are short, and the children of a parent
+// are processed together (two block barriers instead of twelve).
+constexpr int UD_T = 256;
+
+// P2M: chunks of 64 points; four threads per point build the powers zeta^k, each a
+// quarter of k from its own starting power; then one thread per output (d, k) sums the
+// chunk.  a_0 = sum q, a_k = -sum q zeta^k / k (box-width scaled, fmm.cu header).
+__global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *leaf_box, const double2 *xs,
+                                                    const double *t, int power, int nd, int P, double2 *mp) {
+    extern __shared__ double2 p2m_sm[];
+    double2 *pw = p2m_sm;                                 // [64][P]
+    double *qs = reinterpret_cast<double *>(pw + 64 * P);  // [64][nd]
+    const int b = leaf_box[blockIdx.x];
+    double cx, cy, w;
+    box_geom(tv, b, cx, cy, w);
+    const double iw = 1.0 / w;
+    const int s = tv.start[b], e = tv.end[b];
+    const int nout = nd * P;
+    const int Q = (P + 3) / 4;
+    double2 acc[OUT_PER_T];
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) acc[i] = make_double2(0.0, 0.0);
+    for (int j0 = s; j0 < e; j0 += 64) {
+        const int jn = min(64, e - j0);
+        {
+            const int jp = threadIdx.x >> 2, q = threadIdx.x & 3;
+            if (jp < jn) {
+                const double2 xj = xs[j0 + jp];
+                const double2 z = make_double2((xj.x - cx) * iw, (xj.y - cy) * iw);
+                double2 zk = make_double2(1.0, 0.0), base = z;
+                for (int e2 = q * Q; e2 > 0; e2 >>= 1) {
+                    if (e2 & 1) zk = cmul(zk, base);
+                    base = cmul(base, base);
+                }
+                const int k1 = min(P, (q + 1) * Q);
+                for (int k = q * Q; k < k1; ++k) {
+                    pw[jp * P + k] = zk;
+                    zk = cmul(zk, z);
+                }
+                if (q == 0) {
+                    double v[kMaxNd];
+                    had_v(power, z.x, z.y, v);
+                    const double tj = t[j0 + jp];
+                    for (int d = 0; d < nd; ++d) qs[jp * nd + d] = v[d] * tj;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < OUT_PER_T; ++i) {
+            const int o = threadIdx.x + i * UD_T;
+            if (o < nout) {
+                const int d = o / P, k = o - d * P;
+                double2 a = acc[i];
+                for (int jj = 0; jj < jn; ++jj) {
+                    const double q = qs[jj * nd + d];
+                    const double2 z = pw[jj * P + k];
+                    a.x = fma(q, z.x, a.x);
+                    a.y = fma(q, z.y, a.y);
+                }
+                acc[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < OUT_PER_T; ++i) {
+        const int o = threadIdx.x + i * UD_T;
+        if (o < nout) {
+            const int d = o / P, k = o - d * P;
+            double2 a = acc[i];
+            if (k > 0) {
+                const double sc = -1.0 / k;
+                a.x *= sc;
+                a.y *= sc;
+            }
+            mp[((size_t)b * nd + d) * P + k] = a;
+        }
+    }
+}
+
+// M2M for the parents of one level: all children load and shift at once; each thread
+// takes row pairs (l, P-1-l) so the triangular shift is balanced; then the parent sums
+// the children through the frame changes Rv (mix slots 49 + quadrant).
+__global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd, int P, const double2 *ops,
+                                                    const double *mix, double2 *mp) {
+    extern __shared__ double2 m2m_sm[];
+    const int b = b0 + blockIdx.x;
+    const int nc = tv.nchild[b];
+    if (nc == 0) return;
+    const int nout = nd * P, c0 = tv.child[b];
+    double2 *ch = m2m_sm, *sh = m2m_sm + 4 * nout;
+    for (int i = threadIdx.x; i < nc * nout; i += UD_T) ch[i] = mp[(size_t)c0 * nout + i];
+    __syncthreads();
+    const int half = (P + 1) / 2;
+    for (int it = threadIdx.x; it < nc * nd * half; it += UD_T) {
+        const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
+        const double2 *A = ops + (size_t)(tv.key[c0 + c] & 3) * P * P;
+        const double2 *src = ch + c * nout + d * P;
+        for (int h = 0; h < 2; ++h) {
+            const int l = h == 0 ? p : P - 1 - p;
+            if (h == 1 && l == p) break;
+            const double2 *Ar = A + (size_t)l * P;
+            double ax = 0.0, ay = 0.0;
+            for (int k = 0; k <= l; ++k) {
+                const double2 a = Ar[k], m = src[k];
+                ax = fma(a.x, m.x, fma(-a.y, m.y, ax));
+                ay = fma(a.x, m.y, fma(a.y, m.x, ay));
+            }
+            sh[c * nout + d * P + l] = make_double2(ax, ay);
+        }
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += UD_T) {
+        const int d = o / P, l = o - d * P;
+        double ax = 0.0, ay = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            const double *Rv = mix + (size_t)(49 + (tv.key[c0 + c] & 3)) * nd * nd + d * nd;
+            for (int bb = 0; bb < nd; ++bb) {
+                const double r = Rv[bb];
+                if (r != 0.0) {
+                    const double2 v = sh[c * nout + bb * P + l];
+                    ax = fma(r, v.x, ax);
+                    ay = fma(r, v.y, ay);
+                }
+            }
+        }
+        mp[(size_t)b * nout + o] = make_double2(ax, ay);
+    }
+}
+
+// L2L for the parents of one level: the parent's local expansion loads once, shifts to
+// each child centre (rows m paired with P-1-m: sum over l >= m) and mixes through Ru
+// (mix slots 53 + quadrant) into the child's local expansion.
+__global__ void __launch_bounds__(UD_T) l2l64_kernel(TreeView tv, int b0, int nd, int P, const double2 *ops,
+                                                    const double *mix, double2 *lc) {
+    extern __shared__ double2 l2l_sm[];
+    const int b = b0 + blockIdx.x;
+    const int nc = tv.nchild[b];
+    if (nc == 0) return;
+    const int nout = nd * P, c0 = tv.child[b];
+    double2 *par = l2l_sm, *sh = l2l_sm + nout;
+    for (int i = threadIdx.x; i < nout; i += UD_T) par[i] = lc[(size_t)b * nout + i];
+    __syncthreads();
+    const int half = (P + 1) / 2;
+    for (int it = threadIdx.x; it < nc * nd * half; it += UD_T) {
+        const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
+        const double2 *A = ops + (size_t)(4 + (tv.key[c0 + c] & 3)) * P * P;
+        const double2 *src = par + d * P;
+        for (int h = 0; h < 2; ++h) {
+            const int m = h == 0 ? p : P - 1 - p;
+            if (h == 1 && m == p) break;
+            const double2 *Ar = A + (size_t)m * P;
+            double ax = 0.0, ay = 0.0;
+            for (int l = m; l < P; ++l) {
+                const double2 a = Ar[l], v = src[l];
+                ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
+                ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+            }
+            sh[c * nout + d * P + m] = make_double2(ax, ay);
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < nc * nout; it += UD_T) {
+        const int c = it / nout, o = it - c * nout, a_ = o / P, m = o - a_ * P;
+        const double *Ru = mix + (size_t)(53 + (tv.key[c0 + c] & 3)) * nd * nd;
+        double2 acc = lc[(size_t)(c0 + c) * nout + o];
+        for (int l = 0; l < nd; ++l) {
+            const double r = Ru[l * nd + a_];
+            if (r != 0.0) {
+                const double2 v = sh[c * nout + l * P + m];
+                acc.x = fma(r, v.x, acc.x);
+                acc.y = fma(r, v.y, acc.y);
+            }
+        }
+        lc[(size_t)(c0 + c) * nout + o] = acc;
+    }
+}
+
+// L2P + Hadamard combination: four threads per point, each on densities d = sub,
+// sub + 4, ... (Horner in FMAs), then a shuffle sum over the four
+__global__ void __launch_bounds__(UD_T) l2p64_kernel(TreeView tv, const int *leaf_box, const double2 *xs, int power,
+                                                    int nd, int P, const double2 *lc, double *y) {
+    extern __shared__ double2 l2p_sm[];
+    const int b = leaf_box[blockIdx.x];
+    const int nout = nd * P;
+    for (int i = threadIdx.x; i < nout; i += UD_T) l2p_sm[i] = lc[(size_t)b * nout + i];
+    __syncthreads();
+    double cx, cy, w;
+    box_geom(tv, b, cx, cy, w);
+    const double iw = 1.0 / w;
+    const int s = tv.start[b], e = tv.end[b];
+    const int sub = threadIdx.x & 3;
+    for (int j0 = s; j0 < e; j0 += UD_T / 4) {
+        const int j = j0 + (threadIdx.x >> 2);
+        const bool ok = j < e;
+        const double2 xj = ok ? xs[j] : make_double2(cx, cy);
+        const double vx = (xj.x - cx) * iw, vy = (xj.y - cy) * iw;
+        double u[kMaxNd];
+        had_u(power, vx, vy, u);
+        double sum = 0.0;
+        for (int d = sub; d < nd; d += 4) {
+            const double2 *L = l2p_sm + d * P;
+            double hx = L[P - 1].x, hy = L[P - 1].y;
+            for (int l = P - 2; l >= 0; --l) {
+                const double nx = fma(hx, vx, fma(-hy, vy, L[l].x));
+                hy = fma(hx, vy, fma(hy, vx, L[l].y));
+                hx = nx;
+            }
+            sum = fma(u[d], hx, sum);
+        }
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (ok && sub == 0) y[j] += sum;
     }
 }
 
@@ -809,6 +1030,19 @@ static void ensure_bufs(Fmm &f, const Tree &t) {
     }
 }
 
+// dynamic shared memory of the FP64 passes exceeds 48 KB for nd = 9, P = 61 (M2M: 8 nd P
+// complex values, 70 KB)
+static void set_pass_smem_limits() {
+    static bool done = false;
+    if (done) return;
+    const int lim = 100 * 1024;
+    PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    PHS_CUDA(cudaFuncSetAttribute(m2m64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    PHS_CUDA(cudaFuncSetAttribute(l2l64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    PHS_CUDA(cudaFuncSetAttribute(l2p64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    done = true;
+}
+
 template <typename T>
 static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, typename C2T<T>::type *mp,
                    const typename C2T<T>::type *ops, int P, cudaStream_t s) {
@@ -816,6 +1050,18 @@ static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_s
     TreeView tv = tree_view(t);
     const int nd = f.nd;
     const size_t esz = (size_t)nd * P * sizeof(C);
+    if constexpr (sizeof(T) == 8) {
+        set_pass_smem_limits();
+        p2m64_kernel<<<t.nleaf, UD_T, (size_t)64 * P * sizeof(double2) + (size_t)64 * nd * sizeof(double), s>>>(
+            tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, nd, P, mp);
+        PHS_LAUNCH_CHECK();
+        for (int l = t.depth - 1; l >= 0; --l) {
+            const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
+            if (nb > 0) m2m64_kernel<<<nb, UD_T, 8 * esz, s>>>(tv, b0, nd, P, ops, mix_buf<T>(f), mp);
+            PHS_LAUNCH_CHECK();
+        }
+        return;
+    }
     const size_t p2m_smem = 32 * P * sizeof(C) + 32 * nd * sizeof(T);
     p2m_kernel<T><<<t.nleaf, FMM_T, p2m_smem, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, nd, P, mp);
     PHS_LAUNCH_CHECK();
@@ -850,6 +1096,16 @@ static void downward(Fmm &f, const Tree &t, typename C2T<T>::type *lc, const typ
                      cudaStream_t s) {
     using C = typename C2T<T>::type;
     const size_t esz = (size_t)f.nd * P * sizeof(C);
+    if constexpr (sizeof(T) == 8) {
+        set_pass_smem_limits();
+        // parents of levels 2 .. depth-1 pass their local expansions to levels 3 .. depth
+        for (int l = 2; l < t.depth; ++l) {
+            const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
+            if (nb > 0) l2l64_kernel<<<nb, UD_T, 5 * esz, s>>>(tree_view(t), b0, f.nd, P, ops, mix_buf<T>(f), lc);
+            PHS_LAUNCH_CHECK();
+        }
+        return;
+    }
     for (int l = 3; l <= t.depth; ++l) {
         const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
         if (nb > 0) l2l_kernel<T><<<nb, FMM_T, 2 * esz, s>>>(tree_view(t), b0, f.nd, P, ops, mix_buf<T>(f), lc);
@@ -981,6 +1237,13 @@ static void p2p_dispatch(Fmm &f, int k, const Tree &t, const PointSet &ps, const
 template <typename T>
 static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s) {
     using C = typename C2T<T>::type;
+    if constexpr (sizeof(T) == 8) {
+        set_pass_smem_limits();
+        l2p64_kernel<<<t.nleaf, UD_T, (size_t)f.nd * f.P * sizeof(double2), s>>>(
+            tree_view(t), t.leaf_box.get(), ps.xs.get(), f.power, f.nd, f.P, f.lc64.get(), y);
+        PHS_LAUNCH_CHECK();
+        return;
+    }
     l2p_kernel<T><<<t.nleaf, 128, (size_t)f.nd * P_of<T>(f) * sizeof(C), s>>>(
         tree_view(t), t.leaf_box.get(), ps.xs.get(), f.power, f.nd, P_of<T>(f), lc_buf<T>(f), y);
     PHS_LAUNCH_CHECK();
@@ -1014,6 +1277,24 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
     if (tm) tm->end(T_DOWN, s);
 }
 
+// The level-invariant operator tables depend only on the order and the Hadamard power:
+// built once per process in long double and reused by every plan.
+static std::mutex g_table_mu;
+static const std::vector<std::complex<long double>> &ops_cached(int P) {
+    static std::map<int, std::vector<std::complex<long double>>> cache;
+    std::lock_guard<std::mutex> g(g_table_mu);
+    auto it = cache.find(P);
+    if (it == cache.end()) it = cache.emplace(P, build_ops(P)).first;
+    return it->second;
+}
+static const std::vector<long double> &mix_cached(int power, int nd) {
+    static std::map<int, std::vector<long double>> cache;
+    std::lock_guard<std::mutex> g(g_table_mu);
+    auto it = cache.find(power);
+    if (it == cache.end()) it = cache.emplace(power, build_mix(power, nd)).first;
+    return it->second;
+}
+
 void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s) {
     PHS_REQUIRE(k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "k must be in 1..5");
     PHS_REQUIRE(p >= 2 && p + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "fmm_order must be in 2..60");
@@ -1027,8 +1308,8 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     f.power = f.log_core ? k : k - 1;
     f.nd = f.power == 0 ? 1 : (f.power == 2 ? 4 : 9);
     PHS_REQUIRE(f.nd * f.P <= FMM_T * OUT_PER_T, PHS_ERR_INVALID_ARG, "fmm_order too large for this spline order");
-    auto ops = build_ops(f.P);
-    auto opsf = build_ops(f.P32);
+    const auto &ops = ops_cached(f.P);
+    const auto &opsf = ops_cached(f.P32);
     std::vector<double2> o64(ops.size());
     std::vector<float2> o32(opsf.size()), o32p(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) {
@@ -1043,7 +1324,7 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     PHS_CUDA(cudaMemcpyAsync(f.ops32.get(), o32.data(), o32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32p.get(), o32p.data(), o32p.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     {
-        auto mx = build_mix(f.power, f.nd);
+        const auto &mx = mix_cached(f.power, f.nd);
         std::vector<double> m64(mx.size());
         std::vector<float> m32(mx.size());
         for (size_t i = 0; i < mx.size(); ++i) {
@@ -1144,14 +1425,18 @@ __global__ void eval_far_log_kernel(TreeView tv, const double2 *tgt, int64_t m, 
     out[i] += acc;
 }
 
-// direct sum over all sources for targets outside the root box (block per target)
+// direct sum over all sources for targets outside the root box: blockIdx.y = target,
+// blockIdx.x = a chunk of the sources, so one target spreads over many SMs; per-chunk
+// partial sums are added in chunk order by eval_outside_sum (deterministic)
+constexpr int kOutsideChunk = 4096;
 template <int K>
 __global__ void eval_outside_kernel(const double2 *xs, int64_t n, const double *w, const double2 *tgt,
-                                    const int *out_idx, double *out) {
-    const int64_t i = out_idx[blockIdx.x];
+                                    const int *out_idx, double *partial) {
+    const int64_t i = out_idx[blockIdx.y];
     const double2 y = tgt[i];
+    const int64_t j0 = (int64_t)blockIdx.x * kOutsideChunk, j1 = min(n, j0 + kOutsideChunk);
     double acc = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         const double dx = y.x - xs[j].x, dy = y.y - xs[j].y;
         const double r2 = dx * dx + dy * dy;
         if (r2 > 0) acc += phi_r2<double, K>(r2) * w[j];
@@ -1163,7 +1448,14 @@ __global__ void eval_outside_kernel(const double2 *xs, int64_t n, const double *
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[i] = red[0];
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+__global__ void eval_outside_sum(const int *out_idx, int nout, int nchunk, const double *partial, double *out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nout) return;
+    double acc = 0.0;
+    for (int c = 0; c < nchunk; ++c) acc += partial[(size_t)q * nchunk + c];
+    out[out_idx[q]] = acc;
 }
 
 template <int K>
@@ -1193,9 +1485,17 @@ static void eval_launch(Fmm &f, const Tree &t, const PointSet &ps, const double 
     if (!outside.empty()) {
         DBuf<int> oi(outside.size());
         PHS_CUDA(cudaMemcpyAsync(oi.get(), outside.data(), outside.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-        eval_outside_kernel<K><<<(unsigned)outside.size(), 256, 0, s>>>(ps.xs.get(), ps.n, w_sorted, tgt, oi.get(),
-                                                                        out);
-        PHS_LAUNCH_CHECK();
+        const int nchunk = (int)((ps.n + kOutsideChunk - 1) / kOutsideChunk);
+        const int nout = (int)outside.size(), batch = 65535;  // grid y limit
+        DBuf<double> part((size_t)nchunk * std::min(nout, batch));
+        for (int q0 = 0; q0 < nout; q0 += batch) {
+            const int nq = std::min(batch, nout - q0);
+            eval_outside_kernel<K><<<dim3((unsigned)nchunk, (unsigned)nq), 256, 0, s>>>(ps.xs.get(), ps.n, w_sorted,
+                                                                                        tgt, oi.get() + q0, part.get());
+            PHS_LAUNCH_CHECK();
+            eval_outside_sum<<<blocks_for(nq, 128), 128, 0, s>>>(oi.get() + q0, nq, nchunk, part.get(), out);
+            PHS_LAUNCH_CHECK();
+        }
         PHS_CUDA(cudaStreamSynchronize(s));
     }
 }

@@ -25,6 +25,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <cuda_bf16.h>
 #include <vector>
 
@@ -522,13 +524,51 @@ static inline uint16_t bf16_bits_of_int(int v) {
     return (uint16_t)(u >> 16);
 }
 
+struct TcHostTables {
+    std::vector<uint16_t> B;
+    std::vector<int> F, S, gexp;
+    std::vector<int2> off;
+};
+static TcHostTables build_tc_tables(int P, int nd, const std::vector<long double> &ops_re,
+                                    const std::vector<long double> &ops_im, const std::vector<long double> &mix);
+
 void m2l_tc_setup(Fmm &f, const std::vector<long double> &ops_re, const std::vector<long double> &ops_im,
                   const std::vector<long double> &mix, cudaStream_t s) {
     const int P = f.P, nd = f.nd;
     PHS_REQUIRE(m2l_tc_supported(nd, P), PHS_ERR_INVALID_ARG, "tensor-core M2L needs nd in {4, 9} and P <= 64");
     f.tc_npad = (P + 15) / 16 * 16;
     f.tc_nch = (2 * P + TC_KC - 1) / TC_KC;
-    const int npad = f.tc_npad, nch = f.tc_nch;
+    // the tables depend on (P, nd) only: built once per process
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, TcHostTables> cache;
+    const TcHostTables *tab;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find({P, nd});
+        if (it == cache.end()) it = cache.emplace(std::make_pair(P, nd), build_tc_tables(P, nd, ops_re, ops_im, mix)).first;
+        tab = &it->second;
+    }
+    f.tc_off.alloc(TC_NCLS);
+    f.tc_b.alloc(tab->B.size());
+    f.tc_F.alloc(P);
+    f.tc_S.alloc(tab->S.size());
+    f.tc_gexp.alloc(tab->gexp.size());
+    f.tc_err.alloc(1);
+    PHS_CUDA(cudaMemcpyAsync(f.tc_off.get(), tab->off.data(), TC_NCLS * sizeof(int2), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.tc_b.get(), tab->B.data(), tab->B.size() * 2, cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.tc_F.get(), tab->F.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.tc_S.get(), tab->S.data(), tab->S.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.tc_gexp.get(), tab->gexp.data(), tab->gexp.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             s));
+    PHS_CUDA(cudaMemsetAsync(f.tc_err.get(), 0, sizeof(int), s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    f.tc = true;
+}
+
+static TcHostTables build_tc_tables(int P, int nd, const std::vector<long double> &ops_re,
+                                    const std::vector<long double> &ops_im, const std::vector<long double> &mix) {
+    TcHostTables out;
+    const int npad = (P + 15) / 16 * 16, nch = (2 * P + TC_KC - 1) / TC_KC;
     auto opv = [&](const std::vector<long double> &o, int c, int l, int k) -> long double {
         return o[((size_t)(8 + c) * P + l) * P + k];
     };
@@ -608,20 +648,12 @@ void m2l_tc_setup(Fmm &f, const std::vector<long double> &ops_re, const std::vec
             off[c] = make_int2(ox, oy);
         }
     }
-    f.tc_off.alloc(TC_NCLS);
-    PHS_CUDA(cudaMemcpyAsync(f.tc_off.get(), off.data(), TC_NCLS * sizeof(int2), cudaMemcpyHostToDevice, s));
-    f.tc_b.alloc(B.size());
-    f.tc_F.alloc(P);
-    f.tc_S.alloc(S.size());
-    f.tc_gexp.alloc(gexp.size());
-    f.tc_err.alloc(1);
-    PHS_CUDA(cudaMemcpyAsync(f.tc_b.get(), B.data(), B.size() * 2, cudaMemcpyHostToDevice, s));
-    PHS_CUDA(cudaMemcpyAsync(f.tc_F.get(), F.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
-    PHS_CUDA(cudaMemcpyAsync(f.tc_S.get(), S.data(), S.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    PHS_CUDA(cudaMemcpyAsync(f.tc_gexp.get(), gexp.data(), gexp.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    PHS_CUDA(cudaMemsetAsync(f.tc_err.get(), 0, sizeof(int), s));
-    PHS_CUDA(cudaStreamSynchronize(s));
-    f.tc = true;
+    out.B = std::move(B);
+    out.F = std::move(F);
+    out.S = std::move(S);
+    out.gexp = std::move(gexp);
+    out.off = std::move(off);
+    return out;
 }
 
 template <int ND>
