@@ -764,6 +764,7 @@ __device__ __forceinline__ double phi_sym(double dx, double dy, const double2 *t
 // holds because the near relation is symmetric (its complement, the V-list relation,
 // is).  One pass per leaf: the plan enables this path only when every leaf has at most
 // P2P_T points.
+
 template <int K>
 __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, const int *leaf_box,
                                                        const int *order, int *ticket, const int *near_off,
@@ -771,6 +772,8 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
                                                        const double *t, double *y, double *scratch) {
     __shared__ double sx[P2P_T], sy[P2P_T], st[P2P_T];
     __shared__ double colp[P2P_T / 32][P2P_T];
+    __shared__ int2 ups[kMaxUpRanges];  // (start, prefix length) of the ranges after the leaf
+    __shared__ int nup, next_leaf;
     extern __shared__ double2 logtab_sm[];
     constexpr bool kTab = (K % 2 == 0);
     const double *eln2 = reinterpret_cast<const double *>(logtab_sm + kLogTab);
@@ -782,13 +785,11 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double scale = kTab ? 0.5 : 1.0;  // r^k log r = r^k log(r^2) / 2
-    __shared__ int next_leaf;
     for (;;) {
         // dynamic schedule over the leaves in decreasing cost order
         if (threadIdx.x == 0) next_leaf = atomicAdd(ticket, 1);
         __syncthreads();
         const int oi = next_leaf;
-        __syncthreads();
         if (oi >= nleaf) break;
         const int li = order[oi];
         const int b = leaf_box[li];
@@ -801,6 +802,9 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
         const int sub = threadIdx.x & (G - 1);
         const int i = s + threadIdx.x / G;
         const bool act = i < e;
+        // warps without an active target skip the arithmetic (warp-uniform)
+        const int nwarp = (nt * G + 31) >> 5;
+        const bool wact = warp < nwarp;
         double xi = 0, yi = 0, ti = 0;
         if (act) {
             const double2 p = xs[i];
@@ -808,67 +812,90 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
             yi = p.y - cy;
             ti = t[i];
         }
+        // own box (rows only) and the list of ranges after the leaf
+        if (threadIdx.x == 0) {
+            int n = 0, pre = 0;
+            for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
+                const int2 rg = near_rng[r];
+                if (rg.x >= e && n < kMaxUpRanges - 1) {  // the plan guarantees fewer
+                    ups[n++] = make_int2(rg.x, pre);
+                    pre += rg.y - rg.x;
+                }
+            }
+            nup = n;
+            ups[n] = make_int2(0, pre);  // total length
+        }
+        if (threadIdx.x < nt) {
+            const double2 p = xs[s + threadIdx.x];
+            sx[threadIdx.x] = p.x - cx;
+            sy[threadIdx.x] = p.y - cy;
+            st[threadIdx.x] = t[s + threadIdx.x];
+        }
+        __syncthreads();
         double acc = 0;
-        int slot = slot_off[li];
-        for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
-            const int2 rg = near_rng[r];
-            const bool self = rg.x == s;
-            if (!self && rg.x < e) continue;
-            for (int j0 = rg.x; j0 < rg.y; j0 += P2P_T) {
-                const int j = j0 + threadIdx.x;
-                __syncthreads();
-                if (j < rg.y) {
+        if (wact) {
+            const int nk = (nt + G - 1) / G;
+            for (int k = 0; k < nk; ++k) {
+                const int jj = k * G + sub;
+                const bool v = jj < nt;
+                const int jc = v ? jj : 0;
+                const double f = v ? phi_sym<K, kTab>(xi - sx[jc], yi - sy[jc], logtab_sm, eln2) : 0.0;
+                acc = fma(f, st[jc], acc);
+            }
+        }
+        const int nu = nup, tot = ups[nu].y;
+        const int slot = slot_off[li];
+        int r0 = 0;  // range of the chunk's first column (advances monotonically)
+        for (int c0 = 0; c0 < tot; c0 += P2P_T) {
+            __syncthreads();
+            {
+                const int g = c0 + threadIdx.x;
+                if (g < tot) {
+                    int r = r0;
+                    while (ups[r + 1].y <= g) ++r;
+                    const int j = ups[r].x + (g - ups[r].y);
                     const double2 p = xs[j];
                     sx[threadIdx.x] = p.x - cx;
                     sy[threadIdx.x] = p.y - cy;
                     st[threadIdx.x] = t[j];
                 }
-                __syncthreads();
-                const int jn = min(P2P_T, rg.y - j0);
-                if (self) {
-                    const int nk = (jn + G - 1) / G;
-                    for (int k = 0; k < nk; ++k) {
-                        const int jj = k * G + sub;
+            }
+            while (r0 + 1 < nu && ups[r0 + 1].y <= c0 + P2P_T) ++r0;
+            __syncthreads();
+            const int jn = min(P2P_T, tot - c0);
+            if (wact) {
+                // systolic column sums: the S = 32/G lanes of a sub-group (same sub) take the
+                // columns of a tile in rotation, step k: lane u on column (k + u) mod S, and
+                // pass the running column sum to lane u - 1, so after S steps lane u holds
+                // the sum of column u over the sub-group's targets (one FMA per pair)
+                const int S = 32 / G, u = lane / G;
+                for (int t0 = 0; t0 < jn; t0 += 32) {
+                    double cs = 0.0;
+                    for (int k = 0; k < S; ++k) {
+                        const int jj = t0 + ((k + u) & (S - 1)) * G + sub;
                         const bool v = jj < jn;
                         const int jc = v ? jj : 0;
                         const double f = v ? phi_sym<K, kTab>(xi - sx[jc], yi - sy[jc], logtab_sm, eln2) : 0.0;
                         acc = fma(f, st[jc], acc);
+                        cs = fma(f, ti, cs);
+                        cs = __shfl_sync(0xffffffffu, cs, (lane + G) & 31);
                     }
-                } else {
-                    // systolic column sums: the S = 32/G lanes of a sub-group (same sub) take the
-                    // columns of a tile in rotation, step k: lane u on column (k + u) mod S, and
-                    // pass the running column sum to lane u - 1, so after S steps lane u holds
-                    // the sum of column u over the sub-group's targets (one FMA per pair)
-                    const int S = 32 / G, u = lane / G;
-                    for (int t0 = 0; t0 < jn; t0 += 32) {
-                        double cs = 0.0;
-                        for (int k = 0; k < S; ++k) {
-                            const int jj = t0 + ((k + u) & (S - 1)) * G + sub;
-                            const bool v = jj < jn;
-                            const int jc = v ? jj : 0;
-                            const double f = v ? phi_sym<K, kTab>(xi - sx[jc], yi - sy[jc], logtab_sm, eln2) : 0.0;
-                            acc = fma(f, st[jc], acc);
-                            cs = fma(f, ti, cs);
-                            cs = __shfl_sync(0xffffffffu, cs, (lane + G) & 31);
-                        }
-                        const int jo = t0 + u * G + sub;
-                        if (jo < jn) colp[warp][jo] = cs;
-                    }
-                }
-                if (!self) {
-                    __syncthreads();
-                    for (int q = threadIdx.x; q < jn; q += P2P_T) {
-                        double sum = 0;
-#pragma unroll
-                        for (int w2 = 0; w2 < P2P_T / 32; ++w2) sum += colp[w2][q];
-                        scratch[slot + (j0 - rg.x) + q] = scale * sum;
-                    }
+                    const int jo = t0 + u * G + sub;
+                    if (jo < jn) colp[warp][jo] = cs;
                 }
             }
-            if (!self) slot += rg.y - rg.x;
+            __syncthreads();
+            for (int q = threadIdx.x; q < jn; q += P2P_T) {
+                double sum = 0;
+                for (int w2 = 0; w2 < nwarp; ++w2) sum += colp[w2][q];
+                scratch[slot + c0 + q] = scale * sum;
+            }
         }
-        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (sub == 0 && act) y[i] = scale * acc;
+        if (wact) {
+            for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (sub == 0 && act) y[i] = scale * acc;
+        }
+        __syncthreads();
     }
 }
 

@@ -106,12 +106,13 @@ struct Tree {
     // slots of earlier leaves, starting at the offsets sym_gbase[sym_goff[d] .. sym_goff[d+1])
     bool sym_ok = false;             // every leaf fits one P2P pass (<= kP2PThreads points)
     int64_t p2p_self_pairs = 0, p2p_upper_pairs = 0;  // pairs in own leaves / ranges after a leaf
-    int max_leaf = 0;
+    int max_leaf = 0, max_up_ranges = 0;
     int64_t sym_total = 0;
     DBuf<int> sym_slot, sym_goff, sym_gbase;
     DBuf<int> p2p_order;             // leaves by decreasing near-field pair count
 };
 constexpr int kP2PThreads = 128;     // threads of a near-field block
+constexpr int kMaxUpRanges = 256;    // near ranges after a leaf that one block holds
 
 struct PointSet {
     int64_t n = 0;

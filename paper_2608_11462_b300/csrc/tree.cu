@@ -215,11 +215,12 @@ __global__ void sym_count(TreeView tv, const int *leaf_box, int nleaf, const int
     const int e = tv.end[b];
     const long long nt = e - tv.start[b];
     atomicMax(maxleaf, (int)nt);
-    int len = 0;
+    int len = 0, nr = 0;
     for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
         const int2 rg = near_rng[r];
         if (rg.x < e) continue;  // b itself or before b
         len += rg.y - rg.x;
+        ++nr;
         for (int j = rg.x; j < rg.y;) {
             const int d = point_leaf[j];
             atomicAdd(&gcnt[d], 1);
@@ -227,6 +228,7 @@ __global__ void sym_count(TreeView tv, const int *leaf_box, int nleaf, const int
         }
     }
     up_len[li] = len;
+    atomicMax(&maxleaf[1], nr);
     atomicAdd(&pairs[0], (unsigned long long)(nt * nt));
     atomicAdd(&pairs[1], (unsigned long long)(nt * len));
     // processing order of the near-field blocks: decreasing pair count
@@ -438,14 +440,14 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     }
     {
         const int nl = tree.nleaf;
-        DBuf<int> up_len(nl), gcnt(nl), gcur(nl), mx(1);
+        DBuf<int> up_len(nl), gcnt(nl), gcur(nl), mx(2);
         DBuf<uint64_t> ckey(nl);
         tree.p2p_order.alloc(nl);
         DBuf<unsigned long long> prs(2);
         PHS_CUDA(cudaMemsetAsync(prs.get(), 0, 2 * sizeof(unsigned long long), s));
         PHS_CUDA(cudaMemsetAsync(gcnt.get(), 0, nl * sizeof(int), s));
         PHS_CUDA(cudaMemsetAsync(gcur.get(), 0, nl * sizeof(int), s));
-        PHS_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
+        PHS_CUDA(cudaMemsetAsync(mx.get(), 0, 2 * sizeof(int), s));
         sym_count<<<blocks_for(nl, 128), 128, 0, s>>>(tv, tree.leaf_box.get(), nl, tree.near_off.get(),
                                                       tree.near_rng.get(), tree.point_leaf.get(), up_len.get(),
                                                       gcnt.get(), mx.get(), prs.get(), ckey.get(),
@@ -468,10 +470,13 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
         sym_sort<<<blocks_for(nl, 128), 128, 0, s>>>(tree.sym_goff.get(), nl, tree.sym_gbase.get());
         PHS_LAUNCH_CHECK();
         unsigned long long hp[2];
-        PHS_CUDA(cudaMemcpyAsync(&tree.max_leaf, mx.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        int hm[2];
+        PHS_CUDA(cudaMemcpyAsync(hm, mx.get(), sizeof(hm), cudaMemcpyDeviceToHost, s));
         PHS_CUDA(cudaMemcpyAsync(hp, prs.get(), sizeof(hp), cudaMemcpyDeviceToHost, s));
         PHS_CUDA(cudaStreamSynchronize(s));
-        tree.sym_ok = tree.max_leaf <= kP2PThreads;
+        tree.max_leaf = hm[0];
+        tree.max_up_ranges = hm[1];
+        tree.sym_ok = tree.max_leaf <= kP2PThreads && tree.max_up_ranges < kMaxUpRanges;
         tree.p2p_self_pairs = (int64_t)hp[0];
         tree.p2p_upper_pairs = (int64_t)hp[1];
     }
