@@ -514,13 +514,22 @@ __global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd
             const int l = h == 0 ? p : P - 1 - p;
             if (h == 1 && l == p) break;
             const double2 *Ar = A + (size_t)l * P;
-            double ax = 0.0, ay = 0.0;
-            for (int k = 0; k <= l; ++k) {
+            // two partial sums (even / odd k) halve the dependent FMA chain
+            double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+            int k = 0;
+            for (; k + 1 <= l; k += 2) {
+                const double2 a = Ar[k], m = src[k], a1 = Ar[k + 1], m1 = src[k + 1];
+                ax = fma(a.x, m.x, fma(-a.y, m.y, ax));
+                ay = fma(a.x, m.y, fma(a.y, m.x, ay));
+                bx = fma(a1.x, m1.x, fma(-a1.y, m1.y, bx));
+                by = fma(a1.x, m1.y, fma(a1.y, m1.x, by));
+            }
+            if (k <= l) {
                 const double2 a = Ar[k], m = src[k];
                 ax = fma(a.x, m.x, fma(-a.y, m.y, ax));
                 ay = fma(a.x, m.y, fma(a.y, m.x, ay));
             }
-            sh[c * nout + d * P + l] = make_double2(ax, ay);
+            sh[c * nout + d * P + l] = make_double2(ax + bx, ay + by);
         }
     }
     __syncthreads();
@@ -564,13 +573,21 @@ __global__ void __launch_bounds__(UD_T) l2l64_kernel(TreeView tv, int b0, int nd
             const int m = h == 0 ? p : P - 1 - p;
             if (h == 1 && m == p) break;
             const double2 *Ar = A + (size_t)m * P;
-            double ax = 0.0, ay = 0.0;
-            for (int l = m; l < P; ++l) {
+            double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+            int l = m;
+            for (; l + 1 < P; l += 2) {
+                const double2 a = Ar[l], v = src[l], a1 = Ar[l + 1], v1 = src[l + 1];
+                ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
+                ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+                bx = fma(a1.x, v1.x, fma(-a1.y, v1.y, bx));
+                by = fma(a1.x, v1.y, fma(a1.y, v1.x, by));
+            }
+            if (l < P) {
                 const double2 a = Ar[l], v = src[l];
                 ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
                 ay = fma(a.x, v.y, fma(a.y, v.x, ay));
             }
-            sh[c * nout + d * P + m] = make_double2(ax, ay);
+            sh[c * nout + d * P + m] = make_double2(ax + bx, ay + by);
         }
     }
     __syncthreads();
@@ -605,6 +622,8 @@ __global__ void __launch_bounds__(UD_T) l2p64_kernel(TreeView tv, const int *lea
     const int s = tv.start[b], e = tv.end[b];
     const int sub = threadIdx.x & 3;
     for (int j0 = s; j0 < e; j0 += UD_T / 4) {
+        // a warp covers 8 points; warps past the leaf's last point skip (warp-uniform)
+        if (j0 + ((threadIdx.x >> 5) << 3) >= e) continue;
         const int j = j0 + (threadIdx.x >> 2);
         const bool ok = j < e;
         const double2 xj = ok ? xs[j] : make_double2(cx, cy);
