@@ -492,44 +492,53 @@ __global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *lea
     }
 }
 
-// M2M for the parents of one level: all children load and shift at once; each thread
-// takes row pairs (l, P-1-l) so the triangular shift is balanced; then the parent sums
-// the children through the frame changes Rv (mix slots 49 + quadrant).
-__global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd, int P, const double2 *ops,
-                                                    const double *mix, double2 *mp) {
+// M2M for the parents of one level: all children load and shift at once.  The shift of
+// quadrant q factors as e^{i th_q l} R[l][k] e^{-i th_q k} with a real lower-triangular
+// core R common to the four quadrants, so the O(P^2) part is real x complex (2 FMA per
+// entry instead of 4).  Each thread takes row pairs (l, P-1-l) to balance the triangle;
+// then the parent sums the children through the frame changes Rv (mix slots 49 + q).
+__global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd, int P, const double *R,
+                                                    const double2 *ph, const double *mix, double2 *mp) {
     extern __shared__ double2 m2m_sm[];
     const int b = b0 + blockIdx.x;
     const int nc = tv.nchild[b];
     if (nc == 0) return;
     const int nout = nd * P, c0 = tv.child[b];
     double2 *ch = m2m_sm, *sh = m2m_sm + 4 * nout;
-    for (int i = threadIdx.x; i < nc * nout; i += UD_T) ch[i] = mp[(size_t)c0 * nout + i];
+    for (int i = threadIdx.x; i < nc * nout; i += UD_T) {
+        const int c = i / nout, k = (i - c * nout) % P;
+        const double2 a = mp[(size_t)c0 * nout + i], e = ph[(size_t)(tv.key[c0 + c] & 3) * P + k];
+        ch[i] = make_double2(fma(a.x, e.x, a.y * e.y), fma(a.y, e.x, -a.x * e.y));  // a e^{-i th k}
+    }
     __syncthreads();
     const int half = (P + 1) / 2;
     for (int it = threadIdx.x; it < nc * nd * half; it += UD_T) {
         const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
-        const double2 *A = ops + (size_t)(tv.key[c0 + c] & 3) * P * P;
+        const double2 *ephq = ph + (size_t)(tv.key[c0 + c] & 3) * P;
         const double2 *src = ch + c * nout + d * P;
         for (int h = 0; h < 2; ++h) {
             const int l = h == 0 ? p : P - 1 - p;
             if (h == 1 && l == p) break;
-            const double2 *Ar = A + (size_t)l * P;
-            // two partial sums (even / odd k) halve the dependent FMA chain
+            const double *Rr = R + (size_t)l * P;
             double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
             int k = 0;
             for (; k + 1 <= l; k += 2) {
-                const double2 a = Ar[k], m = src[k], a1 = Ar[k + 1], m1 = src[k + 1];
-                ax = fma(a.x, m.x, fma(-a.y, m.y, ax));
-                ay = fma(a.x, m.y, fma(a.y, m.x, ay));
-                bx = fma(a1.x, m1.x, fma(-a1.y, m1.y, bx));
-                by = fma(a1.x, m1.y, fma(a1.y, m1.x, by));
+                const double r0 = Rr[k], r1 = Rr[k + 1];
+                const double2 m0 = src[k], m1 = src[k + 1];
+                ax = fma(r0, m0.x, ax);
+                ay = fma(r0, m0.y, ay);
+                bx = fma(r1, m1.x, bx);
+                by = fma(r1, m1.y, by);
             }
             if (k <= l) {
-                const double2 a = Ar[k], m = src[k];
-                ax = fma(a.x, m.x, fma(-a.y, m.y, ax));
-                ay = fma(a.x, m.y, fma(a.y, m.x, ay));
+                const double r0 = Rr[k];
+                const double2 m0 = src[k];
+                ax = fma(r0, m0.x, ax);
+                ay = fma(r0, m0.y, ay);
             }
-            sh[c * nout + d * P + l] = make_double2(ax + bx, ay + by);
+            const double zx = ax + bx, zy = ay + by;
+            const double2 e = ephq[l];  // z e^{i th l}
+            sh[c * nout + d * P + l] = make_double2(fma(zx, e.x, -zy * e.y), fma(zx, e.y, zy * e.x));
         }
     }
     __syncthreads();
@@ -551,43 +560,52 @@ __global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd
     }
 }
 
-// L2L for the parents of one level: the parent's local expansion loads once, shifts to
-// each child centre (rows m paired with P-1-m: sum over l >= m) and mixes through Ru
-// (mix slots 53 + quadrant) into the child's local expansion.
-__global__ void __launch_bounds__(UD_T) l2l64_kernel(TreeView tv, int b0, int nd, int P, const double2 *ops,
-                                                    const double *mix, double2 *lc) {
+// L2L for the parents of one level: the parent's local expansion loads once, takes each
+// child's phase e^{i th_q l}, shifts through the real upper-triangular core (rows m
+// paired with P-1-m: sum over l >= m), takes e^{-i th_q m}, and mixes through Ru (mix
+// slots 53 + q) into the child's local expansion.
+__global__ void __launch_bounds__(UD_T) l2l64_kernel(TreeView tv, int b0, int nd, int P, const double *R,
+                                                    const double2 *ph, const double *mix, double2 *lc) {
     extern __shared__ double2 l2l_sm[];
     const int b = b0 + blockIdx.x;
     const int nc = tv.nchild[b];
     if (nc == 0) return;
     const int nout = nd * P, c0 = tv.child[b];
-    double2 *par = l2l_sm, *sh = l2l_sm + nout;
-    for (int i = threadIdx.x; i < nout; i += UD_T) par[i] = lc[(size_t)b * nout + i];
+    double2 *y = l2l_sm, *sh = l2l_sm + 4 * nout;
+    for (int i = threadIdx.x; i < nc * nout; i += UD_T) {
+        const int c = i / nout, o = i - c * nout, l = o % P;
+        const double2 v = lc[(size_t)b * nout + o], e = ph[(size_t)(tv.key[c0 + c] & 3) * P + l];
+        y[i] = make_double2(fma(v.x, e.x, -v.y * e.y), fma(v.x, e.y, v.y * e.x));  // b e^{i th l}
+    }
     __syncthreads();
     const int half = (P + 1) / 2;
     for (int it = threadIdx.x; it < nc * nd * half; it += UD_T) {
         const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
-        const double2 *A = ops + (size_t)(4 + (tv.key[c0 + c] & 3)) * P * P;
-        const double2 *src = par + d * P;
+        const double2 *ephq = ph + (size_t)(tv.key[c0 + c] & 3) * P;
+        const double2 *src = y + c * nout + d * P;
         for (int h = 0; h < 2; ++h) {
             const int m = h == 0 ? p : P - 1 - p;
             if (h == 1 && m == p) break;
-            const double2 *Ar = A + (size_t)m * P;
+            const double *Rr = R + (size_t)m * P;
             double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
             int l = m;
             for (; l + 1 < P; l += 2) {
-                const double2 a = Ar[l], v = src[l], a1 = Ar[l + 1], v1 = src[l + 1];
-                ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
-                ay = fma(a.x, v.y, fma(a.y, v.x, ay));
-                bx = fma(a1.x, v1.x, fma(-a1.y, v1.y, bx));
-                by = fma(a1.x, v1.y, fma(a1.y, v1.x, by));
+                const double r0 = Rr[l], r1 = Rr[l + 1];
+                const double2 v0 = src[l], v1 = src[l + 1];
+                ax = fma(r0, v0.x, ax);
+                ay = fma(r0, v0.y, ay);
+                bx = fma(r1, v1.x, bx);
+                by = fma(r1, v1.y, by);
             }
             if (l < P) {
-                const double2 a = Ar[l], v = src[l];
-                ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
-                ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+                const double r0 = Rr[l];
+                const double2 v0 = src[l];
+                ax = fma(r0, v0.x, ax);
+                ay = fma(r0, v0.y, ay);
             }
-            sh[c * nout + d * P + m] = make_double2(ax + bx, ay + by);
+            const double zx = ax + bx, zy = ay + by;
+            const double2 e = ephq[m];  // z e^{-i th m}
+            sh[c * nout + d * P + m] = make_double2(fma(zx, e.x, zy * e.y), fma(zy, e.x, -zx * e.y));
         }
     }
     __syncthreads();
@@ -1103,7 +1121,9 @@ static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_s
         PHS_LAUNCH_CHECK();
         for (int l = t.depth - 1; l >= 0; --l) {
             const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-            if (nb > 0) m2m64_kernel<<<nb, UD_T, 8 * esz, s>>>(tv, b0, nd, P, ops, mix_buf<T>(f), mp);
+            if (nb > 0)
+                m2m64_kernel<<<nb, UD_T, 8 * esz, s>>>(tv, b0, nd, P, f.shift_r.get(), f.shift_ph.get(), mix_buf<T>(f),
+                                                       mp);
             PHS_LAUNCH_CHECK();
         }
         return;
@@ -1147,7 +1167,9 @@ static void downward(Fmm &f, const Tree &t, typename C2T<T>::type *lc, const typ
         // parents of levels 2 .. depth-1 pass their local expansions to levels 3 .. depth
         for (int l = 2; l < t.depth; ++l) {
             const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-            if (nb > 0) l2l64_kernel<<<nb, UD_T, 5 * esz, s>>>(tree_view(t), b0, f.nd, P, ops, mix_buf<T>(f), lc);
+            if (nb > 0)
+                l2l64_kernel<<<nb, UD_T, 8 * esz, s>>>(tree_view(t), b0, f.nd, P, f.shift_r.get() + (size_t)P * P,
+                                                       f.shift_ph.get(), mix_buf<T>(f), lc);
             PHS_LAUNCH_CHECK();
         }
         return;
@@ -1369,6 +1391,45 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     PHS_CUDA(cudaMemcpyAsync(f.ops64.get(), o64.data(), o64.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32.get(), o32.data(), o32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32p.get(), o32p.data(), o32p.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    {
+        // real shift cores: R[l][k] = A_0[l][k] e^{-i th_0 (l - k)} (quadrant 0), checked real and
+        // equal for the other quadrants
+        const int P = f.P;
+        std::vector<double> R((size_t)2 * P * P);
+        std::vector<double2> ph((size_t)4 * P);
+        const long double pi = 3.141592653589793238462643383279502884L;
+        for (int q = 0; q < 4; ++q) {
+            const long double th = std::atan2((long double)((q & 2) ? 0.25L : -0.25L), (long double)((q & 1) ? 0.25L : -0.25L));
+            for (int k = 0; k < P; ++k) {
+                const long double a = th * k;
+                // exact unit values at multiples of 45 degrees
+                const long double c = std::cos(a), sn = std::sin(a);
+                ph[(size_t)q * P + k] = make_double2((double)c, (double)sn);
+            }
+            for (int t2 = 0; t2 < 2; ++t2)
+                for (int r = 0; r < P; ++r)
+                    for (int c2 = 0; c2 < P; ++c2) {
+                        const std::complex<long double> A = ops[((size_t)(4 * t2 + q) * P + r) * P + c2];
+                        // M2M: row l = r, col k = c2, phase e^{i th (l - k)}; L2L: row m = r, col l = c2,
+                        // phase e^{i th (l - m)}
+                        const long double ang = t2 == 0 ? th * (r - c2) : th * (c2 - r);
+                        const std::complex<long double> v = A * std::polar(1.0L, -ang);
+                        const long double mag = std::abs(A);
+                        PHS_REQUIRE(std::fabs(v.imag()) <= 1e-12L * std::max(mag, 1e-300L) + 1e-300L, PHS_ERR_INVALID_ARG,
+                                    "shift operator does not factor through a real core");
+                        double &dst = R[((size_t)t2 * P + r) * P + c2];
+                        if (q == 0) dst = (double)v.real();
+                        else
+                            PHS_REQUIRE(std::fabs((long double)dst - v.real()) <= 1e-12L * std::max(mag, 1e-300L) + 1e-300L,
+                                        PHS_ERR_INVALID_ARG, "shift cores differ between quadrants");
+                    }
+        }
+        (void)pi;
+        f.shift_r.alloc(R.size());
+        f.shift_ph.alloc(ph.size());
+        PHS_CUDA(cudaMemcpyAsync(f.shift_r.get(), R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        PHS_CUDA(cudaMemcpyAsync(f.shift_ph.get(), ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+    }
     {
         const auto &mx = mix_cached(f.power, f.nd);
         std::vector<double> m64(mx.size());

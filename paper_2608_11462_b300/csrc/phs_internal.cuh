@@ -146,6 +146,10 @@ struct Fmm {
     DBuf<double2> mp64, lc64;
     DBuf<float2> mp32, lc32;
     DBuf<double2> ops64;  // M2M[4], L2L[4], M2L[49] (P x P each)
+    // M2M/L2L of quadrant q = e^{i th_q l} R[l][k] e^{-i th_q k} (offset d_q = |d| e^{i th_q}):
+    // the real shift cores [2][P][P] (M2M, L2L) and the phases e^{i th_q k} [4][P]
+    DBuf<double> shift_r;
+    DBuf<double2> shift_ph;
     DBuf<float2> ops32;   // same for the FP32 order P32
     DBuf<float2> ops32p, mpx32, lcx32;  // FP32 copies at the FP64 order (FP32 M2L mode)
     DBuf<double> mix64;                 // box-local Hadamard frame changes [57][nd][nd]
