@@ -163,7 +163,7 @@ __constant__ double c_s1[kSerTerms], c_p1[kSerTerms], c_s0[kSerTerms], c_h0[kSer
 
 // terms for a truncation below 1e-16 relative: q^n / (n!)^2 at the bound of each class
 __device__ __forceinline__ int ser_terms(double q) {
-    return q <= 6.103515625e-05 ? 4 : (q <= 0.015625 ? 6 : (q <= 0.125 ? 9 : kSerTerms));
+    return q <= 3.814697265625e-06 ? 3 : (q <= 6.103515625e-05 ? 4 : (q <= 0.015625 ? 6 : (q <= 0.125 ? 9 : kSerTerms)));
 }
 
 // Table-driven FP64 logarithm for the series (P. T. P. Tang, ACM TOMS 16(4), 1990):
@@ -326,9 +326,24 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
             if (!(rj > 0.0)) { ok = false; break; }
             for (int a = j + 1 + lane; a < s; a += 32) A[a * ld + j] *= rj;
             __syncwarp();
-            for (int a = j + 1 + lane; a < s; a += 32) {
-                const double laj = A[a * ld + j];
-                for (int c = j + 1; c <= a; ++c) A[a * ld + c] = fma(-laj, A[c * ld + j], A[a * ld + c]);
+            // trailing update over the entries (not the rows) of the lower triangle, so every
+            // lane has the same work: entry t = a'(a'+1)/2 + c', c' <= a', of the trailing block
+            {
+                const int mm = s - j - 1, ntr = mm * (mm + 1) / 2;
+                int ap = 0, cp = lane;
+                while (cp > ap) {
+                    cp -= ap + 1;
+                    ++ap;
+                }
+                for (int t = lane; t < ntr; t += 32) {
+                    const int a = j + 1 + ap, c = j + 1 + cp;
+                    A[a * ld + c] = fma(-A[a * ld + j], A[c * ld + j], A[a * ld + c]);
+                    cp += 32;
+                    while (cp > ap) {
+                        cp -= ap + 1;
+                        ++ap;
+                    }
+                }
             }
             __syncwarp();
         }
@@ -398,40 +413,25 @@ __global__ void t_count(const int *nbr_ell, int64_t n, int m, int *cnt) {
         if (r >= 0) atomicAdd(&cnt[r], 1);
     }
 }
-__global__ void t_fill(const int *nbr_ell, const double *val_ell, int64_t n, int m, const int *off, int *cur, int *col,
-                       double *val) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    int pos = off[j] + atomicAdd(&cur[j], 1);
-    col[pos] = (int)j;
-    val[pos] = val_ell[j];
-    for (int q = 0; q < m; ++q) {
-        const int r = nbr_ell[(int64_t)q * n + j];
-        if (r >= 0) {
-            pos = off[r] + atomicAdd(&cur[r], 1);
-            col[pos] = (int)j;
-            val[pos] = val_ell[(int64_t)(1 + q) * n + j];
-        }
-    }
+// entries of U~ as (row, entry) pairs in column-major order: entry e = slot * n + j of the
+// ELL factor (slot 0 the diagonal, slot 1 + q neighbour q); absent neighbours get row n
+__global__ void t_pairs(const int *nbr_ell, int64_t n, int m, uint64_t *key, int *ent) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)(m + 1) * n) return;
+    const int64_t j = p / (m + 1);
+    const int slot = (int)(p - j * (m + 1));
+    const int r = slot == 0 ? (int)j : nbr_ell[(int64_t)(slot - 1) * n + j];
+    key[p] = r >= 0 ? (uint64_t)r : (uint64_t)n;
+    ent[p] = (int)((int64_t)slot * n + j);
 }
-// deterministic order within each row (by column)
-__global__ void t_sort_rows(const int *off, int64_t n, int *col, double *val) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int a = off[i] + 1; a < off[i + 1]; ++a) {
-        const int c = col[a];
-        const double v = val[a];
-        int b = a - 1;
-        while (b >= off[i] && col[b] > c) {
-            col[b + 1] = col[b];
-            val[b + 1] = val[b];
-            --b;
-        }
-        col[b + 1] = c;
-        val[b + 1] = v;
-    }
+// after a stable sort by row the entries of a row are in column order (deterministic)
+__global__ void t_gather(const int *ent, int64_t nnz, int64_t n, const double *val_ell, int *col, double *val) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nnz) return;
+    const int e = ent[i];
+    col[i] = (int)(e % n);
+    val[i] = val_ell[e];
 }
-
 // y = U~' r  (column j of U~ dotted with r)
 __global__ void apply_ut(const int *nbr_ell, const double *val_ell, int64_t n, int m, const double *r, double *y) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -686,9 +686,8 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     permute_ell<<<blocks_for(n, 256), 256, 0, s>>>(ps.iperm.get(), n, 1, order_c.get(), v.order.get());
     PHS_LAUNCH_CHECK();
     // transpose
-    DBuf<int> cnt(n), cur(n);
+    DBuf<int> cnt(n);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, n * sizeof(int), s));
-    PHS_CUDA(cudaMemsetAsync(cur.get(), 0, n * sizeof(int), s));
     t_count<<<blocks_for(n, 256), 256, 0, s>>>(v.nbr.get(), n, m, cnt.get());
     PHS_LAUNCH_CHECK();
     v.t_off.alloc(n + 1);
@@ -697,11 +696,19 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     PHS_CUDA(cudaMemcpyAsync(v.t_off.get() + n, &nz32, sizeof(int), cudaMemcpyHostToDevice, s));
     v.t_col.alloc(nnz);
     v.t_val.alloc(nnz);
-    t_fill<<<blocks_for(n, 256), 256, 0, s>>>(v.nbr.get(), v.val.get(), n, m, v.t_off.get(), cur.get(), v.t_col.get(),
-                                              v.t_val.get());
-    PHS_LAUNCH_CHECK();
-    t_sort_rows<<<blocks_for(n, 256), 256, 0, s>>>(v.t_off.get(), n, v.t_col.get(), v.t_val.get());
-    PHS_LAUNCH_CHECK();
+    {
+        const int64_t np = (int64_t)(m + 1) * n;
+        PHS_REQUIRE(np < (1ll << 31), PHS_ERR_INVALID_ARG, "Vecchia factor too large for 32-bit entry indices");
+        DBuf<uint64_t> key(np);
+        DBuf<int> ent(np);
+        t_pairs<<<blocks_for(np, 256), 256, 0, s>>>(v.nbr.get(), n, m, key.get(), ent.get());
+        PHS_LAUNCH_CHECK();
+        int bits = 1;
+        while ((1ll << bits) <= n) ++bits;
+        radix_sort_pairs(key.get(), ent.get(), np, bits, s);
+        t_gather<<<blocks_for(nnz, 256), 256, 0, s>>>(ent.get(), nnz, n, v.val.get(), v.t_col.get(), v.t_val.get());
+        PHS_LAUNCH_CHECK();
+    }
     PHS_CUDA(cudaStreamSynchronize(s));
 }
 
