@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the point count (smaller parity runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--leaf-cap", type=int, default=64, help="quadtree leaf capacity")
+    ap.add_argument("--ordering", type=int, default=2, choices=[0, 1, 2],
+                    help="Vecchia enumeration: 0 random, 1 exact maxmin, 2 hierarchical maximin")
     return ap.parse_args()
 
 
@@ -114,8 +116,8 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- CPU oracle leg
 def oracle_step(points, f, targets, n_sample, seed=0):
-    """The oracle as it stands on a bounded random subsample: normalisation, random
-    order, brute-force neighbours, Vecchia factor, dense-matvec PCG to 1e-8, dense
+    """The oracle as it stands on a bounded random subsample: normalisation,
+    hierarchical maximin order, brute-force neighbours, Vecchia factor, dense-matvec PCG to 1e-8, dense
     evaluation at the targets.  Returns (seconds, n_sample, iterations)."""
     import numpy as np
 
@@ -125,7 +127,7 @@ def oracle_step(points, f, targets, n_sample, seed=0):
     p, fs = points[idx], f[idx]
     t0 = time.perf_counter()
     xn, c, rho = oracle.normalize(p, 0.25)
-    order = oracle.random_order(n_sample, 1)
+    order, _ = oracle.hmaxmin_order(xn, 1)
     nbr = oracle.knn_prev(xn, order, 30)
     d, o, _ = oracle.vecchia_factor(xn, order, nbr, 30, NU, ALPHA)
     w, beta, it, _ = oracle.pcg(xn, fs, 2, 1, (nbr, d, o), tol=1e-8, maxiter=300)
@@ -192,7 +194,8 @@ def main():
     import paper_2608_11462_b300 as phs
 
     L = phs.lib()
-    opts = phs.options(2, precision=args.precision, tol=1e-8, nu=NU, alpha=ALPHA, leaf_cap=args.leaf_cap)
+    opts = phs.options(2, precision=args.precision, tol=1e-8, nu=NU, alpha=ALPHA, leaf_cap=args.leaf_cap,
+                       ordering=args.ordering)
     pts_d = torch.tensor(points, device=dev)
     f_d = torch.tensor(f, device=dev)
     tg_d = torch.tensor(targets, device=dev)
@@ -314,7 +317,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
         "fits_per_s": world / t_step,
         "config": {"workload": WORKLOAD, "n": n, "targets": m_t, "k": 2, "poly_degree": 1, "vecchia_m": 30,
-                   "nu": NU, "alpha_normalised": ALPHA, "ordering": "random", "leaf_cap": args.leaf_cap, "fmm_order": sizes[3],
+                   "nu": NU, "alpha_normalised": ALPHA, "ordering": ["random", "maxmin", "hierarchical maximin"][args.ordering], "leaf_cap": args.leaf_cap, "fmm_order": sizes[3],
                    "precision_mode": args.precision, "tol": 1e-8, "parallelism": f"replicas{world}",
                    "l2": "flushed (256 MB write) between timed steps"},
         "pcg": {"iters": info["iters"], "outer_iters": info["outer_iters"], "converged": info["converged"],

@@ -65,7 +65,9 @@ typedef struct {
     double atol;            /* default 0 */
     int maxiter;            /* PCG iterations (precision 0) or total inner iterations; default 200 */
     int leaf_cap;           /* quadtree leaf capacity s; default 64 */
-    int ordering;           /* Vecchia enumeration: 0 random (Sec. 3), 1 exact maxmin */
+    int ordering;           /* Vecchia enumeration: 0 random (Sec. 3), 1 exact maxmin (single
+                               block, O(n^2): small n), 2 hierarchical maximin (phs_hmaxmin_order,
+                               the default: fewer PCG iterations than random at any n) */
     double nu;              /* Matern smoothness: 0.5, 1, 1.5, 2 or 2.5; default k/2, whose
                                leading non-analytic term is the PHS kernel (nu = 1 for the
                                thin-plate spline, Sec. 2.2, Eq. 2.17) */
@@ -218,6 +220,17 @@ phs_status phs_random_order(int64_t n, uint64_t seed, int64_t *order_dev, phs_st
  * set; ties to the smaller index.  Squared distances dx*dx+dy*dy, no FMA. */
 phs_status phs_maxmin_order(const double *pts_dev, int64_t n, int64_t *order_dev,
                             phs_stream_t stream);
+/* Hierarchical maximin enumeration (parallel, O(n log n)): over a dyadic grid of the
+ * bounding square (side E = larger extent, level-30 cell coordinates
+ * ix = min(floor((x - xmin) * (2^30 / E)), 2^30 - 1)), each level-L cell is represented
+ * by its parent cell's representative if that lies in it, else by its point nearest the
+ * cell centre ((x-cx)^2 + (y-cy)^2 in FP64 without FMA, ties to the smaller index); a
+ * point's level is the first level at which it represents its cell (31 if never), and
+ * points are enumerated by (level, SplitMix64(seed, i) >> 7, i).  The points first
+ * picked at level L are one per cell, about a cell width from everything earlier: the
+ * spacing property of an exact maxmin ordering, level by level. */
+phs_status phs_hmaxmin_order(const double *pts_dev, int64_t n, uint64_t seed, int64_t *order_dev,
+                             phs_stream_t stream);
 /* Conditioning sets (Sec. 2.2): for the point of rank r (order_dev as above) the
  * min(m, r) points of smaller rank nearest to it, by (squared distance
  * dx*dx+dy*dy without FMA, rank); nbr_dev is n x m int64, -1 padded. */

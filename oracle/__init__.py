@@ -16,7 +16,7 @@ What it computes, each function citing the passage it follows:
                              pivoting (a library primitive).
 * ``solve_qperp``         -- the same system by the sequence (2.5) with an
                              explicit complete QR and a Cholesky factor.
-* ``random_order``, ``maxmin_order``, ``knn_prev``, ``vecchia_factor``,
+* ``random_order``, ``maxmin_order``, ``hmaxmin_order``, ``knn_prev``, ``vecchia_factor``,
   ``vecchia_apply``       -- the Vecchia preconditioner of Sec. 2.2 (Eq. 2.19,
                              Fig. 1) with brute-force neighbour search.
 * ``pcg``                 -- preconditioned CG on Q_perp^T M Q_perp (Sec. 2,
@@ -217,6 +217,50 @@ def maxmin_order(x):
     dm = np.empty(n, dtype=np.float64)
     lib().or_maxmin_order(n, _p(x), _p(out), _p(dm))
     return out, dm
+
+
+def hmaxmin_order(x, seed: int):
+    """Hierarchical maximin enumeration, restated from its definition level by level
+    (the spacing property of maxmin enumeration kept per dyadic level of the bounding
+    square, for the ordering of Sec. 2.2):
+    level-30 cell coordinates ix = min(floor((x - xmin) * (2^30 / E)), 2^30 - 1) with E
+    the larger extent; a level-L cell (ix >> (30 - L), iy >> (30 - L)) is represented by
+    its parent's representative when that lies in it, else by its point nearest the cell
+    centre ((x - cx)^2 + (y - cy)^2 in FP64, one rounding per operation, ties to the
+    smaller index); a point's level is the first level at which it represents its cell
+    (31 if never); the enumeration sorts by (level, splitmix64(seed, i) >> 7, i).
+    Returns (order, level)."""
+    x = _f64(x).reshape(-1, 2)
+    n = x.shape[0]
+    idx = np.arange(n)
+    xmin, ymin = x[:, 0].min(), x[:, 1].min()
+    E = max(x[:, 0].max() - xmin, x[:, 1].max() - ymin)
+    if not E > 0:
+        E = 1.0
+    scale = 2.0 ** 30 / E
+    lim = 2 ** 30 - 1
+    ix = np.clip(np.floor((x[:, 0] - xmin) * scale), 0, lim).astype(np.int64)
+    iy = np.clip(np.floor((x[:, 1] - ymin) * scale), 0, lim).astype(np.int64)
+    level = np.full(n, 31, dtype=np.int64)
+    rep = None
+    for L in range(31):
+        cx_i, cy_i = ix >> (30 - L), iy >> (30 - L)
+        cell = cx_i * (1 << 31) + cy_i
+        w = np.ldexp(E, -L)
+        dx = x[:, 0] - (xmin + (cx_i + 0.5) * w)
+        dy = x[:, 1] - (ymin + (cy_i + 0.5) * w)
+        d2 = dx * dx + dy * dy
+        o = np.lexsort((idx, d2, cell))          # by cell, then distance, then index
+        first = np.ones(n, dtype=bool)
+        first[1:] = cell[o][1:] != cell[o][:-1]
+        ucell, best = cell[o][first], o[first]   # the nearest point of each cell
+        nearest = best[np.searchsorted(ucell, cell)]
+        rep = nearest if rep is None else np.where(cell[rep] == cell, rep, nearest)
+        newly = (rep == idx) & (level == 31)
+        level[newly] = L
+    h = np.array([splitmix64(seed, int(i)) >> 7 for i in range(n)], dtype=np.uint64)
+    order = np.lexsort((idx, h, level))
+    return order.astype(np.int64), level
 
 
 def knn_prev(x, order, m: int) -> np.ndarray:

@@ -199,6 +199,35 @@ def test_maxmin_order_bit_exact(phs):
     assert phs.phs_maxmin_order(_t(g)).cpu().numpy().tolist() == [3, 4, 0, 1, 2]
 
 
+@pytest.mark.parametrize("clustered", [False, True])
+def test_hmaxmin_order_bit_exact(phs, clustered):
+    rng = np.random.default_rng(31)
+    pts = rng.random((5000, 2))
+    if clustered:
+        pts = _clustered(5000, 32)
+    got = phs.phs_hmaxmin_order(_t(pts), seed=9).cpu().numpy()
+    want, _ = oracle.hmaxmin_order(pts, 9)
+    assert np.array_equal(got, want)
+    tiny = np.array([[0, 0], [1, 0], [0, 1], [1, 1], [0.5, 0.5]], dtype=float)
+    assert phs.phs_hmaxmin_order(_t(tiny), seed=3).cpu().numpy().tolist() == oracle.hmaxmin_order(tiny, 3)[0].tolist()
+    assert phs.phs_hmaxmin_order(_t(np.array([[0.2, 0.7]])), seed=1).cpu().numpy().tolist() == [0]
+
+
+def test_plan_hmaxmin_vecchia_matches_oracle(phs):
+    """The plan's hierarchical maximin ordering (normalised frame), its neighbour lists
+    and factor against the oracle."""
+    w_ = synth.workload("uniform_tps", n=3000)
+    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=30, opts=phs.options(2, seed=42, ordering=2))
+    order, nbr = plan.vecchia()
+    xn, _, _ = oracle.normalize(w_["points"], 0.25)
+    want, _ = oracle.hmaxmin_order(xn, 42)
+    assert np.array_equal(order, want)
+    assert np.array_equal(nbr, oracle.knn_prev(xn, order, 30))
+    d_g, o_g = plan.vecchia_factor()
+    d_w, o_w, _ = oracle.vecchia_factor(xn, order, nbr, 30, 1.0, 0.35)
+    _check_factor(d_g, o_g, d_w, o_w, _local_kappa(xn, nbr, 1.0, 0.35), xn, nbr, 1.0, 0.35)
+
+
 def _local_kappa(x, nbr, nu, alpha):
     """Condition number of the covariance of each point together with its conditioning
     set, K({x_i} u X_sigma): lambda and c of Eq. (2.19) are the last column of its
@@ -292,7 +321,7 @@ def test_vecchia_factor_matches_oracle(phs, nu, alpha):
 
 def test_plan_vecchia_matches_oracle(phs):
     w_ = synth.workload("uniform_tps", n=3000)
-    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=30, opts=phs.options(2, seed=42))
+    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=30, opts=phs.options(2, seed=42, ordering=0))
     order, nbr = plan.vecchia()
     xn, _, _ = oracle.normalize(w_["points"], 0.25)
     assert np.array_equal(order, oracle.random_order(3000, 42))

@@ -335,3 +335,42 @@ def test_pcg_converges_to_direct_solution():
     _, _, it_plain, _ = oracle.pcg(x, f, 2, 1, None, tol=1e-6, maxiter=2000)
     _, _, it_pre, _ = oracle.pcg(x, f, 2, 1, (nbr, d, o), tol=1e-6, maxiter=2000)
     assert it_plain > 5 * it_pre
+
+
+# ---------------------------------------------------------------- hierarchical maximin
+def test_hmaxmin_hand_worked_square():
+    """Corners of the unit square plus its centre (E = 1): level 0 picks the centre
+    (nearest to (1/2, 1/2)); at level 1 the centre's quadrant (1, 1) inherits it, so the
+    other three corners are picked there; the corner (1, 1) shares that quadrant and is
+    picked at level 2, where it and the centre fall in different cells ((3, 3) vs (2, 2))."""
+    x = np.array([[0, 0], [1, 0], [0, 1], [1, 1], [0.5, 0.5]], dtype=float)
+    order, level = oracle.hmaxmin_order(x, 3)
+    assert level.tolist() == [1, 1, 1, 2, 0]
+    assert order[0] == 4 and sorted(order[1:4].tolist()) == [0, 1, 2] and order[4] == 3
+    h = [oracle.splitmix64(3, i) >> 7 for i in (0, 1, 2)]
+    assert order[1:4].tolist() == [i for _, i in sorted(zip(h, (0, 1, 2)))]
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_hmaxmin_one_new_point_per_cell_per_level(clustered):
+    """Invariant of the definition: the points of level <= L are exactly one per
+    non-empty level-L cell, and the level-0 point is the point nearest the centre of
+    the bounding square (brute force)."""
+    rng = np.random.default_rng(21)
+    x = rng.random((2000, 2))
+    if clustered:
+        x[:600] = 0.3 + 0.01 * rng.standard_normal((600, 2))
+    order, level = oracle.hmaxmin_order(x, 5)
+    assert np.array_equal(np.sort(order), np.arange(len(x)))
+    assert np.all(np.diff(level[order]) >= 0)
+    xmin, ymin = x.min(0)
+    E = max(np.ptp(x[:, 0]), np.ptp(x[:, 1]))
+    ix = np.clip(np.floor((x[:, 0] - xmin) * (2.0 ** 30 / E)), 0, 2 ** 30 - 1).astype(np.int64)
+    iy = np.clip(np.floor((x[:, 1] - ymin) * (2.0 ** 30 / E)), 0, 2 ** 30 - 1).astype(np.int64)
+    for L in range(0, 31, 3):
+        cells = set(zip((ix >> (30 - L)).tolist(), (iy >> (30 - L)).tolist()))
+        picked = np.nonzero(level <= L)[0]
+        assert len(picked) == len(cells)
+        assert len(set(zip((ix[picked] >> (30 - L)).tolist(), (iy[picked] >> (30 - L)).tolist()))) == len(cells)
+    c = np.array([xmin + E / 2, ymin + E / 2])
+    assert order[0] == np.argmin(((x - c) ** 2).sum(1))
