@@ -47,7 +47,8 @@ typedef enum {
     PHS_ERR_OOM = 3,              /* device allocation failed */
     PHS_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed */
     PHS_ERR_NOT_CONVERGED = 5,    /* PCG reached maxiter above tolerance (results still written) */
-    PHS_ERR_CHOLESKY = 6,         /* a local Vecchia factor failed even after jitter */
+    PHS_ERR_CHOLESKY = 6,         /* a local Vecchia factor failed even after jitter, or the
+                                     S x S matrix Q' S~^{-1} Q of the low-rank term did */
     PHS_ERR_TIMEOUT = 7           /* reserved for bounded device waits */
 } phs_status;
 
@@ -83,6 +84,14 @@ typedef struct {
                                them in FP64 on the CUDA cores.  A bounded device wait of the
                                tensor-core path that expires is reported as PHS_ERR_TIMEOUT by
                                the next phs_fit or phs_eval (phs_matvec is asynchronous). */
+    int precond_lowrank;    /* 1: the preconditioner is the inverse of Q_perp' S~ Q_perp
+                               on range(P) (S~^{-1} = U U' the Vecchia factor), i.e.
+                               S~^{-1} r - G (B' G)^{-1} G' r with G = S~^{-1} B -- the low-rank
+                               (Schur complement) term of Sec. 2.2, built once per plan and
+                               applied at the cost of the projection it replaces; 0 (default):
+                               the plain Q_perp' S~^{-1} Q_perp that the paper runs (on the
+                               clustered 1M-point TPS workload the low-rank form takes one
+                               iteration more; on 4k-40k points one fewer). */
 } phs_options;
 
 typedef struct {

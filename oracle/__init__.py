@@ -19,6 +19,9 @@ What it computes, each function citing the passage it follows:
 * ``random_order``, ``maxmin_order``, ``hmaxmin_order``, ``knn_prev``, ``vecchia_factor``,
   ``vecchia_apply``       -- the Vecchia preconditioner of Sec. 2.2 (Eq. 2.19,
                              Fig. 1) with brute-force neighbour search.
+* ``projected_precond``   -- the preconditioner of the projected system, with or
+                             without the low-rank (Schur complement) term that
+                             Sec. 2.2 discusses and sets aside.
 * ``pcg``                 -- preconditioned CG on Q_perp^T M Q_perp (Sec. 2,
                              after Eq. 2.5; Sec. 2.2) with a dense matvec.
 
@@ -328,9 +331,35 @@ def vecchia_dense(nbr, diag, offd) -> np.ndarray:
 
 # --------------------------------------------------------------------------
 # preconditioned CG, Sec. 2 (after Eq. 2.5) and Sec. 2.2
-def pcg(x, f, k: int, deg: int, precond=None, tol: float = 1e-10, maxiter: int = 500, atol: float = 0.0):
+def projected_precond(x, deg: int, precond, v, lowrank: bool) -> np.ndarray:
+    """Preconditioner of the projected system (Sec. 2.2), applied to v in range(P),
+    P = I - Q Q^T.  With S~^{-1} = U~ U~^T the Vecchia approximation of the Matern
+    precision (Eq. 2.19, Fig. 1):
+
+    * lowrank = False: z = P S~^{-1} v, i.e. Q_perp^T S~^{-1} Q_perp, the form the
+      paper runs (it drops the Schur complement term of the inverse);
+    * lowrank = True:  z = S~^{-1} v - S~^{-1} B (B^T S~^{-1} B)^{-1} B^T S~^{-1} v,
+      the block-elimination (Schur complement) solution of the saddle-point system
+      [S~ B; B^T 0] [z; lam] = [v; 0], i.e. the inverse of Q_perp^T S~ Q_perp on
+      range(P) -- the "low-rank update" that Sec. 2.2 mentions and sets aside.
+
+    precond = (nbr, diag, offd)."""
+    x = _f64(x).reshape(-1, 2)
+    nbr, diag, offd = precond
+    t = vecchia_apply(nbr, diag, offd, v)
+    B = poly_basis(x, deg)
+    if lowrank:
+        G = np.stack([vecchia_apply(nbr, diag, offd, B[:, j]) for j in range(B.shape[1])], axis=1)
+        return t - G @ np.linalg.solve(B.T @ G, G.T @ v)
+    Q, _ = np.linalg.qr(B)
+    return t - Q @ (Q.T @ t)
+
+
+def pcg(x, f, k: int, deg: int, precond=None, tol: float = 1e-10, maxiter: int = 500, atol: float = 0.0,
+        lowrank: bool = False):
     """PCG for Q_perp^T M Q_perp u = Q_perp^T f with preconditioner
-    Q_perp^T U~ U~^T Q_perp, run on the iterates w = Q_perp u in R^n using
+    ``projected_precond`` (Q_perp^T U~ U~^T Q_perp, or with ``lowrank`` the inverse
+    of Q_perp^T S~ Q_perp), run on the iterates w = Q_perp u in R^n using
     Q_perp Q_perp^T = I - Q Q^T (Q from the thin QR of B).  x_0 = 0; stops when
     the recursive residual satisfies ||r_k|| <= max(tol ||Q_perp^T f||, atol).
     The system is multiplied by cpd_sign(k) so that CG sees a positive definite
@@ -350,7 +379,7 @@ def pcg(x, f, k: int, deg: int, precond=None, tol: float = 1e-10, maxiter: int =
     def prec(v):
         if precond is None:
             return v.copy()
-        return proj(vecchia_apply(precond[0], precond[1], precond[2], v))
+        return projected_precond(x, deg, precond, v, lowrank)
 
     w = np.zeros_like(f)
     r = sg * proj(f)

@@ -16,7 +16,8 @@ class PhsOptions(ctypes.Structure):
                 ("maxiter", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("ordering", ctypes.c_int),
                 ("nu", ctypes.c_double), ("alpha", ctypes.c_double), ("domain_halfwidth", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("fmm_eps", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("m2l_tensor", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("m2l_tensor", ctypes.c_int),
+                ("precond_lowrank", ctypes.c_int)]
 
 
 class PhsFitInfo(ctypes.Structure):

@@ -41,6 +41,8 @@ struct phs_plan {
     phs::Vecchia vec;
     phs::DBuf<double> Q;      // [S][n] sorted order
     phs::DBuf<double> R;      // S x S upper triangular, row-major
+    phs::DBuf<double> G;      // [S][n] S~^{-1} Q Rc^{-1}, Rc'Rc = Q' S~^{-1} Q (low-rank preconditioner term)
+    bool lowrank = false;
     phs::DBuf<double> work;   // 12 work vectors of n
     phs::DBuf<double> part;   // reduction partials
     phs::DBuf<double> scal;   // device scalars
@@ -456,12 +458,53 @@ static double read_scalar(phs_plan *pl, const double *dev, cudaStream_t s) {
     return pl->hscal[0];
 }
 
-// z = P U~ U~' r
+// Preconditioner of the projected system, r in range(P):
+//   plain:    z = P S~^{-1} r                       (S~^{-1} = U~ U~')
+//   low-rank: z = S~^{-1} r - G (G' r)              (the inverse of Q_perp' S~ Q_perp on range(P))
+// With G = S~^{-1} Q Rc^{-1} and Rc'Rc = Q' S~^{-1} Q, G G' = S~^{-1} Q (Q' S~^{-1} Q)^{-1} Q' S~^{-1},
+// the Schur complement term of block elimination on [S~ B; B' 0], and Q'z = 0 by construction.
+// Both forms cost one reduction over S basis vectors and one update pass after the factor apply.
 static void precond(phs_plan *pl, const double *r, double *z, double *tmp, double *tmp2, cudaStream_t s) {
     pl->tm.begin(s);
     vecchia_apply(pl->vec, r, tmp, tmp2, s);
     pl->tm.end(T_PRECOND, s);
-    project(pl, tmp2, 1.0, z, nullptr, nullptr, s);
+    if (!pl->lowrank) {
+        project(pl, tmp2, 1.0, z, nullptr, nullptr, s);
+        return;
+    }
+    const int64_t n = pl->ps.n;
+    double *coef = pl->scal.get() + 16;
+    qt_partial<<<RED_B, RED_T, 0, s>>>(pl->G.get(), pl->S, n, r, pl->part.get());
+    PHS_LAUNCH_CHECK();
+    dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, pl->S, coef);
+    PHS_LAUNCH_CHECK();
+    proj_apply<<<RED_B, RED_T, 0, s>>>(pl->G.get(), pl->S, n, coef, tmp2, 1.0, z, nullptr, nullptr);
+    PHS_LAUNCH_CHECK();
+}
+
+// G = U~ (U~' Q) Rc^{-1} with Rc the Cholesky factor of C = (U~' Q)'(U~' Q) = Q' S~^{-1} Q
+// (symmetric by construction).  Work vectors 0..S-1 hold U~' Q.
+static void build_lowrank(phs_plan *pl, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    const int S = pl->S;
+    PHS_REQUIRE(S <= MAXS, PHS_ERR_INVALID_ARG, "too many polynomial terms for the low-rank term");
+    pl->G.alloc((size_t)S * n);
+    double *Y = W(pl, 0);
+    for (int c = 0; c < S; ++c) vecchia_apply_ut(pl->vec, pl->Q.get() + (size_t)c * n, Y + (size_t)c * n, s);
+    DBuf<double> Rc((size_t)S * S);
+    DBuf<int> st(1);
+    gram_partial<<<RED_B, RED_T, 0, s>>>(Y, n, S, pl->part.get());
+    PHS_LAUNCH_CHECK();
+    gram_chol<<<1, 1, 0, s>>>(pl->part.get(), RED_B, S, Rc.get(), st.get());
+    PHS_LAUNCH_CHECK();
+    for (int c = 0; c < S; ++c) vecchia_apply_u(pl->vec, Y + (size_t)c * n, pl->G.get() + (size_t)c * n, s);
+    apply_rinv<<<blocks_for(n, 256), 256, 0, s>>>(pl->G.get(), n, S, Rc.get());
+    PHS_LAUNCH_CHECK();
+    int hs = 0;
+    PHS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_REQUIRE(hs == 0, PHS_ERR_CHOLESKY, "Q' S~^{-1} Q is not positive definite");
+    pl->lowrank = true;
 }
 
 // PCG on sign * P M' P x = rhs (rhs in range(P)), x0 = 0.  Returns iterations; *relres = ||r||/||rhs||.
@@ -558,6 +601,7 @@ void phs_options_default(phs_options *o, int k) {
     o->inner_tol = 1e-4;
     o->max_refine = 8;
     o->m2l_tensor = 1;
+    o->precond_lowrank = 0;
 }
 
 const char *phs_last_error(void) { return phs::last_error(); }
@@ -629,6 +673,7 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         // Vecchia preconditioner
         vecchia_build(pl->vec, pl->ps, vecchia_m, o.ordering, o.seed, o.nu, o.alpha, s);
         pl->work.alloc((size_t)12 * n);
+        if (o.precond_lowrank) build_lowrank(pl, s);
         PHS_CUDA(cudaStreamSynchronize(s));
     } catch (...) {
         delete pl;
@@ -732,6 +777,8 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
             if (it == 0) break;
         }
     }
+    // the low-rank preconditioner keeps the iterates in range(P) only up to rounding
+    if (pl->lowrank) project(pl, x, 1.0, x, nullptr, nullptr, s);
     // beta: R beta = Q' (f - M' w)
     matvec_norm(pl, x, y, 0, s);
     sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, fs, y, n);

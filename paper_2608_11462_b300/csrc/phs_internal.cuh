@@ -252,5 +252,8 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
                    double alpha, cudaStream_t s);
 // z = U~ (U~' r) (sorted order)
 void vecchia_apply(const Vecchia &v, const double *r, double *tmp, double *z, cudaStream_t s);
+// the two halves of z = U (U' r): y = U' r and z = U y
+void vecchia_apply_ut(const Vecchia &v, const double *r, double *y, cudaStream_t s);
+void vecchia_apply_u(const Vecchia &v, const double *y, double *z, cudaStream_t s);
 
 }  // namespace phs

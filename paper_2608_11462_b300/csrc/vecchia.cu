@@ -713,11 +713,17 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     PHS_CUDA(cudaStreamSynchronize(s));
 }
 
+void vecchia_apply_ut(const Vecchia &v, const double *r, double *y, cudaStream_t s) {
+    apply_ut<<<blocks_for(v.n, 256), 256, 0, s>>>(v.nbr.get(), v.val.get(), v.n, v.m, r, y);
+    PHS_LAUNCH_CHECK();
+}
+void vecchia_apply_u(const Vecchia &v, const double *y, double *z, cudaStream_t s) {
+    apply_u<<<blocks_for(v.n * 32, 256), 256, 0, s>>>(v.t_off.get(), v.t_col.get(), v.t_val.get(), v.n, y, z);
+    PHS_LAUNCH_CHECK();
+}
 void vecchia_apply(const Vecchia &v, const double *r, double *tmp, double *z, cudaStream_t s) {
-    apply_ut<<<blocks_for(v.n, 256), 256, 0, s>>>(v.nbr.get(), v.val.get(), v.n, v.m, r, tmp);
-    PHS_LAUNCH_CHECK();
-    apply_u<<<blocks_for(v.n * 32, 256), 256, 0, s>>>(v.t_off.get(), v.t_col.get(), v.t_val.get(), v.n, tmp, z);
-    PHS_LAUNCH_CHECK();
+    vecchia_apply_ut(v, r, tmp, s);
+    vecchia_apply_u(v, tmp, z, s);
 }
 
 }  // namespace phs

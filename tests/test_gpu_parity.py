@@ -331,20 +331,32 @@ def test_plan_vecchia_matches_oracle(phs):
     _check_factor(d_g, o_g, d_w, o_w, _local_kappa(xn, nbr, 1.0, 0.35), xn, nbr, 1.0, 0.35)
 
 
-def test_plan_precond_matches_oracle(phs):
-    w_ = synth.workload("uniform_tps", n=2000)
-    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=20)
+@pytest.mark.parametrize("lowrank", [0, 1])
+@pytest.mark.parametrize("wl,n", [("uniform_tps", 2000), ("tps_1m", 5003)])
+def test_plan_precond_matches_oracle(phs, lowrank, wl, n):
+    """Preconditioner of the projected system, plain (P S~^{-1} P) and with the
+    low-rank term (the inverse of Q_perp' S~ Q_perp), against the oracle on the
+    plan's own factor.  Error bound: the factor apply carries eps * kappa of the
+    local covariances; the low-rank form subtracts G (G' r) from t = S~^{-1} r, so
+    its absolute error scales with ||t||, not with the (possibly smaller) result."""
+    w_ = synth.workload(wl, n=n)
+    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=20, opts=phs.options(2, precond_lowrank=lowrank))
     xn, _, _ = oracle.normalize(w_["points"], 0.25)
     order, nbr = plan.vecchia()
     d, o, _ = oracle.vecchia_factor(xn, order, nbr, 20, 1.0, 0.35)
-    r = np.random.default_rng(0).standard_normal(2000)
+    r = np.random.default_rng(0).standard_normal(n)
     B = oracle.poly_basis(xn, 1)
     Q, _ = np.linalg.qr(B)
     P = lambda v: v - Q @ (Q.T @ v)  # noqa: E731
-    want = P(oracle.vecchia_apply(nbr, d, o, P(r)))
+    want = oracle.projected_precond(xn, 1, (nbr, d, o), P(r), bool(lowrank))
     got = plan.precond(_t(r)).cpu().numpy()
     kap = _local_kappa(xn, nbr, 1.0, 0.35).max()
-    assert np.linalg.norm(got - want) <= 64 * 2.2e-16 * kap * np.linalg.norm(want)
+    scale = np.linalg.norm(oracle.vecchia_apply(nbr, d, o, P(r))) if lowrank else np.linalg.norm(want)
+    err = np.linalg.norm(got - want)
+    assert err <= 64 * 2.2e-16 * kap * scale, (err, np.linalg.norm(want), scale, kap)
+    # the low-rank result lies in range(P) without a final projection
+    if lowrank:
+        assert np.linalg.norm(B.T @ got) <= 1e-9 * np.linalg.norm(B) * np.linalg.norm(got)
 
 
 # ---------------------------------------------------------------- fit and eval
@@ -379,6 +391,24 @@ def test_fit_uniform_tps_matches_dense_solve(phs, precision):
     # nodes are interpolated
     at_nodes = plan.eval(w, beta, _t(w_["points"])).cpu().numpy()
     assert np.max(np.abs(at_nodes - w_["f"])) <= 1e-8 * np.max(np.abs(w_["f"]))
+
+
+def test_lowrank_precond_fit_same_solution_fewer_iterations(phs):
+    """Clustered TPS workload (n = 40,000): with the low-rank term the PCG needs no
+    more iterations than the plain preconditioner, and both reach the same true
+    residual bound and interpolant."""
+    w_ = synth.workload("tps_1m", n=40000, n_targets=500)
+    pts, f, tg = _t(w_["points"]), _t(w_["f"]), _t(w_["targets"])
+    res = {}
+    for lowrank in (0, 1):
+        plan = phs.Plan(pts, 2, vecchia_m=30, opts=phs.options(2, tol=1e-8, precond_lowrank=lowrank))
+        w, beta, info = plan.fit(f)
+        assert info["converged"] == 1 and info["rel_res_true"] <= 2e-8
+        res[lowrank] = (info["iters"], plan.eval(w, beta, tg).cpu().numpy())
+        plan.close()
+    assert res[1][0] <= res[0][0], (res[0][0], res[1][0])
+    a, b = res[0][1], res[1][1]
+    assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(a))
 
 
 @pytest.mark.parametrize("k", [4])

@@ -313,7 +313,77 @@ def test_vecchia_apply_matches_dense_factor():
     assert np.allclose(oracle.vecchia_apply(nbr, diag, offd, r), U @ (U.T @ r), rtol=1e-13, atol=1e-12)
 
 
+# ---------------------------------------------------------------- projected preconditioner
+def _small_factor(n=60, m=8, seed=21, deg=1):
+    x = _pts(n, seed) * 0.5
+    order = oracle.random_order(n, 3)
+    nbr = oracle.knn_prev(x, order, m)
+    d, o, _ = oracle.vecchia_factor(x, order, nbr, m, 1.0, 4.0)
+    return x, (nbr, d, o)
+
+
+@pytest.mark.parametrize("deg", [1, 2])
+def test_lowrank_precond_solves_the_saddle_point_system(deg):
+    """Sec. 2.2's low-rank term: the preconditioned vector is the z-block of the dense
+    saddle-point solve [S~ B; B^T 0][z; lam] = [v; 0], with S~ = (U U^T)^{-1} formed and
+    the augmented matrix factored directly (no Schur formula)."""
+    x, fac = _small_factor(deg=deg)
+    n = len(x)
+    B = oracle.poly_basis(x, deg)
+    S = B.shape[1]
+    U = oracle.vecchia_dense(*fac)
+    St = np.linalg.inv(U @ U.T)
+    v = np.random.default_rng(4).standard_normal(n)
+    A = np.block([[St, B], [B.T, np.zeros((S, S))]])
+    want = np.linalg.solve(A, np.concatenate([v, np.zeros(S)]))[:n]
+    got = oracle.projected_precond(x, deg, fac, v, True)
+    assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want)
+    assert np.linalg.norm(B.T @ got) <= 1e-10 * np.linalg.norm(B) * np.linalg.norm(got)
+
+
+def test_lowrank_precond_inverts_the_projected_matern():
+    """On range(P) the low-rank form is the inverse of Q_perp^T S~ Q_perp (checked in
+    the coordinates of a complete QR of B); the plain form is Q_perp^T S~^{-1} Q_perp,
+    which differs from it (the two agree only when S~^{-1} maps range(B) to itself)."""
+    x, fac = _small_factor()
+    n = len(x)
+    B = oracle.poly_basis(x, 1)
+    Qc, _ = np.linalg.qr(B, mode="complete")
+    Qp = Qc[:, 3:]
+    U = oracle.vecchia_dense(*fac)
+    St = np.linalg.inv(U @ U.T)
+    u = np.random.default_rng(5).standard_normal(n - 3)
+    v = Qp @ u
+    z = oracle.projected_precond(x, 1, fac, v, True)
+    assert np.linalg.norm(Qp.T @ St @ Qp @ (Qp.T @ z) - u) <= 1e-8 * np.linalg.norm(u)
+    assert np.linalg.norm(z - Qp @ (Qp.T @ z)) <= 1e-10 * np.linalg.norm(z)
+    zp = oracle.projected_precond(x, 1, fac, v, False)
+    assert np.linalg.norm(zp - Qp @ (Qp.T @ (U @ (U.T @ v)))) <= 1e-12 * np.linalg.norm(zp)
+    assert np.linalg.norm(zp - z) > 1e-3 * np.linalg.norm(z)
+
+
 # ---------------------------------------------------------------- PCG
+@pytest.mark.parametrize("lowrank", [False, True])
+def test_pcg_converges_to_direct_solution_either_form(lowrank):
+    """Both preconditioner forms converge to the direct solution; the low-rank form
+    needs no more iterations than the plain one."""
+    w_ = synth.workload("uniform_tps", n=600, n_targets=10)
+    x, c, rho = oracle.normalize(w_["points"], 0.25)
+    f = w_["f"]
+    order = oracle.hmaxmin_order(x, 1)[0]
+    nbr = oracle.knn_prev(x, order, 30)
+    d, o, _ = oracle.vecchia_factor(x, order, nbr, 30, 1.0, 0.35)
+    w, beta, it, hist = oracle.pcg(x, f, 2, 1, (nbr, d, o), tol=1e-12, maxiter=200, lowrank=lowrank)
+    w0, b0 = oracle.solve_augmented(x, f, 2, 1)
+    assert hist[-1] <= 1e-12 * hist[0]
+    y = (w_["targets"] - c) * rho
+    a = oracle.interpolant(x, w, beta, 2, 1, y)
+    b = oracle.interpolant(x, w0, b0, 2, 1, y)
+    assert np.max(np.abs(a - b)) <= 1e-8 * np.max(np.abs(b))
+    _, _, it_plain, _ = oracle.pcg(x, f, 2, 1, (nbr, d, o), tol=1e-12, maxiter=200, lowrank=False)
+    assert it <= it_plain
+
+
 def test_pcg_converges_to_direct_solution():
     """Sec. 2.2 / Sec. 3: the Vecchia-preconditioned CG (nu = 1, alpha = 0.35,
     points in [-1/4,1/4]^2, m = 30, random order) converges in few iterations to
