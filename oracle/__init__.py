@@ -16,7 +16,8 @@ What it computes, each function citing the passage it follows:
                              pivoting (a library primitive).
 * ``solve_qperp``         -- the same system by the sequence (2.5) with an
                              explicit complete QR and a Cholesky factor.
-* ``random_order``, ``maxmin_order``, ``hmaxmin_order``, ``knn_prev``, ``vecchia_factor``,
+* ``random_order``, ``maxmin_order``, ``hmaxmin_order``, ``amaxmin_order``, ``knn_prev``,
+  ``vecchia_factor``,
   ``vecchia_apply``       -- the Vecchia preconditioner of Sec. 2.2 (Eq. 2.19,
                              Fig. 1) with brute-force neighbour search.
 * ``projected_precond``   -- the preconditioner of the projected system, with or
@@ -264,6 +265,105 @@ def hmaxmin_order(x, seed: int):
     h = np.array([splitmix64(seed, int(i)) >> 7 for i in range(n)], dtype=np.uint64)
     order = np.lexsort((idx, h, level))
     return order.astype(np.int64), level
+
+
+def amaxmin_order(x):
+    """Dyadic approximate maximin enumeration (for the ordering of Sec. 2.2), restated
+    from its definition.  An exact maxmin order appends, one at a time, the point
+    farthest from those already taken; this one appends whole batches, each point of a
+    batch at least half as far from the points already taken as the farthest remaining
+    one, so it can be built in parallel.  Definition:
+
+    * E, xmin, ymin and the level-30 integer coordinates ix, iy as in hmaxmin_order;
+      c_L = E 2^-L and the level-L cell of a point (ix >> (30 - L), iy >> (30 - L));
+    * the first point is the one nearest the square's centre (xmin + E/2, ymin + E/2),
+      ties to the smaller index; l2[i] = squared distance of i to the taken points
+      (FP64, dx*dx + dy*dy with one rounding per operation);
+    * for L = 0, 1, ..., 30, passes repeat while some untaken point has l2 >= c_L^2
+      (a candidate): in each level-L cell the candidate with the largest l2 (ties to the
+      smaller index) is eligible; eligible points are visited by (l2 descending, index)
+      and each is accepted unless an accepted point of the same pass lies at squared
+      distance < c_L^2; the accepted points are appended in that visiting order and
+      l2 is lowered by their distances;
+    * points still untaken after level 30 (coincident points) follow by (l2 descending,
+      index).
+
+    Returns (order, level, l2 at selection); the first point has level -1 and l2 = inf,
+    the tail level 31."""
+    from scipy.spatial import cKDTree
+
+    x = _f64(x).reshape(-1, 2)
+    n = x.shape[0]
+    idx = np.arange(n)
+    xmin, ymin = x[:, 0].min(), x[:, 1].min()
+    E = max(x[:, 0].max() - xmin, x[:, 1].max() - ymin)
+    if not E > 0:
+        E = 1.0
+    scale = 2.0 ** 30 / E
+    lim = 2 ** 30 - 1
+    ix = np.clip(np.floor((x[:, 0] - xmin) * scale), 0, lim).astype(np.int64)
+    iy = np.clip(np.floor((x[:, 1] - ymin) * scale), 0, lim).astype(np.int64)
+
+    def d2_to(p):
+        dx = x[:, 0] - p[0]
+        dy = x[:, 1] - p[1]
+        return dx * dx + dy * dy
+
+    d2c = d2_to((xmin + 0.5 * E, ymin + 0.5 * E))
+    root = int(np.lexsort((idx, d2c))[0])
+    taken = np.zeros(n, dtype=bool)
+    taken[root] = True
+    order, level, l2sel = [root], [-1], [np.inf]
+    l2 = d2_to(x[root])
+    for L in range(31):
+        cL = np.ldexp(E, -L)
+        c2 = cL * cL
+        sh = 30 - L
+        while True:
+            cand = np.nonzero(~taken & (l2 >= c2))[0]
+            if cand.size == 0:
+                break
+            cell = (ix[cand] >> sh) * (1 << 31) + (iy[cand] >> sh)
+            o = np.lexsort((cand, -l2[cand], cell))          # by cell, then l2 descending, then index
+            first = np.ones(cand.size, dtype=bool)
+            first[1:] = cell[o][1:] != cell[o][:-1]
+            elig = cand[o][first]
+            elig = elig[np.lexsort((elig, -l2[elig]))]        # visiting order
+            acc, grid = [], {}
+            for e in elig:
+                gx, gy = int(ix[e] >> sh), int(iy[e] >> sh)
+                ok = True
+                for ax in range(gx - 2, gx + 3):              # a conflict (distance < c_L) lies
+                    for ay in range(gy - 2, gy + 3):          # within one cell; two checked
+                        for a in grid.get((ax, ay), ()):
+                            dx = x[e, 0] - x[a, 0]
+                            dy = x[e, 1] - x[a, 1]
+                            if dx * dx + dy * dy < c2:
+                                ok = False
+                if ok:
+                    acc.append(int(e))
+                    grid.setdefault((gx, gy), []).append(int(e))
+            acc = np.array(acc, dtype=np.int64)
+            order.extend(acc.tolist())
+            level.extend([L] * acc.size)
+            l2sel.extend(l2[acc].tolist())
+            taken[acc] = True
+            rest = np.nonzero(~taken)[0]
+            if rest.size:
+                k = min(4, acc.size)
+                _, nb = cKDTree(x[acc]).query(x[rest], k=k)
+                nb = nb.reshape(rest.size, k)
+                for j in range(k):
+                    a = acc[nb[:, j]]
+                    dx = x[rest, 0] - x[a, 0]
+                    dy = x[rest, 1] - x[a, 1]
+                    l2[rest] = np.minimum(l2[rest], dx * dx + dy * dy)
+    rest = np.nonzero(~taken)[0]
+    rest = rest[np.lexsort((rest, -l2[rest]))]
+    order.extend(rest.tolist())
+    level.extend([31] * rest.size)
+    l2sel.extend(l2[rest].tolist())
+    return np.array(order, dtype=np.int64), np.array(level, dtype=np.int64), np.array(l2sel)
 
 
 def knn_prev(x, order, m: int) -> np.ndarray:

@@ -444,3 +444,88 @@ def test_hmaxmin_one_new_point_per_cell_per_level(clustered):
         assert len(set(zip((ix[picked] >> (30 - L)).tolist(), (iy[picked] >> (30 - L)).tolist()))) == len(cells)
     c = np.array([xmin + E / 2, ymin + E / 2])
     assert order[0] == np.argmin(((x - c) ** 2).sum(1))
+
+
+# ---------------------------------------------------------------- dyadic approximate maximin
+def _prefix_ratios(x, order):
+    """Brute force: for each rank k >= 1, the squared distance of order[k] to the
+    points of smaller rank, and the largest such distance over all points of rank >= k."""
+    n = len(order)
+    d2 = ((x[:, None, :] - x[None, :, :]) ** 2).sum(-1)
+    dmin = np.full(n, np.inf)
+    got, best = [], []
+    for k in range(n):
+        p = order[k]
+        if k:
+            rest = order[k:]
+            got.append(dmin[p])
+            best.append(dmin[rest].max())
+        dmin = np.minimum(dmin, d2[p])
+    return np.array(got), np.array(best)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered", "lattice"])
+def test_amaxmin_half_maximin_property(kind):
+    """Each point, when appended, is at least half as far from the points before it as
+    the farthest point still to come (exact maxmin: equally far); checked by brute
+    force, independently of the level/pass bookkeeping."""
+    rng = np.random.default_rng(7)
+    if kind == "uniform":
+        x = rng.random((700, 2))
+    elif kind == "clustered":
+        c = rng.random((6, 2))
+        x = np.concatenate([rng.random((300, 2)), (c[:, None, :] + 0.01 * rng.standard_normal((6, 60, 2))).reshape(-1, 2)])
+    else:
+        g = np.arange(24) / 23.0
+        x = np.stack(np.meshgrid(g, g), -1).reshape(-1, 2)
+    order, level, l2 = oracle.amaxmin_order(x)
+    assert sorted(order.tolist()) == list(range(len(x)))
+    got, best = _prefix_ratios(x, order)
+    assert np.all(got >= 0.25 * best * (1 - 1e-12)), np.min(got / best)
+    # the recorded selection distance is the one at the start of the point's pass:
+    # points accepted before it in the same pass can only be closer
+    assert np.all(got <= l2[1:])
+    first_of_pass = np.r_[True, (level[2:] != level[1:-1]) | (l2[2:] > l2[1:-1])]
+    assert np.array_equal(got[first_of_pass], l2[1:][first_of_pass])
+    # levels are non-decreasing along the order, and at level L the selection distance
+    # is in [c_L, 2 c_L)
+    assert np.all(np.diff(level) >= 0)
+    E = max(np.ptp(x[:, 0]), np.ptp(x[:, 1]))
+    c = E * 2.0 ** -level[1:].astype(float)
+    assert np.all(got >= c * c) and np.all(got < 4 * c * c)
+
+
+def test_amaxmin_hand_worked_line():
+    """Five points on a line, E = 1: the first is 0.5 (nearest the centre (0.5, 0));
+    level 0 (c = 1) has no candidate; level 1 (c = 1/2): 0 and 1 are 0.5 away, in
+    different cells, accepted in index order (ties); level 2 (c = 1/4): 0.3 is 0.2 from
+    0.5 (< 1/4, no), 0.8 is 0.2 from 1 (no): level 3 (c = 1/8): both candidates,
+    different cells, 0.3 (l2 = 0.04) and 0.8 (l2 = 0.04) tie, index order."""
+    x = np.array([[0.0, 0.0], [0.3, 0.0], [0.5, 0.0], [0.8, 0.0], [1.0, 0.0]])
+    order, level, l2 = oracle.amaxmin_order(x)
+    assert order.tolist() == [2, 0, 4, 1, 3]
+    assert level.tolist() == [-1, 1, 1, 3, 3]
+
+
+def test_amaxmin_one_eligible_point_per_cell():
+    """A = (0.5, 0.5) is first (the centre).  At level 1 (c = 1/2, c^2 = 1/4) B = (0, 0)
+    and C = (0.2, 0) share cell (0, 0) and are both candidates (l2 = 0.5 and 0.34); only
+    B, the farther, is eligible; D = (1, 1) in cell (1, 1) is accepted in the same pass
+    (ties with B on l2 = 0.5, larger index).  C is then 0.2 from B (l2 = 0.04) and is
+    first a candidate at level 3 (c^2 = 1/64)."""
+    x = np.array([[0.5, 0.5], [0.0, 0.0], [0.2, 0.0], [1.0, 1.0]])
+    order, level, _ = oracle.amaxmin_order(x)
+    assert order.tolist() == [0, 1, 3, 2]
+    assert level.tolist() == [-1, 1, 1, 3]
+
+
+def test_amaxmin_conflict_between_adjacent_cells():
+    """A = (0.5, 0.5) first.  At level 1 the eligible points R = (0, 1), S = (1, 1)
+    (l2 = 0.5), P = (0.45, 0) and Q = (0.55, 0) (l2 = 0.2525) sit in four different
+    cells and are visited R, S, P, Q; Q is 0.1 from the accepted P (0.01 < c^2 = 1/4),
+    so it is rejected, its l2 drops to 0.01 and it waits until level 4 (c^2 = 1/256)."""
+    x = np.array([[0.5, 0.5], [0.45, 0.0], [0.55, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    order, level, l2 = oracle.amaxmin_order(x)
+    assert order.tolist() == [0, 3, 4, 1, 2]
+    assert level.tolist() == [-1, 1, 1, 1, 4]
+    assert l2[4] == (0.55 - 0.45) ** 2
