@@ -27,10 +27,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PCG fit time to 1e-8 at n=1M TPS"
 WORKLOAD = "tps_1m"
-# Preconditioner covariance: Matern nu = 1 with alpha = 0.35 in the normalised frame
-# [-1/4,1/4]^2 (Sec. 2.2: the nu = 1 kernel carries the thin-plate term, Eq. 2.17).
-# nu = 1.5 fails to converge within 200 iterations at this size for alpha in {5, 20, 60}.
-NU, ALPHA = 1.0, 0.35
+# Preconditioner covariance: Matern nu = 1 in the normalised frame [-1/4,1/4]^2 (Sec. 2.2:
+# the nu = 1 kernel carries the thin-plate term, Eq. 2.17).  alpha is the tuning knob of
+# Sec. 2.2 (the paper settles on 0.35 for its sets); on this clustered set with the
+# approximate maximin order, alpha = 0.03 needs 12 PCG iterations against 14 at 0.35
+# (0.01-0.03 are equal; at 0.003 and below the local covariances need jitter and the
+# count rises).  nu = 1.5 fails to converge within 200 iterations for alpha in {5, 20, 60}.
+NU, ALPHA = 1.0, 0.03
 # DRAM bytes (read + write) per launch from ncu captures summarised under profiles/,
 # taken on the n = 262144 case of this workload and scaled to the bench size: the
 # tensor-core M2L by its tile count (618 tiles there), the near field by the point count.
@@ -48,8 +51,9 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the point count (smaller parity runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--leaf-cap", type=int, default=64, help="quadtree leaf capacity")
-    ap.add_argument("--ordering", type=int, default=2, choices=[0, 1, 2],
-                    help="Vecchia enumeration: 0 random, 1 exact maxmin, 2 hierarchical maximin")
+    ap.add_argument("--ordering", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="Vecchia enumeration: 0 random, 1 exact maxmin, 2 hierarchical maximin, "
+                         "3 dyadic approximate maximin")
     return ap.parse_args()
 
 
@@ -117,7 +121,7 @@ class ClockSampler:
 # --------------------------------------------------------------------------- CPU oracle leg
 def oracle_step(points, f, targets, n_sample, seed=0):
     """The oracle as it stands on a bounded random subsample: normalisation,
-    hierarchical maximin order, brute-force neighbours, Vecchia factor, dense-matvec PCG to 1e-8, dense
+    approximate maximin order, brute-force neighbours, Vecchia factor, dense-matvec PCG to 1e-8, dense
     evaluation at the targets.  Returns (seconds, n_sample, iterations)."""
     import numpy as np
 
@@ -127,7 +131,7 @@ def oracle_step(points, f, targets, n_sample, seed=0):
     p, fs = points[idx], f[idx]
     t0 = time.perf_counter()
     xn, c, rho = oracle.normalize(p, 0.25)
-    order, _ = oracle.hmaxmin_order(xn, 1)
+    order, _, _ = oracle.amaxmin_order(xn)
     nbr = oracle.knn_prev(xn, order, 30)
     d, o, _ = oracle.vecchia_factor(xn, order, nbr, 30, NU, ALPHA)
     w, beta, it, _ = oracle.pcg(xn, fs, 2, 1, (nbr, d, o), tol=1e-8, maxiter=300)
@@ -317,7 +321,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
         "fits_per_s": world / t_step,
         "config": {"workload": WORKLOAD, "n": n, "targets": m_t, "k": 2, "poly_degree": 1, "vecchia_m": 30,
-                   "nu": NU, "alpha_normalised": ALPHA, "ordering": ["random", "maxmin", "hierarchical maximin"][args.ordering], "leaf_cap": args.leaf_cap, "fmm_order": sizes[3],
+                   "nu": NU, "alpha_normalised": ALPHA, "ordering": ["random", "maxmin", "hierarchical maximin", "approximate maximin"][args.ordering], "leaf_cap": args.leaf_cap, "fmm_order": sizes[3],
                    "precision_mode": args.precision, "tol": 1e-8, "parallelism": f"replicas{world}",
                    "l2": "flushed (256 MB write) between timed steps"},
         "pcg": {"iters": info["iters"], "outer_iters": info["outer_iters"], "converged": info["converged"],

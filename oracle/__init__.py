@@ -350,7 +350,7 @@ def amaxmin_order(x):
             taken[acc] = True
             rest = np.nonzero(~taken)[0]
             if rest.size:
-                k = min(4, acc.size)
+                k = min(8, acc.size)
                 _, nb = cKDTree(x[acc]).query(x[rest], k=k)
                 nb = nb.reshape(rest.size, k)
                 for j in range(k):

@@ -15,7 +15,7 @@ from . import _native
 from ._native import PhsError, PhsFitInfo, PhsOptions, check, lib
 
 __all__ = ["Plan", "PhsError", "PhsOptions", "PhsFitInfo", "options", "phs_dense_matvec", "phs_random_order",
-           "phs_maxmin_order", "phs_hmaxmin_order", "phs_knn_prev", "phs_vecchia_factor", "phs_fit_predict_host", "lib"]
+           "phs_maxmin_order", "phs_hmaxmin_order", "phs_amaxmin_order", "phs_knn_prev", "phs_vecchia_factor", "phs_fit_predict_host", "lib"]
 
 
 def _stream(stream=None):
@@ -178,6 +178,13 @@ def phs_hmaxmin_order(points: torch.Tensor, seed: int = 1, stream=None) -> torch
     pts = _dev(points, name="points")
     out = torch.empty(pts.shape[0], dtype=torch.int64, device=pts.device)
     check(lib().phs_hmaxmin_order(_ptr(pts), pts.shape[0], ctypes.c_uint64(seed), _ptr(out), _stream(stream)))
+    return out
+
+
+def phs_amaxmin_order(points: torch.Tensor, stream=None) -> torch.Tensor:
+    pts = _dev(points, name="points")
+    out = torch.empty(pts.shape[0], dtype=torch.int64, device=pts.device)
+    check(lib().phs_amaxmin_order(_ptr(pts), pts.shape[0], _ptr(out), _stream(stream)))
     return out
 
 

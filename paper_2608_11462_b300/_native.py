@@ -35,7 +35,8 @@ EXPORTS = [
     "phs_fit_predict_host", "phs_plan_destroy", "phs_plan_frame", "phs_plan_vecchia", "phs_plan_vecchia_factor",
     "phs_plan_precond", "phs_plan_work", "phs_plan_kernel_work", "phs_plan_set_timing", "phs_plan_timing", "phs_dense_matvec",
     "phs_dense_matvec_noalloc",
-    "phs_random_order", "phs_maxmin_order", "phs_hmaxmin_order", "phs_knn_prev", "phs_vecchia_factor",
+    "phs_random_order", "phs_maxmin_order", "phs_hmaxmin_order", "phs_amaxmin_order", "phs_knn_prev",
+    "phs_vecchia_factor",
 ]
 
 _lib = None
@@ -74,6 +75,7 @@ def lib():
         "phs_random_order": (st, [i64, u64, P, P]),
         "phs_maxmin_order": (st, [P, i64, P, P]),
         "phs_hmaxmin_order": (st, [P, i64, ctypes.c_uint64, P, P]),
+        "phs_amaxmin_order": (st, [P, i64, P, P]),
         "phs_knn_prev": (st, [P, i64, P, i32, P, P]),
         "phs_vecchia_factor": (st, [P, i64, P, P, i32, d, d, P, P, P, P]),
     }

@@ -591,7 +591,7 @@ void phs_options_default(phs_options *o, int k) {
     o->atol = 0.0;
     o->maxiter = 200;
     o->leaf_cap = 64;
-    o->ordering = 2;
+    o->ordering = 3;
     // Matern smoothness k/2: its leading non-analytic term is r^k (log r), the PHS kernel
     o->nu = 0.5 * (k < 1 ? 2 : k);
     o->alpha = k >= 4 ? 0.5 : 0.35;
@@ -632,7 +632,7 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         const phs_options &o = pl->opt;
         PHS_REQUIRE(o.tol > 0 && o.maxiter >= 1 && o.precision >= 0 && o.precision <= 3, PHS_ERR_INVALID_ARG,
                     "bad solver options");
-        PHS_REQUIRE(o.ordering >= 0 && o.ordering <= 2, PHS_ERR_INVALID_ARG, "ordering must be 0, 1 or 2");
+        PHS_REQUIRE(o.ordering >= 0 && o.ordering <= 3, PHS_ERR_INVALID_ARG, "ordering must be 0, 1, 2 or 3");
         int p = fmm_order;
         if (p <= 0) {
             PHS_REQUIRE(o.fmm_eps > 0 && o.fmm_eps < 1, PHS_ERR_INVALID_ARG, "fmm_eps must be in (0,1)");
@@ -1059,6 +1059,22 @@ phs_status phs_hmaxmin_order(const double *pts_dev, int64_t n, uint64_t seed, in
     PHS_LAUNCH_CHECK();
     DBuf<int> o(n);
     hmaxmin_order_dev(x.get(), n, seed, o.get(), s);
+    to_i64<<<blocks_for(n, 256), 256, 0, s>>>(o.get(), n, order_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_CATCH
+}
+
+phs_status phs_amaxmin_order(const double *pts_dev, int64_t n, int64_t *order_dev, phs_stream_t stream) {
+    PHS_TRY
+    PHS_REQUIRE(pts_dev && order_dev && n >= 0 && n < (1ll << 31) - 1, PHS_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return PHS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<double2> x(n);
+    pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
+    PHS_LAUNCH_CHECK();
+    DBuf<int> o(n);
+    amaxmin_order_dev(x.get(), n, o.get(), s);
     to_i64<<<blocks_for(n, 256), 256, 0, s>>>(o.get(), n, order_dev);
     PHS_LAUNCH_CHECK();
     PHS_CUDA(cudaStreamSynchronize(s));

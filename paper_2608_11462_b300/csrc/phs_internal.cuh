@@ -244,7 +244,9 @@ struct Vecchia {
 };
 void random_order_dev(int64_t n, uint64_t seed, int *order_out, cudaStream_t s);
 void maxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t s);
-void hmaxmin_order_dev(const double2 *x, int64_t n, uint64_t seed, int *order_out, cudaStream_t s);  // hmaxmin.cu
+// maximin.cu
+void hmaxmin_order_dev(const double2 *x, int64_t n, uint64_t seed, int *order_out, cudaStream_t s);
+void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t s);
 void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr_ell, cudaStream_t s);
 int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m,
                            double nu, double alpha, double *val_ell, cudaStream_t s);

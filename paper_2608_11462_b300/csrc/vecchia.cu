@@ -661,7 +661,8 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     DBuf<int> order_c(n);
     if (ordering == 0) random_order_dev(n, seed, order_c.get(), s);
     else if (ordering == 1) maxmin_order_dev(xcal.get(), n, order_c.get(), s);
-    else hmaxmin_order_dev(xcal.get(), n, seed, order_c.get(), s);
+    else if (ordering == 2) hmaxmin_order_dev(xcal.get(), n, seed, order_c.get(), s);
+    else amaxmin_order_dev(xcal.get(), n, order_c.get(), s);
     DBuf<int> nbr_c((size_t)m * n);
     knn_prev_dev(xcal.get(), n, order_c.get(), m, nbr_c.get(), s);
     DBuf<int> rank_c(n);

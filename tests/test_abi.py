@@ -40,14 +40,14 @@ def test_options_default_host_only(native):
     o = native.PhsOptions()
     native.lib().phs_options_default(ctypes.byref(o), 2)
     assert o.tol == 1e-8 and o.domain_halfwidth == 0.25 and abs(o.alpha - 0.35) < 1e-15 and o.nu == 1.0
-    assert o.m2l_tensor == 1 and o.precond_lowrank == 0 and o.ordering == 2
+    assert o.m2l_tensor == 1 and o.precond_lowrank == 0 and o.ordering == 3
     # the ctypes mirror is as large as the C struct: phs_options_default clears
     # sizeof(phs_options) bytes, so nothing past the mirror's size may change
     size = ctypes.sizeof(native.PhsOptions)
     buf = (ctypes.c_ubyte * (size + 64))(*([0xA5] * (size + 64)))
     native.lib().phs_options_default(ctypes.cast(buf, ctypes.POINTER(native.PhsOptions)), 2)
     assert bytes(buf[size:]) == bytes([0xA5] * 64)
-    assert ctypes.cast(buf, ctypes.POINTER(native.PhsOptions)).contents.ordering == 2
+    assert ctypes.cast(buf, ctypes.POINTER(native.PhsOptions)).contents.ordering == 3
     native.lib().phs_options_default(ctypes.byref(o), 4)
     assert o.domain_halfwidth == 1.0 and o.alpha == 0.5 and o.nu == 2.0
     native.lib().phs_options_default(ctypes.byref(o), 3)

@@ -228,6 +228,56 @@ def test_plan_hmaxmin_vecchia_matches_oracle(phs):
     _check_factor(d_g, o_g, d_w, o_w, _local_kappa(xn, nbr, 1.0, 0.35), xn, nbr, 1.0, 0.35)
 
 
+@pytest.mark.parametrize("kind", ["uniform", "clustered", "lattice", "duplicates", "tps_1m"])
+def test_amaxmin_order_bit_exact(phs, kind):
+    """Dyadic approximate maximin: GPU order identical to the oracle's, including ties
+    on a lattice and coincident points (which come last, by distance then index)."""
+    rng = np.random.default_rng(41)
+    if kind == "uniform":
+        pts = rng.random((20000, 2))
+    elif kind == "clustered":
+        pts = _clustered(20000, 33)
+    elif kind == "lattice":
+        g = np.arange(90) / 89.0
+        pts = np.stack(np.meshgrid(g, g), -1).reshape(-1, 2)
+    elif kind == "duplicates":
+        pts = rng.random((3000, 2))
+        pts = np.concatenate([pts, pts[:40], pts[:5]])
+    else:
+        pts = synth.workload("tps_1m", n=30011)["points"]
+    got = phs.phs_amaxmin_order(_t(pts)).cpu().numpy()
+    want, level, _ = oracle.amaxmin_order(pts)
+    assert np.array_equal(got, want)
+    if kind == "duplicates":
+        assert np.sum(level == 31) == 45
+
+
+def test_amaxmin_order_small_cases(phs):
+    cases = [np.array([[0.2, 0.7]]), np.array([[0.2, 0.7], [0.3, 0.1]]),
+             np.array([[0.0, 0.0], [0.3, 0.0], [0.5, 0.0], [0.8, 0.0], [1.0, 0.0]]),
+             np.array([[0.5, 0.5], [0.45, 0.0], [0.55, 0.0], [0.0, 1.0], [1.0, 1.0]]),
+             np.array([[0.5, 0.5], [0.0, 0.0], [0.2, 0.0], [1.0, 1.0]]),
+             np.zeros((6, 2))]
+    for x in cases:
+        got = phs.phs_amaxmin_order(_t(x)).cpu().numpy().tolist()
+        assert got == oracle.amaxmin_order(x)[0].tolist(), x
+
+
+def test_plan_amaxmin_vecchia_matches_oracle(phs):
+    """The plan's approximate maximin ordering (normalised frame), its neighbour lists
+    and factor against the oracle."""
+    w_ = synth.workload("tps_1m", n=4000)
+    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=30, opts=phs.options(2, ordering=3))
+    order, nbr = plan.vecchia()
+    xn, _, _ = oracle.normalize(w_["points"], 0.25)
+    want, _, _ = oracle.amaxmin_order(xn)
+    assert np.array_equal(order, want)
+    assert np.array_equal(nbr, oracle.knn_prev(xn, order, 30))
+    d_g, o_g = plan.vecchia_factor()
+    d_w, o_w, _ = oracle.vecchia_factor(xn, order, nbr, 30, 1.0, 0.35)
+    _check_factor(d_g, o_g, d_w, o_w, _local_kappa(xn, nbr, 1.0, 0.35), xn, nbr, 1.0, 0.35)
+
+
 def _local_kappa(x, nbr, nu, alpha):
     """Condition number of the covariance of each point together with its conditioning
     set, K({x_i} u X_sigma): lambda and c of Eq. (2.19) are the last column of its
