@@ -161,11 +161,13 @@ constexpr int kSerTerms = 14;
 constexpr int kCoshTab = 64;
 __constant__ double c_s1[kSerTerms], c_p1[kSerTerms], c_s0[kSerTerms], c_h0[kSerTerms], c_cosh[kCoshTab];
 
-// terms for a truncation below 1e-16 relative: q^n / (n!)^2 at the bound of each class
+// terms for a truncation below 1e-16 relative: q^n / (n!)^2 at the bound of each class.
+// The class bounds are powers of two, so q < 2^k is a compare of the high words (q > 0),
+// which keeps these decisions off the FP64 pipe.
 __device__ __forceinline__ int ser_terms(double q) {
-    return q <= 3.814697265625e-06 ? 3 : (q <= 6.103515625e-05 ? 4 : (q <= 0.015625 ? 6 : (q <= 0.125 ? 9 : kSerTerms)));
+    const int hi = __double2hiint(q);
+    return hi < 0x3ED00000 ? 3 : (hi < 0x3F100000 ? 4 : (hi < 0x3F900000 ? 6 : (hi < 0x3FC00000 ? 9 : kSerTerms)));
 }
-
 // Table-driven FP64 logarithm for the series (P. T. P. Tang, ACM TOMS 16(4), 1990):
 // x = 2^e m, F_j = 1 + j/2048 nearest m, log x = e log 2 + log F_j + log(1 + r) with
 // r = m/F_j - 1 (|r| < 2^-12) and a three-term log(1 + r); exponents below 2^-255 clamp
@@ -206,24 +208,26 @@ __device__ __forceinline__ void bessel_quad(double a, double &k0, double &ak1) {
     ak1 = a * 0.25 * s1;
 }
 
-// Matern with K(0) = 1 as a function of q = (alpha r)^2 / 4 (q > 0)
-__device__ __forceinline__ double matern_q(double nu, double q) {
-    if (nu == 0.5 || nu == 1.5 || nu == 2.5) {
+// Matern with K(0) = 1 as a function of q = (alpha r)^2 / 4 (q > 0); NUC selects
+// nu = 0.5, 1, 1.5, 2, 2.5 at compile time
+template <int NUC>
+__device__ __forceinline__ double matern_q(double q) {
+    if (NUC == 0 || NUC == 2 || NUC == 4) {
         const double a = 2.0 * sqrt(q), e = exp(-a);
-        if (nu == 0.5) return e;
-        if (nu == 1.5) return (1.0 + a) * e;
+        if (NUC == 0) return e;
+        if (NUC == 2) return (1.0 + a) * e;
         return (1.0 + a + a * a / 3.0) * e;
     }
     double k0, ak1;
-    if (q <= 1.0) {
+    if (__double2hiint(q) < 0x3FF00000) {  // q < 1
         const int nt = ser_terms(q);
         const double lq = vtab_log(q);
-        ak1 = 1.0 + q * (lq * horner(c_s1, nt, q) - horner(c_p1, nt, q));
-        if (nu == 1.0) return ak1;
-        k0 = -(0.5 * lq + 0.57721566490153286061) * horner(c_s0, nt, q) + horner(c_h0, nt, q);
+        ak1 = fma(q, fma(lq, horner(c_s1, nt, q), -horner(c_p1, nt, q)), 1.0);
+        if (NUC == 1) return ak1;
+        k0 = fma(-(0.5 * lq + 0.57721566490153286061), horner(c_s0, nt, q), horner(c_h0, nt, q));
     } else {
         bessel_quad(2.0 * sqrt(q), k0, ak1);
-        if (nu == 1.0) return ak1;
+        if (NUC == 1) return ak1;
     }
     return 2.0 * q * k0 + ak1;  // nu = 2: a^2 K_2(a) / 2 = a^2 K_0(a) / 2 + a K_1(a)
 }
@@ -267,31 +271,47 @@ static void upload_bessel_tables() {
     PHS_CUDA(cudaMemcpyToSymbol(c_cosh, ch, sizeof(ch)));
 }
 
-// Warp per point: local Cholesky of K(X_sigma, X_sigma), lambda and c (Eq. 2.19).
-// The lower triangle (row stride ld, odd) lives in shared memory; lane a owns row a
-// of the right-looking updates and entries a, a + 32 of the triangular solves.
+// 1/d for normal d > 0: the hardware approximation rcp.approx.ftz.f64 refined by three
+// Newton-Raphson steps r <- r + r (1 - d r) (each squares the relative error; Markstein,
+// IBM J. Res. Dev. 34(1), 1990), ending at the FP64 rounding level.
+__device__ __forceinline__ double recip_nr(double d) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r = fma(r, fma(-d, r, 1.0), r);
+    return r;
+}
+
+// Warp per point i with conditioning set sigma (s = |sigma| points): LDL' of the
+// (s+1) x (s+1) covariance of (X_sigma, x_i), the point itself last (Eq. 2.19).  With
+// K = [K_ss k; k' 1] = L D L' (L unit lower), row s of L is (D^-1 L_ss^-1 k)' and its
+// last pivot is c = 1 - k' K_ss^-1 k, so the elimination itself does the forward solve;
+// lambda = K_ss^-1 k is one unit-diagonal back solve with that row.  The lower triangle
+// (row stride ld, odd) lives in shared memory; the trailing update is spread over the
+// entries (not the rows) so every lane has the same work; the FP64 pipe is the bound, so
+// every warp instruction on it counts: pivots are reciprocals (recip_nr), distances use
+// coordinates pre-scaled by alpha/2 (q = dx^2 + dy^2) and the nu dispatch is static.
+template <int NUC>
 __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, int ld,
-                              double nu, double alpha, double *val_ell, unsigned long long *njit) {
+                              double halpha, double *val_ell, unsigned long long *njit) {
     extern __shared__ double fsm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int per = m * ld + 3 * m;
+    const int per = (m + 1) * ld + 3 * (m + 1);
     double *A = fsm + (size_t)wib * per;
-    double *rd = A + m * ld;  // reciprocal pivots
-    double *X = rd + m;
-    double *Y = X + m;
+    double *W = A + (m + 1) * ld;  // column j before scaling by 1/d_j
+    double *X = W + (m + 1);
+    double *Y = X + (m + 1);
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (i >= n) return;
     const unsigned full = 0xffffffffu;
     const int s = min(m, rank[i]);
-    const double2 xi = x[i];
-    for (int a = lane; a < s; a += 32) {
-        const int j = nbr_ell[(int64_t)a * n + i];
-        X[a] = x[j].x;
-        Y[a] = x[j].y;
+    for (int a = lane; a <= s; a += 32) {
+        const double2 p = a < s ? x[nbr_ell[(int64_t)a * n + i]] : x[i];
+        X[a] = p.x * halpha;
+        Y[a] = p.y * halpha;
     }
     __syncwarp();
-    const double c2 = 0.25 * alpha * alpha;  // q = c2 r^2
-    const int ntri = s * (s + 1) / 2;
+    const int nn = s + 1, ntri = nn * (nn + 1) / 2;
     bool ok = false;
     int tries = 0;
     for (int t = 0; t <= 7 && !ok; ++t) {
@@ -301,48 +321,42 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
             while (a * (a + 1) / 2 > idx) --a;
             while ((a + 1) * (a + 2) / 2 <= idx) ++a;
             const int b = idx - a * (a + 1) / 2;
-            double v = 1.0 + jit;
-            if (b != a) {
+            double v;
+            if (b == a) {
+                v = a < s ? 1.0 + jit : 1.0;  // jitter on K_ss only
+            } else {
                 const double dx = X[a] - X[b], dy = Y[a] - Y[b];
-                const double q = c2 * (dx * dx + dy * dy);
-                v = q > 0.0 ? matern_q(nu, q) : 1.0;
+                const double q = fma(dx, dx, dy * dy);
+                v = __double2hiint(q) > 0 ? matern_q<NUC>(q) : 1.0;
             }
             A[a * ld + b] = v;
         }
         __syncwarp();
         ok = true;
         for (int j = 0; j < s; ++j) {
-            double dj = 0.0, rj = 0.0;
-            if (lane == 0) {
-                const double d = A[j * ld + j];
-                if (d > 0.0) {
-                    dj = sqrt(d);
-                    rj = 1.0 / dj;
-                    A[j * ld + j] = dj;
-                    rd[j] = rj;
-                }
+            const double d = A[j * ld + j];  // same value in every lane: the branch is uniform
+            if (!(d >= 2.2250738585072014e-308)) { ok = false; break; }
+            const double r = recip_nr(d);
+            for (int a = j + 1 + lane; a <= s; a += 32) {
+                const double w = A[a * ld + j];
+                W[a] = w;
+                A[a * ld + j] = w * r;
             }
-            rj = __shfl_sync(full, rj, 0);
-            if (!(rj > 0.0)) { ok = false; break; }
-            for (int a = j + 1 + lane; a < s; a += 32) A[a * ld + j] *= rj;
             __syncwarp();
-            // trailing update over the entries (not the rows) of the lower triangle, so every
-            // lane has the same work: entry t = a'(a'+1)/2 + c', c' <= a', of the trailing block
-            {
-                const int mm = s - j - 1, ntr = mm * (mm + 1) / 2;
-                int ap = 0, cp = lane;
+            // entry t = a'(a'+1)/2 + c', c' <= a', of the trailing block (rows and columns j+1..s)
+            const int mm = s - j, ntr = mm * (mm + 1) / 2;
+            int ap = 0, cp = lane;
+            while (cp > ap) {
+                cp -= ap + 1;
+                ++ap;
+            }
+            for (int e = lane; e < ntr; e += 32) {
+                const int a = j + 1 + ap, c = j + 1 + cp;
+                A[a * ld + c] = fma(-A[a * ld + j], W[c], A[a * ld + c]);
+                cp += 32;
                 while (cp > ap) {
                     cp -= ap + 1;
                     ++ap;
-                }
-                for (int t = lane; t < ntr; t += 32) {
-                    const int a = j + 1 + ap, c = j + 1 + cp;
-                    A[a * ld + c] = fma(-A[a * ld + j], A[c * ld + j], A[a * ld + c]);
-                    cp += 32;
-                    while (cp > ap) {
-                        cp -= ap + 1;
-                        ++ap;
-                    }
                 }
             }
             __syncwarp();
@@ -350,57 +364,27 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
         __syncwarp();
         if (!ok) ++tries;
     }
-    if (!ok) {
-        // still indefinite after the largest jitter: empty conditioning set for this point
-        if (lane == 0) atomicAdd(njit, 1ull);
+    const double cc = ok ? A[s * ld + s] : 0.0;
+    if (!ok || !(cc > 0.0)) {
+        // indefinite after the largest jitter, or no positive conditional variance:
+        // empty conditioning set for this point
+        if (lane == 0 && (!ok || tries == 0)) atomicAdd(njit, 1ull);
         for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = q == 0 ? 1.0 : 0.0;
         return;
     }
     if (tries > 0 && lane == 0) atomicAdd(njit, 1ull);
-    // k = K(X_sigma, x_i); forward solve L y = k, then L' lambda = y (entries a, a + 32 per lane)
-    double kv[2] = {0.0, 0.0};
-    for (int h = 0; h < 2; ++h) {
-        const int a = lane + 32 * h;
-        if (a < s) {
-            const double dx = X[a] - xi.x, dy = Y[a] - xi.y;
-            const double q = c2 * (dx * dx + dy * dy);
-            kv[h] = q > 0.0 ? matern_q(nu, q) : 1.0;
-        }
-    }
-    for (int c = 0; c < s; ++c) {
-        const int hc = c >> 5;
-        double yc = __shfl_sync(full, hc ? kv[1] : kv[0], c & 31);
-        yc *= rd[c];
-        if (lane == (c & 31)) kv[hc] = yc;
-        for (int h = 0; h < 2; ++h) {
-            const int a = lane + 32 * h;
-            if (a > c && a < s) kv[h] = fma(-A[a * ld + c], yc, kv[h]);
-        }
-    }
-    double part = kv[0] * kv[0] + kv[1] * kv[1];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(full, part, o);
-    const double cc = 1.0 - part;
+    // L_ss' lambda = (row s of L)'; entries a and a + 32 in the lanes' registers
+    double l0 = lane < s ? A[s * ld + lane] : 0.0;
+    double l1 = lane + 32 < s ? A[s * ld + lane + 32] : 0.0;
     for (int c = s - 1; c >= 0; --c) {
-        const int hc = c >> 5;
-        double lc = __shfl_sync(full, hc ? kv[1] : kv[0], c & 31);
-        lc *= rd[c];
-        if (lane == (c & 31)) kv[hc] = lc;
-        for (int h = 0; h < 2; ++h) {
-            const int a = lane + 32 * h;
-            if (a < c) kv[h] = fma(-A[c * ld + a], lc, kv[h]);
-        }
+        const double lc = __shfl_sync(full, c >= 32 ? l1 : l0, c & 31);
+        if (lane < c) l0 = fma(-A[c * ld + lane], lc, l0);
+        if (s > 32 && lane + 32 < c) l1 = fma(-A[c * ld + lane + 32], lc, l1);
     }
-    if (!(cc > 0.0)) {
-        if (lane == 0 && tries == 0) atomicAdd(njit, 1ull);
-        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = q == 0 ? 1.0 : 0.0;
-        return;
-    }
-    const double ic = 1.0 / sqrt(cc);
+    const double ic = rsqrt(cc);
     if (lane == 0) val_ell[i] = ic;
-    for (int h = 0; h < 2; ++h) {
-        const int q = lane + 32 * h;
-        if (q < m) val_ell[(int64_t)(1 + q) * n + i] = q < s ? -kv[h] * ic : 0.0;
-    }
+    if (lane < m) val_ell[(int64_t)(1 + lane) * n + i] = lane < s ? -l0 * ic : 0.0;
+    if (lane + 32 < m) val_ell[(int64_t)(33 + lane) * n + i] = lane + 32 < s ? -l1 * ic : 0.0;
 }
 
 // ---------------------------------------------------------------- transpose of U~ (rows of U~)
@@ -631,15 +615,24 @@ int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const i
                 "nu must be 0.5, 1, 1.5, 2 or 2.5");
     PHS_REQUIRE(alpha > 0 && std::isfinite(alpha), PHS_ERR_INVALID_ARG, "alpha must be positive");
     upload_bessel_tables();
-    const int ld = m | 1;  // odd row stride: rows of consecutive lanes fall in different banks
-    const size_t per = (size_t)(m * ld + 3 * m) * sizeof(double);
+    const int ld = (m + 1) | 1;  // odd row stride: rows of consecutive lanes fall in different banks
+    const size_t per = (size_t)((m + 1) * ld + 3 * (m + 1)) * sizeof(double);
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
     const size_t smem = per * wpb;
-    PHS_CUDA(cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     DBuf<unsigned long long> cnt(2);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, 2 * sizeof(unsigned long long), s));
-    factor_kernel<<<blocks_for(n, wpb), 32 * wpb, smem, s>>>(x, n, rank, nbr_ell, m, ld, nu, alpha, val_ell,
-                                                             cnt.get());
+    const int nuc = nu == 0.5 ? 0 : (nu == 1.0 ? 1 : (nu == 1.5 ? 2 : (nu == 2.0 ? 3 : 4)));
+    auto launch = [&](auto kern) {
+        PHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<blocks_for(n, wpb), 32 * wpb, smem, s>>>(x, n, rank, nbr_ell, m, ld, 0.5 * alpha, val_ell, cnt.get());
+    };
+    switch (nuc) {
+        case 0: launch(factor_kernel<0>); break;
+        case 1: launch(factor_kernel<1>); break;
+        case 2: launch(factor_kernel<2>); break;
+        case 3: launch(factor_kernel<3>); break;
+        default: launch(factor_kernel<4>); break;
+    }
     PHS_LAUNCH_CHECK();
     unsigned long long h[2];
     PHS_CUDA(cudaMemcpyAsync(h, cnt.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
