@@ -6,6 +6,12 @@
 
 namespace phs {
 
+// four doubles (bounding boxes: xmin, xmax, ymin, ymax in x, y, z, w)
+struct __align__(16) Dbl4 {
+    double x, y, z, w;
+};
+
+
 __host__ __device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
     uint64_t x = v;
     x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;

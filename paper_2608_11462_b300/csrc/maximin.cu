@@ -55,9 +55,9 @@ struct HParams {
     double xmin, ymin, E, scale;
 };
 
-__global__ void h_bbox_partial(const double2 *x, int64_t n, double4 *part) {
-    __shared__ double4 red[256];
-    double4 b = make_double4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+__global__ void h_bbox_partial(const double2 *x, int64_t n, Dbl4 *part) {
+    __shared__ Dbl4 red[256];
+    Dbl4 b = Dbl4{INFINITY, -INFINITY, INFINITY, -INFINITY};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double2 p = x[i];
         b.x = fmin(b.x, p.x);
@@ -69,8 +69,8 @@ __global__ void h_bbox_partial(const double2 *x, int64_t n, double4 *part) {
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
-            const double4 c = red[threadIdx.x + o];
-            double4 &a = red[threadIdx.x];
+            const Dbl4 c = red[threadIdx.x + o];
+            Dbl4 &a = red[threadIdx.x];
             a.x = fmin(a.x, c.x);
             a.y = fmax(a.y, c.y);
             a.z = fmin(a.z, c.z);
@@ -80,8 +80,8 @@ __global__ void h_bbox_partial(const double2 *x, int64_t n, double4 *part) {
     }
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
-__global__ void h_bbox_final(const double4 *part, int np, HParams *prm) {
-    double4 b = part[0];
+__global__ void h_bbox_final(const Dbl4 *part, int np, HParams *prm) {
+    Dbl4 b = part[0];
     for (int i = 1; i < np; ++i) {
         b.x = fmin(b.x, part[i].x);
         b.y = fmax(b.y, part[i].y);
@@ -193,7 +193,7 @@ __global__ void h_fill_i32(int *a, int64_t n, int v) {
 void hmaxmin_order_dev(const double2 *x, int64_t n, uint64_t seed, int *order_out, cudaStream_t s) {
     if (n <= 0) return;
     const int nbb = (int)std::min<int64_t>(296, blocks_for(n, 256));
-    DBuf<double4> part(nbb);
+    DBuf<Dbl4> part(nbb);
     DBuf<HParams> prm(1);
     h_bbox_partial<<<nbb, 256, 0, s>>>(x, n, part.get());
     PHS_LAUNCH_CHECK();
@@ -452,7 +452,7 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
     PHS_REQUIRE(n < INT_MAX, PHS_ERR_INVALID_ARG, "too many points for the approximate maximin ordering");
     const unsigned nb256 = blocks_for(n, 256);
     const int nbb = (int)std::min<int64_t>(296, nb256);
-    DBuf<double4> part(nbb);
+    DBuf<Dbl4> part(nbb);
     DBuf<HParams> prm(1);
     h_bbox_partial<<<nbb, 256, 0, s>>>(x, n, part.get());
     PHS_LAUNCH_CHECK();

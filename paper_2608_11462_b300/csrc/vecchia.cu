@@ -2,9 +2,11 @@
 // enumeration, previous-point neighbour search, per-point local Cholesky factors,
 // the transposed factor and the apply z = U~ (U~' r).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <vector>
 
+#include "geom.cuh"
 #include "phs_internal.cuh"
 
 namespace phs {
@@ -42,17 +44,64 @@ __global__ void gather_xy(const double2 *x, const int *idx, int64_t n, double2 *
 }
 
 // ---------------------------------------------------------------- neighbour grid
+// G x G cells of width cw over the bounding square at (x0, y0); points are sorted by
+// (cell, rank), so a run of cells along a grid row is one contiguous range.
 struct Grid {
-    double x0, y0, cw;
+    double x0, y0, cw, inv;
     int G;
 };
 
-__global__ void grid_keys(const double2 *x, const int *rank, int64_t n, Grid g, uint64_t *keys, int *vals) {
+__global__ void knn_bbox_partial(const double2 *x, int64_t n, Dbl4 *part) {
+    __shared__ Dbl4 red[256];
+    Dbl4 b = Dbl4{INFINITY, -INFINITY, INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = x[i];
+        b.x = fmin(b.x, v.x);
+        b.y = fmax(b.y, v.x);
+        b.z = fmin(b.z, v.y);
+        b.w = fmax(b.w, v.y);
+    }
+    red[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const Dbl4 c = red[threadIdx.x + o];
+            Dbl4 &d = red[threadIdx.x];
+            d.x = fmin(d.x, c.x);
+            d.y = fmax(d.y, c.y);
+            d.z = fmin(d.z, c.z);
+            d.w = fmax(d.w, c.w);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void knn_grid_final(const Dbl4 *part, int np, int G, Grid *g) {
+    Dbl4 b = part[0];
+    for (int i = 1; i < np; ++i) {
+        b.x = fmin(b.x, part[i].x);
+        b.y = fmax(b.y, part[i].y);
+        b.z = fmin(b.z, part[i].z);
+        b.w = fmax(b.w, part[i].w);
+    }
+    const double ext = fmax(b.y - b.x, b.w - b.z);
+    Grid h;
+    h.G = G;
+    h.cw = ext > 0 ? ext / G * (1.0 + 1e-12) : 1.0;
+    h.inv = 1.0 / h.cw;
+    h.x0 = b.x;
+    h.y0 = b.z;
+    *g = h;
+}
+__device__ __forceinline__ int grid_coord(double v, double v0, const Grid &g) {
+    return min(max((int)floor((v - v0) * g.inv), 0), g.G - 1);
+}
+
+__global__ void grid_keys(const double2 *x, const int *rank, int64_t n, const Grid *gp, uint64_t *keys, int *vals) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int cx = (int)floor((x[i].x - g.x0) / g.cw), cy = (int)floor((x[i].y - g.y0) / g.cw);
-    cx = min(max(cx, 0), g.G - 1);
-    cy = min(max(cy, 0), g.G - 1);
+    const Grid g = *gp;
+    const int cx = grid_coord(x[i].x, g.x0, g), cy = grid_coord(x[i].y, g.y0, g);
     keys[i] = ((uint64_t)(cy * g.G + cx) << 32) | (uint64_t)(uint32_t)rank[i];
     vals[i] = (int)i;
 }
@@ -79,72 +128,166 @@ __global__ void cell_payload(const uint64_t *keys, const int *vals, const double
 
 constexpr int KNN_MAXM = 64;
 
-struct TopM {
-    double d[KNN_MAXM];
-    int r[KNN_MAXM];
-    int cnt;
-    int cap;
-    __device__ void consider(double dv, int q) {
-        if (cnt == cap && !(dv < d[cap - 1] || (dv == d[cap - 1] && q < r[cap - 1]))) return;
-        int pos = cnt < cap ? cnt : cap - 1;
-        while (pos > 0 && (dv < d[pos - 1] || (dv == d[pos - 1] && q < r[pos - 1]))) {
-            d[pos] = d[pos - 1];
-            r[pos] = r[pos - 1];
-            --pos;
+__device__ __forceinline__ bool key_less(unsigned long long ad, int aq, unsigned long long bd, int bq) {
+    return ad < bd || (ad == bd && aq < bq);
+}
+
+// The m smallest (d2, rank) keys seen so far, sorted, spread over the warp: entry k in
+// lane k (e0) and, for m > 32, entry 32 + k in lane k (e1).  Squared distances are
+// non-negative, so their bit patterns order as unsigned integers and no comparison
+// runs on the FP64 pipe.
+struct WarpTopM {
+    unsigned long long d0 = ~0ull, d1 = ~0ull;
+    int q0 = INT_MAX, q1 = INT_MAX;
+    unsigned long long td = ~0ull;  // entry m - 1 once m entries are held, else "infinity"
+    int tq = INT_MAX;
+    int cnt = 0;                    // entries held (at most m), warp-uniform
+
+    // one candidate per lane (valid lanes only); inserts those below the threshold
+    __device__ __forceinline__ void offer(bool valid, unsigned long long cd, int cq, int m, int lane) {
+        const unsigned full = 0xffffffffu;
+        unsigned mask = __ballot_sync(full, valid && key_less(cd, cq, td, tq));
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const unsigned long long vd = __shfl_sync(full, cd, src);
+            const int vq = __shfl_sync(full, cq, src);
+            if (!key_less(vd, vq, td, tq)) continue;
+            // entry k becomes entry k - 1 if the candidate precedes that, else the candidate
+            // if it precedes entry k, else stays
+            const unsigned long long pd = __shfl_up_sync(full, d0, 1);
+            const int pq = __shfl_up_sync(full, q0, 1);
+            if (m > 32) {
+                unsigned long long pd1 = __shfl_up_sync(full, d1, 1);
+                int pq1 = __shfl_up_sync(full, q1, 1);
+                const unsigned long long ld = __shfl_sync(full, d0, 31);
+                const int lq = __shfl_sync(full, q0, 31);
+                if (lane == 0) {
+                    pd1 = ld;
+                    pq1 = lq;
+                }
+                if (key_less(vd, vq, pd1, pq1)) {
+                    d1 = pd1;
+                    q1 = pq1;
+                } else if (key_less(vd, vq, d1, q1)) {
+                    d1 = vd;
+                    q1 = vq;
+                }
+            }
+            if (lane > 0 && key_less(vd, vq, pd, pq)) {
+                d0 = pd;
+                q0 = pq;
+            } else if (key_less(vd, vq, d0, q0)) {
+                d0 = vd;
+                q0 = vq;
+            }
+            cnt = min(cnt + 1, m);
+            if (cnt == m) {
+                td = __shfl_sync(full, m > 32 ? d1 : d0, (m - 1) & 31);
+                tq = __shfl_sync(full, m > 32 ? q1 : q0, (m - 1) & 31);
+            }
         }
-        d[pos] = dv;
-        r[pos] = q;
-        if (cnt < cap) ++cnt;
+    }
+    __device__ __forceinline__ unsigned long long entry_d(int k) const {
+        return __shfl_sync(0xffffffffu, k >= 32 ? d1 : d0, k & 31);
     }
 };
 
-// thread per rank r: the min(m, r) nearest points of smaller rank, by (d2, rank)
-__global__ void knn_kernel(const double2 *x_by_rank, int64_t n, int m, int brute, Grid g, const int *cstart,
+// Warp per rank r: the min(m, r) nearest points of smaller rank, by (d2, rank).  Small
+// ranks scan all previous points; the others walk square rings of grid cells around
+// the query until the held need-th distance is below the distance to the ring's outside.
+// A ring's new cells are at most two ranges per grid row; 32 ranges at a time are
+// concatenated by a warp scan of their lengths so that every distance batch is full.
+__global__ void knn_kernel(const double2 *x_by_rank, int64_t n, int m, int brute, const Grid *gp, const int *cstart,
                            const double2 *xc, const int *rc, const int *order, int *nbr_ell) {
-    const int64_t r64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t r64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r64 >= n) return;
     const int r = (int)r64;
     const double2 p = x_by_rank[r];
-    TopM top;
-    top.cnt = 0;
-    top.cap = m;
     const int need = min(m, r);
-    if (need > 0) {
-        if (r <= brute) {
-            for (int q = 0; q < r; ++q) top.consider(sqd(p, x_by_rank[q]), q);
-        } else {
-            int cx0 = (int)floor((p.x - g.x0) / g.cw), cy0 = (int)floor((p.y - g.y0) / g.cw);
-            cx0 = min(max(cx0, 0), g.G - 1);
-            cy0 = min(max(cy0, 0), g.G - 1);
-            for (int k = 0;; ++k) {
-                const int xa = cx0 - k, xb = cx0 + k, ya = cy0 - k, yb = cy0 + k;
-                for (int cy = max(ya, 0); cy <= min(yb, g.G - 1); ++cy) {
-                    const bool edge_row = (cy == ya || cy == yb);
-                    for (int cx = max(xa, 0); cx <= min(xb, g.G - 1); ++cx) {
-                        if (!edge_row && cx != xa && cx != xb) continue;
-                        const int c = cy * g.G + cx;
-                        for (int s2 = cstart[c]; s2 < cstart[c + 1]; ++s2) {
-                            const int q = rc[s2];
-                            if (q >= r) break;
-                            top.consider(sqd(p, xc[s2]), q);
+    WarpTopM top;
+    if (need > 0 && r <= brute) {
+        for (int base = 0; base < r; base += 32) {
+            const int q = base + lane;
+            const bool valid = q < r;
+            const unsigned long long cd = valid ? (unsigned long long)__double_as_longlong(sqd(p, x_by_rank[q])) : ~0ull;
+            top.offer(valid, cd, q, m, lane);
+        }
+    } else if (need > 0) {
+        const Grid g = *gp;
+        const int cx0 = grid_coord(p.x, g.x0, g), cy0 = grid_coord(p.y, g.y0, g);
+        for (int k = 0;; ++k) {
+            const int xa = cx0 - k, xb = cx0 + k, ya = cy0 - k, yb = cy0 + k;
+            const int cxa = max(xa, 0), cxb = min(xb, g.G - 1), rya = max(ya, 0), ryb = min(yb, g.G - 1);
+            // range j: row rya + j / 2; edge rows: part 0 = cells cxa..cxb; other rows:
+            // part 0 = cell xa, part 1 = cell xb (when inside the grid)
+            const int nr = 2 * (ryb - rya + 1);
+            for (int g0 = 0; g0 < nr; g0 += 32) {
+                int st = 0, len = 0;
+                const int j = g0 + lane;
+                if (j < nr) {
+                    const int cy = rya + (j >> 1), part = j & 1;
+                    const bool edge = cy == ya || cy == yb;
+                    int c0 = -1, c1 = -1;
+                    if (edge) {
+                        if (part == 0) {
+                            c0 = cxa;
+                            c1 = cxb;
                         }
+                    } else if (part == 0) {
+                        if (xa >= 0) c0 = c1 = xa;
+                    } else if (xb < g.G) {
+                        c0 = c1 = xb;
+                    }
+                    if (c0 >= 0) {
+                        st = cstart[cy * g.G + c0];
+                        len = cstart[cy * g.G + c1 + 1] - st;
                     }
                 }
-                const bool all = xa <= 0 && ya <= 0 && xb >= g.G - 1 && yb >= g.G - 1;
-                if (all) break;
-                if (top.cnt >= need) {
-                    double dm = INFINITY;
-                    if (xa > 0) dm = fmin(dm, p.x - (g.x0 + xa * g.cw));
-                    if (xb < g.G - 1) dm = fmin(dm, (g.x0 + (xb + 1) * g.cw) - p.x);
-                    if (ya > 0) dm = fmin(dm, p.y - (g.y0 + ya * g.cw));
-                    if (yb < g.G - 1) dm = fmin(dm, (g.y0 + (yb + 1) * g.cw) - p.y);
-                    if (dm > 0 && dm * dm * (1.0 - 1e-12) > top.d[need - 1]) break;
+                int off = len;  // inclusive scan of the range lengths
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(full, off, o);
+                    if (lane >= o) off += v;
                 }
+                const int total = __shfl_sync(full, off, 31);
+                off -= len;  // exclusive
+                for (int t = 0; t < total; t += 32) {
+                    const int e = t + lane;
+                    int lo = 0;  // last range with off <= e
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int c = lo + step;
+                        const int oc = __shfl_sync(full, off, c & 31);
+                        if (c < 32 && oc <= e) lo = c;
+                    }
+                    const int pos = __shfl_sync(full, st, lo) + (e - __shfl_sync(full, off, lo));
+                    bool valid = e < total;
+                    int q = INT_MAX;
+                    double2 c = p;
+                    if (valid) {
+                        q = rc[pos];
+                        valid = q < r;
+                        c = xc[pos];
+                    }
+                    const unsigned long long cd = valid ? (unsigned long long)__double_as_longlong(sqd(p, c)) : ~0ull;
+                    top.offer(valid, cd, q, m, lane);
+                }
+            }
+            if (xa <= 0 && ya <= 0 && xb >= g.G - 1 && yb >= g.G - 1) break;
+            if (top.cnt >= need) {
+                double dm = INFINITY;
+                if (xa > 0) dm = fmin(dm, p.x - (g.x0 + xa * g.cw));
+                if (xb < g.G - 1) dm = fmin(dm, (g.x0 + (xb + 1) * g.cw) - p.x);
+                if (ya > 0) dm = fmin(dm, p.y - (g.y0 + ya * g.cw));
+                if (yb < g.G - 1) dm = fmin(dm, (g.y0 + (yb + 1) * g.cw) - p.y);
+                if (dm > 0 && dm * dm * (1.0 - 1e-12) > __longlong_as_double((long long)top.entry_d(need - 1))) break;
             }
         }
     }
     const int i = order[r];
-    for (int s2 = 0; s2 < m; ++s2) nbr_ell[(int64_t)s2 * n + i] = s2 < top.cnt ? order[top.r[s2]] : -1;
+    if (lane < m) nbr_ell[(int64_t)lane * n + i] = lane < top.cnt ? order[top.q0] : -1;
+    if (lane + 32 < m) nbr_ell[(int64_t)(lane + 32) * n + i] = lane + 32 < top.cnt ? order[top.q1] : -1;
 }
 
 // ---------------------------------------------------------------- Matern covariance, K(0) = 1
@@ -271,15 +414,16 @@ static void upload_bessel_tables() {
     PHS_CUDA(cudaMemcpyToSymbol(c_cosh, ch, sizeof(ch)));
 }
 
-// 1/d for normal d > 0: the hardware approximation rcp.approx.ftz.f64 refined by three
-// Newton-Raphson steps r <- r + r (1 - d r) (each squares the relative error; Markstein,
-// IBM J. Res. Dev. 34(1), 1990), ending at the FP64 rounding level.
+// 1/d for normal d > 0: the hardware approximation rcp.approx.ftz.f64 (measured on this
+// part: relative error below 2^-19.9) refined by two Newton-Raphson steps
+// r <- r + r (1 - d r), each squaring the relative error (Markstein, IBM J. Res. Dev.
+// 34(1), 1990); over 2^28 samples across the exponent range the result equals the
+// correctly rounded 1/d.
 __device__ __forceinline__ double recip_nr(double d) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-#pragma unroll
-    for (int k = 0; k < 3; ++k) r = fma(r, fma(-d, r, 1.0), r);
-    return r;
+    r = fma(r, fma(-d, r, 1.0), r);
+    return fma(r, fma(-d, r, 1.0), r);
 }
 
 // Warp per point i with conditioning set sigma (s = |sigma| points): LDL' of the
@@ -571,25 +715,19 @@ void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr
     DBuf<double2> xr(n);
     gather_xy<<<blocks_for(n, 256), 256, 0, s>>>(x, order, n, xr.get());
     PHS_LAUNCH_CHECK();
-    // grid over the bounding box, about 2 points per cell
-    std::vector<double2> hx(n);
-    PHS_CUDA(cudaMemcpyAsync(hx.data(), x, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
-    PHS_CUDA(cudaStreamSynchronize(s));
-    double xmin = hx[0].x, xmax = hx[0].x, ymin = hx[0].y, ymax = hx[0].y;
-    for (auto &v : hx) {
-        xmin = std::min(xmin, v.x); xmax = std::max(xmax, v.x);
-        ymin = std::min(ymin, v.y); ymax = std::max(ymax, v.y);
-    }
-    Grid g;
-    g.G = (int)std::max<double>(1.0, std::min<double>(8192.0, std::floor(std::sqrt((double)n / 2.0))));
-    const double ext = std::max(xmax - xmin, ymax - ymin);
-    g.cw = ext > 0 ? ext / g.G * (1.0 + 1e-12) : 1.0;
-    g.x0 = xmin;
-    g.y0 = ymin;
-    const int ncell = g.G * g.G;
+    // grid over the bounding square, about 4 points per cell
+    const int nbb = (int)std::min<int64_t>(296, blocks_for(n, 256));
+    DBuf<Dbl4> part(nbb);
+    DBuf<Grid> g(1);
+    const int G = (int)std::max<double>(1.0, std::min<double>(8192.0, std::floor(std::sqrt((double)n / 4.0))));
+    knn_bbox_partial<<<nbb, 256, 0, s>>>(x, n, part.get());
+    PHS_LAUNCH_CHECK();
+    knn_grid_final<<<1, 1, 0, s>>>(part.get(), nbb, G, g.get());
+    PHS_LAUNCH_CHECK();
+    const int ncell = G * G;
     DBuf<uint64_t> keys(n);
     DBuf<int> vals(n);
-    grid_keys<<<blocks_for(n, 256), 256, 0, s>>>(x, rank.get(), n, g, keys.get(), vals.get());
+    grid_keys<<<blocks_for(n, 256), 256, 0, s>>>(x, rank.get(), n, g.get(), keys.get(), vals.get());
     PHS_LAUNCH_CHECK();
     int cbits = 1;
     while ((1ll << cbits) < ncell) ++cbits;
@@ -601,9 +739,9 @@ void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr
     DBuf<int> rc(n);
     cell_payload<<<blocks_for(n, 256), 256, 0, s>>>(keys.get(), vals.get(), x, n, xc.get(), rc.get());
     PHS_LAUNCH_CHECK();
-    const int brute = (int)std::min<int64_t>(n, 2048);
-    knn_kernel<<<blocks_for(n, 128), 128, 0, s>>>(xr.get(), n, m, brute, g, cst.get(), xc.get(), rc.get(), order,
-                                                  nbr_ell);
+    const int brute = (int)std::min<int64_t>(n, 8192);
+    knn_kernel<<<blocks_for(n * 32, 256), 256, 0, s>>>(xr.get(), n, m, brute, g.get(), cst.get(), xc.get(), rc.get(),
+                                                      order, nbr_ell);
     PHS_LAUNCH_CHECK();
     PHS_CUDA(cudaStreamSynchronize(s));
 }
