@@ -238,8 +238,15 @@ struct Vecchia {
     DBuf<int> order;      // order[r] = sorted position of rank r
     DBuf<int> nbr;        // ELL [m][n] sorted positions of neighbours (-1 pad)
     DBuf<double> val;     // ELL [m+1][n]: slot 0 = 1/c, slot 1+q = -lambda_q/c
-    DBuf<int> t_off, t_col;  // transpose (CSR by row) of U~
-    DBuf<double> t_val;
+    // rows of U~ (for z = U~ y) as sliced ELL: rows sorted by length (descending, stable),
+    // slices of 32 consecutive sorted rows padded to the slice's longest row and stored
+    // column-major (entry k of sorted position p at s_off[p/32] + 32 k + p%32), each row's
+    // entries in column order; padding has value 0
+    DBuf<int> s_row;   // row of sorted position p
+    DBuf<int> s_off;   // first entry of each slice
+    DBuf<int> s_len;   // entries per row of each slice
+    DBuf<int> s_col;
+    DBuf<double> s_val;
     int64_t jittered = 0;
 };
 void random_order_dev(int64_t n, uint64_t seed, int *order_out, cudaStream_t s);

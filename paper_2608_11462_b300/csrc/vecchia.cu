@@ -571,15 +571,69 @@ __global__ void apply_ut(const int *nbr_ell, const double *val_ell, int64_t n, i
     }
     y[j] = acc;
 }
-// z = U~ y, warp per row of the transposed (CSR) factor
-__global__ void apply_u(const int *off, const int *col, const double *val, int64_t n, const double *y, double *z) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+// z = U~ y: thread per row over the sliced-ELL rows (coalesced across the slice's 32
+// rows).  Four entries per step with all index and value loads issued before the
+// gathers of y keep enough bytes in flight; entry k goes to accumulator k mod 4 (the last
+// L mod 4 entries to a fifth) and they are added in a fixed order.
+__global__ void apply_u(const int *s_row, const int *s_off, const int *s_len, const int *col, const double *val,
+                        int64_t n, const double *y, double *z) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int sl = (int)(p >> 5);
+    const int L = s_len[sl];
+    const int *cp = col + s_off[sl] + (p & 31);
+    const double *vp = val + s_off[sl] + (p & 31);
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    int k = 0;
+    for (; k + 3 < L; k += 4) {
+        int c[4];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = __ldg(cp + 32 * (k + u));
+            v[u] = __ldg(vp + 32 * (k + u));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = fma(v[u], y[c[u]], a[u]);
+    }
+    double t = 0.0;
+    for (; k < L; ++k) t = fma(__ldg(vp + 32 * k), y[__ldg(cp + 32 * k)], t);
+    z[s_row[p]] = ((a[0] + a[1]) + (a[2] + a[3])) + t;
+}
+// sliced-ELL build from the CSR rows.  Rows are sorted by descending length over the
+// whole factor (sorting only within windows of spatially close rows was measured: the
+// extra padding costs more than the gather locality gains).
+__global__ void sell_keys(const int *off, int64_t n, uint64_t *key, int *row) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double acc = 0.0;
-    for (int e = off[i] + lane; e < off[i + 1]; e += 32) acc += val[e] * y[col[e]];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) z[i] = acc;
+    key[i] = (uint64_t)(0x7fffffff - (off[i + 1] - off[i]));  // stable: equal lengths keep row order
+    row[i] = (int)i;
+}
+__global__ void sell_len(const int *off, const int *s_row, int nslice, int *s_len) {
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= nslice) return;
+    const int r = s_row[(int64_t)sl * 32];
+    s_len[sl] = off[r + 1] - off[r];  // the slice's first row is its longest
+}
+__global__ void sell_width(const int *s_len, int nslice, int *w, unsigned long long *total) {
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl < nslice) {
+        w[sl] = 32 * s_len[sl];
+        atomicAdd(total, 32ull * (unsigned long long)s_len[sl]);
+    }
+}
+__global__ void sell_fill(const int *off, const int *col, const double *val, const int *s_row, const int *s_off,
+                          const int *s_len, int64_t n, int *s_col, double *s_val) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int r = s_row[p], sl = (int)(p >> 5);
+    const int L = s_len[sl], src = off[r], rl = off[r + 1] - src;
+    const int64_t base = (int64_t)s_off[sl] + (p & 31);
+    for (int k = 0; k < L; ++k) {
+        const int64_t e = base + 32 * (int64_t)k;
+        s_col[e] = k < rl ? col[src + k] : r;
+        s_val[e] = k < rl ? val[src + k] : 0.0;
+    }
 }
 
 __global__ void ell_to_positions(int *nbr_ell, int64_t total, const int *iperm) {
@@ -818,17 +872,17 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     // order (ranks -> sorted positions) = iperm[order_c]
     permute_ell<<<blocks_for(n, 256), 256, 0, s>>>(ps.iperm.get(), n, 1, order_c.get(), v.order.get());
     PHS_LAUNCH_CHECK();
-    // transpose
+    // transpose: CSR rows of U~ in column order, then the sliced-ELL copy the apply reads
     DBuf<int> cnt(n);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, n * sizeof(int), s));
     t_count<<<blocks_for(n, 256), 256, 0, s>>>(v.nbr.get(), n, m, cnt.get());
     PHS_LAUNCH_CHECK();
-    v.t_off.alloc(n + 1);
-    int64_t nnz = exclusive_scan_i32(cnt.get(), v.t_off.get(), n, s);
+    DBuf<int> t_off(n + 1);
+    int64_t nnz = exclusive_scan_i32(cnt.get(), t_off.get(), n, s);
     int nz32 = (int)nnz;
-    PHS_CUDA(cudaMemcpyAsync(v.t_off.get() + n, &nz32, sizeof(int), cudaMemcpyHostToDevice, s));
-    v.t_col.alloc(nnz);
-    v.t_val.alloc(nnz);
+    PHS_CUDA(cudaMemcpyAsync(t_off.get() + n, &nz32, sizeof(int), cudaMemcpyHostToDevice, s));
+    DBuf<int> t_col(nnz);
+    DBuf<double> t_val(nnz);
     {
         const int64_t np = (int64_t)(m + 1) * n;
         PHS_REQUIRE(np < (1ll << 31), PHS_ERR_INVALID_ARG, "Vecchia factor too large for 32-bit entry indices");
@@ -839,7 +893,34 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
         int bits = 1;
         while ((1ll << bits) <= n) ++bits;
         radix_sort_pairs(key.get(), ent.get(), np, bits, s);
-        t_gather<<<blocks_for(nnz, 256), 256, 0, s>>>(ent.get(), nnz, n, v.val.get(), v.t_col.get(), v.t_val.get());
+        t_gather<<<blocks_for(nnz, 256), 256, 0, s>>>(ent.get(), nnz, n, v.val.get(), t_col.get(), t_val.get());
+        PHS_LAUNCH_CHECK();
+    }
+    {
+        const int nslice = (int)((n + 31) / 32);
+        DBuf<uint64_t> key(n);
+        v.s_row.alloc(n);
+        sell_keys<<<blocks_for(n, 256), 256, 0, s>>>(t_off.get(), n, key.get(), v.s_row.get());
+        PHS_LAUNCH_CHECK();
+        radix_sort_pairs(key.get(), v.s_row.get(), n, 31, s);
+        v.s_len.alloc(nslice);
+        v.s_off.alloc(nslice + 1);
+        sell_len<<<blocks_for(nslice, 256), 256, 0, s>>>(t_off.get(), v.s_row.get(), nslice, v.s_len.get());
+        PHS_LAUNCH_CHECK();
+        DBuf<int> w(nslice);
+        DBuf<unsigned long long> wt(1);
+        PHS_CUDA(cudaMemsetAsync(wt.get(), 0, sizeof(unsigned long long), s));
+        sell_width<<<blocks_for(nslice, 256), 256, 0, s>>>(v.s_len.get(), nslice, w.get(), wt.get());
+        PHS_LAUNCH_CHECK();
+        unsigned long long hwt = 0;  // padded entries, counted in 64 bits before the 32-bit scan
+        PHS_CUDA(cudaMemcpyAsync(&hwt, wt.get(), sizeof(hwt), cudaMemcpyDeviceToHost, s));
+        PHS_CUDA(cudaStreamSynchronize(s));
+        PHS_REQUIRE(hwt < (1ull << 31), PHS_ERR_INVALID_ARG, "Vecchia factor too large for 32-bit entry indices");
+        const int64_t tot = exclusive_scan_i32(w.get(), v.s_off.get(), nslice, s);
+        v.s_col.alloc(std::max<int64_t>(tot, 1));
+        v.s_val.alloc(std::max<int64_t>(tot, 1));
+        sell_fill<<<blocks_for(n, 256), 256, 0, s>>>(t_off.get(), t_col.get(), t_val.get(), v.s_row.get(),
+                                                     v.s_off.get(), v.s_len.get(), n, v.s_col.get(), v.s_val.get());
         PHS_LAUNCH_CHECK();
     }
     PHS_CUDA(cudaStreamSynchronize(s));
@@ -850,7 +931,8 @@ void vecchia_apply_ut(const Vecchia &v, const double *r, double *y, cudaStream_t
     PHS_LAUNCH_CHECK();
 }
 void vecchia_apply_u(const Vecchia &v, const double *y, double *z, cudaStream_t s) {
-    apply_u<<<blocks_for(v.n * 32, 256), 256, 0, s>>>(v.t_off.get(), v.t_col.get(), v.t_val.get(), v.n, y, z);
+    apply_u<<<blocks_for(v.n, 256), 256, 0, s>>>(v.s_row.get(), v.s_off.get(), v.s_len.get(), v.s_col.get(),
+                                                 v.s_val.get(), v.n, y, z);
     PHS_LAUNCH_CHECK();
 }
 void vecchia_apply(const Vecchia &v, const double *r, double *tmp, double *z, cudaStream_t s) {
