@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--ordering", type=int, default=3, choices=[0, 1, 2, 3],
                     help="Vecchia enumeration: 0 random, 1 exact maxmin, 2 hierarchical maximin, "
                          "3 dyadic approximate maximin")
+    ap.add_argument("--case", default="step", choices=["step", "plan", "matvec", "precond"],
+                    help="step: the bench (plan + fit + evaluation, the JSON contract line); plan / "
+                         "matvec / precond: one piece of it repeated --steps times on one plan, for "
+                         "profiling (prints its own short line)")
     return ap.parse_args()
 
 
@@ -204,6 +208,22 @@ def main():
     f_d = torch.tensor(f, device=dev)
     tg_d = torch.tensor(targets, device=dev)
     stream = torch.cuda.current_stream(dev)
+    if args.case != "step":
+        # one piece of the step on the bench workload, for profilers; no timing contract
+        reps = max(1, args.steps)
+        if args.case == "plan":
+            for _ in range(reps):
+                phs.Plan(pts_d, 2, fmm_order=0, vecchia_m=30, opts=opts).close()
+        else:
+            p = phs.Plan(pts_d, 2, fmm_order=0, vecchia_m=30, opts=opts)
+            for _ in range(reps):
+                p.matvec(f_d) if args.case == "matvec" else p.precond(f_d)
+            torch.cuda.synchronize(dev)
+            p.close()
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"case": args.case, "n": n, "repeats": reps, "workload": WORKLOAD}))
+        return
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
 
     def barrier():
