@@ -299,9 +299,10 @@ def main():
     # FP64 pipe: 2 instructions (DFMA, DMUL or DADD) per clock per SM
     fp64_peak_g = 148 * 2 * sm_mhz_max * 1e6 / 1e9
     ms_p2p = phases["p2p"][0] / max(phases["p2p"][1], 1)
-    # per evaluated pair: 2 DADD + DMUL + DFMA (r^2), 4 DFMA + DADD (table log), DMUL
-    # (r^2 log r^2), DFMA (row sum) = 11; one more DFMA where the pair also feeds a column sum
-    p2p_ops = 11 * kwork["p2p_pairs"] + kwork["p2p_column_pairs"]
+    # per evaluated pair: DADD + 2 DFMA (r^2 = a_i + a_j - 2 x_i.x_j), 4 DFMA + DADD (table
+    # log), DMUL (r^2 log r^2), DFMA (row sum) = 10; one more DFMA where the pair also feeds
+    # a column sum
+    p2p_ops = 10 * kwork["p2p_pairs"] + kwork["p2p_column_pairs"]
     ach = p2p_ops / (ms_p2p / 1e3) / 1e9
     roof_p2p = {"kernel": "p2p_sym_kernel<2> + p2p_gather", "bound": "alu", "achieved": ach, "peak": fp64_peak_g,
                 "unit": "G FP64-pipe instr/s", "frac": ach / fp64_peak_g,

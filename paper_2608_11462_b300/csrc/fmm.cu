@@ -780,15 +780,21 @@ __global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, int nleaf, cons
     }
 }
 
-// phi(r) up to the factor 1/2 of the log kernels (applied once per sum), from dx, dy
+// phi(r) up to the factor 1/2 of the log kernels (applied once per sum), from
+// r^2 = a_i + a_j - 2 (x_i x_j + y_i y_j) with a = x^2 + y^2 of coordinates
+// centred on the target leaf (mx = -2 x_i, my = -2 y_i kept per row, a_j per column):
+// one DADD and two DFMA instead of two DADD, a DMUL and a DFMA.  The cancellation error
+// is at most eps (a_i + a_j), small beside every term of the sum; a self pair may give a
+// tiny non-zero r^2 instead of 0, whose contribution (r^2 log r^2) is below 1e-17.
 template <int K, bool kTab>
-__device__ __forceinline__ double phi_sym(double dx, double dy, const double2 *tab, const double *eln2) {
-    const double r2 = fma(dy, dy, dx * dx);
+__device__ __forceinline__ double phi_sym_a(double mx, double my, double ai, double xj, double yj, double aj,
+                                            const double2 *tab, const double *eln2) {
+    const double r2 = fma(mx, xj, fma(my, yj, ai + aj));
     if constexpr (kTab) {
         const double L = tab_log(r2, tab, eln2);
         return K == 2 ? r2 * L : (r2 * r2) * L;
     } else {
-        return phi_r2<double, K>(r2);
+        return phi_r2<double, K>(fmax(r2, 0.0));
     }
 }
 
@@ -807,7 +813,7 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
                                                        const int *order, int *ticket, const int *near_off,
                                                        const int2 *near_rng, const int *slot_off, const double2 *xs,
                                                        const double *t, double *y, double *scratch) {
-    __shared__ double sx[P2P_T], sy[P2P_T], st[P2P_T];
+    __shared__ double sx[P2P_T], sy[P2P_T], sa[P2P_T], st[P2P_T];
     __shared__ double colp[P2P_T / 32][P2P_T];
     __shared__ int2 ups[kMaxUpRanges];  // (start, prefix length) of the ranges after the leaf
     __shared__ int nup, next_leaf;
@@ -842,11 +848,13 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
         // warps without an active target skip the arithmetic (warp-uniform)
         const int nwarp = (nt * G + 31) >> 5;
         const bool wact = warp < nwarp;
-        double xi = 0, yi = 0, ti = 0;
+        double mx = 0, my = 0, ai = 0, ti = 0;
         if (act) {
             const double2 p = xs[i];
-            xi = p.x - cx;
-            yi = p.y - cy;
+            const double xi = p.x - cx, yi = p.y - cy;
+            mx = -2.0 * xi;
+            my = -2.0 * yi;
+            ai = fma(yi, yi, xi * xi);
             ti = t[i];
         }
         // own box (rows only) and the list of ranges after the leaf
@@ -864,8 +872,10 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
         }
         if (threadIdx.x < nt) {
             const double2 p = xs[s + threadIdx.x];
-            sx[threadIdx.x] = p.x - cx;
-            sy[threadIdx.x] = p.y - cy;
+            const double xj = p.x - cx, yj = p.y - cy;
+            sx[threadIdx.x] = xj;
+            sy[threadIdx.x] = yj;
+            sa[threadIdx.x] = fma(yj, yj, xj * xj);
             st[threadIdx.x] = t[s + threadIdx.x];
         }
         __syncthreads();
@@ -876,7 +886,7 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
                 const int jj = k * G + sub;
                 const bool v = jj < nt;
                 const int jc = v ? jj : 0;
-                const double f = v ? phi_sym<K, kTab>(xi - sx[jc], yi - sy[jc], logtab_sm, eln2) : 0.0;
+                const double f = v ? phi_sym_a<K, kTab>(mx, my, ai, sx[jc], sy[jc], sa[jc], logtab_sm, eln2) : 0.0;
                 acc = fma(f, st[jc], acc);
             }
         }
@@ -892,8 +902,10 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
                     while (ups[r + 1].y <= g) ++r;
                     const int j = ups[r].x + (g - ups[r].y);
                     const double2 p = xs[j];
-                    sx[threadIdx.x] = p.x - cx;
-                    sy[threadIdx.x] = p.y - cy;
+                    const double xj = p.x - cx, yj = p.y - cy;
+                    sx[threadIdx.x] = xj;
+                    sy[threadIdx.x] = yj;
+                    sa[threadIdx.x] = fma(yj, yj, xj * xj);
                     st[threadIdx.x] = t[j];
                 }
             }
@@ -912,7 +924,8 @@ __global__ void __launch_bounds__(P2P_T) p2p_sym_kernel(TreeView tv, int nleaf, 
                         const int jj = t0 + ((k + u) & (S - 1)) * G + sub;
                         const bool v = jj < jn;
                         const int jc = v ? jj : 0;
-                        const double f = v ? phi_sym<K, kTab>(xi - sx[jc], yi - sy[jc], logtab_sm, eln2) : 0.0;
+                        const double f = v ? phi_sym_a<K, kTab>(mx, my, ai, sx[jc], sy[jc], sa[jc], logtab_sm, eln2)
+                                           : 0.0;
                         acc = fma(f, st[jc], acc);
                         cs = fma(f, ti, cs);
                         cs = __shfl_sync(0xffffffffu, cs, (lane + G) & 31);

@@ -494,10 +494,12 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
         PHS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(AStat), cudaMemcpyDeviceToHost, s));
         PHS_CUDA(cudaStreamSynchronize(s));
     };
-    for (int L = 0; L <= kHL; ++L) {
+    auto level_c2 = [&](int L) {
         const double cL = std::ldexp(h.E, -L);
-        const double c2 = cL * cL;
-        // skip levels without candidates
+        return cL * cL;
+    };
+    for (int L = 0; L <= kHL; ++L) {
+        // jump over levels without candidates: one statistics read per level that has work
         PHS_CUDA(cudaMemsetAsync(st.get(), 0, offsetof(AStat, cand), s));
         a_stats<<<nb256, 256, 0, s>>>(l2.get(), taken.get(), n, st.get());
         PHS_LAUNCH_CHECK();
@@ -505,7 +507,9 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
         if (hs.taken >= n) break;
         double maxl2;
         std::memcpy(&maxl2, &hs.maxbits, sizeof(double));
-        if (!(maxl2 >= c2)) continue;
+        while (L <= kHL && !(maxl2 >= level_c2(L))) ++L;
+        if (L > kHL) break;
+        const double c2 = level_c2(L);
         // level-L cells: segments of the Morton order and their 5 x 5 neighbourhoods
         const int shift = 2 * (kHL - L);
         h_flags<<<nb256, 256, 0, s>>>(key.get(), n, shift, flag.get());
@@ -525,32 +529,38 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
         a_seg_nbrs<<<sb, 256, 0, s>>>(segkey.get(), nseg, L, nbr.get());
         PHS_LAUNCH_CHECK();
         for (;;) {
+            // a pass: candidates, one eligible point per cell, then rounds of the parallel
+            // greedy (each decides at least the highest-priority undecided point; rounds
+            // after the last change change nothing).  The candidate count is read together
+            // with the undecided count after the first two rounds: an empty pass leaves no
+            // eligible point and ends the level.
             a_pass_reset<<<sb, 256, 0, s>>>(nseg, segbest.get(), segarg.get());
             PHS_LAUNCH_CHECK();
             PHS_CUDA(cudaMemsetAsync(&st.get()->cand, 0, sizeof(int), s));
             a_cand<<<nb256, 256, 0, s>>>(l2.get(), taken.get(), segx.get(), flag.get(), n, c2, segbest.get(),
                                          st.get());
             PHS_LAUNCH_CHECK();
-            read_stat();
-            if (hs.cand == 0) break;
-            ++pass;
-            PHS_REQUIRE((int64_t)pass <= kMaxPass, PHS_ERR_INVALID_ARG, "approximate maximin: too many passes");
             a_cand_arg<<<nb256, 256, 0, s>>>(l2.get(), taken.get(), segx.get(), flag.get(), idx.get(), n, c2,
                                              segbest.get(), segarg.get());
             PHS_LAUNCH_CHECK();
             a_elig<<<sb, 256, 0, s>>>(nseg, segbest.get(), segarg.get(), pos.get(), elig.get(), status.get());
             PHS_LAUNCH_CHECK();
-            // parallel greedy: each round decides at least the highest-priority undecided point
             int rounds = 0;
             for (;;) {
-                PHS_CUDA(cudaMemsetAsync(&st.get()->undecided, 0, sizeof(int), s));
-                a_mis<<<sb, 256, 0, s>>>(nseg, nbr.get(), elig.get(), l2.get(), idx.get(), xs.get(), c2,
-                                         status.get(), st.get());
-                PHS_LAUNCH_CHECK();
+                for (int k = 0; k < (rounds == 0 ? 2 : 1); ++k) {
+                    PHS_CUDA(cudaMemsetAsync(&st.get()->undecided, 0, sizeof(int), s));
+                    a_mis<<<sb, 256, 0, s>>>(nseg, nbr.get(), elig.get(), l2.get(), idx.get(), xs.get(), c2,
+                                             status.get(), st.get());
+                    PHS_LAUNCH_CHECK();
+                    ++rounds;
+                }
                 read_stat();
-                if (hs.undecided == 0) break;
-                PHS_REQUIRE(++rounds <= nseg, PHS_ERR_CUDA, "approximate maximin: independent set did not settle");
+                if (hs.cand == 0 || hs.undecided == 0) break;
+                PHS_REQUIRE(rounds <= nseg + 1, PHS_ERR_CUDA, "approximate maximin: independent set did not settle");
             }
+            if (hs.cand == 0) break;
+            ++pass;
+            PHS_REQUIRE((int64_t)pass <= kMaxPass, PHS_ERR_INVALID_ARG, "approximate maximin: too many passes");
             a_accept<<<sb, 256, 0, s>>>(nseg, elig.get(), status.get(), l2.get(), c2, pass, taken.get(),
                                         keysel.get());
             PHS_LAUNCH_CHECK();
