@@ -11,7 +11,9 @@ What it computes, each function citing the passage it follows:
                              and the domain choices of Sec. 2.2).
 * ``poly_basis``          -- the polynomial block B of Eq. (1.3).
 * ``dense_*``             -- the kernel matrix M, M t and the interpolant,
-                             Eqs. (1.1)-(1.3), by their O(n^2) definitions.
+                             Eqs. (1.1)-(1.3), by their O(n^2) definitions
+                             (row by row for sampled rows; ``dense_eval_abs``
+                             the sums of absolute terms, their rounding scale).
 * ``solve_augmented``     -- the augmented system (1.3) by LU with partial
                              pivoting (a library primitive).
 * ``solve_qperp``         -- the same system by the sequence (2.5) with an
@@ -52,6 +54,7 @@ def lib():
         L.or_dense_matrix.argtypes = [i64, P, i32, P]
         L.or_dense_matvec.argtypes = [i64, P, i32, P, P]
         L.or_dense_eval.argtypes = [i64, P, P, i32, i64, P, P]
+        L.or_dense_eval_abs.argtypes = [i64, P, P, i32, i64, P, P]
         L.or_splitmix64.restype = u64
         L.or_splitmix64.argtypes = [u64, u64]
         L.or_random_order.argtypes = [i64, u64, P]
@@ -155,6 +158,17 @@ def dense_eval(x, w, k: int, y) -> np.ndarray:
     w = _f64(w)
     out = np.empty(y.shape[0], dtype=np.float64)
     lib().or_dense_eval(x.shape[0], _p(x), _p(w), int(k), y.shape[0], _p(y), _p(out))
+    return out
+
+
+def dense_eval_abs(x, w, k: int, y) -> np.ndarray:
+    """sum_j |w_j phi(|x_j - y|)|: the scale against which the rounding of dense_eval's
+    sums (any summation order, any fast method) is measured."""
+    x = _f64(x).reshape(-1, 2)
+    y = _f64(y).reshape(-1, 2)
+    w = _f64(w)
+    out = np.empty(y.shape[0], dtype=np.float64)
+    lib().or_dense_eval_abs(x.shape[0], _p(x), _p(w), int(k), y.shape[0], _p(y), _p(out))
     return out
 
 

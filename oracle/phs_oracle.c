@@ -74,6 +74,21 @@ void or_dense_eval(int64_t n, const double *x, const double *w, int k,
     }
 }
 
+/* The scale of that sum's rounding: out_i = sum_j |w_j phi(|x_j - y_i|)|, the sum of the
+ * absolute values of its terms (the error bound of any summation order is relative to
+ * it; the sums of an interpolant cancel heavily). */
+void or_dense_eval_abs(int64_t n, const double *x, const double *w, int k,
+                       int64_t m, const double *y, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j)
+            s += fabs(w[j] * or_phi(k, sqrt(sqdist(y + 2 * i, x + 2 * j))));
+        out[i] = s;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the i-th output (i = 0, 1, ...)
  * of the generator seeded with `seed`.  Counter-based: state_i = seed + (i+1)*gamma. */

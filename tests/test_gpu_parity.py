@@ -526,3 +526,53 @@ def test_errors_are_reported(phs):
     plan = phs.Plan(_t(pts), 2, vecchia_m=5)
     t = np.ones(50)
     assert np.allclose(plan.matvec(_t(t)).cpu().numpy(), oracle.dense_matvec(pts, 2, t), rtol=1e-10)
+
+
+# ---------------------------------------------------------------- the bench workload at full size
+def test_full_size_tps_1m_sampled_rows(phs):
+    """The clustered TPS workload at n = 1,048,576 with the bench's options (nu = 1,
+    alpha = 0.03, approximate maximin order, leaf cap 64, FMM order from 1e-11).  No dense
+    solve exists at this size, so the oracle computes sampled rows one by one (O(n) each):
+    * FMM matvec rows within 1e-10 of the exact row sums, relative to the sum of the
+      absolute terms (the rounding scale of any summation order);
+    * the fit converges in fewer than 15 iterations; B'w = 0 to rounding; at sampled
+      nodes the exact interpolant misses f by no more than the solve's residual, since
+      f - M w - B beta = P (f - M w) (plus the FMM error on that row);
+    * evaluation at sampled held-out targets within 1e-10 of the exact interpolant,
+      relative to the same absolute scale."""
+    w_ = synth.workload("tps_1m")
+    pts, f, tg = w_["points"], w_["f"], w_["targets"]
+    n = len(f)
+    assert n == 1_048_576
+    plan = phs.Plan(_t(pts), 2, fmm_order=0, vecchia_m=30, opts=phs.options(2, tol=1e-8, nu=1.0, alpha=0.03))
+    rng = np.random.default_rng(77)
+    rows = np.sort(rng.choice(n, 800, replace=False))
+    # matvec rows
+    t = rng.standard_normal(n)
+    y = plan.matvec(_t(t)).cpu().numpy()
+    exact = oracle.dense_eval(pts, t, 2, pts[rows])
+    scale = oracle.dense_eval_abs(pts, t, 2, pts[rows])
+    err = np.abs(y[rows] - exact) / scale
+    assert err.max() <= 1e-10, err.max()
+    # fit
+    w, beta, info = plan.fit(_t(f))
+    assert info["converged"] == 1 and info["iters"] < 15 and info["rel_res_true"] <= 1e-8, info
+    xn, c, rho = oracle.normalize(pts, 0.25)
+    wn = w.cpu().numpy() / rho ** 2
+    beta = beta.cpu().numpy()
+    B = oracle.poly_basis(xn, 1)
+    assert np.linalg.norm(B.T @ wn) <= 1e-12 * np.linalg.norm(B) * np.linalg.norm(wn)
+    fhat = oracle.interpolant(xn, wn, beta, 2, 1, xn[rows])
+    wscale = oracle.dense_eval_abs(xn, wn, 2, xn[rows])
+    res = np.abs(f[rows] - fhat)
+    bound = 2e-8 * np.linalg.norm(f) + 1e-10 * wscale
+    assert np.all(res <= bound), (res / bound).max()
+    # evaluation at held-out targets
+    sel = rng.choice(len(tg), 400, replace=False)
+    got = plan.eval(w, _t(beta), _t(tg[sel])).cpu().numpy()
+    yn = (tg[sel] - c) * rho
+    want = oracle.interpolant(xn, wn, beta, 2, 1, yn)
+    tscale = oracle.dense_eval_abs(xn, wn, 2, yn) + np.abs(oracle.poly_basis(yn, 1) @ beta)
+    terr = np.abs(got - want) / tscale
+    assert terr.max() <= 1e-10, terr.max()
+    plan.close()

@@ -529,3 +529,18 @@ def test_amaxmin_conflict_between_adjacent_cells():
     assert order.tolist() == [0, 3, 4, 1, 2]
     assert level.tolist() == [-1, 1, 1, 1, 4]
     assert l2[4] == (0.55 - 0.45) ** 2
+
+
+def test_dense_eval_abs_is_abs_matrix_times_abs_weights():
+    """The rounding scale sum_j |w_j phi_ij| equals |M| |w| built from the dense matrix
+    (another route), and bounds |dense_eval| with equality for one-signed terms."""
+    rng = np.random.default_rng(12)
+    x = rng.random((300, 2))
+    w = rng.standard_normal(300)
+    for k in (1, 2, 3, 4):
+        M = oracle.dense_matrix(x, k)
+        got = oracle.dense_eval_abs(x, w, k, x[:40])
+        assert np.allclose(got, np.abs(M[:40]) @ np.abs(w), rtol=1e-13, atol=0)
+        assert np.all(np.abs(oracle.dense_eval(x, w, k, x[:40])) <= got * (1 + 1e-13))
+    M = oracle.dense_matrix(x, 3)  # r^3 >= 0: with w >= 0 every term has one sign
+    assert np.allclose(oracle.dense_eval_abs(x, np.abs(w), 3, x[:10]), M[:10] @ np.abs(w), rtol=1e-13)
