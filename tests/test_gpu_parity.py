@@ -576,3 +576,42 @@ def test_full_size_tps_1m_sampled_rows(phs):
     terr = np.abs(got - want) / tscale
     assert terr.max() <= 1e-10, terr.max()
     plan.close()
+
+
+def test_full_size_cubic_mix_sampled_rows(phs):
+    """The cubic PHS workload at its full size (n = 100,000 from 20 clustered Gaussians,
+    k = 3, S = 3, Vecchia m = 20, nu = 1.5, tol 1e-8) on sampled rows, as for the 1M TPS
+    set: Chebyshev-FMM matvec rows, the interpolant at sampled nodes within the solve's
+    residual, B'w = 0 and held-out targets."""
+    w_ = synth.workload("cubic_mix")
+    pts, f, tg = w_["points"], w_["f"], w_["targets"]
+    n = len(f)
+    assert n == 100_000
+    plan = phs.Plan(_t(pts), 3, vecchia_m=20, opts=phs.options(3, tol=1e-8, maxiter=400))
+    rng = np.random.default_rng(78)
+    rows = np.sort(rng.choice(n, 600, replace=False))
+    t = rng.standard_normal(n)
+    y = plan.matvec(_t(t)).cpu().numpy()
+    exact = oracle.dense_eval(pts, t, 3, pts[rows])
+    scale = oracle.dense_eval_abs(pts, t, 3, pts[rows])
+    err = np.abs(y[rows] - exact) / scale
+    assert err.max() <= 1e-10, err.max()
+    w, beta, info = plan.fit(_t(f))
+    assert info["converged"] == 1 and info["rel_res_true"] <= 1e-8, info
+    xn, c, rho = oracle.normalize(pts, 0.25)
+    wn = w.cpu().numpy() / rho ** 3
+    beta = beta.cpu().numpy()
+    B = oracle.poly_basis(xn, 1)
+    assert np.linalg.norm(B.T @ wn) <= 1e-12 * np.linalg.norm(B) * np.linalg.norm(wn)
+    fhat = oracle.interpolant(xn, wn, beta, 3, 1, xn[rows])
+    bound = 2e-8 * np.linalg.norm(f) + 1e-10 * oracle.dense_eval_abs(xn, wn, 3, xn[rows])
+    res = np.abs(f[rows] - fhat)
+    assert np.all(res <= bound), (res / bound).max()
+    sel = rng.choice(len(tg), 300, replace=False)
+    got = plan.eval(w, _t(beta), _t(tg[sel])).cpu().numpy()
+    yn = (tg[sel] - c) * rho
+    want = oracle.interpolant(xn, wn, beta, 3, 1, yn)
+    tscale = oracle.dense_eval_abs(xn, wn, 3, yn) + np.abs(oracle.poly_basis(yn, 1) @ beta)
+    terr = np.abs(got - want) / tscale
+    assert terr.max() <= 1e-10, terr.max()
+    plan.close()
