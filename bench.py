@@ -41,6 +41,21 @@ M2L_DRAM_BYTES_PER_TILE = (29.62176e6 + 39.68e3) / 618
 P2P_DRAM_BYTES_PER_POINT = (7.3408e6 + 768) / 262144
 
 
+def workload_config(args, n, m_t, fmm_order, world):
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": WORKLOAD, "n": n, "targets": m_t, "k": 2, "poly_degree": 1, "vecchia_m": 30,
+            "nu": NU, "alpha_normalised": ALPHA,
+            "ordering": ["random", "maxmin", "hierarchical maximin", "approximate maximin"][args.ordering],
+            "leaf_cap": args.leaf_cap, "fmm_order": fmm_order, "precision_mode": args.precision, "tol": 1e-8,
+            "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) between timed steps"}
+
+
+def default_fmm_order(eps=1e-11):
+    """The library's order for fmm_order <= 0: ceil(log eps / log 0.55), clamped to 4..60."""
+    import math
+    return max(4, min(60, math.ceil(math.log(eps) / math.log(0.55))))
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,7 +202,7 @@ def main():
         print(json.dumps({"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
                           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "impl": "reference", "config": {"workload": WORKLOAD, "n": n, "k": 2, "vecchia_m": 30},
+                          "impl": "reference", "config": workload_config(args, n, m_t, default_fmm_order(), 1),
                           "cpu_baseline": cb,
                           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
@@ -341,10 +356,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
         "fits_per_s": world / t_step,
-        "config": {"workload": WORKLOAD, "n": n, "targets": m_t, "k": 2, "poly_degree": 1, "vecchia_m": 30,
-                   "nu": NU, "alpha_normalised": ALPHA, "ordering": ["random", "maxmin", "hierarchical maximin", "approximate maximin"][args.ordering], "leaf_cap": args.leaf_cap, "fmm_order": sizes[3],
-                   "precision_mode": args.precision, "tol": 1e-8, "parallelism": f"replicas{world}",
-                   "l2": "flushed (256 MB write) between timed steps"},
+        "config": workload_config(args, n, m_t, int(sizes[3]), world),
         "pcg": {"iters": info["iters"], "outer_iters": info["outer_iters"], "converged": info["converged"],
                 "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"], "ms_fit": info["ms_fit"],
                 "ms_matvec_avg": info["ms_matvec_avg"]},
