@@ -121,12 +121,21 @@ __global__ void dots_partial(DotSet ds, int64_t n, double *part) {
     }
 }
 // fixed-order final sum of the partials: out[i] = sum_b part[b][i]
-__global__ void dots_final(const double *part, int nblk, int cnt, double *out) {
-    const int i = threadIdx.x;
-    if (i >= cnt) return;
+// out[i] = sum over the nblk block partials of value i; block i, RED_T threads: thread t
+// sums partials t, t + RED_T, ... and a fixed shared-memory tree adds the threads, so the
+// order is the same on every call (one dependent chain over all partials took ~50 us)
+__global__ void dots_final(const double *part, int nblk, double *out) {
+    const int i = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[b * 12 + i];
-    out[i] = s;
+    for (int b = threadIdx.x; b < nblk; b += RED_T) s += part[b * 12 + i];
+    __shared__ double sh[RED_T];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = RED_T / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = sh[0];
 }
 
 // monomials 1, x, y, x^2, xy, y^2, ... (graded lexicographic), Eq. (1.3)
@@ -426,7 +435,7 @@ static void dots(phs_plan *pl, std::initializer_list<std::pair<const double *, c
     }
     dots_partial<<<RED_B, RED_T, 0, s>>>(ds, pl->ps.n, pl->part.get());
     PHS_LAUNCH_CHECK();
-    dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, ds.cnt, out);
+    dots_final<<<ds.cnt, RED_T, 0, s>>>(pl->part.get(), RED_B, out);
     PHS_LAUNCH_CHECK();
 }
 
@@ -437,13 +446,13 @@ static void project(phs_plan *pl, const double *v, double sign, double *out, con
     double *coef = pl->scal.get() + 16;
     qt_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, v, pl->part.get());
     PHS_LAUNCH_CHECK();
-    dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, pl->S, coef);
+    dots_final<<<pl->S, RED_T, 0, s>>>(pl->part.get(), RED_B, coef);
     PHS_LAUNCH_CHECK();
     proj_apply<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, coef, v, sign, out, other,
                                         other ? pl->part.get() + 8 * 0 : nullptr);
     PHS_LAUNCH_CHECK();
     if (other) {
-        dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, 1, dot_out);
+        dots_final<<<1, RED_T, 0, s>>>(pl->part.get(), RED_B, dot_out);
         PHS_LAUNCH_CHECK();
     }
 }
@@ -476,7 +485,7 @@ static void precond(phs_plan *pl, const double *r, double *z, double *tmp, doubl
     double *coef = pl->scal.get() + 16;
     qt_partial<<<RED_B, RED_T, 0, s>>>(pl->G.get(), pl->S, n, r, pl->part.get());
     PHS_LAUNCH_CHECK();
-    dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, pl->S, coef);
+    dots_final<<<pl->S, RED_T, 0, s>>>(pl->part.get(), RED_B, coef);
     PHS_LAUNCH_CHECK();
     proj_apply<<<RED_B, RED_T, 0, s>>>(pl->G.get(), pl->S, n, coef, tmp2, 1.0, z, nullptr, nullptr);
     PHS_LAUNCH_CHECK();
@@ -535,7 +544,7 @@ static int pcg(phs_plan *pl, const double *rhs, double *x, double tol_abs, int m
         project(pl, y, (double)pl->sign, q, p, sc + 1, s);
         cg_update<<<RED_B, RED_T, 0, s>>>(x, r, p, q, n, sc + 0, sc + 1, pl->part.get());
         PHS_LAUNCH_CHECK();
-        dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, 1, sc + 2);
+        dots_final<<<1, RED_T, 0, s>>>(pl->part.get(), RED_B, sc + 2);
         PHS_LAUNCH_CHECK();
         pl->tm.end(T_VEC, s);
         rr = read_scalar(pl, sc + 2, s);
@@ -711,7 +720,7 @@ phs_status phs_matvec(phs_plan_t pl, const double *t_dev, double *out_dev, int p
         const int power = pl->k;
         had_dots<<<RED_B, RED_T, 0, s>>>(pl->ps.xs.get(), ts, n, power, pl->part.get());
         PHS_LAUNCH_CHECK();
-        dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, power == 2 ? 4 : 10, pl->scal.get() + 32);
+        dots_final<<<power == 2 ? 4 : 10, RED_T, 0, s>>>(pl->part.get(), RED_B, pl->scal.get() + 32);
         PHS_LAUNCH_CHECK();
         had_correct<<<blocks_for(n, 256), 256, 0, s>>>(pl->ps.xs.get(), n, power, pl->scal.get() + 32, std::log(rho), y);
         PHS_LAUNCH_CHECK();
@@ -785,7 +794,7 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
     PHS_LAUNCH_CHECK();
     qt_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, y, pl->part.get());
     PHS_LAUNCH_CHECK();
-    dots_final<<<1, 32, 0, s>>>(pl->part.get(), RED_B, pl->S, sc + 40);
+    dots_final<<<pl->S, RED_T, 0, s>>>(pl->part.get(), RED_B, sc + 40);
     PHS_LAUNCH_CHECK();
     tri_solve<<<1, 1, 0, s>>>(pl->R.get(), pl->S, sc + 40, beta_dev);
     PHS_LAUNCH_CHECK();

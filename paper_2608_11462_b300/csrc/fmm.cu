@@ -625,43 +625,47 @@ __global__ void __launch_bounds__(UD_T) l2l64_kernel(TreeView tv, int b0, int nd
     }
 }
 
-// L2P + Hadamard combination: four threads per point, each on densities d = sub,
-// sub + 4, ... (Horner in FMAs), then a shuffle sum over the four
-__global__ void __launch_bounds__(UD_T) l2p64_kernel(TreeView tv, const int *leaf_box, const double2 *xs, int power,
-                                                    int nd, int P, const double2 *lc, double *y) {
+// L2P with the powers z^k shared by the densities: thread per point, P steps of one
+// complex product (4 FP64) and, per density, two FMAs on the real part (Re(L_d(z)) is all
+// the Hadamard combination sum_d u_d Re(L_d(z)) needs), against 4 FP64 per density and
+// step for separate complex Horner recurrences.  |z| <= sqrt(2)/2 inside the leaf, so the
+// direct sum of the powers is as accurate as Horner's rule.
+constexpr int L2P_T = 64;
+template <int ND>
+__global__ void __launch_bounds__(L2P_T) l2p64_kernel(TreeView tv, const int *leaf_box, const double2 *xs,
+                                                     int power, int P, const double2 *lc, double *y) {
     extern __shared__ double2 l2p_sm[];
     const int b = leaf_box[blockIdx.x];
-    const int nout = nd * P;
-    for (int i = threadIdx.x; i < nout; i += UD_T) l2p_sm[i] = lc[(size_t)b * nout + i];
+    const int nout = ND * P;
+    for (int i = threadIdx.x; i < nout; i += L2P_T) l2p_sm[i] = lc[(size_t)b * nout + i];
     __syncthreads();
     double cx, cy, w;
     box_geom(tv, b, cx, cy, w);
     const double iw = 1.0 / w;
     const int s = tv.start[b], e = tv.end[b];
-    const int sub = threadIdx.x & 3;
-    for (int j0 = s; j0 < e; j0 += UD_T / 4) {
-        // a warp covers 8 points; warps past the leaf's last point skip (warp-uniform)
-        if (j0 + ((threadIdx.x >> 5) << 3) >= e) continue;
-        const int j = j0 + (threadIdx.x >> 2);
-        const bool ok = j < e;
-        const double2 xj = ok ? xs[j] : make_double2(cx, cy);
+    for (int j = s + threadIdx.x; j < e; j += L2P_T) {
+        const double2 xj = xs[j];
         const double vx = (xj.x - cx) * iw, vy = (xj.y - cy) * iw;
         double u[kMaxNd];
         had_u(power, vx, vy, u);
-        double sum = 0.0;
-        for (int d = sub; d < nd; d += 4) {
-            const double2 *L = l2p_sm + d * P;
-            double hx = L[P - 1].x, hy = L[P - 1].y;
-            for (int l = P - 2; l >= 0; --l) {
-                const double nx = fma(hx, vx, fma(-hy, vy, L[l].x));
-                hy = fma(hx, vy, fma(hy, vx, L[l].y));
-                hx = nx;
+        double acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = 0.0;
+        double zx = 1.0, zy = 0.0;
+        for (int k = 0; k < P; ++k) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const double2 L = l2p_sm[d * P + k];
+                acc[d] = fma(L.x, zx, fma(-L.y, zy, acc[d]));
             }
-            sum = fma(u[d], hx, sum);
+            const double nx = fma(zx, vx, -zy * vy);
+            zy = fma(zx, vy, zy * vx);
+            zx = nx;
         }
-        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-        if (ok && sub == 0) y[j] += sum;
+        double sum = 0.0;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) sum = fma(u[d], acc[d], sum);
+        y[j] += sum;
     }
 }
 
@@ -1116,7 +1120,6 @@ static void set_pass_smem_limits() {
     PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     PHS_CUDA(cudaFuncSetAttribute(m2m64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     PHS_CUDA(cudaFuncSetAttribute(l2l64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    PHS_CUDA(cudaFuncSetAttribute(l2p64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     done = true;
 }
 
@@ -1319,9 +1322,11 @@ template <typename T>
 static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s) {
     using C = typename C2T<T>::type;
     if constexpr (sizeof(T) == 8) {
-        set_pass_smem_limits();
-        l2p64_kernel<<<t.nleaf, UD_T, (size_t)f.nd * f.P * sizeof(double2), s>>>(
-            tree_view(t), t.leaf_box.get(), ps.xs.get(), f.power, f.nd, f.P, f.lc64.get(), y);
+        const size_t sm = (size_t)f.nd * f.P * sizeof(double2);  // at most 9 x 61 x 16 B
+        const TreeView tv = tree_view(t);
+        if (f.nd == 4) l2p64_kernel<4><<<t.nleaf, L2P_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), f.power, f.P, f.lc64.get(), y);
+        else if (f.nd == 9) l2p64_kernel<9><<<t.nleaf, L2P_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), f.power, f.P, f.lc64.get(), y);
+        else l2p64_kernel<1><<<t.nleaf, L2P_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), f.power, f.P, f.lc64.get(), y);
         PHS_LAUNCH_CHECK();
         return;
     }
