@@ -418,8 +418,10 @@ constexpr int UD_T = 256;
 // P2M: chunks of 64 points; four threads per point build the powers zeta^k, each a
 // quarter of k from its own starting power; then one thread per output (d, k) sums the
 // chunk.  a_0 = sum q, a_k = -sum q zeta^k / k (box-width scaled, fmm.cu header).
+template <int ND>  // density count (static, so the Hadamard factors stay in registers)
 __global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *leaf_box, const double2 *xs,
-                                                    const double *t, int power, int nd, int P, double2 *mp) {
+                                                    const double *t, int power, int P, double2 *mp) {
+    constexpr int nd = ND;
     extern __shared__ double2 p2m_sm[];
     double2 *pw = p2m_sm;                                 // [64][P]
     double *qs = reinterpret_cast<double *>(pw + 64 * P);  // [64][nd]
@@ -1117,7 +1119,9 @@ static void set_pass_smem_limits() {
     static bool done = false;
     if (done) return;
     const int lim = 100 * 1024;
-    PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     PHS_CUDA(cudaFuncSetAttribute(m2m64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     PHS_CUDA(cudaFuncSetAttribute(l2l64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     done = true;
@@ -1132,8 +1136,10 @@ static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_s
     const size_t esz = (size_t)nd * P * sizeof(C);
     if constexpr (sizeof(T) == 8) {
         set_pass_smem_limits();
-        p2m64_kernel<<<t.nleaf, UD_T, (size_t)64 * P * sizeof(double2) + (size_t)64 * nd * sizeof(double), s>>>(
-            tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, nd, P, mp);
+        const size_t sm = (size_t)64 * P * sizeof(double2) + (size_t)64 * nd * sizeof(double);
+        if (nd == 4) p2m64_kernel<4><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
+        else if (nd == 9) p2m64_kernel<9><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
+        else p2m64_kernel<1><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
         PHS_LAUNCH_CHECK();
         for (int l = t.depth - 1; l >= 0; --l) {
             const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
