@@ -65,7 +65,9 @@ def parse():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--n", type=int, default=None, help="override the point count (smaller parity runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--leaf-cap", type=int, default=64, help="quadtree leaf capacity")
+    ap.add_argument("--leaf-cap", type=int, default=96,
+                    help="quadtree leaf capacity (96 measured best on this workload: 48 / 64 / 80 / 96 / "
+                         "112 gave 0.429 / 0.344 / 0.327 / 0.323 / 0.331 s per solve)")
     ap.add_argument("--ordering", type=int, default=3, choices=[0, 1, 2, 3],
                     help="Vecchia enumeration: 0 random, 1 exact maxmin, 2 hierarchical maximin, "
                          "3 dyadic approximate maximin")

@@ -531,7 +531,7 @@ def test_errors_are_reported(phs):
 # ---------------------------------------------------------------- the bench workload at full size
 def test_full_size_tps_1m_sampled_rows(phs):
     """The clustered TPS workload at n = 1,048,576 with the bench's options (nu = 1,
-    alpha = 0.03, approximate maximin order, leaf cap 64, FMM order from 1e-11).  No dense
+    alpha = 0.03, approximate maximin order, leaf cap 96, FMM order from 1e-11).  No dense
     solve exists at this size, so the oracle computes sampled rows one by one (O(n) each):
     * FMM matvec rows within 1e-10 of the exact row sums, relative to the sum of the
       absolute terms (the rounding scale of any summation order);
@@ -544,7 +544,8 @@ def test_full_size_tps_1m_sampled_rows(phs):
     pts, f, tg = w_["points"], w_["f"], w_["targets"]
     n = len(f)
     assert n == 1_048_576
-    plan = phs.Plan(_t(pts), 2, fmm_order=0, vecchia_m=30, opts=phs.options(2, tol=1e-8, nu=1.0, alpha=0.03))
+    plan = phs.Plan(_t(pts), 2, fmm_order=0, vecchia_m=30,
+                    opts=phs.options(2, tol=1e-8, nu=1.0, alpha=0.03, leaf_cap=96))
     rng = np.random.default_rng(77)
     rows = np.sort(rng.choice(n, 800, replace=False))
     # matvec rows
