@@ -1387,6 +1387,64 @@ static const std::vector<long double> &mix_cached(int power, int nd) {
     return it->second;
 }
 
+// The device forms of the level-invariant tables, also per order and per process: the
+// operators in FP64 and FP32, and the real shift cores of M2M/L2L with their phases
+// (R[l][k] = A_0[l][k] e^{-i th_0 (l - k)} for quadrant 0, checked real and equal for the
+// other quadrants; th_q the quadrant's angle).
+struct DevTables {
+    std::vector<double2> o64;
+    std::vector<float2> o32;
+    std::vector<double> R;    // [2][P][P]: M2M, L2L
+    std::vector<double2> ph;  // [4][P]: e^{i th_q k}
+    std::vector<long double> re, im;  // the operators split for the tensor-core setup
+};
+static std::mutex g_dev_tables_mu;
+static const DevTables &dev_tables_cached(int P) {
+    const auto &ops = ops_cached(P);
+    static std::map<int, DevTables> cache;
+    std::lock_guard<std::mutex> g(g_dev_tables_mu);
+    auto it = cache.find(P);
+    if (it != cache.end()) return it->second;
+    DevTables d;
+    d.o64.resize(ops.size());
+    d.o32.resize(ops.size());
+    d.re.resize(ops.size());
+    d.im.resize(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+        d.o64[i] = make_double2((double)ops[i].real(), (double)ops[i].imag());
+        d.o32[i] = make_float2((float)ops[i].real(), (float)ops[i].imag());
+        d.re[i] = ops[i].real();
+        d.im[i] = ops[i].imag();
+    }
+    d.R.assign((size_t)2 * P * P, 0.0);
+    d.ph.resize((size_t)4 * P);
+    for (int q = 0; q < 4; ++q) {
+        const long double th = std::atan2((long double)((q & 2) ? 0.25L : -0.25L), (long double)((q & 1) ? 0.25L : -0.25L));
+        for (int k = 0; k < P; ++k) {
+            const long double a = th * k;
+            d.ph[(size_t)q * P + k] = make_double2((double)std::cos(a), (double)std::sin(a));
+        }
+        for (int t2 = 0; t2 < 2; ++t2)
+            for (int r = 0; r < P; ++r)
+                for (int c2 = 0; c2 < P; ++c2) {
+                    const std::complex<long double> A = ops[((size_t)(4 * t2 + q) * P + r) * P + c2];
+                    // M2M: row l = r, col k = c2, phase e^{i th (l - k)}; L2L: row m = r, col l = c2,
+                    // phase e^{i th (l - m)}
+                    const long double ang = t2 == 0 ? th * (r - c2) : th * (c2 - r);
+                    const std::complex<long double> v = A * std::polar(1.0L, -ang);
+                    const long double mag = std::abs(A);
+                    PHS_REQUIRE(std::fabs(v.imag()) <= 1e-12L * std::max(mag, 1e-300L) + 1e-300L, PHS_ERR_INVALID_ARG,
+                                "shift operator does not factor through a real core");
+                    double &dst = d.R[((size_t)t2 * P + r) * P + c2];
+                    if (q == 0) dst = (double)v.real();
+                    else
+                        PHS_REQUIRE(std::fabs((long double)dst - v.real()) <= 1e-12L * std::max(mag, 1e-300L) + 1e-300L,
+                                    PHS_ERR_INVALID_ARG, "shift cores differ between quadrants");
+                }
+    }
+    return cache.emplace(P, std::move(d)).first->second;
+}
+
 void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s) {
     PHS_REQUIRE(k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "k must be in 1..5");
     PHS_REQUIRE(p >= 2 && p + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "fmm_order must be in 2..60");
@@ -1400,60 +1458,20 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     f.power = f.log_core ? k : k - 1;
     f.nd = f.power == 0 ? 1 : (f.power == 2 ? 4 : 9);
     PHS_REQUIRE(f.nd * f.P <= FMM_T * OUT_PER_T, PHS_ERR_INVALID_ARG, "fmm_order too large for this spline order");
-    const auto &ops = ops_cached(f.P);
-    const auto &opsf = ops_cached(f.P32);
-    std::vector<double2> o64(ops.size());
-    std::vector<float2> o32(opsf.size()), o32p(ops.size());
-    for (size_t i = 0; i < ops.size(); ++i) {
-        o64[i] = make_double2((double)ops[i].real(), (double)ops[i].imag());
-        o32p[i] = make_float2((float)ops[i].real(), (float)ops[i].imag());
-    }
-    for (size_t i = 0; i < opsf.size(); ++i) o32[i] = make_float2((float)opsf[i].real(), (float)opsf[i].imag());
+    const DevTables &dt = dev_tables_cached(f.P);
+    const DevTables &dtf = dev_tables_cached(f.P32);
+    const std::vector<double2> &o64 = dt.o64;
+    const std::vector<float2> &o32 = dtf.o32, &o32p = dt.o32;
     f.ops64.alloc(o64.size());
     f.ops32.alloc(o32.size());
     f.ops32p.alloc(o32p.size());
     PHS_CUDA(cudaMemcpyAsync(f.ops64.get(), o64.data(), o64.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32.get(), o32.data(), o32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.ops32p.get(), o32p.data(), o32p.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
-    {
-        // real shift cores: R[l][k] = A_0[l][k] e^{-i th_0 (l - k)} (quadrant 0), checked real and
-        // equal for the other quadrants
-        const int P = f.P;
-        std::vector<double> R((size_t)2 * P * P);
-        std::vector<double2> ph((size_t)4 * P);
-        const long double pi = 3.141592653589793238462643383279502884L;
-        for (int q = 0; q < 4; ++q) {
-            const long double th = std::atan2((long double)((q & 2) ? 0.25L : -0.25L), (long double)((q & 1) ? 0.25L : -0.25L));
-            for (int k = 0; k < P; ++k) {
-                const long double a = th * k;
-                // exact unit values at multiples of 45 degrees
-                const long double c = std::cos(a), sn = std::sin(a);
-                ph[(size_t)q * P + k] = make_double2((double)c, (double)sn);
-            }
-            for (int t2 = 0; t2 < 2; ++t2)
-                for (int r = 0; r < P; ++r)
-                    for (int c2 = 0; c2 < P; ++c2) {
-                        const std::complex<long double> A = ops[((size_t)(4 * t2 + q) * P + r) * P + c2];
-                        // M2M: row l = r, col k = c2, phase e^{i th (l - k)}; L2L: row m = r, col l = c2,
-                        // phase e^{i th (l - m)}
-                        const long double ang = t2 == 0 ? th * (r - c2) : th * (c2 - r);
-                        const std::complex<long double> v = A * std::polar(1.0L, -ang);
-                        const long double mag = std::abs(A);
-                        PHS_REQUIRE(std::fabs(v.imag()) <= 1e-12L * std::max(mag, 1e-300L) + 1e-300L, PHS_ERR_INVALID_ARG,
-                                    "shift operator does not factor through a real core");
-                        double &dst = R[((size_t)t2 * P + r) * P + c2];
-                        if (q == 0) dst = (double)v.real();
-                        else
-                            PHS_REQUIRE(std::fabs((long double)dst - v.real()) <= 1e-12L * std::max(mag, 1e-300L) + 1e-300L,
-                                        PHS_ERR_INVALID_ARG, "shift cores differ between quadrants");
-                    }
-        }
-        (void)pi;
-        f.shift_r.alloc(R.size());
-        f.shift_ph.alloc(ph.size());
-        PHS_CUDA(cudaMemcpyAsync(f.shift_r.get(), R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        PHS_CUDA(cudaMemcpyAsync(f.shift_ph.get(), ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-    }
+    f.shift_r.alloc(dt.R.size());
+    f.shift_ph.alloc(dt.ph.size());
+    PHS_CUDA(cudaMemcpyAsync(f.shift_r.get(), dt.R.data(), dt.R.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.shift_ph.get(), dt.ph.data(), dt.ph.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     {
         const auto &mx = mix_cached(f.power, f.nd);
         std::vector<double> m64(mx.size());
@@ -1467,14 +1485,7 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
         PHS_CUDA(cudaMemcpyAsync(f.mix64.get(), m64.data(), m64.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         PHS_CUDA(cudaMemcpyAsync(f.mix32.get(), m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
         f.tc = false;
-        if (tensor_m2l && f.log_core && m2l_tc_supported(f.nd, f.P)) {
-            std::vector<long double> ore(ops.size()), oim(ops.size());
-            for (size_t i = 0; i < ops.size(); ++i) {
-                ore[i] = ops[i].real();
-                oim[i] = ops[i].imag();
-            }
-            m2l_tc_setup(f, ore, oim, mx, s);
-        }
+        if (tensor_m2l && f.log_core && m2l_tc_supported(f.nd, f.P)) m2l_tc_setup(f, dt.re, dt.im, mx, s);
     }
     PHS_CUDA(cudaStreamSynchronize(s));
     upload_log_tables();
