@@ -71,6 +71,26 @@ struct DBuf {
     T *get() const { return p; }
 };
 
+// Stream-ordered scratch from the library's memory pool of the current device (created on
+// first use, keeping up to 1 GB of freed blocks for reuse): allocation and release are
+// ordered on the stream that uses the buffer, so neither synchronises the device the way
+// cudaMalloc / cudaFree do.  For temporaries whose every use is on one stream.
+cudaMemPool_t scratch_pool();
+template <typename T>
+struct SBuf {
+    T *p = nullptr;
+    cudaStream_t s = nullptr;
+    SBuf(size_t count, cudaStream_t stream) : s(stream) {
+        if (count) PHS_CUDA(cudaMallocFromPoolAsync((void **)&p, count * sizeof(T), scratch_pool(), s));
+    }
+    SBuf(const SBuf &) = delete;
+    SBuf &operator=(const SBuf &) = delete;
+    ~SBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    T *get() const { return p; }
+};
+
 // ---------------------------------------------------------------- primitives (sort_scan.cu)
 // exclusive scan of int32 counts; returns total (synchronises stream)
 int64_t exclusive_scan_i32(const int *in, int *out, int64_t n, cudaStream_t s);

@@ -1,8 +1,32 @@
 // sort_scan.cu -- device exclusive scan and stable LSD radix sort of (key, value) pairs.
 // Used by the setup phase (Morton sort, random enumeration, neighbour grid).
+#include <mutex>
+
 #include "phs_internal.cuh"
 
 namespace phs {
+
+cudaMemPool_t scratch_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    PHS_CUDA(cudaGetDevice(&dev));
+    PHS_REQUIRE(dev >= 0 && dev < 64, PHS_ERR_CUDA, "device ordinal out of range for the scratch pool");
+    std::lock_guard<std::mutex> g(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        PHS_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = 1ull << 30;
+        PHS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
 namespace {
 
 constexpr int SCAN_T = 1024;
@@ -156,7 +180,7 @@ __global__ void rs_scatter(const uint64_t *kin, const int *vin, uint64_t *kout, 
 int64_t exclusive_scan_i32(const int *in, int *out, int64_t n, cudaStream_t s) {
     int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntiles < 1) ntiles = 1;
-    DBuf<int> sums(ntiles + 1);
+    SBuf<int> sums(ntiles + 1, s);
     scan_tile_sums<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, n, sums.get());
     PHS_LAUNCH_CHECK();
     scan_sums<<<1, SCAN_T, 0, s>>>(sums.get(), ntiles);
@@ -174,9 +198,9 @@ int64_t exclusive_scan_i32(const int *in, int *out, int64_t n, cudaStream_t s) {
 void radix_sort_pairs(uint64_t *keys, int *vals, int64_t n, int bits, cudaStream_t s) {
     if (n <= 1) return;
     int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
-    DBuf<uint64_t> k2(n);
-    DBuf<int> v2(n);
-    DBuf<int> hist((size_t)256 * ntiles), offs((size_t)256 * ntiles);
+    SBuf<uint64_t> k2(n, s);
+    SBuf<int> v2(n, s);
+    SBuf<int> hist((size_t)256 * ntiles, s), offs((size_t)256 * ntiles, s);
     uint64_t *ka = keys, *kb = k2.get();
     int *va = vals, *vb = v2.get();
     int passes = (bits + 7) / 8;
