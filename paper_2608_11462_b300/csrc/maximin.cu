@@ -193,17 +193,17 @@ __global__ void h_fill_i32(int *a, int64_t n, int v) {
 void hmaxmin_order_dev(const double2 *x, int64_t n, uint64_t seed, int *order_out, cudaStream_t s) {
     if (n <= 0) return;
     const int nbb = (int)std::min<int64_t>(296, blocks_for(n, 256));
-    DBuf<Dbl4> part(nbb);
-    DBuf<HParams> prm(1);
+    SBuf<Dbl4> part(nbb, s);
+    SBuf<HParams> prm(1, s);
     h_bbox_partial<<<nbb, 256, 0, s>>>(x, n, part.get());
     PHS_LAUNCH_CHECK();
     h_bbox_final<<<1, 1, 0, s>>>(part.get(), nbb, prm.get());
     PHS_LAUNCH_CHECK();
-    DBuf<uint64_t> key(n);
-    DBuf<int> idx(n), pos(n), flag(n), segx(n), segi(n), repa(n), repb(n);
-    DBuf<double> d2(n);
-    DBuf<unsigned long long> segd(n);
-    DBuf<unsigned char> lvl(n);
+    SBuf<uint64_t> key(n, s);
+    SBuf<int> idx(n, s), pos(n, s), flag(n, s), segx(n, s), segi(n, s), repa(n, s), repb(n, s);
+    SBuf<double> d2(n, s);
+    SBuf<unsigned long long> segd(n, s);
+    SBuf<unsigned char> lvl(n, s);
     h_keys<<<blocks_for(n, 256), 256, 0, s>>>(x, n, prm.get(), key.get(), idx.get());
     PHS_LAUNCH_CHECK();
     radix_sort_pairs(key.get(), idx.get(), n, 2 * kHL, s);
@@ -230,7 +230,7 @@ void hmaxmin_order_dev(const double2 *x, int64_t n, uint64_t seed, int *order_ou
         PHS_LAUNCH_CHECK();
         std::swap(rep_prev, rep);
     }
-    DBuf<uint64_t> k2(n);
+    SBuf<uint64_t> k2(n, s);
     h_order_keys<<<blocks_for(n, 256), 256, 0, s>>>(idx.get(), lvl.get(), n, seed, k2.get(), order_out);
     PHS_LAUNCH_CHECK();
     radix_sort_pairs(k2.get(), order_out, n, 62, s);
@@ -452,18 +452,18 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
     PHS_REQUIRE(n < INT_MAX, PHS_ERR_INVALID_ARG, "too many points for the approximate maximin ordering");
     const unsigned nb256 = blocks_for(n, 256);
     const int nbb = (int)std::min<int64_t>(296, nb256);
-    DBuf<Dbl4> part(nbb);
-    DBuf<HParams> prm(1);
+    SBuf<Dbl4> part(nbb, s);
+    SBuf<HParams> prm(1, s);
     h_bbox_partial<<<nbb, 256, 0, s>>>(x, n, part.get());
     PHS_LAUNCH_CHECK();
     h_bbox_final<<<1, 1, 0, s>>>(part.get(), nbb, prm.get());
     PHS_LAUNCH_CHECK();
-    DBuf<uint64_t> key(n), keysel(n);
-    DBuf<int> idx(n), pos(n), flag(n), segx(n);
-    DBuf<double2> xs(n);
-    DBuf<double> l2(n);
-    DBuf<unsigned char> taken(n);
-    DBuf<AStat> st(1);
+    SBuf<uint64_t> key(n, s), keysel(n, s);
+    SBuf<int> idx(n, s), pos(n, s), flag(n, s), segx(n, s);
+    SBuf<double2> xs(n, s);
+    SBuf<double> l2(n, s);
+    SBuf<unsigned char> taken(n, s);
+    SBuf<AStat> st(1, s);
     h_keys<<<nb256, 256, 0, s>>>(x, n, prm.get(), key.get(), idx.get());
     PHS_LAUNCH_CHECK();
     radix_sort_pairs(key.get(), idx.get(), n, 2 * kHL, s);
@@ -571,7 +571,7 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
     }
     // one stable sort by (pass, l2 descending) over caller indices; the tail (never a
     // candidate) keeps key ~0 and is then ordered by l2 descending
-    DBuf<uint64_t> fk(n);
+    SBuf<uint64_t> fk(n, s);
     a_final_keys<<<nb256, 256, 0, s>>>(pos.get(), taken.get(), keysel.get(), n, fk.get(), order_out);
     PHS_LAUNCH_CHECK();
     radix_sort_pairs(fk.get(), order_out, n, 64, s);
@@ -581,7 +581,7 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
     read_stat();
     const int64_t ntail = n - hs.taken;
     if (ntail > 1) {
-        DBuf<uint64_t> tk(ntail);
+        SBuf<uint64_t> tk(ntail, s);
         a_tail_keys<<<blocks_for(ntail, 256), 256, 0, s>>>(order_out, pos.get(), l2.get(), hs.taken, ntail, tk.get());
         PHS_LAUNCH_CHECK();
         radix_sort_pairs(tk.get(), order_out + hs.taken, ntail, 64, s);

@@ -747,15 +747,15 @@ __global__ void __launch_bounds__(MM_T) maxmin_block(const double2 *x, int64_t n
 }  // namespace
 
 void maxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t s) {
-    DBuf<double> dmin(n);
-    DBuf<unsigned char> sel(n);
+    SBuf<double> dmin(n, s);
+    SBuf<unsigned char> sel(n, s);
     maxmin_block<<<1, MM_T, 0, s>>>(x, n, dmin.get(), sel.get(), order_out);
     PHS_LAUNCH_CHECK();
     PHS_CUDA(cudaStreamSynchronize(s));
 }
 
 void random_order_dev(int64_t n, uint64_t seed, int *order_out, cudaStream_t s) {
-    DBuf<uint64_t> keys(n);
+    SBuf<uint64_t> keys(n, s);
     rand_keys<<<blocks_for(n, 256), 256, 0, s>>>(n, seed, keys.get(), order_out);
     PHS_LAUNCH_CHECK();
     radix_sort_pairs(keys.get(), order_out, n, 64, s);
@@ -763,34 +763,34 @@ void random_order_dev(int64_t n, uint64_t seed, int *order_out, cudaStream_t s) 
 
 void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr_ell, cudaStream_t s) {
     PHS_REQUIRE(m >= 1 && m <= KNN_MAXM, PHS_ERR_INVALID_ARG, "conditioning-set size m must be in 1..64");
-    DBuf<int> rank(n);
+    SBuf<int> rank(n, s);
     ranks_from_order<<<blocks_for(n, 256), 256, 0, s>>>(order, n, rank.get());
     PHS_LAUNCH_CHECK();
-    DBuf<double2> xr(n);
+    SBuf<double2> xr(n, s);
     gather_xy<<<blocks_for(n, 256), 256, 0, s>>>(x, order, n, xr.get());
     PHS_LAUNCH_CHECK();
     // grid over the bounding square, about 4 points per cell
     const int nbb = (int)std::min<int64_t>(296, blocks_for(n, 256));
-    DBuf<Dbl4> part(nbb);
-    DBuf<Grid> g(1);
+    SBuf<Dbl4> part(nbb, s);
+    SBuf<Grid> g(1, s);
     const int G = (int)std::max<double>(1.0, std::min<double>(8192.0, std::floor(std::sqrt((double)n / 4.0))));
     knn_bbox_partial<<<nbb, 256, 0, s>>>(x, n, part.get());
     PHS_LAUNCH_CHECK();
     knn_grid_final<<<1, 1, 0, s>>>(part.get(), nbb, G, g.get());
     PHS_LAUNCH_CHECK();
     const int ncell = G * G;
-    DBuf<uint64_t> keys(n);
-    DBuf<int> vals(n);
+    SBuf<uint64_t> keys(n, s);
+    SBuf<int> vals(n, s);
     grid_keys<<<blocks_for(n, 256), 256, 0, s>>>(x, rank.get(), n, g.get(), keys.get(), vals.get());
     PHS_LAUNCH_CHECK();
     int cbits = 1;
     while ((1ll << cbits) < ncell) ++cbits;
     radix_sort_pairs(keys.get(), vals.get(), n, 32 + cbits, s);
-    DBuf<int> cst(ncell + 1);
+    SBuf<int> cst(ncell + 1, s);
     cell_starts<<<blocks_for(ncell + 1, 256), 256, 0, s>>>(keys.get(), n, ncell, cst.get());
     PHS_LAUNCH_CHECK();
-    DBuf<double2> xc(n);
-    DBuf<int> rc(n);
+    SBuf<double2> xc(n, s);
+    SBuf<int> rc(n, s);
     cell_payload<<<blocks_for(n, 256), 256, 0, s>>>(keys.get(), vals.get(), x, n, xc.get(), rc.get());
     PHS_LAUNCH_CHECK();
     const int brute = (int)std::min<int64_t>(n, 8192);
@@ -811,7 +811,7 @@ int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const i
     const size_t per = (size_t)((m + 1) * ld + 3 * (m + 1)) * sizeof(double);
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
     const size_t smem = per * wpb;
-    DBuf<unsigned long long> cnt(2);
+    SBuf<unsigned long long> cnt(2, s);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, 2 * sizeof(unsigned long long), s));
     const int nuc = nu == 0.5 ? 0 : (nu == 1.0 ? 1 : (nu == 1.5 ? 2 : (nu == 2.0 ? 3 : 4)));
     auto launch = [&](auto kern) {
@@ -840,20 +840,20 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     v.m = m;
     // caller-order coordinates (normalised frame): ties in orderings and neighbour lists
     // resolve by caller index, the definition the interface documents
-    DBuf<double2> xcal(n);
+    SBuf<double2> xcal(n, s);
     gather_xy<<<blocks_for(n, 256), 256, 0, s>>>(ps.xs.get(), ps.iperm.get(), n, xcal.get());
     PHS_LAUNCH_CHECK();
-    DBuf<int> order_c(n);
+    SBuf<int> order_c(n, s);
     if (ordering == 0) random_order_dev(n, seed, order_c.get(), s);
     else if (ordering == 1) maxmin_order_dev(xcal.get(), n, order_c.get(), s);
     else if (ordering == 2) hmaxmin_order_dev(xcal.get(), n, seed, order_c.get(), s);
     else amaxmin_order_dev(xcal.get(), n, order_c.get(), s);
-    DBuf<int> nbr_c((size_t)m * n);
+    SBuf<int> nbr_c((size_t)m * n, s);
     knn_prev_dev(xcal.get(), n, order_c.get(), m, nbr_c.get(), s);
-    DBuf<int> rank_c(n);
+    SBuf<int> rank_c(n, s);
     ranks_from_order<<<blocks_for(n, 256), 256, 0, s>>>(order_c.get(), n, rank_c.get());
     PHS_LAUNCH_CHECK();
-    DBuf<double> val_c((size_t)(m + 1) * n);
+    SBuf<double> val_c((size_t)(m + 1) * n, s);
     v.jittered = vecchia_factor_dev(xcal.get(), n, rank_c.get(), nbr_c.get(), m, nu, alpha, val_c.get(), s);
     // move to sorted positions: columns permuted by perm, entries mapped by iperm
     v.nbr.alloc((size_t)m * n);
@@ -873,21 +873,21 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     permute_ell<<<blocks_for(n, 256), 256, 0, s>>>(ps.iperm.get(), n, 1, order_c.get(), v.order.get());
     PHS_LAUNCH_CHECK();
     // transpose: CSR rows of U~ in column order, then the sliced-ELL copy the apply reads
-    DBuf<int> cnt(n);
+    SBuf<int> cnt(n, s);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, n * sizeof(int), s));
     t_count<<<blocks_for(n, 256), 256, 0, s>>>(v.nbr.get(), n, m, cnt.get());
     PHS_LAUNCH_CHECK();
-    DBuf<int> t_off(n + 1);
+    SBuf<int> t_off(n + 1, s);
     int64_t nnz = exclusive_scan_i32(cnt.get(), t_off.get(), n, s);
     int nz32 = (int)nnz;
     PHS_CUDA(cudaMemcpyAsync(t_off.get() + n, &nz32, sizeof(int), cudaMemcpyHostToDevice, s));
-    DBuf<int> t_col(nnz);
-    DBuf<double> t_val(nnz);
+    SBuf<int> t_col(nnz, s);
+    SBuf<double> t_val(nnz, s);
     {
         const int64_t np = (int64_t)(m + 1) * n;
         PHS_REQUIRE(np < (1ll << 31), PHS_ERR_INVALID_ARG, "Vecchia factor too large for 32-bit entry indices");
-        DBuf<uint64_t> key(np);
-        DBuf<int> ent(np);
+        SBuf<uint64_t> key(np, s);
+        SBuf<int> ent(np, s);
         t_pairs<<<blocks_for(np, 256), 256, 0, s>>>(v.nbr.get(), n, m, key.get(), ent.get());
         PHS_LAUNCH_CHECK();
         int bits = 1;
@@ -898,7 +898,7 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     }
     {
         const int nslice = (int)((n + 31) / 32);
-        DBuf<uint64_t> key(n);
+        SBuf<uint64_t> key(n, s);
         v.s_row.alloc(n);
         sell_keys<<<blocks_for(n, 256), 256, 0, s>>>(t_off.get(), n, key.get(), v.s_row.get());
         PHS_LAUNCH_CHECK();
@@ -907,8 +907,8 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
         v.s_off.alloc(nslice + 1);
         sell_len<<<blocks_for(nslice, 256), 256, 0, s>>>(t_off.get(), v.s_row.get(), nslice, v.s_len.get());
         PHS_LAUNCH_CHECK();
-        DBuf<int> w(nslice);
-        DBuf<unsigned long long> wt(1);
+        SBuf<int> w(nslice, s);
+        SBuf<unsigned long long> wt(1, s);
         PHS_CUDA(cudaMemsetAsync(wt.get(), 0, sizeof(unsigned long long), s));
         sell_width<<<blocks_for(nslice, 256), 256, 0, s>>>(v.s_len.get(), nslice, w.get(), wt.get());
         PHS_LAUNCH_CHECK();
