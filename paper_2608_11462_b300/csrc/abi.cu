@@ -500,8 +500,8 @@ static void build_lowrank(phs_plan *pl, cudaStream_t s) {
     pl->G.alloc((size_t)S * n);
     double *Y = W(pl, 0);
     for (int c = 0; c < S; ++c) vecchia_apply_ut(pl->vec, pl->Q.get() + (size_t)c * n, Y + (size_t)c * n, s);
-    DBuf<double> Rc((size_t)S * S);
-    DBuf<int> st(1);
+    SBuf<double> Rc((size_t)S * S, s);
+    SBuf<int> st(1, s);
     gram_partial<<<RED_B, RED_T, 0, s>>>(Y, n, S, pl->part.get());
     PHS_LAUNCH_CHECK();
     gram_chol<<<1, 1, 0, s>>>(pl->part.get(), RED_B, S, Rc.get(), st.get());
@@ -664,7 +664,7 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         pl->scal.alloc(64);
         build_B<<<blocks_for(n, 256), 256, 0, s>>>(pl->ps.xs.get(), n, deg, S, pl->Q.get());
         PHS_LAUNCH_CHECK();
-        DBuf<int> st(1);
+        SBuf<int> st(1, s);
         for (int round = 0; round < 2; ++round) {
             gram_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), n, S, pl->part.get());
             PHS_LAUNCH_CHECK();
@@ -835,7 +835,7 @@ phs_status phs_eval(phs_plan_t pl, const double *w_dev, const double *beta_dev, 
     gather_scaled<<<blocks_for(n, 256), 256, 0, s>>>(w_dev, pl->ps.perm.get(), n, std::pow(pl->ps.frame.rho, -(double)pl->k),
                                                       ws);
     PHS_LAUNCH_CHECK();
-    DBuf<double2> yn(m);
+    SBuf<double2> yn(m, s);
     const Frame &fr = pl->ps.frame;
     norm_targets<<<blocks_for(m, 256), 256, 0, s>>>(tgt_dev, m, fr.cx, fr.cy, fr.rho, yn.get());
     PHS_LAUNCH_CHECK();
@@ -854,7 +854,8 @@ phs_status phs_fit_predict_host(const double *pts_host, const double *f_host, in
     PHS_TRY
     PHS_REQUIRE(pts_host && f_host && n > 0 && m >= 0 && (tgt_host || m == 0), PHS_ERR_INVALID_ARG, "bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
-    DBuf<double> pts(2 * n), f(n), w(n), beta(16), tgt(std::max<int64_t>(2 * m, 1)), pred(std::max<int64_t>(m, 1));
+    SBuf<double> pts(2 * n, s), f(n, s), w(n, s), beta(16, s), tgt(std::max<int64_t>(2 * m, 1), s),
+        pred(std::max<int64_t>(m, 1), s);
     PHS_CUDA(cudaMemcpyAsync(pts.get(), pts_host, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.get(), f_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
     if (m) PHS_CUDA(cudaMemcpyAsync(tgt.get(), tgt_host, 2 * m * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1020,7 +1021,7 @@ phs_status phs_dense_matvec(const double *pts_dev, int64_t n, int k, const doubl
     PHS_REQUIRE(pts_dev && t_dev && out_dev && n >= 0 && k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "bad arguments");
     if (n == 0) return PHS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    DBuf<double2> x(n);
+    SBuf<double2> x(n, s);
     pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
     PHS_LAUNCH_CHECK();
     dense_matvec64(x.get(), n, k, t_dev, out_dev, s);
@@ -1033,7 +1034,7 @@ phs_status phs_random_order(int64_t n, uint64_t seed, int64_t *order_dev, phs_st
     PHS_REQUIRE(order_dev && n >= 0 && n < (1ll << 31), PHS_ERR_INVALID_ARG, "bad arguments");
     if (n == 0) return PHS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    DBuf<int> o(n);
+    SBuf<int> o(n, s);
     random_order_dev(n, seed, o.get(), s);
     to_i64<<<blocks_for(n, 256), 256, 0, s>>>(o.get(), n, order_dev);
     PHS_LAUNCH_CHECK();
@@ -1046,10 +1047,10 @@ phs_status phs_maxmin_order(const double *pts_dev, int64_t n, int64_t *order_dev
     PHS_REQUIRE(pts_dev && order_dev && n >= 0 && n < (1ll << 31), PHS_ERR_INVALID_ARG, "bad arguments");
     if (n == 0) return PHS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    DBuf<double2> x(n);
+    SBuf<double2> x(n, s);
     pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
     PHS_LAUNCH_CHECK();
-    DBuf<int> o(n);
+    SBuf<int> o(n, s);
     maxmin_order_dev(x.get(), n, o.get(), s);
     to_i64<<<blocks_for(n, 256), 256, 0, s>>>(o.get(), n, order_dev);
     PHS_LAUNCH_CHECK();
@@ -1063,10 +1064,10 @@ phs_status phs_hmaxmin_order(const double *pts_dev, int64_t n, uint64_t seed, in
     PHS_REQUIRE(pts_dev && order_dev && n >= 0 && n < (1ll << 31), PHS_ERR_INVALID_ARG, "bad arguments");
     if (n == 0) return PHS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    DBuf<double2> x(n);
+    SBuf<double2> x(n, s);
     pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
     PHS_LAUNCH_CHECK();
-    DBuf<int> o(n);
+    SBuf<int> o(n, s);
     hmaxmin_order_dev(x.get(), n, seed, o.get(), s);
     to_i64<<<blocks_for(n, 256), 256, 0, s>>>(o.get(), n, order_dev);
     PHS_LAUNCH_CHECK();
@@ -1079,10 +1080,10 @@ phs_status phs_amaxmin_order(const double *pts_dev, int64_t n, int64_t *order_de
     PHS_REQUIRE(pts_dev && order_dev && n >= 0 && n < (1ll << 31) - 1, PHS_ERR_INVALID_ARG, "bad arguments");
     if (n == 0) return PHS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    DBuf<double2> x(n);
+    SBuf<double2> x(n, s);
     pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
     PHS_LAUNCH_CHECK();
-    DBuf<int> o(n);
+    SBuf<int> o(n, s);
     amaxmin_order_dev(x.get(), n, o.get(), s);
     to_i64<<<blocks_for(n, 256), 256, 0, s>>>(o.get(), n, order_dev);
     PHS_LAUNCH_CHECK();
@@ -1097,10 +1098,10 @@ phs_status phs_knn_prev(const double *pts_dev, int64_t n, const int64_t *order_d
                 PHS_ERR_INVALID_ARG, "bad arguments");
     if (n == 0) return PHS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    DBuf<double2> x(n);
+    SBuf<double2> x(n, s);
     pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
     PHS_LAUNCH_CHECK();
-    DBuf<int> o(n), ell((size_t)m * n);
+    SBuf<int> o(n, s), ell((size_t)m * n, s);
     from_i64<<<blocks_for(n, 256), 256, 0, s>>>(order_dev, n, o.get());
     PHS_LAUNCH_CHECK();
     knn_prev_dev(x.get(), n, o.get(), m, ell.get(), s);
@@ -1118,10 +1119,10 @@ phs_status phs_vecchia_factor(const double *pts_dev, int64_t n, const int64_t *o
                 PHS_ERR_INVALID_ARG, "bad arguments");
     if (n == 0) return PHS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    DBuf<double2> x(n);
+    SBuf<double2> x(n, s);
     pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
     PHS_LAUNCH_CHECK();
-    DBuf<int> o(n), rank(n), ell((size_t)m * n);
+    SBuf<int> o(n, s), rank(n, s), ell((size_t)m * n, s);
     from_i64<<<blocks_for(n, 256), 256, 0, s>>>(order_dev, n, o.get());
     PHS_LAUNCH_CHECK();
     {
@@ -1133,7 +1134,7 @@ phs_status phs_vecchia_factor(const double *pts_dev, int64_t n, const int64_t *o
     }
     rows_to_ell_i32<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>(nbr_dev, n, m, ell.get());
     PHS_LAUNCH_CHECK();
-    DBuf<double> val((size_t)(m + 1) * n);
+    SBuf<double> val((size_t)(m + 1) * n, s);
     int64_t nj = vecchia_factor_dev(x.get(), n, rank.get(), ell.get(), m, nu, alpha, val.get(), s);
     PHS_CUDA(cudaMemcpyAsync(diag_dev, val.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     ell_to_rows_d<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>(val.get(), n, m, 1, offd_dev);

@@ -1603,7 +1603,7 @@ __global__ void eval_outside_sum(const int *out_idx, int nout, int nchunk, const
 template <int K>
 static void eval_launch(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted, const double2 *tgt, int64_t m,
                         double *out, cudaStream_t s) {
-    DBuf<int> box_of(std::max<int64_t>(m, 1));
+    SBuf<int> box_of(std::max<int64_t>(m, 1), s);
     TreeView tv = tree_view(t);
     eval_box_kernel<<<blocks_for(m, 128), 128, 0, s>>>(tv, tgt, m, box_of.get());
     PHS_LAUNCH_CHECK();
@@ -1625,11 +1625,11 @@ static void eval_launch(Fmm &f, const Tree &t, const PointSet &ps, const double 
     for (int64_t i = 0; i < m; ++i)
         if (hb[i] < 0) outside.push_back((int)i);
     if (!outside.empty()) {
-        DBuf<int> oi(outside.size());
+        SBuf<int> oi(outside.size(), s);
         PHS_CUDA(cudaMemcpyAsync(oi.get(), outside.data(), outside.size() * sizeof(int), cudaMemcpyHostToDevice, s));
         const int nchunk = (int)((ps.n + kOutsideChunk - 1) / kOutsideChunk);
         const int nout = (int)outside.size(), batch = 65535;  // grid y limit
-        DBuf<double> part((size_t)nchunk * std::min(nout, batch));
+        SBuf<double> part((size_t)nchunk * std::min(nout, batch), s);
         for (int q0 = 0; q0 < nout; q0 += batch) {
             const int nq = std::min(batch, nout - q0);
             eval_outside_kernel<K><<<dim3((unsigned)nchunk, (unsigned)nq), 256, 0, s>>>(ps.xs.get(), ps.n, w_sorted,

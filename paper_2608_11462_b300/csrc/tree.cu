@@ -292,7 +292,7 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     PHS_REQUIRE(halfwidth > 0 && std::isfinite(halfwidth), PHS_ERR_INVALID_ARG, "domain half-width must be > 0");
     // ---- bounding box and frame
     const int nbb = (int)std::min<int64_t>(592, blocks_for(n, BB_T));
-    DBuf<BBox> part(nbb);
+    SBuf<BBox> part(nbb, s);
     bbox_partial<<<nbb, BB_T, 0, s>>>(pts_dev, n, part.get());
     PHS_LAUNCH_CHECK();
     std::vector<BBox> hp(nbb);
@@ -321,9 +321,9 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     tree.n = n;
     tree.leaf_cap = leaf_cap;
     // ---- Morton sort
-    DBuf<double2> xn(n);
-    DBuf<uint64_t> keys(n);
-    DBuf<int> idx(n);
+    SBuf<double2> xn(n, s);
+    SBuf<uint64_t> keys(n, s);
+    SBuf<int> idx(n, s);
     normalize_keys<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, fr.cx, fr.cy, fr.rho, R, xn.get(), keys.get(),
                                                        idx.get());
     PHS_LAUNCH_CHECK();
@@ -335,7 +335,7 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
                                                      ps.iperm.get());
     PHS_LAUNCH_CHECK();
     {
-        DBuf<int> flag(1);
+        SBuf<int> flag(1, s);
         PHS_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int), s));
         find_duplicates<<<blocks_for(n, 256), 256, 0, s>>>(ps.xs.get(), keys.get(), n, flag.get());
         PHS_LAUNCH_CHECK();
@@ -362,7 +362,7 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     }
     tree.lvl_off.assign(1, 0);
     tree.lvl_off.push_back(1);
-    DBuf<int> coff(cap);
+    SBuf<int> coff(cap, s);
     int l = 0;
     for (;; ++l) {
         const int b0 = tree.lvl_off[l], nb = tree.lvl_off[l + 1] - b0;
@@ -384,7 +384,7 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     // nchild of the deepest level was written by split_count (all zero)
     // ---- leaves
     {
-        DBuf<int> flag(tree.nbox), off(tree.nbox);
+        SBuf<int> flag(tree.nbox, s), off(tree.nbox, s);
         leaf_flags<<<blocks_for(tree.nbox, 256), 256, 0, s>>>(tree.nchild.get(), tree.nbox, flag.get());
         PHS_LAUNCH_CHECK();
         tree.nleaf = (int)exclusive_scan_i32(flag.get(), off.get(), tree.nbox, s);
@@ -403,7 +403,7 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
                              cudaMemcpyHostToDevice, s));
     TreeView tv = tree_view(tree);
     {
-        DBuf<int> cnt(tree.nbox);
+        SBuf<int> cnt(tree.nbox, s);
         tree.v_off.alloc(tree.nbox + 1);
         vlist_kernel<false><<<blocks_for(tree.nbox, 128), 128, 0, s>>>(tv, tree.nbox, cnt.get(), nullptr, nullptr,
                                                                        nullptr);
@@ -419,8 +419,8 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
         tree.m2l_pairs = tot;
     }
     {
-        DBuf<int> cnt(tree.nbox);
-        DBuf<unsigned long long> pairs(1);
+        SBuf<int> cnt(tree.nbox, s);
+        SBuf<unsigned long long> pairs(1, s);
         PHS_CUDA(cudaMemsetAsync(pairs.get(), 0, sizeof(unsigned long long), s));
         tree.near_off.alloc(tree.nbox + 1);
         nearlist_kernel<false><<<blocks_for(tree.nbox, 128), 128, 0, s>>>(tv, tree.nbox, cnt.get(), nullptr, nullptr,
@@ -440,10 +440,10 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     }
     {
         const int nl = tree.nleaf;
-        DBuf<int> up_len(nl), gcnt(nl), gcur(nl), mx(2);
-        DBuf<uint64_t> ckey(nl);
+        SBuf<int> up_len(nl, s), gcnt(nl, s), gcur(nl, s), mx(2, s);
+        SBuf<uint64_t> ckey(nl, s);
         tree.p2p_order.alloc(nl);
-        DBuf<unsigned long long> prs(2);
+        SBuf<unsigned long long> prs(2, s);
         PHS_CUDA(cudaMemsetAsync(prs.get(), 0, 2 * sizeof(unsigned long long), s));
         PHS_CUDA(cudaMemsetAsync(gcnt.get(), 0, nl * sizeof(int), s));
         PHS_CUDA(cudaMemsetAsync(gcur.get(), 0, nl * sizeof(int), s));
