@@ -58,3 +58,23 @@ def test_options_default_host_only(native):
 def test_build_targets_sm103a_only():
     from paper_2608_11462_b300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _header_struct(name):
+    """(type, field) pairs of a `typedef struct { ... } name;` in include/phs.h, comments
+    stripped."""
+    with open(os.path.join(ROOT, "include", "phs.h")) as fh:
+        txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", txt).group(1)
+    return re.findall(r"^\s*(int|double|float|uint64_t|int64_t)\s+(\w+)\s*;", body, re.M)
+
+
+def test_ctypes_mirrors_follow_the_header(native):
+    """PhsOptions and PhsFitInfo list the header's fields in its order with matching C
+    types, so a field added on one side only is caught on CPU."""
+    ctype = {"int": ctypes.c_int, "double": ctypes.c_double, "float": ctypes.c_float,
+             "uint64_t": ctypes.c_uint64, "int64_t": ctypes.c_int64}
+    for cname, mirror in (("phs_options", native.PhsOptions), ("phs_fit_info", native.PhsFitInfo)):
+        want = [(f, ctype[t]) for t, f in _header_struct(cname)]
+        assert want, cname
+        assert [(f, t) for f, t in mirror._fields_] == want, cname
