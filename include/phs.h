@@ -169,6 +169,9 @@ phs_status phs_fit_predict_host(const double *pts_host, const double *f_host, in
                                 double *w_host, double *beta_host, double *pred_host,
                                 phs_fit_info *info, phs_stream_t stream);
 
+/* Releases every device buffer the plan owns (resource management, no counterpart in the
+ * paper).  Synchronises the device first, so work still queued on the plan's stream
+ * finishes; NULL is accepted and does nothing; the handle is invalid afterwards. */
 phs_status phs_plan_destroy(phs_plan_t plan);
 
 /* ---- inspection (small host copies; synchronise) --------------------------- */
