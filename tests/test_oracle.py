@@ -293,7 +293,8 @@ def test_vecchia_full_conditioning_is_exact_inverse(nu, alpha):
     diag, offd, nj = oracle.vecchia_factor(x, order, nbr, n - 1, nu, alpha)
     assert nj == 0
     U = oracle.vecchia_dense(nbr, diag, offd)
-    Sigma = 2 ** (1 - nu) / scipy.special.gamma(nu) * (alpha * cdist(x, x)) ** nu * scipy.special.kv(nu, alpha * cdist(x, x) + 1e-300)
+    with np.errstate(invalid="ignore"):  # the diagonal (0 x inf) is set to K(0) = 1 below
+        Sigma = 2 ** (1 - nu) / scipy.special.gamma(nu) * (alpha * cdist(x, x)) ** nu * scipy.special.kv(nu, alpha * cdist(x, x) + 1e-300)
     np.fill_diagonal(Sigma, 1.0)
     Sinv = np.linalg.inv(Sigma)
     assert np.linalg.norm(U @ U.T - Sinv) <= 1e-8 * np.linalg.norm(Sinv)
