@@ -545,3 +545,38 @@ def test_dense_eval_abs_is_abs_matrix_times_abs_weights():
         assert np.all(np.abs(oracle.dense_eval(x, w, k, x[:40])) <= got * (1 + 1e-13))
     M = oracle.dense_matrix(x, 3)  # r^3 >= 0: with w >= 0 every term has one sign
     assert np.allclose(oracle.dense_eval_abs(x, np.abs(w), 3, x[:10]), M[:10] @ np.abs(w), rtol=1e-13)
+
+
+try:
+    from hypothesis import given, settings, strategies as hst
+    HAVE_HYPOTHESIS = True
+except ImportError:  # pragma: no cover
+    HAVE_HYPOTHESIS = False
+
+if HAVE_HYPOTHESIS:
+    @settings(max_examples=60, deadline=None)
+    @given(n=hst.integers(2, 70), seed=hst.integers(0, 2**31 - 1), kind=hst.sampled_from(["uniform", "dups", "grid"]))
+    def test_amaxmin_properties_random(n, seed, kind):
+        """Random small sets (with coincident points and lattices): the order is a
+        permutation, levels never decrease, and every point before the coincident tail
+        is at least half as far from its predecessors as the farthest point still to
+        come (brute force)."""
+        rng = np.random.default_rng(seed)
+        if kind == "uniform":
+            x = rng.random((n, 2))
+        elif kind == "dups":
+            x = rng.random((max(1, n // 2), 2))
+            x = x[rng.integers(0, len(x), n)]
+        else:
+            g = int(np.ceil(np.sqrt(n)))
+            x = np.stack(np.meshgrid(np.arange(g), np.arange(g)), -1).reshape(-1, 2)[:n] / max(g - 1, 1)
+        order, level, _ = oracle.amaxmin_order(x)
+        assert sorted(order.tolist()) == list(range(n))
+        assert np.all(np.diff(level) >= 0)
+        head = int(np.sum(level < 31))
+        d2 = ((x[:, None, :] - x[None, :, :]) ** 2).sum(-1)
+        dmin = d2[order[0]].copy()
+        for k in range(1, head):
+            rest = order[k:head]  # coincident tail points (distance 0) are left out
+            assert dmin[order[k]] >= 0.25 * dmin[rest].max() * (1 - 1e-12)
+            dmin = np.minimum(dmin, d2[order[k]])
