@@ -1,0 +1,38 @@
+"""CPU checks that the seeded generators produce the workloads the benchmark and the
+full-size parity tests are described with (sizes, mixes, bounds, fields, determinism)."""
+import numpy as np
+
+import synth
+
+
+def test_tps_1m_recipe():
+    w = synth.workload("tps_1m")
+    p, f, t = w["points"], w["f"], w["targets"]
+    assert p.shape == (1_048_576, 2) and t.shape == (10_000, 2) and w["k"] == 2
+    assert p.min() >= 0.0 and p.max() <= 1.0 and t.min() >= 0.0 and t.max() <= 1.0
+    # 943,718 uniform points first, then 104,858 clustered ones in 50 equal clusters
+    uni, cl = p[:943_718], p[943_718:]
+    assert len(cl) == 104_858
+    # the clustered tail is far denser than the uniform head: its points have much closer
+    # nearest neighbours (sigma = 0.005 against a uniform spacing of ~1e-3)
+    from scipy.spatial import cKDTree
+    d_uni = cKDTree(uni[:20000]).query(uni[:2000], k=2)[0][:, 1].mean()
+    d_cl = cKDTree(cl).query(cl[:2000], k=2)[0][:, 1].mean()
+    assert d_cl < 0.3 * d_uni
+    x, y = p[:, 0], p[:, 1]
+    assert np.array_equal(f, np.exp(-8 * ((x - 0.3) ** 2 + (y - 0.6) ** 2)) + np.sin(10 * x * y))
+    # deterministic
+    w2 = synth.workload("tps_1m", n=4096)
+    w3 = synth.workload("tps_1m", n=4096)
+    assert np.array_equal(w2["points"], w3["points"]) and np.array_equal(w2["targets"], w3["targets"])
+
+
+def test_small_workloads_recipe():
+    u = synth.workload("uniform_tps")
+    assert u["points"].shape == (1500, 2) and u["targets"].shape == (500, 2) and u["k"] == 2
+    x, y = u["points"][:, 0], u["points"][:, 1]
+    assert np.array_equal(u["f"], np.sin(4 * x) * np.cos(3 * y) + 0.5 * x ** 2)
+    c = synth.workload("cubic_mix", n=20_000)
+    assert c["points"].shape == (20_000, 2) and c["k"] == 3
+    assert c["points"].min() >= 0.0 and c["points"].max() <= 1.0
+    assert synth.workload("cubic_mix")["points"].shape == (100_000, 2)
