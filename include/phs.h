@@ -27,6 +27,12 @@
  *    human-readable message for the most recent failing call on the calling
  *    host thread is available from phs_last_error().
  *  - A plan may be used from one stream at a time.
+ *  - Device memory: a plan's state is allocated by phs_plan_create and freed by
+ *    phs_plan_destroy.  Temporaries of the calls come from a memory pool the
+ *    library creates per device on first use, allocated and released in order
+ *    on `stream`; the pool keeps up to 1 GB of freed blocks for reuse by later
+ *    calls and returns them at process exit.  phs_dense_matvec_noalloc uses
+ *    neither (see its entry).
  */
 #ifndef PHS_B300_H
 #define PHS_B300_H
