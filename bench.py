@@ -71,10 +71,12 @@ def parse():
     ap.add_argument("--ordering", type=int, default=3, choices=[0, 1, 2, 3],
                     help="Vecchia enumeration: 0 random, 1 exact maxmin, 2 hierarchical maximin, "
                          "3 dyadic approximate maximin")
-    ap.add_argument("--case", default="step", choices=["step", "plan", "matvec", "precond"],
+    ap.add_argument("--case", default="step", choices=["step", "plan", "matvec", "precond", "cubic"],
                     help="step: the bench (plan + fit + evaluation, the JSON contract line); plan / "
                          "matvec / precond: one piece of it repeated --steps times on one plan, for "
-                         "profiling (prints its own short line)")
+                         "profiling; cubic: the cubic-PHS workload (n = 100,000 from 20 clusters, "
+                         "k = 3, m = 20, library defaults, tol 1e-8) timed like a step (each of these "
+                         "prints its own short line)")
     return ap.parse_args()
 
 
@@ -225,6 +227,31 @@ def main():
     f_d = torch.tensor(f, device=dev)
     tg_d = torch.tensor(targets, device=dev)
     stream = torch.cuda.current_stream(dev)
+    if args.case == "cubic":
+        wc = synth.workload("cubic_mix")
+        pc, fc, tc = (torch.tensor(wc[key], device=dev) for key in ("points", "f", "targets"))
+        copts = phs.options(3, tol=1e-8, maxiter=400)
+        res = []
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan = phs.Plan(pc, 3, vecchia_m=20, opts=copts)
+            w, beta, info = plan.fit(fc)
+            plan.eval(w, beta, tc)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            plan.close()
+            if i >= args.warmup:
+                res.append((e0.elapsed_time(e1) / 1e3, info))
+        if rank == 0:
+            t = float(np.mean([r[0] for r in res]))
+            info = res[-1][1]
+            print(json.dumps({"case": "cubic", "workload": "cubic_mix", "n": len(wc["f"]), "k": 3, "vecchia_m": 20,
+                              "value_s": t, "steps": args.steps, "iters": info["iters"],
+                              "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"],
+                              "ms_fit": info["ms_fit"], "ms_matvec_avg": info["ms_matvec_avg"]}))
+        return
     if args.case != "step":
         # one piece of the step on the bench workload, for profilers; no timing contract
         reps = max(1, args.steps)
