@@ -41,6 +41,20 @@ def test_phi_closed_forms_345_triangle():
             assert M[j, i] == M[i, j]
 
 
+def test_poly_basis_hand_worked_rows():
+    """B of Eq. (1.3) against rows worked by hand: the monomial order (graded
+    lexicographic), the x/y roles and the powers are fixed independently of the code."""
+    g = _gold("poly_basis.json")
+    for case in g["rows"]:
+        got = oracle.poly_basis(np.array([case["point"]]), case["deg"])[0]
+        assert got.tolist() == [float(v) for v in case["row"]], case
+    # several points at once: one row each, in input order
+    pts = np.array([c["point"] for c in g["rows"] if c["deg"] == 2])
+    want = np.array([c["row"] for c in g["rows"] if c["deg"] == 2], dtype=float)
+    assert np.array_equal(oracle.poly_basis(pts, 2), want)
+    assert oracle.n_poly(2) == 6 and oracle.n_poly(3) == 10
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_dense_matvec_is_symmetric_form(k):
     x = _pts(300, 1)
