@@ -138,8 +138,9 @@ def test_eval_matches_dense_interpolant(phs, k):
 def test_fit_cubic_mix_matches_dense_solve(phs):
     """Workload cubic_mix scaled to n = 2,000 (k = 3, S = 3, Vecchia m = 20)."""
     w_ = synth.workload("cubic_mix", n=2000, n_targets=300)
-    plan = phs.Plan(_t(w_["points"]), 3, vecchia_m=20, opts=phs.options(3, tol=1e-11, maxiter=400))
-    w, beta, info = plan.fit(_t(w_["f"]), allow_not_converged=True)
+    plan = phs.Plan(_t(w_["points"]), 3, vecchia_m=20, opts=phs.options(3, tol=1e-10, maxiter=400))
+    w, beta, info = plan.fit(_t(w_["f"]))
+    assert info["converged"] == 1, info
     pred = plan.eval(w, beta, _t(w_["targets"])).cpu().numpy()
     ref = oracle.fit_dense(w_["points"], w_["f"], 3)
     want = oracle.predict(ref, w_["targets"])
@@ -381,32 +382,118 @@ def test_plan_vecchia_matches_oracle(phs):
     _check_factor(d_g, o_g, d_w, o_w, _local_kappa(xn, nbr, 1.0, 0.35), xn, nbr, 1.0, 0.35)
 
 
+EPS = 2.0 ** -52
+
+
+def _sparse_u(nbr, diag, offd):
+    """U~ of Fig. 1 as a sparse matrix: column i holds 1/c_i at row i and -lambda/c_i at
+    the rows sigma(i)."""
+    import scipy.sparse as sp
+    n, m = nbr.shape
+    cols = np.repeat(np.arange(n), m + 1)
+    rows = np.concatenate([np.arange(n)[:, None], nbr], axis=1).ravel()
+    vals = np.concatenate([diag[:, None], offd], axis=1).ravel()
+    keep = rows >= 0
+    return sp.csc_matrix((vals[keep], (rows[keep], cols[keep])), shape=(n, n))
+
+
+def _precond_bound(U, B, r, lowrank):
+    """Componentwise bound on |z_gpu - z_oracle| when both apply the SAME factor U~ to r:
+    the two differ only by the rounding of their sums and of the projection (GPU: Q from
+    Cholesky QR; oracle: Householder QR; the projector P = I - QQ' is the same up to
+    ~eps kappa(B)).  With |.| taken entrywise, g = 8 (row length + m + S) eps:
+      v = P r:        |dv| <= g kB (|r| + |Q||Q|'|r|)
+      y = U' v:       |dy| <= g |U|'|v| + |U|'|dv|
+      t = U y:        |dt| <= g |U||y| + |U||dy|
+      z = P t (plain) or t - G(G'v) (low-rank, G = U U'Q Rc^-1, Rc'Rc = Q'U U'Q):
+                      |dz| <= |dt| + |Q||Q|'|dt| + g kB (|t| + |Q||Q|'|t|)   (plain)
+                      |dz| <= |dt| + 4 g kC |G|(|G|'|v|) + |G|(|G|'|dv|)     (low-rank)
+    (kB = cond(B), kC = cond(Q'U U'Q); the four products U'Q, C, Rc^-1 and U Y each
+    contribute a relative error up to g kC to G G'v.)
+    Returns (bound, z_scale) where z_scale is the size of the terms summed."""
+    Ua = abs(U)
+    Q, _ = np.linalg.qr(B)
+    S = Q.shape[1]
+    row_len = np.diff(U.tocsr().indptr).max()
+    col_len = np.diff(U.indptr).max()
+    g = 8 * (row_len + col_len + S) * EPS
+    kB = np.linalg.cond(B)  # sensitivity of the projector to the QR algorithm
+    Qa = np.abs(Q)
+    v = r - Q @ (Q.T @ r)
+    dv = g * kB * (np.abs(r) + Qa @ (Qa.T @ np.abs(r)))
+    y = U.T @ v
+    dy = g * (Ua.T @ np.abs(v)) + Ua.T @ dv
+    t = U @ y
+    dt = g * (Ua @ np.abs(y)) + Ua @ dy
+    if not lowrank:
+        dz = dt + Qa @ (Qa.T @ dt) + g * kB * (np.abs(t) + Qa @ (Qa.T @ np.abs(t)))
+        return dz, np.abs(t) + Qa @ (Qa.T @ np.abs(t))
+    Y = U.T @ Q
+    C = Y.T @ Y
+    Rc = np.linalg.cholesky(C).T
+    G = U @ np.linalg.solve(Rc.T, Y.T).T
+    Ga = np.abs(G)
+    kC = np.linalg.cond(C)
+    dz = dt + 4 * g * kC * (Ga @ (Ga.T @ np.abs(v))) + Ga @ (Ga.T @ dv)
+    return dz, np.abs(t) + Ga @ (Ga.T @ np.abs(v))
+
+
 @pytest.mark.parametrize("lowrank", [0, 1])
 @pytest.mark.parametrize("wl,n", [("uniform_tps", 2000), ("tps_1m", 5003)])
 def test_plan_precond_matches_oracle(phs, lowrank, wl, n):
-    """Preconditioner of the projected system, plain (P S~^{-1} P) and with the
-    low-rank term (the inverse of Q_perp' S~ Q_perp), against the oracle on the
-    plan's own factor.  Error bound: the factor apply carries eps * kappa of the
-    local covariances; the low-rank form subtracts G (G' r) from t = S~^{-1} r, so
-    its absolute error scales with ||t||, not with the (possibly smaller) result."""
+    """Preconditioner apply of the projected system (Sec. 2.2), plain (P S~^{-1} P) and
+    with the low-rank term (the inverse of Q_perp' S~ Q_perp), against the oracle's
+    apply of the plan's OWN factor (read back exactly), so the comparison measures the
+    apply alone: every entry within a componentwise rounding bound, whatever the
+    conditioning of the local covariances.  The factor itself is compared with the
+    oracle's, per point and with each point's own condition number, by
+    test_plan_*vecchia_matches_oracle."""
     w_ = synth.workload(wl, n=n)
     plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=20, opts=phs.options(2, precond_lowrank=lowrank))
     xn, _, _ = oracle.normalize(w_["points"], 0.25)
     order, nbr = plan.vecchia()
-    d, o, _ = oracle.vecchia_factor(xn, order, nbr, 20, 1.0, 0.35)
+    d, o = plan.vecchia_factor()
     r = np.random.default_rng(0).standard_normal(n)
     B = oracle.poly_basis(xn, 1)
     Q, _ = np.linalg.qr(B)
     P = lambda v: v - Q @ (Q.T @ v)  # noqa: E731
     want = oracle.projected_precond(xn, 1, (nbr, d, o), P(r), bool(lowrank))
     got = plan.precond(_t(r)).cpu().numpy()
-    kap = _local_kappa(xn, nbr, 1.0, 0.35).max()
-    scale = np.linalg.norm(oracle.vecchia_apply(nbr, d, o, P(r))) if lowrank else np.linalg.norm(want)
-    err = np.linalg.norm(got - want)
-    assert err <= 64 * 2.2e-16 * kap * scale, (err, np.linalg.norm(want), scale, kap)
+    bound, scale = _precond_bound(_sparse_u(nbr, d, o), B, r, bool(lowrank))
+    err = np.abs(got - want)
+    worst = np.max(err / bound)
+    print(f"precond {wl} n={n} lowrank={lowrank}: max |dz|/bound = {worst:.3g}, "
+          f"max |dz|/scale = {np.max(err / scale):.3g}, ||dz||/||z|| = {np.linalg.norm(err) / np.linalg.norm(want):.3g}")
+    assert worst <= 1.0, worst
     # the low-rank result lies in range(P) without a final projection
     if lowrank:
         assert np.linalg.norm(B.T @ got) <= 1e-9 * np.linalg.norm(B) * np.linalg.norm(got)
+
+
+@pytest.mark.parametrize("lowrank", [0, 1])
+def test_plan_precond_well_conditioned_strict(phs, lowrank):
+    """A short-range Matern (alpha = 160 in the normalised frame, nu = 1) keeps every
+    local covariance well conditioned (kappa printed, < 1e5), so the factor is unique to
+    rounding: the GPU preconditioner -- its own factor and apply -- matches the oracle's
+    end to end within 1e-12 relative."""
+    w_ = synth.workload("tps_1m", n=4001)
+    alpha = 160.0
+    plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=20,
+                    opts=phs.options(2, precond_lowrank=lowrank, alpha=alpha, nu=1.0))
+    xn, _, _ = oracle.normalize(w_["points"], 0.25)
+    order, nbr = plan.vecchia()
+    kap = _local_kappa(xn, nbr, 1.0, alpha)
+    d, o, nj = oracle.vecchia_factor(xn, order, nbr, 20, 1.0, alpha)
+    assert nj == 0
+    r = np.random.default_rng(1).standard_normal(len(xn))
+    B = oracle.poly_basis(xn, 1)
+    Q, _ = np.linalg.qr(B)
+    want = oracle.projected_precond(xn, 1, (nbr, d, o), r - Q @ (Q.T @ r), bool(lowrank))
+    got = plan.precond(_t(r)).cpu().numpy()
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    print(f"precond alpha={alpha} lowrank={lowrank}: max local kappa = {kap.max():.3g}, rel err = {rel:.3g}")
+    assert kap.max() < 1e5
+    assert rel <= 1e-12, rel
 
 
 # ---------------------------------------------------------------- fit and eval
@@ -461,17 +548,46 @@ def test_lowrank_precond_fit_same_solution_fewer_iterations(phs):
     assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(a))
 
 
-@pytest.mark.parametrize("k", [4])
-def test_fit_even_k_higher_order(phs, k):
-    pts = np.random.default_rng(21).random((900, 2))
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("n", [900, 2000])
+def test_fit_higher_order_matches_dense_solve(phs, k, n):
+    """k = 4 (r^4 log r) and k = 5 (r^5), quadratic block (S = 6), domain [-1, 1]^2
+    (Sec. 2.2, Sec. 3.3): the PCG converges to 1e-10 and the interpolant is within 1e-8
+    relative of the dense augmented solve at held-out points; B'w = 0 and the nodes
+    are interpolated."""
+    pts = np.random.default_rng(21).random((n, 2))
     f = synth.f_uniform_tps(pts)
     tg = np.random.default_rng(22).random((200, 2))
-    plan = phs.Plan(_t(pts), k, vecchia_m=30, opts=phs.options(k, tol=1e-11, maxiter=400))
-    w, beta, info = plan.fit(_t(f), allow_not_converged=True)
+    plan = phs.Plan(_t(pts), k, vecchia_m=30, opts=phs.options(k, tol=1e-10, maxiter=400))
+    w, beta, info = plan.fit(_t(f))
+    assert info["converged"] == 1, info
     pred = plan.eval(w, beta, _t(tg)).cpu().numpy()
     ref = oracle.fit_dense(pts, f, k, halfwidth=1.0)
     want = oracle.predict(ref, tg)
-    assert np.max(np.abs(pred - want)) <= 1e-6 * np.max(np.abs(want))
+    err = np.max(np.abs(pred - want)) / np.max(np.abs(want))
+    print(f"k={k} n={n}: iters {info['iters']}, rel_res_true {info['rel_res_true']:.2e}, interpolant err {err:.2e}")
+    assert err <= 1e-8, (err, info)
+    wg = w.cpu().numpy()
+    B = oracle.poly_basis(pts, 2)
+    assert np.linalg.norm(B.T @ wg) <= 1e-10 * np.linalg.norm(B) * np.linalg.norm(wg)
+    at_nodes = plan.eval(w, beta, _t(pts)).cpu().numpy()
+    assert np.max(np.abs(at_nodes - f)) <= 1e-8 * np.max(np.abs(f))
+
+
+def test_beta_monomial_order_gpu(phs):
+    """f a full quadratic in the plan's normalised frame, k = 4 (S = 6): f lies in span(B),
+    so w = 0 and beta must return the coefficients in the order 1, x, y, x^2, xy, y^2
+    (Eq. 1.3, graded lexicographic) -- fixed here by hand, independently of the oracle."""
+    pts = np.random.default_rng(33).random((700, 2))
+    plan = phs.Plan(_t(pts), 4, vecchia_m=10)
+    fr, _ = plan.frame()
+    xn = (pts - np.array(fr[:2])) * fr[2]
+    x, y = xn[:, 0], xn[:, 1]
+    coef = np.array([0.5, -1.0, 2.0, 3.0, -4.0, 5.0])
+    f = coef[0] + coef[1] * x + coef[2] * y + coef[3] * x * x + coef[4] * x * y + coef[5] * y * y
+    w, beta, info = plan.fit(_t(f))
+    assert np.max(np.abs(w.cpu().numpy())) <= 1e-10
+    assert np.allclose(beta.cpu().numpy(), coef, rtol=0, atol=1e-12), beta
 
 
 def test_polynomial_reproduction_gpu(phs):
@@ -505,6 +621,35 @@ def test_host_end_to_end(phs):
     assert np.max(np.abs(pred - want)) <= 1e-8 * np.max(np.abs(want))
 
 
+# ---------------------------------------------------------------- bounded device waits
+def test_tc_wait_limit_reports_timeout_and_plan_stays_usable(phs):
+    """The tensor-core M2L's pipeline waits are bounded.  With the limit set to 1 ns a wait
+    gives up: the pass stops issuing work, drains the multiply-adds and copies already in
+    flight (fixed 2 s limit) and flags the plan; phs_eval then returns PHS_ERR_TIMEOUT.
+    With the default limit restored the same plan evaluates and fits correctly."""
+    w_ = synth.workload("tps_1m", n=60000, n_targets=300)
+    pts, f, tg = w_["points"], w_["f"], w_["targets"]
+    plan = phs.Plan(_t(pts), 2, vecchia_m=10, opts=phs.options(2, m2l_tensor=1, leaf_cap=32))
+    assert plan.kernel_work()["tc_steps"] > 0
+    rng = np.random.default_rng(4)
+    w = rng.standard_normal(len(f))
+    beta = np.zeros(3)
+    plan.set_wait_limit(1)
+    with pytest.raises(phs.PhsError) as ei:
+        plan.eval(_t(w), _t(beta), _t(tg))
+    assert ei.value.code == 7, ei.value
+    plan.set_wait_limit(0)
+    got = plan.eval(_t(w), _t(beta), _t(tg)).cpu().numpy()
+    xn, c, rho = oracle.normalize(pts, 0.25)
+    yn = (tg - c) * rho
+    want = oracle.dense_eval(xn, w / rho ** 2, 2, yn)
+    scale = oracle.dense_eval_abs(xn, w / rho ** 2, 2, yn)
+    assert np.max(np.abs(got - want) / scale) <= 1e-10
+    wf, bf, info = plan.fit(_t(f))
+    assert info["converged"] == 1 and info["rel_res_true"] <= 1e-8, info
+    plan.close()
+
+
 # ---------------------------------------------------------------- errors and edge cases
 def test_errors_are_reported(phs):
     pts = np.random.default_rng(0).random((50, 2))
@@ -528,6 +673,42 @@ def test_errors_are_reported(phs):
     assert np.allclose(plan.matvec(_t(t)).cpu().numpy(), oracle.dense_matvec(pts, 2, t), rtol=1e-10)
 
 
+def _node_residual_check(plan, pts, f, w, beta, k, rows):
+    """Per-node check of a fit at a size with no dense solve.  The solver returns beta with
+    R beta = Q'(f - M w), so at every node the interpolant misses f by exactly the
+    projected residual: f - M w - B beta = P (f - M w), P = I - QQ'.  The test recomputes
+    that residual vector r = P (f - M w) with the library's FP64 matvec and a numpy QR of
+    B, then, at sampled nodes, evaluates the interpolant EXACTLY with the oracle (O(n) per
+    row) and checks
+      * |f_i - f^(x_i) - r_i| <= 1e-10 * sum_j |w_j phi_ij| + 1e-12 ||f||_inf  (the
+        identity above, up to the matvec's error on that row), and
+      * ||r||_inf <= 1e-8 ||f||_inf: the interpolation misfit at EVERY node within 1e-8
+        of the data's scale, and ||r||_2 / ||P f||_2 as reported (rel_res_true).
+    Returns (max_i |r_i| / ||f||_inf, the sampled node misfit / ||f||_inf)."""
+    xn, c, rho = oracle.normalize(pts, 0.25)
+    wg = w.cpu().numpy()
+    wn = wg / rho ** k
+    bn = beta.cpu().numpy()
+    Mw = plan.matvec(w).cpu().numpy()
+    B = oracle.poly_basis(xn, 1)
+    Q, _ = np.linalg.qr(B)
+    g = f - Mw
+    r = g - Q @ (Q.T @ g)
+    Pf = f - Q @ (Q.T @ f)
+    fin = np.max(np.abs(f))
+    fhat = oracle.interpolant(xn, wn, bn, k, 1, xn[rows])
+    wscale = oracle.dense_eval_abs(xn, wn, k, xn[rows])
+    d = f[rows] - fhat
+    gap = np.abs(d - r[rows])
+    assert np.all(gap <= 1e-10 * wscale + 1e-12 * fin), np.max(gap / (1e-10 * wscale + 1e-12 * fin))
+    rinf = np.max(np.abs(r)) / fin
+    print(f"node residual: ||r||_inf/||f||_inf = {rinf:.3e}, sampled misfit {np.max(np.abs(d)) / fin:.3e}, "
+          f"||r||_2/||Pf||_2 = {np.linalg.norm(r) / np.linalg.norm(Pf):.3e}")
+    assert rinf <= 1e-8, rinf
+    assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(Pf)
+    return rinf, np.max(np.abs(d)) / fin
+
+
 # ---------------------------------------------------------------- the bench workload at full size
 def test_full_size_tps_1m_sampled_rows(phs):
     """The clustered TPS workload at n = 1,048,576 with the bench's options (nu = 1,
@@ -536,8 +717,9 @@ def test_full_size_tps_1m_sampled_rows(phs):
     * FMM matvec rows within 1e-10 of the exact row sums, relative to the sum of the
       absolute terms (the rounding scale of any summation order);
     * the fit converges in fewer than 15 iterations; B'w = 0 to rounding; at sampled
-      nodes the exact interpolant misses f by no more than the solve's residual, since
-      f - M w - B beta = P (f - M w) (plus the FMM error on that row);
+      nodes the exact interpolant misses f by exactly the recomputed projected residual
+      P (f - M w) (plus the FMM error on that row), whose inf-norm over all nodes is
+      within 1e-8 of ||f||_inf (_node_residual_check);
     * evaluation at sampled held-out targets within 1e-10 of the exact interpolant,
       relative to the same absolute scale."""
     w_ = synth.workload("tps_1m")
@@ -558,16 +740,12 @@ def test_full_size_tps_1m_sampled_rows(phs):
     # fit
     w, beta, info = plan.fit(_t(f))
     assert info["converged"] == 1 and info["iters"] < 15 and info["rel_res_true"] <= 1e-8, info
+    _node_residual_check(plan, pts, f, w, beta, 2, rows)
     xn, c, rho = oracle.normalize(pts, 0.25)
     wn = w.cpu().numpy() / rho ** 2
     beta = beta.cpu().numpy()
     B = oracle.poly_basis(xn, 1)
     assert np.linalg.norm(B.T @ wn) <= 1e-12 * np.linalg.norm(B) * np.linalg.norm(wn)
-    fhat = oracle.interpolant(xn, wn, beta, 2, 1, xn[rows])
-    wscale = oracle.dense_eval_abs(xn, wn, 2, xn[rows])
-    res = np.abs(f[rows] - fhat)
-    bound = 2e-8 * np.linalg.norm(f) + 1e-10 * wscale
-    assert np.all(res <= bound), (res / bound).max()
     # evaluation at held-out targets
     sel = rng.choice(len(tg), 400, replace=False)
     got = plan.eval(w, _t(beta), _t(tg[sel])).cpu().numpy()
@@ -582,8 +760,8 @@ def test_full_size_tps_1m_sampled_rows(phs):
 def test_full_size_cubic_mix_sampled_rows(phs):
     """The cubic PHS workload at its full size (n = 100,000 from 20 clustered Gaussians,
     k = 3, S = 3, Vecchia m = 20, nu = 1.5, tol 1e-8) on sampled rows, as for the 1M TPS
-    set: Chebyshev-FMM matvec rows, the interpolant at sampled nodes within the solve's
-    residual, B'w = 0 and held-out targets."""
+    set: Chebyshev-FMM matvec rows, the interpolant at sampled nodes against the
+    recomputed residual (_node_residual_check), B'w = 0 and held-out targets."""
     w_ = synth.workload("cubic_mix")
     pts, f, tg = w_["points"], w_["f"], w_["targets"]
     n = len(f)
@@ -599,15 +777,12 @@ def test_full_size_cubic_mix_sampled_rows(phs):
     assert err.max() <= 1e-10, err.max()
     w, beta, info = plan.fit(_t(f))
     assert info["converged"] == 1 and info["rel_res_true"] <= 1e-8, info
+    _node_residual_check(plan, pts, f, w, beta, 3, rows)
     xn, c, rho = oracle.normalize(pts, 0.25)
     wn = w.cpu().numpy() / rho ** 3
     beta = beta.cpu().numpy()
     B = oracle.poly_basis(xn, 1)
     assert np.linalg.norm(B.T @ wn) <= 1e-12 * np.linalg.norm(B) * np.linalg.norm(wn)
-    fhat = oracle.interpolant(xn, wn, beta, 3, 1, xn[rows])
-    bound = 2e-8 * np.linalg.norm(f) + 1e-10 * oracle.dense_eval_abs(xn, wn, 3, xn[rows])
-    res = np.abs(f[rows] - fhat)
-    assert np.all(res <= bound), (res / bound).max()
     sel = rng.choice(len(tg), 300, replace=False)
     got = plan.eval(w, _t(beta), _t(tg[sel])).cpu().numpy()
     yn = (tg[sel] - c) * rho
