@@ -55,7 +55,7 @@ typedef enum {
     PHS_ERR_NOT_CONVERGED = 5,    /* PCG reached maxiter above tolerance (results still written) */
     PHS_ERR_CHOLESKY = 6,         /* a local Vecchia factor failed even after jitter, or the
                                      S x S matrix Q' S~^{-1} Q of the low-rank term did */
-    PHS_ERR_TIMEOUT = 7           /* reserved for bounded device waits */
+    PHS_ERR_TIMEOUT = 7           /* a bounded device wait expired (see phs_plan_set_wait_limit) */
 } phs_status;
 
 /* Solver options (defaults from phs_options_default). */
@@ -207,6 +207,14 @@ phs_status phs_plan_work(phs_plan_t plan, int64_t *counts_host);
  *   [4] tcgen05.mma instructions per step,
  *   [5] multiply-adds of one instruction (M * N * K). */
 phs_status phs_plan_kernel_work(phs_plan_t plan, int64_t *counts_host);
+/* Wall-time limit, in ns, of each pipeline wait in the main loop of the tensor-core
+ * M2L (a diagnostics and test hook; no counterpart in the paper).  0 restores the
+ * default of 2 s.  A wait that exceeds it makes every block of the pass stop issuing
+ * work; the multiply-adds and copies already issued are still waited for (with the
+ * fixed 2 s limit) before the kernel exits, so the device and the plan stay usable, and
+ * the next phs_fit or phs_eval on the plan returns PHS_ERR_TIMEOUT (phs_matvec is
+ * asynchronous and does not check). */
+phs_status phs_plan_set_wait_limit(phs_plan_t plan, int64_t ns);
 /* Per-phase device timing of the most recent phs_fit / phs_matvec calls, in ms,
  * measured with CUDA events on the plan's stream when enabled (0/1).
  * ms_host[0..7] = (p2p, m2l, upward, downward, precond, vector, eval, total);
@@ -220,15 +228,19 @@ phs_status phs_dense_matvec(const double *pts_dev, int64_t n, int k, const doubl
                             double *out_dev, phs_stream_t stream);
 /* The same exact product as phs_dense_matvec without allocating device memory.  The
  * paper has no counterpart: this entry point exists for callers that cannot call
- * cudaMalloc -- code issuing work while a stream is being captured, real-time loops
- * that must not hit the implicit device synchronisation of cudaMalloc/cudaFree, and
- * applications that hand all device memory to their own pool.  The points are staged
- * in a fixed device array inside the library (65,536 points, 1 MiB, kept by every GPU
- * that loads the library until the process exits); n > 65536 returns
- * PHS_ERR_INVALID_ARG.  The first call on a device looks up that array's address
- * (cudaGetSymbolAddress); make it before any stream capture.  All calls share the
- * array: calls whose work overlaps on the GPU (other streams, other host threads)
- * race and must be serialised by the caller.  Asynchronous on `stream`. */
+ * cudaMalloc -- real-time loops that must not hit the implicit device synchronisation
+ * of cudaMalloc/cudaFree, and applications that hand all device memory to their own
+ * pool.  The points are staged in a fixed device array inside the library (65,536
+ * points, 1 MiB, kept by every GPU that loads the library until the process exits);
+ * n > 65536 returns PHS_ERR_INVALID_ARG.  The first call on a device, made with that
+ * device current, looks up that array's address (cudaGetSymbolAddress) and keeps it
+ * for the life of the process; make that first call before any stream capture, and do
+ * not use the library across a cudaDeviceReset of that device (the address would be
+ * stale).  All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Asynchronous on `stream`, unlike phs_dense_matvec, which synchronises before it
+ * returns: pts_dev, t_dev and out_dev must stay valid, and out_dev unread, until the
+ * stream has reached this work. */
 phs_status phs_dense_matvec_noalloc(const double *pts_dev, int64_t n, int k, const double *t_dev,
                                     double *out_dev, phs_stream_t stream);
 
@@ -269,10 +281,16 @@ phs_status phs_amaxmin_order(const double *pts_dev, int64_t n, int64_t *order_de
 phs_status phs_knn_prev(const double *pts_dev, int64_t n, const int64_t *order_dev, int m,
                         int64_t *nbr_dev, phs_stream_t stream);
 /* Vecchia factor columns (Eq. 2.19, Fig. 1) for conditioning sets nbr_dev
- * (n x m, -1 padded) of a Matern(nu, alpha) covariance with K(0) = 1:
- * diag_dev[i] = 1/c_i, offd_dev[i*m+q] = -lambda_q / c_i.  A failed local
- * Cholesky is retried with diagonal jitter 1e-12 * 10^t, t = 0..4;
- * *jittered_host (may be NULL) receives how many points needed it. */
+ * (n x m int64, -1 padded) of a Matern(nu, alpha) covariance with K(0) = 1:
+ * diag_dev[i] = 1/c_i, offd_dev[i*m+q] = -lambda_q / c_i.  order_dev (n int64)
+ * must be a permutation of 0..n-1, and the first min(m, rank(i)) entries of row i
+ * of nbr_dev points of smaller rank; otherwise PHS_ERR_INVALID_ARG (checked on the
+ * device before any coordinate is read).  nu in {0.5, 1, 1.5, 2, 2.5}, alpha > 0.
+ * A local Cholesky that fails (a pivot that is not positive) is retried with
+ * diagonal jitter 1e-12 * 10^(t-1) on the conditioning block, t = 1..7 (up to 1e-6);
+ * if it still fails, or the conditional variance c is not positive, that point gets
+ * an empty conditioning set (diag = 1, offd = 0).  *jittered_host (may be NULL)
+ * receives how many points needed either.  Synchronises. */
 phs_status phs_vecchia_factor(const double *pts_dev, int64_t n, const int64_t *order_dev,
                               const int64_t *nbr_dev, int m, double nu, double alpha,
                               double *diag_dev, double *offd_dev, int64_t *jittered_host,

@@ -33,7 +33,8 @@ class PhsFitInfo(ctypes.Structure):
 EXPORTS = [
     "phs_options_default", "phs_last_error", "phs_kernel_launches", "phs_plan_create", "phs_matvec", "phs_fit", "phs_eval",
     "phs_fit_predict_host", "phs_plan_destroy", "phs_plan_frame", "phs_plan_vecchia", "phs_plan_vecchia_factor",
-    "phs_plan_precond", "phs_plan_work", "phs_plan_kernel_work", "phs_plan_set_timing", "phs_plan_timing", "phs_dense_matvec",
+    "phs_plan_precond", "phs_plan_work", "phs_plan_kernel_work", "phs_plan_set_wait_limit", "phs_plan_set_timing",
+    "phs_plan_timing", "phs_dense_matvec",
     "phs_dense_matvec_noalloc",
     "phs_random_order", "phs_maxmin_order", "phs_hmaxmin_order", "phs_amaxmin_order", "phs_knn_prev",
     "phs_vecchia_factor",
@@ -68,6 +69,7 @@ def lib():
         "phs_plan_precond": (st, [P, P, P, P]),
         "phs_plan_work": (st, [P, P]),
         "phs_plan_kernel_work": (st, [P, P]),
+        "phs_plan_set_wait_limit": (st, [P, i64]),
         "phs_plan_set_timing": (st, [P, i32]),
         "phs_plan_timing": (st, [P, P, P]),
         "phs_dense_matvec": (st, [P, i64, i32, P, P, P]),

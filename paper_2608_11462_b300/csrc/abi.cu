@@ -518,8 +518,38 @@ static void build_lowrank(phs_plan *pl, cudaStream_t s) {
 
 // PCG on sign * P M' P x = rhs (rhs in range(P)), x0 = 0.  Returns iterations; *relres = ||r||/||rhs||.
 // Work vectors used: 0..6.
+// Matvec timing of a fit: an event pair around each matvec on the fit's stream, resolved
+// once after the fit's final synchronisation (no synchronisation per matvec).
+struct MvTimes {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    void begin(cudaStream_t s) {
+        ev.emplace_back(ev_get(), ev_get());
+        cudaEventRecord(ev.back().first, s);
+    }
+    void end(cudaStream_t s) { cudaEventRecord(ev.back().second, s); }
+    // sum of the recorded intervals in ms (the stream must have passed them); recycles the events
+    double resolve(int *count) {
+        double tot = 0;
+        for (auto &p : ev) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) tot += ms;
+            g_pool.push_back(p.first);
+            g_pool.push_back(p.second);
+        }
+        *count = (int)ev.size();
+        ev.clear();
+        return tot;
+    }
+    ~MvTimes() {
+        for (auto &p : ev) {
+            g_pool.push_back(p.first);
+            g_pool.push_back(p.second);
+        }
+    }
+};
+
 static int pcg(phs_plan *pl, const double *rhs, double *x, double tol_abs, int maxiter, int precision,
-               double *rr_final, cudaStream_t s, double *ms_mv, int *n_mv) {
+               double *rr_final, cudaStream_t s, MvTimes *mvt) {
     const int64_t n = pl->ps.n;
     double *r = W(pl, 0), *z = W(pl, 1), *p = W(pl, 2), *q = W(pl, 3), *y = W(pl, 4), *t1 = W(pl, 5),
            *t2 = W(pl, 6);
@@ -533,13 +563,9 @@ static int pcg(phs_plan *pl, const double *rhs, double *x, double tol_abs, int m
     double rr = read_scalar(pl, sc + 5, s);
     int it = 0;
     while (std::sqrt(rr) > tol_abs && it < maxiter) {
-        auto t0 = std::chrono::steady_clock::now();
+        if (mvt) mvt->begin(s);
         matvec_norm(pl, p, y, precision, s);
-        if (ms_mv) {
-            PHS_CUDA(cudaStreamSynchronize(s));
-            *ms_mv += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-            ++*n_mv;
-        }
+        if (mvt) mvt->end(s);
         pl->tm.begin(s);
         project(pl, y, (double)pl->sign, q, p, sc + 1, s);
         cg_update<<<RED_B, RED_T, 0, s>>>(x, r, p, q, n, sc + 0, sc + 1, pl->part.get());
@@ -566,24 +592,6 @@ static int pcg(phs_plan *pl, const double *rhs, double *x, double tol_abs, int m
 }  // namespace phs
 
 using namespace phs;
-
-#define PHS_TRY try {
-#define PHS_CATCH                                                        \
-    }                                                                    \
-    catch (const phs::Error &e) {                                        \
-        phs::set_error(e.msg);                                           \
-        return e.code;                                                   \
-    }                                                                    \
-    catch (const std::bad_alloc &) {                                     \
-        phs::set_error("host allocation failed");                        \
-        return PHS_ERR_OOM;                                              \
-    }                                                                    \
-    catch (const std::exception &e) {                                    \
-        phs::set_error(e.what());                                        \
-        return PHS_ERR_CUDA;                                             \
-    }                                                                    \
-    phs::set_error("");                                                  \
-    return PHS_OK;
 
 static int min_degree(int k) { return k % 2 == 0 ? k / 2 : (k - 1) / 2; }
 static int cpd_sign(int k) {
@@ -749,8 +757,7 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
     const double fnrm = std::sqrt(read_scalar(pl, sc + 9, s));
     const double nrm0 = std::sqrt(rr0);
     const double stop = std::max(o.tol * nrm0, o.atol);
-    double ms_mv = 0;
-    int n_mv = 0;
+    MvTimes mvt;
     int iters = 0, outer = 0;
     double rr = rr0;
     bool converged = false;
@@ -759,7 +766,7 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
         zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
         converged = true;
     } else if (o.precision == 0) {
-        iters = pcg(pl, rhs, x, stop, o.maxiter, 0, &rr, s, &ms_mv, &n_mv);
+        iters = pcg(pl, rhs, x, stop, o.maxiter, 0, &rr, s, &mvt);
         converged = std::sqrt(rr) <= stop;
     } else {
         // FP64 iterative refinement around FP32-FMM inner PCG solves
@@ -770,7 +777,7 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
             double rri = 0;
             double *dx = W(pl, 8);  // rhs no longer needed
             int it = pcg(pl, d, dx, std::max(o.inner_tol * res, 0.5 * stop), std::min(o.maxiter - iters, 100),
-                         o.precision, &rri, s, &ms_mv, &n_mv);
+                         o.precision, &rri, s, &mvt);
             iters += it;
             ++outer;
             axpy_k<<<blocks_for(n, 256), 256, 0, s>>>(x, dx, n, 1.0);
@@ -806,6 +813,8 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
                                                        w_dev);
     PHS_LAUNCH_CHECK();
     PHS_CUDA(cudaStreamSynchronize(s));
+    int n_mv = 0;
+    const double ms_mv = mvt.resolve(&n_mv);
     m2l_tc_check(pl->fmm, s);
     if (info) {
         info->iters = iters;
@@ -995,6 +1004,13 @@ phs_status phs_plan_kernel_work(phs_plan_t pl, int64_t *counts_host) {
     PHS_CATCH
 }
 
+phs_status phs_plan_set_wait_limit(phs_plan_t pl, int64_t ns) {
+    PHS_TRY
+    PHS_REQUIRE(pl && ns >= 0, PHS_ERR_INVALID_ARG, "bad arguments");
+    pl->fmm.tc_wait_ns = (uint64_t)ns;
+    PHS_CATCH
+}
+
 phs_status phs_plan_set_timing(phs_plan_t pl, int enabled) {
     PHS_TRY
     PHS_REQUIRE(pl, PHS_ERR_INVALID_ARG, "null plan");
@@ -1122,16 +1138,8 @@ phs_status phs_vecchia_factor(const double *pts_dev, int64_t n, const int64_t *o
     SBuf<double2> x(n, s);
     pts_to_d2<<<blocks_for(n, 256), 256, 0, s>>>(pts_dev, n, x.get());
     PHS_LAUNCH_CHECK();
-    SBuf<int> o(n, s), rank(n, s), ell((size_t)m * n, s);
-    from_i64<<<blocks_for(n, 256), 256, 0, s>>>(order_dev, n, o.get());
-    PHS_LAUNCH_CHECK();
-    {
-        std::vector<int> ho(n), hr(n);
-        PHS_CUDA(cudaMemcpyAsync(ho.data(), o.get(), n * sizeof(int), cudaMemcpyDeviceToHost, s));
-        PHS_CUDA(cudaStreamSynchronize(s));
-        for (int64_t r = 0; r < n; ++r) hr[ho[r]] = (int)r;
-        PHS_CUDA(cudaMemcpyAsync(rank.get(), hr.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
-    }
+    SBuf<int> rank(n, s), ell((size_t)m * n, s);
+    checked_ranks_dev(order_dev, nbr_dev, n, m, rank.get(), s);
     rows_to_ell_i32<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>(nbr_dev, n, m, ell.get());
     PHS_LAUNCH_CHECK();
     SBuf<double> val((size_t)(m + 1) * n, s);

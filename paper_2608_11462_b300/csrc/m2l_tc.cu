@@ -66,6 +66,7 @@ struct TcArgs {
     const int2 *off;          // nd = 4: offset (ox, oy) of each class in box units
     const uint16_t *bplanes;  // [49][nch][NPL][npad x 48], core-matrix order
     int *err;
+    uint64_t wait_ns;         // limit of the pipeline waits of the main loop
 };
 
 // round(x * 2^sh) for |x| * 2^sh < 2^62, from the bit pattern (no FP64 arithmetic);
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             const int u = s & 1;
             const int c = clist[s / a.nch], h = s % a.nch;
             if (misc[2]) break;
-            if (s >= 2 && !tc::mbar_wait(&mbar[u], (uint32_t)(((s >> 1) - 1) & 1), TC_TIMEOUT_NS)) {
+            if (s >= 2 && !tc::mbar_wait(&mbar[u], (uint32_t)(((s >> 1) - 1) & 1), a.wait_ns)) {
                 misc[2] = 1;
                 break;
             }
@@ -406,8 +407,8 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
         for (int s = 0; s < nsteps; ++s) {
             const int u = s & 1;
             if (misc[2]) break;
-            if (!tc::mbar_wait(&mbar[5 + u], (uint32_t)((s >> 1) & 1), TC_TIMEOUT_NS) ||
-                !tc::mbar_wait(&mbar[2 + u], (uint32_t)((s >> 1) & 1), TC_TIMEOUT_NS)) {
+            if (!tc::mbar_wait(&mbar[5 + u], (uint32_t)((s >> 1) & 1), a.wait_ns) ||
+                !tc::mbar_wait(&mbar[2 + u], (uint32_t)((s >> 1) & 1), a.wait_ns)) {
                 misc[2] = 1;
                 break;
             }
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             tc::mma_commit(&mbar[u]);
             // the operator of step s + 1 goes into the buffer step s - 1 read
             if (s >= 1 && s + 1 < nsteps) {
-                if (!tc::mbar_wait(&mbar[u ^ 1], (uint32_t)(((s - 1) >> 1) & 1), TC_TIMEOUT_NS)) {
+                if (!tc::mbar_wait(&mbar[u ^ 1], (uint32_t)(((s - 1) >> 1) & 1), a.wait_ns)) {
                     misc[2] = 1;
                     break;
                 }
@@ -441,6 +442,9 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             }
         }
     }
+    // Drain: whatever the main loop's limit, the MMAs issued and the operator copies in
+    // flight are waited for with the fixed 2 s limit before TMEM is released and the CTA
+    // exits, so an early give-up never leaves asynchronous work behind.
     __syncthreads();
     const bool aborted = misc[2] != 0;
     bool ok = !aborted;
@@ -685,6 +689,7 @@ static void launch_tc(Fmm &f, const Tree &t, double2 *mp, double2 *lc, int b0, c
     a.off = f.tc_off.get();
     a.bplanes = f.tc_b.get();
     a.err = f.tc_err.get();
+    a.wait_ns = f.tc_wait_ns > 0 ? f.tc_wait_ns : TC_TIMEOUT_NS;
     const int nb = t.nbox - b0;
     const unsigned grid = (unsigned)((nb + TcLayout<ND>::TPB - 1) / TcLayout<ND>::TPB);
     m2l_tc_kernel<ND><<<grid, tc_threads<ND>(), lay.total, s>>>(a);

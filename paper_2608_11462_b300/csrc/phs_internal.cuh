@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -37,6 +39,27 @@ void count_launch();
     do {                                                                                \
         if (!(cond)) throw ::phs::Error{code, msg};                                     \
     } while (0)
+
+// every extern "C" entry point wraps its body in PHS_TRY ... PHS_CATCH: library errors
+// return their code, host allocation failures PHS_ERR_OOM, any other C++ exception
+// PHS_ERR_CUDA, each with its message for phs_last_error(); success clears the message
+#define PHS_TRY try {
+#define PHS_CATCH                                                        \
+    }                                                                    \
+    catch (const ::phs::Error &e) {                                      \
+        ::phs::set_error(e.msg);                                         \
+        return e.code;                                                   \
+    }                                                                    \
+    catch (const std::bad_alloc &) {                                     \
+        ::phs::set_error("host allocation failed");                      \
+        return PHS_ERR_OOM;                                              \
+    }                                                                    \
+    catch (const std::exception &e) {                                    \
+        ::phs::set_error(e.what());                                      \
+        return PHS_ERR_CUDA;                                             \
+    }                                                                    \
+    ::phs::set_error("");                                                \
+    return PHS_OK;
 
 inline unsigned blocks_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
@@ -191,6 +214,7 @@ struct Fmm {
     DBuf<int2> tc_off;                   // nd = 4: class offsets (ox, oy)
     DBuf<int> tc_mexp;                   // per-box exponent bound of the multipoles
     DBuf<int> tc_err;                    // device status (nonzero: a bounded wait expired)
+    uint64_t tc_wait_ns = 0;             // main-loop wait limit of the pass (0: the 2 s default)
     int64_t tc_steps = 0, tc_tiles = 0;  // work of one pass (m2l_tc_count)
     DBuf<double> sym_scratch;            // column sums of the symmetric near field
     DBuf<int> p2p_ticket;                // next leaf of the near-field blocks (reset per launch)
@@ -277,6 +301,10 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
 void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr_ell, cudaStream_t s);
 int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m,
                            double nu, double alpha, double *val_ell, cudaStream_t s);
+// rank[order[r]] = r for a caller's enumeration (int64, any device buffer), checking that
+// order is a permutation and, if nbr (n x m int64 rows) is given, that the first
+// min(m, rank(i)) entries of row i are points of smaller rank; PHS_ERR_INVALID_ARG otherwise
+void checked_ranks_dev(const int64_t *order, const int64_t *nbr, int64_t n, int m, int *rank, cudaStream_t s);
 void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t seed, double nu,
                    double alpha, cudaStream_t s);
 // z = U~ (U~' r) (sorted order)

@@ -185,6 +185,9 @@ __global__ void vlist_kernel(TreeView tv, int nbox, int *cnt, const int *off, in
 
 // near lists of every box (leaves: the P2P lists; all boxes: direct parts of target
 // evaluation); the pair count covers leaves only
+// The fill pass writes only inside the box's counted slice [off[b], off[b+1]) and
+// counts in pairs[1] every box whose enumeration disagrees with the count pass, so a
+// disagreement becomes an error at plan creation instead of a write past the list.
 template <bool FILL>
 __global__ void nearlist_kernel(TreeView tv, int nbox, int *cnt, const int *off, int2 *rng,
                                 unsigned long long *pairs) {
@@ -192,15 +195,20 @@ __global__ void nearlist_kernel(TreeView tv, int nbox, int *cnt, const int *off,
     if (b >= nbox) return;
     int c = 0;
     const int o = FILL ? off[b] : 0;
+    const int cap = FILL ? off[b + 1] - o : 0;
     long long np = 0;
     const int nt = tv.end[b] - tv.start[b];
     enumerate_near(tv, b, [&](int s, int e) {
-        if (FILL) rng[o + c] = make_int2(s, e);
+        if (FILL && c < cap) rng[o + c] = make_int2(s, e);
         np += (long long)nt * (e - s);
         ++c;
     });
-    if (!FILL) cnt[b] = c;
-    else if (tv.nchild[b] == 0) atomicAdd(pairs, (unsigned long long)np);
+    if (!FILL) {
+        cnt[b] = c;
+    } else {
+        if (c != cap) atomicAdd(pairs + 1, 1ull);
+        if (tv.nchild[b] == 0) atomicAdd(pairs, (unsigned long long)np);
+    }
 }
 
 // Symmetric near field (see Tree::sym_*): a near range of leaf b is either b itself, or
@@ -420,8 +428,8 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     }
     {
         SBuf<int> cnt(tree.nbox, s);
-        SBuf<unsigned long long> pairs(1, s);
-        PHS_CUDA(cudaMemsetAsync(pairs.get(), 0, sizeof(unsigned long long), s));
+        SBuf<unsigned long long> pairs(2, s);  // [0] leaf pair count, [1] boxes whose fill disagreed
+        PHS_CUDA(cudaMemsetAsync(pairs.get(), 0, 2 * sizeof(unsigned long long), s));
         tree.near_off.alloc(tree.nbox + 1);
         nearlist_kernel<false><<<blocks_for(tree.nbox, 128), 128, 0, s>>>(tv, tree.nbox, cnt.get(), nullptr, nullptr,
                                                                           nullptr);
@@ -433,10 +441,11 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
         nearlist_kernel<true><<<blocks_for(tree.nbox, 128), 128, 0, s>>>(tv, tree.nbox, nullptr, tree.near_off.get(),
                                                                          tree.near_rng.get(), pairs.get());
         PHS_LAUNCH_CHECK();
-        unsigned long long hp2 = 0;
-        PHS_CUDA(cudaMemcpyAsync(&hp2, pairs.get(), sizeof(hp2), cudaMemcpyDeviceToHost, s));
+        unsigned long long hp2[2] = {0, 0};
+        PHS_CUDA(cudaMemcpyAsync(hp2, pairs.get(), sizeof(hp2), cudaMemcpyDeviceToHost, s));
         PHS_CUDA(cudaStreamSynchronize(s));
-        tree.near_pairs = (int64_t)hp2;
+        PHS_REQUIRE(hp2[1] == 0, PHS_ERR_CUDA, "near-list fill pass disagreed with its count pass");
+        tree.near_pairs = (int64_t)hp2[0];
     }
     {
         const int nl = tree.nleaf;

@@ -744,6 +744,31 @@ __global__ void __launch_bounds__(MM_T) maxmin_block(const double2 *x, int64_t n
     }
 }
 
+// rank[order[r]] = r for a caller-supplied enumeration; bad[0] counts entries outside
+// [0, n) (skipped) and bad[1] ranks given twice (a repeated entry leaves another rank unset)
+__global__ void ranks_checked(const int64_t *order, int64_t n, int *rank, unsigned long long *bad) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t v = order[r];
+    if (v < 0 || v >= n) {
+        atomicAdd(bad, 1ull);
+        return;
+    }
+    if (atomicExch(rank + v, (int)r) != -1) atomicAdd(bad + 1, 1ull);
+}
+// conditioning sets of a caller: the first min(m, rank(i)) entries of row i must be
+// points of smaller rank (they are read as coordinates); bad[2] counts violations
+__global__ void check_nbr_rows(const int64_t *nbr, const int *rank, int64_t n, int m, unsigned long long *bad) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * m) return;
+    const int64_t i = t / m;
+    const int q = (int)(t - i * m);
+    const int s = min(m, rank[i]);
+    if (q >= s) return;
+    const int64_t v = nbr[t];
+    if (v < 0 || v >= n || rank[v] >= rank[i]) atomicAdd(bad + 2, 1ull);
+}
+
 }  // namespace
 
 void maxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t s) {
@@ -831,6 +856,25 @@ int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const i
     PHS_CUDA(cudaStreamSynchronize(s));
     PHS_REQUIRE(h[1] == 0, PHS_ERR_CHOLESKY, "a local Vecchia factor failed even with jitter");
     return (int64_t)h[0];
+}
+
+void checked_ranks_dev(const int64_t *order, const int64_t *nbr, int64_t n, int m, int *rank, cudaStream_t s) {
+    SBuf<unsigned long long> bad(3, s);
+    PHS_CUDA(cudaMemsetAsync(bad.get(), 0, 3 * sizeof(unsigned long long), s));
+    PHS_CUDA(cudaMemsetAsync(rank, 0xff, n * sizeof(int), s));
+    ranks_checked<<<blocks_for(n, 256), 256, 0, s>>>(order, n, rank, bad.get());
+    PHS_LAUNCH_CHECK();
+    unsigned long long h[3];
+    PHS_CUDA(cudaMemcpyAsync(h, bad.get(), 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_REQUIRE(h[0] == 0 && h[1] == 0, PHS_ERR_INVALID_ARG, "order is not a permutation of 0..n-1");
+    if (!nbr) return;
+    check_nbr_rows<<<blocks_for(n * m, 256), 256, 0, s>>>(nbr, rank, n, m, bad.get());
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaMemcpyAsync(h, bad.get(), 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    PHS_REQUIRE(h[2] == 0, PHS_ERR_INVALID_ARG,
+                "a conditioning set lists a point that is out of range or not of smaller rank");
 }
 
 void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t seed, double nu, double alpha,
