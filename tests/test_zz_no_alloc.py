@@ -1,7 +1,6 @@
 """phs_dense_matvec_noalloc: the dense PHS product for callers that cannot allocate
-device memory (stream capture in progress, real-time loops that must avoid the
-implicit synchronisation of cudaMalloc/cudaFree, applications that own all device
-memory).  Called through the C ABI and compared with phs_dense_matvec, which
+device memory (real-time loops that must avoid the implicit synchronisation of
+cudaMalloc/cudaFree, applications that own all device memory).  Called through the C ABI and compared with phs_dense_matvec, which
 allocates its own scratch, on two calls in a row that reuse the library's fixed
 staging array.  This file is collected last on purpose."""
 import ctypes
