@@ -22,16 +22,33 @@ def test_reference_arm_prints_one_contract_line():
     for k in REQUIRED:
         assert k in d, k
     assert d["impl"] == "reference" and d["higher_is_better"] is False and d["unit"] == "s"
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 * d["value"]) <= 1e-9 * d["ms_per_step"]
-    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["value"] > 0 and d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "sample" in cb
-    # the native arm builds its config with the same function; the keys describe the workload
+    # one labelled extrapolation shared with the native line's cpu_baseline: ms_per_step is
+    # the measured time of the sampled step, value that time scaled by (n / n_sample)^2
     sys.path.insert(0, ROOT)
     import bench
+    assert d["value_extrapolated"] is True and cb["extrapolated"] is True
+    assert cb["n_sample"] == bench.CPU_SAMPLE and abs(cb["measured_s"] * 1e3 - d["ms_per_step"]) <= 1e-6
+    scale = (d["config"]["n"] / bench.CPU_SAMPLE) ** 2
+    assert abs(d["value"] - cb["measured_s"] * scale) <= 1e-9 * d["value"]
+    # the native arm builds its config with the same function; the keys describe the workload
     cfg = d["config"]
     assert cfg["workload"] == bench.WORKLOAD and cfg["n"] == 1_048_576 and cfg["fmm_order"] == bench.default_fmm_order()
     assert cfg["alpha_normalised"] == bench.ALPHA and cfg["nu"] == bench.NU and cfg["leaf_cap"] == 96
+
+
+def test_cpu_record_is_shared_by_both_legs():
+    """The native line's cpu_baseline and the reference arm describe the oracle time with
+    the same function, sample size and labels."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = bench.cpu_record(2.0, 8, 1_048_576, 3)
+    assert rec["extrapolated"] is True and rec["n_sample"] == bench.CPU_SAMPLE and rec["measured_s"] == 2.0
+    assert rec["value"] == 2.0 * (1_048_576 / bench.CPU_SAMPLE) ** 2
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert src.count("cpu_record(") >= 3  # definition, native leg, reference arm
 
 
 def test_default_fmm_order_rule():
