@@ -34,11 +34,12 @@ WORKLOAD = "tps_1m"
 # (0.01-0.03 are equal; at 0.003 and below the local covariances need jitter and the
 # count rises).  nu = 1.5 fails to converge within 200 iterations for alpha in {5, 20, 60}.
 NU, ALPHA = 1.0, 0.03
-# DRAM bytes (read + write) per launch from ncu captures summarised under profiles/,
-# taken on the n = 262144 case of this workload and scaled to the bench size: the
-# tensor-core M2L by its tile count (618 tiles there), the near field by the point count.
-M2L_DRAM_BYTES_PER_TILE = (29.62176e6 + 39.68e3) / 618
-P2P_DRAM_BYTES_PER_POINT = (7.3408e6 + 768) / 262144
+# DRAM bytes (read + write) per launch from the ncu capture summarised in
+# profiles/p2p_sym_kernel_tps_262k.md and profiles/m2l_tc_kernel_tps_262k.md, taken on the
+# n = 262144 case of this workload at leaf capacity 96 and scaled to the bench size: the
+# tensor-core M2L by its tile count (408 tiles there), the near field by the point count.
+M2L_DRAM_BYTES_PER_TILE = (21.427712e6 + 21.76e3) / 408
+P2P_DRAM_BYTES_PER_POINT = (6.951936e6 + 512) / 262144
 
 
 def workload_config(args, n, m_t, fmm_order, world):

@@ -64,10 +64,15 @@ typedef struct {
                                0: FP64 throughout (plain PCG);
                                1: FP32 near field, FP64 far field;
                                2: FP32 near field and FP32 M2L, FP64 elsewhere;
-                               3: FP32 throughout (order min(p, 24)).
-                               Modes 1-3 run inside FP64 iterative refinement: the
+                               3: FP32 throughout (order min(p, 24));
+                               4: near field in float-float (hi + lo FP32, about 2^-46 per
+                                  term) on the FP32 pipe, far field FP64 (M2L as m2l_tensor).
+                               Modes 1-4 run inside FP64 iterative refinement: the
                                outer residual uses the FP64 FMM; residuals, inner
-                               products, projection and preconditioner stay FP64. */
+                               products, projection and preconditioner stay FP64.  Modes
+                               1-3 do not converge on large clustered sets (the projected
+                               system amplifies FP32 rounding); mode 4 does.  Odd k: 0 or 4.
+                               Modes 1-4 need |t| < 1e37 in the vectors they multiply. */
     double tol;             /* stop when ||r_k|| <= max(tol*||Q_perp' f||, atol); default 1e-8 */
     double atol;            /* default 0 */
     int maxiter;            /* PCG iterations (precision 0) or total inner iterations; default 200 */
@@ -84,8 +89,9 @@ typedef struct {
     double domain_halfwidth;/* points are mapped into [-h, h]^2; default 0.25 (k<=3), 1 (k>=4) */
     uint64_t seed;          /* random enumeration seed */
     double fmm_eps;         /* FMM truncation target used when fmm_order <= 0; default 1e-11 */
-    double inner_tol;       /* precision 1: relative tolerance of each inner FP32 solve; default 1e-4 */
-    int max_refine;         /* precision 1: maximum refinement steps; default 8 */
+    double inner_tol;       /* precision 1-3: relative tolerance of each inner solve; default 1e-4
+                               (precision 4 aims each inner solve at the final tolerance) */
+    int max_refine;         /* precision 1-4: maximum refinement steps; default 8 */
     int m2l_tensor;         /* even k, FP64 far field: 1 (default) runs the multipole-to-local
                                translations (Sec. 2.1, Eq. 2.14) on the tensor cores in exact
                                fixed point (bf16 digit planes, about 1e-12 relative); 0 runs
@@ -147,8 +153,8 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
 
 /* out = M t in the caller's frame and order, M_ij = phi(|x_i - x_j|) (Eq. 1.3),
  * by the FMM of Sec. 2.1 applied through Eq. (2.6).  precision selects the
- * arithmetic as in phs_options.precision (0 = FP64 FMM).  t_dev, out_dev: n
- * doubles on the device (may not alias). */
+ * arithmetic as in phs_options.precision (0 = FP64 FMM, 0..4; odd k: 0 or 4).
+ * t_dev, out_dev: n doubles on the device (may not alias). */
 phs_status phs_matvec(phs_plan_t plan, const double *t_dev, double *out_dev, int precision,
                       phs_stream_t stream);
 
@@ -207,14 +213,18 @@ phs_status phs_plan_work(phs_plan_t plan, int64_t *counts_host);
  *   [4] tcgen05.mma instructions per step,
  *   [5] multiply-adds of one instruction (M * N * K). */
 phs_status phs_plan_kernel_work(phs_plan_t plan, int64_t *counts_host);
-/* Wall-time limit, in ns, of each pipeline wait in the main loop of the tensor-core
- * M2L (a diagnostics and test hook; no counterpart in the paper).  0 restores the
- * default of 2 s.  A wait that exceeds it makes every block of the pass stop issuing
- * work; the multiply-adds and copies already issued are still waited for (with the
- * fixed 2 s limit) before the kernel exits, so the device and the plan stay usable, and
- * the next phs_fit or phs_eval on the plan returns PHS_ERR_TIMEOUT (phs_matvec is
- * asynchronous and does not check). */
-phs_status phs_plan_set_wait_limit(phs_plan_t plan, int64_t ns);
+/* Diagnostics and test hook of the tensor-core M2L's bounded waits (no counterpart in
+ * the paper).  ns: wall-time limit of each pipeline wait in the pass's main loop (0
+ * restores the default of 2 s); every wait also gives up after ns / 4 polls, so it ends
+ * even if the device timer stalls.  probe = 1 makes each block of the later passes wait
+ * first on a barrier that nothing completes, so that wait always expires: the block
+ * issues no work, and the pass flags the plan.  A wait that expires makes every block
+ * of the pass stop issuing work; the multiply-adds and copies already issued are still
+ * waited for (with the fixed 2 s limit) before the kernel exits, so the device and the
+ * plan stay usable, and the next phs_fit or phs_eval on the plan returns
+ * PHS_ERR_TIMEOUT (phs_matvec is asynchronous and does not check).  probe = 0 and
+ * ns = 0 restore normal operation. */
+phs_status phs_plan_set_wait_limit(phs_plan_t plan, int64_t ns, int probe);
 /* Per-phase device timing of the most recent phs_fit / phs_matvec calls, in ms,
  * measured with CUDA events on the plan's stream when enabled (0/1).
  * ms_host[0..7] = (p2p, m2l, upward, downward, precond, vector, eval, total);

@@ -141,9 +141,10 @@ class Plan:
         return {"p2p_pairs": c[0], "p2p_column_pairs": c[1], "tc_steps": c[2], "tc_tiles": c[3],
                 "tc_mmas_per_step": c[4], "tc_mma_macs": c[5]}
 
-    def set_wait_limit(self, ns: int):
-        """phs_plan_set_wait_limit: main-loop wait limit of the tensor-core M2L (0: 2 s)."""
-        check(lib().phs_plan_set_wait_limit(self._h, int(ns)))
+    def set_wait_limit(self, ns: int, probe: bool = False):
+        """phs_plan_set_wait_limit: main-loop wait limit of the tensor-core M2L (0: 2 s) and
+        the probe that makes its first wait expire (a test of the timeout path)."""
+        check(lib().phs_plan_set_wait_limit(self._h, int(ns), int(bool(probe))))
 
     def set_timing(self, enabled: bool):
         check(lib().phs_plan_set_timing(self._h, int(bool(enabled))))

@@ -69,7 +69,7 @@ def lib():
         "phs_plan_precond": (st, [P, P, P, P]),
         "phs_plan_work": (st, [P, P]),
         "phs_plan_kernel_work": (st, [P, P]),
-        "phs_plan_set_wait_limit": (st, [P, i64]),
+        "phs_plan_set_wait_limit": (st, [P, i64, i32]),
         "phs_plan_set_timing": (st, [P, i32]),
         "phs_plan_timing": (st, [P, P, P]),
         "phs_dense_matvec": (st, [P, i64, i32, P, P, P]),

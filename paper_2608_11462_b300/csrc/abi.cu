@@ -647,8 +647,10 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         if (opt) pl->opt = *opt;
         else phs_options_default(&pl->opt, k);
         const phs_options &o = pl->opt;
-        PHS_REQUIRE(o.tol > 0 && o.maxiter >= 1 && o.precision >= 0 && o.precision <= 3, PHS_ERR_INVALID_ARG,
+        PHS_REQUIRE(o.tol > 0 && o.maxiter >= 1 && o.precision >= 0 && o.precision <= 4, PHS_ERR_INVALID_ARG,
                     "bad solver options");
+        PHS_REQUIRE(k % 2 == 0 || o.precision == 0 || o.precision == 4, PHS_ERR_INVALID_ARG,
+                    "odd spline orders run in precision 0 or 4");
         PHS_REQUIRE(o.ordering >= 0 && o.ordering <= 3, PHS_ERR_INVALID_ARG, "ordering must be 0, 1, 2 or 3");
         int p = fmm_order;
         if (p <= 0) {
@@ -713,7 +715,7 @@ phs_status phs_plan_destroy(phs_plan_t plan) {
 phs_status phs_matvec(phs_plan_t pl, const double *t_dev, double *out_dev, int precision, phs_stream_t stream) {
     PHS_TRY
     PHS_REQUIRE(pl && t_dev && out_dev && t_dev != out_dev, PHS_ERR_INVALID_ARG, "bad arguments");
-    PHS_REQUIRE(precision >= 0 && precision <= 3, PHS_ERR_INVALID_ARG, "precision must be 0..3");
+    PHS_REQUIRE(precision >= 0 && precision <= 4, PHS_ERR_INVALID_ARG, "precision must be 0..4");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = pl->ps.n;
     double *ts = W(pl, 8), *y = W(pl, 9);
@@ -769,14 +771,19 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
         iters = pcg(pl, rhs, x, stop, o.maxiter, 0, &rr, s, &mvt);
         converged = std::sqrt(rr) <= stop;
     } else {
-        // FP64 iterative refinement around FP32-FMM inner PCG solves
+        // FP64 iterative refinement around inner PCG solves with the reduced-precision
+        // operator.  Modes 1-3 (plain FP32 pieces) solve each correction to inner_tol;
+        // mode 4 (float-float near field) is accurate enough that its first inner solve
+        // aims at the final tolerance, and refinement only mops up what the operator's
+        // rounding leaves in the true residual.
         zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
         PHS_CUDA(cudaMemcpyAsync(d, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));  // residual
         double res = nrm0;
         while (outer < o.max_refine && iters < o.maxiter) {
             double rri = 0;
             double *dx = W(pl, 8);  // rhs no longer needed
-            int it = pcg(pl, d, dx, std::max(o.inner_tol * res, 0.5 * stop), std::min(o.maxiter - iters, 100),
+            const double itol = o.precision == 4 ? 0.5 * stop : std::max(o.inner_tol * res, 0.5 * stop);
+            int it = pcg(pl, d, dx, itol, std::min(o.maxiter - iters, o.precision == 4 ? o.maxiter : 100),
                          o.precision, &rri, s, &mvt);
             iters += it;
             ++outer;
@@ -1004,10 +1011,11 @@ phs_status phs_plan_kernel_work(phs_plan_t pl, int64_t *counts_host) {
     PHS_CATCH
 }
 
-phs_status phs_plan_set_wait_limit(phs_plan_t pl, int64_t ns) {
+phs_status phs_plan_set_wait_limit(phs_plan_t pl, int64_t ns, int probe) {
     PHS_TRY
-    PHS_REQUIRE(pl && ns >= 0, PHS_ERR_INVALID_ARG, "bad arguments");
+    PHS_REQUIRE(pl && ns >= 0 && (probe == 0 || probe == 1), PHS_ERR_INVALID_ARG, "bad arguments");
     pl->fmm.tc_wait_ns = (uint64_t)ns;
+    pl->fmm.tc_probe = probe;
     PHS_CATCH
 }
 

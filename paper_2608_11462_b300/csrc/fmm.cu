@@ -78,13 +78,6 @@ __device__ __forceinline__ void had_u(int power, double x, double y, double *u) 
 constexpr int kMaxNd = 10;
 constexpr int kMaxP = 61;
 
-__device__ __forceinline__ void box_geom(const TreeView &tv, int b, double &cx, double &cy, double &w) {
-    int ix, iy;
-    demorton(tv.key[b], ix, iy);
-    w = box_width(tv.R, tv.level[b]);
-    cx = -tv.R + (ix + 0.5) * w;
-    cy = -tv.R + (iy + 0.5) * w;
-}
 
 // ---------------------------------------------------------------- operators (host)
 // layout: slot s in [0,4) M2M quadrant, [4,8) L2L quadrant, [8,57) M2L class (dx+3)*7+(dy+3)
@@ -1324,6 +1317,22 @@ static void p2p_dispatch(Fmm &f, int k, const Tree &t, const PointSet &ps, const
     }
 }
 
+// mode 4: the near field in float-float on the FP32 pipe (nearfield_ff.cu) with the
+// symmetric schedule; trees with a leaf of more than 128 points keep the FP64 kernel
+static void p2p_ff_dispatch(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y,
+                            cudaStream_t s) {
+    if (!t.sym_ok) {
+        p2p_dispatch<double>(f, f.k, t, ps, tv_sorted, y, s);
+        return;
+    }
+    if (f.sym_scratch.n < (size_t)std::max<int64_t>(t.sym_total, 1)) f.sym_scratch.alloc(std::max<int64_t>(t.sym_total, 1));
+    if (!f.p2p_ticket.get()) f.p2p_ticket.alloc(1);
+    p2p_sym_ff(t, ps, f.k, tv_sorted, y, f.sym_scratch.get(), f.p2p_ticket.get(), s);
+    p2p_gather<<<blocks_for(ps.n, 256), 256, 0, s>>>(tree_view(t), t.leaf_box.get(), t.point_leaf.get(),
+                                                     t.sym_goff.get(), t.sym_gbase.get(), ps.n, f.sym_scratch.get(), y);
+    PHS_LAUNCH_CHECK();
+}
+
 template <typename T>
 static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s) {
     using C = typename C2T<T>::type;
@@ -1343,12 +1352,14 @@ static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaS
 
 void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, int mode, cudaStream_t s,
                Timers *tm) {
-    PHS_REQUIRE(mode >= 0 && mode <= 3, PHS_ERR_INVALID_ARG, "precision mode must be 0..3");
+    PHS_REQUIRE(mode >= 0 && mode <= 4, PHS_ERR_INVALID_ARG, "precision mode must be 0..4");
     if (!f.log_core) {
-        // odd k: distance-kernel far field by Chebyshev interpolation, FP64 only
-        PHS_REQUIRE(mode == 0, PHS_ERR_INVALID_ARG, "odd spline orders run in FP64 (precision 0)");
+        // odd k: distance-kernel far field by Chebyshev interpolation in FP64; the near
+        // field in FP64 or (mode 4) float-float
+        PHS_REQUIRE(mode == 0 || mode == 4, PHS_ERR_INVALID_ARG, "odd spline orders run in precision 0 or 4");
         if (tm) tm->begin(s);
-        p2p_dispatch<double>(f, f.k, t, ps, t_sorted, y, s);
+        if (mode == 4) p2p_ff_dispatch(f, t, ps, t_sorted, y, s);
+        else p2p_dispatch<double>(f, f.k, t, ps, t_sorted, y, s);
         if (tm) tm->end(T_P2P, s);
         cheb_far_field(f, t, ps, t_sorted, s, tm);
         if (tm) tm->begin(s);
@@ -1358,9 +1369,10 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
     }
     if (tm) tm->begin(s);
     if (mode == 0) p2p_dispatch<double>(f, f.k, t, ps, t_sorted, y, s);
+    else if (mode == 4) p2p_ff_dispatch(f, t, ps, t_sorted, y, s);
     else p2p_dispatch<float>(f, f.k, t, ps, t_sorted, y, s);
     if (tm) tm->end(T_P2P, s);
-    if (mode <= 1) far_field<double>(f, t, ps, t_sorted, s, tm);
+    if (mode <= 1 || mode == 4) far_field<double>(f, t, ps, t_sorted, s, tm);
     else if (mode == 2) far_field_m2l32(f, t, ps, t_sorted, s, tm);
     else far_field<float>(f, t, ps, t_sorted, s, tm);
     if (tm) tm->begin(s);
@@ -1489,6 +1501,7 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     }
     PHS_CUDA(cudaStreamSynchronize(s));
     upload_log_tables();
+    upload_ff_tables();
     if (!f.log_core) cheb_setup(f, cheb_q, s);
     m2l_tc_count(f, t, s);
 }

@@ -42,6 +42,15 @@ __host__ __device__ __forceinline__ void demorton(uint64_t key, int &ix, int &iy
 // box of level l in the root [-R, R]^2: width 2R/2^l, centre -R + (i + 1/2) * width
 __host__ __device__ __forceinline__ double box_width(double R, int l) { return 2.0 * R / (double)(1ll << l); }
 
+// centre (cx, cy) and width w of box b
+__device__ __forceinline__ void box_geom(const TreeView &tv, int b, double &cx, double &cy, double &w) {
+    int ix, iy;
+    demorton(tv.key[b], ix, iy);
+    w = box_width(tv.R, tv.level[b]);
+    cx = -tv.R + (ix + 0.5) * w;
+    cy = -tv.R + (iy + 0.5) * w;
+}
+
 // index of the box at (l, ix, iy), or -1 if it does not exist
 __device__ __forceinline__ int find_box(const TreeView &tv, int l, int ix, int iy) {
     if (l < 0 || l > tv.depth) return -1;

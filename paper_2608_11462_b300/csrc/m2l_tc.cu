@@ -67,6 +67,7 @@ struct TcArgs {
     const uint16_t *bplanes;  // [49][nch][NPL][npad x 48], core-matrix order
     int *err;
     uint64_t wait_ns;         // limit of the pipeline waits of the main loop
+    int probe;                // nonzero: the issuer first waits on a barrier nothing completes
 };
 
 // round(x * 2^sh) for |x| * 2^sh < 2^62, from the bit pattern (no FP64 arithmetic);
@@ -402,8 +403,14 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             tc::mbar_arrive(&mbar[5 + u]);
         }
     } else if (issuer && nsteps > 0) {
-        copy_b(0);
-        if (nsteps > 1) copy_b(1);
+        // test of the timeout path: before anything is issued, wait (bounded) for the
+        // "done" barrier, which only this thread's final commit completes, so the wait
+        // expires, the pass aborts, and the drain below finds no work in flight
+        if (a.probe && !tc::mbar_wait(&mbar[4], 0, a.wait_ns)) misc[2] = 1;
+        if (!misc[2]) {
+            copy_b(0);
+            if (nsteps > 1) copy_b(1);
+        }
         for (int s = 0; s < nsteps; ++s) {
             const int u = s & 1;
             if (misc[2]) break;
@@ -690,6 +697,7 @@ static void launch_tc(Fmm &f, const Tree &t, double2 *mp, double2 *lc, int b0, c
     a.bplanes = f.tc_b.get();
     a.err = f.tc_err.get();
     a.wait_ns = f.tc_wait_ns > 0 ? f.tc_wait_ns : TC_TIMEOUT_NS;
+    a.probe = f.tc_probe;
     const int nb = t.nbox - b0;
     const unsigned grid = (unsigned)((nb + TcLayout<ND>::TPB - 1) / TcLayout<ND>::TPB);
     m2l_tc_kernel<ND><<<grid, tc_threads<ND>(), lay.total, s>>>(a);

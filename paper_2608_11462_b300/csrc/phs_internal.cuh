@@ -215,6 +215,7 @@ struct Fmm {
     DBuf<int> tc_mexp;                   // per-box exponent bound of the multipoles
     DBuf<int> tc_err;                    // device status (nonzero: a bounded wait expired)
     uint64_t tc_wait_ns = 0;             // main-loop wait limit of the pass (0: the 2 s default)
+    int tc_probe = 0;                    // test hook: make the pass's first wait expire
     int64_t tc_steps = 0, tc_tiles = 0;  // work of one pass (m2l_tc_count)
     DBuf<double> sym_scratch;            // column sums of the symmetric near field
     DBuf<int> p2p_ticket;                // next leaf of the near-field blocks (reset per launch)
@@ -241,9 +242,17 @@ void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *t_s
 void cheb_l2p_apply(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s);
 void cheb_eval_far_launch(Fmm &f, const Tree &t, const double2 *tgt, const int *box_of, int64_t m, double *out,
                           cudaStream_t s);
+// near field in float-float arithmetic on the FP32 pipe (nearfield_ff.cu), symmetric
+// schedule: rows into y, column sums of the ranges after each leaf into scratch (the
+// caller adds them with p2p_gather); needs t.sym_ok.  upload_ff_tables() loads its
+// logarithm tables on the current device (once per plan).
+void p2p_sym_ff(const Tree &t, const PointSet &ps, int k, const double *tv_sorted, double *y, double *scratch,
+                int *ticket, cudaStream_t s);
+void upload_ff_tables();
 // y = M' t for sorted-order vectors in the normalised frame (M' of the normalised points)
 // mode 0: FP64 throughout; 1: FP32 near field + FP64 far field; 2: FP32 near field and
-// FP32 M2L inside FP64 upward/downward passes; 3: FP32 throughout (order p32)
+// FP32 M2L inside FP64 upward/downward passes; 3: FP32 throughout (order p32);
+// 4: float-float near field on the FP32 pipe + FP64 far field (M2L as configured)
 void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted, int mode,
                cudaStream_t s, struct Timers *tm);
 // evaluate sum_j w_j phi(|x_j - y|) at normalised targets (after an FMM upward/downward

@@ -86,11 +86,14 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 // Wait for the phase with the given parity to complete, giving up after timeout_ns
-// nanoseconds of wall time; false on timeout.
+// nanoseconds of wall time or after timeout_ns / 4 polls, whichever comes first (a poll
+// takes more than 4 ns, so the poll cap only binds if %globaltimer does not advance);
+// false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint64_t timeout_ns) {
     const uint32_t a = smem_u32(mbar);
+    const uint64_t max_polls = timeout_ns / 4 + 64;
     uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
+    for (uint64_t it = 0;; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -105,6 +108,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint6
             if (t0 == 0) t0 = t;
             else if (t - t0 > timeout_ns) return false;
         }
+        if (it >= max_polls) return false;
     }
 }
 

@@ -101,6 +101,28 @@ def test_fmm_matvec_mixed_precision(phs, k, mode, tol):
     assert err <= tol, err
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("geom", ["uniform", "clustered"])
+def test_fmm_matvec_float_float_near_field(phs, k, geom):
+    """Mode 4 (near field in float-float on the FP32 pipe): every row within 1e-11 of the
+    oracle's exact row sum, relative to that row's sum of absolute terms -- the scale of
+    any summation's rounding -- on a random vector and on an oscillating one (the
+    preconditioned vector, whose near-field sums cancel most); and the 2-norm within
+    1e-10 of the dense product, as for FP64."""
+    n = 3001
+    pts = np.random.default_rng(12).random((n, 2)) if geom == "uniform" else _clustered(n, 13)
+    plan = phs.Plan(_t(pts), k, fmm_order=0, vecchia_m=8, opts=phs.options(k, leaf_cap=32))
+    rng = np.random.default_rng(14)
+    t_rand = rng.standard_normal(n)
+    t_osc = plan.precond(_t(t_rand)).cpu().numpy()
+    for t in (t_rand, t_osc):
+        got = plan.matvec(_t(t), precision=4).cpu().numpy()
+        want = oracle.dense_matvec(pts, k, t)
+        scale = oracle.dense_eval_abs(pts, t, k, pts)
+        assert np.max(np.abs(got - want) / scale) <= 1e-11, np.max(np.abs(got - want) / scale)
+        assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+
+
 @pytest.mark.parametrize("k", [1, 3, 5])
 @pytest.mark.parametrize("geom", ["uniform", "clustered"])
 def test_fmm_matvec_odd_k_distance_kernel(phs, k, geom):
@@ -135,10 +157,13 @@ def test_eval_matches_dense_interpolant(phs, k):
     assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
 
 
-def test_fit_cubic_mix_matches_dense_solve(phs):
-    """Workload cubic_mix scaled to n = 2,000 (k = 3, S = 3, Vecchia m = 20)."""
+@pytest.mark.parametrize("precision", [0, 4])
+def test_fit_cubic_mix_matches_dense_solve(phs, precision):
+    """Workload cubic_mix scaled to n = 2,000 (k = 3, S = 3, Vecchia m = 20), FP64 and the
+    float-float near field."""
     w_ = synth.workload("cubic_mix", n=2000, n_targets=300)
-    plan = phs.Plan(_t(w_["points"]), 3, vecchia_m=20, opts=phs.options(3, tol=1e-10, maxiter=400))
+    plan = phs.Plan(_t(w_["points"]), 3, vecchia_m=20,
+                    opts=phs.options(3, tol=1e-10, maxiter=400, precision=precision))
     w, beta, info = plan.fit(_t(w_["f"]))
     assert info["converged"] == 1, info
     pred = plan.eval(w, beta, _t(w_["targets"])).cpu().numpy()
@@ -497,7 +522,7 @@ def test_plan_precond_well_conditioned_strict(phs, lowrank):
 
 
 # ---------------------------------------------------------------- fit and eval
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 4])
 def test_fit_uniform_tps_matches_dense_solve(phs, precision):
     """Workload uniform_tps (n = 1,500, k = 2, S = 3): interpolant within 1e-8
     relative of the dense augmented solve at 500 held-out targets."""
@@ -623,10 +648,11 @@ def test_host_end_to_end(phs):
 
 # ---------------------------------------------------------------- bounded device waits
 def test_tc_wait_limit_reports_timeout_and_plan_stays_usable(phs):
-    """The tensor-core M2L's pipeline waits are bounded.  With the limit set to 1 ns a wait
-    gives up: the pass stops issuing work, drains the multiply-adds and copies already in
-    flight (fixed 2 s limit) and flags the plan; phs_eval then returns PHS_ERR_TIMEOUT.
-    With the default limit restored the same plan evaluates and fits correctly."""
+    """The tensor-core M2L's pipeline waits are bounded.  With the probe on, each block first
+    waits (limit 1 ms) on a barrier that nothing completes: the wait expires, the block
+    issues nothing, drains (nothing in flight) and flags the plan; phs_eval then returns
+    PHS_ERR_TIMEOUT.  With the probe off and the default limit restored, the same plan
+    evaluates and fits correctly."""
     w_ = synth.workload("tps_1m", n=60000, n_targets=300)
     pts, f, tg = w_["points"], w_["f"], w_["targets"]
     plan = phs.Plan(_t(pts), 2, vecchia_m=10, opts=phs.options(2, m2l_tensor=1, leaf_cap=32))
@@ -634,11 +660,11 @@ def test_tc_wait_limit_reports_timeout_and_plan_stays_usable(phs):
     rng = np.random.default_rng(4)
     w = rng.standard_normal(len(f))
     beta = np.zeros(3)
-    plan.set_wait_limit(1)
+    plan.set_wait_limit(1_000_000, probe=True)
     with pytest.raises(phs.PhsError) as ei:
         plan.eval(_t(w), _t(beta), _t(tg))
     assert ei.value.code == 7, ei.value
-    plan.set_wait_limit(0)
+    plan.set_wait_limit(0, probe=False)
     got = plan.eval(_t(w), _t(beta), _t(tg)).cpu().numpy()
     xn, c, rho = oracle.normalize(pts, 0.25)
     yn = (tg - c) * rho
@@ -710,7 +736,8 @@ def _node_residual_check(plan, pts, f, w, beta, k, rows):
 
 
 # ---------------------------------------------------------------- the bench workload at full size
-def test_full_size_tps_1m_sampled_rows(phs):
+@pytest.mark.parametrize("precision", [0, 4])
+def test_full_size_tps_1m_sampled_rows(phs, precision):
     """The clustered TPS workload at n = 1,048,576 with the bench's options (nu = 1,
     alpha = 0.03, approximate maximin order, leaf cap 96, FMM order from 1e-11).  No dense
     solve exists at this size, so the oracle computes sampled rows one by one (O(n) each):
@@ -721,24 +748,28 @@ def test_full_size_tps_1m_sampled_rows(phs):
       P (f - M w) (plus the FMM error on that row), whose inf-norm over all nodes is
       within 1e-8 of ||f||_inf (_node_residual_check);
     * evaluation at sampled held-out targets within 1e-10 of the exact interpolant,
-      relative to the same absolute scale."""
+      relative to the same absolute scale.
+    Precision 0 is the FP64 solve; precision 4 runs the near field in float-float inside
+    FP64 refinement, and its fit is held to the same checks (the true residual and the
+    node residuals are computed with the FP64 matvec)."""
     w_ = synth.workload("tps_1m")
     pts, f, tg = w_["points"], w_["f"], w_["targets"]
     n = len(f)
     assert n == 1_048_576
     plan = phs.Plan(_t(pts), 2, fmm_order=0, vecchia_m=30,
-                    opts=phs.options(2, tol=1e-8, nu=1.0, alpha=0.03, leaf_cap=96))
+                    opts=phs.options(2, tol=1e-8, nu=1.0, alpha=0.03, leaf_cap=96, precision=precision))
     rng = np.random.default_rng(77)
     rows = np.sort(rng.choice(n, 800, replace=False))
     # matvec rows
     t = rng.standard_normal(n)
-    y = plan.matvec(_t(t)).cpu().numpy()
+    y = plan.matvec(_t(t), precision=precision).cpu().numpy()
     exact = oracle.dense_eval(pts, t, 2, pts[rows])
     scale = oracle.dense_eval_abs(pts, t, 2, pts[rows])
     err = np.abs(y[rows] - exact) / scale
     assert err.max() <= 1e-10, err.max()
     # fit
     w, beta, info = plan.fit(_t(f))
+    print(f"tps_1m precision {precision}: {info}")
     assert info["converged"] == 1 and info["iters"] < 15 and info["rel_res_true"] <= 1e-8, info
     _node_residual_check(plan, pts, f, w, beta, 2, rows)
     xn, c, rho = oracle.normalize(pts, 0.25)
