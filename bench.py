@@ -40,6 +40,8 @@ NU, ALPHA = 1.0, 0.03
 # tensor-core M2L by its tile count (408 tiles there), the near field by the point count.
 M2L_DRAM_BYTES_PER_TILE = (21.427712e6 + 21.76e3) / 408
 P2P_DRAM_BYTES_PER_POINT = (6.951936e6 + 512) / 262144
+# the float-float near field (precision 4): not captured yet
+P2P_FF_DRAM_BYTES_PER_POINT = None
 
 
 def workload_config(args, n, m_t, fmm_order, world):
@@ -66,6 +68,8 @@ def parse():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--n", type=int, default=None, help="override the point count (smaller parity runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="with --precision != 0, skip timing the plain FP64 solve beside it")
     ap.add_argument("--leaf-cap", type=int, default=96,
                     help="quadtree leaf capacity (96 measured best on this workload: 48 / 64 / 80 / 96 / "
                          "112 gave 0.429 / 0.344 / 0.327 / 0.323 / 0.331 s per solve)")
@@ -324,6 +328,28 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
 
+    # ---- the plain FP64 solve on the same workload, beside a mixed-precision line
+    fp64_cmp = None
+    if args.precision != 0 and not args.no_fp64_compare:
+        o64 = phs.options(2, precision=0, tol=1e-8, nu=NU, alpha=ALPHA, leaf_cap=args.leaf_cap,
+                          ordering=args.ordering)
+        t64, i64 = [], None
+        for i in range(3):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p64 = phs.Plan(pts_d, 2, fmm_order=0, vecchia_m=30, opts=o64)
+            w64, b64, i64 = p64.fit(f_d)
+            p64.eval(w64, b64, tg_d)
+            e1.record(stream)
+            barrier()
+            p64.close()
+            if i > 0:
+                t64.append(e0.elapsed_time(e1) / 1e3)
+        fp64_cmp = {"fp64_step_s": float(np.mean(t64)), "fp64_iters": i64["iters"],
+                    "fp64_rel_res_true": i64["rel_res_true"], "speedup_vs_fp64": float(np.mean(t64)) / t_step}
+
     # ---- end to end from host buffers through the C ABI
     e2e_times = []
     for i in range(max(1, min(args.steps, 2))):
@@ -349,20 +375,34 @@ def main():
             a[1] += calls
     phases = {k_: v for k_, v in agg.items() if k_ in ("p2p", "m2l", "upward", "downward", "precond", "vector")}
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2032.0))
-    # FP64 pipe: 2 instructions (DFMA, DMUL or DADD) per clock per SM
-    fp64_peak_g = 148 * 2 * sm_mhz_max * 1e6 / 1e9
     ms_p2p = phases["p2p"][0] / max(phases["p2p"][1], 1)
-    # per evaluated pair: DADD + 2 DFMA (r^2 = a_i + a_j - 2 x_i.x_j), 4 DFMA + DADD (table
-    # log), DMUL (r^2 log r^2), DFMA (row sum) = 10; one more DFMA where the pair also feeds
-    # a column sum
-    p2p_ops = 10 * kwork["p2p_pairs"] + kwork["p2p_column_pairs"]
-    ach = p2p_ops / (ms_p2p / 1e3) / 1e9
-    roof_p2p = {"kernel": "p2p_sym_kernel<2> + p2p_gather", "bound": "alu", "achieved": ach, "peak": fp64_peak_g,
-                "unit": "G FP64-pipe instr/s", "frac": ach / fp64_peak_g,
-                "peak_source": f"derived: 148 SMs x 2 FP64 instr/clk x {sm_mhz_max:.0f} MHz",
-                "work_per_launch": f"{kwork['p2p_pairs']} pairs evaluated ({kwork['p2p_column_pairs']} with column "
-                                   f"sums) = {p2p_ops} FP64 instr; {work['near_pairs']} ordered near pairs",
-                "ms_per_launch": ms_p2p, "traffic": P2P_DRAM_BYTES_PER_POINT * n}
+    if args.precision == 4:
+        # float-float near field (nearfield_ff.cu): FP32-pipe operations per pair as written
+        # there -- coordinates 16, s = r^2 19, logarithm 32, s log s 4, row term and sum 12 --
+        # 83 per pair, plus 12 where the pair also feeds a column sum
+        fp32_peak_g = 148 * 128 * sm_mhz_max * 1e6 / 1e9
+        p2p_ops = 83 * kwork["p2p_pairs"] + 12 * kwork["p2p_column_pairs"]
+        ach = p2p_ops / (ms_p2p / 1e3) / 1e9
+        roof_p2p = {"kernel": "p2p_sym_ff_kernel<2> + p2p_gather", "bound": "alu", "achieved": ach,
+                    "peak": fp32_peak_g, "unit": "G FP32-pipe instr/s", "frac": ach / fp32_peak_g,
+                    "peak_source": f"derived: 148 SMs x 128 FP32 lanes x {sm_mhz_max:.0f} MHz",
+                    "work_per_launch": f"{kwork['p2p_pairs']} pairs evaluated ({kwork['p2p_column_pairs']} with "
+                                       f"column sums) = {p2p_ops} FP32-pipe instr; {work['near_pairs']} ordered near "
+                                       f"pairs", "ms_per_launch": ms_p2p, "traffic": P2P_FF_DRAM_BYTES_PER_POINT * n
+                    if P2P_FF_DRAM_BYTES_PER_POINT else None}
+    else:
+        # FP64 pipe: 2 instructions (DFMA, DMUL or DADD) per clock per SM.  Per evaluated pair:
+        # DADD + 2 DFMA (r^2 = a_i + a_j - 2 x_i.x_j), 4 DFMA + DADD (table log), DMUL
+        # (r^2 log r^2), DFMA (row sum) = 10; one more DFMA where the pair also feeds a column sum
+        fp64_peak_g = 148 * 2 * sm_mhz_max * 1e6 / 1e9
+        p2p_ops = 10 * kwork["p2p_pairs"] + kwork["p2p_column_pairs"]
+        ach = p2p_ops / (ms_p2p / 1e3) / 1e9
+        roof_p2p = {"kernel": "p2p_sym_kernel<2> + p2p_gather", "bound": "alu", "achieved": ach,
+                    "peak": fp64_peak_g, "unit": "G FP64-pipe instr/s", "frac": ach / fp64_peak_g,
+                    "peak_source": f"derived: 148 SMs x 2 FP64 instr/clk x {sm_mhz_max:.0f} MHz",
+                    "work_per_launch": f"{kwork['p2p_pairs']} pairs evaluated ({kwork['p2p_column_pairs']} with "
+                                       f"column sums) = {p2p_ops} FP64 instr; {work['near_pairs']} ordered near pairs",
+                    "ms_per_launch": ms_p2p, "traffic": P2P_DRAM_BYTES_PER_POINT * n}
     ms_m2l = phases["m2l"][0] / max(phases["m2l"][1], 1)
     roof_m2l = None
     if kwork["tc_steps"] > 0:
@@ -408,13 +448,14 @@ def main():
     out = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {0: "f64", 4: "f64+ff32"}.get(args.precision, "f64+f32"), "data": "synthetic",
         "fits_per_s": world / t_step,
         "config": workload_config(args, n, m_t, int(sizes[3]), world),
         "pcg": {"iters": info["iters"], "outer_iters": info["outer_iters"], "converged": info["converged"],
                 "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"], "ms_fit": info["ms_fit"],
                 "ms_matvec_avg": info["ms_matvec_avg"]},
         "phases_ms_per_step": {k_: v[0] / args.steps for k_, v in agg.items()},
+        **({"fp64_comparison": fp64_cmp} if fp64_cmp else {}),
         "fmm_throughput": fmm,
         "roofline": roof, **roof_other, "roofline_precond": pre, "clocks": clk, "gpu_launches": int(launches),
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(16 * n + 8 * n + 16 * m_t),

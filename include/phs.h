@@ -186,6 +186,39 @@ phs_status phs_fit_predict_host(const double *pts_host, const double *f_host, in
  * finishes; NULL is accepted and does nothing; the handle is invalid afterwards. */
 phs_status phs_plan_destroy(phs_plan_t plan);
 
+/* Solve M c = b for the kernel matrix ALONE (no polynomial block; the preconditioning
+ * comparison of Sec. 3.1) by restarted GMRES with the plan's Vecchia factor U~ U~' as a
+ * right preconditioner, so the residual it minimises is ||b - M c||.  b_dev, c_dev: n
+ * doubles, caller order (may not alias).  Tolerance stop = max(tol ||b||, atol) with the
+ * plan's tol and atol; maxiter bounds the total iterations; restart: Krylov vectors per
+ * cycle, 1..127 (the basis takes restart + 1 vectors of n doubles from the memory pool).
+ * A cycle ends when its least-squares residual estimate is <= stop.  check_true = 0
+ * stops there (the iteration count a GMRES library reports); check_true = 1 recomputes
+ * ||b - M c|| and restarts until it meets stop (it can stall near rounding, about
+ * eps ||M|| ||c||, for ill-conditioned M).  The FMM runs in FP64 (plan precision 0..3)
+ * or with the float-float near field (precision 4).  info (may be NULL): iters = GMRES
+ * iterations, outer_iters = cycles, rel_res_recursive = the last estimate / ||b||,
+ * rel_res_true = the recomputed ||b - M c|| / ||b||, ms_matvec_avg as for phs_fit.
+ * Returns PHS_ERR_NOT_CONVERGED (c still written) when maxiter is reached first.
+ * Synchronises. */
+phs_status phs_gmres(phs_plan_t plan, const double *b_dev, double *c_dev, int restart, int check_true,
+                     phs_fit_info *info, phs_stream_t stream);
+
+/* Choose the Matern inverse range alpha of the Vecchia preconditioner for these points
+ * and values by a gradient-free search on PCG's iteration count (the tuning of Sec. 2.2).
+ * The domain scaling and alpha enter the preconditioned iteration only through their
+ * product, so the search is over alpha at the domain of opt (domain_halfwidth).  Trials
+ * are full plans and fits on a seeded random subsample of n_sample points (<= 0 or >= n:
+ * all points): alpha0 * 10^(i/4), i = -8..4, with alpha0 = opt->alpha, then six steps of
+ * golden-section search around the best; a trial costs its iteration count plus
+ * log10(final residual / tol) in [-1, 0].  *alpha_out receives the best alpha (never
+ * worse on the subsample than alpha0), *iters_out (may be NULL) its iteration count.
+ * pts_dev, f_dev: as phs_plan_create and phs_fit; other arguments as phs_plan_create.
+ * Synchronises. */
+phs_status phs_tune_alpha(const double *pts_dev, const double *f_dev, int64_t n, int k, int poly_degree,
+                          int fmm_order, int vecchia_m, const phs_options *opt, int64_t n_sample,
+                          double *alpha_out, int *iters_out, phs_stream_t stream);
+
 /* ---- inspection (small host copies; synchronise) --------------------------- */
 /* frame[0..3] = (centre_x, centre_y, rho, halfwidth); sizes[0..7] = (n, k, S, p,
  * nd, n_boxes, n_leaves, depth). */

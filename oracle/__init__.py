@@ -27,6 +27,9 @@ What it computes, each function citing the passage it follows:
                              Sec. 2.2 discusses and sets aside.
 * ``pcg``                 -- preconditioned CG on Q_perp^T M Q_perp (Sec. 2,
                              after Eq. 2.5; Sec. 2.2) with a dense matvec.
+* ``gmres``               -- restarted GMRES with the Vecchia factor as right
+                             preconditioner on M c = b, the kernel matrix alone
+                             (the comparison of Sec. 3.1), dense matvec.
 
 The FMM of Sec. 2.1 is not restated here: it approximates M t, whose plain
 definition ``dense_matvec`` is the oracle for it.
@@ -518,6 +521,73 @@ def pcg(x, f, k: int, deg: int, precond=None, tol: float = 1e-10, maxiter: int =
         rz = rz_new
     beta = np.linalg.solve(R, Q.T @ (f - dense_matvec(x, k, w)))
     return w, beta, it, np.array(hist)
+
+
+# --------------------------------------------------------------------------
+# GMRES on the kernel matrix alone, Sec. 3.1
+def gmres(x, k: int, b, precond=None, tol: float = 1e-8, atol: float = 0.0, restart: int = 50,
+          maxiter: int = 500, check_true: bool = True):
+    """Right-preconditioned restarted GMRES for M c = b (Sec. 3.1: the kernel matrix of
+    Eq. 1.3 alone, no polynomial block), M dense, preconditioner S = U~ U~^T of
+    precond = (nbr, diag, offd) (identity if None).  Textbook GMRES(m): Arnoldi with
+    modified Gram-Schmidt on A = M S from v_1 = r / ||r||, the Hessenberg least-squares
+    problem min ||beta e_1 - H y|| reduced by Givens rotations, c += S V y at the end of a
+    cycle and r = b - M c recomputed.  A cycle ends when its least-squares residual
+    estimate is <= max(tol ||b||, atol) (or after `restart` iterations); with check_true the
+    solve restarts until the RECOMPUTED residual meets the tolerance, without it it stops
+    at the first estimate that does (the count a GMRES library reports).  At most maxiter
+    iterations.  Returns (c, iterations, cycles, recomputed ||b - M c||)."""
+    x = _f64(x).reshape(-1, 2)
+    b = _f64(b)
+    n = b.size
+    M = dense_matrix(x, k)
+
+    def S(v):
+        return v.copy() if precond is None else vecchia_apply(*precond, v)
+
+    stop = max(tol * np.linalg.norm(b), atol)
+    c = np.zeros(n)
+    r = b.copy()
+    beta = np.linalg.norm(r)
+    it = cycles = 0
+    est = beta
+    while beta > stop and it < maxiter and (check_true or est > stop):
+        cycles += 1
+        m = restart
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        j = 0
+        while j < m and it < maxiter:
+            w = M @ S(V[j])
+            for q in range(j + 1):           # modified Gram-Schmidt
+                H[q, j] = V[q] @ w
+                w = w - H[q, j] * V[q]
+            H[j + 1, j] = np.linalg.norm(w)
+            for q in range(j):               # earlier rotations on the new column
+                a = cs[q] * H[q, j] + sn[q] * H[q + 1, j]
+                H[q + 1, j] = -sn[q] * H[q, j] + cs[q] * H[q + 1, j]
+                H[q, j] = a
+            rr = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = (H[j, j] / rr, H[j + 1, j] / rr) if rr > 0 else (1.0, 0.0)
+            H[j, j], H[j + 1, j] = rr, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            j += 1
+            hn = np.linalg.norm(w)
+            if abs(g[j]) <= stop or hn == 0.0:
+                break
+            V[j] = w / hn
+        est = abs(g[j])
+        y = np.linalg.solve(np.triu(H[:j, :j]), g[:j])
+        c = c + S(V[:j].T @ y)
+        r = b - M @ c
+        beta = np.linalg.norm(r)
+    return c, it, cycles, beta
 
 
 # --------------------------------------------------------------------------

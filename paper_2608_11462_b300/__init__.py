@@ -15,7 +15,8 @@ from . import _native
 from ._native import PhsError, PhsFitInfo, PhsOptions, check, lib
 
 __all__ = ["Plan", "PhsError", "PhsOptions", "PhsFitInfo", "options", "phs_dense_matvec", "phs_random_order",
-           "phs_maxmin_order", "phs_hmaxmin_order", "phs_amaxmin_order", "phs_knn_prev", "phs_vecchia_factor", "phs_fit_predict_host", "lib"]
+           "phs_maxmin_order", "phs_hmaxmin_order", "phs_amaxmin_order", "phs_knn_prev", "phs_vecchia_factor",
+           "phs_fit_predict_host", "phs_tune_alpha", "lib"]
 
 
 def _stream(stream=None):
@@ -92,6 +93,17 @@ class Plan:
         check(lib().phs_fit(self._h, _ptr(f), _ptr(w), _ptr(beta), ctypes.byref(info), _stream(stream)),
               allow=(5,) if allow_not_converged else ())
         return w, beta, info.as_dict()
+
+    def gmres(self, b: torch.Tensor, restart: int = 50, check_true: bool = True, stream=None,
+              allow_not_converged: bool = False):
+        """phs_gmres: M c = b (kernel matrix alone), Vecchia right preconditioner (Sec. 3.1)."""
+        b = _dev(b, name="b")
+        c = torch.empty_like(b)
+        info = PhsFitInfo()
+        check(lib().phs_gmres(self._h, _ptr(b), _ptr(c), int(restart), int(bool(check_true)), ctypes.byref(info),
+                              _stream(stream)),
+              allow=(5,) if allow_not_converged else ())
+        return c, info.as_dict()
 
     def eval(self, w: torch.Tensor, beta: torch.Tensor, targets: torch.Tensor, stream=None) -> torch.Tensor:
         w = _dev(w, name="w")
@@ -212,6 +224,21 @@ def phs_vecchia_factor(points, order, nbr, m: int, nu: float, alpha: float, stre
     check(lib().phs_vecchia_factor(_ptr(pts), n, _ptr(order), _ptr(nbr), int(m), float(nu), float(alpha),
                                    _ptr(diag), _ptr(offd), ctypes.byref(nj), _stream(stream)))
     return diag, offd, nj.value
+
+
+def phs_tune_alpha(points: torch.Tensor, f: torch.Tensor, k: int, poly_degree: int = -1, fmm_order: int = 0,
+                   vecchia_m: int = 30, opts: PhsOptions | None = None, n_sample: int = 32768, stream=None):
+    """phs_tune_alpha: the preconditioner's alpha by a search on PCG iterations (Sec. 2.2).
+    Returns (alpha, iterations on the subsample)."""
+    pts = _dev(points, name="points")
+    f = _dev(f, name="f")
+    o = opts if opts is not None else options(k)
+    a = ctypes.c_double()
+    it = ctypes.c_int()
+    check(lib().phs_tune_alpha(_ptr(pts), _ptr(f), pts.shape[0], int(k), int(poly_degree), int(fmm_order),
+                               int(vecchia_m), ctypes.byref(o), int(n_sample), ctypes.byref(a), ctypes.byref(it),
+                               _stream(stream)))
+    return a.value, it.value
 
 
 def phs_fit_predict_host(points, f, targets, k: int, poly_degree: int = -1, fmm_order: int = 0,

@@ -37,7 +37,7 @@ EXPORTS = [
     "phs_plan_timing", "phs_dense_matvec",
     "phs_dense_matvec_noalloc",
     "phs_random_order", "phs_maxmin_order", "phs_hmaxmin_order", "phs_amaxmin_order", "phs_knn_prev",
-    "phs_vecchia_factor",
+    "phs_vecchia_factor", "phs_gmres", "phs_tune_alpha",
 ]
 
 _lib = None
@@ -80,6 +80,9 @@ def lib():
         "phs_amaxmin_order": (st, [P, i64, P, P]),
         "phs_knn_prev": (st, [P, i64, P, i32, P, P]),
         "phs_vecchia_factor": (st, [P, i64, P, P, i32, d, d, P, P, P, P]),
+        "phs_gmres": (st, [P, P, P, i32, i32, ctypes.POINTER(PhsFitInfo), P]),
+        "phs_tune_alpha": (st, [P, P, i64, i32, i32, i32, i32, ctypes.POINTER(PhsOptions), i64,
+                                ctypes.POINTER(d), ctypes.POINTER(i32), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -7,7 +7,7 @@
 #include <cstring>
 #include <new>
 
-#include "phs_internal.cuh"
+#include "plan.cuh"
 
 namespace phs {
 
@@ -19,7 +19,8 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- timers
 static thread_local std::vector<cudaEvent_t> g_pool;
-static cudaEvent_t ev_get() {
+void ev_put(cudaEvent_t e) { g_pool.push_back(e); }
+cudaEvent_t ev_get() {
     if (!g_pool.empty()) {
         cudaEvent_t e = g_pool.back();
         g_pool.pop_back();
@@ -32,28 +33,6 @@ static cudaEvent_t ev_get() {
 
 }  // namespace phs
 
-struct phs_plan {
-    int k = 2, S = 3, deg = 1, m = 30, p = 20;
-    phs_options opt{};
-    phs::PointSet ps;
-    phs::Tree tree;
-    phs::Fmm fmm;
-    phs::Vecchia vec;
-    phs::DBuf<double> Q;      // [S][n] sorted order
-    phs::DBuf<double> R;      // S x S upper triangular, row-major
-    phs::DBuf<double> G;      // [S][n] S~^{-1} Q Rc^{-1}, Rc'Rc = Q' S~^{-1} Q (low-rank preconditioner term)
-    bool lowrank = false;
-    phs::DBuf<double> work;   // 12 work vectors of n
-    phs::DBuf<double> part;   // reduction partials
-    phs::DBuf<double> scal;   // device scalars
-    double *hscal = nullptr;  // pinned host mirror
-    phs::Timers tm;
-    float ms_plan = 0;
-    int sign = 1;             // sign * Q_perp' M Q_perp is positive definite
-    ~phs_plan() {
-        if (hscal) cudaFreeHost(hscal);
-    }
-};
 
 namespace phs {
 
@@ -318,6 +297,10 @@ __global__ void axpy_k(double *y, const double *x, int64_t n, double a) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) y[j] += a * x[j];
 }
+__global__ void scale_k(double *y, int64_t n, double a) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) y[j] *= a;
+}
 __global__ void zero_k(double *y, int64_t n) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) y[j] = 0.0;
@@ -422,9 +405,9 @@ __global__ void pts_to_d2(const double *p, int64_t n, double2 *out) {
 }  // namespace
 
 // ---------------------------------------------------------------- plan helpers
-static double *W(phs_plan *pl, int i) { return pl->work.get() + (size_t)i * pl->ps.n; }
+double *W(phs_plan *pl, int i) { return pl->work.get() + (size_t)i * pl->ps.n; }
 
-static void dots(phs_plan *pl, std::initializer_list<std::pair<const double *, const double *>> prs, double *out,
+void dots(phs_plan *pl, std::initializer_list<std::pair<const double *, const double *>> prs, double *out,
                  cudaStream_t s) {
     DotSet ds;
     ds.cnt = 0;
@@ -440,7 +423,7 @@ static void dots(phs_plan *pl, std::initializer_list<std::pair<const double *, c
 }
 
 // out = sign * P v  (P = I - Q Q'); if other != null, dot(other, out) -> *dot_out
-static void project(phs_plan *pl, const double *v, double sign, double *out, const double *other, double *dot_out,
+void project(phs_plan *pl, const double *v, double sign, double *out, const double *other, double *dot_out,
                     cudaStream_t s) {
     const int64_t n = pl->ps.n;
     double *coef = pl->scal.get() + 16;
@@ -457,14 +440,47 @@ static void project(phs_plan *pl, const double *v, double sign, double *out, con
     }
 }
 
-static void matvec_norm(phs_plan *pl, const double *t, double *y, int precision, cudaStream_t s) {
+void matvec_norm(phs_plan *pl, const double *t, double *y, int precision, cudaStream_t s) {
     fmm_apply(pl->fmm, pl->tree, pl->ps, t, y, precision, s, &pl->tm);
 }
 
-static double read_scalar(phs_plan *pl, const double *dev, cudaStream_t s) {
+double read_scalar(phs_plan *pl, const double *dev, cudaStream_t s) {
     PHS_CUDA(cudaMemcpyAsync(pl->hscal, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     PHS_CUDA(cudaStreamSynchronize(s));
     return pl->hscal[0];
+}
+
+// y = M t with M the kernel matrix of the CALLER's points (Eq. 1.3), vectors in sorted
+// order: M' of the normalised points gives rho^k M + log(rho) [r'^k] for even k (Eq. 2.1
+// generalised), so M t = rho^-k (M' t - log(rho) U(V' t)) with the Hadamard factors of
+// [r'^k]; for odd k the log term is absent.
+void matvec_user_sorted(phs_plan *pl, const double *ts, double *y, int precision, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    matvec_norm(pl, ts, y, precision, s);
+    const double rho = pl->ps.frame.rho;
+    if (pl->k % 2 == 0) {
+        const int power = pl->k;
+        had_dots<<<RED_B, RED_T, 0, s>>>(pl->ps.xs.get(), ts, n, power, pl->part.get());
+        PHS_LAUNCH_CHECK();
+        dots_final<<<power == 2 ? 4 : 10, RED_T, 0, s>>>(pl->part.get(), RED_B, pl->scal.get() + 32);
+        PHS_LAUNCH_CHECK();
+        had_correct<<<blocks_for(n, 256), 256, 0, s>>>(pl->ps.xs.get(), n, power, pl->scal.get() + 32, std::log(rho), y);
+        PHS_LAUNCH_CHECK();
+    }
+    scale_k<<<blocks_for(n, 256), 256, 0, s>>>(y, n, std::pow(rho, -(double)pl->k));
+    PHS_LAUNCH_CHECK();
+}
+// dst[p] = scale * src[perm[p]] (caller order -> sorted order)
+void to_sorted(phs_plan *pl, const double *src, double *dst, double scale, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    gather_scaled<<<blocks_for(n, 256), 256, 0, s>>>(src, pl->ps.perm.get(), n, scale, dst);
+    PHS_LAUNCH_CHECK();
+}
+// dst[perm[p]] = scale * src[p] (sorted order -> caller order)
+void to_caller(phs_plan *pl, const double *src, double *dst, double scale, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    scatter_scaled<<<blocks_for(n, 256), 256, 0, s>>>(src, pl->ps.perm.get(), n, scale, dst);
+    PHS_LAUNCH_CHECK();
 }
 
 // Preconditioner of the projected system, r in range(P):
@@ -473,7 +489,7 @@ static double read_scalar(phs_plan *pl, const double *dev, cudaStream_t s) {
 // With G = S~^{-1} Q Rc^{-1} and Rc'Rc = Q' S~^{-1} Q, G G' = S~^{-1} Q (Q' S~^{-1} Q)^{-1} Q' S~^{-1},
 // the Schur complement term of block elimination on [S~ B; B' 0], and Q'z = 0 by construction.
 // Both forms cost one reduction over S basis vectors and one update pass after the factor apply.
-static void precond(phs_plan *pl, const double *r, double *z, double *tmp, double *tmp2, cudaStream_t s) {
+void precond(phs_plan *pl, const double *r, double *z, double *tmp, double *tmp2, cudaStream_t s) {
     pl->tm.begin(s);
     vecchia_apply(pl->vec, r, tmp, tmp2, s);
     pl->tm.end(T_PRECOND, s);
@@ -493,7 +509,7 @@ static void precond(phs_plan *pl, const double *r, double *z, double *tmp, doubl
 
 // G = U~ (U~' Q) Rc^{-1} with Rc the Cholesky factor of C = (U~' Q)'(U~' Q) = Q' S~^{-1} Q
 // (symmetric by construction).  Work vectors 0..S-1 hold U~' Q.
-static void build_lowrank(phs_plan *pl, cudaStream_t s) {
+void build_lowrank(phs_plan *pl, cudaStream_t s) {
     const int64_t n = pl->ps.n;
     const int S = pl->S;
     PHS_REQUIRE(S <= MAXS, PHS_ERR_INVALID_ARG, "too many polynomial terms for the low-rank term");
@@ -516,37 +532,38 @@ static void build_lowrank(phs_plan *pl, cudaStream_t s) {
     pl->lowrank = true;
 }
 
+// Rebuild the plan's preconditioner for a new Matern inverse range (the tuner's step):
+// enumeration, conditioning sets and local factors (Sec. 2.2), and the low-rank term if
+// the plan uses it.  The tree, FMM and QR do not depend on alpha.
+void plan_set_alpha(phs_plan *pl, double alpha, cudaStream_t s) {
+    PHS_REQUIRE(alpha > 0 && std::isfinite(alpha), PHS_ERR_INVALID_ARG, "alpha must be positive");
+    pl->opt.alpha = alpha;
+    vecchia_build(pl->vec, pl->ps, pl->m, pl->opt.ordering, pl->opt.seed, pl->opt.nu, alpha, s);
+    pl->lowrank = false;
+    if (pl->opt.precond_lowrank) build_lowrank(pl, s);
+    PHS_CUDA(cudaStreamSynchronize(s));
+}
+
 // PCG on sign * P M' P x = rhs (rhs in range(P)), x0 = 0.  Returns iterations; *relres = ||r||/||rhs||.
 // Work vectors used: 0..6.
-// Matvec timing of a fit: an event pair around each matvec on the fit's stream, resolved
-// once after the fit's final synchronisation (no synchronisation per matvec).
-struct MvTimes {
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-    void begin(cudaStream_t s) {
-        ev.emplace_back(ev_get(), ev_get());
-        cudaEventRecord(ev.back().first, s);
+double MvTimes::resolve(int *count) {
+    double tot = 0;
+    for (auto &p : ev) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) tot += ms;
+        ev_put(p.first);
+        ev_put(p.second);
     }
-    void end(cudaStream_t s) { cudaEventRecord(ev.back().second, s); }
-    // sum of the recorded intervals in ms (the stream must have passed them); recycles the events
-    double resolve(int *count) {
-        double tot = 0;
-        for (auto &p : ev) {
-            float ms = 0;
-            if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) tot += ms;
-            g_pool.push_back(p.first);
-            g_pool.push_back(p.second);
-        }
-        *count = (int)ev.size();
-        ev.clear();
-        return tot;
+    *count = (int)ev.size();
+    ev.clear();
+    return tot;
+}
+MvTimes::~MvTimes() {
+    for (auto &p : ev) {
+        ev_put(p.first);
+        ev_put(p.second);
     }
-    ~MvTimes() {
-        for (auto &p : ev) {
-            g_pool.push_back(p.first);
-            g_pool.push_back(p.second);
-        }
-    }
-};
+}
 
 static int pcg(phs_plan *pl, const double *rhs, double *x, double tol_abs, int maxiter, int precision,
                double *rr_final, cudaStream_t s, MvTimes *mvt) {
@@ -717,26 +734,12 @@ phs_status phs_matvec(phs_plan_t pl, const double *t_dev, double *out_dev, int p
     PHS_REQUIRE(pl && t_dev && out_dev && t_dev != out_dev, PHS_ERR_INVALID_ARG, "bad arguments");
     PHS_REQUIRE(precision >= 0 && precision <= 4, PHS_ERR_INVALID_ARG, "precision must be 0..4");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = pl->ps.n;
     double *ts = W(pl, 8), *y = W(pl, 9);
-    gather_vec<<<blocks_for(n, 256), 256, 0, s>>>(t_dev, pl->ps.perm.get(), n, ts);
-    PHS_LAUNCH_CHECK();
+    to_sorted(pl, t_dev, ts, 1.0, s);
     pl->tm.begin(s);
-    matvec_norm(pl, ts, y, precision, s);
+    matvec_user_sorted(pl, ts, y, precision, s);
     pl->tm.end(T_TOTAL, s);
-    const double rho = pl->ps.frame.rho;
-    if (pl->k % 2 == 0) {
-        // M' = rho^k M + log(rho) [r'^k]  =>  M t = rho^-k (M' t - log(rho) U'(V'^T t))
-        const int power = pl->k;
-        had_dots<<<RED_B, RED_T, 0, s>>>(pl->ps.xs.get(), ts, n, power, pl->part.get());
-        PHS_LAUNCH_CHECK();
-        dots_final<<<power == 2 ? 4 : 10, RED_T, 0, s>>>(pl->part.get(), RED_B, pl->scal.get() + 32);
-        PHS_LAUNCH_CHECK();
-        had_correct<<<blocks_for(n, 256), 256, 0, s>>>(pl->ps.xs.get(), n, power, pl->scal.get() + 32, std::log(rho), y);
-        PHS_LAUNCH_CHECK();
-    }
-    scatter_scaled<<<blocks_for(n, 256), 256, 0, s>>>(y, pl->ps.perm.get(), n, std::pow(rho, -(double)pl->k), out_dev);
-    PHS_LAUNCH_CHECK();
+    to_caller(pl, y, out_dev, 1.0, s);
     PHS_CATCH
 }
 

@@ -1,0 +1,80 @@
+// plan.cuh -- the plan object behind the C ABI and the solver helpers shared by the
+// files that run solves on it (abi.cu: PCG fit, evaluation; krylov.cu: GMRES, tuning).
+#pragma once
+#include <initializer_list>
+#include <utility>
+#include <vector>
+
+#include "phs_internal.cuh"
+
+// A plan: one point set with its tree, FMM tables, polynomial QR and Vecchia factor, and
+// the work vectors of its solves.  Vectors inside are in sorted (Morton) order.
+struct phs_plan {
+    int k = 2, S = 3, deg = 1, m = 30, p = 20;
+    phs_options opt{};
+    phs::PointSet ps;
+    phs::Tree tree;
+    phs::Fmm fmm;
+    phs::Vecchia vec;
+    phs::DBuf<double> Q;      // [S][n] sorted order
+    phs::DBuf<double> R;      // S x S upper triangular, row-major
+    phs::DBuf<double> G;      // [S][n] S~^{-1} Q Rc^{-1}, Rc'Rc = Q' S~^{-1} Q (low-rank preconditioner term)
+    bool lowrank = false;
+    phs::DBuf<double> work;   // 12 work vectors of n
+    phs::DBuf<double> part;   // reduction partials
+    phs::DBuf<double> scal;   // device scalars
+    double *hscal = nullptr;  // pinned host mirror
+    phs::Timers tm;
+    float ms_plan = 0;
+    int sign = 1;             // sign * Q_perp' M Q_perp is positive definite
+    ~phs_plan() {
+        if (hscal) cudaFreeHost(hscal);
+    }
+};
+
+namespace phs {
+
+// work vector i (n doubles; 12 of them)
+double *W(phs_plan *pl, int i);
+// out[q] = a_q . b_q for the pairs given (deterministic two-level reductions), on the device
+void dots(phs_plan *pl, std::initializer_list<std::pair<const double *, const double *>> prs, double *out,
+          cudaStream_t s);
+// out = sign * P v (P = I - Q Q'); if other != null, dot(other, out) -> *dot_out (device)
+void project(phs_plan *pl, const double *v, double sign, double *out, const double *other, double *dot_out,
+             cudaStream_t s);
+// y = M' t in the normalised frame (FMM), sorted order
+void matvec_norm(phs_plan *pl, const double *t, double *y, int precision, cudaStream_t s);
+// y = M t with the caller's kernel matrix, sorted order
+void matvec_user_sorted(phs_plan *pl, const double *ts, double *y, int precision, cudaStream_t s);
+// caller order <-> sorted order, times a scale
+void to_sorted(phs_plan *pl, const double *src, double *dst, double scale, cudaStream_t s);
+void to_caller(phs_plan *pl, const double *src, double *dst, double scale, cudaStream_t s);
+// one device double to the host (synchronises s)
+double read_scalar(phs_plan *pl, const double *dev, cudaStream_t s);
+// preconditioner of the projected system (Sec. 2.2): z from r in range(P); tmp, tmp2 scratch
+void precond(phs_plan *pl, const double *r, double *z, double *tmp, double *tmp2, cudaStream_t s);
+// the low-rank (Schur complement) preconditioner term of the plan (Sec. 2.2)
+void build_lowrank(phs_plan *pl, cudaStream_t s);
+// rebuild the Vecchia preconditioner for a new Matern inverse range (synchronises s)
+void plan_set_alpha(phs_plan *pl, double alpha, cudaStream_t s);
+// restarted right-preconditioned GMRES on M c = b in sorted order (krylov.cu)
+int gmres_solve(phs_plan *pl, const double *b_s, double *x_s, int restart, double stop, int maxiter, int precision,
+                bool check_true, double *res, double *est, int *restarts, struct MvTimes *mvt, cudaStream_t s);
+// pooled CUDA events of the calling thread
+cudaEvent_t ev_get();
+void ev_put(cudaEvent_t e);
+// Matvec timing of a solve: an event pair around each matvec on the solve's stream,
+// resolved once after the solve's final synchronisation (no synchronisation per matvec).
+struct MvTimes {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    void begin(cudaStream_t s) {
+        ev.emplace_back(ev_get(), ev_get());
+        cudaEventRecord(ev.back().first, s);
+    }
+    void end(cudaStream_t s) { cudaEventRecord(ev.back().second, s); }
+    // sum of the recorded intervals in ms (the stream must have passed them); recycles the events
+    double resolve(int *count);
+    ~MvTimes();
+};
+
+}  // namespace phs

@@ -594,3 +594,52 @@ if HAVE_HYPOTHESIS:
             rest = order[k:head]  # coincident tail points (distance 0) are left out
             assert dmin[order[k]] >= 0.25 * dmin[rest].max() * (1 - 1e-12)
             dmin = np.minimum(dmin, d2[order[k]])
+
+
+# ---------------------------------------------------------------- GMRES on M alone (Sec. 3.1)
+def _small_precond(x, m=8, alpha=0.35):
+    xn, _, _ = oracle.normalize(x, 0.25)
+    order = oracle.random_order(len(x), 3)
+    nbr = oracle.knn_prev(xn, order, m)
+    d, o, _ = oracle.vecchia_factor(xn, order, nbr, m, 1.0, alpha)
+    return nbr, d, o
+
+
+@pytest.mark.parametrize("j", [1, 2, 3, 5])
+def test_gmres_minimal_residual_property(j):
+    """After j iterations (one cycle) GMRES's iterate minimises ||b - M c|| over
+    c in S K_j(M S, b): checked against a least-squares solve on an explicit, separately
+    orthonormalised Krylov basis [b, (M S) b, ..., (M S)^(j-1) b]."""
+    x = _pts(60, 21)
+    b = np.random.default_rng(22).standard_normal(60)
+    pre = _small_precond(x)
+    M = oracle.dense_matrix(x, 2)
+    S = lambda v: oracle.vecchia_apply(*pre, v)  # noqa: E731
+    c, it, cyc, res = oracle.gmres(x, 2, b, pre, tol=1e-300, restart=50, maxiter=j)
+    assert it == j and cyc == 1
+    K = [b.copy()]
+    for _ in range(j - 1):
+        K.append(M @ S(K[-1]))
+    Qk, _ = np.linalg.qr(np.array(K).T)
+    A = np.array([M @ S(Qk[:, i]) for i in range(j)]).T
+    y, *_ = np.linalg.lstsq(A, b, rcond=None)
+    want = np.linalg.norm(b - A @ y)
+    assert res == pytest.approx(want, rel=1e-9, abs=1e-12 * np.linalg.norm(b))
+
+
+def test_gmres_converges_to_direct_solve():
+    """On a small problem GMRES with the Vecchia right preconditioner reaches the dense
+    solution of M c = b; without check_true it stops at the first estimate below tol."""
+    x = _pts(250, 23)
+    b = np.random.default_rng(24).standard_normal(250)
+    pre = _small_precond(x, m=20)
+    M = oracle.dense_matrix(x, 2)
+    c_ref = np.linalg.solve(M, b)
+    c, it, cyc, res = oracle.gmres(x, 2, b, pre, tol=1e-11, restart=60, maxiter=400)
+    assert res <= 1e-11 * np.linalg.norm(b) and np.linalg.norm(b - M @ c) == pytest.approx(res, rel=1e-6)
+    assert np.linalg.norm(c - c_ref) <= 1e-11 * np.linalg.cond(M) * np.linalg.norm(c_ref)
+    c2, it2, cyc2, res2 = oracle.gmres(x, 2, b, pre, tol=1e-6, restart=60, maxiter=400, check_true=False)
+    assert cyc2 == 1 and it2 <= it
+    # without the preconditioner the same problem takes more iterations
+    c3, it3, _, _ = oracle.gmres(x, 2, b, None, tol=1e-6, restart=250, maxiter=400, check_true=False)
+    assert it3 > it2
