@@ -104,23 +104,32 @@ def test_fmm_matvec_mixed_precision(phs, k, mode, tol):
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("geom", ["uniform", "clustered"])
 def test_fmm_matvec_float_float_near_field(phs, k, geom):
-    """Mode 4 (near field in float-float on the FP32 pipe): every row within 1e-11 of the
-    oracle's exact row sum, relative to that row's sum of absolute terms -- the scale of
-    any summation's rounding -- on a random vector and on an oscillating one (the
-    preconditioned vector, whose near-field sums cancel most); and the 2-norm within
-    1e-10 of the dense product, as for FP64."""
+    """Mode 4 (near field in float-float on the FP32 pipe).  Every row within 1e-11 of the
+    oracle's exact row sum, relative to that row's sum of absolute terms (the scale of
+    any summation's rounding), on a random vector and on an oscillating one (the
+    preconditioned vector, whose sums cancel most: there ||M t|| is up to ~1e9 below the
+    sum of absolute terms for r^5, so a 2-norm bound would measure the cancellation, not
+    the arithmetic); the random vector's 2-norm within 1e-10 of the dense product, as for
+    FP64; and mode 4 against the FP64 matvec of the same plan within 1e-12 of the row
+    scale (their far fields are identical, so this isolates the near field)."""
     n = 3001
     pts = np.random.default_rng(12).random((n, 2)) if geom == "uniform" else _clustered(n, 13)
     plan = phs.Plan(_t(pts), k, fmm_order=0, vecchia_m=8, opts=phs.options(k, leaf_cap=32))
     rng = np.random.default_rng(14)
     t_rand = rng.standard_normal(n)
     t_osc = plan.precond(_t(t_rand)).cpu().numpy()
-    for t in (t_rand, t_osc):
+    for name, t in (("random", t_rand), ("oscillating", t_osc)):
         got = plan.matvec(_t(t), precision=4).cpu().numpy()
+        ref64 = plan.matvec(_t(t), precision=0).cpu().numpy()
         want = oracle.dense_matvec(pts, k, t)
         scale = oracle.dense_eval_abs(pts, t, k, pts)
-        assert np.max(np.abs(got - want) / scale) <= 1e-11, np.max(np.abs(got - want) / scale)
-        assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+        e_or = np.max(np.abs(got - want) / scale)
+        e_64 = np.max(np.abs(got - ref64) / scale)
+        rel2 = np.linalg.norm(got - want) / np.linalg.norm(want)
+        print(f"ff k={k} {geom} {name}: rows/scale {e_or:.2e}, vs FP64 {e_64:.2e}, 2-norm {rel2:.2e}")
+        assert e_or <= 1e-11 and e_64 <= 1e-12, (e_or, e_64)
+        if name == "random":
+            assert rel2 <= 1e-10, rel2
 
 
 @pytest.mark.parametrize("k", [1, 3, 5])
