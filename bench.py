@@ -76,12 +76,19 @@ def parse():
     ap.add_argument("--ordering", type=int, default=3, choices=[0, 1, 2, 3],
                     help="Vecchia enumeration: 0 random, 1 exact maxmin, 2 hierarchical maximin, "
                          "3 dyadic approximate maximin")
-    ap.add_argument("--case", default="step", choices=["step", "plan", "matvec", "precond", "cubic"],
+    ap.add_argument("--requests", type=int, default=120, help="serving case: number of requests")
+    ap.add_argument("--rates", default="4,16,saturate",
+                    help="serving case: Poisson arrival rates (requests/s), comma separated; 'saturate' = all at once")
+    ap.add_argument("--max-active", type=int, default=32, help="serving case: jobs in flight")
+    ap.add_argument("--n-max", type=int, default=500_000, help="serving case: largest request")
+    ap.add_argument("--case", default="step", choices=["step", "plan", "matvec", "precond", "cubic", "serving"],
                     help="step: the bench (plan + fit + evaluation, the JSON contract line); plan / "
                          "matvec / precond: one piece of it repeated --steps times on one plan, for "
                          "profiling; cubic: the cubic-PHS workload (n = 100,000 from 20 clusters, "
-                         "k = 3, m = 20, library defaults, tol 1e-8) timed like a step (each of these "
-                         "prints its own short line)")
+                         "k = 3, m = 20, library defaults, tol 1e-8) timed like a step; serving: the "
+                         "serving engine on a stream of requests with Poisson arrivals (n log-uniform in "
+                         "[1000, --n-max], k in 1..3) against the same stream served one job at a time "
+                         "(each of these prints its own short line)")
     return ap.parse_args()
 
 
@@ -190,6 +197,50 @@ def cpu_baseline(points, f, targets, n_full, repeats=2):
     return cpu_record(sum(r[0] for r in runs) / repeats, runs[-1][2], n_full, repeats)
 
 
+# --------------------------------------------------------------------------- serving
+def serve_stream(phs, reqs, arrivals, max_active, threads=4):
+    """Submit the requests at their arrival times (s from the start) to a server with
+    max_active slots; returns per-request latencies and the server's statistics."""
+    sv = phs.Server(max_active=max_active, setup_threads=threads)
+    t0 = time.perf_counter()
+    ids = []
+    for r, ta in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        ids.append(sv.submit(r["points"], r["f"], r["targets"], r["k"], vecchia_m=30, opts=phs.options(r["k"])))
+    res = [sv.wait(i, allow_not_converged=True) for i in ids]
+    st = sv.stats()
+    sv.close()
+    times = [r[4] for r in res]
+    lat = sorted(t[3] - t[0] for t in times)
+    span = max(t[3] for t in times) - min(t[0] for t in times)
+    import numpy as np
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(np.mean(lat)), "solves_per_s": len(reqs) / span, "span_s": span,
+            "converged": int(sum(r[3]["converged"] for r in res)),
+            "max_true_rel_res": float(max(r[3]["rel_res_true"] for r in res)),
+            "max_concurrent": st["max_concurrent"], "ticks": st["ticks"],
+            "mean_jobs_per_tick": st["job_iterations"] / max(st["ticks"], 1)}
+
+
+def serving_case(args, phs):
+    import numpy as np
+
+    import synth
+    reqs = synth.serving_requests(args.requests, n_hi=args.n_max)
+    out = {"case": "serving", "metric": "serving p50/p99 latency and solves/s at 1e-8 (FP64)",
+           "requests": len(reqs), "n_range": [1000, args.n_max],
+           "points_total": int(sum(len(r["f"]) for r in reqs)),
+           "k_mix": {str(k): sum(r["k"] == k for r in reqs) for k in (1, 2, 3)},
+           "max_active": args.max_active, "rates": {}}
+    for rate in args.rates.split(","):
+        arr = np.zeros(len(reqs)) if rate == "saturate" else synth.poisson_arrivals(len(reqs), float(rate))
+        out["rates"][rate] = {"batched": serve_stream(phs, reqs, arr, args.max_active),
+                              "sequential": serve_stream(phs, reqs, arr, 1)}
+    print(json.dumps(out))
+
+
 # --------------------------------------------------------------------------- native leg
 def main():
     args = parse()
@@ -264,6 +315,10 @@ def main():
                               "value_s": t, "steps": args.steps, "iters": info["iters"],
                               "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"],
                               "ms_fit": info["ms_fit"], "ms_matvec_avg": info["ms_matvec_avg"]}))
+        return
+    if args.case == "serving":
+        if rank == 0:
+            serving_case(args, phs)
         return
     if args.case != "step":
         # one piece of the step on the bench workload, for profilers; no timing contract

@@ -26,13 +26,15 @@
  *  - Errors are returned as phs_status; no exception crosses the ABI.  A
  *    human-readable message for the most recent failing call on the calling
  *    host thread is available from phs_last_error().
- *  - A plan may be used from one stream at a time.
- *  - Device memory: a plan's state is allocated by phs_plan_create and freed by
- *    phs_plan_destroy.  Temporaries of the calls come from a memory pool the
- *    library creates per device on first use, allocated and released in order
- *    on `stream`; the pool keeps up to 1 GB of freed blocks for reuse by later
- *    calls and returns them at process exit.  phs_dense_matvec_noalloc uses
- *    neither (see its entry).
+ *  - A plan may be used from one stream at a time: a call on another stream must
+ *    not start before the previous call's work on the plan has completed.
+ *  - Device memory: a plan's state and the temporaries of every call come from a
+ *    stream-ordered memory pool the library creates per device on first use
+ *    (cudaMallocFromPoolAsync / cudaFreeAsync on the call's stream), so creating,
+ *    using and destroying plans never synchronises the device the way
+ *    cudaMalloc / cudaFree do; the pool keeps up to 1 GB of freed blocks for reuse
+ *    and returns the rest.  phs_plan_memory reports a plan's bytes.
+ *    phs_dense_matvec_noalloc uses no pool (see its entry).
  */
 #ifndef PHS_B300_H
 #define PHS_B300_H
@@ -182,8 +184,9 @@ phs_status phs_fit_predict_host(const double *pts_host, const double *f_host, in
                                 phs_fit_info *info, phs_stream_t stream);
 
 /* Releases every device buffer the plan owns (resource management, no counterpart in the
- * paper).  Synchronises the device first, so work still queued on the plan's stream
- * finishes; NULL is accepted and does nothing; the handle is invalid afterwards. */
+ * paper).  Synchronises the stream of the plan's most recent call first (that stream
+ * must still exist), then returns the buffers to the memory pool without synchronising
+ * the device; NULL is accepted and does nothing; the handle is invalid afterwards. */
 phs_status phs_plan_destroy(phs_plan_t plan);
 
 /* Solve M c = b for the kernel matrix ALONE (no polynomial block; the preconditioning
@@ -236,6 +239,9 @@ phs_status phs_plan_precond(phs_plan_t plan, const double *r_dev, double *z_dev,
 /* Direct-interaction pair count of the tree (P2P work per matvec) and V-list
  * translation count (M2L work per matvec): counts_host[0..1]. */
 phs_status phs_plan_work(phs_plan_t plan, int64_t *counts_host);
+/* Device bytes held by the plan (tree, lists, expansions, operators, QR, Vecchia factor,
+ * work vectors; not the temporaries of calls in flight): *bytes_host. */
+phs_status phs_plan_memory(phs_plan_t plan, int64_t *bytes_host);
 /* Work of one FP64 matvec per kernel, for roofline accounting (host array of 6):
  *   [0] point pairs the near-field kernel evaluates (own leaf: all ordered pairs;
  *       pairs across leaves once on the symmetric path, both orders otherwise),
@@ -338,6 +344,52 @@ phs_status phs_vecchia_factor(const double *pts_dev, int64_t n, const int64_t *o
                               const int64_t *nbr_dev, int m, double nu, double alpha,
                               double *diag_dev, double *offd_dev, int64_t *jittered_host,
                               phs_stream_t stream);
+
+/* ---- serving: continuous batching of many interpolation requests ------------- */
+/* A server owns a scheduler thread and setup_threads host worker threads on the device
+ * current at phs_server_create.  Requests arrive through phs_server_submit from any host
+ * thread at any time.  A request is admitted while fewer than max_active are in setup or
+ * in PCG and the memory it reserves fits memory_budget (an a-priori estimate, replaced
+ * by the plan's measured bytes plus a quarter once its plan exists; a request larger
+ * than the budget still runs, alone).  Each admitted job keeps its plan (tree, FMM
+ * tables, QR, Vecchia factor -- Sec. 2) and its PCG state (Eq. 2.5) on the device until
+ * it finishes.  Every scheduler tick advances all active jobs by one PCG iteration: each
+ * job's FMM matvec and Vecchia apply run on its own stream, and the vector operations of
+ * all jobs run as shared launches, one device-to-host copy of the residuals per tick.
+ * A job computes exactly what phs_fit followed by phs_eval computes for it (same steps,
+ * same arithmetic), alone or in any mix.  FP64 solves (precision 0).  No counterpart in
+ * the paper: the serving form of its solve. */
+typedef struct phs_server *phs_server_t;
+typedef struct {
+    int64_t memory_budget;  /* device bytes the admitted jobs may reserve; <= 0: half the free memory */
+    int max_active;         /* jobs in setup or PCG at once, 1..96; <= 0: 32 */
+    int setup_threads;      /* host threads building plans and finishing jobs, 1..64; <= 0: 4 */
+} phs_server_config;
+
+/* cfg may be NULL (defaults).  Allocates the engine's stream and two small buffers. */
+phs_status phs_server_create(const phs_server_config *cfg, phs_server_t *out);
+/* Queue one request: points (n x 2), values (n) and targets (m x 2) are HOST arrays,
+ * copied before the call returns; k, poly_degree, fmm_order, vecchia_m and opt as for
+ * phs_plan_create (opt->precision must be 0; NULL: phs_options_default(k)).
+ * *job_id receives the request's id.  Thread-safe; does not wait for the GPU. */
+phs_status phs_server_submit(phs_server_t server, const double *pts_host, const double *f_host, int64_t n,
+                             const double *tgt_host, int64_t m, int k, int poly_degree, int fmm_order,
+                             int vecchia_m, const phs_options *opt, int64_t *job_id);
+/* Block until the job finishes, then copy its results to host arrays (any may be NULL):
+ * w (n), beta (S, normalised frame as phs_fit), predictions at the targets (m), info
+ * (as phs_fit's; ms_fit is the time from the end of setup to completion), and
+ * times_host[0..3] = submission, admission, end of setup and completion, in seconds
+ * since phs_server_create.  Returns the job's status (PHS_ERR_NOT_CONVERGED with results,
+ * or the error that ended it).  A job's results can be collected once. */
+phs_status phs_server_wait(phs_server_t server, int64_t job_id, double *w_host, double *beta_host,
+                           double *pred_host, phs_fit_info *info, double *times_host);
+/* stats_host[0..7] = (ticks, job-iterations run in ticks, most jobs in one tick, most
+ * bytes reserved at once, the budget, jobs completed, requests waiting for admission,
+ * bytes reserved now). */
+phs_status phs_server_stats(phs_server_t server, int64_t *stats_host);
+/* Finish every submitted job, stop the threads and release the server.  Results not
+ * collected are discarded. */
+phs_status phs_server_destroy(phs_server_t server);
 
 #ifdef __cplusplus
 }

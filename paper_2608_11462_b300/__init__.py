@@ -12,11 +12,11 @@ import ctypes
 import torch
 
 from . import _native
-from ._native import PhsError, PhsFitInfo, PhsOptions, check, lib
+from ._native import PhsError, PhsFitInfo, PhsOptions, PhsServerConfig, check, lib
 
 __all__ = ["Plan", "PhsError", "PhsOptions", "PhsFitInfo", "options", "phs_dense_matvec", "phs_random_order",
            "phs_maxmin_order", "phs_hmaxmin_order", "phs_amaxmin_order", "phs_knn_prev", "phs_vecchia_factor",
-           "phs_fit_predict_host", "phs_tune_alpha", "lib"]
+           "phs_fit_predict_host", "phs_tune_alpha", "Server", "lib"]
 
 
 def _stream(stream=None):
@@ -153,6 +153,12 @@ class Plan:
         return {"p2p_pairs": c[0], "p2p_column_pairs": c[1], "tc_steps": c[2], "tc_tiles": c[3],
                 "tc_mmas_per_step": c[4], "tc_mma_macs": c[5]}
 
+    def memory(self) -> int:
+        """phs_plan_memory: device bytes held by the plan."""
+        b = ctypes.c_int64()
+        check(lib().phs_plan_memory(self._h, ctypes.byref(b)))
+        return b.value
+
     def set_wait_limit(self, ns: int, probe: bool = False):
         """phs_plan_set_wait_limit: main-loop wait limit of the tensor-core M2L (0: 2 s) and
         the probe that makes its first wait expire (a test of the timeout path)."""
@@ -262,3 +268,61 @@ def phs_fit_predict_host(points, f, targets, k: int, poly_degree: int = -1, fmm_
     check(code)
     S = {0: 1, 1: 3, 2: 6, 3: 10}[poly_degree if poly_degree >= 0 else (k // 2 if k % 2 == 0 else (k - 1) // 2)]
     return w, beta[:S], pred, info.as_dict()
+
+
+class Server:
+    """phs_server_*: continuous batching of interpolation requests on the current device.
+    Requests are host (numpy) arrays; results come back as numpy arrays."""
+
+    def __init__(self, memory_budget: int = 0, max_active: int = 32, setup_threads: int = 4):
+        cfg = PhsServerConfig(int(memory_budget), int(max_active), int(setup_threads))
+        h = ctypes.c_void_p()
+        check(lib().phs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._shape = {}
+
+    def submit(self, points, f, targets, k: int, poly_degree: int = -1, fmm_order: int = 0, vecchia_m: int = 30,
+               opts: PhsOptions | None = None) -> int:
+        import numpy as np
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        fv = np.ascontiguousarray(f, dtype=np.float64)
+        tg = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 2)
+        o = opts if opts is not None else options(k)
+        jid = ctypes.c_int64()
+        P = ctypes.c_void_p
+        check(lib().phs_server_submit(self._h, pts.ctypes.data_as(P), fv.ctypes.data_as(P), pts.shape[0],
+                                      tg.ctypes.data_as(P), tg.shape[0], int(k), int(poly_degree), int(fmm_order),
+                                      int(vecchia_m), ctypes.byref(o), ctypes.byref(jid)))
+        deg = poly_degree if poly_degree >= 0 else (k // 2 if k % 2 == 0 else (k - 1) // 2)
+        self._shape[jid.value] = (pts.shape[0], tg.shape[0], (deg + 1) * (deg + 2) // 2)
+        return jid.value
+
+    def wait(self, job_id: int, allow_not_converged: bool = False):
+        """(w, beta, predictions, info, times = [submitted, admitted, set up, done] in s)."""
+        import numpy as np
+        n, m, S = self._shape.pop(job_id)
+        w, beta, pred, times = np.empty(n), np.empty(S), np.empty(max(m, 1)), np.empty(4)
+        info = PhsFitInfo()
+        P = ctypes.c_void_p
+        check(lib().phs_server_wait(self._h, int(job_id), w.ctypes.data_as(P), beta.ctypes.data_as(P),
+                                    pred.ctypes.data_as(P), ctypes.byref(info), times.ctypes.data_as(P)),
+              allow=(5,) if allow_not_converged else ())
+        return w, beta, pred[:m], info.as_dict(), times
+
+    def stats(self):
+        c = (ctypes.c_int64 * 8)()
+        check(lib().phs_server_stats(self._h, c))
+        keys = ["ticks", "job_iterations", "max_concurrent", "max_reserved", "budget", "completed", "waiting",
+                "reserved"]
+        return dict(zip(keys, list(c)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            check(lib().phs_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -20,6 +20,10 @@ class PhsOptions(ctypes.Structure):
                 ("precond_lowrank", ctypes.c_int)]
 
 
+class PhsServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_int64), ("max_active", ctypes.c_int), ("setup_threads", ctypes.c_int)]
+
+
 class PhsFitInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("jittered", ctypes.c_int), ("rel_res_recursive", ctypes.c_double),
@@ -33,11 +37,12 @@ class PhsFitInfo(ctypes.Structure):
 EXPORTS = [
     "phs_options_default", "phs_last_error", "phs_kernel_launches", "phs_plan_create", "phs_matvec", "phs_fit", "phs_eval",
     "phs_fit_predict_host", "phs_plan_destroy", "phs_plan_frame", "phs_plan_vecchia", "phs_plan_vecchia_factor",
-    "phs_plan_precond", "phs_plan_work", "phs_plan_kernel_work", "phs_plan_set_wait_limit", "phs_plan_set_timing",
+    "phs_plan_precond", "phs_plan_work", "phs_plan_kernel_work", "phs_plan_memory", "phs_plan_set_wait_limit", "phs_plan_set_timing",
     "phs_plan_timing", "phs_dense_matvec",
     "phs_dense_matvec_noalloc",
     "phs_random_order", "phs_maxmin_order", "phs_hmaxmin_order", "phs_amaxmin_order", "phs_knn_prev",
-    "phs_vecchia_factor", "phs_gmres", "phs_tune_alpha",
+    "phs_vecchia_factor", "phs_gmres", "phs_tune_alpha", "phs_server_create", "phs_server_submit",
+    "phs_server_wait", "phs_server_stats", "phs_server_destroy",
 ]
 
 _lib = None
@@ -69,6 +74,7 @@ def lib():
         "phs_plan_precond": (st, [P, P, P, P]),
         "phs_plan_work": (st, [P, P]),
         "phs_plan_kernel_work": (st, [P, P]),
+        "phs_plan_memory": (st, [P, P]),
         "phs_plan_set_wait_limit": (st, [P, i64, i32]),
         "phs_plan_set_timing": (st, [P, i32]),
         "phs_plan_timing": (st, [P, P, P]),
@@ -83,6 +89,12 @@ def lib():
         "phs_gmres": (st, [P, P, P, i32, i32, ctypes.POINTER(PhsFitInfo), P]),
         "phs_tune_alpha": (st, [P, P, i64, i32, i32, i32, i32, ctypes.POINTER(PhsOptions), i64,
                                 ctypes.POINTER(d), ctypes.POINTER(i32), P]),
+        "phs_server_create": (st, [ctypes.POINTER(PhsServerConfig), ctypes.POINTER(P)]),
+        "phs_server_submit": (st, [P, P, P, i64, P, i64, i32, i32, i32, i32, ctypes.POINTER(PhsOptions),
+                                   ctypes.POINTER(i64)]),
+        "phs_server_wait": (st, [P, i64, P, P, P, ctypes.POINTER(PhsFitInfo), P]),
+        "phs_server_stats": (st, [P, P]),
+        "phs_server_destroy": (st, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

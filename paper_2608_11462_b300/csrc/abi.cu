@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "plan.cuh"
@@ -31,8 +32,29 @@ cudaEvent_t ev_get() {
     return e;
 }
 
+static std::mutex g_pin_mu;
+static std::vector<double *> g_pin_free;
+double *pinned_block() {
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    if (g_pin_free.empty()) {
+        double *chunk = nullptr;
+        PHS_CUDA(cudaMallocHost((void **)&chunk, 64 * 64 * sizeof(double)));
+        for (int i = 63; i >= 0; --i) g_pin_free.push_back(chunk + 64 * i);
+    }
+    double *b = g_pin_free.back();
+    g_pin_free.pop_back();
+    return b;
+}
+void pinned_release(double *b) {
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    g_pin_free.push_back(b);
+}
+
 }  // namespace phs
 
+phs_plan::~phs_plan() {
+    if (hscal) phs::pinned_release(hscal);
+}
 
 namespace phs {
 
@@ -253,34 +275,6 @@ __global__ void proj_apply(const double *Q, int S, int64_t n, const double *c, c
     }
     if (threadIdx.x == 0) part[blockIdx.x * 12] = sh[0];
 }
-// x += alpha p, r -= alpha q, partial r.r ; alpha = sc[0] / sc[1]
-__global__ void cg_update(double *x, double *r, const double *p, const double *q, int64_t n, const double *num,
-                          const double *den, double *part) {
-    const double alpha = num[0] / den[0];
-    double acc = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * RED_T + threadIdx.x; j < n; j += (int64_t)gridDim.x * RED_T) {
-        x[j] += alpha * p[j];
-        const double rj = r[j] - alpha * q[j];
-        r[j] = rj;
-        acc += rj * rj;
-    }
-    __shared__ double sh[RED_T];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = RED_T / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x * 12] = sh[0];
-}
-// p = z + (num/den) p
-__global__ void p_update(double *p, const double *z, int64_t n, const double *num, const double *den) {
-    const double beta = num[0] / den[0];
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        p[j] = z[j] + beta * p[j];
-}
-__global__ void copy_scalar(const double *src, double *dst) { dst[0] = src[0]; }
-
 __global__ void gather_vec(const double *src, const int *idx, int64_t n, double *dst) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) dst[j] = src[idx[j]];
@@ -400,6 +394,166 @@ __global__ void ell_to_rows_d(const double *ell, int64_t n, int m, int slot0, do
 __global__ void pts_to_d2(const double *p, int64_t n, double2 *out) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) out[j] = make_double2(p[2 * j], p[2 * j + 1]);
+}
+
+// ---------------------------------------------------------------- PCG steps, one or many plans
+// The PCG vector operations (projection of the matvec, CG update, preconditioner
+// projection, p update) are written once as bodies parameterised by the block's
+// coordinates and applied to a table of plans: blockIdx.y selects the plan and
+// blockIdx.x / gridDim.x play the roles they have in a one-plan launch (RED_B blocks of
+// RED_T threads per plan).  The single-plan solve uses a table of one, the serving
+// engine a table of the active jobs, so a job's arithmetic -- and its result -- does
+// not depend on which other jobs share the launch.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = RED_T / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+// coefficients B' v, this block's share: part[bx * 12 + c]
+__device__ void b_coef_body(const double *B, int S, int64_t n, const double *v, double *part, int bx, int gx) {
+    __shared__ double sh[RED_T];
+    double acc[MAXS];
+    for (int c = 0; c < S; ++c) acc[c] = 0.0;
+    for (int64_t j = (int64_t)bx * RED_T + threadIdx.x; j < n; j += (int64_t)gx * RED_T) {
+        const double vj = v[j];
+        for (int c = 0; c < S; ++c) acc[c] = fma(B[(int64_t)c * n + j], vj, acc[c]);
+    }
+    for (int c = 0; c < S; ++c) {
+        const double t = block_sum(acc[c], sh);
+        if (threadIdx.x == 0) part[bx * 12 + c] = t;
+    }
+}
+// out = sum of the RED_B partials of value i, fixed order
+__device__ void b_final_body(const double *part, int i, double *out) {
+    __shared__ double sh[RED_T];
+    double sacc = 0.0;
+    for (int b = threadIdx.x; b < RED_B; b += RED_T) sacc += part[b * 12 + i];
+    const double t = block_sum(sacc, sh);
+    if (threadIdx.x == 0) out[0] = t;
+}
+// out = sign (v - B c); if other, this block's share of other . out in part[bx * 12]
+__device__ void b_proj_body(const double *B, int S, int64_t n, const double *c, const double *v, double sign,
+                            double *out, const double *other, double *part, int bx, int gx) {
+    __shared__ double sh[RED_T];
+    double cc[MAXS];
+    for (int q = 0; q < S; ++q) cc[q] = c[q];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)bx * RED_T + threadIdx.x; j < n; j += (int64_t)gx * RED_T) {
+        double xv = v[j];
+        for (int q = 0; q < S; ++q) xv = fma(-B[(int64_t)q * n + j], cc[q], xv);
+        xv *= sign;
+        out[j] = xv;
+        if (other) acc = fma(other[j], xv, acc);
+    }
+    if (!other) return;
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[bx * 12] = t;
+}
+
+template <int N>
+__global__ void bk_coef(BTable<N> t, int stage) {
+    // stage 0: Q' y (matvec projection); 1: the preconditioner's projection coefficients
+    // (plain: Q' t2; low-rank: G' r)
+    const BJob &j = t.j[blockIdx.y];
+    const bool lr = stage == 1 && j.lowrank;
+    const double *B = lr ? j.G : j.Q;
+    const double *v = stage == 0 ? j.W + 4 * j.n : (lr ? j.W : j.W + 6 * j.n);
+    b_coef_body(B, j.S, j.n, v, j.part, blockIdx.x, gridDim.x);
+}
+template <int N>
+__global__ void bk_final(BTable<N> t, int cnt, int out_off) {
+    // value i = blockIdx.x; cnt < 0: the plan's S values
+    const BJob &j = t.j[blockIdx.y];
+    const int nv = cnt < 0 ? j.S : cnt;
+    if ((int)blockIdx.x >= nv) return;
+    b_final_body(j.part, blockIdx.x, j.scal + out_off + blockIdx.x);
+}
+template <int N>
+__global__ void bk_proj(BTable<N> t, int stage) {
+    // stage 0: q = sign P y and partial p . q; 1: z = t2 - B c (B = Q or G)
+    const BJob &j = t.j[blockIdx.y];
+    const int64_t n = j.n;
+    if (stage == 0)
+        b_proj_body(j.Q, j.S, n, j.scal + 16, j.W + 4 * n, j.sign, j.W + 3 * n, j.W + 2 * n, j.part, blockIdx.x,
+                    gridDim.x);
+    else
+        b_proj_body(j.lowrank ? j.G : j.Q, j.S, n, j.scal + 16, j.W + 6 * n, 1.0, j.W + n, nullptr, nullptr,
+                    blockIdx.x, gridDim.x);
+}
+// x += alpha p, r -= alpha q, partial r . r; alpha = rz / pq
+template <int N>
+__global__ void bk_cg_update(BTable<N> t) {
+    __shared__ double sh[RED_T];
+    const BJob &j = t.j[blockIdx.y];
+    const int64_t n = j.n;
+    double *r = j.W;
+    const double *p = j.W + 2 * n, *q = j.W + 3 * n;
+    const double alpha = j.scal[0] / j.scal[1];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RED_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_T) {
+        j.x[i] = fma(alpha, p[i], j.x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    const double tt = block_sum(acc, sh);
+    if (threadIdx.x == 0) j.part[blockIdx.x * 12] = tt;
+}
+// partials of W[a] . W[b] into part[bx * 12 + slot]
+template <int N>
+__global__ void bk_dot(BTable<N> t, int a, int b, int slot) {
+    __shared__ double sh[RED_T];
+    const BJob &j = t.j[blockIdx.y];
+    const int64_t n = j.n;
+    const double *u = j.W + a * n, *v = j.W + b * n;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RED_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_T)
+        acc = fma(u[i], v[i], acc);
+    const double tt = block_sum(acc, sh);
+    if (threadIdx.x == 0) j.part[blockIdx.x * 12 + slot] = tt;
+}
+// p = z + (rz_new / rz) p (rz = rz_new follows in a separate launch, bk_copy)
+template <int N>
+__global__ void bk_p_update(BTable<N> t) {
+    const BJob &j = t.j[blockIdx.y];
+    const int64_t n = j.n;
+    double *p = j.W + 2 * n;
+    const double *z = j.W + n;
+    const double beta = j.scal[3] / j.scal[0];
+    for (int64_t i = (int64_t)blockIdx.x * RED_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_T)
+        p[i] = fma(beta, p[i], z[i]);
+}
+template <int N>
+__global__ void bk_copy(BTable<N> t, int from, int to) {
+    const BJob &j = t.j[blockIdx.x];
+    if (threadIdx.x == 0) j.scal[to] = j.scal[from];
+}
+// out[k] = scal_k[off] for the table's plans
+template <int N>
+__global__ void bk_gather(BTable<N> t, int off, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < t.nj) out[k] = t.j[k].scal[off];
+}
+// r = rhs, x = 0 (the start of a solve); p = z after the first preconditioner application
+template <int N>
+__global__ void bk_start(BTable<N> t) {
+    const BJob &j = t.j[blockIdx.y];
+    for (int64_t i = (int64_t)blockIdx.x * RED_T + threadIdx.x; i < j.n; i += (int64_t)gridDim.x * RED_T) {
+        j.x[i] = 0.0;
+        j.W[i] = j.rhs[i];
+    }
+}
+template <int N>
+__global__ void bk_p_from_z(BTable<N> t) {
+    const BJob &j = t.j[blockIdx.y];
+    for (int64_t i = (int64_t)blockIdx.x * RED_T + threadIdx.x; i < j.n; i += (int64_t)gridDim.x * RED_T)
+        j.W[2 * j.n + i] = j.W[j.n + i];
 }
 
 }  // namespace
@@ -565,45 +719,183 @@ MvTimes::~MvTimes() {
     }
 }
 
+template <int N>
+static void steps_matvec_update(const BTable<N> &t, cudaStream_t s) {
+    const dim3 g(RED_B, t.nj);
+    bk_coef<N><<<g, RED_T, 0, s>>>(t, 0);
+    PHS_LAUNCH_CHECK();
+    bk_final<N><<<dim3(MAXS, t.nj), RED_T, 0, s>>>(t, -1, 16);
+    PHS_LAUNCH_CHECK();
+    bk_proj<N><<<g, RED_T, 0, s>>>(t, 0);
+    PHS_LAUNCH_CHECK();
+    bk_final<N><<<dim3(1, t.nj), RED_T, 0, s>>>(t, 1, 1);
+    PHS_LAUNCH_CHECK();
+    bk_cg_update<N><<<g, RED_T, 0, s>>>(t);
+    PHS_LAUNCH_CHECK();
+    bk_final<N><<<dim3(1, t.nj), RED_T, 0, s>>>(t, 1, 2);
+    PHS_LAUNCH_CHECK();
+}
+template <int N>
+static void steps_zproj(const BTable<N> &t, cudaStream_t s) {
+    const dim3 g(RED_B, t.nj);
+    bk_coef<N><<<g, RED_T, 0, s>>>(t, 1);
+    PHS_LAUNCH_CHECK();
+    bk_final<N><<<dim3(MAXS, t.nj), RED_T, 0, s>>>(t, -1, 16);
+    PHS_LAUNCH_CHECK();
+    bk_proj<N><<<g, RED_T, 0, s>>>(t, 1);
+    PHS_LAUNCH_CHECK();
+}
+template <int N>
+static void steps_pupdate(const BTable<N> &t, cudaStream_t s) {
+    const dim3 g(RED_B, t.nj);
+    bk_dot<N><<<g, RED_T, 0, s>>>(t, 0, 1, 0);
+    PHS_LAUNCH_CHECK();
+    bk_final<N><<<dim3(1, t.nj), RED_T, 0, s>>>(t, 1, 3);
+    PHS_LAUNCH_CHECK();
+    bk_p_update<N><<<g, RED_T, 0, s>>>(t);
+    PHS_LAUNCH_CHECK();
+    bk_copy<N><<<t.nj, 32, 0, s>>>(t, 3, 0);
+    PHS_LAUNCH_CHECK();
+}
+template <int N>
+static void steps_start(const BTable<N> &t, cudaStream_t s) {
+    // after z = P S~^-1 r: p = z, rz and rr into scal 4 and 5, rz into scal 0
+    const dim3 g(RED_B, t.nj);
+    bk_p_from_z<N><<<g, RED_T, 0, s>>>(t);
+    PHS_LAUNCH_CHECK();
+    bk_dot<N><<<g, RED_T, 0, s>>>(t, 0, 1, 0);
+    PHS_LAUNCH_CHECK();
+    bk_dot<N><<<g, RED_T, 0, s>>>(t, 0, 0, 1);
+    PHS_LAUNCH_CHECK();
+    bk_final<N><<<dim3(2, t.nj), RED_T, 0, s>>>(t, 2, 4);
+    PHS_LAUNCH_CHECK();
+    bk_copy<N><<<t.nj, 32, 0, s>>>(t, 4, 0);
+    PHS_LAUNCH_CHECK();
+}
+
+BJob bjob_of(phs_plan *pl, const double *rhs, double *x) {
+    BJob b;
+    b.n = pl->ps.n;
+    b.S = pl->S;
+    b.lowrank = pl->lowrank ? 1 : 0;
+    b.sign = (double)pl->sign;
+    b.Q = pl->Q.get();
+    b.G = pl->lowrank ? pl->G.get() : nullptr;
+    b.W = pl->work.get();
+    b.x = x;
+    b.rhs = rhs;
+    b.part = pl->part.get();
+    b.scal = pl->scal.get();
+    return b;
+}
+void batch_matvec_update(const BatchTable &t, cudaStream_t s) { steps_matvec_update(t, s); }
+void batch_zproj(const BatchTable &t, cudaStream_t s) { steps_zproj(t, s); }
+void batch_pupdate(const BatchTable &t, cudaStream_t s) { steps_pupdate(t, s); }
+void batch_gather(const BatchTable &t, int off, double *out_dev, cudaStream_t s) {
+    bk_gather<kMaxBatch><<<1, kMaxBatch, 0, s>>>(t, off, out_dev);
+    PHS_LAUNCH_CHECK();
+}
+
+// The start of PCG on one plan: x = 0, r = rhs, z = P S~^-1 r, p = z, rz; returns r . r
+// (synchronises s).  Work vectors 0..6.
+double pcg_start(phs_plan *pl, const double *rhs, double *x, cudaStream_t s) {
+    BTable<1> t;
+    t.nj = 1;
+    t.j[0] = bjob_of(pl, rhs, x);
+    const int64_t n = pl->ps.n;
+    bk_start<1><<<dim3(RED_B, 1), RED_T, 0, s>>>(t);
+    PHS_LAUNCH_CHECK();
+    pl->tm.begin(s);
+    vecchia_apply(pl->vec, W(pl, 0), W(pl, 5), W(pl, 6), s);
+    pl->tm.end(T_PRECOND, s);
+    steps_zproj(t, s);
+    steps_start(t, s);
+    (void)n;
+    return read_scalar(pl, pl->scal.get() + 5, s);
+}
+
+// PCG on sign * P M' P x = rhs (rhs in range(P)), x0 = 0.  Returns iterations; *rr_final
+// the last recursive r . r.  Work vectors 0..6.  The vector operations are the table
+// steps above with a table of one plan (the serving engine runs the same steps on many).
 static int pcg(phs_plan *pl, const double *rhs, double *x, double tol_abs, int maxiter, int precision,
                double *rr_final, cudaStream_t s, MvTimes *mvt) {
-    const int64_t n = pl->ps.n;
-    double *r = W(pl, 0), *z = W(pl, 1), *p = W(pl, 2), *q = W(pl, 3), *y = W(pl, 4), *t1 = W(pl, 5),
-           *t2 = W(pl, 6);
-    double *sc = pl->scal.get();  // 0 rz, 1 pq, 2 rr, 3 rz_new
-    zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
-    PHS_CUDA(cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    precond(pl, r, z, t1, t2, s);
-    PHS_CUDA(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    dots(pl, {{r, z}, {r, r}}, sc + 4, s);
-    copy_scalar<<<1, 1, 0, s>>>(sc + 4, sc + 0);
-    double rr = read_scalar(pl, sc + 5, s);
+    BTable<1> t;
+    t.nj = 1;
+    t.j[0] = bjob_of(pl, rhs, x);
+    double rr = pcg_start(pl, rhs, x, s);
     int it = 0;
     while (std::sqrt(rr) > tol_abs && it < maxiter) {
         if (mvt) mvt->begin(s);
-        matvec_norm(pl, p, y, precision, s);
+        matvec_norm(pl, W(pl, 2), W(pl, 4), precision, s);
         if (mvt) mvt->end(s);
         pl->tm.begin(s);
-        project(pl, y, (double)pl->sign, q, p, sc + 1, s);
-        cg_update<<<RED_B, RED_T, 0, s>>>(x, r, p, q, n, sc + 0, sc + 1, pl->part.get());
-        PHS_LAUNCH_CHECK();
-        dots_final<<<1, RED_T, 0, s>>>(pl->part.get(), RED_B, sc + 2);
-        PHS_LAUNCH_CHECK();
+        steps_matvec_update(t, s);
         pl->tm.end(T_VEC, s);
-        rr = read_scalar(pl, sc + 2, s);
+        rr = read_scalar(pl, pl->scal.get() + 2, s);
         ++it;
         if (std::sqrt(rr) <= tol_abs) break;
-        precond(pl, r, z, t1, t2, s);
         pl->tm.begin(s);
-        dots(pl, {{r, z}}, sc + 3, s);
-        p_update<<<RED_B, RED_T, 0, s>>>(p, z, n, sc + 3, sc + 0);
-        PHS_LAUNCH_CHECK();
-        copy_scalar<<<1, 1, 0, s>>>(sc + 3, sc + 0);
-        PHS_LAUNCH_CHECK();
+        vecchia_apply(pl->vec, W(pl, 0), W(pl, 5), W(pl, 6), s);
+        pl->tm.end(T_PRECOND, s);
+        pl->tm.begin(s);
+        steps_zproj(t, s);
+        steps_pupdate(t, s);
         pl->tm.end(T_VEC, s);
     }
     *rr_final = rr;
     return it;
+}
+
+// The start of a fit (Eq. 2.5): f to sorted order (work vector 7), rhs = sign P f (work
+// vector 8), the norms and the stopping threshold; synchronises s.  When P f vanishes to
+// rounding (f in span(B)) the solution is w = 0 and x (work vector 9) is zeroed.
+FitStart fit_begin(phs_plan *pl, const double *f_dev, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    const phs_options &o = pl->opt;
+    double *fs = W(pl, 7), *rhs = W(pl, 8), *x = W(pl, 9);
+    double *sc = pl->scal.get();
+    gather_vec<<<blocks_for(n, 256), 256, 0, s>>>(f_dev, pl->ps.perm.get(), n, fs);
+    PHS_LAUNCH_CHECK();
+    project(pl, fs, (double)pl->sign, rhs, rhs, sc + 6, s);
+    const double rr0 = read_scalar(pl, sc + 6, s);
+    dots(pl, {{fs, fs}}, sc + 9, s);
+    FitStart st;
+    st.fnrm = std::sqrt(read_scalar(pl, sc + 9, s));
+    st.nrm0 = std::sqrt(rr0);
+    st.stop = std::max(o.tol * st.nrm0, o.atol);
+    st.trivial = st.nrm0 <= 1e-14 * st.fnrm || st.nrm0 == 0.0;
+    if (st.trivial) {
+        zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
+        PHS_LAUNCH_CHECK();
+    }
+    return st;
+}
+
+// The end of a fit from x (work vector 9) and f (work vector 7): beta from
+// R beta = Q'(f - M' x) (Eq. 2.5), the true residual ||P (f - M' x)||^2 (returned), and
+// w = rho^k x in caller order; synchronises s.
+double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    double *fs = W(pl, 7), *x = W(pl, 9), *y = W(pl, 10), *d = W(pl, 11);
+    double *sc = pl->scal.get();
+    // the low-rank preconditioner keeps the iterates in range(P) only up to rounding
+    if (pl->lowrank) project(pl, x, 1.0, x, nullptr, nullptr, s);
+    matvec_norm(pl, x, y, 0, s);
+    sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, fs, y, n);
+    PHS_LAUNCH_CHECK();
+    qt_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, y, pl->part.get());
+    PHS_LAUNCH_CHECK();
+    dots_final<<<pl->S, RED_T, 0, s>>>(pl->part.get(), RED_B, sc + 40);
+    PHS_LAUNCH_CHECK();
+    tri_solve<<<1, 1, 0, s>>>(pl->R.get(), pl->S, sc + 40, beta_dev);
+    PHS_LAUNCH_CHECK();
+    project(pl, y, 1.0, d, d, sc + 8, s);
+    const double rr_true = read_scalar(pl, sc + 8, s);
+    scatter_scaled<<<blocks_for(n, 256), 256, 0, s>>>(x, pl->ps.perm.get(), n, std::pow(pl->ps.frame.rho, (double)pl->k),
+                                                       w_dev);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaStreamSynchronize(s));
+    return rr_true;
 }
 
 }  // namespace phs
@@ -656,7 +948,9 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     phs_plan *pl = new phs_plan();
+    pl->last_stream = s;
     try {
+        AllocScope scope(s, &pl->dev_bytes);
         pl->k = k;
         pl->deg = deg;
         pl->S = S;
@@ -677,7 +971,7 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         }
         pl->p = p;
         pl->sign = cpd_sign(k);
-        PHS_CUDA(cudaMallocHost((void **)&pl->hscal, 64 * sizeof(double)));
+        pl->hscal = pinned_block();
         build_points_and_tree(pts_dev, n, o.domain_halfwidth, o.leaf_cap, pl->ps, pl->tree, s);
         // Chebyshev order for the distance kernel: interpolation error ~ 5.83^-q at the
         // V-list separation (Bernstein ellipse of a unit gap), q in [6, 16]
@@ -723,7 +1017,8 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
 phs_status phs_plan_destroy(phs_plan_t plan) {
     PHS_TRY
     if (plan) {
-        cudaDeviceSynchronize();
+        // the plan's work was issued on its last call's stream (calls on a plan are ordered)
+        cudaStreamSynchronize(plan->last_stream);
         delete plan;
     }
     PHS_CATCH
@@ -734,6 +1029,8 @@ phs_status phs_matvec(phs_plan_t pl, const double *t_dev, double *out_dev, int p
     PHS_REQUIRE(pl && t_dev && out_dev && t_dev != out_dev, PHS_ERR_INVALID_ARG, "bad arguments");
     PHS_REQUIRE(precision >= 0 && precision <= 4, PHS_ERR_INVALID_ARG, "precision must be 0..4");
     cudaStream_t s = (cudaStream_t)stream;
+    AllocScope scope(s, &pl->dev_bytes);
+    pl->last_stream = s;
     double *ts = W(pl, 8), *y = W(pl, 9);
     to_sorted(pl, t_dev, ts, 1.0, s);
     pl->tm.begin(s);
@@ -748,27 +1045,20 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
     PHS_TRY
     PHS_REQUIRE(pl && f_dev && w_dev && beta_dev, PHS_ERR_INVALID_ARG, "bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
+    AllocScope scope(s, &pl->dev_bytes);
+    pl->last_stream = s;
     auto t0 = std::chrono::steady_clock::now();
     const int64_t n = pl->ps.n;
     const phs_options &o = pl->opt;
     double *fs = W(pl, 7), *rhs = W(pl, 8), *x = W(pl, 9), *y = W(pl, 10), *d = W(pl, 11);
     double *sc = pl->scal.get();
-    gather_vec<<<blocks_for(n, 256), 256, 0, s>>>(f_dev, pl->ps.perm.get(), n, fs);
-    PHS_LAUNCH_CHECK();
-    // rhs = sign * P f
-    project(pl, fs, (double)pl->sign, rhs, rhs, sc + 6, s);
-    const double rr0 = read_scalar(pl, sc + 6, s);
-    dots(pl, {{fs, fs}}, sc + 9, s);
-    const double fnrm = std::sqrt(read_scalar(pl, sc + 9, s));
-    const double nrm0 = std::sqrt(rr0);
-    const double stop = std::max(o.tol * nrm0, o.atol);
+    const FitStart st = fit_begin(pl, f_dev, s);
+    const double nrm0 = st.nrm0, stop = st.stop;
     MvTimes mvt;
     int iters = 0, outer = 0;
-    double rr = rr0;
+    double rr = nrm0 * nrm0;
     bool converged = false;
-    // f in span(B) up to rounding: the projected right-hand side is noise, w = 0
-    if (nrm0 <= 1e-14 * fnrm || nrm0 == 0.0) {
-        zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
+    if (st.trivial) {
         converged = true;
     } else if (o.precision == 0) {
         iters = pcg(pl, rhs, x, stop, o.maxiter, 0, &rr, s, &mvt);
@@ -803,26 +1093,7 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
             if (it == 0) break;
         }
     }
-    // the low-rank preconditioner keeps the iterates in range(P) only up to rounding
-    if (pl->lowrank) project(pl, x, 1.0, x, nullptr, nullptr, s);
-    // beta: R beta = Q' (f - M' w)
-    matvec_norm(pl, x, y, 0, s);
-    sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, fs, y, n);
-    PHS_LAUNCH_CHECK();
-    qt_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, y, pl->part.get());
-    PHS_LAUNCH_CHECK();
-    dots_final<<<pl->S, RED_T, 0, s>>>(pl->part.get(), RED_B, sc + 40);
-    PHS_LAUNCH_CHECK();
-    tri_solve<<<1, 1, 0, s>>>(pl->R.get(), pl->S, sc + 40, beta_dev);
-    PHS_LAUNCH_CHECK();
-    // true relative residual ||P (f - M' w)|| / ||P f||
-    project(pl, y, 1.0, d, d, sc + 8, s);
-    const double rr_true = read_scalar(pl, sc + 8, s);
-    // caller frame and order: w_user = rho^k w'
-    scatter_scaled<<<blocks_for(n, 256), 256, 0, s>>>(x, pl->ps.perm.get(), n, std::pow(pl->ps.frame.rho, (double)pl->k),
-                                                       w_dev);
-    PHS_LAUNCH_CHECK();
-    PHS_CUDA(cudaStreamSynchronize(s));
+    const double rr_true = fit_end(pl, w_dev, beta_dev, s);
     int n_mv = 0;
     const double ms_mv = mvt.resolve(&n_mv);
     m2l_tc_check(pl->fmm, s);
@@ -848,6 +1119,8 @@ phs_status phs_eval(phs_plan_t pl, const double *w_dev, const double *beta_dev, 
                 "bad arguments");
     if (m == 0) return PHS_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    AllocScope scope(s, &pl->dev_bytes);
+    pl->last_stream = s;
     const int64_t n = pl->ps.n;
     double *ws = W(pl, 8);
     // w' = rho^-k w_user in sorted order
@@ -980,6 +1253,8 @@ phs_status phs_plan_precond(phs_plan_t pl, const double *r_dev, double *z_dev, p
     PHS_TRY
     PHS_REQUIRE(pl && r_dev && z_dev, PHS_ERR_INVALID_ARG, "bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
+    AllocScope scope(s, &pl->dev_bytes);
+    pl->last_stream = s;
     const int64_t n = pl->ps.n;
     double *rs = W(pl, 8), *zs = W(pl, 9);
     gather_vec<<<blocks_for(n, 256), 256, 0, s>>>(r_dev, pl->ps.perm.get(), n, rs);
@@ -997,6 +1272,13 @@ phs_status phs_plan_work(phs_plan_t pl, int64_t *counts_host) {
     PHS_REQUIRE(pl && counts_host, PHS_ERR_INVALID_ARG, "bad arguments");
     counts_host[0] = pl->tree.near_pairs;
     counts_host[1] = pl->tree.m2l_pairs;
+    PHS_CATCH
+}
+
+phs_status phs_plan_memory(phs_plan_t pl, int64_t *bytes_host) {
+    PHS_TRY
+    PHS_REQUIRE(pl && bytes_host, PHS_ERR_INVALID_ARG, "bad arguments");
+    *bytes_host = pl->dev_bytes;
     PHS_CATCH
 }
 

@@ -785,15 +785,19 @@ __global__ void __launch_bounds__(P2P_T) p2p_kernel(TreeView tv, int nleaf, cons
 // one DADD and two DFMA instead of two DADD, a DMUL and a DFMA.  The cancellation error
 // is at most eps (a_i + a_j), small beside every term of the sum; a self pair may give a
 // tiny non-zero r^2 instead of 0, whose contribution (r^2 log r^2) is below 1e-17.
+// For odd k the square root turns that absolute error into eps (a_i + a_j) / (2 r) in
+// r -- large for close pairs, and a self pair would get r ~ 1e-8 w instead of 0 -- so
+// odd k forms r^2 from the differences (x_i = -mx / 2 exactly).
 template <int K, bool kTab>
 __device__ __forceinline__ double phi_sym_a(double mx, double my, double ai, double xj, double yj, double aj,
                                             const double2 *tab, const double *eln2) {
-    const double r2 = fma(mx, xj, fma(my, yj, ai + aj));
     if constexpr (kTab) {
+        const double r2 = fma(mx, xj, fma(my, yj, ai + aj));
         const double L = tab_log(r2, tab, eln2);
         return K == 2 ? r2 * L : (r2 * r2) * L;
     } else {
-        return phi_r2<double, K>(fmax(r2, 0.0));
+        const double dx = fma(-0.5, mx, -xj), dy = fma(-0.5, my, -yj);
+        return phi_r2<double, K>(fma(dx, dx, dy * dy));
     }
 }
 
@@ -1109,15 +1113,14 @@ static void ensure_bufs(Fmm &f, const Tree &t) {
 // dynamic shared memory of the FP64 passes exceeds 48 KB for nd = 9, P = 61 (M2M: 8 nd P
 // complex values, 70 KB)
 static void set_pass_smem_limits() {
-    static bool done = false;
-    if (done) return;
+    once_per_device(4, [] {
     const int lim = 100 * 1024;
     PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     PHS_CUDA(cudaFuncSetAttribute(p2m64_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     PHS_CUDA(cudaFuncSetAttribute(m2m64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     PHS_CUDA(cudaFuncSetAttribute(l2l64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    done = true;
+    });
 }
 
 template <typename T>
@@ -1500,8 +1503,8 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
         if (tensor_m2l && f.log_core && m2l_tc_supported(f.nd, f.P)) m2l_tc_setup(f, dt.re, dt.im, mx, s);
     }
     PHS_CUDA(cudaStreamSynchronize(s));
-    upload_log_tables();
-    upload_ff_tables();
+    once_per_device(1, upload_log_tables);
+    once_per_device(2, upload_ff_tables);
     if (!f.log_core) cheb_setup(f, cheb_q, s);
     m2l_tc_count(f, t, s);
 }

@@ -216,6 +216,8 @@ extern "C" phs_status phs_gmres(phs_plan_t pl, const double *b_dev, double *c_de
     PHS_REQUIRE(pl && b_dev && c_dev && b_dev != c_dev, PHS_ERR_INVALID_ARG, "bad arguments");
     PHS_REQUIRE(restart >= 1 && restart < kMaxRestart, PHS_ERR_INVALID_ARG, "restart must be in 1..127");
     cudaStream_t s = (cudaStream_t)stream;
+    AllocScope scope(s, &pl->dev_bytes);
+    pl->last_stream = s;
     auto t0 = std::chrono::steady_clock::now();
     const int64_t n = pl->ps.n;
     const phs_options &o = pl->opt;

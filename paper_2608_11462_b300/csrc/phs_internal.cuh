@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <exception>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -67,29 +68,68 @@ inline unsigned blocks_for(int64_t n, int threads) {
 }
 
 // ---------------------------------------------------------------- device buffers
+// Allocation context of the calling thread.  While an AllocScope is alive (the plan
+// entry points open one), DBuf allocations come from the library's stream-ordered memory
+// pool on the scope's stream and are counted into the scope's byte counter, so creating
+// and destroying plans never triggers the implicit device synchronisation of
+// cudaMalloc/cudaFree.  A pooled buffer is released in stream order: on the stream of
+// the scope active at release, else on a library-owned stream of the device (used after
+// the caller's work on the buffer is known to be complete, as in phs_plan_destroy).
+// Outside any scope DBuf falls back to cudaMalloc/cudaFree.
+struct AllocCtx {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    int64_t *bytes = nullptr;
+};
+AllocCtx &alloc_ctx();
+struct AllocScope {
+    AllocCtx prev;
+    AllocScope(cudaStream_t s, int64_t *bytes) : prev(alloc_ctx()) { alloc_ctx() = AllocCtx{true, s, bytes}; }
+    ~AllocScope() { alloc_ctx() = prev; }
+    AllocScope(const AllocScope &) = delete;
+    AllocScope &operator=(const AllocScope &) = delete;
+};
+void dbuf_alloc(void **p, size_t bytes, bool *pooled, int64_t **acct);
+// run fn once per (device, id) in this process, under a lock (constant tables, function
+// attributes); ids: 1 log tables, 2 float-float tables, 3 Bessel tables, 4 pass limits
+void once_per_device(int id, const std::function<void()> &fn);
+void dbuf_free(void *p, size_t bytes, bool pooled, int64_t *acct);
+
 template <typename T>
 struct DBuf {
     T *p = nullptr;
     size_t n = 0;
+    bool pooled = false;
+    int64_t *acct = nullptr;
     DBuf() = default;
     explicit DBuf(size_t count) { alloc(count); }
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
-    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), pooled(o.pooled), acct(o.acct) {
+        o.p = nullptr;
+        o.n = 0;
+        o.acct = nullptr;
+    }
     DBuf &operator=(DBuf &&o) noexcept {
-        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; pooled = o.pooled; acct = o.acct;
+            o.p = nullptr; o.n = 0; o.acct = nullptr;
+        }
         return *this;
     }
     ~DBuf() { release(); }
     void alloc(size_t count) {
         release();
-        if (count) PHS_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+        if (count) dbuf_alloc((void **)&p, count * sizeof(T), &pooled, &acct);
         n = count;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) dbuf_free(p, n * sizeof(T), pooled, acct);
         p = nullptr;
         n = 0;
+        pooled = false;
+        acct = nullptr;
     }
     T *get() const { return p; }
 };

@@ -10,6 +10,10 @@
 // A plan: one point set with its tree, FMM tables, polynomial QR and Vecchia factor, and
 // the work vectors of its solves.  Vectors inside are in sorted (Morton) order.
 struct phs_plan {
+    // device bytes held by the plan's buffers (first member: destroyed last, after every
+    // buffer that counts into it)
+    int64_t dev_bytes = 0;
+    cudaStream_t last_stream = nullptr;  // stream of the plan's most recent call
     int k = 2, S = 3, deg = 1, m = 30, p = 20;
     phs_options opt{};
     phs::PointSet ps;
@@ -23,16 +27,19 @@ struct phs_plan {
     phs::DBuf<double> work;   // 12 work vectors of n
     phs::DBuf<double> part;   // reduction partials
     phs::DBuf<double> scal;   // device scalars
-    double *hscal = nullptr;  // pinned host mirror
+    double *hscal = nullptr;  // pinned host mirror (64 doubles from phs::pinned_block)
     phs::Timers tm;
     float ms_plan = 0;
     int sign = 1;             // sign * Q_perp' M Q_perp is positive definite
-    ~phs_plan() {
-        if (hscal) cudaFreeHost(hscal);
-    }
+    ~phs_plan();
 };
 
 namespace phs {
+
+// 64 pinned host doubles from a process-wide pool (never returned to the driver, so a
+// plan's destruction does not synchronise the device through cudaFreeHost)
+double *pinned_block();
+void pinned_release(double *b);
 
 // work vector i (n doubles; 12 of them)
 double *W(phs_plan *pl, int i);
@@ -60,6 +67,47 @@ void plan_set_alpha(phs_plan *pl, double alpha, cudaStream_t s);
 // restarted right-preconditioned GMRES on M c = b in sorted order (krylov.cu)
 int gmres_solve(phs_plan *pl, const double *b_s, double *x_s, int restart, double stop, int maxiter, int precision,
                 bool check_true, double *res, double *est, int *restarts, struct MvTimes *mvt, cudaStream_t s);
+// ---- a fit in pieces (abi.cu): begin, the PCG iterations, end
+struct FitStart {
+    double nrm0, fnrm, stop;  // ||P f||, ||f||, max(tol ||P f||, atol)
+    bool trivial;             // P f vanishes to rounding: w = 0 (x already zeroed)
+};
+FitStart fit_begin(phs_plan *pl, const double *f_dev, cudaStream_t s);
+double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s);
+
+// ---- PCG steps on a table of plans (abi.cu).  Each step runs RED_B x RED_T blocks per
+// plan with blockIdx.y selecting the plan, the same arithmetic as on a one-plan table,
+// so a plan's iterates do not depend on the other plans of the table.
+struct BJob {
+    int64_t n;
+    int S, lowrank;
+    double sign;
+    const double *Q, *G;  // projection basis; the low-rank term's basis (or null)
+    double *W;            // work vectors: r 0, z 1, p 2, q 3, y 4, t1 5, t2 6
+    double *x;            // iterate
+    const double *rhs;    // right-hand side (read by the start step)
+    double *part;         // reduction partials [RED_B][12]
+    double *scal;         // device scalars: 0 rz, 1 pq, 2 rr, 3 rz_new, 4-5 start, 16.. coefficients
+};
+template <int N>
+struct BTable {
+    int nj;
+    BJob j[N];
+};
+constexpr int kMaxBatch = 96;  // plans per table (passed by value: 96 x 88 bytes of parameters)
+using BatchTable = BTable<kMaxBatch>;
+BJob bjob_of(phs_plan *pl, const double *rhs, double *x);
+// the start of PCG on one plan (x = 0, r = rhs, z, p, rz); returns r . r (synchronises s)
+double pcg_start(phs_plan *pl, const double *rhs, double *x, cudaStream_t s);
+// after y = M' p (work vector 4) of every plan: q = sign P y, p . q, x, r and r . r (scal 2)
+void batch_matvec_update(const BatchTable &t, cudaStream_t s);
+// after t2 = S~^-1 r (work vector 6): z = P t2 (or the low-rank form)
+void batch_zproj(const BatchTable &t, cudaStream_t s);
+// rz_new = r . z, p = z + (rz_new / rz) p, rz = rz_new
+void batch_pupdate(const BatchTable &t, cudaStream_t s);
+// out[k] = scal_k[off] (device)
+void batch_gather(const BatchTable &t, int off, double *out_dev, cudaStream_t s);
+
 // pooled CUDA events of the calling thread
 cudaEvent_t ev_get();
 void ev_put(cudaEvent_t e);

@@ -1,6 +1,10 @@
-// sort_scan.cu -- device exclusive scan and stable LSD radix sort of (key, value) pairs.
-// Used by the setup phase (Morton sort, random enumeration, neighbour grid).
+// sort_scan.cu -- device exclusive scan and stable LSD radix sort of (key, value) pairs,
+// used by the setup phase (Morton sort, random enumeration, neighbour grid), and the
+// library's per-device stream-ordered memory pool with the allocation context that
+// plans and call temporaries draw on.
+#include <functional>
 #include <mutex>
+#include <set>
 
 #include "phs_internal.cuh"
 
@@ -25,6 +29,70 @@ cudaMemPool_t scratch_pool() {
         pools[dev] = pool;
     }
     return pools[dev];
+}
+
+AllocCtx &alloc_ctx() {
+    static thread_local AllocCtx ctx;
+    return ctx;
+}
+
+// a non-blocking stream per device for releases made outside any allocation scope
+static cudaStream_t free_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    PHS_CUDA(cudaGetDevice(&dev));
+    PHS_REQUIRE(dev >= 0 && dev < 64, PHS_ERR_CUDA, "device ordinal out of range for the release stream");
+    std::lock_guard<std::mutex> g(mu);
+    if (!streams[dev]) PHS_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    return streams[dev];
+}
+
+void once_per_device(int id, const std::function<void()> &fn) {
+    static std::mutex mu;
+    static std::set<std::pair<int, int>> done;
+    int dev = 0;
+    PHS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    if (done.count({dev, id})) return;
+    fn();
+    done.insert({dev, id});
+}
+
+void dbuf_alloc(void **p, size_t bytes, bool *pooled, int64_t **acct) {
+    const AllocCtx &c = alloc_ctx();
+    *pooled = false;
+    *acct = nullptr;
+    if (c.on) {
+        PHS_CUDA(cudaMallocFromPoolAsync(p, bytes, scratch_pool(), c.s));
+        *pooled = true;
+        if (c.bytes) {
+            *c.bytes += (int64_t)bytes;
+            *acct = c.bytes;
+        }
+    } else {
+        PHS_CUDA(cudaMalloc(p, bytes));
+    }
+}
+
+void dbuf_free(void *p, size_t bytes, bool pooled, int64_t *acct) {
+    // release paths run in destructors: errors are not thrown from here
+    if (pooled) {
+        const AllocCtx &c = alloc_ctx();
+        cudaStream_t st = nullptr;
+        if (c.on) st = c.s;
+        else {
+            try {
+                st = free_stream();
+            } catch (...) {
+                st = nullptr;
+            }
+        }
+        cudaFreeAsync(p, st);
+    } else {
+        cudaFree(p);
+    }
+    if (acct) *acct -= (int64_t)bytes;
 }
 
 namespace {

@@ -831,7 +831,7 @@ int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const i
     PHS_REQUIRE(nu == 0.5 || nu == 1.0 || nu == 1.5 || nu == 2.0 || nu == 2.5, PHS_ERR_INVALID_ARG,
                 "nu must be 0.5, 1, 1.5, 2 or 2.5");
     PHS_REQUIRE(alpha > 0 && std::isfinite(alpha), PHS_ERR_INVALID_ARG, "alpha must be positive");
-    upload_bessel_tables();
+    once_per_device(3, upload_bessel_tables);
     const int ld = (m + 1) | 1;  // odd row stride: rows of consecutive lanes fall in different banks
     const size_t per = (size_t)((m + 1) * ld + 3 * (m + 1)) * sizeof(double);
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));

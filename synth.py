@@ -16,6 +16,11 @@ Workloads (points in [0,1]^2):
                      f = exp(-8((x-.3)^2+(y-.6)^2)) + sin(10xy), 10,000 targets (k = 2).
 The paper's own experiments use Sobol/uniform points and public data that are not
 available here; these sets stand in for them with the same shapes and mixes.
+
+Streams of independent requests (``serving_requests``: n log-uniform in [1,000, 500,000],
+k in {1, 2, 3}, uniform or clustered points, bump-sum fields; ``batch_jobs``: k in {4, 5},
+n log-uniform in [2,000, 200,000], the Franke function of Sec. 3.3) and Poisson arrival
+times (``poisson_arrivals``) feed the serving and batched forms.
 """
 from __future__ import annotations
 
@@ -107,3 +112,55 @@ def workload(name: str, n: int | None = None, n_targets: int | None = None):
     targets = uniform(nt, trng)
     return {"points": np.ascontiguousarray(pts), "f": np.ascontiguousarray(f), "targets": targets,
             "k": k, "seed": seed, "name": name}
+
+
+def franke(p: np.ndarray) -> np.ndarray:
+    """The Franke function as Sec. 3.3 states it: sum_j w_j exp(-(9x - c_j)' L_j (9x - c_j))
+    with w = (0.75, 0.75, 0.5, -0.2), c = (2,2), (-1,-1), (7,3), (4,7), and diagonal
+    L_1 = L_3 = I/4, L_2 = diag(1/49, 1/10), L_4 = I."""
+    x, y = 9 * p[:, 0], 9 * p[:, 1]
+    return (0.75 * np.exp(-((x - 2) ** 2 + (y - 2) ** 2) / 4) + 0.75 * np.exp(-(x + 1) ** 2 / 49 - (y + 1) ** 2 / 10)
+            + 0.5 * np.exp(-((x - 7) ** 2 + (y - 3) ** 2) / 4) - 0.2 * np.exp(-(x - 4) ** 2 - (y - 7) ** 2))
+
+
+def _geometry(n: int, clustered: bool, rng) -> np.ndarray:
+    if clustered:
+        return gaussian_mixture(n, 10, 0.02, 0.1, 0.9, rng)
+    return uniform(n, rng)
+
+
+def serving_requests(count: int, seed: int = 1004, n_lo: int = 1000, n_hi: int = 500_000, n_targets: int = 100):
+    """Independent interpolation requests: n log-uniform in [n_lo, n_hi], k uniform in
+    {1, 2, 3} (minimal polynomial block), uniform or clustered points (even odds), a
+    bump-sum field with a linear trend, n_targets uniform targets.  Returns a list of
+    dicts(points, f, targets, k)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        k = int(rng.integers(1, 4))
+        pts = _geometry(n, bool(rng.integers(0, 2)), rng)
+        f = bump_field(rng)(pts)
+        out.append({"points": np.ascontiguousarray(pts), "f": np.ascontiguousarray(f),
+                    "targets": uniform(n_targets, rng), "k": k})
+    return out
+
+
+def batch_jobs(count: int = 64, seed: int = 1003, n_lo: int = 2000, n_hi: int = 200_000, n_targets: int = 100):
+    """Independent higher-order jobs: k in {4, 5} (quadratic block), n log-uniform in
+    [n_lo, n_hi], uniform or clustered geometry per job, the Franke function."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        k = int(rng.integers(4, 6))
+        pts = _geometry(n, bool(rng.integers(0, 2)), rng)
+        out.append({"points": np.ascontiguousarray(pts), "f": franke(pts), "targets": uniform(n_targets, rng),
+                    "k": k})
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 1005) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate (requests per second)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, count))

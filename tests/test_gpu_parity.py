@@ -708,18 +708,21 @@ def test_domain_scale_and_alpha_act_through_their_product(phs):
     """Scaling the domain by 2 and alpha by 1/2 leaves the Vecchia factor bit-identical
     (the covariance sees alpha |x_i - x_j| and both factors are powers of two) and the
     PCG iteration count unchanged (the projected operator only scales, Eq. 2.1): the
-    reading that lets the tuner search alpha alone."""
-    w_ = synth.workload("tps_1m", n=20000)
+    reading that lets the tuner search alpha alone.  The two fits are the same solve up
+    to the FMM's rounding, so their interpolants agree to the solve's tolerance (w itself,
+    on an operator with condition number ~1e10, only to ~1e-8 x that)."""
+    w_ = synth.workload("tps_1m", n=20000, n_targets=300)
     res = []
     for h, a in ((0.25, 0.35), (0.5, 0.175)):
         plan = phs.Plan(_t(w_["points"]), 2, vecchia_m=30, opts=phs.options(2, domain_halfwidth=h, alpha=a))
         d, o = plan.vecchia_factor()
         w, beta, info = plan.fit(_t(w_["f"]))
-        res.append((d, o, info["iters"], w.cpu().numpy()))
+        pred = plan.eval(w, beta, _t(w_["targets"])).cpu().numpy()
+        res.append((d, o, info["iters"], pred))
         plan.close()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert res[0][2] == res[1][2]
-    assert np.linalg.norm(res[0][3] - res[1][3]) <= 1e-9 * np.linalg.norm(res[0][3])
+    assert np.max(np.abs(res[0][3] - res[1][3])) <= 1e-8 * np.max(np.abs(res[0][3]))
 
 
 def test_tune_alpha(phs):

@@ -1,6 +1,7 @@
 """CPU checks that the seeded generators produce the workloads the benchmark and the
 full-size parity tests are described with (sizes, mixes, bounds, fields, determinism)."""
 import numpy as np
+import pytest
 
 import synth
 
@@ -36,3 +37,23 @@ def test_small_workloads_recipe():
     assert c["points"].shape == (20_000, 2) and c["k"] == 3
     assert c["points"].min() >= 0.0 and c["points"].max() <= 1.0
     assert synth.workload("cubic_mix")["points"].shape == (100_000, 2)
+
+
+def test_franke_as_printed():
+    """Sec. 3.3's form of the Franke function at hand-checked points: at 9x = c_1 = (2, 2)
+    the first term is 0.75 and the others follow from their metrics."""
+    import math
+    p = np.array([[2 / 9, 2 / 9]])
+    want = (0.75 + 0.75 * math.exp(-(3 ** 2) / 49 - (3 ** 2) / 10) + 0.5 * math.exp(-(25 + 1) / 4)
+            - 0.2 * math.exp(-4 - 25))
+    assert synth.franke(p)[0] == pytest.approx(want, rel=1e-15)
+
+
+def test_request_streams():
+    reqs = synth.serving_requests(40, seed=3)
+    assert all(1000 <= len(r["f"]) <= 500_000 and r["k"] in (1, 2, 3) for r in reqs)
+    assert {r["k"] for r in reqs} == {1, 2, 3}
+    jobs = synth.batch_jobs(20, seed=4, n_hi=20_000)
+    assert all(j["k"] in (4, 5) and 2000 <= len(j["f"]) <= 20_000 for j in jobs)
+    t = synth.poisson_arrivals(2000, 10.0, seed=1)
+    assert np.all(np.diff(t) > 0) and abs(t[-1] / 2000 - 0.1) < 0.01
