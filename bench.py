@@ -294,7 +294,7 @@ def main():
     if args.case == "cubic":
         wc = synth.workload("cubic_mix")
         pc, fc, tc = (torch.tensor(wc[key], device=dev) for key in ("points", "f", "targets"))
-        copts = phs.options(3, tol=1e-8, maxiter=400)
+        copts = phs.options(3, tol=1e-8, maxiter=400, precision=args.precision)
         res = []
         for i in range(args.warmup + args.steps):
             torch.cuda.synchronize(dev)
@@ -312,7 +312,7 @@ def main():
             t = float(np.mean([r[0] for r in res]))
             info = res[-1][1]
             print(json.dumps({"case": "cubic", "workload": "cubic_mix", "n": len(wc["f"]), "k": 3, "vecchia_m": 20,
-                              "value_s": t, "steps": args.steps, "iters": info["iters"],
+                              "precision": args.precision, "value_s": t, "steps": args.steps, "iters": info["iters"],
                               "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"],
                               "ms_fit": info["ms_fit"], "ms_matvec_avg": info["ms_matvec_avg"]}))
         return

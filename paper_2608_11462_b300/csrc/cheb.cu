@@ -8,10 +8,19 @@
 //   P2M         W[m] = sum_j q_j S(xb_m1, s_j1) S(xb_m2, s_j2),  s_j = (x_j - c)/h
 //   M2M / L2L   child nodes sit at +-1/2 + xb/2 in the parent frame
 //   M2L         L_t[m] += h * sum_n |xb_m - xb_n - 2 o| W_s[n]  (o = source offset in
-//               box widths; |x - y| is homogeneous, so one matrix per offset class
-//               serves every level after scaling by the half-width h)
+//               box widths; |x - y| is homogeneous, so one matrix K_o per offset class
+//               serves every level after scaling by the half-width h), applied in
+//               compressed form: the 40 matrices share a target basis U (left singular
+//               vectors of [K_o ...]) and a source basis V (right singular vectors of
+//               [K_o; ...]), truncated where the singular values fall below lr_eps times
+//               the largest, so K_o ~ U C_o V' and an interaction costs rt x rs instead
+//               of (q^2)^2: W~ = V' W once per source box, L~ += C_o (S_o W~) per
+//               V-list entry, L = U L~ once per target box
 //   L2P         pot(x) = sum_m S(xb_m1, s1) S(xb_m2, s2) L[m]
+#include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "geom.cuh"
@@ -171,45 +180,6 @@ __global__ void cheb_m2m(TreeView tv, int b0, int nd, int q, const double *A, co
         for (int l = 0; l < nd; ++l) W[((size_t)b * nd + l) * qq + m] = acc[l];
 }
 
-// M2L over V lists: L_t[l][m] = w^{2m'} h sum_v sum_n K[cls][n][m] (S[cls] W_src)[l][n]
-__global__ void cheb_m2l(TreeView tv, int b0, const int *v_off, const int *v_src, const unsigned char *v_cls, int nd,
-                         int q, int power, const double *K, const double *mix, const double *W, double *L) {
-    extern __shared__ double wsm[];  // [nd][q*q] source weights, then [nd][q*q] mixed
-    const int b = b0 + blockIdx.x;
-    const int qq = q * q;
-    double *wmx = wsm + nd * qq;
-    const int m = threadIdx.x;
-    double acc[10];
-    for (int d = 0; d < nd; ++d) acc[d] = 0.0;
-    for (int v = v_off[b]; v < v_off[b + 1]; ++v) {
-        const int src = v_src[v];
-        for (int i = threadIdx.x; i < nd * qq; i += blockDim.x) wsm[i] = W[(size_t)src * nd * qq + i];
-        __syncthreads();
-        const double *S = mix + (size_t)v_cls[v] * nd * nd;
-        for (int i = threadIdx.x; i < nd * qq; i += blockDim.x) {
-            const int l = i / qq, n = i - l * qq;
-            double s = 0.0;
-            for (int bb = 0; bb < nd; ++bb) s += S[l * nd + bb] * wsm[bb * qq + n];
-            wmx[i] = s;
-        }
-        __syncthreads();
-        if (m < qq) {
-            const double *Kc = K + (size_t)v_cls[v] * qq * qq;
-            for (int n = 0; n < qq; ++n) {
-                const double kv = Kc[(size_t)n * qq + m];
-                for (int d = 0; d < nd; ++d) acc[d] = fma(kv, wmx[d * qq + n], acc[d]);
-            }
-        }
-        __syncthreads();
-    }
-    if (m < qq) {
-        const double w = box_width(tv.R, tv.level[b]);
-        double sc = 0.5 * w;
-        for (int i = 0; i < power; ++i) sc *= w;
-        for (int d = 0; d < nd; ++d) L[((size_t)b * nd + d) * qq + m] = sc * acc[d];
-    }
-}
-
 // L2L for one level: interpolate each parent factor's potential to the child nodes,
 // then mix into the child's factors through Ru (mix slot 53 + quadrant)
 __global__ void cheb_l2l(TreeView tv, int b0, int nd, int q, const double *A, const double *mix, double *L) {
@@ -286,10 +256,204 @@ __global__ void cheb_l2p(TreeView tv, const int *leaf_box, const double2 *xs, in
     }
 }
 
+// W~[b][d][j] = sum_n V[n][j] W[b][d][n]  (boxes b0.., all densities)
+__global__ void cheb_compress(int b0, int nd, int qq, int rs, const double *V, const double *W, double *Wc) {
+    extern __shared__ double wsh[];  // [nd][qq]
+    const int b = b0 + blockIdx.x;
+    for (int i = threadIdx.x; i < nd * qq; i += blockDim.x) wsh[i] = W[(size_t)b * nd * qq + i];
+    __syncthreads();
+    for (int o = threadIdx.x; o < nd * rs; o += blockDim.x) {
+        const int d = o / rs, jj = o - d * rs;
+        double acc = 0.0;
+        for (int n = 0; n < qq; ++n) acc = fma(V[(size_t)n * rs + jj], wsh[d * qq + n], acc);
+        Wc[((size_t)b * nd + d) * rs + jj] = acc;
+    }
+}
+
+// L~_t[d][i] = sum over the V list of sum_j C[cls][i][j] (S[cls] W~_src)[d][j]
+__global__ void cheb_m2l_lr(int b0, const int *v_off, const int *v_src, const unsigned char *v_cls, int nd, int rt,
+                            int rs, const double *C, const double *mix, const double *Wc, double *Lc) {
+    extern __shared__ double csm[];  // [nd][rs] source, then [nd][rs] mixed
+    const int b = b0 + blockIdx.x;
+    double *wmx = csm + nd * rs;
+    double acc[10];
+    for (int d = 0; d < nd; ++d) acc[d] = 0.0;
+    const int i = threadIdx.x;
+    for (int v = v_off[b]; v < v_off[b + 1]; ++v) {
+        const int src = v_src[v];
+        for (int o = threadIdx.x; o < nd * rs; o += blockDim.x) csm[o] = Wc[(size_t)src * nd * rs + o];
+        __syncthreads();
+        const double *S = mix + (size_t)v_cls[v] * nd * nd;
+        for (int o = threadIdx.x; o < nd * rs; o += blockDim.x) {
+            const int l = o / rs, jj = o - l * rs;
+            double sacc = 0.0;
+            for (int bb = 0; bb < nd; ++bb) sacc = fma(S[l * nd + bb], csm[bb * rs + jj], sacc);
+            wmx[o] = sacc;
+        }
+        __syncthreads();
+        if (i < rt) {
+            const double *Cc = C + ((size_t)v_cls[v] * rt + i) * rs;
+            for (int jj = 0; jj < rs; ++jj) {
+                const double cv = Cc[jj];
+                for (int d = 0; d < nd; ++d) acc[d] = fma(cv, wmx[d * rs + jj], acc[d]);
+            }
+        }
+        __syncthreads();
+    }
+    if (i < rt)
+        for (int d = 0; d < nd; ++d) Lc[((size_t)b * nd + d) * rt + i] = acc[d];
+}
+
+// L[b][d][m] = sc_b sum_i U[m][i] L~[b][d][i], sc_b = h w^power (the homogeneity scaling)
+__global__ void cheb_expand(TreeView tv, int b0, int nd, int qq, int rt, int power, const double *U, const double *Lc,
+                            double *L) {
+    extern __shared__ double lsh[];  // [nd][rt]
+    const int b = b0 + blockIdx.x;
+    for (int o = threadIdx.x; o < nd * rt; o += blockDim.x) lsh[o] = Lc[(size_t)b * nd * rt + o];
+    __syncthreads();
+    const double w = box_width(tv.R, tv.level[b]);
+    double sc = 0.5 * w;
+    for (int k = 0; k < power; ++k) sc *= w;
+    for (int o = threadIdx.x; o < nd * qq; o += blockDim.x) {
+        const int d = o / qq, m = o - d * qq;
+        double acc = 0.0;
+        for (int k = 0; k < rt; ++k) acc = fma(U[(size_t)m * rt + k], lsh[d * rt + k], acc);
+        L[((size_t)b * nd + d) * qq + m] = sc * acc;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-void cheb_setup(Fmm &f, int q, cudaStream_t s) {
+// Eigen-decomposition of a symmetric n x n matrix A (row-major, overwritten) by cyclic
+// Jacobi rotations: on return w holds the eigenvalues in decreasing order and the
+// columns of V (row-major, V[i][k]) the matching orthonormal eigenvectors.
+static void sym_eig(int n, std::vector<double> &A, std::vector<double> &V, std::vector<double> &w) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < n; ++i) {
+            diag += A[(size_t)i * n + i] * A[(size_t)i * n + i];
+            for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        }
+        if (off <= 1e-32 * diag) break;
+        for (int p = 0; p < n; ++p)
+            for (int r = p + 1; r < n; ++r) {
+                const double apr = A[(size_t)p * n + r];
+                if (apr == 0.0) continue;
+                const double app = A[(size_t)p * n + p], arr = A[(size_t)r * n + r];
+                const double theta = (arr - app) / (2.0 * apr);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {  // columns p, r
+                    const double akp = A[(size_t)k * n + p], akr = A[(size_t)k * n + r];
+                    A[(size_t)k * n + p] = c * akp - sn * akr;
+                    A[(size_t)k * n + r] = sn * akp + c * akr;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, r
+                    const double apk = A[(size_t)p * n + k], ark = A[(size_t)r * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * ark;
+                    A[(size_t)r * n + k] = sn * apk + c * ark;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[(size_t)k * n + p], vkr = V[(size_t)k * n + r];
+                    V[(size_t)k * n + p] = c * vkp - sn * vkr;
+                    V[(size_t)k * n + r] = sn * vkp + c * vkr;
+                }
+            }
+    }
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return A[(size_t)a * n + a] > A[(size_t)b * n + b]; });
+    std::vector<double> Vs((size_t)n * n);
+    w.resize(n);
+    for (int c = 0; c < n; ++c) {
+        w[c] = A[(size_t)idx[c] * n + idx[c]];
+        for (int k = 0; k < n; ++k) Vs[(size_t)k * n + c] = V[(size_t)k * n + idx[c]];
+    }
+    V.swap(Vs);
+}
+
+struct ChebLowRank {
+    int rt = 0, rs = 0;
+    std::vector<double> buf;  // U [qq][rt] | V [qq][rs] | C [49][rt][rs]
+};
+
+// Shared bases of the 40 M2L matrices A_o[m][n] = K[o][n][m] (target m, source n): U from
+// sum_o A_o A_o', V from sum_o A_o' A_o (their eigenvalues are the squared singular
+// values of the matrices stacked side by side / on top of each other), each truncated
+// where sqrt(eigenvalue) < eps * the largest; C_o = U' A_o V.  Built once per (q, eps).
+static const ChebLowRank &cheb_lowrank(int q, double eps, const std::vector<double> &K) {
+    static std::mutex mu;
+    static std::map<std::pair<int, double>, ChebLowRank> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find({q, eps});
+    if (it != cache.end()) return it->second;
+    const int qq = q * q;
+    std::vector<int> cls;
+    for (int c = 0; c < 49; ++c) {
+        const int dx = c / 7 - 3, dy = c % 7 - 3;
+        if (std::abs(dx) > 1 || std::abs(dy) > 1) cls.push_back(c);
+    }
+    std::vector<double> Gt((size_t)qq * qq, 0.0), Gs((size_t)qq * qq, 0.0);
+    for (int c : cls) {
+        const double *Kc = K.data() + (size_t)c * qq * qq;  // Kc[n * qq + m] = A_o[m][n]
+        for (int m = 0; m < qq; ++m)
+            for (int m2 = m; m2 < qq; ++m2) {
+                double st = 0.0, ss = 0.0;
+                for (int n = 0; n < qq; ++n) {
+                    st += Kc[(size_t)n * qq + m] * Kc[(size_t)n * qq + m2];
+                    ss += Kc[(size_t)m * qq + n] * Kc[(size_t)m2 * qq + n];
+                }
+                Gt[(size_t)m * qq + m2] += st;
+                Gs[(size_t)m * qq + m2] += ss;
+            }
+    }
+    for (int m = 0; m < qq; ++m)
+        for (int m2 = 0; m2 < m; ++m2) {
+            Gt[(size_t)m * qq + m2] = Gt[(size_t)m2 * qq + m];
+            Gs[(size_t)m * qq + m2] = Gs[(size_t)m2 * qq + m];
+        }
+    std::vector<double> Ut, wt, Vs, ws;
+    sym_eig(qq, Gt, Ut, wt);
+    sym_eig(qq, Gs, Vs, ws);
+    auto rank_of = [&](const std::vector<double> &w) {
+        const double top = std::sqrt(std::max(w[0], 0.0));
+        int r = 0;
+        while (r < qq && std::sqrt(std::max(w[r], 0.0)) > eps * top) ++r;
+        return std::max(r, 1);
+    };
+    ChebLowRank lr;
+    lr.rt = rank_of(wt);
+    lr.rs = rank_of(ws);
+    const int rt = lr.rt, rs = lr.rs;
+    lr.buf.assign((size_t)qq * rt + (size_t)qq * rs + (size_t)49 * rt * rs, 0.0);
+    double *U = lr.buf.data(), *V = U + (size_t)qq * rt, *C = V + (size_t)qq * rs;
+    for (int m = 0; m < qq; ++m)
+        for (int i = 0; i < rt; ++i) U[(size_t)m * rt + i] = Ut[(size_t)m * qq + i];
+    for (int n = 0; n < qq; ++n)
+        for (int j = 0; j < rs; ++j) V[(size_t)n * rs + j] = Vs[(size_t)n * qq + j];
+    std::vector<double> AV((size_t)qq * rs);
+    for (int c : cls) {
+        const double *Kc = K.data() + (size_t)c * qq * qq;
+        for (int m = 0; m < qq; ++m)  // AV = A_o V
+            for (int j = 0; j < rs; ++j) {
+                double a = 0.0;
+                for (int n = 0; n < qq; ++n) a += Kc[(size_t)n * qq + m] * V[(size_t)n * rs + j];
+                AV[(size_t)m * rs + j] = a;
+            }
+        for (int i = 0; i < rt; ++i)  // C_o = U' AV
+            for (int j = 0; j < rs; ++j) {
+                double a = 0.0;
+                for (int m = 0; m < qq; ++m) a += U[(size_t)m * rt + i] * AV[(size_t)m * rs + j];
+                C[((size_t)c * rt + i) * rs + j] = a;
+            }
+    }
+    return cache.emplace(std::make_pair(q, eps), std::move(lr)).first->second;
+}
+
+void cheb_setup(Fmm &f, int q, double lr_eps, cudaStream_t s) {
     PHS_REQUIRE(q >= 3 && q <= kChebMaxQ, PHS_ERR_INVALID_ARG, "Chebyshev order must be in 3..16");
     f.cheb_q = q;
     const int qq = q * q;
@@ -330,6 +494,14 @@ void cheb_setup(Fmm &f, int q, cudaStream_t s) {
         }
     f.cheb64.alloc(buf.size());
     PHS_CUDA(cudaMemcpyAsync(f.cheb64.get(), buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    const std::vector<double> K(buf.begin() + 3 * qq, buf.end());
+    const ChebLowRank &lr = cheb_lowrank(q, lr_eps, K);
+    f.cheb_rt = lr.rt;
+    f.cheb_rs = lr.rs;
+    PHS_REQUIRE(lr.rt <= 256 && lr.rs <= 256, PHS_ERR_INVALID_ARG, "compressed M2L rank above 256");
+    f.cheb_lr.alloc(lr.buf.size());
+    PHS_CUDA(cudaMemcpyAsync(f.cheb_lr.get(), lr.buf.data(), lr.buf.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             s));
     PHS_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -358,12 +530,25 @@ void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_
     PHS_CUDA(cudaMemsetAsync(f.cl64.get(), 0, sz * sizeof(double), s));
     if (t.depth >= 2) {
         const int b0 = t.lvl_off[2], nb = t.nbox - b0;
-        if (nb > 0)
-            cheb_m2l<<<nb, CHEB_T, 2 * (size_t)nd * qq * sizeof(double), s>>>(
-                tv, b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), nd, q, f.power, K, f.mix64.get(), f.cw64.get(),
-                f.cl64.get());
-        PHS_LAUNCH_CHECK();
+        const int rt = f.cheb_rt, rs = f.cheb_rs;
+        if (f.cwc64.n != (size_t)t.nbox * nd * rs) f.cwc64.alloc((size_t)t.nbox * nd * rs);
+        if (f.clc64.n != (size_t)t.nbox * nd * rt) f.clc64.alloc((size_t)t.nbox * nd * rt);
+        const double *U = f.cheb_lr.get(), *V = U + (size_t)qq * rt, *C = V + (size_t)qq * rs;
+        if (nb > 0) {
+            cheb_compress<<<nb, CHEB_T, (size_t)nd * qq * sizeof(double), s>>>(b0, nd, qq, rs, V, f.cw64.get(),
+                                                                               f.cwc64.get());
+            PHS_LAUNCH_CHECK();
+            const int thr = std::max(32, (rt + 31) / 32 * 32);
+            cheb_m2l_lr<<<nb, thr, 2 * (size_t)nd * rs * sizeof(double), s>>>(
+                b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), nd, rt, rs, C, f.mix64.get(), f.cwc64.get(),
+                f.clc64.get());
+            PHS_LAUNCH_CHECK();
+            cheb_expand<<<nb, CHEB_T, (size_t)nd * rt * sizeof(double), s>>>(tv, b0, nd, qq, rt, f.power, U,
+                                                                             f.clc64.get(), f.cl64.get());
+            PHS_LAUNCH_CHECK();
+        }
     }
+    (void)K;
     if (tm) tm->end(T_M2L, s);
     if (tm) tm->begin(s);
     for (int l = 3; l <= t.depth; ++l) {

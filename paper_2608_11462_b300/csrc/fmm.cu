@@ -1505,7 +1505,9 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     PHS_CUDA(cudaStreamSynchronize(s));
     once_per_device(1, upload_log_tables);
     once_per_device(2, upload_ff_tables);
-    if (!f.log_core) cheb_setup(f, cheb_q, s);
+    // the compressed M2L truncates at a fifth of the accuracy the order was chosen for
+    // (q = the smallest order with 5.83^-(q-1) <= eps): rank 81 of 256 at q = 16
+    if (!f.log_core) cheb_setup(f, cheb_q, 0.2 * std::pow(5.83, -(double)(cheb_q - 1)), s);
     m2l_tc_count(f, t, s);
 }
 

@@ -240,7 +240,10 @@ struct Fmm {
     DBuf<int> lvl_off_dev;
     // Chebyshev (distance kernel) data
     int cheb_q = 0;                      // nodes per dimension
+    int cheb_rt = 0, cheb_rs = 0;        // ranks of the compressed M2L (target, source bases)
     DBuf<double> cheb64;                 // operators
+    DBuf<double> cheb_lr;                // compressed M2L: U [q*q][rt] | V [q*q][rs] | C [49][rt][rs]
+    DBuf<double> cwc64, clc64;           // compressed weights [box][nd][rs], potentials [box][nd][rt]
     DBuf<float> cheb32;
     DBuf<double> cw64, cl64;             // weights/potentials at nodes [box][nd][q*q]
     DBuf<float> cw32, cl32;
@@ -276,7 +279,8 @@ int m2l_tc_mmas_per_step();
 // throws PHS_ERR_TIMEOUT if a tensor-core wait expired since the last check (synchronises s)
 void m2l_tc_check(Fmm &f, cudaStream_t s);
 // distance-kernel far field (cheb.cu)
-void cheb_setup(Fmm &f, int q, cudaStream_t s);
+// q Chebyshev nodes per axis; the M2L operators compressed to relative accuracy lr_eps
+void cheb_setup(Fmm &f, int q, double lr_eps, cudaStream_t s);
 void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, cudaStream_t s,
                     struct Timers *tm);
 void cheb_l2p_apply(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s);
