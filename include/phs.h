@@ -78,7 +78,11 @@ typedef struct {
     double tol;             /* stop when ||r_k|| <= max(tol*||Q_perp' f||, atol); default 1e-8 */
     double atol;            /* default 0 */
     int maxiter;            /* PCG iterations (precision 0) or total inner iterations; default 200 */
-    int leaf_cap;           /* quadtree leaf capacity s; default 64 */
+    int leaf_cap;           /* quadtree leaf capacity s (the near-field tile: a leaf's points
+                               are the rows of its direct-sum tiles); default 64.  <= 0: the
+                               capacity of {32, 48, 64, 96, 128} whose FMM matvec is fastest,
+                               timed once per process for each (device, k, floor(log2 n),
+                               precision, m2l_tensor) on synthetic uniform points */
     int ordering;           /* Vecchia enumeration: 0 random (Sec. 3), 1 exact maxmin (single
                                block, O(n^2): small n), 2 hierarchical maximin (phs_hmaxmin_order),
                                3 dyadic approximate maximin (phs_amaxmin_order; the default: on
@@ -357,8 +361,9 @@ phs_status phs_vecchia_factor(const double *pts_dev, int64_t n, const int64_t *o
  * job's FMM matvec and Vecchia apply run on its own stream, and the vector operations of
  * all jobs run as shared launches, one device-to-host copy of the residuals per tick.
  * A job computes exactly what phs_fit followed by phs_eval computes for it (same steps,
- * same arithmetic), alone or in any mix.  FP64 solves (precision 0).  No counterpart in
- * the paper: the serving form of its solve. */
+ * same arithmetic), alone or in any mix; precision 1-4 jobs run phs_fit's FP64
+ * refinement around their inner solves (odd k: precision 0 or 4).  No counterpart in the
+ * paper: the serving and batched forms of its solve. */
 typedef struct phs_server *phs_server_t;
 typedef struct {
     int64_t memory_budget;  /* device bytes the admitted jobs may reserve; <= 0: half the free memory */
@@ -370,7 +375,7 @@ typedef struct {
 phs_status phs_server_create(const phs_server_config *cfg, phs_server_t *out);
 /* Queue one request: points (n x 2), values (n) and targets (m x 2) are HOST arrays,
  * copied before the call returns; k, poly_degree, fmm_order, vecchia_m and opt as for
- * phs_plan_create (opt->precision must be 0; NULL: phs_options_default(k)).
+ * phs_plan_create (NULL: phs_options_default(k)).
  * *job_id receives the request's id.  Thread-safe; does not wait for the GPU. */
 phs_status phs_server_submit(phs_server_t server, const double *pts_host, const double *f_host, int64_t n,
                              const double *tgt_host, int64_t m, int k, int poly_degree, int fmm_order,

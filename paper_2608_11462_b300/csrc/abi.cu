@@ -5,8 +5,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 
 #include "plan.cuh"
 
@@ -556,6 +558,20 @@ __global__ void bk_p_from_z(BTable<N> t) {
         j.W[2 * j.n + i] = j.W[j.n + i];
 }
 
+// uniform points on [0,1)^2 for the leaf-capacity tuner: coordinates from SplitMix64 of
+// (seed, 2i) and (seed, 2i + 1), 53 bits each
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__global__ void tune_points(int64_t n, uint64_t seed, double *pts) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * n) return;
+    const uint64_t z = mix64(seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull);
+    pts[i] = (double)(z >> 11) * 0x1.0p-53;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- plan helpers
@@ -871,6 +887,37 @@ FitStart fit_begin(phs_plan *pl, const double *f_dev, cudaStream_t s) {
     return st;
 }
 
+// FP64 iterative refinement around inner solves with the reduced-precision operator
+// (precision 1-4).  Begin: x = 0 (work vector 9), d = rhs (work vector 11, the first
+// correction's right-hand side).
+void fit_refine_begin(phs_plan *pl, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    zero_k<<<blocks_for(n, 256), 256, 0, s>>>(W(pl, 9), n);
+    PHS_LAUNCH_CHECK();
+    PHS_CUDA(cudaMemcpyAsync(W(pl, 11), W(pl, 8), n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+// After an inner solve left its correction dx in work vector 8: x += dx, then the true
+// residual in FP64, d = sign P (f - M' x) (work vector 11); returns ||d|| (synchronises).
+double fit_refine_step(phs_plan *pl, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    double *x = W(pl, 9), *y = W(pl, 10), *d = W(pl, 11);
+    axpy_k<<<blocks_for(n, 256), 256, 0, s>>>(x, W(pl, 8), n, 1.0);
+    PHS_LAUNCH_CHECK();
+    matvec_norm(pl, x, y, 0, s);
+    sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, W(pl, 7), y, n);
+    PHS_LAUNCH_CHECK();
+    project(pl, y, (double)pl->sign, d, d, pl->scal.get() + 7, s);
+    return std::sqrt(read_scalar(pl, pl->scal.get() + 7, s));
+}
+// Modes 1-3 solve each correction to inner_tol of the current residual; mode 4 (float-
+// float near field) is accurate enough that each inner solve aims at the final tolerance.
+double refine_inner_tol(const phs_options &o, double res, double stop) {
+    return o.precision == 4 ? 0.5 * stop : std::max(o.inner_tol * res, 0.5 * stop);
+}
+int refine_inner_maxiter(const phs_options &o, int iters_done) {
+    return std::min(o.maxiter - iters_done, o.precision == 4 ? o.maxiter : 100);
+}
+
 // The end of a fit from x (work vector 9) and f (work vector 7): beta from
 // R beta = Q'(f - M' x) (Eq. 2.5), the true residual ||P (f - M' x)||^2 (returned), and
 // w = rho^k x in caller order; synchronises s.
@@ -906,6 +953,55 @@ static int min_degree(int k) { return k % 2 == 0 ? k / 2 : (k - 1) / 2; }
 static int cpd_sign(int k) {
     if (k % 2 == 1) return ((k + 1) / 2) % 2 ? -1 : 1;
     return (k / 2 + 1) % 2 ? -1 : 1;
+}
+
+// Leaf capacity chosen by measurement: for the (device, k, floor(log2 n), precision,
+// m2l_tensor) of a plan created with leaf_cap <= 0, time the FMM matvec on
+// min(max(n, 4096), 131072) synthetic uniform points at each capacity of kLeafCaps (one
+// warm-up and two timed applies, CUDA events) and keep the fastest; once per process.
+static const int kLeafCaps[] = {32, 48, 64, 96, 128};
+static int autotune_leaf_cap(int k, int64_t n, const phs_options &o, cudaStream_t s) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int>, int> cache;
+    int dev = 0;
+    PHS_CUDA(cudaGetDevice(&dev));
+    int bucket = 0;
+    while ((int64_t)1 << (bucket + 1) <= n) ++bucket;
+    const auto key = std::make_tuple(dev, k, bucket, o.precision, o.m2l_tensor);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const int64_t nt = std::min<int64_t>(std::max<int64_t>(n, 4096), 131072);
+    SBuf<double> pts(2 * nt, s), t(nt, s), y(nt, s);
+    tune_points<<<blocks_for(2 * nt, 256), 256, 0, s>>>(nt, 0x5eedull + (uint64_t)bucket, pts.get());
+    PHS_LAUNCH_CHECK();
+    tune_points<<<blocks_for(nt, 256), 256, 0, s>>>(nt / 2, 0xfeedull, t.get());
+    PHS_LAUNCH_CHECK();
+    cudaEvent_t e0 = ev_get(), e1 = ev_get();
+    int best = 64;
+    float best_ms = 1e30f;
+    for (int cap : kLeafCaps) {
+        phs_options ot = o;
+        ot.leaf_cap = cap;
+        phs_plan_t pl = nullptr;
+        if (phs_plan_create(pts.get(), nt, k, -1, 0, 1, &ot, (phs_stream_t)s, &pl) != PHS_OK) continue;
+        float ms = 0;
+        bool ok = phs_matvec(pl, t.get(), y.get(), o.precision == 4 ? 4 : 0, (phs_stream_t)s) == PHS_OK;
+        PHS_CUDA(cudaEventRecord(e0, s));
+        for (int r = 0; r < 2 && ok; ++r) ok = phs_matvec(pl, t.get(), y.get(), o.precision == 4 ? 4 : 0, (phs_stream_t)s) == PHS_OK;
+        PHS_CUDA(cudaEventRecord(e1, s));
+        PHS_CUDA(cudaEventSynchronize(e1));
+        PHS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        phs_plan_destroy(pl);
+        if (ok && ms < best_ms) {
+            best_ms = ms;
+            best = cap;
+        }
+    }
+    ev_put(e0);
+    ev_put(e1);
+    cache[key] = best;
+    return best;
 }
 
 extern "C" {
@@ -971,8 +1067,9 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         }
         pl->p = p;
         pl->sign = cpd_sign(k);
+        if (o.leaf_cap <= 0) pl->opt.leaf_cap = autotune_leaf_cap(k, n, o, s);
         pl->hscal = pinned_block();
-        build_points_and_tree(pts_dev, n, o.domain_halfwidth, o.leaf_cap, pl->ps, pl->tree, s);
+        build_points_and_tree(pts_dev, n, o.domain_halfwidth, pl->opt.leaf_cap, pl->ps, pl->tree, s);
         // Chebyshev order for the distance kernel: interpolation error ~ 5.83^-q at the
         // V-list separation (Bernstein ellipse of a unit gap), q in [6, 16]
         const double eps_q = fmm_order > 0 ? std::pow(0.55, fmm_order) : o.fmm_eps;
@@ -1050,8 +1147,7 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
     auto t0 = std::chrono::steady_clock::now();
     const int64_t n = pl->ps.n;
     const phs_options &o = pl->opt;
-    double *fs = W(pl, 7), *rhs = W(pl, 8), *x = W(pl, 9), *y = W(pl, 10), *d = W(pl, 11);
-    double *sc = pl->scal.get();
+    double *rhs = W(pl, 8), *x = W(pl, 9);
     const FitStart st = fit_begin(pl, f_dev, s);
     const double nrm0 = st.nrm0, stop = st.stop;
     MvTimes mvt;
@@ -1069,25 +1165,15 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
         // mode 4 (float-float near field) is accurate enough that its first inner solve
         // aims at the final tolerance, and refinement only mops up what the operator's
         // rounding leaves in the true residual.
-        zero_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n);
-        PHS_CUDA(cudaMemcpyAsync(d, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));  // residual
+        fit_refine_begin(pl, s);
         double res = nrm0;
         while (outer < o.max_refine && iters < o.maxiter) {
             double rri = 0;
-            double *dx = W(pl, 8);  // rhs no longer needed
-            const double itol = o.precision == 4 ? 0.5 * stop : std::max(o.inner_tol * res, 0.5 * stop);
-            int it = pcg(pl, d, dx, itol, std::min(o.maxiter - iters, o.precision == 4 ? o.maxiter : 100),
-                         o.precision, &rri, s, &mvt);
+            const double itol = refine_inner_tol(o, res, stop);
+            int it = pcg(pl, W(pl, 11), W(pl, 8), itol, refine_inner_maxiter(o, iters), o.precision, &rri, s, &mvt);
             iters += it;
             ++outer;
-            axpy_k<<<blocks_for(n, 256), 256, 0, s>>>(x, dx, n, 1.0);
-            PHS_LAUNCH_CHECK();
-            // true residual in FP64: d = sign * P (f - M' x)
-            matvec_norm(pl, x, y, 0, s);
-            sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, fs, y, n);
-            PHS_LAUNCH_CHECK();
-            project(pl, y, (double)pl->sign, d, d, sc + 7, s);
-            res = std::sqrt(read_scalar(pl, sc + 7, s));
+            res = fit_refine_step(pl, s);
             rr = res * res;
             if (res <= stop) { converged = true; break; }
             if (it == 0) break;

@@ -74,6 +74,12 @@ struct FitStart {
 };
 FitStart fit_begin(phs_plan *pl, const double *f_dev, cudaStream_t s);
 double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s);
+// refinement (precision 1-4): x = 0, d = rhs; one step x += dx, d = sign P(f - M' x) in
+// FP64, returning ||d||; the inner solves run PCG with rhs = work vector 11, x = 8
+void fit_refine_begin(phs_plan *pl, cudaStream_t s);
+double fit_refine_step(phs_plan *pl, cudaStream_t s);
+double refine_inner_tol(const phs_options &o, double res, double stop);
+int refine_inner_maxiter(const phs_options &o, int iters_done);
 
 // ---- PCG steps on a table of plans (abi.cu).  Each step runs RED_B x RED_T blocks per
 // plan with blockIdx.y selecting the plan, the same arithmetic as on a one-plan table,

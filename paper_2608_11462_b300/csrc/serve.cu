@@ -14,8 +14,9 @@
 // leave the tick (a worker computes beta, evaluates the targets and returns the
 // results), and new jobs join as slots and memory free up.  A job's arithmetic is the
 // same as phs_fit's (the same begin/end and the same table steps with a table of one),
-// so its result is identical whether it runs alone or in the mix.  The engine runs the
-// FP64 solve (precision 0).
+// so its result is identical whether it runs alone or in the mix.  Precision 1-4 jobs
+// run phs_fit's FP64 refinement around their inner solves (a worker takes each
+// refinement step between the inner solves' ticks).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -32,7 +33,7 @@
 namespace phs {
 namespace {
 
-enum JobState { J_PENDING, J_SETUP, J_ACTIVE, J_FINISH, J_DONE };
+enum JobState { J_PENDING, J_SETUP, J_ACTIVE, J_REFINE, J_FINISH, J_DONE };
 
 struct Job {
     int64_t id = 0;
@@ -52,8 +53,12 @@ struct Job {
     double *dbuf = nullptr;  // inputs and outputs on the device: pts 2n, f n, tgt 2m, w n, beta 16, pred m
     size_t dbytes = 0;
     FitStart st{};
-    double rr = 0;
-    int it = 0;
+    double rr = 0;            // r . r of the current (inner) solve
+    int it = 0;               // iterations of the current (inner) solve
+    int iters = 0, outer = 0; // refinement: inner iterations so far, refinement steps
+    double itol = 0;          // the current solve's stopping threshold
+    int imax = 0;             // and its iteration limit
+    double *rhs_p = nullptr, *x_p = nullptr;  // the current solve's right-hand side and iterate
     bool converged = false;
     phs_fit_info info{};
     double *pts_d() { return dbuf; }
@@ -70,6 +75,29 @@ struct Job {
 int64_t estimate_bytes(int64_t n, int64_t m, int vm) {
     return (64ll << 20) + n * (int64_t)(700 + 48 * vm) + 24 * m;
 }
+
+// Start the job's next PCG solve, as phs_fit does: the whole solve (precision 0: rhs =
+// work vector 8, x = 9, to tol) or the next correction of the refinement (precision 1-4:
+// rhs = 11, x = 8, to the inner tolerance).  Synchronises the job's stream.
+void start_solve(Job *j) {
+    phs_plan *pl = j->pl;
+    const phs_options &o = pl->opt;
+    if (o.precision == 0) {
+        j->rhs_p = W(pl, 8);
+        j->x_p = W(pl, 9);
+        j->itol = j->st.stop;
+        j->imax = o.maxiter;
+    } else {
+        j->rhs_p = W(pl, 11);
+        j->x_p = W(pl, 8);
+        j->itol = refine_inner_tol(o, std::sqrt(j->rr), j->st.stop);
+        j->imax = refine_inner_maxiter(o, j->iters);
+    }
+    j->it = 0;
+    j->rr = pcg_start(pl, j->rhs_p, j->x_p, j->s);
+}
+// the current solve has ended (converged to itol or reached imax)
+bool solve_ended(const Job *j) { return std::sqrt(j->rr) <= j->itol || j->it >= j->imax; }
 
 double now_s(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -105,6 +133,7 @@ struct phs_server {
     void sched_loop();
     void setup(Job *j);
     void finish(Job *j);
+    void refine(Job *j);
     void tick(std::vector<Job *> &act);
 };
 
@@ -125,8 +154,11 @@ void phs_server::setup(Job *j) {
         AllocScope scope(j->s, &pl->dev_bytes);
         pl->last_stream = j->s;
         j->st = fit_begin(pl, j->f_d(), j->s);
-        if (!j->st.trivial) j->rr = pcg_start(pl, W(pl, 8), W(pl, 9), j->s);
-        j->it = 0;
+        if (!j->st.trivial) {
+            if (j->opt.precision != 0) fit_refine_begin(pl, j->s);
+            j->rr = j->st.nrm0 * j->st.nrm0;
+            start_solve(j);
+        }
         // the measured plan size replaces the a-priori estimate (temporaries: a quarter more)
         const int64_t actual = pl->dev_bytes + pl->dev_bytes / 4 + (int64_t)j->dbytes;
         std::lock_guard<std::mutex> g(mu);
@@ -134,9 +166,16 @@ void phs_server::setup(Job *j) {
         j->reserved = actual;
         max_reserved = std::max(max_reserved, reserved);
         j->t_ready = now_s(t0);
-        if (j->st.trivial || std::sqrt(j->rr) <= j->st.stop) {
+        if (j->st.trivial) {
             j->converged = true;
             j->state = J_FINISH;
+            ++n_finish;
+            work.push_back(j);
+            cv_work.notify_one();
+        } else if (solve_ended(j)) {
+            j->state = j->opt.precision == 0 ? J_FINISH : J_REFINE;
+            if (j->opt.precision == 0) j->converged = true;
+            ++n_finish;
             work.push_back(j);
             cv_work.notify_one();
         } else {
@@ -150,8 +189,53 @@ void phs_server::setup(Job *j) {
         j->status = e.code;
         j->err = e.msg;
         j->state = J_FINISH;
+        ++n_finish;
         work.push_back(j);
         --n_setup;
+        cv_work.notify_one();
+    }
+}
+
+// A correction has ended (precision 1-4): x += dx and the FP64 residual; then, as in
+// phs_fit's loop, finish when it meets the tolerance, or when the correction took no
+// iteration, or when the refinement budget is spent; else start the next correction.
+void phs_server::refine(Job *j) {
+    bool again = false;
+    try {
+        phs_plan *pl = j->pl;
+        AllocScope scope(j->s, &pl->dev_bytes);
+        pl->last_stream = j->s;
+        const phs_options &o = pl->opt;
+        j->iters += j->it;
+        ++j->outer;
+        const double res = fit_refine_step(pl, j->s);
+        const int it_inner = j->it;
+        j->rr = res * res;
+        if (res <= j->st.stop) {
+            j->converged = true;
+        } else if (it_inner != 0 && j->outer < o.max_refine && j->iters < o.maxiter) {
+            start_solve(j);
+            again = !solve_ended(j);
+            if (!again) {  // the correction ended at once: refine again
+                std::lock_guard<std::mutex> g(mu);
+                work.push_back(j);
+                cv_work.notify_one();
+                return;
+            }
+        }
+    } catch (const Error &e) {
+        j->status = e.code;
+        j->err = e.msg;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    if (again) {
+        j->state = J_ACTIVE;
+        active.push_back(j);
+        --n_finish;
+        cv_sched.notify_one();
+    } else {
+        j->state = J_FINISH;
+        work.push_back(j);
         cv_work.notify_one();
     }
 }
@@ -179,8 +263,8 @@ void phs_server::finish(Job *j) {
                                          j->s));
             PHS_CUDA(cudaStreamSynchronize(j->s));
             const double nrm0 = j->st.nrm0;
-            j->info.iters = j->it;
-            j->info.outer_iters = 0;
+            j->info.iters = j->opt.precision == 0 ? j->it : j->iters;
+            j->info.outer_iters = j->outer;
             j->info.converged = j->converged ? 1 : 0;
             j->info.jittered = (int)pl->vec.jittered;
             j->info.rel_res_recursive = nrm0 > 0 ? std::sqrt(j->rr) / nrm0 : 0.0;
@@ -231,6 +315,7 @@ void phs_server::worker_loop() {
             work.pop_front();
         }
         if (j->state == J_SETUP) setup(j);
+        else if (j->state == J_REFINE) refine(j);
         else finish(j);
     }
 }
@@ -240,14 +325,14 @@ void phs_server::tick(std::vector<Job *> &act) {
     const int nj = (int)act.size();
     BatchTable t;
     t.nj = nj;
-    for (int i = 0; i < nj; ++i) t.j[i] = bjob_of(act[i]->pl, W(act[i]->pl, 8), W(act[i]->pl, 9));
+    for (int i = 0; i < nj; ++i) t.j[i] = bjob_of(act[i]->pl, act[i]->rhs_p, act[i]->x_p);
     cudaEvent_t ev_e = ev_get();
     PHS_CUDA(cudaEventRecord(ev_e, engine));
     for (Job *j : act) {  // y = M' p on each job's stream
         phs_plan *pl = j->pl;
         AllocScope scope(j->s, &pl->dev_bytes);
         PHS_CUDA(cudaStreamWaitEvent(j->s, ev_e, 0));
-        matvec_norm(pl, W(pl, 2), W(pl, 4), 0, j->s);
+        matvec_norm(pl, W(pl, 2), W(pl, 4), j->opt.precision, j->s);
         PHS_CUDA(cudaEventRecord(j->ev, j->s));
         PHS_CUDA(cudaStreamWaitEvent(engine, j->ev, 0));
     }
@@ -262,10 +347,8 @@ void phs_server::tick(std::vector<Job *> &act) {
         Job *j = act[i];
         j->rr = rr_host[i];
         ++j->it;
-        if (std::sqrt(j->rr) <= j->st.stop) {
-            j->converged = true;
-            done.push_back(j);
-        } else if (j->it >= j->opt.maxiter) {
+        if (solve_ended(j)) {
+            if (j->opt.precision == 0 && std::sqrt(j->rr) <= j->itol) j->converged = true;
             done.push_back(j);
         } else {
             cont.push_back(j);
@@ -274,7 +357,7 @@ void phs_server::tick(std::vector<Job *> &act) {
     if (!cont.empty()) {
         BatchTable t2;
         t2.nj = (int)cont.size();
-        for (int i = 0; i < t2.nj; ++i) t2.j[i] = bjob_of(cont[i]->pl, W(cont[i]->pl, 8), W(cont[i]->pl, 9));
+        for (int i = 0; i < t2.nj; ++i) t2.j[i] = bjob_of(cont[i]->pl, cont[i]->rhs_p, cont[i]->x_p);
         PHS_CUDA(cudaEventRecord(ev_e, engine));
         for (Job *j : cont) {  // t2 = S~^-1 r on each job's stream
             phs_plan *pl = j->pl;
@@ -293,7 +376,7 @@ void phs_server::tick(std::vector<Job *> &act) {
     ev_put(ev_e);
     std::lock_guard<std::mutex> g(mu);
     for (Job *j : done) {
-        j->state = J_FINISH;
+        j->state = j->opt.precision == 0 ? J_FINISH : J_REFINE;
         act.erase(std::find(act.begin(), act.end(), j));
         ++n_finish;
         work.push_back(j);
@@ -400,7 +483,9 @@ phs_status phs_server_submit(phs_server_t sv, const double *pts_host, const doub
     j->vm = vecchia_m;
     if (opt) j->opt = *opt;
     else phs_options_default(&j->opt, k);
-    PHS_REQUIRE(j->opt.precision == 0, PHS_ERR_INVALID_ARG, "the serving engine runs precision 0");
+    PHS_REQUIRE(j->opt.precision >= 0 && j->opt.precision <= 4, PHS_ERR_INVALID_ARG, "precision must be 0..4");
+    PHS_REQUIRE(k % 2 == 0 || j->opt.precision == 0 || j->opt.precision == 4, PHS_ERR_INVALID_ARG,
+                "odd spline orders run in precision 0 or 4");
     j->n = n;
     j->m = m;
     j->pts.assign(pts_host, pts_host + 2 * n);

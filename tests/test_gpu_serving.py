@@ -104,3 +104,28 @@ def test_server_admission_respects_memory_budget(phs):
     t = [r[4] for r in res]
     for a, b in zip(t, t[1:]):
         assert b[1] >= a[3] - 1e-3
+
+
+def test_batch_of_higher_order_jobs(phs):
+    """Config-4 style batch: k = 4 and 5 (quadratic block), Franke function, points
+    uniform or clustered per job, the float-float near field inside FP64 refinement
+    (precision 4), leaf capacity autotuned (leaf_cap = 0), all jobs submitted at once.
+    Every job equals the same job run alone through phs_fit + phs_eval, and a small one
+    matches the dense oracle at 1e-8."""
+    jobs = synth.batch_jobs(8, seed=77, n_lo=2000, n_hi=20000, n_targets=60)
+    opts = lambda k: phs.options(k, precision=4, leaf_cap=0, tol=1e-10, maxiter=400)  # noqa: E731
+    ref = [_alone(phs, j["points"], j["f"], j["targets"], j["k"], opts(j["k"])) for j in jobs]
+    sv = phs.Server(max_active=8)
+    ids = [sv.submit(j["points"], j["f"], j["targets"], j["k"], vecchia_m=20, opts=opts(j["k"])) for j in jobs]
+    got = [sv.wait(i) for i in ids]
+    st = sv.stats()
+    sv.close()
+    print("batch stats", st, [(j["k"], len(j["f"]), g[3]["iters"], g[3]["outer_iters"]) for j, g in zip(jobs, got)])
+    for (w0, b0, p0, i0), (w1, b1, p1, i1, _) in zip(ref, got):
+        assert i1["converged"] == 1 and i1["iters"] == i0["iters"] and i1["outer_iters"] == i0["outer_iters"]
+        assert np.array_equal(w1, w0) and np.array_equal(b1, b0) and np.array_equal(p1, p0)
+    small = min(range(len(jobs)), key=lambda i: len(jobs[i]["f"]))
+    j = jobs[small]
+    dense = oracle.fit_dense(j["points"], j["f"], j["k"], halfwidth=1.0)
+    want = oracle.predict(dense, j["targets"])
+    assert np.max(np.abs(got[small][2] - want)) <= 1e-8 * np.max(np.abs(want))
