@@ -19,6 +19,7 @@ void set_error(const std::string &msg) { g_err = msg; }
 const char *last_error() { return g_err.c_str(); }
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- timers
 static thread_local std::vector<cudaEvent_t> g_pool;

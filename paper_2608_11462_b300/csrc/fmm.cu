@@ -1353,31 +1353,55 @@ static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaS
     PHS_LAUNCH_CHECK();
 }
 
+Fmm::~Fmm() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+}
+
+// buffers of the near field, allocated on s before the near field forks onto the side
+// stream (so the stream-ordered allocation precedes every use)
+static void p2p_prepare(Fmm &f, const Tree &t) {
+    if (!t.sym_ok) return;
+    if (f.sym_scratch.n < (size_t)std::max<int64_t>(t.sym_total, 1)) f.sym_scratch.alloc(std::max<int64_t>(t.sym_total, 1));
+    if (!f.p2p_ticket.get()) f.p2p_ticket.alloc(1);
+    if (!f.side) {
+        PHS_CUDA(cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking));
+        PHS_CUDA(cudaEventCreateWithFlags(&f.ev_fork, cudaEventDisableTiming));
+        PHS_CUDA(cudaEventCreateWithFlags(&f.ev_join, cudaEventDisableTiming));
+    }
+}
+
 void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, int mode, cudaStream_t s,
                Timers *tm) {
     PHS_REQUIRE(mode >= 0 && mode <= 4, PHS_ERR_INVALID_ARG, "precision mode must be 0..4");
+    PHS_REQUIRE(f.log_core || mode == 0 || mode == 4, PHS_ERR_INVALID_ARG, "odd spline orders run in precision 0 or 4");
+    // near field on the side stream (it writes y; the far field's L2P adds to y after the join)
+    p2p_prepare(f, t);
+    cudaStream_t ns = f.side ? f.side : s;
+    if (f.side) {
+        PHS_CUDA(cudaEventRecord(f.ev_fork, s));
+        PHS_CUDA(cudaStreamWaitEvent(f.side, f.ev_fork, 0));
+    }
+    if (tm) tm->begin(ns);
+    if (mode == 0) p2p_dispatch<double>(f, f.k, t, ps, t_sorted, y, ns);
+    else if (mode == 4) p2p_ff_dispatch(f, t, ps, t_sorted, y, ns);
+    else p2p_dispatch<float>(f, f.k, t, ps, t_sorted, y, ns);
+    if (tm) tm->end(T_P2P, ns);
+    if (f.side) PHS_CUDA(cudaEventRecord(f.ev_join, f.side));
     if (!f.log_core) {
-        // odd k: distance-kernel far field by Chebyshev interpolation in FP64; the near
-        // field in FP64 or (mode 4) float-float
-        PHS_REQUIRE(mode == 0 || mode == 4, PHS_ERR_INVALID_ARG, "odd spline orders run in precision 0 or 4");
-        if (tm) tm->begin(s);
-        if (mode == 4) p2p_ff_dispatch(f, t, ps, t_sorted, y, s);
-        else p2p_dispatch<double>(f, f.k, t, ps, t_sorted, y, s);
-        if (tm) tm->end(T_P2P, s);
+        // odd k: distance-kernel far field by Chebyshev interpolation in FP64
         cheb_far_field(f, t, ps, t_sorted, s, tm);
+        if (f.side) PHS_CUDA(cudaStreamWaitEvent(s, f.ev_join, 0));
         if (tm) tm->begin(s);
         cheb_l2p_apply(f, t, ps, y, s);
         if (tm) tm->end(T_DOWN, s);
         return;
     }
-    if (tm) tm->begin(s);
-    if (mode == 0) p2p_dispatch<double>(f, f.k, t, ps, t_sorted, y, s);
-    else if (mode == 4) p2p_ff_dispatch(f, t, ps, t_sorted, y, s);
-    else p2p_dispatch<float>(f, f.k, t, ps, t_sorted, y, s);
-    if (tm) tm->end(T_P2P, s);
     if (mode <= 1 || mode == 4) far_field<double>(f, t, ps, t_sorted, s, tm);
     else if (mode == 2) far_field_m2l32(f, t, ps, t_sorted, s, tm);
     else far_field<float>(f, t, ps, t_sorted, s, tm);
+    if (f.side) PHS_CUDA(cudaStreamWaitEvent(s, f.ev_join, 0));
     if (tm) tm->begin(s);
     if (mode == 3) l2p_pass<float>(f, t, ps, y, s);
     else l2p_pass<double>(f, t, ps, y, s);

@@ -31,6 +31,7 @@ const char *last_error();
 // every kernel launch in the library is followed by PHS_LAUNCH_CHECK(), which also
 // counts it (phs_kernel_launches)
 void count_launch();
+void count_launches(int64_t k);  // k launches at once (kernels of a replayed graph)
 #define PHS_LAUNCH_CHECK()        \
     do {                          \
         ::phs::count_launch();    \
@@ -262,6 +263,14 @@ struct Fmm {
     int64_t tc_steps = 0, tc_tiles = 0;  // work of one pass (m2l_tc_count)
     DBuf<double> sym_scratch;            // column sums of the symmetric near field
     DBuf<int> p2p_ticket;                // next leaf of the near-field blocks (reset per launch)
+    // the near field runs on a second stream, overlapping the upward pass, M2L and L2L,
+    // and joins before L2P adds the far field into y (created on first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    Fmm() = default;
+    Fmm(const Fmm &) = delete;
+    Fmm &operator=(const Fmm &) = delete;
+    ~Fmm();
 };
 // tensor_m2l: run the FP64 M2L of the log kernel on the tensor cores (m2l_tc.cu)
 void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s);

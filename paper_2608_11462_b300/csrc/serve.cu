@@ -10,7 +10,10 @@
 // Vecchia apply run on its own stream, so jobs of different sizes overlap on the GPU, and
 // the vector operations of all of them -- projection, CG update, inner products, direction
 // update -- run as shared launches over a table of the active jobs (plan.cuh: the table
-// steps).  One device-to-host copy per tick brings every job's residual; converged jobs
+// steps).  A job's FMM matvec and Vecchia apply are captured once, at setup, into CUDA
+// graphs replayed every tick (one launch each instead of the FMM's ~100 kernel launches,
+// which for small jobs is what limits a tick).  One device-to-host copy per tick brings
+// every job's residual; converged jobs
 // leave the tick (a worker computes beta, evaluates the targets and returns the
 // results), and new jobs join as slots and memory free up.  A job's arithmetic is the
 // same as phs_fit's (the same begin/end and the same table steps with a table of one),
@@ -60,6 +63,9 @@ struct Job {
     int imax = 0;             // and its iteration limit
     double *rhs_p = nullptr, *x_p = nullptr;  // the current solve's right-hand side and iterate
     bool converged = false;
+    // the iteration's per-job work captured once: y = M' p (FMM) and t2 = S~^-1 r (Vecchia)
+    cudaGraphExec_t g_mv = nullptr, g_pc = nullptr;
+    int64_t n_mv_kernels = 0, n_pc_kernels = 0;
     phs_fit_info info{};
     double *pts_d() { return dbuf; }
     double *f_d() { return dbuf + 2 * n; }
@@ -98,6 +104,38 @@ void start_solve(Job *j) {
 }
 // the current solve has ended (converged to itol or reached imax)
 bool solve_ended(const Job *j) { return std::sqrt(j->rr) <= j->itol || j->it >= j->imax; }
+
+// Capture fn's work on the job's stream into an executable graph (thread-local capture:
+// other threads keep issuing work meanwhile); *kernels receives its kernel count.
+template <typename Fn>
+cudaGraphExec_t capture(cudaStream_t s, int64_t *kernels, Fn &&fn) {
+    cudaGraph_t g = nullptr;
+    PHS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+        fn();
+    } catch (...) {
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    PHS_CUDA(cudaStreamEndCapture(s, &g));
+    size_t nn = 0;
+    PHS_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) PHS_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+    int64_t kc = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        PHS_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+        if (t == cudaGraphNodeTypeKernel) ++kc;
+    }
+    *kernels = kc;
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    PHS_CUDA(e);
+    return ex;
+}
 
 double now_s(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -158,6 +196,14 @@ void phs_server::setup(Job *j) {
             if (j->opt.precision != 0) fit_refine_begin(pl, j->s);
             j->rr = j->st.nrm0 * j->st.nrm0;
             start_solve(j);
+            // one uncaptured matvec sizes every lazily allocated buffer (its output, work
+            // vector 4, is overwritten by the first tick); then both pieces are captured
+            const int prec = j->opt.precision;
+            matvec_norm(pl, W(pl, 2), W(pl, 4), prec, j->s);
+            j->g_mv = capture(j->s, &j->n_mv_kernels, [&] { matvec_norm(pl, W(pl, 2), W(pl, 4), prec, j->s); });
+            j->g_pc = capture(j->s, &j->n_pc_kernels,
+                              [&] { vecchia_apply(pl->vec, W(pl, 0), W(pl, 5), W(pl, 6), j->s); });
+            PHS_CUDA(cudaStreamSynchronize(j->s));
         }
         // the measured plan size replaces the a-priori estimate (temporaries: a quarter more)
         const int64_t actual = pl->dev_bytes + pl->dev_bytes / 4 + (int64_t)j->dbytes;
@@ -279,6 +325,9 @@ void phs_server::finish(Job *j) {
             j->err = e.msg;
         }
     }
+    if (j->g_mv) cudaGraphExecDestroy(j->g_mv);
+    if (j->g_pc) cudaGraphExecDestroy(j->g_pc);
+    j->g_mv = j->g_pc = nullptr;
     if (j->pl) phs_plan_destroy(j->pl);
     j->pl = nullptr;
     if (j->dbuf) cudaFreeAsync(j->dbuf, j->s);
@@ -332,7 +381,12 @@ void phs_server::tick(std::vector<Job *> &act) {
         phs_plan *pl = j->pl;
         AllocScope scope(j->s, &pl->dev_bytes);
         PHS_CUDA(cudaStreamWaitEvent(j->s, ev_e, 0));
-        matvec_norm(pl, W(pl, 2), W(pl, 4), j->opt.precision, j->s);
+        if (j->g_mv) {
+            PHS_CUDA(cudaGraphLaunch(j->g_mv, j->s));
+            count_launches(j->n_mv_kernels);
+        } else {
+            matvec_norm(pl, W(pl, 2), W(pl, 4), j->opt.precision, j->s);
+        }
         PHS_CUDA(cudaEventRecord(j->ev, j->s));
         PHS_CUDA(cudaStreamWaitEvent(engine, j->ev, 0));
     }
@@ -363,7 +417,12 @@ void phs_server::tick(std::vector<Job *> &act) {
             phs_plan *pl = j->pl;
             AllocScope scope(j->s, &pl->dev_bytes);
             PHS_CUDA(cudaStreamWaitEvent(j->s, ev_e, 0));
-            vecchia_apply(pl->vec, W(pl, 0), W(pl, 5), W(pl, 6), j->s);
+            if (j->g_pc) {
+                PHS_CUDA(cudaGraphLaunch(j->g_pc, j->s));
+                count_launches(j->n_pc_kernels);
+            } else {
+                vecchia_apply(pl->vec, W(pl, 0), W(pl, 5), W(pl, 6), j->s);
+            }
             PHS_CUDA(cudaEventRecord(j->ev, j->s));
             PHS_CUDA(cudaStreamWaitEvent(engine, j->ev, 0));
         }

@@ -70,11 +70,12 @@ def _header_struct(name):
 
 
 def test_ctypes_mirrors_follow_the_header(native):
-    """PhsOptions and PhsFitInfo list the header's fields in its order with matching C
-    types, so a field added on one side only is caught on CPU."""
+    """PhsOptions, PhsFitInfo and PhsServerConfig list the header's fields in its order
+    with matching C types, so a field added on one side only is caught on CPU."""
     ctype = {"int": ctypes.c_int, "double": ctypes.c_double, "float": ctypes.c_float,
              "uint64_t": ctypes.c_uint64, "int64_t": ctypes.c_int64}
-    for cname, mirror in (("phs_options", native.PhsOptions), ("phs_fit_info", native.PhsFitInfo)):
+    for cname, mirror in (("phs_options", native.PhsOptions), ("phs_fit_info", native.PhsFitInfo),
+                          ("phs_server_config", native.PhsServerConfig)):
         want = [(f, ctype[t]) for t, f in _header_struct(cname)]
         assert want, cname
         assert [(f, t) for f, t in mirror._fields_] == want, cname
