@@ -12,7 +12,7 @@
 //               serves every level after scaling by the half-width h), applied in
 //               compressed form: the 40 matrices share a target basis U (left singular
 //               vectors of [K_o ...]) and a source basis V (right singular vectors of
-//               [K_o; ...]), truncated where the singular values fall below lr_eps times
+//               [K_o; ...]; U = V by symmetry), truncated where the singular values fall below lr_eps times
 //               the largest, so K_o ~ U C_o V' and an interaction costs rt x rs instead
 //               of (q^2)^2: W~ = V' W once per source box, L~ += C_o (S_o W~) per
 //               V-list entry, L = U L~ once per target box
@@ -21,9 +21,11 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "geom.cuh"
+#include "hadamard.cuh"
 #include "phs_internal.cuh"
 
 namespace phs {
@@ -56,29 +58,6 @@ __device__ __forceinline__ void cheb_basis(double t, int q, const double *Tn, do
     }
 }
 
-__device__ __forceinline__ void had_v_cheb(int power, double x, double y, double *v) {
-    const double a = x * x + y * y;
-    if (power == 0) {
-        v[0] = 1.0;
-    } else if (power == 2) {
-        v[0] = 1.0; v[1] = a; v[2] = x; v[3] = y;
-    } else {
-        v[0] = 1.0; v[1] = a * a; v[2] = x; v[3] = y; v[4] = a * x; v[5] = a * y;
-        v[6] = x * x; v[7] = x * y; v[8] = y * y;
-    }
-}
-__device__ __forceinline__ void had_u_cheb(int power, double x, double y, double *u) {
-    const double a = x * x + y * y;
-    if (power == 0) {
-        u[0] = 1.0;
-    } else if (power == 2) {
-        u[0] = a; u[1] = 1.0; u[2] = -2.0 * x; u[3] = -2.0 * y;
-    } else {
-        u[0] = a * a; u[1] = 1.0; u[2] = -4.0 * a * x; u[3] = -4.0 * a * y; u[4] = -4.0 * x; u[5] = -4.0 * y;
-        u[6] = 4.0 * x * x + 2.0 * a; u[7] = 8.0 * x * y; u[8] = 4.0 * y * y + 2.0 * a;
-    }
-}
-
 // P2M on leaves: W[b][d][m1*q+m2]
 __global__ void cheb_p2m(TreeView tv, const int *leaf_box, const double2 *xs, const double *t, int power, int nd, int q,
                          const double *Tn_g, double *W) {
@@ -104,7 +83,7 @@ __global__ void cheb_p2m(TreeView tv, const int *leaf_box, const double2 *xs, co
                 cheb_basis(fmin(1.0, fmax(-1.0, (p.x - cx) * ih)), q, Tn, S1[threadIdx.x]);
                 cheb_basis(fmin(1.0, fmax(-1.0, (p.y - cy) * ih)), q, Tn, S2[threadIdx.x]);
                 double v[10];
-                had_v_cheb(power, 0.5 * (p.x - cx) * ih, 0.5 * (p.y - cy) * ih, v);  // box-local densities
+                had_v(power, 0.5 * (p.x - cx) * ih, 0.5 * (p.y - cy) * ih, v);  // box-local densities
                 const double tj = t[j];
                 for (int d = 0; d < nd; ++d) qd[threadIdx.x][d] = v[d] * tj;
             } else {
@@ -240,7 +219,7 @@ __global__ void cheb_l2p(TreeView tv, const int *leaf_box, const double2 *xs, in
         cheb_basis(sx, q, Tn, S1);
         cheb_basis(sy, q, Tn, S2);
         double u[10];
-        had_u_cheb(power, 0.5 * sx, 0.5 * sy, u);  // box-local factors
+        had_u(power, 0.5 * sx, 0.5 * sy, u);  // box-local factors
         double sum = 0.0;
         for (int d = 0; d < nd; ++d) {
             const double *Lb = lsm + d * qq;
@@ -325,52 +304,108 @@ __global__ void cheb_expand(TreeView tv, int b0, int nd, int qq, int rt, int pow
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-// Eigen-decomposition of a symmetric n x n matrix A (row-major, overwritten) by cyclic
-// Jacobi rotations: on return w holds the eigenvalues in decreasing order and the
-// columns of V (row-major, V[i][k]) the matching orthonormal eigenvectors.
-static void sym_eig(int n, std::vector<double> &A, std::vector<double> &V, std::vector<double> &w) {
+// R of a Householder QR of the column-major m x n matrix M (m >= n): column j's reflector
+// v = a - alpha e_j (alpha = -sign(a_j) |a|) is applied to the columns right of j, spread
+// over threads by column.  Backward stable: the singular values of R are those of M to
+// within eps ||M||, which is what lets the truncation below reach 1e-12 (forming M'M
+// first would square the condition and stop near 1e-8).
+static std::vector<double> householder_r(int m, int n, std::vector<double> M) {
+    const int nth = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    for (int j = 0; j < n; ++j) {
+        double *a = M.data() + (size_t)j * m;
+        double nrm2 = 0.0;
+        for (int i = j; i < m; ++i) nrm2 += a[i] * a[i];
+        if (nrm2 == 0.0) continue;
+        const double nrm = std::sqrt(nrm2), aj = a[j];
+        const double alpha = aj > 0 ? -nrm : nrm;
+        a[j] = aj - alpha;
+        const double vv = nrm2 - aj * aj + a[j] * a[j];  // |v|^2
+        auto update = [&](int k0, int k1) {
+            for (int k = k0; k < k1; ++k) {
+                double *c = M.data() + (size_t)k * m;
+                double d = 0.0;
+                for (int i = j; i < m; ++i) d += a[i] * c[i];
+                const double fct = 2.0 * d / vv;
+                for (int i = j; i < m; ++i) c[i] -= fct * a[i];
+            }
+        };
+        const int rest = n - j - 1;
+        if (rest >= 4 * nth) {
+            std::vector<std::thread> th;
+            const int per = (rest + nth - 1) / nth;
+            for (int t = 0; t < nth; ++t) {
+                const int k0 = j + 1 + t * per, k1 = std::min(n, k0 + per);
+                if (k0 < k1) th.emplace_back(update, k0, k1);
+            }
+            for (auto &x : th) x.join();
+        } else {
+            update(j + 1, n);
+        }
+        a[j] = alpha;
+    }
+    std::vector<double> R((size_t)n * n, 0.0);  // column-major, upper triangle
+    for (int k = 0; k < n; ++k)
+        for (int i = 0; i <= k; ++i) R[(size_t)k * n + i] = M[(size_t)k * m + i];
+    return R;
+}
+
+// Right singular vectors of the n x n column-major R by one-sided (Hestenes) Jacobi:
+// column pairs of R are rotated until orthogonal, the rotations accumulated in V (which
+// stays orthogonal to rounding whatever the stopping point).  On return the columns of V
+// (column-major) are sorted by the norms of R's columns, the singular values, returned
+// in s in decreasing order.  Pairs whose smaller column is below 1e-13 of the largest
+// norm are left alone: such columns are truncated anyway and rotating rounding noise
+// against rounding noise does not converge.
+static void jacobi_right(int n, std::vector<double> &R, std::vector<double> &V, std::vector<double> &s) {
     V.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    auto col2 = [&](const double *c) {
+        double a = 0.0;
+        for (int i = 0; i < n; ++i) a += c[i] * c[i];
+        return a;
+    };
     for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, diag = 0.0;
-        for (int i = 0; i < n; ++i) {
-            diag += A[(size_t)i * n + i] * A[(size_t)i * n + i];
-            for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
-        }
-        if (off <= 1e-32 * diag) break;
-        for (int p = 0; p < n; ++p)
-            for (int r = p + 1; r < n; ++r) {
-                const double apr = A[(size_t)p * n + r];
-                if (apr == 0.0) continue;
-                const double app = A[(size_t)p * n + p], arr = A[(size_t)r * n + r];
-                const double theta = (arr - app) / (2.0 * apr);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
-                for (int k = 0; k < n; ++k) {  // columns p, r
-                    const double akp = A[(size_t)k * n + p], akr = A[(size_t)k * n + r];
-                    A[(size_t)k * n + p] = c * akp - sn * akr;
-                    A[(size_t)k * n + r] = sn * akp + c * akr;
+        double top = 0.0;
+        for (int k = 0; k < n; ++k) top = std::max(top, col2(R.data() + (size_t)k * n));
+        bool rotated = false;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double *a = R.data() + (size_t)p * n, *b = R.data() + (size_t)q * n;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < n; ++i) {
+                    al += a[i] * a[i];
+                    be += b[i] * b[i];
+                    ga += a[i] * b[i];
                 }
-                for (int k = 0; k < n; ++k) {  // rows p, r
-                    const double apk = A[(size_t)p * n + k], ark = A[(size_t)r * n + k];
-                    A[(size_t)p * n + k] = c * apk - sn * ark;
-                    A[(size_t)r * n + k] = sn * apk + c * ark;
+                if (std::min(al, be) < 1e-26 * top || std::fabs(ga) <= 1e-14 * std::sqrt(al * be)) continue;
+                rotated = true;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                for (int i = 0; i < n; ++i) {
+                    const double x = a[i], y = b[i];
+                    a[i] = c * x - sn * y;
+                    b[i] = sn * x + c * y;
                 }
-                for (int k = 0; k < n; ++k) {
-                    const double vkp = V[(size_t)k * n + p], vkr = V[(size_t)k * n + r];
-                    V[(size_t)k * n + p] = c * vkp - sn * vkr;
-                    V[(size_t)k * n + r] = sn * vkp + c * vkr;
+                double *va = V.data() + (size_t)p * n, *vb = V.data() + (size_t)q * n;
+                for (int i = 0; i < n; ++i) {
+                    const double x = va[i], y = vb[i];
+                    va[i] = c * x - sn * y;
+                    vb[i] = sn * x + c * y;
                 }
             }
+        if (!rotated) break;
     }
+    std::vector<double> nrm(n);
+    for (int k = 0; k < n; ++k) nrm[k] = std::sqrt(col2(R.data() + (size_t)k * n));
     std::vector<int> idx(n);
     for (int i = 0; i < n; ++i) idx[i] = i;
-    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return A[(size_t)a * n + a] > A[(size_t)b * n + b]; });
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return nrm[x] > nrm[y]; });
     std::vector<double> Vs((size_t)n * n);
-    w.resize(n);
+    s.resize(n);
     for (int c = 0; c < n; ++c) {
-        w[c] = A[(size_t)idx[c] * n + idx[c]];
-        for (int k = 0; k < n; ++k) Vs[(size_t)k * n + c] = V[(size_t)k * n + idx[c]];
+        s[c] = nrm[idx[c]];
+        std::copy(V.begin() + (size_t)idx[c] * n, V.begin() + (size_t)(idx[c] + 1) * n, Vs.begin() + (size_t)c * n);
     }
     V.swap(Vs);
 }
@@ -380,10 +415,13 @@ struct ChebLowRank {
     std::vector<double> buf;  // U [qq][rt] | V [qq][rs] | C [49][rt][rs]
 };
 
-// Shared bases of the 40 M2L matrices A_o[m][n] = K[o][n][m] (target m, source n): U from
-// sum_o A_o A_o', V from sum_o A_o' A_o (their eigenvalues are the squared singular
-// values of the matrices stacked side by side / on top of each other), each truncated
-// where sqrt(eigenvalue) < eps * the largest; C_o = U' A_o V.  Built once per (q, eps).
+// Shared bases of the 40 M2L matrices A_o[m][n] = K[o][n][m] (target m, source n).  The
+// source basis V is the leading right singular vectors of the stacked [A_o; ...]
+// (Householder R, then one-sided Jacobi), truncated where the singular values fall
+// below eps times the largest.  The target basis is the leading left singular vectors
+// of [A_o ...]; since A_o' = A_{-o} (|x_m - x_n - 2o| = |x_n - x_m + 2o|) and the offset
+// set is symmetric, [A_o ...]' is the same stack with its blocks reordered, so U = V.
+// C_o = U' A_o V.  Built once per (q, eps).
 static const ChebLowRank &cheb_lowrank(int q, double eps, const std::vector<double> &K) {
     static std::mutex mu;
     static std::map<std::pair<int, double>, ChebLowRank> cache;
@@ -396,58 +434,39 @@ static const ChebLowRank &cheb_lowrank(int q, double eps, const std::vector<doub
         const int dx = c / 7 - 3, dy = c % 7 - 3;
         if (std::abs(dx) > 1 || std::abs(dy) > 1) cls.push_back(c);
     }
-    std::vector<double> Gt((size_t)qq * qq, 0.0), Gs((size_t)qq * qq, 0.0);
-    for (int c : cls) {
-        const double *Kc = K.data() + (size_t)c * qq * qq;  // Kc[n * qq + m] = A_o[m][n]
-        for (int m = 0; m < qq; ++m)
-            for (int m2 = m; m2 < qq; ++m2) {
-                double st = 0.0, ss = 0.0;
-                for (int n = 0; n < qq; ++n) {
-                    st += Kc[(size_t)n * qq + m] * Kc[(size_t)n * qq + m2];
-                    ss += Kc[(size_t)m * qq + n] * Kc[(size_t)m2 * qq + n];
-                }
-                Gt[(size_t)m * qq + m2] += st;
-                Gs[(size_t)m * qq + m2] += ss;
-            }
+    const int rows = (int)cls.size() * qq;
+    std::vector<double> St((size_t)rows * qq);  // column n: (class, target m) rows
+    for (size_t ci = 0; ci < cls.size(); ++ci) {
+        const double *Kc = K.data() + (size_t)cls[ci] * qq * qq;  // Kc[n * qq + m] = A_o[m][n]
+        for (int n = 0; n < qq; ++n)
+            std::copy(Kc + (size_t)n * qq, Kc + (size_t)(n + 1) * qq, St.begin() + (size_t)n * rows + ci * qq);
     }
-    for (int m = 0; m < qq; ++m)
-        for (int m2 = 0; m2 < m; ++m2) {
-            Gt[(size_t)m * qq + m2] = Gt[(size_t)m2 * qq + m];
-            Gs[(size_t)m * qq + m2] = Gs[(size_t)m2 * qq + m];
-        }
-    std::vector<double> Ut, wt, Vs, ws;
-    sym_eig(qq, Gt, Ut, wt);
-    sym_eig(qq, Gs, Vs, ws);
-    auto rank_of = [&](const std::vector<double> &w) {
-        const double top = std::sqrt(std::max(w[0], 0.0));
-        int r = 0;
-        while (r < qq && std::sqrt(std::max(w[r], 0.0)) > eps * top) ++r;
-        return std::max(r, 1);
-    };
+    std::vector<double> R = householder_r(rows, qq, std::move(St));
+    std::vector<double> Vc, sv;
+    jacobi_right(qq, R, Vc, sv);
+    int r = 0;
+    while (r < qq && sv[r] > eps * sv[0]) ++r;
+    r = std::max(r, 1);
     ChebLowRank lr;
-    lr.rt = rank_of(wt);
-    lr.rs = rank_of(ws);
-    const int rt = lr.rt, rs = lr.rs;
-    lr.buf.assign((size_t)qq * rt + (size_t)qq * rs + (size_t)49 * rt * rs, 0.0);
-    double *U = lr.buf.data(), *V = U + (size_t)qq * rt, *C = V + (size_t)qq * rs;
+    lr.rt = lr.rs = r;
+    lr.buf.assign((size_t)2 * qq * r + (size_t)49 * r * r, 0.0);
+    double *U = lr.buf.data(), *V = U + (size_t)qq * r, *C = V + (size_t)qq * r;
     for (int m = 0; m < qq; ++m)
-        for (int i = 0; i < rt; ++i) U[(size_t)m * rt + i] = Ut[(size_t)m * qq + i];
-    for (int n = 0; n < qq; ++n)
-        for (int j = 0; j < rs; ++j) V[(size_t)n * rs + j] = Vs[(size_t)n * qq + j];
-    std::vector<double> AV((size_t)qq * rs);
+        for (int i = 0; i < r; ++i) U[(size_t)m * r + i] = V[(size_t)m * r + i] = Vc[(size_t)i * qq + m];
+    std::vector<double> AV((size_t)qq * r);
     for (int c : cls) {
         const double *Kc = K.data() + (size_t)c * qq * qq;
-        for (int m = 0; m < qq; ++m)  // AV = A_o V
-            for (int j = 0; j < rs; ++j) {
-                double a = 0.0;
-                for (int n = 0; n < qq; ++n) a += Kc[(size_t)n * qq + m] * V[(size_t)n * rs + j];
-                AV[(size_t)m * rs + j] = a;
+        std::fill(AV.begin(), AV.end(), 0.0);  // AV = A_o V
+        for (int n = 0; n < qq; ++n)
+            for (int m = 0; m < qq; ++m) {
+                const double k = Kc[(size_t)n * qq + m];
+                for (int j = 0; j < r; ++j) AV[(size_t)m * r + j] += k * V[(size_t)n * r + j];
             }
-        for (int i = 0; i < rt; ++i)  // C_o = U' AV
-            for (int j = 0; j < rs; ++j) {
-                double a = 0.0;
-                for (int m = 0; m < qq; ++m) a += U[(size_t)m * rt + i] * AV[(size_t)m * rs + j];
-                C[((size_t)c * rt + i) * rs + j] = a;
+        double *Cc = C + (size_t)c * r * r;  // C_o = U' AV
+        for (int m = 0; m < qq; ++m)
+            for (int i = 0; i < r; ++i) {
+                const double u = U[(size_t)m * r + i];
+                for (int j = 0; j < r; ++j) Cc[(size_t)i * r + j] += u * AV[(size_t)m * r + j];
             }
     }
     return cache.emplace(std::make_pair(q, eps), std::move(lr)).first->second;
@@ -581,7 +600,7 @@ __global__ void cheb_eval_far(TreeView tv, const double2 *tgt, const int *box_of
     const double2 y = tgt[i];
     const double sx = fmin(1.0, fmax(-1.0, (y.x - cx) / h)), sy = fmin(1.0, fmax(-1.0, (y.y - cy) / h));
     double u[10];
-    had_u_cheb(power, 0.5 * (y.x - cx) / h, 0.5 * (y.y - cy) / h, u);  // box-local factors
+    had_u(power, 0.5 * (y.x - cx) / h, 0.5 * (y.y - cy) / h, u);  // box-local factors
     const int qq = q * q;
     double acc = 0.0;
     for (int d = 0; d < nd; ++d) acc += u[d] * cheb_l2p_point(L + ((size_t)b * nd + d) * qq, q, Tn, sx, sy);
