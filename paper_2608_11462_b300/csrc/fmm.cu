@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "geom.cuh"
+#include "hadamard.cuh"
 #include "phs_internal.cuh"
 
 namespace phs {
@@ -50,31 +51,6 @@ __device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
     acc.y = fmaf(a.y, b.x, acc.y);
 }
 
-// Hadamard factors of [|x_i - x_j|^power] (Sec. 2): u_l(x_i) v_l(x_j) summed over l.
-// power 2: rank 4.  power 4: rank 9 (|x|^2 |y|^2 folds into the quadratic monomials,
-// so the separable rank is 9 rather than the 10 terms of the plain expansion).
-__device__ __forceinline__ void had_v(int power, double x, double y, double *v) {
-    const double a = x * x + y * y;
-    if (power == 0) {
-        v[0] = 1.0;
-    } else if (power == 2) {
-        v[0] = 1.0; v[1] = a; v[2] = x; v[3] = y;
-    } else {
-        v[0] = 1.0; v[1] = a * a; v[2] = x; v[3] = y; v[4] = a * x; v[5] = a * y;
-        v[6] = x * x; v[7] = x * y; v[8] = y * y;
-    }
-}
-__device__ __forceinline__ void had_u(int power, double x, double y, double *u) {
-    const double a = x * x + y * y;
-    if (power == 0) {
-        u[0] = 1.0;
-    } else if (power == 2) {
-        u[0] = a; u[1] = 1.0; u[2] = -2.0 * x; u[3] = -2.0 * y;
-    } else {
-        u[0] = a * a; u[1] = 1.0; u[2] = -4.0 * a * x; u[3] = -4.0 * a * y; u[4] = -4.0 * x; u[5] = -4.0 * y;
-        u[6] = 4.0 * x * x + 2.0 * a; u[7] = 8.0 * x * y; u[8] = 4.0 * y * y + 2.0 * a;
-    }
-}
 constexpr int kMaxNd = 10;
 constexpr int kMaxP = 61;
 
@@ -1125,7 +1101,7 @@ static void set_pass_smem_limits() {
 
 template <typename T>
 static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, typename C2T<T>::type *mp,
-                   const typename C2T<T>::type *ops, int P, cudaStream_t s) {
+                   const typename C2T<T>::type *ops, int P, cudaStream_t s, bool ff = false) {
     using C = typename C2T<T>::type;
     TreeView tv = tree_view(t);
     const int nd = f.nd;
@@ -1133,7 +1109,8 @@ static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_s
     if constexpr (sizeof(T) == 8) {
         set_pass_smem_limits();
         const size_t sm = (size_t)64 * P * sizeof(double2) + (size_t)64 * nd * sizeof(double);
-        if (nd == 4) p2m64_kernel<4><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
+        if (ff) p2m_ff_launch(f, t, ps, tv_sorted, mp, s);
+        else if (nd == 4) p2m64_kernel<4><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
         else if (nd == 9) p2m64_kernel<9><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
         else p2m64_kernel<1><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
         PHS_LAUNCH_CHECK();
@@ -1211,11 +1188,11 @@ __global__ void f2d_kernel(const float2 *in, double2 *out, size_t n) {
 // upward pass, M2L and downward pass (local expansions of every box) in one precision
 template <typename T>
 static void far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, cudaStream_t s,
-                      Timers *tm) {
+                      Timers *tm, bool ff = false) {
     ensure_bufs<T>(f, t);
     const int P = P_of<T>(f);
     if (tm) tm->begin(s);
-    upward<T>(f, t, ps, tv_sorted, mp_buf<T>(f), ops_buf<T>(f), P, s);
+    upward<T>(f, t, ps, tv_sorted, mp_buf<T>(f), ops_buf<T>(f), P, s, ff);
     if (tm) tm->end(T_UP, s);
     if (tm) tm->begin(s);
     m2l_pass<T>(f, t, mp_buf<T>(f), lc_buf<T>(f), ops_buf<T>(f), P, s);
@@ -1337,9 +1314,13 @@ static void p2p_ff_dispatch(Fmm &f, const Tree &t, const PointSet &ps, const dou
 }
 
 template <typename T>
-static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s) {
+static void l2p_pass(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s, bool ff = false) {
     using C = typename C2T<T>::type;
     if constexpr (sizeof(T) == 8) {
+        if (ff) {
+            l2p_ff_launch(f, t, ps, f.lc64.get(), y, s);
+            return;
+        }
         const size_t sm = (size_t)f.nd * f.P * sizeof(double2);  // at most 9 x 61 x 16 B
         const TreeView tv = tree_view(t);
         if (f.nd == 4) l2p64_kernel<4><<<t.nleaf, L2P_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), f.power, f.P, f.lc64.get(), y);
@@ -1398,13 +1379,13 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
         if (tm) tm->end(T_DOWN, s);
         return;
     }
-    if (mode <= 1 || mode == 4) far_field<double>(f, t, ps, t_sorted, s, tm);
+    if (mode <= 1 || mode == 4) far_field<double>(f, t, ps, t_sorted, s, tm, mode == 4 && f.ff_passes);
     else if (mode == 2) far_field_m2l32(f, t, ps, t_sorted, s, tm);
     else far_field<float>(f, t, ps, t_sorted, s, tm);
     if (f.side) PHS_CUDA(cudaStreamWaitEvent(s, f.ev_join, 0));
     if (tm) tm->begin(s);
     if (mode == 3) l2p_pass<float>(f, t, ps, y, s);
-    else l2p_pass<double>(f, t, ps, y, s);
+    else l2p_pass<double>(f, t, ps, y, s, mode == 4 && f.ff_passes);
     if (tm) tm->end(T_DOWN, s);
 }
 

@@ -33,11 +33,13 @@
 #include <cmath>
 #include <vector>
 
+#include "ff.cuh"
 #include "geom.cuh"
 #include "phs_internal.cuh"
 
 namespace phs {
 namespace {
+using namespace ffa;
 
 constexpr int NF_T = kP2PThreads;
 constexpr int kFfTab = 256;  // table cells of the mantissa (top 8 fraction bits)
@@ -46,56 +48,6 @@ constexpr int kFfExp = 256;  // biased FP32 exponents
 __device__ float g_ff_rcp[kFfTab];    // R_j, 9 significant bits
 __device__ float2 g_ff_tlog[kFfTab];  // -log R_j as (hi, lo)
 __device__ float2 g_ff_eln2[kFfExp];  // (e - 127) log 2 as (hi, lo), e the biased exponent
-
-struct F2 {
-    float h, l;
-};
-
-// error-free transformations; explicit roundings keep the compiler from contracting them
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // requires |a| >= |b| (or a = 0)
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ F2 two_prod(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
-// (a.h + a.l)(b.h + b.l) without the lo*lo term; the result's lo is not renormalised
-__device__ __forceinline__ F2 ff_mul(F2 a, F2 b) {
-    F2 p = two_prod(a.h, b.h);
-    p.l = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l));
-    return p;
-}
-__device__ __forceinline__ F2 ff_sub(F2 a, F2 b) {
-    F2 s = two_sum(a.h, -b.h);
-    s.l = __fadd_rn(s.l, __fsub_rn(a.l, b.l));
-    return s;
-}
-__device__ __forceinline__ void ff_acc(F2 &acc, F2 v) {
-    const F2 s = two_sum(acc.h, v.h);
-    acc.h = s.h;
-    acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, v.l));
-}
-__device__ __forceinline__ F2 split_d(double v) {
-    const float h = __double2float_rn(v);
-    return {h, __double2float_rn(v - (double)h)};
-}
-__device__ __forceinline__ double to_d(F2 a) { return (double)a.h + (double)a.l; }
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float rsqrt_approx(float x) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 // s = dx^2 + dy^2, renormalised so that |s.l| <= ulp(s.h) / 2
 __device__ __forceinline__ F2 ff_norm2(F2 dx, F2 dy) {

@@ -250,6 +250,7 @@ struct Fmm {
     DBuf<float> cw32, cl32;
     // tensor-core M2L of the log kernel (m2l_tc.cu)
     bool tc = false;                     // use it for the FP64 far field
+    bool ff_passes = true;               // precision 4: P2M and L2P in float-float too
     int tc_npad = 0, tc_nch = 0;         // output columns (P rounded up to 16), K chunks
     DBuf<uint16_t> tc_b;                 // operator digit planes (bf16 bits)
     DBuf<int> tc_F;                      // column exponents [P]
@@ -302,10 +303,17 @@ void cheb_eval_far_launch(Fmm &f, const Tree &t, const double2 *tgt, const int *
 void p2p_sym_ff(const Tree &t, const PointSet &ps, int k, const double *tv_sorted, double *y, double *scratch,
                 int *ticket, cudaStream_t s);
 void upload_ff_tables();
+// float-float P2M and L2P of the log-kernel far field (farfield_ff.cu): the same FP64
+// expansion layout as the FP64 passes ([box][d][k] complex coefficients), per-point
+// arithmetic on the FP32 pipe; P2M overwrites every leaf's mp, L2P adds into y.
+void p2m_ff_launch(const Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, double2 *mp,
+                   cudaStream_t s);
+void l2p_ff_launch(const Fmm &f, const Tree &t, const PointSet &ps, const double2 *lc, double *y, cudaStream_t s);
 // y = M' t for sorted-order vectors in the normalised frame (M' of the normalised points)
 // mode 0: FP64 throughout; 1: FP32 near field + FP64 far field; 2: FP32 near field and
 // FP32 M2L inside FP64 upward/downward passes; 3: FP32 throughout (order p32);
-// 4: float-float near field on the FP32 pipe + FP64 far field (M2L as configured)
+// 4: float-float near field, P2M and L2P on the FP32 pipe + FP64 M2M/M2L/L2L (M2L as
+//    configured)
 void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted, int mode,
                cudaStream_t s, struct Timers *tm);
 // evaluate sum_j w_j phi(|x_j - y|) at normalised targets (after an FMM upward/downward

@@ -104,14 +104,16 @@ def test_fmm_matvec_mixed_precision(phs, k, mode, tol):
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("geom", ["uniform", "clustered"])
 def test_fmm_matvec_float_float_near_field(phs, k, geom):
-    """Mode 4 (near field in float-float on the FP32 pipe).  Every row within 1e-11 of the
+    """Mode 4 (near field, and for even k the far field's P2M and L2P, in float-float on
+    the FP32 pipe).  Every row within 1e-11 of the
     oracle's exact row sum, relative to that row's sum of absolute terms (the scale of
     any summation's rounding), on a random vector and on an oscillating one (the
     preconditioned vector, whose sums cancel most: there ||M t|| is up to ~1e9 below the
     sum of absolute terms for r^5, so a 2-norm bound would measure the cancellation, not
     the arithmetic); the random vector's 2-norm within 1e-10 of the dense product, as for
     FP64; and mode 4 against the FP64 matvec of the same plan within 1e-12 of the row
-    scale (their far fields are identical, so this isolates the near field)."""
+    scale (M2M, M2L and L2L are shared, so this isolates the per-point float-float
+    arithmetic)."""
     n = 3001
     pts = np.random.default_rng(12).random((n, 2)) if geom == "uniform" else _clustered(n, 13)
     plan = phs.Plan(_t(pts), k, fmm_order=0, vecchia_m=8, opts=phs.options(k, leaf_cap=32))
