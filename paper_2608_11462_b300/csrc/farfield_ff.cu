@@ -1,12 +1,13 @@
-// farfield_ff.cu -- the per-point passes of the log-kernel FMM (Sec. 2.1) in float-float
-// arithmetic on the FP32 pipe, for precision 4: P2M (outgoing expansions of the leaves,
-// Eq. 2.14, with the Hadamard charges of Eq. 2.6) and L2P (evaluation of the incoming
+// farfield_ff.cu -- the upward and downward passes of the log-kernel FMM (Sec. 2.1) in
+// float-float arithmetic on the FP32 pipe, for precision 4: P2M (outgoing expansions of
+// the leaves, Eq. 2.14, with the Hadamard charges of Eq. 2.6), M2M and L2L (the shifts of
+// Sec. 2.1 through their real triangular cores) and L2P (evaluation of the incoming
 // expansions, Eq. 2.15, combined with the Hadamard factors).  They read and write the
-// same FP64 expansions as the FP64 passes (fmm.cu p2m64_kernel / l2p64_kernel), so M2M,
-// M2L and L2L are unchanged; only the per-point arithmetic moves to hi + lo floats
-// (about 2^-46 per operation, ff.cuh).  Their rounding enters the expansion coefficients,
-// so it reaches the matvec as a smooth far-field perturbation, not as the pairwise noise
-// the preconditioned system amplifies.
+// same FP64 expansions as the FP64 passes (fmm.cu p2m64_kernel, m2m64_kernel,
+// l2l64_kernel, l2p64_kernel), so the M2L is unchanged; the bulk arithmetic moves to hi +
+// lo floats (about 2^-46 per operation, ff.cuh).  Their rounding enters the expansion
+// coefficients, so it reaches the matvec as a smooth far-field perturbation, not as the
+// pairwise noise the preconditioned system amplifies.
 //
 // P2M, per leaf: z_j = (x_j - c)/w, q_{d,j} = v_d(z_j) t_j; a~_0 = sum_j q, a~_k = -sum_j q
 // z^k / k.  Points in chunks of 64: four threads per point build the powers z^k (a
@@ -149,7 +150,166 @@ __global__ void __launch_bounds__(LF_T) l2p_ff_kernel(TreeView tv, const int *le
     }
 }
 
+// M2M for the parents of one level, as fmm.cu m2m64_kernel: each child's multipole takes
+// the phase e^{-i th_q k} (FP64, split to float-float in shared memory), passes through
+// the real lower-triangular core R (row l: sum over k <= l) in float-float with two
+// interleaved accumulator pairs, takes e^{i th_q l}, and the parent sums the children
+// through the frame changes (FP64; nd x nd per coefficient, a small share of the work).
+__global__ void __launch_bounds__(PF_T) m2m_ff_kernel(TreeView tv, int b0, int nd, int P, const float2 *R,
+                                                      const double2 *ph, const double *mix, double2 *mp) {
+    extern __shared__ float4 mf_sm[];
+    const int b = b0 + blockIdx.x;
+    const int nc = tv.nchild[b];
+    if (nc == 0) return;
+    const int nout = nd * P, c0 = tv.child[b];
+    float4 *ch = mf_sm;                                     // [4][nd][P] rotated children
+    double2 *sh = reinterpret_cast<double2 *>(mf_sm + 4 * nout);  // [4][nd][P] shifted
+    for (int i = threadIdx.x; i < nc * nout; i += PF_T) {
+        const int c = i / nout, k = (i - c * nout) % P;
+        const double2 a = mp[(size_t)c0 * nout + i], e = ph[(size_t)(tv.key[c0 + c] & 3) * P + k];
+        ch[i] = c4_pack(c4_of(make_double2(fma(a.x, e.x, a.y * e.y), fma(a.y, e.x, -a.x * e.y))));
+    }
+    __syncthreads();
+    const int half = (P + 1) / 2;
+    for (int it = threadIdx.x; it < nc * nd * half; it += PF_T) {
+        const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
+        const double2 *ephq = ph + (size_t)(tv.key[c0 + c] & 3) * P;
+        const float4 *src = ch + c * nout + d * P;
+        for (int h = 0; h < 2; ++h) {
+            const int l = h == 0 ? p : P - 1 - p;
+            if (h == 1 && l == p) break;
+            const float2 *Rr = R + (size_t)l * P;
+            F2 ax{0.f, 0.f}, ay{0.f, 0.f}, bx{0.f, 0.f}, by{0.f, 0.f};
+            int k = 0;
+            for (; k + 1 <= l; k += 2) {
+                const float2 r0 = Rr[k], r1 = Rr[k + 1];
+                const C4 m0 = c4_unpack(src[k]), m1 = c4_unpack(src[k + 1]);
+                ff_acc(ax, ff_mul(F2{r0.x, r0.y}, m0.re));
+                ff_acc(ay, ff_mul(F2{r0.x, r0.y}, m0.im));
+                ff_acc(bx, ff_mul(F2{r1.x, r1.y}, m1.re));
+                ff_acc(by, ff_mul(F2{r1.x, r1.y}, m1.im));
+            }
+            if (k <= l) {
+                const float2 r0 = Rr[k];
+                const C4 m0 = c4_unpack(src[k]);
+                ff_acc(ax, ff_mul(F2{r0.x, r0.y}, m0.re));
+                ff_acc(ay, ff_mul(F2{r0.x, r0.y}, m0.im));
+            }
+            const double zx = to_d(ax) + to_d(bx), zy = to_d(ay) + to_d(by);
+            const double2 e = ephq[l];
+            sh[c * nout + d * P + l] = make_double2(fma(zx, e.x, -zy * e.y), fma(zx, e.y, zy * e.x));
+        }
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += PF_T) {
+        const int d = o / P, l = o - d * P;
+        double ax = 0.0, ay = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            const double *Rv = mix + (size_t)(49 + (tv.key[c0 + c] & 3)) * nd * nd + d * nd;
+            for (int bb = 0; bb < nd; ++bb) {
+                const double r = Rv[bb];
+                if (r != 0.0) {
+                    const double2 v = sh[c * nout + bb * P + l];
+                    ax = fma(r, v.x, ax);
+                    ay = fma(r, v.y, ay);
+                }
+            }
+        }
+        mp[(size_t)b * nout + o] = make_double2(ax, ay);
+    }
+}
+
+// L2L for the parents of one level, as fmm.cu l2l64_kernel: the parent's local expansion
+// takes each child's phase e^{i th_q l} (FP64, split), passes through the real
+// upper-triangular core (row m: sum over l >= m) in float-float, takes e^{-i th_q m}, and
+// mixes through the frame changes into the child's local expansion (FP64).
+__global__ void __launch_bounds__(PF_T) l2l_ff_kernel(TreeView tv, int b0, int nd, int P, const float2 *R,
+                                                      const double2 *ph, const double *mix, double2 *lc) {
+    extern __shared__ float4 lf2_sm[];
+    const int b = b0 + blockIdx.x;
+    const int nc = tv.nchild[b];
+    if (nc == 0) return;
+    const int nout = nd * P, c0 = tv.child[b];
+    float4 *y = lf2_sm;
+    double2 *sh = reinterpret_cast<double2 *>(lf2_sm + 4 * nout);
+    for (int i = threadIdx.x; i < nc * nout; i += PF_T) {
+        const int c = i / nout, o = i - c * nout, l = o % P;
+        const double2 v = lc[(size_t)b * nout + o], e = ph[(size_t)(tv.key[c0 + c] & 3) * P + l];
+        y[i] = c4_pack(c4_of(make_double2(fma(v.x, e.x, -v.y * e.y), fma(v.x, e.y, v.y * e.x))));
+    }
+    __syncthreads();
+    const int half = (P + 1) / 2;
+    for (int it = threadIdx.x; it < nc * nd * half; it += PF_T) {
+        const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
+        const double2 *ephq = ph + (size_t)(tv.key[c0 + c] & 3) * P;
+        const float4 *src = y + c * nout + d * P;
+        for (int h = 0; h < 2; ++h) {
+            const int m = h == 0 ? p : P - 1 - p;
+            if (h == 1 && m == p) break;
+            const float2 *Rr = R + (size_t)m * P;
+            F2 ax{0.f, 0.f}, ay{0.f, 0.f}, bx{0.f, 0.f}, by{0.f, 0.f};
+            int l = m;
+            for (; l + 1 < P; l += 2) {
+                const float2 r0 = Rr[l], r1 = Rr[l + 1];
+                const C4 v0 = c4_unpack(src[l]), v1 = c4_unpack(src[l + 1]);
+                ff_acc(ax, ff_mul(F2{r0.x, r0.y}, v0.re));
+                ff_acc(ay, ff_mul(F2{r0.x, r0.y}, v0.im));
+                ff_acc(bx, ff_mul(F2{r1.x, r1.y}, v1.re));
+                ff_acc(by, ff_mul(F2{r1.x, r1.y}, v1.im));
+            }
+            if (l < P) {
+                const float2 r0 = Rr[l];
+                const C4 v0 = c4_unpack(src[l]);
+                ff_acc(ax, ff_mul(F2{r0.x, r0.y}, v0.re));
+                ff_acc(ay, ff_mul(F2{r0.x, r0.y}, v0.im));
+            }
+            const double zx = to_d(ax) + to_d(bx), zy = to_d(ay) + to_d(by);
+            const double2 e = ephq[m];
+            sh[c * nout + d * P + m] = make_double2(fma(zx, e.x, zy * e.y), fma(zy, e.x, -zx * e.y));
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < nc * nout; it += PF_T) {
+        const int c = it / nout, o = it - c * nout, a_ = o / P, m = o - a_ * P;
+        const double *Ru = mix + (size_t)(53 + (tv.key[c0 + c] & 3)) * nd * nd;
+        double2 acc = lc[(size_t)(c0 + c) * nout + o];
+        for (int l = 0; l < nd; ++l) {
+            const double r = Ru[l * nd + a_];
+            if (r != 0.0) {
+                const double2 v = sh[c * nout + l * P + m];
+                acc.x = fma(r, v.x, acc.x);
+                acc.y = fma(r, v.y, acc.y);
+            }
+        }
+        lc[(size_t)(c0 + c) * nout + o] = acc;
+    }
+}
+
 }  // namespace
+
+void m2m_ff_launch(const Fmm &f, const Tree &t, int b0, int nb, double2 *mp, cudaStream_t s) {
+    const size_t sm = (size_t)8 * f.nd * f.P * 16;  // [4][nd][P] float4 + [4][nd][P] double2
+    once_per_device(6, [] {
+        const int lim = 100 * 1024;
+        PHS_CUDA(cudaFuncSetAttribute(m2m_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        PHS_CUDA(cudaFuncSetAttribute(l2l_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    });
+    m2m_ff_kernel<<<nb, PF_T, sm, s>>>(tree_view(t), b0, f.nd, f.P, f.shift_rff.get(), f.shift_ph.get(), f.mix64.get(),
+                                       mp);
+    PHS_LAUNCH_CHECK();
+}
+
+void l2l_ff_launch(const Fmm &f, const Tree &t, int b0, int nb, double2 *lc, cudaStream_t s) {
+    const size_t sm = (size_t)8 * f.nd * f.P * 16;
+    once_per_device(6, [] {
+        const int lim = 100 * 1024;
+        PHS_CUDA(cudaFuncSetAttribute(m2m_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        PHS_CUDA(cudaFuncSetAttribute(l2l_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    });
+    l2l_ff_kernel<<<nb, PF_T, sm, s>>>(tree_view(t), b0, f.nd, f.P, f.shift_rff.get() + (size_t)f.P * f.P,
+                                       f.shift_ph.get(), f.mix64.get(), lc);
+    PHS_LAUNCH_CHECK();
+}
 
 void p2m_ff_launch(const Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, double2 *mp,
                    cudaStream_t s) {

@@ -1116,7 +1116,8 @@ static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_s
         PHS_LAUNCH_CHECK();
         for (int l = t.depth - 1; l >= 0; --l) {
             const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-            if (nb > 0)
+            if (nb > 0 && ff) m2m_ff_launch(f, t, b0, nb, mp, s);
+            else if (nb > 0)
                 m2m64_kernel<<<nb, UD_T, 8 * esz, s>>>(tv, b0, nd, P, f.shift_r.get(), f.shift_ph.get(), mix_buf<T>(f),
                                                        mp);
             PHS_LAUNCH_CHECK();
@@ -1154,7 +1155,7 @@ static void m2l_pass(Fmm &f, const Tree &t, typename C2T<T>::type *mp, typename 
 }
 template <typename T>
 static void downward(Fmm &f, const Tree &t, typename C2T<T>::type *lc, const typename C2T<T>::type *ops, int P,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool ff = false) {
     using C = typename C2T<T>::type;
     const size_t esz = (size_t)f.nd * P * sizeof(C);
     if constexpr (sizeof(T) == 8) {
@@ -1162,7 +1163,8 @@ static void downward(Fmm &f, const Tree &t, typename C2T<T>::type *lc, const typ
         // parents of levels 2 .. depth-1 pass their local expansions to levels 3 .. depth
         for (int l = 2; l < t.depth; ++l) {
             const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
-            if (nb > 0)
+            if (nb > 0 && ff) l2l_ff_launch(f, t, b0, nb, lc, s);
+            else if (nb > 0)
                 l2l64_kernel<<<nb, UD_T, 8 * esz, s>>>(tree_view(t), b0, f.nd, P, f.shift_r.get() + (size_t)P * P,
                                                        f.shift_ph.get(), mix_buf<T>(f), lc);
             PHS_LAUNCH_CHECK();
@@ -1198,7 +1200,7 @@ static void far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *t
     m2l_pass<T>(f, t, mp_buf<T>(f), lc_buf<T>(f), ops_buf<T>(f), P, s);
     if (tm) tm->end(T_M2L, s);
     if (tm) tm->begin(s);
-    downward<T>(f, t, lc_buf<T>(f), ops_buf<T>(f), P, s);
+    downward<T>(f, t, lc_buf<T>(f), ops_buf<T>(f), P, s, ff);
     if (tm) tm->end(T_DOWN, s);
 }
 
@@ -1357,10 +1359,13 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
                Timers *tm) {
     PHS_REQUIRE(mode >= 0 && mode <= 4, PHS_ERR_INVALID_ARG, "precision mode must be 0..4");
     PHS_REQUIRE(f.log_core || mode == 0 || mode == 4, PHS_ERR_INVALID_ARG, "odd spline orders run in precision 0 or 4");
-    // near field on the side stream (it writes y; the far field's L2P adds to y after the join)
+    // near field on the side stream (it writes y; the far field's L2P adds to y after the
+    // join).  With phase timing on it stays on s, so each phase's events time that phase
+    // alone; the arithmetic and its order are the same either way.
     p2p_prepare(f, t);
-    cudaStream_t ns = f.side ? f.side : s;
-    if (f.side) {
+    const bool fork = f.side && !(tm && tm->enabled);
+    cudaStream_t ns = fork ? f.side : s;
+    if (fork) {
         PHS_CUDA(cudaEventRecord(f.ev_fork, s));
         PHS_CUDA(cudaStreamWaitEvent(f.side, f.ev_fork, 0));
     }
@@ -1369,11 +1374,11 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
     else if (mode == 4) p2p_ff_dispatch(f, t, ps, t_sorted, y, ns);
     else p2p_dispatch<float>(f, f.k, t, ps, t_sorted, y, ns);
     if (tm) tm->end(T_P2P, ns);
-    if (f.side) PHS_CUDA(cudaEventRecord(f.ev_join, f.side));
+    if (fork) PHS_CUDA(cudaEventRecord(f.ev_join, f.side));
     if (!f.log_core) {
         // odd k: distance-kernel far field by Chebyshev interpolation in FP64
         cheb_far_field(f, t, ps, t_sorted, s, tm);
-        if (f.side) PHS_CUDA(cudaStreamWaitEvent(s, f.ev_join, 0));
+        if (fork) PHS_CUDA(cudaStreamWaitEvent(s, f.ev_join, 0));
         if (tm) tm->begin(s);
         cheb_l2p_apply(f, t, ps, y, s);
         if (tm) tm->end(T_DOWN, s);
@@ -1382,7 +1387,7 @@ void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted
     if (mode <= 1 || mode == 4) far_field<double>(f, t, ps, t_sorted, s, tm, mode == 4 && f.ff_passes);
     else if (mode == 2) far_field_m2l32(f, t, ps, t_sorted, s, tm);
     else far_field<float>(f, t, ps, t_sorted, s, tm);
-    if (f.side) PHS_CUDA(cudaStreamWaitEvent(s, f.ev_join, 0));
+    if (fork) PHS_CUDA(cudaStreamWaitEvent(s, f.ev_join, 0));
     if (tm) tm->begin(s);
     if (mode == 3) l2p_pass<float>(f, t, ps, y, s);
     else l2p_pass<double>(f, t, ps, y, s, mode == 4 && f.ff_passes);
@@ -1415,6 +1420,7 @@ struct DevTables {
     std::vector<double2> o64;
     std::vector<float2> o32;
     std::vector<double> R;    // [2][P][P]: M2M, L2L
+    std::vector<float2> Rff;  // the same split into hi + lo floats (float-float passes)
     std::vector<double2> ph;  // [4][P]: e^{i th_q k}
     std::vector<long double> re, im;  // the operators split for the tensor-core setup
 };
@@ -1437,6 +1443,7 @@ static const DevTables &dev_tables_cached(int P) {
         d.im[i] = ops[i].imag();
     }
     d.R.assign((size_t)2 * P * P, 0.0);
+    d.Rff.assign((size_t)2 * P * P, make_float2(0.f, 0.f));
     d.ph.resize((size_t)4 * P);
     for (int q = 0; q < 4; ++q) {
         const long double th = std::atan2((long double)((q & 2) ? 0.25L : -0.25L), (long double)((q & 1) ? 0.25L : -0.25L));
@@ -1456,7 +1463,11 @@ static const DevTables &dev_tables_cached(int P) {
                     PHS_REQUIRE(std::fabs(v.imag()) <= 1e-12L * std::max(mag, 1e-300L) + 1e-300L, PHS_ERR_INVALID_ARG,
                                 "shift operator does not factor through a real core");
                     double &dst = d.R[((size_t)t2 * P + r) * P + c2];
-                    if (q == 0) dst = (double)v.real();
+                    if (q == 0) {
+                        dst = (double)v.real();
+                        const float hi = (float)v.real();
+                        d.Rff[((size_t)t2 * P + r) * P + c2] = make_float2(hi, (float)(v.real() - (long double)hi));
+                    }
                     else
                         PHS_REQUIRE(std::fabs((long double)dst - v.real()) <= 1e-12L * std::max(mag, 1e-300L) + 1e-300L,
                                     PHS_ERR_INVALID_ARG, "shift cores differ between quadrants");
@@ -1490,7 +1501,10 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     PHS_CUDA(cudaMemcpyAsync(f.ops32p.get(), o32p.data(), o32p.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     f.shift_r.alloc(dt.R.size());
     f.shift_ph.alloc(dt.ph.size());
+    f.shift_rff.alloc(dt.Rff.size());
     PHS_CUDA(cudaMemcpyAsync(f.shift_r.get(), dt.R.data(), dt.R.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    PHS_CUDA(cudaMemcpyAsync(f.shift_rff.get(), dt.Rff.data(), dt.Rff.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                             s));
     PHS_CUDA(cudaMemcpyAsync(f.shift_ph.get(), dt.ph.data(), dt.ph.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     {
         const auto &mx = mix_cached(f.power, f.nd);

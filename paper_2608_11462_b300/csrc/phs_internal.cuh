@@ -234,6 +234,7 @@ struct Fmm {
     // the real shift cores [2][P][P] (M2M, L2L) and the phases e^{i th_q k} [4][P]
     DBuf<double> shift_r;
     DBuf<double2> shift_ph;
+    DBuf<float2> shift_rff;  // shift_r split into hi + lo floats
     DBuf<float2> ops32;   // same for the FP32 order P32
     DBuf<float2> ops32p, mpx32, lcx32;  // FP32 copies at the FP64 order (FP32 M2L mode)
     DBuf<double> mix64;                 // box-local Hadamard frame changes [57][nd][nd]
@@ -309,11 +310,15 @@ void upload_ff_tables();
 void p2m_ff_launch(const Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, double2 *mp,
                    cudaStream_t s);
 void l2p_ff_launch(const Fmm &f, const Tree &t, const PointSet &ps, const double2 *lc, double *y, cudaStream_t s);
+// float-float M2M (parents b0 .. b0+nb-1 from their children's mp) and L2L (those parents
+// into their children's lc); the phases and frame changes in FP64, the triangular core
+// in float-float
+void m2m_ff_launch(const Fmm &f, const Tree &t, int b0, int nb, double2 *mp, cudaStream_t s);
+void l2l_ff_launch(const Fmm &f, const Tree &t, int b0, int nb, double2 *lc, cudaStream_t s);
 // y = M' t for sorted-order vectors in the normalised frame (M' of the normalised points)
 // mode 0: FP64 throughout; 1: FP32 near field + FP64 far field; 2: FP32 near field and
 // FP32 M2L inside FP64 upward/downward passes; 3: FP32 throughout (order p32);
-// 4: float-float near field, P2M and L2P on the FP32 pipe + FP64 M2M/M2L/L2L (M2L as
-//    configured)
+// 4: float-float near field, P2M, M2M, L2L and L2P on the FP32 pipe + M2L as configured
 void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted, int mode,
                cudaStream_t s, struct Timers *tm);
 // evaluate sum_j w_j phi(|x_j - y|) at normalised targets (after an FMM upward/downward
