@@ -34,14 +34,15 @@ WORKLOAD = "tps_1m"
 # (0.01-0.03 are equal; at 0.003 and below the local covariances need jitter and the
 # count rises).  nu = 1.5 fails to converge within 200 iterations for alpha in {5, 20, 60}.
 NU, ALPHA = 1.0, 0.03
+TUNE_SEED = 2002  # --case tune: the alpha search runs on this draw of the recipe
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/p2p_sym_kernel_tps_262k.md and profiles/m2l_tc_kernel_tps_262k.md, taken on the
 # n = 262144 case of this workload at leaf capacity 96 and scaled to the bench size: the
 # tensor-core M2L by its tile count (408 tiles there), the near field by the point count.
 M2L_DRAM_BYTES_PER_TILE = (21.427712e6 + 21.76e3) / 408
 P2P_DRAM_BYTES_PER_POINT = (6.951936e6 + 512) / 262144
-# the float-float near field (precision 4): not captured yet
-P2P_FF_DRAM_BYTES_PER_POINT = None
+# the float-float near field (precision 4): profiles/p2p_sym_ff_kernel_tps_262k.md
+P2P_FF_DRAM_BYTES_PER_POINT = (6.909696e6 + 256) / 262144
 
 
 def workload_config(args, n, m_t, fmm_order, world):
@@ -83,14 +84,16 @@ def parse():
     ap.add_argument("--n-max", type=int, default=500_000, help="serving case: largest request")
     ap.add_argument("--jobs", type=int, default=64, help="batch case: number of jobs")
     ap.add_argument("--case", default="step", choices=["step", "plan", "matvec", "precond", "cubic", "serving",
-                                                       "batch"],
+                                                       "batch", "tune"],
                     help="step: the bench (plan + fit + evaluation, the JSON contract line); plan / "
                          "matvec / precond: one piece of it repeated --steps times on one plan, for "
                          "profiling; cubic: the cubic-PHS workload (n = 100,000 from 20 clusters, "
                          "k = 3, m = 20, library defaults, tol 1e-8) timed like a step; serving: the "
                          "serving engine on a stream of requests with Poisson arrivals (n log-uniform in "
                          "[1000, --n-max], k in 1..3) against the same stream served one job at a time "
-                         "(each of these prints its own short line)")
+                         "(each of these prints its own short line); tune: phs_tune_alpha on the bench "
+                         "workload (all points) for nu = 1 and nu = 1.5 from the library's default alpha, "
+                         "then a fit at the alpha found")
     return ap.parse_args()
 
 
@@ -369,6 +372,33 @@ def main():
         if rank == 0:
             batch_case(args, phs)
         return
+    if args.case == "tune":
+        if rank == 0:
+            # the search runs on another draw of the same recipe, the fits on the bench's own
+            held = synth.workload(WORKLOAD, n=n, seed=TUNE_SEED)
+            hp, hf = torch.tensor(held["points"], device=dev), torch.tensor(held["f"], device=dev)
+            out = {"case": "tune", "workload": WORKLOAD, "n": n, "vecchia_m": 30, "tol": 1e-8,
+                   "search_on": f"{WORKLOAD} drawn with seed {TUNE_SEED}", "runs": []}
+            for nu in (NU, 1.5):
+                o = phs.options(2, tol=1e-8, nu=nu, leaf_cap=args.leaf_cap, ordering=args.ordering, maxiter=200)
+                a0 = o.alpha
+                t0 = time.perf_counter()
+                a, it_tune = phs.phs_tune_alpha(hp, hf, 2, vecchia_m=30, opts=o, n_sample=n)
+                t_tune = time.perf_counter() - t0
+                run = {"nu": nu, "alpha_start": a0, "alpha": a, "iters_in_search": it_tune, "s_search": t_tune}
+                for tag, al in (("at_alpha", a), ("at_default", a0), ("at_bench_alpha", ALPHA)):
+                    o2 = phs.options(2, tol=1e-8, nu=nu, alpha=al, leaf_cap=args.leaf_cap, ordering=args.ordering,
+                                     maxiter=200)
+                    plan = phs.Plan(pts_d, 2, fmm_order=0, vecchia_m=30, opts=o2)
+                    try:
+                        _, _, info = plan.fit(f_d)
+                        run[tag] = {"alpha": al, "iters": info["iters"], "rel_res_true": info["rel_res_true"]}
+                    except phs.PhsError as e:
+                        run[tag] = {"alpha": al, "error": str(e)}
+                    plan.close()
+                out["runs"].append(run)
+            print(json.dumps(out))
+        return
     if args.case != "step":
         # one piece of the step on the bench workload, for profilers; no timing contract
         reps = max(1, args.steps)
@@ -559,6 +589,9 @@ def main():
                 "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"], "ms_fit": info["ms_fit"],
                 "ms_matvec_avg": info["ms_matvec_avg"]},
         "phases_ms_per_step": {k_: v[0] / args.steps for k_, v in agg.items()},
+        "phases_note": "the timed steps run with phase timing on, which keeps the near field on the plan's "
+                       "stream (without timing it overlaps the upward pass and M2L on a second stream), so "
+                       "each phase's events time that phase alone",
         **({"fp64_comparison": fp64_cmp} if fp64_cmp else {}),
         "fmm_throughput": fmm,
         "roofline": roof, **roof_other, "roofline_precond": pre, "clocks": clk, "gpu_launches": int(launches),

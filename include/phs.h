@@ -269,7 +269,9 @@ phs_status phs_plan_kernel_work(phs_plan_t plan, int64_t *counts_host);
  * ns = 0 restore normal operation. */
 phs_status phs_plan_set_wait_limit(phs_plan_t plan, int64_t ns, int probe);
 /* Per-phase device timing of the most recent phs_fit / phs_matvec calls, in ms,
- * measured with CUDA events on the plan's stream when enabled (0/1).
+ * measured with CUDA events on the plan's stream when enabled (0/1).  While enabled the
+ * near field runs on the plan's stream instead of beside the far field on a second
+ * stream, so each phase's events time that phase alone (results are bit-identical).
  * ms_host[0..7] = (p2p, m2l, upward, downward, precond, vector, eval, total);
  * calls_host[0..7] = launches timed per phase. */
 phs_status phs_plan_set_timing(phs_plan_t plan, int enabled);

@@ -921,16 +921,20 @@ int refine_inner_maxiter(const phs_options &o, int iters_done) {
 
 // The end of a fit from x (work vector 9) and f (work vector 7): beta from
 // R beta = Q'(f - M' x) (Eq. 2.5), the true residual ||P (f - M' x)||^2 (returned), and
-// w = rho^k x in caller order; synchronises s.
-double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s) {
+// w = rho^k x in caller order; synchronises s.  After a refinement step on the same x
+// (refined = true) work vector 10 already holds M' x - f from that step's FP64 matvec,
+// the same product bit for bit, and it is not formed again.
+double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s, bool refined) {
     const int64_t n = pl->ps.n;
     double *fs = W(pl, 7), *x = W(pl, 9), *y = W(pl, 10), *d = W(pl, 11);
     double *sc = pl->scal.get();
     // the low-rank preconditioner keeps the iterates in range(P) only up to rounding
     if (pl->lowrank) project(pl, x, 1.0, x, nullptr, nullptr, s);
-    matvec_norm(pl, x, y, 0, s);
-    sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, fs, y, n);
-    PHS_LAUNCH_CHECK();
+    if (!refined || pl->lowrank) {
+        matvec_norm(pl, x, y, 0, s);
+        sub_k<<<blocks_for(n, 256), 256, 0, s>>>(y, fs, y, n);
+        PHS_LAUNCH_CHECK();
+    }
     qt_partial<<<RED_B, RED_T, 0, s>>>(pl->Q.get(), pl->S, n, y, pl->part.get());
     PHS_LAUNCH_CHECK();
     dots_final<<<pl->S, RED_T, 0, s>>>(pl->part.get(), RED_B, sc + 40);
@@ -1180,7 +1184,7 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
             if (it == 0) break;
         }
     }
-    const double rr_true = fit_end(pl, w_dev, beta_dev, s);
+    const double rr_true = fit_end(pl, w_dev, beta_dev, s, outer > 0);
     int n_mv = 0;
     const double ms_mv = mvt.resolve(&n_mv);
     m2l_tc_check(pl->fmm, s);

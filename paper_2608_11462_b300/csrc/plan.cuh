@@ -73,7 +73,7 @@ struct FitStart {
     bool trivial;             // P f vanishes to rounding: w = 0 (x already zeroed)
 };
 FitStart fit_begin(phs_plan *pl, const double *f_dev, cudaStream_t s);
-double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s);
+double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s, bool refined);
 // refinement (precision 1-4): x = 0, d = rhs; one step x += dx, d = sign P(f - M' x) in
 // FP64, returning ||d||; the inner solves run PCG with rhs = work vector 11, x = 8
 void fit_refine_begin(phs_plan *pl, cudaStream_t s);

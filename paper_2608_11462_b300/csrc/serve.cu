@@ -292,7 +292,7 @@ void phs_server::finish(Job *j) {
             phs_plan *pl = j->pl;
             AllocScope scope(j->s, &pl->dev_bytes);
             pl->last_stream = j->s;
-            const double rr_true = fit_end(pl, j->w_d(), j->beta_d(), j->s);
+            const double rr_true = fit_end(pl, j->w_d(), j->beta_d(), j->s, j->outer > 0);
             if (j->m) {
                 const phs_status st = phs_eval(j->pl, j->w_d(), j->beta_d(), j->tgt_d(), j->m, j->pred_d(),
                                                (phs_stream_t)j->s);

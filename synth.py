@@ -78,11 +78,12 @@ def f_sec32(p: np.ndarray) -> np.ndarray:
     return np.cos(30 * x + 0.8) * np.sin(30 * y - 2.1) + 5 * np.exp(-5 * np.sqrt((x - 0.25) ** 2 + (y - 0.75) ** 2))
 
 
-def workload(name: str, n: int | None = None, n_targets: int | None = None):
+def workload(name: str, n: int | None = None, n_targets: int | None = None, seed: int | None = None):
     """Return dict(points, f, targets, k, meta) for a named workload.  `n`
-    overrides the point count (same recipe), for scaled-down parity cases."""
+    overrides the point count (same recipe), for scaled-down parity cases; `seed`
+    overrides the recipe's seed (another draw of the same workload)."""
     if name == "uniform_tps":
-        seed = 1000
+        seed = 1000 if seed is None else seed
         n = 1500 if n is None else n
         nt = 500 if n_targets is None else n_targets
         rng = np.random.default_rng(seed)
@@ -90,7 +91,7 @@ def workload(name: str, n: int | None = None, n_targets: int | None = None):
         f = f_uniform_tps(pts)
         k = 2
     elif name == "cubic_mix":
-        seed = 1001
+        seed = 1001 if seed is None else seed
         n = 100_000 if n is None else n
         nt = 1000 if n_targets is None else n_targets
         rng = np.random.default_rng(seed)
@@ -98,7 +99,7 @@ def workload(name: str, n: int | None = None, n_targets: int | None = None):
         f = bump_field(rng)(pts)
         k = 3
     elif name == "tps_1m":
-        seed = 1002
+        seed = 1002 if seed is None else seed
         n = 1_048_576 if n is None else n
         nt = 10_000 if n_targets is None else n_targets
         rng = np.random.default_rng(seed)
