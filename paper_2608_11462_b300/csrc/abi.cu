@@ -991,9 +991,10 @@ static int autotune_leaf_cap(int k, int64_t n, const phs_options &o, cudaStream_
         phs_plan_t pl = nullptr;
         if (phs_plan_create(pts.get(), nt, k, -1, 0, 1, &ot, (phs_stream_t)s, &pl) != PHS_OK) continue;
         float ms = 0;
-        bool ok = phs_matvec(pl, t.get(), y.get(), o.precision == 4 ? 4 : 0, (phs_stream_t)s) == PHS_OK;
+        const int mp = o.precision == 4 && k % 2 == 0 ? 4 : 0;  // the operator the fit iterates with
+        bool ok = phs_matvec(pl, t.get(), y.get(), mp, (phs_stream_t)s) == PHS_OK;
         PHS_CUDA(cudaEventRecord(e0, s));
-        for (int r = 0; r < 2 && ok; ++r) ok = phs_matvec(pl, t.get(), y.get(), o.precision == 4 ? 4 : 0, (phs_stream_t)s) == PHS_OK;
+        for (int r = 0; r < 2 && ok; ++r) ok = phs_matvec(pl, t.get(), y.get(), mp, (phs_stream_t)s) == PHS_OK;
         PHS_CUDA(cudaEventRecord(e1, s));
         PHS_CUDA(cudaEventSynchronize(e1));
         PHS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -1161,21 +1162,22 @@ phs_status phs_fit(phs_plan_t pl, const double *f_dev, double *w_dev, double *be
     bool converged = false;
     if (st.trivial) {
         converged = true;
-    } else if (o.precision == 0) {
+    } else if (fit_precision(pl) == 0) {
         iters = pcg(pl, rhs, x, stop, o.maxiter, 0, &rr, s, &mvt);
         converged = std::sqrt(rr) <= stop;
     } else {
         // FP64 iterative refinement around inner PCG solves with the reduced-precision
         // operator.  Modes 1-3 (plain FP32 pieces) solve each correction to inner_tol;
-        // mode 4 (float-float near field) is accurate enough that its first inner solve
-        // aims at the final tolerance, and refinement only mops up what the operator's
-        // rounding leaves in the true residual.
+        // mode 4 (float-float) is accurate enough that its first inner solve aims at the
+        // final tolerance; if the FP64 residual still misses it, the corrections run with
+        // the FP64 operator (inner_precision).
         fit_refine_begin(pl, s);
         double res = nrm0;
         while (outer < o.max_refine && iters < o.maxiter) {
             double rri = 0;
             const double itol = refine_inner_tol(o, res, stop);
-            int it = pcg(pl, W(pl, 11), W(pl, 8), itol, refine_inner_maxiter(o, iters), o.precision, &rri, s, &mvt);
+            int it = pcg(pl, W(pl, 11), W(pl, 8), itol, refine_inner_maxiter(o, iters), inner_precision(pl, outer), &rri,
+                         s, &mvt);
             iters += it;
             ++outer;
             res = fit_refine_step(pl, s);

@@ -78,6 +78,18 @@ double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s, bo
 // FP64, returning ||d||; the inner solves run PCG with rhs = work vector 11, x = 8
 void fit_refine_begin(phs_plan *pl, cudaStream_t s);
 double fit_refine_step(phs_plan *pl, cudaStream_t s);
+// The arithmetic a fit runs in.  Precision 4 with odd k solves with the FP64 operator:
+// the distance-kernel far field (FP64) dominates there, so the float-float near field
+// saves under a tenth of a matvec, less than the Krylov restart a refinement step costs
+// on those ill-conditioned systems.
+inline int fit_precision(const phs_plan *pl) { return pl->opt.precision == 4 && pl->k % 2 ? 0 : pl->opt.precision; }
+// The operator of a refinement's inner solve: precision 4 runs its first solve in
+// float-float; when the FP64 residual check after it fails, the operator's rounding is
+// what remains, so the corrections use the FP64 operator.  Modes 1-3 keep theirs.
+inline int inner_precision(const phs_plan *pl, int outer) {
+    const int fp = fit_precision(pl);
+    return fp == 4 && outer > 0 ? 0 : fp;
+}
 double refine_inner_tol(const phs_options &o, double res, double stop);
 int refine_inner_maxiter(const phs_options &o, int iters_done);
 

@@ -66,6 +66,8 @@ struct Job {
     // the iteration's per-job work captured once: y = M' p (FMM) and t2 = S~^-1 r (Vecchia)
     cudaGraphExec_t g_mv = nullptr, g_pc = nullptr;
     int64_t n_mv_kernels = 0, n_pc_kernels = 0;
+    int mv_prec = 0;          // the current solve's operator (fit_precision / inner_precision)
+    int g_mv_prec = -1;       // the operator g_mv was captured with
     phs_fit_info info{};
     double *pts_d() { return dbuf; }
     double *f_d() { return dbuf + 2 * n; }
@@ -88,12 +90,14 @@ int64_t estimate_bytes(int64_t n, int64_t m, int vm) {
 void start_solve(Job *j) {
     phs_plan *pl = j->pl;
     const phs_options &o = pl->opt;
-    if (o.precision == 0) {
+    if (fit_precision(pl) == 0) {
+        j->mv_prec = 0;
         j->rhs_p = W(pl, 8);
         j->x_p = W(pl, 9);
         j->itol = j->st.stop;
         j->imax = o.maxiter;
     } else {
+        j->mv_prec = inner_precision(pl, j->outer);
         j->rhs_p = W(pl, 11);
         j->x_p = W(pl, 8);
         j->itol = refine_inner_tol(o, std::sqrt(j->rr), j->st.stop);
@@ -193,14 +197,15 @@ void phs_server::setup(Job *j) {
         pl->last_stream = j->s;
         j->st = fit_begin(pl, j->f_d(), j->s);
         if (!j->st.trivial) {
-            if (j->opt.precision != 0) fit_refine_begin(pl, j->s);
+            if (fit_precision(pl) != 0) fit_refine_begin(pl, j->s);
             j->rr = j->st.nrm0 * j->st.nrm0;
             start_solve(j);
             // one uncaptured matvec sizes every lazily allocated buffer (its output, work
             // vector 4, is overwritten by the first tick); then both pieces are captured
-            const int prec = j->opt.precision;
+            const int prec = j->mv_prec;
             matvec_norm(pl, W(pl, 2), W(pl, 4), prec, j->s);
             j->g_mv = capture(j->s, &j->n_mv_kernels, [&] { matvec_norm(pl, W(pl, 2), W(pl, 4), prec, j->s); });
+            j->g_mv_prec = prec;
             j->g_pc = capture(j->s, &j->n_pc_kernels,
                               [&] { vecchia_apply(pl->vec, W(pl, 0), W(pl, 5), W(pl, 6), j->s); });
             PHS_CUDA(cudaStreamSynchronize(j->s));
@@ -219,8 +224,8 @@ void phs_server::setup(Job *j) {
             work.push_back(j);
             cv_work.notify_one();
         } else if (solve_ended(j)) {
-            j->state = j->opt.precision == 0 ? J_FINISH : J_REFINE;
-            if (j->opt.precision == 0) j->converged = true;
+            j->state = fit_precision(pl) == 0 ? J_FINISH : J_REFINE;
+            if (fit_precision(pl) == 0) j->converged = true;
             ++n_finish;
             work.push_back(j);
             cv_work.notify_one();
@@ -261,6 +266,13 @@ void phs_server::refine(Job *j) {
             j->converged = true;
         } else if (it_inner != 0 && j->outer < o.max_refine && j->iters < o.maxiter) {
             start_solve(j);
+            if (j->g_mv && j->g_mv_prec != j->mv_prec) {  // the corrections' operator differs
+                PHS_CUDA(cudaGraphExecDestroy(j->g_mv));
+                const int prec = j->mv_prec;
+                matvec_norm(pl, W(pl, 2), W(pl, 4), prec, j->s);
+                j->g_mv = capture(j->s, &j->n_mv_kernels, [&] { matvec_norm(pl, W(pl, 2), W(pl, 4), prec, j->s); });
+                j->g_mv_prec = prec;
+            }
             again = !solve_ended(j);
             if (!again) {  // the correction ended at once: refine again
                 std::lock_guard<std::mutex> g(mu);
@@ -309,7 +321,7 @@ void phs_server::finish(Job *j) {
                                          j->s));
             PHS_CUDA(cudaStreamSynchronize(j->s));
             const double nrm0 = j->st.nrm0;
-            j->info.iters = j->opt.precision == 0 ? j->it : j->iters;
+            j->info.iters = fit_precision(j->pl) == 0 ? j->it : j->iters;
             j->info.outer_iters = j->outer;
             j->info.converged = j->converged ? 1 : 0;
             j->info.jittered = (int)pl->vec.jittered;
@@ -385,7 +397,7 @@ void phs_server::tick(std::vector<Job *> &act) {
             PHS_CUDA(cudaGraphLaunch(j->g_mv, j->s));
             count_launches(j->n_mv_kernels);
         } else {
-            matvec_norm(pl, W(pl, 2), W(pl, 4), j->opt.precision, j->s);
+            matvec_norm(pl, W(pl, 2), W(pl, 4), j->mv_prec, j->s);
         }
         PHS_CUDA(cudaEventRecord(j->ev, j->s));
         PHS_CUDA(cudaStreamWaitEvent(engine, j->ev, 0));
@@ -402,7 +414,7 @@ void phs_server::tick(std::vector<Job *> &act) {
         j->rr = rr_host[i];
         ++j->it;
         if (solve_ended(j)) {
-            if (j->opt.precision == 0 && std::sqrt(j->rr) <= j->itol) j->converged = true;
+            if (fit_precision(j->pl) == 0 && std::sqrt(j->rr) <= j->itol) j->converged = true;
             done.push_back(j);
         } else {
             cont.push_back(j);
@@ -435,7 +447,7 @@ void phs_server::tick(std::vector<Job *> &act) {
     ev_put(ev_e);
     std::lock_guard<std::mutex> g(mu);
     for (Job *j : done) {
-        j->state = j->opt.precision == 0 ? J_FINISH : J_REFINE;
+        j->state = fit_precision(j->pl) == 0 ? J_FINISH : J_REFINE;
         act.erase(std::find(act.begin(), act.end(), j));
         ++n_finish;
         work.push_back(j);

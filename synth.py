@@ -147,15 +147,28 @@ def serving_requests(count: int, seed: int = 1004, n_lo: int = 1000, n_hi: int =
     return out
 
 
+def sobol(n: int, seed: int) -> np.ndarray:
+    """The first n points of a scrambled 2D Sobol sequence on [0,1]^2 (Sec. 3.3 samples
+    its points from a Sobol sequence)."""
+    import warnings
+
+    from scipy.stats import qmc
+
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")  # n need not be a power of two
+        return qmc.Sobol(d=2, scramble=True, seed=seed).random(n)
+
+
 def batch_jobs(count: int = 64, seed: int = 1003, n_lo: int = 2000, n_hi: int = 200_000, n_targets: int = 100):
-    """Independent higher-order jobs: k in {4, 5} (quadratic block), n log-uniform in
-    [n_lo, n_hi], uniform or clustered geometry per job, the Franke function."""
+    """Independent higher-order jobs as in Sec. 3.3: k in {4, 5} (quadratic block), n
+    log-uniform in [n_lo, n_hi], points from a scrambled Sobol sequence on [0,1]^2 (one
+    scramble per job), the Franke function, n_targets uniform targets."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
         n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
         k = int(rng.integers(4, 6))
-        pts = _geometry(n, bool(rng.integers(0, 2)), rng)
+        pts = sobol(n, int(rng.integers(0, 2**31)))
         out.append({"points": np.ascontiguousarray(pts), "f": franke(pts), "targets": uniform(n_targets, rng),
                     "k": k})
     return out

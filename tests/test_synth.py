@@ -57,3 +57,14 @@ def test_request_streams():
     assert all(j["k"] in (4, 5) and 2000 <= len(j["f"]) <= 20_000 for j in jobs)
     t = synth.poisson_arrivals(2000, 10.0, seed=1)
     assert np.all(np.diff(t) > 0) and abs(t[-1] / 2000 - 0.1) < 0.01
+
+
+def test_sobol_points_form_a_net():
+    """Scrambled 2D Sobol points (the Sec. 3.3 samples): the first 2^10 form a (0, 10, 2)-net
+    in base 2, so every 32 x 32 grid cell (volume 2^-10) holds exactly one point."""
+    p = synth.sobol(1024, seed=5)
+    assert p.shape == (1024, 2) and np.all((p >= 0) & (p < 1))
+    cell = np.floor(p * 32).astype(int)
+    counts = np.zeros((32, 32), int)
+    np.add.at(counts, (cell[:, 0], cell[:, 1]), 1)
+    assert np.all(counts == 1)
