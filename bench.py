@@ -71,7 +71,8 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the point count (smaller parity runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true",
-                    help="with --precision != 0, skip timing the plain FP64 solve beside it")
+                    help="skip timing the other arithmetic beside the line (FP64 beside --precision 4, "
+                         "precision 4 beside FP64)")
     ap.add_argument("--leaf-cap", type=int, default=96,
                     help="quadtree leaf capacity (96 measured best on this workload: 48 / 64 / 80 / 96 / "
                          "112 gave 0.429 / 0.344 / 0.327 / 0.323 / 0.331 s per solve)")
@@ -227,14 +228,18 @@ def serve_stream(phs, reqs, arrivals, max_active, threads=4):
             "converged": int(sum(r[3]["converged"] for r in res)),
             "max_true_rel_res": float(max(r[3]["rel_res_true"] for r in res)),
             "max_concurrent": st["max_concurrent"], "ticks": st["ticks"],
-            "mean_jobs_per_tick": st["job_iterations"] / max(st["ticks"], 1)}
+            "mean_jobs_per_tick": st["job_iterations"] / max(st["ticks"], 1),
+            "not_converged": [{"n": len(q["f"]), "k": q["k"], "iters": r[3]["iters"],
+                               "rel_res_true": r[3]["rel_res_true"]}
+                              for q, r in zip(reqs, res) if not r[3]["converged"]]}
 
 
 def batch_case(args, phs):
     """Config-4 style batch: k = 4 / 5 jobs (Franke function, n log-uniform in [2000,
-    200000], uniform or clustered per job) at tol 1e-8 with the float-float near field
-    inside FP64 refinement and autotuned leaf capacity, all submitted at once to the
-    engine (one tick advances every active job), against the same jobs one at a time."""
+    200000], Sobol points as in Sec. 3.3) at tol 1e-8 in precision 4 (float-float inside
+    FP64 refinement for k = 4, the FP64 operator for k = 5) and autotuned leaf capacity,
+    all submitted at once to the engine (one tick advances every active job), against
+    the same jobs one at a time."""
     import numpy as np
 
     import synth
@@ -257,7 +262,15 @@ def batch_case(args, phs):
                 "max_true_rel_res": float(max(r[3]["rel_res_true"] for r in res)),
                 "iters_mean": float(np.mean([r[3]["iters"] for r in res])),
                 "max_concurrent": st["max_concurrent"], "ticks": st["ticks"],
-                "mean_jobs_per_tick": st["job_iterations"] / max(st["ticks"], 1)}
+                "mean_jobs_per_tick": st["job_iterations"] / max(st["ticks"], 1),
+                "by_k": {str(k): {"converged": sum(1 for j, r in zip(js, res) if j["k"] == k and r[3]["converged"]),
+                                  "jobs": sum(1 for j in js if j["k"] == k),
+                                  "largest_n_converged": max([len(j["f"]) for j, r in zip(js, res)
+                                                              if j["k"] == k and r[3]["converged"]], default=0),
+                                  "smallest_n_not_converged": min([len(j["f"]) for j, r in zip(js, res)
+                                                                   if j["k"] == k and not r[3]["converged"]],
+                                                                  default=0)}
+                         for k in (4, 5)}}
 
     # warm-up: one job per (k, floor(log2 n)) fills the leaf-capacity tuner and the
     # operator caches that the timed runs then share
@@ -463,27 +476,39 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
 
-    # ---- the plain FP64 solve on the same workload, beside a mixed-precision line
-    fp64_cmp = None
-    if args.precision != 0 and not args.no_fp64_compare:
-        o64 = phs.options(2, precision=0, tol=1e-8, nu=NU, alpha=ALPHA, leaf_cap=args.leaf_cap,
-                          ordering=args.ordering)
-        t64, i64 = [], None
+    # ---- the other arithmetic on the same workload: beside a precision-4 line the plain
+    # FP64 solve, beside the FP64 line the precision-4 solve (float-float bulk inside FP64
+    # refinement; its true residual is checked with the FP64 operator).  Untimed steps
+    # for the headline; each timed with events like a step, the first of three dropped.
+    def other_solve(prec):
+        oo = phs.options(2, precision=prec, tol=1e-8, nu=NU, alpha=ALPHA, leaf_cap=args.leaf_cap,
+                         ordering=args.ordering)
+        ts, inf = [], None
         for i in range(3):
             flush.zero_()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            p64 = phs.Plan(pts_d, 2, fmm_order=0, vecchia_m=30, opts=o64)
-            w64, b64, i64 = p64.fit(f_d)
-            p64.eval(w64, b64, tg_d)
+            po = phs.Plan(pts_d, 2, fmm_order=0, vecchia_m=30, opts=oo)
+            wo, bo, inf = po.fit(f_d)
+            po.eval(wo, bo, tg_d)
             e1.record(stream)
             barrier()
-            p64.close()
+            po.close()
             if i > 0:
-                t64.append(e0.elapsed_time(e1) / 1e3)
-        fp64_cmp = {"fp64_step_s": float(np.mean(t64)), "fp64_iters": i64["iters"],
-                    "fp64_rel_res_true": i64["rel_res_true"], "speedup_vs_fp64": float(np.mean(t64)) / t_step}
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        return float(np.mean(ts)), inf
+
+    fp64_cmp = None
+    if args.precision != 0 and not args.no_fp64_compare:
+        t64, i64 = other_solve(0)
+        fp64_cmp = {"fp64_step_s": t64, "fp64_iters": i64["iters"], "fp64_rel_res_true": i64["rel_res_true"],
+                    "speedup_vs_fp64": t64 / t_step}
+    elif args.precision == 0 and not args.no_fp64_compare:
+        t4, i4 = other_solve(4)
+        fp64_cmp = {"precision4_step_s": t4, "precision4_iters": i4["iters"],
+                    "precision4_outer_iters": i4["outer_iters"], "precision4_rel_res_true": i4["rel_res_true"],
+                    "precision4_speedup": t_step / t4}
 
     # ---- end to end from host buffers through the C ABI
     e2e_times = []
@@ -593,7 +618,7 @@ def main():
         "phases_note": "the timed steps run with phase timing on, which keeps the near field on the plan's "
                        "stream (without timing it overlaps the upward pass and M2L on a second stream), so "
                        "each phase's events time that phase alone",
-        **({"fp64_comparison": fp64_cmp} if fp64_cmp else {}),
+        **({("fp64_comparison" if args.precision != 0 else "precision4_comparison"): fp64_cmp} if fp64_cmp else {}),
         "fmm_throughput": fmm,
         "roofline": roof, **roof_other, "roofline_precond": pre, "clocks": clk, "gpu_launches": int(launches),
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(16 * n + 8 * n + 16 * m_t),

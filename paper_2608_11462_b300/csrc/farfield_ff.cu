@@ -10,16 +10,18 @@
 // pairwise noise the preconditioned system amplifies.
 //
 // P2M, per leaf: z_j = (x_j - c)/w, q_{d,j} = v_d(z_j) t_j; a~_0 = sum_j q, a~_k = -sum_j q
-// z^k / k.  Points in chunks of 64: four threads per point build the powers z^k (a
-// quarter each, started by binary powering) into shared memory, then each thread owns
-// outputs (d, k) and sums over the chunk.
+// z^k / k.  Points in chunks of 64: one thread per point forms z (FP64, then split) and
+// the charges (float-float), four threads per point build the powers z^k (a quarter
+// each, started by binary powering) into shared memory, then each thread owns outputs
+// (d, k) and sums over the chunk.  FP64 work is a few instructions per point: the FP64
+// pipe has 1/64 of the FP32 pipe's rate on this part.
 // L2P, per point of a leaf: y += sum_d u_d(v) Re sum_k b~_{d,k} v^k, v = (x - c)/w, the
-// leaf's coefficients split once into hi + lo in shared memory.
+// leaf's coefficients split once into hi + lo in shared memory, the Hadamard factors
+// and the combination in float-float.
 #include <algorithm>
 
 #include "ff.cuh"
 #include "geom.cuh"
-#include "hadamard.cuh"
 #include "phs_internal.cuh"
 
 namespace phs {
@@ -31,12 +33,67 @@ constexpr int PF_OUT = 3;   // outputs per thread: nd P <= 768
 constexpr int LF_T = 128;   // L2P threads per leaf
 constexpr int kFfMaxNd = 10;
 
+// a b renormalised (|lo| <= ulp(hi) / 2), for products that feed further products
+__device__ __forceinline__ F2 ff_mulr(F2 a, F2 b) {
+    const F2 p = ff_mul(a, b);
+    return fast_two_sum(p.h, p.l);
+}
+// s a power of two: exact
+__device__ __forceinline__ F2 ff_scale(F2 a, float s) { return {a.h * s, a.l * s}; }
+
+// The Hadamard factors of hadamard.cuh (had_v, had_u) in float-float, from float-float
+// box-local coordinates; ND = 1, 4, 9 for the powers 0, 2, 4 of |x_i - x_j|.
+template <int ND>
+__device__ __forceinline__ void had_v_ff(F2 x, F2 y, F2 *v) {
+    const F2 one{1.f, 0.f};
+    v[0] = one;
+    if constexpr (ND == 4) {
+        v[1] = ff_add(ff_mulr(x, x), ff_mulr(y, y));
+        v[2] = x;
+        v[3] = y;
+    } else if constexpr (ND == 9) {
+        const F2 xx = ff_mulr(x, x), yy = ff_mulr(y, y), a = ff_add(xx, yy);
+        v[1] = ff_mulr(a, a);
+        v[2] = x;
+        v[3] = y;
+        v[4] = ff_mulr(a, x);
+        v[5] = ff_mulr(a, y);
+        v[6] = xx;
+        v[7] = ff_mulr(x, y);
+        v[8] = yy;
+    }
+}
+template <int ND>
+__device__ __forceinline__ void had_u_ff(F2 x, F2 y, F2 *u) {
+    const F2 one{1.f, 0.f};
+    if constexpr (ND == 1) {
+        u[0] = one;
+    } else if constexpr (ND == 4) {
+        u[0] = ff_add(ff_mulr(x, x), ff_mulr(y, y));
+        u[1] = one;
+        u[2] = ff_scale(x, -2.f);
+        u[3] = ff_scale(y, -2.f);
+    } else {
+        const F2 xx = ff_mulr(x, x), yy = ff_mulr(y, y), a = ff_add(xx, yy);
+        u[0] = ff_mulr(a, a);
+        u[1] = one;
+        u[2] = ff_scale(ff_mulr(a, x), -4.f);
+        u[3] = ff_scale(ff_mulr(a, y), -4.f);
+        u[4] = ff_scale(x, -4.f);
+        u[5] = ff_scale(y, -4.f);
+        u[6] = ff_add(ff_scale(xx, 4.f), ff_scale(a, 2.f));
+        u[7] = ff_scale(ff_mulr(x, y), 8.f);
+        u[8] = ff_add(ff_scale(yy, 4.f), ff_scale(a, 2.f));
+    }
+}
+
 template <int ND>
 __global__ void __launch_bounds__(PF_T) p2m_ff_kernel(TreeView tv, const int *leaf_box, const double2 *xs,
-                                                      const double *t, int power, int P, double2 *mp) {
+                                                      const double *t, int P, double2 *mp) {
     extern __shared__ float4 pf_sm[];
-    float4 *pw = pf_sm;                                          // [64][P] powers, hi + lo parts
-    float2 *qs = reinterpret_cast<float2 *>(pw + (size_t)64 * P);  // [64][ND] charges
+    float4 *pw = pf_sm;                                              // [64][P] powers, hi + lo parts
+    float4 *zs = pw + (size_t)64 * P;                                // [64] scaled coordinates
+    float2 *qs = reinterpret_cast<float2 *>(zs + 64);                // [64][ND] charges
     const int b = leaf_box[blockIdx.x];
     double cx, cy, w;
     box_geom(tv, b, cx, cy, w);
@@ -49,12 +106,26 @@ __global__ void __launch_bounds__(PF_T) p2m_ff_kernel(TreeView tv, const int *le
     for (int i = 0; i < PF_OUT; ++i) acc[i] = {F2{0.f, 0.f}, F2{0.f, 0.f}};
     for (int j0 = s; j0 < e; j0 += 64) {
         const int jn = min(64, e - j0);
-        {
+        // one thread per point: the scaled coordinates (FP64, then split) and the
+        // Hadamard charges v_d(z) t_j in float-float
+        if (threadIdx.x < jn) {
+            const double2 xj = xs[j0 + threadIdx.x];
+            const C4 z = c4_of(make_double2((xj.x - cx) * iw, (xj.y - cy) * iw));
+            zs[threadIdx.x] = c4_pack(z);
+            F2 v[ND];
+            had_v_ff<ND>(z.re, z.im, v);
+            const F2 tj = split_d(t[j0 + threadIdx.x]);
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const F2 qd = ff_mulr(v[d], tj);
+                qs[threadIdx.x * ND + d] = make_float2(qd.h, qd.l);
+            }
+        }
+        __syncthreads();
+        {  // four threads per point: powers z^k, a quarter of k each
             const int jp = threadIdx.x >> 2, q = threadIdx.x & 3;
             if (jp < jn) {
-                const double2 xj = xs[j0 + jp];
-                const double zx = (xj.x - cx) * iw, zy = (xj.y - cy) * iw;
-                const C4 z = c4_of(make_double2(zx, zy));
+                const C4 z = c4_unpack(zs[jp]);
                 C4 zk = {F2{1.f, 0.f}, F2{0.f, 0.f}}, base = z;
                 for (int e2 = q * Q; e2 > 0; e2 >>= 1) {
                     if (e2 & 1) zk = c4_mul(zk, base);
@@ -64,16 +135,6 @@ __global__ void __launch_bounds__(PF_T) p2m_ff_kernel(TreeView tv, const int *le
                 for (int k = q * Q; k < k1; ++k) {
                     pw[jp * P + k] = c4_pack(zk);
                     zk = c4_mul(zk, z);
-                }
-                if (q == 0) {
-                    double v[kFfMaxNd];
-                    had_v(power, zx, zy, v);
-                    const double tj = t[j0 + jp];
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        const F2 qd = split_d(v[d] * tj);
-                        qs[jp * ND + d] = make_float2(qd.h, qd.l);
-                    }
                 }
             }
         }
@@ -113,8 +174,8 @@ __global__ void __launch_bounds__(PF_T) p2m_ff_kernel(TreeView tv, const int *le
 }
 
 template <int ND>
-__global__ void __launch_bounds__(LF_T) l2p_ff_kernel(TreeView tv, const int *leaf_box, const double2 *xs, int power,
-                                                      int P, const double2 *lc, double *y) {
+__global__ void __launch_bounds__(LF_T) l2p_ff_kernel(TreeView tv, const int *leaf_box, const double2 *xs, int P,
+                                                      const double2 *lc, double *y) {
     extern __shared__ float4 lf_sm[];  // [ND][P] coefficients, hi + lo parts
     const int b = leaf_box[blockIdx.x];
     const int nout = ND * P;
@@ -126,13 +187,10 @@ __global__ void __launch_bounds__(LF_T) l2p_ff_kernel(TreeView tv, const int *le
     const int s = tv.start[b], e = tv.end[b];
     for (int j = s + threadIdx.x; j < e; j += LF_T) {
         const double2 xj = xs[j];
-        const double vx = (xj.x - cx) * iw, vy = (xj.y - cy) * iw;
-        double u[kFfMaxNd];
-        had_u(power, vx, vy, u);
+        const C4 v = c4_of(make_double2((xj.x - cx) * iw, (xj.y - cy) * iw));
         F2 acc[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc[d] = F2{0.f, 0.f};
-        const C4 v = c4_of(make_double2(vx, vy));
         C4 zk = {F2{1.f, 0.f}, F2{0.f, 0.f}};
         for (int k = 0; k < P; ++k) {
 #pragma unroll
@@ -143,10 +201,13 @@ __global__ void __launch_bounds__(LF_T) l2p_ff_kernel(TreeView tv, const int *le
             }
             zk = c4_mul(zk, v);
         }
-        double sum = 0.0;
+        // sum_d u_d(v) Re L_d(v) in float-float; one FP64 add into y
+        F2 u[ND];
+        had_u_ff<ND>(v.re, v.im, u);
+        F2 sum{0.f, 0.f};
 #pragma unroll
-        for (int d = 0; d < ND; ++d) sum = fma(u[d], to_d(acc[d]), sum);
-        y[j] += sum;
+        for (int d = 0; d < ND; ++d) ff_acc(sum, ff_mul(u[d], acc[d]));
+        y[j] += to_d(sum);
     }
 }
 
@@ -315,7 +376,7 @@ void p2m_ff_launch(const Fmm &f, const Tree &t, const PointSet &ps, const double
                    cudaStream_t s) {
     const int P = f.P, nd = f.nd;
     PHS_REQUIRE(nd * P <= PF_T * PF_OUT, PHS_ERR_INVALID_ARG, "float-float P2M: nd * P above 768");
-    const size_t sm = (size_t)64 * P * sizeof(float4) + (size_t)64 * nd * sizeof(float2);
+    const size_t sm = (size_t)64 * P * sizeof(float4) + 64 * sizeof(float4) + (size_t)64 * nd * sizeof(float2);
     once_per_device(5, [] {
         const int lim = 100 * 1024;
         PHS_CUDA(cudaFuncSetAttribute(p2m_ff_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -323,9 +384,9 @@ void p2m_ff_launch(const Fmm &f, const Tree &t, const PointSet &ps, const double
         PHS_CUDA(cudaFuncSetAttribute(p2m_ff_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     });
     const TreeView tv = tree_view(t);
-    if (nd == 4) p2m_ff_kernel<4><<<t.nleaf, PF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
-    else if (nd == 9) p2m_ff_kernel<9><<<t.nleaf, PF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
-    else p2m_ff_kernel<1><<<t.nleaf, PF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
+    if (nd == 4) p2m_ff_kernel<4><<<t.nleaf, PF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, P, mp);
+    else if (nd == 9) p2m_ff_kernel<9><<<t.nleaf, PF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, P, mp);
+    else p2m_ff_kernel<1><<<t.nleaf, PF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, P, mp);
     PHS_LAUNCH_CHECK();
 }
 
@@ -333,9 +394,9 @@ void l2p_ff_launch(const Fmm &f, const Tree &t, const PointSet &ps, const double
     const int P = f.P, nd = f.nd;
     const size_t sm = (size_t)nd * P * sizeof(float4);
     const TreeView tv = tree_view(t);
-    if (nd == 4) l2p_ff_kernel<4><<<t.nleaf, LF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), f.power, P, lc, y);
-    else if (nd == 9) l2p_ff_kernel<9><<<t.nleaf, LF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), f.power, P, lc, y);
-    else l2p_ff_kernel<1><<<t.nleaf, LF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), f.power, P, lc, y);
+    if (nd == 4) l2p_ff_kernel<4><<<t.nleaf, LF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), P, lc, y);
+    else if (nd == 9) l2p_ff_kernel<9><<<t.nleaf, LF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), P, lc, y);
+    else l2p_ff_kernel<1><<<t.nleaf, LF_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), P, lc, y);
     PHS_LAUNCH_CHECK();
 }
 
