@@ -363,20 +363,24 @@ def main():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             plan = phs.Plan(pc, 3, vecchia_m=20, opts=copts)
+            plan.set_timing(True)
             w, beta, info = plan.fit(fc)
             plan.eval(w, beta, tc)
             e1.record(stream)
             torch.cuda.synchronize(dev)
+            tim = plan.timing()
             plan.close()
             if i >= args.warmup:
-                res.append((e0.elapsed_time(e1) / 1e3, info))
+                res.append((e0.elapsed_time(e1) / 1e3, info, tim))
         if rank == 0:
             t = float(np.mean([r[0] for r in res]))
             info = res[-1][1]
             print(json.dumps({"case": "cubic", "workload": "cubic_mix", "n": len(wc["f"]), "k": 3, "vecchia_m": 20,
                               "precision": args.precision, "value_s": t, "steps": args.steps, "iters": info["iters"],
                               "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"],
-                              "ms_fit": info["ms_fit"], "ms_matvec_avg": info["ms_matvec_avg"]}))
+                              "ms_fit": info["ms_fit"], "ms_matvec_avg": info["ms_matvec_avg"],
+                              "phases_ms_per_call": {k_: (v[0] / v[1] if v[1] else 0.0)
+                                                     for k_, v in res[-1][2].items()}}))
         return
     if args.case == "serving":
         if rank == 0:

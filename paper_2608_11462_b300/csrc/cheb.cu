@@ -249,7 +249,7 @@ __global__ void cheb_compress(int b0, int nd, int qq, int rs, const double *V, c
     }
 }
 
-// L~_t[d][i] = sum over the V list of sum_j C[cls][i][j] (S[cls] W~_src)[d][j]
+// L~_t[d][i] = sum over the V list of sum_j C[cls][i][j] (S[cls] W~_src)[d][j]  (C stored as C')
 __global__ void cheb_m2l_lr(int b0, const int *v_off, const int *v_src, const unsigned char *v_cls, int nd, int rt,
                             int rs, const double *C, const double *mix, const double *Wc, double *Lc) {
     extern __shared__ double csm[];  // [nd][rs] source, then [nd][rs] mixed
@@ -271,9 +271,9 @@ __global__ void cheb_m2l_lr(int b0, const int *v_off, const int *v_src, const un
         }
         __syncthreads();
         if (i < rt) {
-            const double *Cc = C + ((size_t)v_cls[v] * rt + i) * rs;
+            const double *Cc = C + (size_t)v_cls[v] * rs * rt + i;  // C' [rs][rt]: coalesced over i
             for (int jj = 0; jj < rs; ++jj) {
-                const double cv = Cc[jj];
+                const double cv = Cc[(size_t)jj * rt];
                 for (int d = 0; d < nd; ++d) acc[d] = fma(cv, wmx[d * rs + jj], acc[d]);
             }
         }
@@ -283,7 +283,7 @@ __global__ void cheb_m2l_lr(int b0, const int *v_off, const int *v_src, const un
         for (int d = 0; d < nd; ++d) Lc[((size_t)b * nd + d) * rt + i] = acc[d];
 }
 
-// L[b][d][m] = sc_b sum_i U[m][i] L~[b][d][i], sc_b = h w^power (the homogeneity scaling)
+// L[b][d][m] = sc_b sum_i U[m][i] L~[b][d][i], sc_b = h w^power (the homogeneity scaling; U stored as U')
 __global__ void cheb_expand(TreeView tv, int b0, int nd, int qq, int rt, int power, const double *U, const double *Lc,
                             double *L) {
     extern __shared__ double lsh[];  // [nd][rt]
@@ -296,7 +296,7 @@ __global__ void cheb_expand(TreeView tv, int b0, int nd, int qq, int rt, int pow
     for (int o = threadIdx.x; o < nd * qq; o += blockDim.x) {
         const int d = o / qq, m = o - d * qq;
         double acc = 0.0;
-        for (int k = 0; k < rt; ++k) acc = fma(U[(size_t)m * rt + k], lsh[d * rt + k], acc);
+        for (int k = 0; k < rt; ++k) acc = fma(U[(size_t)k * qq + m], lsh[d * rt + k], acc);  // U' [rt][qq]
         L[((size_t)b * nd + d) * qq + m] = sc * acc;
     }
 }
@@ -412,7 +412,10 @@ static void jacobi_right(int n, std::vector<double> &R, std::vector<double> &V, 
 
 struct ChebLowRank {
     int rt = 0, rs = 0;
-    std::vector<double> buf;  // U [qq][rt] | V [qq][rs] | C [49][rt][rs]
+    // U' [rt][qq] | V [qq][rs] | C_o' [49][rs][rt]: each laid out so the kernel's threads
+    // (over m in cheb_expand, over j in cheb_compress, over i in cheb_m2l_lr) read
+    // consecutive addresses
+    std::vector<double> buf;
 };
 
 // Shared bases of the 40 M2L matrices A_o[m][n] = K[o][n][m] (target m, source n).  The
@@ -422,12 +425,14 @@ struct ChebLowRank {
 // of [A_o ...]; since A_o' = A_{-o} (|x_m - x_n - 2o| = |x_n - x_m + 2o|) and the offset
 // set is symmetric, [A_o ...]' is the same stack with its blocks reordered, so U = V.
 // C_o = U' A_o V.  Built once per (q, eps).
-static const ChebLowRank &cheb_lowrank(int q, double eps, const std::vector<double> &K) {
+static std::vector<double> cheb_dense_ops(int q);
+static const ChebLowRank &cheb_lowrank(int q, double eps) {
     static std::mutex mu;
     static std::map<std::pair<int, double>, ChebLowRank> cache;
     std::lock_guard<std::mutex> g(mu);
     auto it = cache.find({q, eps});
     if (it != cache.end()) return it->second;
+    const std::vector<double> K = cheb_dense_ops(q);
     const int qq = q * q;
     std::vector<int> cls;
     for (int c = 0; c < 49; ++c) {
@@ -450,9 +455,10 @@ static const ChebLowRank &cheb_lowrank(int q, double eps, const std::vector<doub
     ChebLowRank lr;
     lr.rt = lr.rs = r;
     lr.buf.assign((size_t)2 * qq * r + (size_t)49 * r * r, 0.0);
-    double *U = lr.buf.data(), *V = U + (size_t)qq * r, *C = V + (size_t)qq * r;
+    double *Ut = lr.buf.data(), *V = Ut + (size_t)qq * r, *Ct = V + (size_t)qq * r;
     for (int m = 0; m < qq; ++m)
-        for (int i = 0; i < r; ++i) U[(size_t)m * r + i] = V[(size_t)m * r + i] = Vc[(size_t)i * qq + m];
+        for (int i = 0; i < r; ++i) Ut[(size_t)i * qq + m] = V[(size_t)m * r + i] = Vc[(size_t)i * qq + m];
+    const double *U = V;  // the same basis, [qq][r]
     std::vector<double> AV((size_t)qq * r);
     for (int c : cls) {
         const double *Kc = K.data() + (size_t)c * qq * qq;
@@ -462,23 +468,53 @@ static const ChebLowRank &cheb_lowrank(int q, double eps, const std::vector<doub
                 const double k = Kc[(size_t)n * qq + m];
                 for (int j = 0; j < r; ++j) AV[(size_t)m * r + j] += k * V[(size_t)n * r + j];
             }
-        double *Cc = C + (size_t)c * r * r;  // C_o = U' AV
+        double *Cc = Ct + (size_t)c * r * r;  // C_o = U' AV, stored transposed: Cc[j][i]
         for (int m = 0; m < qq; ++m)
             for (int i = 0; i < r; ++i) {
                 const double u = U[(size_t)m * r + i];
-                for (int j = 0; j < r; ++j) Cc[(size_t)i * r + j] += u * AV[(size_t)m * r + j];
+                for (int j = 0; j < r; ++j) Cc[(size_t)j * r + i] += u * AV[(size_t)m * r + j];
             }
     }
     return cache.emplace(std::make_pair(q, eps), std::move(lr)).first->second;
 }
 
-void cheb_setup(Fmm &f, int q, double lr_eps, cudaStream_t s) {
-    PHS_REQUIRE(q >= 3 && q <= kChebMaxQ, PHS_ERR_INVALID_ARG, "Chebyshev order must be in 3..16");
-    f.cheb_q = q;
+static long double cheb_node(int q, int m) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    return std::cos((2 * m + 1) * pi / (2.0L * q));
+}
+
+// The dense M2L operators K[cls][n][m] = |xb_m - xb_n - 2 o| (source node n, target node
+// m, offset o of class cls in box units), input of the low-rank build only.
+static std::vector<double> cheb_dense_ops(int q) {
+    const int qq = q * q;
+    std::vector<long double> xb(q);
+    for (int m = 0; m < q; ++m) xb[m] = cheb_node(q, m);
+    std::vector<double> K((size_t)49 * qq * qq, 0.0);
+    for (int dx = -3; dx <= 3; ++dx)
+        for (int dy = -3; dy <= 3; ++dy) {
+            if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+            const int cls = (dx + 3) * 7 + (dy + 3);
+            double *Kc = K.data() + (size_t)cls * qq * qq;
+            for (int n = 0; n < qq; ++n)
+                for (int m = 0; m < qq; ++m) {
+                    const long double ex = xb[m / q] - xb[n / q] - 2.0L * dx;
+                    const long double ey = xb[m % q] - xb[n % q] - 2.0L * dy;
+                    Kc[(size_t)n * qq + m] = (double)std::sqrt(ex * ex + ey * ey);
+                }
+        }
+    return K;
+}
+
+// The device tables of one order, built once per process: Tn [q][q] (T_k at the nodes) |
+// A [2][q][q] (the basis at the child nodes of either half).
+static const std::vector<double> &cheb_dev_tables(int q) {
+    static std::mutex mu;
+    static std::map<int, std::vector<double>> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(q);
+    if (it != cache.end()) return it->second;
     const int qq = q * q;
     const long double pi = 3.141592653589793238462643383279502884L;
-    std::vector<long double> xb(q);
-    for (int m = 0; m < q; ++m) xb[m] = std::cos((2 * m + 1) * pi / (2.0L * q));
     auto S = [&](int m, long double t) {
         long double Tk0 = 1, Tk1 = t, s = 0;
         for (int k = 1; k < q; ++k) {
@@ -490,31 +526,24 @@ void cheb_setup(Fmm &f, int q, double lr_eps, cudaStream_t s) {
         }
         return 1.0L / q + 2.0L / q * s;
     };
-    // layout of cheb64: Tn [q*q] | A [2][q][q] | K [49][qq][qq] (K[cls][n][m])
-    const size_t nK = (size_t)49 * qq * qq;
-    std::vector<double> buf((size_t)qq + 2 * qq + nK, 0.0);
+    std::vector<double> buf((size_t)3 * qq, 0.0);
     for (int k = 0; k < q; ++k)
         for (int m = 0; m < q; ++m) buf[k * q + m] = (double)std::cos(k * (2 * m + 1) * pi / (2.0L * q));
     for (int sgn = 0; sgn < 2; ++sgn)
         for (int m = 0; m < q; ++m)
             for (int mp = 0; mp < q; ++mp)
-                buf[qq + (size_t)sgn * qq + m * q + mp] = (double)S(m, (sgn ? 0.5L : -0.5L) + 0.5L * xb[mp]);
-    for (int dx = -3; dx <= 3; ++dx)
-        for (int dy = -3; dy <= 3; ++dy) {
-            if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
-            const int cls = (dx + 3) * 7 + (dy + 3);
-            double *K = buf.data() + 3 * qq + (size_t)cls * qq * qq;
-            for (int n = 0; n < qq; ++n)
-                for (int m = 0; m < qq; ++m) {
-                    const long double ex = xb[m / q] - xb[n / q] - 2.0L * dx;
-                    const long double ey = xb[m % q] - xb[n % q] - 2.0L * dy;
-                    K[(size_t)n * qq + m] = (double)std::sqrt(ex * ex + ey * ey);
-                }
-        }
+                buf[qq + (size_t)sgn * qq + m * q + mp] =
+                    (double)S(m, (sgn ? 0.5L : -0.5L) + 0.5L * cheb_node(q, mp));
+    return cache.emplace(q, std::move(buf)).first->second;
+}
+
+void cheb_setup(Fmm &f, int q, double lr_eps, cudaStream_t s) {
+    PHS_REQUIRE(q >= 3 && q <= kChebMaxQ, PHS_ERR_INVALID_ARG, "Chebyshev order must be in 3..16");
+    f.cheb_q = q;
+    const std::vector<double> &buf = cheb_dev_tables(q);  // cheb64: Tn [q*q] | A [2][q][q]
     f.cheb64.alloc(buf.size());
     PHS_CUDA(cudaMemcpyAsync(f.cheb64.get(), buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    const std::vector<double> K(buf.begin() + 3 * qq, buf.end());
-    const ChebLowRank &lr = cheb_lowrank(q, lr_eps, K);
+    const ChebLowRank &lr = cheb_lowrank(q, lr_eps);
     f.cheb_rt = lr.rt;
     f.cheb_rs = lr.rs;
     PHS_REQUIRE(lr.rt <= 256 && lr.rs <= 256, PHS_ERR_INVALID_ARG, "compressed M2L rank above 256");
@@ -531,7 +560,7 @@ void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_
         f.cw64.alloc(sz);
         f.cl64.alloc(sz);
     }
-    const double *Tn = f.cheb64.get(), *A = Tn + qq, *K = Tn + 3 * qq;
+    const double *Tn = f.cheb64.get(), *A = Tn + qq;
     TreeView tv = tree_view(t);
     if (tm) tm->begin(s);
     cheb_p2m<<<t.nleaf, CHEB_T, 0, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, nd, q, Tn,
@@ -567,7 +596,6 @@ void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_
             PHS_LAUNCH_CHECK();
         }
     }
-    (void)K;
     if (tm) tm->end(T_M2L, s);
     if (tm) tm->begin(s);
     for (int l = 3; l <= t.depth; ++l) {

@@ -162,13 +162,13 @@ __global__ void __launch_bounds__(PF_T) p2m_ff_kernel(TreeView tv, const int *le
         const int o = threadIdx.x + i * PF_T;
         if (o < nout) {
             const int d = o / P, k = o - d * P;
-            double ax = to_d(acc[i].re), ay = to_d(acc[i].im);
-            if (k > 0) {
-                const double sc = -1.0 / k;
-                ax *= sc;
-                ay *= sc;
+            C4 a = acc[i];
+            if (k > 0) {  // times -1/k, the reciprocal in float-float (one Newton correction)
+                const float kf = (float)k, h = __frcp_rn(kf);
+                const F2 nr{-h, -h * __fmaf_rn(-h, kf, 1.f)};
+                a = {ff_mul(a.re, nr), ff_mul(a.im, nr)};
             }
-            mp[((size_t)b * ND + d) * P + k] = make_double2(ax, ay);
+            mp[((size_t)b * ND + d) * P + k] = make_double2(to_d(a.re), to_d(a.im));
         }
     }
 }
@@ -211,35 +211,48 @@ __global__ void __launch_bounds__(LF_T) l2p_ff_kernel(TreeView tv, const int *le
     }
 }
 
-// M2M for the parents of one level, as fmm.cu m2m64_kernel: each child's multipole takes
-// the phase e^{-i th_q k} (FP64, split to float-float in shared memory), passes through
-// the real lower-triangular core R (row l: sum over k <= l) in float-float with two
-// interleaved accumulator pairs, takes e^{i th_q l}, and the parent sums the children
-// through the frame changes (FP64; nd x nd per coefficient, a small share of the work).
+// complex conjugate
+__device__ __forceinline__ C4 c4_conj(C4 a) { return {a.re, ff_neg(a.im)}; }
+
+// M2M for the parents of one level, as fmm.cu m2m64_kernel: each child's multipole (FP64,
+// split once) takes the phase e^{-i th_q k}, passes through the real lower-triangular core
+// R (row l: sum over k <= l) with two interleaved accumulator pairs, takes e^{i th_q l},
+// and the parent sums the children through the frame changes -- all in float-float, with
+// the phases, core and frame changes pre-split; one conversion to FP64 per output.
 __global__ void __launch_bounds__(PF_T) m2m_ff_kernel(TreeView tv, int b0, int nd, int P, const float2 *R,
-                                                      const double2 *ph, const double *mix, double2 *mp) {
+                                                      const float4 *ph, const float2 *mix, double2 *mp) {
     extern __shared__ float4 mf_sm[];
     const int b = b0 + blockIdx.x;
     const int nc = tv.nchild[b];
     if (nc == 0) return;
     const int nout = nd * P, c0 = tv.child[b];
-    float4 *ch = mf_sm;                                     // [4][nd][P] rotated children
-    double2 *sh = reinterpret_cast<double2 *>(mf_sm + 4 * nout);  // [4][nd][P] shifted
+    float4 *ch = mf_sm;               // [4][nd][P] rotated children
+    float4 *sh = mf_sm + 4 * nout;    // [4][nd][P] shifted
+    float4 *phs = sh + 4 * nout;      // [4][P] phases
+    float2 *Rs = reinterpret_cast<float2 *>(phs + 4 * P);  // [P][P] core
+    float2 *mxs = Rs + P * P;         // [4][nd][nd] frame changes of the quadrants
+    // the tables every step reads, staged once per block (the loops below would
+    // otherwise wait on L2 at each dependent step)
+    for (int i = threadIdx.x; i < 4 * P; i += PF_T) phs[i] = ph[i];
+    for (int i = threadIdx.x; i < P * P; i += PF_T) Rs[i] = R[i];
+    for (int i = threadIdx.x; i < 4 * nd * nd; i += PF_T) mxs[i] = mix[(size_t)49 * nd * nd + i];
+    __syncthreads();
     for (int i = threadIdx.x; i < nc * nout; i += PF_T) {
         const int c = i / nout, k = (i - c * nout) % P;
-        const double2 a = mp[(size_t)c0 * nout + i], e = ph[(size_t)(tv.key[c0 + c] & 3) * P + k];
-        ch[i] = c4_pack(c4_of(make_double2(fma(a.x, e.x, a.y * e.y), fma(a.y, e.x, -a.x * e.y))));
+        const C4 a = c4_of(mp[(size_t)c0 * nout + i]);
+        const C4 e = c4_unpack(phs[(tv.key[c0 + c] & 3) * P + k]);
+        ch[i] = c4_pack(c4_mul(a, c4_conj(e)));  // a e^{-i th k}
     }
     __syncthreads();
     const int half = (P + 1) / 2;
     for (int it = threadIdx.x; it < nc * nd * half; it += PF_T) {
         const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
-        const double2 *ephq = ph + (size_t)(tv.key[c0 + c] & 3) * P;
+        const float4 *ephq = phs + (tv.key[c0 + c] & 3) * P;
         const float4 *src = ch + c * nout + d * P;
         for (int h = 0; h < 2; ++h) {
             const int l = h == 0 ? p : P - 1 - p;
             if (h == 1 && l == p) break;
-            const float2 *Rr = R + (size_t)l * P;
+            const float2 *Rr = Rs + l * P;
             F2 ax{0.f, 0.f}, ay{0.f, 0.f}, bx{0.f, 0.f}, by{0.f, 0.f};
             int k = 0;
             for (; k + 1 <= l; k += 2) {
@@ -256,58 +269,65 @@ __global__ void __launch_bounds__(PF_T) m2m_ff_kernel(TreeView tv, int b0, int n
                 ff_acc(ax, ff_mul(F2{r0.x, r0.y}, m0.re));
                 ff_acc(ay, ff_mul(F2{r0.x, r0.y}, m0.im));
             }
-            const double zx = to_d(ax) + to_d(bx), zy = to_d(ay) + to_d(by);
-            const double2 e = ephq[l];
-            sh[c * nout + d * P + l] = make_double2(fma(zx, e.x, -zy * e.y), fma(zx, e.y, zy * e.x));
+            const C4 z{ff_add(ax, bx), ff_add(ay, by)};
+            sh[c * nout + d * P + l] = c4_pack(c4_mul(z, c4_unpack(ephq[l])));  // z e^{i th l}
         }
     }
     __syncthreads();
     for (int o = threadIdx.x; o < nout; o += PF_T) {
         const int d = o / P, l = o - d * P;
-        double ax = 0.0, ay = 0.0;
+        F2 ax{0.f, 0.f}, ay{0.f, 0.f};
         for (int c = 0; c < nc; ++c) {
-            const double *Rv = mix + (size_t)(49 + (tv.key[c0 + c] & 3)) * nd * nd + d * nd;
+            const float2 *Rv = mxs + (tv.key[c0 + c] & 3) * nd * nd + d * nd;
             for (int bb = 0; bb < nd; ++bb) {
-                const double r = Rv[bb];
-                if (r != 0.0) {
-                    const double2 v = sh[c * nout + bb * P + l];
-                    ax = fma(r, v.x, ax);
-                    ay = fma(r, v.y, ay);
+                const float2 r = Rv[bb];
+                if (r.x != 0.f) {
+                    const C4 v = c4_unpack(sh[c * nout + bb * P + l]);
+                    ff_acc(ax, ff_mul(F2{r.x, r.y}, v.re));
+                    ff_acc(ay, ff_mul(F2{r.x, r.y}, v.im));
                 }
             }
         }
-        mp[(size_t)b * nout + o] = make_double2(ax, ay);
+        mp[(size_t)b * nout + o] = make_double2(to_d(ax), to_d(ay));
     }
 }
 
 // L2L for the parents of one level, as fmm.cu l2l64_kernel: the parent's local expansion
-// takes each child's phase e^{i th_q l} (FP64, split), passes through the real
-// upper-triangular core (row m: sum over l >= m) in float-float, takes e^{-i th_q m}, and
-// mixes through the frame changes into the child's local expansion (FP64).
+// (split once) takes each child's phase e^{i th_q l}, passes through the real
+// upper-triangular core (row m: sum over l >= m), takes e^{-i th_q m}, and mixes through
+// the frame changes -- in float-float -- into the child's FP64 local expansion.
 __global__ void __launch_bounds__(PF_T) l2l_ff_kernel(TreeView tv, int b0, int nd, int P, const float2 *R,
-                                                      const double2 *ph, const double *mix, double2 *lc) {
+                                                      const float4 *ph, const float2 *mix, double2 *lc) {
     extern __shared__ float4 lf2_sm[];
     const int b = b0 + blockIdx.x;
     const int nc = tv.nchild[b];
     if (nc == 0) return;
     const int nout = nd * P, c0 = tv.child[b];
-    float4 *y = lf2_sm;
-    double2 *sh = reinterpret_cast<double2 *>(lf2_sm + 4 * nout);
+    float4 *y = lf2_sm;                 // [4][nd][P] rotated copies, then [nd][P] the parent's
+    float4 *sh = lf2_sm + 5 * nout;     // [4][nd][P] shifted
+    float4 *phs = sh + 4 * nout;        // [4][P] phases
+    float2 *Rs = reinterpret_cast<float2 *>(phs + 4 * P);  // [P][P] core
+    float2 *mxs = Rs + P * P;           // [4][nd][nd] frame changes of the quadrants
+    for (int i = threadIdx.x; i < 4 * P; i += PF_T) phs[i] = ph[i];
+    for (int i = threadIdx.x; i < P * P; i += PF_T) Rs[i] = R[i];
+    for (int i = threadIdx.x; i < 4 * nd * nd; i += PF_T) mxs[i] = mix[(size_t)53 * nd * nd + i];
+    for (int i = threadIdx.x; i < nout; i += PF_T) y[4 * nout + i] = c4_pack(c4_of(lc[(size_t)b * nout + i]));
+    __syncthreads();
     for (int i = threadIdx.x; i < nc * nout; i += PF_T) {
         const int c = i / nout, o = i - c * nout, l = o % P;
-        const double2 v = lc[(size_t)b * nout + o], e = ph[(size_t)(tv.key[c0 + c] & 3) * P + l];
-        y[i] = c4_pack(c4_of(make_double2(fma(v.x, e.x, -v.y * e.y), fma(v.x, e.y, v.y * e.x))));
+        const C4 v = c4_unpack(y[4 * nout + o]);
+        y[i] = c4_pack(c4_mul(v, c4_unpack(phs[(tv.key[c0 + c] & 3) * P + l])));  // b e^{i th l}
     }
     __syncthreads();
     const int half = (P + 1) / 2;
     for (int it = threadIdx.x; it < nc * nd * half; it += PF_T) {
         const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
-        const double2 *ephq = ph + (size_t)(tv.key[c0 + c] & 3) * P;
+        const float4 *ephq = phs + (tv.key[c0 + c] & 3) * P;
         const float4 *src = y + c * nout + d * P;
         for (int h = 0; h < 2; ++h) {
             const int m = h == 0 ? p : P - 1 - p;
             if (h == 1 && m == p) break;
-            const float2 *Rr = R + (size_t)m * P;
+            const float2 *Rr = Rs + m * P;
             F2 ax{0.f, 0.f}, ay{0.f, 0.f}, bx{0.f, 0.f}, by{0.f, 0.f};
             int l = m;
             for (; l + 1 < P; l += 2) {
@@ -324,51 +344,57 @@ __global__ void __launch_bounds__(PF_T) l2l_ff_kernel(TreeView tv, int b0, int n
                 ff_acc(ax, ff_mul(F2{r0.x, r0.y}, v0.re));
                 ff_acc(ay, ff_mul(F2{r0.x, r0.y}, v0.im));
             }
-            const double zx = to_d(ax) + to_d(bx), zy = to_d(ay) + to_d(by);
-            const double2 e = ephq[m];
-            sh[c * nout + d * P + m] = make_double2(fma(zx, e.x, zy * e.y), fma(zy, e.x, -zx * e.y));
+            const C4 z{ff_add(ax, bx), ff_add(ay, by)};
+            sh[c * nout + d * P + m] = c4_pack(c4_mul(z, c4_conj(c4_unpack(ephq[m]))));  // z e^{-i th m}
         }
     }
     __syncthreads();
     for (int it = threadIdx.x; it < nc * nout; it += PF_T) {
         const int c = it / nout, o = it - c * nout, a_ = o / P, m = o - a_ * P;
-        const double *Ru = mix + (size_t)(53 + (tv.key[c0 + c] & 3)) * nd * nd;
-        double2 acc = lc[(size_t)(c0 + c) * nout + o];
+        const float2 *Ru = mxs + (tv.key[c0 + c] & 3) * nd * nd;
+        F2 ax{0.f, 0.f}, ay{0.f, 0.f};
         for (int l = 0; l < nd; ++l) {
-            const double r = Ru[l * nd + a_];
-            if (r != 0.0) {
-                const double2 v = sh[c * nout + l * P + m];
-                acc.x = fma(r, v.x, acc.x);
-                acc.y = fma(r, v.y, acc.y);
+            const float2 r = Ru[l * nd + a_];
+            if (r.x != 0.f) {
+                const C4 v = c4_unpack(sh[c * nout + l * P + m]);
+                ff_acc(ax, ff_mul(F2{r.x, r.y}, v.re));
+                ff_acc(ay, ff_mul(F2{r.x, r.y}, v.im));
             }
         }
-        lc[(size_t)(c0 + c) * nout + o] = acc;
+        double2 &dst = lc[(size_t)(c0 + c) * nout + o];
+        dst = make_double2(dst.x + to_d(ax), dst.y + to_d(ay));
     }
 }
 
 }  // namespace
 
+// shared memory of the shift kernels beyond their expansion buffers: phases, core, frame changes
+static size_t shift_tables_smem(const Fmm &f) {
+    return (size_t)4 * f.P * sizeof(float4) + (size_t)f.P * f.P * sizeof(float2) + (size_t)4 * f.nd * f.nd * sizeof(float2);
+}
+
 void m2m_ff_launch(const Fmm &f, const Tree &t, int b0, int nb, double2 *mp, cudaStream_t s) {
-    const size_t sm = (size_t)8 * f.nd * f.P * 16;  // [4][nd][P] float4 + [4][nd][P] double2
+    // [4][nd][P] rotated + [4][nd][P] shifted (float4) + the tables: at most 112 KB (nd 9, P 61)
+    const size_t sm = (size_t)8 * f.nd * f.P * 16 + shift_tables_smem(f);
     once_per_device(6, [] {
-        const int lim = 100 * 1024;
+        const int lim = 128 * 1024;
         PHS_CUDA(cudaFuncSetAttribute(m2m_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         PHS_CUDA(cudaFuncSetAttribute(l2l_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     });
-    m2m_ff_kernel<<<nb, PF_T, sm, s>>>(tree_view(t), b0, f.nd, f.P, f.shift_rff.get(), f.shift_ph.get(), f.mix64.get(),
-                                       mp);
+    m2m_ff_kernel<<<nb, PF_T, sm, s>>>(tree_view(t), b0, f.nd, f.P, f.shift_rff.get(), f.shift_phff.get(),
+                                       f.mixff.get(), mp);
     PHS_LAUNCH_CHECK();
 }
 
 void l2l_ff_launch(const Fmm &f, const Tree &t, int b0, int nb, double2 *lc, cudaStream_t s) {
-    const size_t sm = (size_t)8 * f.nd * f.P * 16;
+    const size_t sm = (size_t)9 * f.nd * f.P * 16 + shift_tables_smem(f);  // and the parent's split local expansion
     once_per_device(6, [] {
-        const int lim = 100 * 1024;
+        const int lim = 128 * 1024;
         PHS_CUDA(cudaFuncSetAttribute(m2m_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         PHS_CUDA(cudaFuncSetAttribute(l2l_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     });
     l2l_ff_kernel<<<nb, PF_T, sm, s>>>(tree_view(t), b0, f.nd, f.P, f.shift_rff.get() + (size_t)f.P * f.P,
-                                       f.shift_ph.get(), f.mix64.get(), lc);
+                                       f.shift_phff.get(), f.mixff.get(), lc);
     PHS_LAUNCH_CHECK();
 }
 

@@ -1421,6 +1421,7 @@ struct DevTables {
     std::vector<float2> o32;
     std::vector<double> R;    // [2][P][P]: M2M, L2L
     std::vector<float2> Rff;  // the same split into hi + lo floats (float-float passes)
+    std::vector<float4> phff; // ph split into hi + lo floats
     std::vector<double2> ph;  // [4][P]: e^{i th_q k}
     std::vector<long double> re, im;  // the operators split for the tensor-core setup
 };
@@ -1445,11 +1446,15 @@ static const DevTables &dev_tables_cached(int P) {
     d.R.assign((size_t)2 * P * P, 0.0);
     d.Rff.assign((size_t)2 * P * P, make_float2(0.f, 0.f));
     d.ph.resize((size_t)4 * P);
+    d.phff.resize((size_t)4 * P);
     for (int q = 0; q < 4; ++q) {
         const long double th = std::atan2((long double)((q & 2) ? 0.25L : -0.25L), (long double)((q & 1) ? 0.25L : -0.25L));
         for (int k = 0; k < P; ++k) {
             const long double a = th * k;
             d.ph[(size_t)q * P + k] = make_double2((double)std::cos(a), (double)std::sin(a));
+            const long double c = std::cos(a), sn = std::sin(a);
+            const float ch = (float)c, sh = (float)sn;
+            d.phff[(size_t)q * P + k] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(sn - (long double)sh));
         }
         for (int t2 = 0; t2 < 2; ++t2)
             for (int r = 0; r < P; ++r)
@@ -1502,6 +1507,9 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     f.shift_r.alloc(dt.R.size());
     f.shift_ph.alloc(dt.ph.size());
     f.shift_rff.alloc(dt.Rff.size());
+    f.shift_phff.alloc(dt.phff.size());
+    PHS_CUDA(cudaMemcpyAsync(f.shift_phff.get(), dt.phff.data(), dt.phff.size() * sizeof(float4),
+                             cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.shift_r.get(), dt.R.data(), dt.R.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     PHS_CUDA(cudaMemcpyAsync(f.shift_rff.get(), dt.Rff.data(), dt.Rff.size() * sizeof(float2), cudaMemcpyHostToDevice,
                              s));
@@ -1510,10 +1518,14 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
         const auto &mx = mix_cached(f.power, f.nd);
         std::vector<double> m64(mx.size());
         std::vector<float> m32(mx.size());
+        std::vector<float2> mff(mx.size());
         for (size_t i = 0; i < mx.size(); ++i) {
             m64[i] = (double)mx[i];
             m32[i] = (float)mx[i];
+            mff[i] = make_float2(m32[i], (float)(mx[i] - (long double)m32[i]));
         }
+        f.mixff.alloc(mff.size());
+        PHS_CUDA(cudaMemcpyAsync(f.mixff.get(), mff.data(), mff.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
         f.mix64.alloc(m64.size());
         f.mix32.alloc(m32.size());
         PHS_CUDA(cudaMemcpyAsync(f.mix64.get(), m64.data(), m64.size() * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1553,28 +1565,37 @@ __global__ void eval_box_kernel(TreeView tv, const double2 *tgt, int64_t m, int 
     box_of[i] = find_deepest(tv, L, (int)ix, (int)iy);
 }
 
-// direct part from the precomputed near list of the target's box
+// direct part from the precomputed near list of the target's box: a warp per target, the
+// lanes striding over each range, one fixed-order shuffle reduction at the end.  A target
+// between clusters lies in a coarse box whose near list holds a large share of all
+// points, so the work per target varies by orders of magnitude; a thread per target left
+// those sums on a few SMs' FP64 pipes.
+constexpr int EVAL_T = 128;
 template <int K>
-__global__ void eval_near_kernel(const double2 *xs, const double *w, const double2 *tgt, int64_t m, const int *box_of,
-                                 const int *near_off, const int2 *near_rng, double *out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+__global__ void __launch_bounds__(EVAL_T) eval_near_kernel(const double2 *xs, const double *w, const double2 *tgt,
+                                                           int64_t m, const int *box_of, const int *near_off,
+                                                           const int2 *near_rng, double *out) {
+    const int64_t i = (int64_t)blockIdx.x * (EVAL_T / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= m) return;  // whole warps leave together
     const int b = box_of[i];
     if (b < 0) {
-        out[i] = 0.0;
+        if (lane == 0) out[i] = 0.0;
         return;
     }
     const double2 y = tgt[i];
     double acc = 0.0;
     for (int r = near_off[b]; r < near_off[b + 1]; ++r) {
         const int2 rg = near_rng[r];
-        for (int j = rg.x; j < rg.y; ++j) {
+        for (int j = rg.x + lane; j < rg.y; j += 32) {
             const double dx = y.x - xs[j].x, dy = y.y - xs[j].y;
             const double r2 = dx * dx + dy * dy;
             if (r2 > 0) acc += phi_r2<double, K>(r2) * w[j];
         }
     }
-    out[i] = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[i] = acc;
 }
 
 __global__ void eval_far_log_kernel(TreeView tv, const double2 *tgt, int64_t m, const int *box_of, int power, int nd,
@@ -1644,8 +1665,8 @@ static void eval_launch(Fmm &f, const Tree &t, const PointSet &ps, const double 
     TreeView tv = tree_view(t);
     eval_box_kernel<<<blocks_for(m, 128), 128, 0, s>>>(tv, tgt, m, box_of.get());
     PHS_LAUNCH_CHECK();
-    eval_near_kernel<K><<<blocks_for(m, 128), 128, 0, s>>>(ps.xs.get(), w_sorted, tgt, m, box_of.get(),
-                                                           t.near_off.get(), t.near_rng.get(), out);
+    eval_near_kernel<K><<<blocks_for(m, EVAL_T / 32), EVAL_T, 0, s>>>(ps.xs.get(), w_sorted, tgt, m, box_of.get(),
+                                                                     t.near_off.get(), t.near_rng.get(), out);
     PHS_LAUNCH_CHECK();
     if (f.log_core) {
         eval_far_log_kernel<<<blocks_for(m, 128), 128, 0, s>>>(tv, tgt, m, box_of.get(), f.power, f.nd, f.P,

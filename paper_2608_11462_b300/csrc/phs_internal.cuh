@@ -235,20 +235,20 @@ struct Fmm {
     DBuf<double> shift_r;
     DBuf<double2> shift_ph;
     DBuf<float2> shift_rff;  // shift_r split into hi + lo floats
+    DBuf<float4> shift_phff; // shift_ph split into hi + lo floats
     DBuf<float2> ops32;   // same for the FP32 order P32
     DBuf<float2> ops32p, mpx32, lcx32;  // FP32 copies at the FP64 order (FP32 M2L mode)
     DBuf<double> mix64;                 // box-local Hadamard frame changes [57][nd][nd]
     DBuf<float> mix32;
+    DBuf<float2> mixff;                 // mix64 split into hi + lo floats
     DBuf<int> lvl_off_dev;
     // Chebyshev (distance kernel) data
     int cheb_q = 0;                      // nodes per dimension
     int cheb_rt = 0, cheb_rs = 0;        // ranks of the compressed M2L (target, source bases)
-    DBuf<double> cheb64;                 // operators
-    DBuf<double> cheb_lr;                // compressed M2L: U [q*q][rt] | V [q*q][rs] | C [49][rt][rs]
+    DBuf<double> cheb64;                 // Tn [q][q] | A [2][q][q]
+    DBuf<double> cheb_lr;                // compressed M2L: U' [rt][q*q] | V [q*q][rs] | C' [49][rs][rt]
     DBuf<double> cwc64, clc64;           // compressed weights [box][nd][rs], potentials [box][nd][rt]
-    DBuf<float> cheb32;
     DBuf<double> cw64, cl64;             // weights/potentials at nodes [box][nd][q*q]
-    DBuf<float> cw32, cl32;
     // tensor-core M2L of the log kernel (m2l_tc.cu)
     bool tc = false;                     // use it for the FP64 far field
     bool ff_passes = true;               // precision 4: P2M and L2P in float-float too
