@@ -77,5 +77,59 @@ __device__ __forceinline__ C4 c4_of(double2 z) { return {split_d(z.x), split_d(z
 __device__ __forceinline__ float4 c4_pack(C4 a) { return make_float4(a.re.h, a.re.l, a.im.h, a.im.l); }
 __device__ __forceinline__ C4 c4_unpack(float4 v) { return {F2{v.x, v.y}, F2{v.z, v.w}}; }
 
+// a b renormalised (|lo| <= ulp(hi) / 2), for products that feed further products
+__device__ __forceinline__ F2 ff_mulr(F2 a, F2 b) {
+    const F2 p = ff_mul(a, b);
+    return fast_two_sum(p.h, p.l);
+}
+// s a power of two: exact
+__device__ __forceinline__ F2 ff_scale(F2 a, float s) { return {a.h * s, a.l * s}; }
+
+// The Hadamard factors of hadamard.cuh (had_v, had_u) in float-float, from float-float
+// box-local coordinates; ND = 1, 4, 9 for the powers 0, 2, 4 of |x_i - x_j|.
+template <int ND>
+__device__ __forceinline__ void had_v_ff(F2 x, F2 y, F2 *v) {
+    const F2 one{1.f, 0.f};
+    v[0] = one;
+    if constexpr (ND == 4) {
+        v[1] = ff_add(ff_mulr(x, x), ff_mulr(y, y));
+        v[2] = x;
+        v[3] = y;
+    } else if constexpr (ND == 9) {
+        const F2 xx = ff_mulr(x, x), yy = ff_mulr(y, y), a = ff_add(xx, yy);
+        v[1] = ff_mulr(a, a);
+        v[2] = x;
+        v[3] = y;
+        v[4] = ff_mulr(a, x);
+        v[5] = ff_mulr(a, y);
+        v[6] = xx;
+        v[7] = ff_mulr(x, y);
+        v[8] = yy;
+    }
+}
+template <int ND>
+__device__ __forceinline__ void had_u_ff(F2 x, F2 y, F2 *u) {
+    const F2 one{1.f, 0.f};
+    if constexpr (ND == 1) {
+        u[0] = one;
+    } else if constexpr (ND == 4) {
+        u[0] = ff_add(ff_mulr(x, x), ff_mulr(y, y));
+        u[1] = one;
+        u[2] = ff_scale(x, -2.f);
+        u[3] = ff_scale(y, -2.f);
+    } else {
+        const F2 xx = ff_mulr(x, x), yy = ff_mulr(y, y), a = ff_add(xx, yy);
+        u[0] = ff_mulr(a, a);
+        u[1] = one;
+        u[2] = ff_scale(ff_mulr(a, x), -4.f);
+        u[3] = ff_scale(ff_mulr(a, y), -4.f);
+        u[4] = ff_scale(x, -4.f);
+        u[5] = ff_scale(y, -4.f);
+        u[6] = ff_add(ff_scale(xx, 4.f), ff_scale(a, 2.f));
+        u[7] = ff_scale(ff_mulr(x, y), 8.f);
+        u[8] = ff_add(ff_scale(yy, 4.f), ff_scale(a, 2.f));
+    }
+}
+
 }  // namespace ffa
 }  // namespace phs

@@ -264,18 +264,16 @@ __global__ void sym_fill(TreeView tv, const int *leaf_box, int nleaf, const int 
     }
 }
 // ascending offsets per leaf: a fixed summation order in the gather
-__global__ void sym_sort(const int *goff, int nleaf, int *gbase) {
+// by a radix sort of (leaf, offset) keys: a leaf beside a dense cluster receives thousands
+// of offsets, so any per-leaf quadratic sort on one thread stalls the plan
+__global__ void sym_keys(const int *goff, int nleaf, const int *gbase, uint64_t *key) {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= nleaf) return;
-    for (int a = goff[d] + 1; a < goff[d + 1]; ++a) {
-        const int v = gbase[a];
-        int c = a - 1;
-        while (c >= goff[d] && gbase[c] > v) {
-            gbase[c + 1] = gbase[c];
-            --c;
-        }
-        gbase[c + 1] = v;
-    }
+    for (int a = goff[d]; a < goff[d + 1]; ++a) key[a] = ((uint64_t)d << 31) | (uint32_t)gbase[a];
+}
+__global__ void sym_unkey(const uint64_t *key, int64_t ng, int *gbase) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ng) gbase[i] = (int)(key[i] & 0x7FFFFFFFull);
 }
 
 __global__ void count_sum(const int *cnt, int n, unsigned long long *out) {
@@ -476,8 +474,17 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
                                                      tree.near_rng.get(), tree.point_leaf.get(), tree.sym_slot.get(),
                                                      tree.sym_goff.get(), gcur.get(), tree.sym_gbase.get());
         PHS_LAUNCH_CHECK();
-        sym_sort<<<blocks_for(nl, 128), 128, 0, s>>>(tree.sym_goff.get(), nl, tree.sym_gbase.get());
-        PHS_LAUNCH_CHECK();
+        if (ng > 1) {
+            SBuf<uint64_t> gkey(ng, s);
+            SBuf<int> gval(ng, s);
+            sym_keys<<<blocks_for(nl, 128), 128, 0, s>>>(tree.sym_goff.get(), nl, tree.sym_gbase.get(), gkey.get());
+            PHS_LAUNCH_CHECK();
+            int lb = 1;
+            while ((1ll << lb) < nl) ++lb;
+            radix_sort_pairs(gkey.get(), gval.get(), ng, 31 + lb, s);
+            sym_unkey<<<blocks_for(ng, 256), 256, 0, s>>>(gkey.get(), ng, tree.sym_gbase.get());
+            PHS_LAUNCH_CHECK();
+        }
         unsigned long long hp[2];
         int hm[2];
         PHS_CUDA(cudaMemcpyAsync(hm, mx.get(), sizeof(hm), cudaMemcpyDeviceToHost, s));
