@@ -709,7 +709,8 @@ void build_lowrank(phs_plan *pl, cudaStream_t s) {
 void plan_set_alpha(phs_plan *pl, double alpha, cudaStream_t s) {
     PHS_REQUIRE(alpha > 0 && std::isfinite(alpha), PHS_ERR_INVALID_ARG, "alpha must be positive");
     pl->opt.alpha = alpha;
-    vecchia_build(pl->vec, pl->ps, pl->m, pl->opt.ordering, pl->opt.seed, pl->opt.nu, alpha, s);
+    vecchia_build(pl->vec, pl->ps, pl->m, pl->opt.ordering, pl->opt.seed, pl->opt.nu, alpha, s,
+                  pl->opt.precision == 4);
     pl->lowrank = false;
     if (pl->opt.precond_lowrank) build_lowrank(pl, s);
     PHS_CUDA(cudaStreamSynchronize(s));
@@ -1104,7 +1105,7 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         mul_upper<<<1, 1, 0, s>>>(pl->R.get() + 2 * S * S, pl->R.get() + S * S, S, pl->R.get());
         PHS_LAUNCH_CHECK();
         // Vecchia preconditioner
-        vecchia_build(pl->vec, pl->ps, vecchia_m, o.ordering, o.seed, o.nu, o.alpha, s);
+        vecchia_build(pl->vec, pl->ps, vecchia_m, o.ordering, o.seed, o.nu, o.alpha, s, o.precision == 4);
         pl->work.alloc((size_t)12 * n);
         if (o.precond_lowrank) build_lowrank(pl, s);
         PHS_CUDA(cudaStreamSynchronize(s));

@@ -375,13 +375,13 @@ void hmaxmin_order_dev(const double2 *x, int64_t n, uint64_t seed, int *order_ou
 void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t s);
 void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr_ell, cudaStream_t s);
 int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m,
-                           double nu, double alpha, double *val_ell, cudaStream_t s);
+                           double nu, double alpha, double *val_ell, cudaStream_t s, bool ff = false);
 // rank[order[r]] = r for a caller's enumeration (int64, any device buffer), checking that
 // order is a permutation and, if nbr (n x m int64 rows) is given, that the first
 // min(m, rank(i)) entries of row i are points of smaller rank; PHS_ERR_INVALID_ARG otherwise
 void checked_ranks_dev(const int64_t *order, const int64_t *nbr, int64_t n, int m, int *rank, cudaStream_t s);
 void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t seed, double nu,
-                   double alpha, cudaStream_t s);
+                   double alpha, cudaStream_t s, bool ff = false);
 // z = U~ (U~' r) (sorted order)
 void vecchia_apply(const Vecchia &v, const double *r, double *tmp, double *z, cudaStream_t s);
 // the two halves of z = U (U' r): y = U' r and z = U y

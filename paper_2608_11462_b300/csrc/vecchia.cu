@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "geom.cuh"
+#include "ff.cuh"
 #include "phs_internal.cuh"
 
 namespace phs {
@@ -531,6 +532,123 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
     if (lane + 32 < m) val_ell[(int64_t)(33 + lane) * n + i] = lane + 32 < s ? -l1 * ic : 0.0;
 }
 
+// The same factorisation with the elimination, pivots and back solve in float-float on the
+// FP32 pipe (precision-4 plans): the Matern entries stay FP64 (then split), the stored
+// factor is FP64.  The factor only shapes the preconditioner: any U gives a symmetric
+// U U' applied in FP64, so float-float's rounding (about 2^-46 per operation, times the
+// local condition number) moves the iteration count, not the fit's accuracy.  A pivot
+// below the smallest normal float counts as non-positive (next rung of the jitter ladder).
+template <int NUC>
+__global__ void factor_kernel_ff(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, int ld,
+                                 double halpha, double *val_ell, unsigned long long *njit) {
+    using ffa::F2;
+    extern __shared__ double fsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int per = (m + 1) * ld + 3 * (m + 1);  // 8-byte words, as in factor_kernel
+    double *base = fsm + (size_t)wib * per;
+    float2 *A = reinterpret_cast<float2 *>(base);
+    float2 *W = A + (m + 1) * ld;
+    double *X = base + (m + 1) * ld + (m + 1);
+    double *Y = X + (m + 1);
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (i >= n) return;
+    const unsigned full = 0xffffffffu;
+    const int s = min(m, rank[i]);
+    for (int a = lane; a <= s; a += 32) {
+        const double2 p = a < s ? x[nbr_ell[(int64_t)a * n + i]] : x[i];
+        X[a] = p.x * halpha;
+        Y[a] = p.y * halpha;
+    }
+    __syncwarp();
+    const int nn = s + 1, ntri = nn * (nn + 1) / 2;
+    bool ok = false;
+    int tries = 0;
+    for (int t = 0; t <= 7 && !ok; ++t) {
+        const double jit = t == 0 ? 0.0 : 1e-12 * pow(10.0, (double)(t - 1));
+        for (int idx = lane; idx < ntri; idx += 32) {
+            int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+            while (a * (a + 1) / 2 > idx) --a;
+            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+            const int b = idx - a * (a + 1) / 2;
+            double v;
+            if (b == a) {
+                v = a < s ? 1.0 + jit : 1.0;  // jitter on K_ss only
+            } else {
+                const double dx = X[a] - X[b], dy = Y[a] - Y[b];
+                const double q = fma(dx, dx, dy * dy);
+                v = __double2hiint(q) > 0 ? matern_q<NUC>(q) : 1.0;
+            }
+            const F2 vf = ffa::split_d(v);
+            A[a * ld + b] = make_float2(vf.h, vf.l);
+        }
+        __syncwarp();
+        ok = true;
+        for (int j = 0; j < s; ++j) {
+            const float2 dd = A[j * ld + j];  // same value in every lane: the branch is uniform
+            if (!(dd.x >= 1.17549435e-38f)) { ok = false; break; }
+            // 1/d in float-float: the float reciprocal and one Newton correction
+            const F2 d{dd.x, dd.y};
+            const float r0 = __frcp_rn(d.h);
+            const F2 e = ffa::ff_sub(F2{1.f, 0.f}, ffa::ff_mul(d, F2{r0, 0.f}));
+            const F2 r = ffa::ff_add(F2{r0, 0.f}, ffa::ff_mul(F2{r0, 0.f}, e));
+            for (int a = j + 1 + lane; a <= s; a += 32) {
+                const float2 w = A[a * ld + j];
+                W[a] = w;
+                const F2 l = ffa::ff_mulr(F2{w.x, w.y}, r);
+                A[a * ld + j] = make_float2(l.h, l.l);
+            }
+            __syncwarp();
+            const int mm = s - j, ntr = mm * (mm + 1) / 2;
+            int ap = 0, cp = lane;
+            while (cp > ap) {
+                cp -= ap + 1;
+                ++ap;
+            }
+            for (int e2 = lane; e2 < ntr; e2 += 32) {
+                const int a = j + 1 + ap, c = j + 1 + cp;
+                const float2 la = A[a * ld + j], wc = W[c], ac = A[a * ld + c];
+                const F2 u = ffa::ff_add(F2{ac.x, ac.y}, ffa::ff_neg(ffa::ff_mul(F2{la.x, la.y}, F2{wc.x, wc.y})));
+                A[a * ld + c] = make_float2(u.h, u.l);
+                cp += 32;
+                while (cp > ap) {
+                    cp -= ap + 1;
+                    ++ap;
+                }
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+        if (!ok) ++tries;
+    }
+    const double cc = ok ? (double)A[s * ld + s].x + (double)A[s * ld + s].y : 0.0;
+    if (!ok || !(cc > 0.0)) {
+        if (lane == 0 && (!ok || tries == 0)) atomicAdd(njit, 1ull);
+        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = q == 0 ? 1.0 : 0.0;
+        return;
+    }
+    if (tries > 0 && lane == 0) atomicAdd(njit, 1ull);
+    // L_ss' lambda = (row s of L)'; entries a and a + 32 in the lanes' registers
+    float2 z0 = lane < s ? A[s * ld + lane] : make_float2(0.f, 0.f);
+    float2 z1 = lane + 32 < s ? A[s * ld + lane + 32] : make_float2(0.f, 0.f);
+    F2 l0{z0.x, z0.y}, l1{z1.x, z1.y};
+    for (int c = s - 1; c >= 0; --c) {
+        const F2 src = c >= 32 ? l1 : l0;
+        const F2 lc{__shfl_sync(full, src.h, c & 31), __shfl_sync(full, src.l, c & 31)};
+        if (lane < c) {
+            const float2 acl = A[c * ld + lane];
+            l0 = ffa::ff_add(l0, ffa::ff_neg(ffa::ff_mul(F2{acl.x, acl.y}, lc)));
+        }
+        if (s > 32 && lane + 32 < c) {
+            const float2 acl = A[c * ld + lane + 32];
+            l1 = ffa::ff_add(l1, ffa::ff_neg(ffa::ff_mul(F2{acl.x, acl.y}, lc)));
+        }
+    }
+    const double ic = rsqrt(cc);
+    if (lane == 0) val_ell[i] = ic;
+    if (lane < m) val_ell[(int64_t)(1 + lane) * n + i] = lane < s ? -ffa::to_d(l0) * ic : 0.0;
+    if (lane + 32 < m) val_ell[(int64_t)(33 + lane) * n + i] = lane + 32 < s ? -ffa::to_d(l1) * ic : 0.0;
+}
+
 // ---------------------------------------------------------------- transpose of U~ (rows of U~)
 __global__ void t_count(const int *nbr_ell, int64_t n, int m, int *cnt) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -826,7 +944,7 @@ void knn_prev_dev(const double2 *x, int64_t n, const int *order, int m, int *nbr
 }
 
 int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, double nu,
-                           double alpha, double *val_ell, cudaStream_t s) {
+                           double alpha, double *val_ell, cudaStream_t s, bool ff) {
     PHS_REQUIRE(m >= 1 && m <= KNN_MAXM, PHS_ERR_INVALID_ARG, "conditioning-set size m must be in 1..64");
     PHS_REQUIRE(nu == 0.5 || nu == 1.0 || nu == 1.5 || nu == 2.0 || nu == 2.5, PHS_ERR_INVALID_ARG,
                 "nu must be 0.5, 1, 1.5, 2 or 2.5");
@@ -843,12 +961,22 @@ int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const i
         PHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks_for(n, wpb), 32 * wpb, smem, s>>>(x, n, rank, nbr_ell, m, ld, 0.5 * alpha, val_ell, cnt.get());
     };
-    switch (nuc) {
-        case 0: launch(factor_kernel<0>); break;
-        case 1: launch(factor_kernel<1>); break;
-        case 2: launch(factor_kernel<2>); break;
-        case 3: launch(factor_kernel<3>); break;
-        default: launch(factor_kernel<4>); break;
+    if (ff) {
+        switch (nuc) {
+            case 0: launch(factor_kernel_ff<0>); break;
+            case 1: launch(factor_kernel_ff<1>); break;
+            case 2: launch(factor_kernel_ff<2>); break;
+            case 3: launch(factor_kernel_ff<3>); break;
+            default: launch(factor_kernel_ff<4>); break;
+        }
+    } else {
+        switch (nuc) {
+            case 0: launch(factor_kernel<0>); break;
+            case 1: launch(factor_kernel<1>); break;
+            case 2: launch(factor_kernel<2>); break;
+            case 3: launch(factor_kernel<3>); break;
+            default: launch(factor_kernel<4>); break;
+        }
     }
     PHS_LAUNCH_CHECK();
     unsigned long long h[2];
@@ -878,7 +1006,7 @@ void checked_ranks_dev(const int64_t *order, const int64_t *nbr, int64_t n, int 
 }
 
 void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t seed, double nu, double alpha,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool ff) {
     const int64_t n = ps.n;
     v.n = n;
     v.m = m;
@@ -898,7 +1026,7 @@ void vecchia_build(Vecchia &v, const PointSet &ps, int m, int ordering, uint64_t
     ranks_from_order<<<blocks_for(n, 256), 256, 0, s>>>(order_c.get(), n, rank_c.get());
     PHS_LAUNCH_CHECK();
     SBuf<double> val_c((size_t)(m + 1) * n, s);
-    v.jittered = vecchia_factor_dev(xcal.get(), n, rank_c.get(), nbr_c.get(), m, nu, alpha, val_c.get(), s);
+    v.jittered = vecchia_factor_dev(xcal.get(), n, rank_c.get(), nbr_c.get(), m, nu, alpha, val_c.get(), s, ff);
     // move to sorted positions: columns permuted by perm, entries mapped by iperm
     v.nbr.alloc((size_t)m * n);
     v.val.alloc((size_t)(m + 1) * n);
