@@ -67,8 +67,11 @@ typedef struct {
                                1: FP32 near field, FP64 far field;
                                2: FP32 near field and FP32 M2L, FP64 elsewhere;
                                3: FP32 throughout (order min(p, 24));
-                               4: near field in float-float (hi + lo FP32, about 2^-46 per
-                                  term) on the FP32 pipe, far field FP64 (M2L as m2l_tensor).
+                               4: near field, P2M, M2M, L2L, L2P (even k) and the local
+                                  factorisations of the preconditioner in float-float (hi +
+                                  lo FP32, about 2^-46 per operation) on the FP32 pipe, M2L
+                                  as m2l_tensor.  Odd k fits with 4 run the FP64 operator
+                                  (phs_matvec with 4 applies the float-float near field).
                                Modes 1-4 run inside FP64 iterative refinement: the
                                outer residual uses the FP64 FMM; residuals, inner
                                products, projection and preconditioner stay FP64.  Modes
@@ -98,12 +101,18 @@ typedef struct {
     double inner_tol;       /* precision 1-3: relative tolerance of each inner solve; default 1e-4
                                (precision 4 aims each inner solve at the final tolerance) */
     int max_refine;         /* precision 1-4: maximum refinement steps; default 8 */
-    int m2l_tensor;         /* even k, FP64 far field: 1 (default) runs the multipole-to-local
-                               translations (Sec. 2.1, Eq. 2.14) on the tensor cores in exact
-                               fixed point (bf16 digit planes, about 1e-12 relative); 0 runs
-                               them in FP64 on the CUDA cores.  A bounded device wait of the
-                               tensor-core path that expires is reported as PHS_ERR_TIMEOUT by
-                               the next phs_fit or phs_eval (phs_matvec is asynchronous). */
+    int m2l_tensor;         /* 1 (default): the log kernel's (even k) multipole-to-local
+                               translations (Sec. 2.1, Eq. 2.14) run on the tensor cores in
+                               exact fixed point (bf16 digit planes, about 1e-12 relative);
+                               the distance kernel's (odd k) compressed M2L in FP64.  2: the
+                               distance kernel's too (about 2e-12 relative to its FP64 form;
+                               its rounding is not symmetric at the 1e-14 level, which the CG
+                               fit of ill-conditioned odd-k systems does not tolerate -- the
+                               100,000-point cubic set then does not converge -- so meant for
+                               phs_matvec and phs_gmres).  0: both in FP64 on the CUDA cores.
+                               A bounded device wait of a tensor-core path that expires is
+                               reported as PHS_ERR_TIMEOUT by the next phs_fit or phs_eval
+                               (phs_matvec is asynchronous). */
     int precond_lowrank;    /* 1: the preconditioner is the inverse of Q_perp' S~ Q_perp
                                on range(P) (S~^{-1} = U U' the Vecchia factor), i.e.
                                S~^{-1} r - G (B' G)^{-1} G' r with G = S~^{-1} B -- the low-rank

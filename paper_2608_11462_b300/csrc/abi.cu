@@ -1081,7 +1081,8 @@ phs_status phs_plan_create(const double *pts_dev, int64_t n, int k, int poly_deg
         // V-list separation (Bernstein ellipse of a unit gap), q in [6, 16]
         const double eps_q = fmm_order > 0 ? std::pow(0.55, fmm_order) : o.fmm_eps;
         const int cq = std::max(6, std::min(16, (int)std::ceil(std::log(eps_q) / std::log(1.0 / 5.83)) + 1));
-        fmm_setup(pl->fmm, k, p, std::min(p, 24), cq, o.m2l_tensor != 0, pl->tree, s);
+        PHS_REQUIRE(o.m2l_tensor >= 0 && o.m2l_tensor <= 2, PHS_ERR_INVALID_ARG, "m2l_tensor must be 0, 1 or 2");
+        fmm_setup(pl->fmm, k, p, std::min(p, 24), cq, o.m2l_tensor, pl->tree, s);
         // thin QR of B by two rounds of Cholesky QR (Q has orthonormal columns, R upper)
         pl->Q.alloc((size_t)S * n);
         pl->R.alloc((size_t)S * S * 3);

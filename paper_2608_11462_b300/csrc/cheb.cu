@@ -31,6 +31,10 @@
 namespace phs {
 
 constexpr int kChebMaxQ = 16;
+// rank cap of the compressed M2L: the tensor-core form keeps 6 digit diagonals of its
+// output columns in 512 TMEM columns (6 x 80); at q = 16 the 81st singular value is
+// 8.3e-13 of the largest, so the cap costs no accuracy the interpolation has
+constexpr int kChebMaxRank = 80;
 constexpr int CHEB_T = 256;
 
 namespace {
@@ -451,7 +455,7 @@ static const ChebLowRank &cheb_lowrank(int q, double eps) {
     jacobi_right(qq, R, Vc, sv);
     int r = 0;
     while (r < qq && sv[r] > eps * sv[0]) ++r;
-    r = std::max(r, 1);
+    r = std::max(1, std::min(r, kChebMaxRank));
     ChebLowRank lr;
     lr.rt = lr.rs = r;
     lr.buf.assign((size_t)2 * qq * r + (size_t)49 * r * r, 0.0);
@@ -537,7 +541,7 @@ static const std::vector<double> &cheb_dev_tables(int q) {
     return cache.emplace(q, std::move(buf)).first->second;
 }
 
-void cheb_setup(Fmm &f, int q, double lr_eps, cudaStream_t s) {
+void cheb_setup(Fmm &f, int q, double lr_eps, bool tensor, const std::vector<long double> &mix, cudaStream_t s) {
     PHS_REQUIRE(q >= 3 && q <= kChebMaxQ, PHS_ERR_INVALID_ARG, "Chebyshev order must be in 3..16");
     f.cheb_q = q;
     const std::vector<double> &buf = cheb_dev_tables(q);  // cheb64: Tn [q*q] | A [2][q][q]
@@ -551,6 +555,9 @@ void cheb_setup(Fmm &f, int q, double lr_eps, cudaStream_t s) {
     PHS_CUDA(cudaMemcpyAsync(f.cheb_lr.get(), lr.buf.data(), lr.buf.size() * sizeof(double), cudaMemcpyHostToDevice,
                              s));
     PHS_CUDA(cudaStreamSynchronize(s));
+    f.ctc = false;
+    if (tensor && cheb_tc_supported(f.nd, lr.rs, lr.rt))
+        cheb_tc_setup(f, lr.buf.data() + (size_t)2 * q * q * lr.rt, mix, s);
 }
 
 void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, cudaStream_t s, Timers *tm) {
@@ -586,11 +593,15 @@ void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_
             cheb_compress<<<nb, CHEB_T, (size_t)nd * qq * sizeof(double), s>>>(b0, nd, qq, rs, V, f.cw64.get(),
                                                                                f.cwc64.get());
             PHS_LAUNCH_CHECK();
-            const int thr = std::max(32, (rt + 31) / 32 * 32);
-            cheb_m2l_lr<<<nb, thr, 2 * (size_t)nd * rs * sizeof(double), s>>>(
-                b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), nd, rt, rs, C, f.mix64.get(), f.cwc64.get(),
-                f.clc64.get());
-            PHS_LAUNCH_CHECK();
+            if (f.ctc) {
+                cheb_m2l_tc_pass(f, t, b0, f.cwc64.get(), f.clc64.get(), s);
+            } else {
+                const int thr = std::max(32, (rt + 31) / 32 * 32);
+                cheb_m2l_lr<<<nb, thr, 2 * (size_t)nd * rs * sizeof(double), s>>>(
+                    b0, t.v_off.get(), t.v_src.get(), t.v_cls.get(), nd, rt, rs, C, f.mix64.get(), f.cwc64.get(),
+                    f.clc64.get());
+                PHS_LAUNCH_CHECK();
+            }
             cheb_expand<<<nb, CHEB_T, (size_t)nd * rt * sizeof(double), s>>>(tv, b0, nd, qq, rt, f.power, U,
                                                                              f.clc64.get(), f.cl64.get());
             PHS_LAUNCH_CHECK();

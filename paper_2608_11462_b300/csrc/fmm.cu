@@ -1481,7 +1481,7 @@ static const DevTables &dev_tables_cached(int P) {
     return cache.emplace(P, std::move(d)).first->second;
 }
 
-void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s) {
+void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, int tensor_m2l, const Tree &t, cudaStream_t s) {
     PHS_REQUIRE(k >= 1 && k <= 5, PHS_ERR_INVALID_ARG, "k must be in 1..5");
     PHS_REQUIRE(p >= 2 && p + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "fmm_order must be in 2..60");
     PHS_REQUIRE(p32 >= 2 && p32 + 1 <= kMaxP, PHS_ERR_INVALID_ARG, "FP32 fmm order must be in 2..60");
@@ -1537,8 +1537,10 @@ void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const
     once_per_device(1, upload_log_tables);
     once_per_device(2, upload_ff_tables);
     // the compressed M2L truncates at a fifth of the accuracy the order was chosen for
-    // (q = the smallest order with 5.83^-(q-1) <= eps): rank 81 of 256 at q = 16
-    if (!f.log_core) cheb_setup(f, cheb_q, 0.2 * std::pow(5.83, -(double)(cheb_q - 1)), s);
+    // (q = the smallest order with 5.83^-(q-1) <= eps), capped at rank 80: 80 of 256 at q = 16
+    if (!f.log_core)
+        cheb_setup(f, cheb_q, 0.2 * std::pow(5.83, -(double)(cheb_q - 1)), tensor_m2l == 2, mix_cached(f.power, f.nd),
+                   s);
     m2l_tc_count(f, t, s);
 }
 

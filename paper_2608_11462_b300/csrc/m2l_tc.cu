@@ -36,10 +36,6 @@
 
 namespace phs {
 
-constexpr int TC_DB = 8;                     // bits per digit
-constexpr int TC_NPL = 6;                    // digit planes per operand
-constexpr int TC_QB = TC_DB * TC_NPL - 1;    // fixed point: |X| <= 2^47
-constexpr int TC_GB = 6;                     // guard bits kept through the frame change
 constexpr int TC_M = 128;                    // rows per tile (one TMEM lane each)
 constexpr int TC_KC = 48;                    // K columns per step
 constexpr int TC_KCC = TC_KC / 2;            // complex coefficients per step
@@ -49,8 +45,6 @@ __host__ __device__ constexpr int tc_staging_warps() { return ND == 4 ? TC_SW4 :
 template <int ND>
 __host__ __device__ constexpr int tc_threads() { return 32 * (tc_staging_warps<ND>() + 1); }
 constexpr int TC_A_PLANE = TC_M * TC_KC * 2; // bytes of one A digit plane
-constexpr int TC_NCLS = 49;
-constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
 
 bool m2l_tc_supported(int nd, int P) { return (nd == 4 || nd == 9) && P <= 64; }
 
@@ -69,43 +63,6 @@ struct TcArgs {
     uint64_t wait_ns;         // limit of the pipeline waits of the main loop
     int probe;                // nonzero: the issuer first waits on a barrier nothing completes
 };
-
-// round(x * 2^sh) for |x| * 2^sh < 2^62, from the bit pattern (no FP64 arithmetic);
-// the caller guarantees a right shift (sh small enough).  Zero and subnormals give 0.
-__device__ __forceinline__ long long to_fixed(double x, int sh) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((bits >> 52) & 0x7FF);
-    if (e == 0) return 0;
-    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-    const int r = 1075 - e - sh;
-    long long v;
-    if (r >= 64) v = 0;
-    else if (r <= 0) v = (long long)(m << (-r));
-    else v = (long long)((m + (1ull << (r - 1))) >> r);
-    return (long long)bits < 0 ? -v : v;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-// Balanced base-256 digits of |y| < 2^47 as floats, d[0] the top digit: with
-// z = y + 0x808080 the three low digits are the bytes of z minus 128 and the rest
-// follow from z >> 24 the same way.  Each byte becomes a float exactly by the
-// magic number 2^23 (bits 0x4B000000 | byte), so no integer-to-float conversion.
-__device__ __forceinline__ void digits_f(long long y, float *d) {
-    const long long z = y + 0x808080ll;
-    const unsigned lo = (unsigned)z;
-    const unsigned z2 = (unsigned)((int)(z >> 24) + 0x8080);
-    constexpr float kBias = 8388736.0f;  // 2^23 + 128
-    d[5] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7540)) - kBias;
-    d[4] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7541)) - kBias;
-    d[3] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7542)) - kBias;
-    d[2] = __int_as_float(__byte_perm(z2, 0x4B000000u, 0x7540)) - kBias;
-    d[1] = __int_as_float(__byte_perm(z2, 0x4B000000u, 0x7541)) - kBias;
-    d[0] = (float)((int)z2 >> 16);
-}
 
 // One warp per box: the exponent bound mexp = max over (b, k, re/im) of the exponent of
 // |a_b[k]| 2^floor(k/2) (so |a_b[k]| 2^floor(k/2) < 2^mexp), then the box's multipoles are
@@ -135,9 +92,6 @@ __global__ void tc_fixed_kernel(double2 *mp, int nbox, int nd, int P, int *mexp)
         xb[i] = make_longlong2(to_fixed(v.x, sh), to_fixed(v.y, sh));
     }
 }
-
-// rounding arithmetic right shift, 1 <= s <= 63
-__device__ __forceinline__ long long rshift_round(long long x, int s) { return (x + (1ll << (s - 1))) >> s; }
 
 template <int ND>
 struct TcLayout {
@@ -535,6 +489,32 @@ static inline uint16_t bf16_bits_of_int(int v) {
     return (uint16_t)(u >> 16);
 }
 
+// Integer frame changes (slots 0..48 of the mix table) and their growth bound (the rows
+// of a target convert at the finest row scale, so the largest growth may add at most 10
+// bits to the 52-bit converted sources: |y| < 2^62).  Shared with the distance kernel's
+// tensor-core M2L (cheb_tc.cu).
+void tc_integer_frames(int nd, const std::vector<long double> &mix, std::vector<int> &S, std::vector<int> &gexp) {
+    S.assign((size_t)TC_NCLS * nd * nd, 0);
+    gexp.assign((size_t)TC_NCLS * nd, 0);
+    for (int c = 0; c < TC_NCLS; ++c) {
+        for (int d = 0; d < nd; ++d) {
+            long long rs = 0;
+            for (int b = 0; b < nd; ++b) {
+                const long double v = mix[((size_t)c * nd + d) * nd + b];
+                const long long iv = std::llround(v);
+                PHS_REQUIRE(std::fabs(v - (long double)iv) < 1e-6L, PHS_ERR_INVALID_ARG,
+                            "tensor-core M2L: frame change is not integral");
+                S[((size_t)c * nd + d) * nd + b] = (int)iv;
+                rs += std::llabs(iv);
+            }
+            int g = 0;
+            while ((1ll << g) < std::max(rs, 1ll)) ++g;
+            PHS_REQUIRE(g <= 10, PHS_ERR_INVALID_ARG, "tensor-core M2L: frame-change growth above 2^10");
+            gexp[(size_t)c * nd + d] = g;
+        }
+    }
+}
+
 struct TcHostTables {
     std::vector<uint16_t> B;
     std::vector<int> F, S, gexp;
@@ -625,27 +605,8 @@ static TcHostTables build_tc_tables(int P, int nd, const std::vector<long double
                         B[(((size_t)c * nch + h) * TC_NPL + j) * plane + boff] = bf16_bits_of_int(dig[j]);
                 }
     }
-    // integer frame changes (slots 0..48 of the mix table) and their growth bound
-    // (the rows of a target convert at the finest row scale, so the largest growth may
-    // add at most 10 bits to the 52-bit converted sources: |y| < 2^62)
-    std::vector<int> S((size_t)TC_NCLS * nd * nd, 0), gexp((size_t)TC_NCLS * nd, 0);
-    for (int c = 0; c < TC_NCLS; ++c) {
-        for (int d = 0; d < nd; ++d) {
-            long long rs = 0;
-            for (int b = 0; b < nd; ++b) {
-                const long double v = mix[((size_t)c * nd + d) * nd + b];
-                const long long iv = std::llround(v);
-                PHS_REQUIRE(std::fabs(v - (long double)iv) < 1e-6L, PHS_ERR_INVALID_ARG,
-                            "tensor-core M2L: frame change is not integral");
-                S[((size_t)c * nd + d) * nd + b] = (int)iv;
-                rs += std::llabs(iv);
-            }
-            int g = 0;
-            while ((1ll << g) < std::max(rs, 1ll)) ++g;
-            PHS_REQUIRE(g <= 10, PHS_ERR_INVALID_ARG, "tensor-core M2L: frame-change growth above 2^10");
-            gexp[(size_t)c * nd + d] = g;
-        }
-    }
+    std::vector<int> S, gexp;
+    tc_integer_frames(nd, mix, S, gexp);
     // nd = 4: the frame change has the closed form of [1, a, x, y] shifted by o = (ox, oy)
     std::vector<int2> off(TC_NCLS, make_int2(0, 0));
     if (nd == 4) {
@@ -749,7 +710,7 @@ void m2l_tc_count(Fmm &f, const Tree &t, cudaStream_t s) {
 }
 
 void m2l_tc_check(Fmm &f, cudaStream_t s) {
-    if (!f.tc || !f.tc_err.get()) return;
+    if ((!f.tc && !f.ctc) || !f.tc_err.get()) return;
     int h = 0;
     PHS_CUDA(cudaMemcpyAsync(&h, f.tc_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     PHS_CUDA(cudaStreamSynchronize(s));

@@ -248,6 +248,12 @@ struct Fmm {
     DBuf<double> cheb64;                 // Tn [q][q] | A [2][q][q]
     DBuf<double> cheb_lr;                // compressed M2L: U' [rt][q*q] | V [q*q][rs] | C' [49][rs][rt]
     DBuf<double> cwc64, clc64;           // compressed weights [box][nd][rs], potentials [box][nd][rt]
+    // its M2L on the tensor cores (cheb_tc.cu)
+    bool ctc = false;
+    int ctc_npad = 0, ctc_nch = 0;       // output columns (rank rounded up to 16), K chunks of 32
+    DBuf<uint16_t> ctc_b;                // operator digit planes (bf16 bits)
+    DBuf<int> ctc_F;                     // column exponents [rt]
+    DBuf<int> ctc_mexp;                  // per-box exponent bound of the compressed weights
     DBuf<double> cw64, cl64;             // weights/potentials at nodes [box][nd][q*q]
     // tensor-core M2L of the log kernel (m2l_tc.cu)
     bool tc = false;                     // use it for the FP64 far field
@@ -274,8 +280,9 @@ struct Fmm {
     Fmm &operator=(const Fmm &) = delete;
     ~Fmm();
 };
-// tensor_m2l: run the FP64 M2L of the log kernel on the tensor cores (m2l_tc.cu)
-void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, bool tensor_m2l, const Tree &t, cudaStream_t s);
+// tensor_m2l: 1 runs the FP64 M2L of the log kernel on the tensor cores (m2l_tc.cu), 2
+// the distance kernel's compressed M2L too (cheb_tc.cu), 0 neither
+void fmm_setup(Fmm &f, int k, int p, int p32, int cheb_q, int tensor_m2l, const Tree &t, cudaStream_t s);
 // tensor-core M2L (m2l_tc.cu): setup from the class operators (slots 8 + cls of the
 // level-invariant operator table, [57][P][P] complex) and the frame changes ([57][nd][nd]);
 // the pass writes lc for every box (zero where the interaction list is empty)
@@ -289,9 +296,19 @@ void m2l_tc_count(Fmm &f, const Tree &t, cudaStream_t s);
 int m2l_tc_mmas_per_step();
 // throws PHS_ERR_TIMEOUT if a tensor-core wait expired since the last check (synchronises s)
 void m2l_tc_check(Fmm &f, cudaStream_t s);
+// integer frame changes (slots 0..48 of the mix table) and their growth bound, shared
+// by the tensor-core M2L passes (m2l_tc.cu)
+void tc_integer_frames(int nd, const std::vector<long double> &mix, std::vector<int> &S, std::vector<int> &gexp);
 // distance-kernel far field (cheb.cu)
 // q Chebyshev nodes per axis; the M2L operators compressed to relative accuracy lr_eps
-void cheb_setup(Fmm &f, int q, double lr_eps, cudaStream_t s);
+// (rank at most 80); tensor: its M2L on the tensor cores where supported (cheb_tc.cu)
+void cheb_setup(Fmm &f, int q, double lr_eps, bool tensor, const std::vector<long double> &mix, cudaStream_t s);
+// the compressed M2L on the tensor cores (cheb_tc.cu): setup from the transposed class
+// operators C' [49][rs][rt]; the pass writes the compressed potentials of boxes b0..
+// (overwritten) and rewrites the compressed weights wc in place as per-box fixed point
+bool cheb_tc_supported(int nd, int rs, int rt);
+void cheb_tc_setup(Fmm &f, const double *Ct, const std::vector<long double> &mix, cudaStream_t s);
+void cheb_m2l_tc_pass(Fmm &f, const Tree &t, int b0, double *wc, double *lc, cudaStream_t s);
 void cheb_far_field(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, cudaStream_t s,
                     struct Timers *tm);
 void cheb_l2p_apply(Fmm &f, const Tree &t, const PointSet &ps, double *y, cudaStream_t s);

@@ -2,6 +2,7 @@
 // tensor memory (TMEM) and shared-memory mbarriers on sm_103a.
 #pragma once
 #include <stdint.h>
+#include <cuda_bf16.h>
 
 namespace phs {
 namespace tc {
@@ -161,4 +162,55 @@ __host__ __device__ __forceinline__ uint32_t kmajor_offset(int r, int k, int kco
 }
 
 }  // namespace tc
+
+// ---- exact fixed point on bf16 digit planes, shared by the tensor-core M2L passes
+// (m2l_tc.cu for the log kernel, cheb_tc.cu for the distance kernel)
+constexpr int TC_DB = 8;                     // bits per digit
+constexpr int TC_NPL = 6;                    // digit planes per operand
+constexpr int TC_QB = TC_DB * TC_NPL - 1;    // fixed point: |X| <= 2^47
+constexpr int TC_GB = 6;                     // guard bits kept through the frame change
+constexpr int TC_NCLS = 49;
+constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
+
+// round(x * 2^sh) for |x| * 2^sh < 2^62, from the bit pattern (no FP64 arithmetic);
+// the caller guarantees a right shift (sh small enough).  Zero and subnormals give 0.
+__device__ __forceinline__ long long to_fixed(double x, int sh) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    if (e == 0) return 0;
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int r = 1075 - e - sh;
+    long long v;
+    if (r >= 64) v = 0;
+    else if (r <= 0) v = (long long)(m << (-r));
+    else v = (long long)((m + (1ull << (r - 1))) >> r);
+    return (long long)bits < 0 ? -v : v;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Balanced base-256 digits of |y| < 2^47 as floats, d[0] the top digit: with
+// z = y + 0x808080 the three low digits are the bytes of z minus 128 and the rest
+// follow from z >> 24 the same way.  Each byte becomes a float exactly by the
+// magic number 2^23 (bits 0x4B000000 | byte), so no integer-to-float conversion.
+__device__ __forceinline__ void digits_f(long long y, float *d) {
+    const long long z = y + 0x808080ll;
+    const unsigned lo = (unsigned)z;
+    const unsigned z2 = (unsigned)((int)(z >> 24) + 0x8080);
+    constexpr float kBias = 8388736.0f;  // 2^23 + 128
+    d[5] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7540)) - kBias;
+    d[4] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7541)) - kBias;
+    d[3] = __int_as_float(__byte_perm(lo, 0x4B000000u, 0x7542)) - kBias;
+    d[2] = __int_as_float(__byte_perm(z2, 0x4B000000u, 0x7540)) - kBias;
+    d[1] = __int_as_float(__byte_perm(z2, 0x4B000000u, 0x7541)) - kBias;
+    d[0] = (float)((int)z2 >> 16);
+}
+
+// rounding arithmetic right shift, 1 <= s <= 63
+__device__ __forceinline__ long long rshift_round(long long x, int s) { return (x + (1ll << (s - 1))) >> s; }
+
+
 }  // namespace phs
