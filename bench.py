@@ -558,7 +558,9 @@ def main():
                     "peak_source": f"derived: 148 SMs x 128 FP32 lanes x {sm_mhz_max:.0f} MHz",
                     "work_per_launch": f"{kwork['p2p_pairs']} pairs evaluated ({kwork['p2p_column_pairs']} with "
                                        f"column sums) = {p2p_ops} FP32-pipe instr; {work['near_pairs']} ordered near "
-                                       f"pairs", "ms_per_launch": ms_p2p, "traffic": P2P_FF_DRAM_BYTES_PER_POINT * n
+                                       f"pairs", "ms_per_launch": ms_p2p,
+                    "gpairs_per_s": work["near_pairs"] / (ms_p2p / 1e3) / 1e9,
+                    "traffic": P2P_FF_DRAM_BYTES_PER_POINT * n
                     if P2P_FF_DRAM_BYTES_PER_POINT else None}
     else:
         # FP64 pipe: 2 instructions (DFMA, DMUL or DADD) per clock per SM.  Per evaluated pair:
@@ -572,7 +574,8 @@ def main():
                     "peak_source": f"derived: 148 SMs x 2 FP64 instr/clk x {sm_mhz_max:.0f} MHz",
                     "work_per_launch": f"{kwork['p2p_pairs']} pairs evaluated ({kwork['p2p_column_pairs']} with "
                                        f"column sums) = {p2p_ops} FP64 instr; {work['near_pairs']} ordered near pairs",
-                    "ms_per_launch": ms_p2p, "traffic": P2P_DRAM_BYTES_PER_POINT * n}
+                    "ms_per_launch": ms_p2p, "gpairs_per_s": work["near_pairs"] / (ms_p2p / 1e3) / 1e9,
+                    "traffic": P2P_DRAM_BYTES_PER_POINT * n}
     ms_m2l = phases["m2l"][0] / max(phases["m2l"][1], 1)
     roof_m2l = None
     if kwork["tc_steps"] > 0:

@@ -4,6 +4,9 @@
 // so the compiler neither contracts nor reorders them.  Shared by the float-float near
 // field and the float-float P2M / L2P.
 #pragma once
+#include <cmath>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace phs {
@@ -128,6 +131,64 @@ __device__ __forceinline__ void had_u_ff(F2 x, F2 y, F2 *u) {
         u[6] = ff_add(ff_scale(xx, 4.f), ff_scale(a, 2.f));
         u[7] = ff_scale(ff_mulr(x, y), 8.f);
         u[8] = ff_add(ff_scale(yy, 4.f), ff_scale(a, 2.f));
+    }
+}
+
+// s = dx^2 + dy^2, renormalised so that |s.l| <= ulp(s.h) / 2
+__device__ __forceinline__ F2 ff_norm2(F2 dx, F2 dy) {
+    F2 px = two_prod(dx.h, dx.h);
+    px.l = __fmaf_rn(2.0f * dx.h, dx.l, px.l);
+    F2 py = two_prod(dy.h, dy.h);
+    py.l = __fmaf_rn(2.0f * dy.h, dy.l, py.l);
+    F2 s = two_sum(px.h, py.h);
+    s.l = __fadd_rn(s.l, __fadd_rn(px.l, py.l));
+    return fast_two_sum(s.h, s.l);
+}
+
+// log(s.h + s.l) for s > 0 with absolute error about 2^-46 max(1, |log s|); s = 0 (a
+// point paired with itself) returns a finite value, so s log s is 0 there
+__device__ __forceinline__ F2 ff_log(F2 s, const float *rcp, const float2 *tlog, const float2 *eln2) {
+    const unsigned bits = __float_as_uint(s.h);
+    const int j = (int)((bits >> 15) & 0xffu);
+    const float m = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);
+    const float2 E = eln2[(bits >> 23) & 0xffu];  // s >= +0 by construction; the mask keeps the index in range
+    const float2 T = tlog[j];
+    const float u = __fmaf_rn(m, rcp[j], -1.0f);  // exact
+    const F2 p2 = two_prod(u, u);
+    float q = __fmaf_rn(u, 0.2f, -0.25f);
+    q = __fmaf_rn(u, q, 0.333333343f);
+    const float tail = __fmul_rn(__fmul_rn(u, p2.h), q);  // u^3 (1/3 - u/4 + u^2/5)
+    const F2 h = fast_two_sum(u, -0.5f * p2.h);            // |u| >= u^2 / 2
+    const float lo1p = __fadd_rn(h.l, __fsub_rn(tail, 0.5f * p2.l));
+    const F2 a = two_sum(E.x, T.x);
+    const F2 b = two_sum(a.h, h.h);
+    float lo = __fadd_rn(__fadd_rn(E.y, T.y), lo1p);
+    lo = __fadd_rn(lo, __fadd_rn(a.l, b.l));
+    // log(s.h + s.l) = log(s.h) + s.l / s.h + O(2^-48)
+    lo = __fmaf_rn(s.l, rcp_approx(fmaxf(s.h, 1e-30f)), lo);
+    return {b.h, lo};
+}
+
+// The tables of ff_log (host side): R_j (1/c_j rounded to 9 significant bits, c_j the
+// centre of the j-th of 256 mantissa cells), -log R_j and (e - 127) log 2 for the biased
+// FP32 exponents e, each logarithm split into hi + lo floats.
+inline void ff_log_tables(std::vector<float> &rc, std::vector<float2> &tl, std::vector<float2> &el) {
+    rc.resize(256);
+    tl.resize(256);
+    el.resize(256);
+    for (int j = 0; j < 256; ++j) {
+        const long double c = 1.0L + ((long double)j + 0.5L) / 256.0L;
+        // 1/c rounded to 9 significant bits: 1/c in (1/2, 1), so a multiple of 2^-9
+        const long double r = std::nearbyint(512.0L / c) / 512.0L;
+        rc[j] = (float)r;
+        const long double v = -std::log(r);
+        const float h = (float)v;
+        tl[j] = make_float2(h, (float)(v - (long double)h));
+    }
+    for (int be = 0; be < 256; ++be) {
+        const long double v = (long double)(be - 127) * std::log(2.0L);
+        const float h = (float)v;
+        el[be] = make_float2(h, (float)(v - (long double)h));
     }
 }
 

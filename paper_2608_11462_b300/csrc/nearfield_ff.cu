@@ -49,41 +49,6 @@ __device__ float g_ff_rcp[kFfTab];    // R_j, 9 significant bits
 __device__ float2 g_ff_tlog[kFfTab];  // -log R_j as (hi, lo)
 __device__ float2 g_ff_eln2[kFfExp];  // (e - 127) log 2 as (hi, lo), e the biased exponent
 
-// s = dx^2 + dy^2, renormalised so that |s.l| <= ulp(s.h) / 2
-__device__ __forceinline__ F2 ff_norm2(F2 dx, F2 dy) {
-    F2 px = two_prod(dx.h, dx.h);
-    px.l = __fmaf_rn(2.0f * dx.h, dx.l, px.l);
-    F2 py = two_prod(dy.h, dy.h);
-    py.l = __fmaf_rn(2.0f * dy.h, dy.l, py.l);
-    F2 s = two_sum(px.h, py.h);
-    s.l = __fadd_rn(s.l, __fadd_rn(px.l, py.l));
-    return fast_two_sum(s.h, s.l);
-}
-
-// log(s.h + s.l) for s > 0 with absolute error about 2^-46 max(1, |log s|); s = 0 (a
-// point paired with itself) returns a finite value, so s log s is 0 there
-__device__ __forceinline__ F2 ff_log(F2 s, const float *rcp, const float2 *tlog, const float2 *eln2) {
-    const unsigned bits = __float_as_uint(s.h);
-    const int j = (int)((bits >> 15) & 0xffu);
-    const float m = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);
-    const float2 E = eln2[(bits >> 23) & 0xffu];  // s >= +0 by construction; the mask keeps the index in range
-    const float2 T = tlog[j];
-    const float u = __fmaf_rn(m, rcp[j], -1.0f);  // exact
-    const F2 p2 = two_prod(u, u);
-    float q = __fmaf_rn(u, 0.2f, -0.25f);
-    q = __fmaf_rn(u, q, 0.333333343f);
-    const float tail = __fmul_rn(__fmul_rn(u, p2.h), q);  // u^3 (1/3 - u/4 + u^2/5)
-    const F2 h = fast_two_sum(u, -0.5f * p2.h);            // |u| >= u^2 / 2
-    const float lo1p = __fadd_rn(h.l, __fsub_rn(tail, 0.5f * p2.l));
-    const F2 a = two_sum(E.x, T.x);
-    const F2 b = two_sum(a.h, h.h);
-    float lo = __fadd_rn(__fadd_rn(E.y, T.y), lo1p);
-    lo = __fadd_rn(lo, __fadd_rn(a.l, b.l));
-    // log(s.h + s.l) = log(s.h) + s.l / s.h + O(2^-48)
-    lo = __fmaf_rn(s.l, rcp_approx(fmaxf(s.h, 1e-30f)), lo);
-    return {b.h, lo};
-}
-
 // r = sqrt(s.h + s.l): r0 from the approximate reciprocal square root, then one
 // correction (s - r0^2) / (2 r0) with s - r0^2 formed exactly by an FMA
 __device__ __forceinline__ F2 ff_sqrt(F2 s) {
@@ -255,22 +220,9 @@ __global__ void __launch_bounds__(NF_T) p2p_sym_ff_kernel(TreeView tv, int nleaf
 
 // R_j, -log R_j and e log 2 for the logarithm, loaded on the current device
 void upload_ff_tables() {
-    std::vector<float> rc(kFfTab);
-    std::vector<float2> tl(kFfTab), el(kFfExp);
-    for (int j = 0; j < kFfTab; ++j) {
-        const long double c = 1.0L + ((long double)j + 0.5L) / 256.0L;
-        // 1/c rounded to 9 significant bits: 1/c in (1/2, 1), so a multiple of 2^-9
-        const long double r = std::nearbyint(512.0L / c) / 512.0L;
-        rc[j] = (float)r;
-        const long double v = -std::log(r);
-        const float h = (float)v;
-        tl[j] = make_float2(h, (float)(v - (long double)h));
-    }
-    for (int be = 0; be < kFfExp; ++be) {
-        const long double v = (long double)(be - 127) * std::log(2.0L);
-        const float h = (float)v;
-        el[be] = make_float2(h, (float)(v - (long double)h));
-    }
+    std::vector<float> rc;
+    std::vector<float2> tl, el;
+    ffa::ff_log_tables(rc, tl, el);
     PHS_CUDA(cudaMemcpyToSymbol(g_ff_rcp, rc.data(), kFfTab * sizeof(float)));
     PHS_CUDA(cudaMemcpyToSymbol(g_ff_tlog, tl.data(), kFfTab * sizeof(float2)));
     PHS_CUDA(cudaMemcpyToSymbol(g_ff_eln2, el.data(), kFfExp * sizeof(float2)));

@@ -332,6 +332,18 @@ __device__ __forceinline__ double vtab_log(double x) {
     return fma(c, r, fj.x + __ldg(&g_veln2[ei]));
 }
 
+// float-float forms for the precision-4 factor (factor_kernel_ff): the same series with
+// the coefficients split into hi + lo floats and the logarithm of ff.cuh (ff_log)
+__constant__ float2 c_s1f[kSerTerms], c_p1f[kSerTerms], c_s0f[kSerTerms], c_h0f[kSerTerms];
+__device__ float g_vf_rcp[256];
+__device__ float2 g_vf_tlog[256], g_vf_eln2[256];
+
+__device__ __forceinline__ ffa::F2 horner_ff(const float2 *c, int nt, ffa::F2 q) {
+    ffa::F2 v{c[nt - 1].x, c[nt - 1].y};
+    for (int k = nt - 2; k >= 0; --k) v = ffa::ff_add(ffa::ff_mul(v, q), ffa::F2{c[k].x, c[k].y});
+    return v;
+}
+
 __device__ __forceinline__ double horner(const double *c, int nt, double q) {
     double v = c[nt - 1];
     for (int k = nt - 2; k >= 0; --k) v = fma(v, q, c[k]);
@@ -413,6 +425,49 @@ static void upload_bessel_tables() {
     PHS_CUDA(cudaMemcpyToSymbol(c_s0, d[2], sizeof(d[2])));
     PHS_CUDA(cudaMemcpyToSymbol(c_h0, d[3], sizeof(d[3])));
     PHS_CUDA(cudaMemcpyToSymbol(c_cosh, ch, sizeof(ch)));
+    float2 f[4][kSerTerms];
+    for (int k = 0; k < kSerTerms; ++k) {
+        const long double src[4] = {s1[k], p1[k], s0[k], h0[k]};
+        for (int t = 0; t < 4; ++t) {
+            const float h = (float)src[t];
+            f[t][k] = make_float2(h, (float)(src[t] - (long double)h));
+        }
+    }
+    PHS_CUDA(cudaMemcpyToSymbol(c_s1f, f[0], sizeof(f[0])));
+    PHS_CUDA(cudaMemcpyToSymbol(c_p1f, f[1], sizeof(f[1])));
+    PHS_CUDA(cudaMemcpyToSymbol(c_s0f, f[2], sizeof(f[2])));
+    PHS_CUDA(cudaMemcpyToSymbol(c_h0f, f[3], sizeof(f[3])));
+    std::vector<float> frc;
+    std::vector<float2> ftl, fel;
+    ffa::ff_log_tables(frc, ftl, fel);
+    PHS_CUDA(cudaMemcpyToSymbol(g_vf_rcp, frc.data(), 256 * sizeof(float)));
+    PHS_CUDA(cudaMemcpyToSymbol(g_vf_tlog, ftl.data(), 256 * sizeof(float2)));
+    PHS_CUDA(cudaMemcpyToSymbol(g_vf_eln2, fel.data(), 256 * sizeof(float2)));
+}
+
+// The Matern entry in float-float from the float-float scaled squared distance q: the
+// series of nu = 1 and nu = 2 (the thin-plate and k = 4 preconditioners) for q < 1, the
+// FP64 form otherwise (the other smoothness values and q >= 1), then split.
+template <int NUC>
+__device__ __forceinline__ ffa::F2 matern_ff(ffa::F2 q) {
+    using ffa::F2;
+    if constexpr (NUC == 1 || NUC == 3) {
+        if (q.h < 1.0f && q.h > 1e-30f) {
+            const float qh = q.h;
+            const int nt = qh < 0x1p-18f ? 3 : (qh < 0x1p-14f ? 4 : (qh < 0x1p-6f ? 6 : (qh < 0x1p-3f ? 9 : kSerTerms)));
+            const F2 lq = ffa::ff_log(q, g_vf_rcp, g_vf_tlog, g_vf_eln2);
+            const F2 ak1 = ffa::ff_add(F2{1.f, 0.f},
+                                       ffa::ff_mul(q, ffa::ff_sub(ffa::ff_mul(lq, horner_ff(c_s1f, nt, q)),
+                                                                  horner_ff(c_p1f, nt, q))));
+            if constexpr (NUC == 1) return ak1;
+            // nu = 2: a^2 K_2(a) / 2 = 2 q K_0 + a K_1, K_0 = -(log(a/2) + gamma) S_0 + H_0
+            const F2 gam{0x1.2788dp-1f, -0x1.c824f4p-28f};  // Euler gamma, hi + lo
+            const F2 g = ffa::ff_add(ffa::ff_scale(lq, 0.5f), gam);
+            const F2 k0 = ffa::ff_sub(horner_ff(c_h0f, nt, q), ffa::ff_mul(g, horner_ff(c_s0f, nt, q)));
+            return ffa::ff_add(ffa::ff_scale(ffa::ff_mul(q, k0), 2.0f), ak1);
+        }
+    }
+    return ffa::split_d(matern_q<NUC>(ffa::to_d(q)));
 }
 
 // 1/d for normal d > 0: the hardware approximation rcp.approx.ftz.f64 (measured on this
@@ -548,16 +603,17 @@ __global__ void factor_kernel_ff(const double2 *x, int64_t n, const int *rank, c
     double *base = fsm + (size_t)wib * per;
     float2 *A = reinterpret_cast<float2 *>(base);
     float2 *W = A + (m + 1) * ld;
-    double *X = base + (m + 1) * ld + (m + 1);
-    double *Y = X + (m + 1);
+    float2 *X = W + (m + 1);  // scaled coordinates, hi + lo
+    float2 *Y = X + (m + 1);
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (i >= n) return;
     const unsigned full = 0xffffffffu;
     const int s = min(m, rank[i]);
     for (int a = lane; a <= s; a += 32) {
         const double2 p = a < s ? x[nbr_ell[(int64_t)a * n + i]] : x[i];
-        X[a] = p.x * halpha;
-        Y[a] = p.y * halpha;
+        const F2 px = ffa::split_d(p.x * halpha), py = ffa::split_d(p.y * halpha);
+        X[a] = make_float2(px.h, px.l);
+        Y[a] = make_float2(py.h, py.l);
     }
     __syncwarp();
     const int nn = s + 1, ntri = nn * (nn + 1) / 2;
@@ -570,15 +626,15 @@ __global__ void factor_kernel_ff(const double2 *x, int64_t n, const int *rank, c
             while (a * (a + 1) / 2 > idx) --a;
             while ((a + 1) * (a + 2) / 2 <= idx) ++a;
             const int b = idx - a * (a + 1) / 2;
-            double v;
+            F2 vf;
             if (b == a) {
-                v = a < s ? 1.0 + jit : 1.0;  // jitter on K_ss only
+                vf = ffa::split_d(a < s ? 1.0 + jit : 1.0);  // jitter on K_ss only
             } else {
-                const double dx = X[a] - X[b], dy = Y[a] - Y[b];
-                const double q = fma(dx, dx, dy * dy);
-                v = __double2hiint(q) > 0 ? matern_q<NUC>(q) : 1.0;
+                const float2 xa = X[a], xb = X[b], ya = Y[a], yb = Y[b];
+                const F2 q = ffa::ff_norm2(ffa::ff_sub(F2{xa.x, xa.y}, F2{xb.x, xb.y}),
+                                           ffa::ff_sub(F2{ya.x, ya.y}, F2{yb.x, yb.y}));
+                vf = q.h > 0.f ? matern_ff<NUC>(q) : F2{1.f, 0.f};
             }
-            const F2 vf = ffa::split_d(v);
             A[a * ld + b] = make_float2(vf.h, vf.l);
         }
         __syncwarp();
