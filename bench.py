@@ -584,8 +584,9 @@ def main():
         ach = flops / (ms_m2l / 1e3) / 1e12
         roof_m2l = {"kernel": "m2l_tc_kernel<4>", "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                     "frac": ach / pk, "peak_source": "measured bf16 (sustained, kernel inside a long step)",
-                    "work_per_launch": f"{kwork['tc_steps']} steps x {kwork['tc_mmas_per_step']} tcgen05.mma x "
-                                       f"{kwork['tc_mma_macs']} MAC (bf16 digit planes, FP32 accumulate)",
+                    "work_per_launch": f"{kwork['tc_steps']} steps x {kwork['tc_mmas_per_step']} digit-plane "
+                                       f"products x {kwork['tc_mma_macs']} MAC (bf16, FP32 accumulate; issued as "
+                                       f"tcgen05.mma spanning up to 256 output columns)",
                     "ms_per_launch": ms_m2l,
                     "traffic": M2L_DRAM_BYTES_PER_TILE * kwork["tc_tiles"]}
     if roof_m2l is not None and ms_m2l > ms_p2p:

@@ -262,8 +262,9 @@ phs_status phs_plan_memory(phs_plan_t plan, int64_t *bytes_host);
  *   [2] tensor-core M2L steps (offset class x 48-column K chunk, summed over the
  *       16-box tiles; 0 when the M2L runs on the CUDA cores),
  *   [3] tensor-core M2L tiles,
- *   [4] tcgen05.mma instructions per step,
- *   [5] multiply-adds of one instruction (M * N * K). */
+ *   [4] digit-plane products per step (plane pairs x 16-deep K slices; the pass issues
+ *       them as fewer tcgen05.mma, each spanning several B planes along N),
+ *   [5] multiply-adds of one product (M * N * K, N = output columns padded to 16). */
 phs_status phs_plan_kernel_work(phs_plan_t plan, int64_t *counts_host);
 /* Diagnostics and test hook of the tensor-core M2L's bounded waits (no counterpart in
  * the paper).  ns: wall-time limit of each pipeline wait in the pass's main loop (0

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(CT_T, 1) cheb_m2l_tc_kernel(CtArgs a) {
     __syncthreads();
     const uint32_t tmem = misc[0];
     const int nsteps = (int)misc[1] * a.nch;
-    const uint32_t idesc = tc::idesc_bf16_f32(CT_M, a.npad);
+    const int pl_per_mma = 256 / a.npad;  // B planes per MMA: N = planes x npad <= 256
     const uint64_t adesc0 = tc::make_desc_kmajor(tc::smem_u32(Abuf), 128, (CT_KC / 8) * 128);
     const uint64_t bdesc0 = tc::make_desc_kmajor(tc::smem_u32(Bbuf), 128, (CT_KC / 8) * 128);
     uint32_t inited = 0;      // accumulators written at least once (issuer)
@@ -292,17 +292,21 @@ __global__ void __launch_bounds__(CT_T, 1) cheb_m2l_tc_kernel(CtArgs a) {
             tc::fence_after_sync();
             const uint64_t au = adesc0 + (uint64_t)((u * TC_NPL * CT_A_PLANE) >> 4);
             const uint64_t bu = bdesc0 + (uint64_t)((u * lay.bstep) >> 4);
+            // one MMA per A plane i and run of B planes j0 .. j0 + nj - 1 (consecutive along N,
+            // N = nj x npad <= 256): each product lands on its diagonal i + j; plane i = 0
+            // covers every diagonal first, so an MMA's diagonals are all fresh or all summed
 #pragma unroll 1
             for (int ks = 0; ks < CT_KC / 16; ++ks) {
 #pragma unroll
                 for (int i = 0; i < TC_NPL; ++i) {
                     const uint64_t ad = au + (uint64_t)((i * CT_A_PLANE + ks * 256) >> 4);
-#pragma unroll
-                    for (int j = 0; j < TC_NPL - i; ++j) {
-                        const int g = i + j;
-                        const uint64_t bd = bu + (uint64_t)((j * lay.bplane + ks * 256) >> 4);
-                        tc::mma_bf16(tmem + (uint32_t)(g * a.npad), ad, bd, idesc, (inited >> g) & 1);
-                        inited |= 1u << g;
+                    for (int j0 = 0; j0 < TC_NPL - i; j0 += pl_per_mma) {
+                        const int nj = min(pl_per_mma, TC_NPL - i - j0);
+                        const int g = i + j0;
+                        const uint64_t bd = bu + (uint64_t)((j0 * lay.bplane + ks * 256) >> 4);
+                        tc::mma_bf16(tmem + (uint32_t)(g * a.npad), ad, bd, tc::idesc_bf16_f32(CT_M, nj * a.npad),
+                                     (inited >> g) & 1);
+                        inited |= ((1u << nj) - 1) << g;
                     }
                 }
             }

@@ -50,7 +50,8 @@ bool m2l_tc_supported(int nd, int P) { return (nd == 4 || nd == 9) && P <= 64; }
 
 struct TcArgs {
     TreeView tv;
-    int b0, nbox;
+    const int *tgt;           // target boxes, 16 per tile in list order
+    int ntgt;
     const int *v_off, *v_src;
     const unsigned char *v_cls;
     int P, npad, nch, power;
@@ -97,7 +98,7 @@ template <int ND>
 struct TcLayout {
     static constexpr int TPB = TC_M / (2 * ND);  // targets per tile
     int bplane, bstep;
-    size_t off_B, off_vsrc, off_vsh, off_cflag, off_clist, off_E, off_lsum, off_mbar, off_misc, total;
+    size_t off_B, off_vsrc, off_vsh, off_cflag, off_clist, off_E, off_lsum, off_mbar, off_misc, off_coff, total;
     __host__ __device__ TcLayout(int npad) {
         bplane = npad * TC_KC * 2;
         bstep = TC_NPL * bplane;
@@ -110,7 +111,8 @@ struct TcLayout {
         off_lsum = (off_E + (size_t)TPB * (ND + 1) * 4 + 7) & ~(size_t)7;
         off_mbar = off_lsum + (size_t)TPB * ND * 8;
         off_misc = off_mbar + 7 * 8;
-        total = off_misc + 16;
+        off_coff = off_misc + 16;                        // [49] class offsets (nd = 4)
+        total = off_coff + (size_t)TC_NCLS * 8;
     }
 };
 
@@ -150,14 +152,18 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
     long long *lsum = reinterpret_cast<long long *>(sm + lay.off_lsum);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + lay.off_mbar);  // empty[2], bfull[2], done, full[2]
     uint32_t *misc = reinterpret_cast<uint32_t *>(sm + lay.off_misc);  // tmem base, ncls, abort
+    int2 *coff = reinterpret_cast<int2 *>(sm + lay.off_coff);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tb0 = a.b0 + blockIdx.x * TPB;
-    const int nt = min(TPB, a.nbox - tb0);
+    const int tb0 = blockIdx.x * TPB;  // first list position of the tile
+    const int nt = min(TPB, a.ntgt - tb0);
 
     // ---- prologue: interaction lists of the tile, exponents, zeroed operand buffers
     for (int i = tid; i < TPB * TC_NCLS; i += TC_T) vsrc[i] = -1;
-    for (int i = tid; i < TC_NCLS; i += TC_T) cflag[i] = 0;
+    for (int i = tid; i < TC_NCLS; i += TC_T) {
+        cflag[i] = 0;
+        coff[i] = ND == 4 ? a.off[i] : make_int2(0, 0);
+    }
     for (int i = tid; i < TPB * ND; i += TC_T) lsum[i] = 0;
     {
         uint4 *z = reinterpret_cast<uint4 *>(Abuf);
@@ -176,13 +182,15 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
         tc::tmem_relinquish();
     }
     __syncthreads();
-    // row exponents: |(S_c a)_d[k] 2^floor(k/2)| < 2^(E[t][d] - 1) over the interaction list
-    for (int ti = tid; ti < nt; ti += TC_T) {
-        const int b = tb0 + ti;
+    // row exponents: |(S_c a)_d[k] 2^floor(k/2)| < 2^(E[t][d] - 1) over the interaction
+    // list; one warp per target, lanes over its list
+    for (int ti = warp; ti < nt; ti += TC_T / 32) {
+        const int b = a.tgt[tb0 + ti];
+        const int v0 = a.v_off[b], v1 = a.v_off[b + 1];
         int e[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) e[d] = -100000;
-        for (int v = a.v_off[b]; v < a.v_off[b + 1]; ++v) {
+        for (int v = v0 + lane; v < v1; v += 32) {
             const int c = a.v_cls[v], src = a.v_src[v];
             vsrc[ti * TC_NCLS + c] = src;
             const int me = a.mexp[src];
@@ -193,12 +201,13 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
         int emin = 1 << 30;
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-            Et[ti * ND + d] = e[d] + 1;
+            for (int o = 16; o; o >>= 1) e[d] = max(e[d], __shfl_xor_sync(0xffffffffu, e[d], o));
+            if (lane == 0) Et[ti * ND + d] = e[d] + 1;
             emin = min(emin, e[d] + 1);
         }
-        Et[TPB * ND + ti] = emin;
+        if (lane == 0) Et[TPB * ND + ti] = emin;
         // emin >= mexp[src] + 1 for every source of the list, so the shift is >= 1
-        for (int v = a.v_off[b]; v < a.v_off[b + 1]; ++v)
+        for (int v = v0 + lane; v < v1; v += 32)
             vsh[ti * TC_NCLS + a.v_cls[v]] = (unsigned char)min(emin - a.mexp[a.v_src[v]], 63);
     }
     tc::fence_proxy_async_smem();
@@ -214,16 +223,22 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
     __syncthreads();
     const uint32_t tmem = misc[0];
     const int nsteps = (int)misc[1] * a.nch;
-    const uint32_t idesc = tc::idesc_bf16_f32(TC_M, a.npad);
+    const int pl_per_mma = 256 / a.npad;  // B planes per MMA: N = planes x npad <= 256
     const uint64_t adesc0 = tc::make_desc_kmajor(tc::smem_u32(Abuf), 128, (TC_KC / 8) * 128);
     const uint64_t bdesc0 = tc::make_desc_kmajor(tc::smem_u32(Bbuf), 128, (TC_KC / 8) * 128);
     // one staging item per staging thread and step when TPB x 24 == NST: its sources for
     // the next step are prefetched into registers
     constexpr bool kPrefetch = TPB * TC_KCC == NST;
     longlong2 mpre[ND];
+    int emin_r = 0, dsh_r[ND];  // the item's exponents (fixed target), kept in registers
     if constexpr (kPrefetch) {
         int ti, kk;
         item_of<TPB>(tid, ti, kk);
+        if (tid < NST && ti < nt) {
+            emin_r = Et[TPB * ND + ti];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) dsh_r[d] = Et[ti * ND + d] - emin_r;
+        }
         if (nsteps > 0 && tid < NST) {
             const int k0 = kk;  // step 0: first K chunk of the first class
             const int src0 = (ti < nt && k0 < a.P) ? vsrc[ti * TC_NCLS + clist[0]] : -1;
@@ -261,7 +276,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             // hit 32 different banks.
             unsigned char *Au = Abuf + (size_t)u * TC_NPL * TC_A_PLANE;
             const int *Sc = a.S + c * ND * ND;
-            const int2 cls_off = ND == 4 ? a.off[c] : make_int2(0, 0);
+            const int2 cls_off = coff[c];
             for (int it = tid; it < TPB * TC_KCC; it += NST) {
                 int ti, kk;
                 item_of<TPB>(it, ti, kk);
@@ -296,7 +311,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
                 }
                 // sources come to the finest row scale of the target (one rounding shift), mix
                 // exactly in integers, and each row rounds once to its own exponent
-                const int emin = Et[TPB * ND + ti];
+                const int emin = kPrefetch ? emin_r : Et[TPB * ND + ti];
                 const int sh2 = vsh[ti * TC_NCLS + c];
                 long long xr[ND], xi[ND];
 #pragma unroll
@@ -336,7 +351,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
                 }
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
-                    const int dsh = Et[ti * ND + d] - emin;
+                    const int dsh = kPrefetch ? dsh_r[d] : Et[ti * ND + d] - emin;
                     if (k == 0) lsum[ti * ND + d] += dsh > 0 ? rshift_round(yrs[d], dsh) : yrs[d];
                     const long long yr = rshift_round(yrs[d], TC_GB + dsh);
                     const long long yi = rshift_round(yis[d], TC_GB + dsh);
@@ -378,17 +393,23 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
             // descriptor start addresses advance by (byte offset >> 4) in the low field
             const uint64_t au = adesc0 + (uint64_t)((u * TC_NPL * TC_A_PLANE) >> 4);
             const uint64_t bu = bdesc0 + (uint64_t)((u * lay.bstep) >> 4);
+            // The B digit planes lie one after another along N and the accumulators of the
+            // diagonals one after another along the TMEM columns, so a single MMA of A plane
+            // i against B planes j0 .. j0 + nj - 1 (N = nj x npad <= 256) adds each product
+            // A_i B_j to its own diagonal i + j.  Plane i = 0 comes first, and its MMAs cover
+            // every diagonal once, so an MMA's diagonals are all fresh or all accumulated.
 #pragma unroll 1
             for (int ks = 0; ks < TC_KC / 16; ++ks) {
 #pragma unroll
                 for (int i = 0; i < TC_NPL; ++i) {
                     const uint64_t ad = au + (uint64_t)((i * TC_A_PLANE + ks * 256) >> 4);
-#pragma unroll
-                    for (int j = 0; j < TC_NPL - i; ++j) {
-                        const int g = i + j;
-                        const uint64_t bd = bu + (uint64_t)((j * lay.bplane + ks * 256) >> 4);
-                        tc::mma_bf16(tmem + (uint32_t)(g * a.npad), ad, bd, idesc, (inited >> g) & 1);
-                        inited |= 1u << g;
+                    for (int j0 = 0; j0 < TC_NPL - i; j0 += pl_per_mma) {
+                        const int nj = min(pl_per_mma, TC_NPL - i - j0);
+                        const int g = i + j0;
+                        const uint64_t bd = bu + (uint64_t)((j0 * lay.bplane + ks * 256) >> 4);
+                        tc::mma_bf16(tmem + (uint32_t)(g * a.npad), ad, bd, tc::idesc_bf16_f32(TC_M, nj * a.npad),
+                                     (inited >> g) & 1);
+                        inited |= ((1u << nj) - 1) << g;
                     }
                 }
             }
@@ -435,7 +456,7 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
         double logw = 0, wpow = 1, l0 = 0;
         double2 *dst = nullptr;
         if (valid) {
-            const int b = tb0 + ti;
+            const int b = a.tgt[tb0 + ti];
             const double w = box_width(a.tv.R, a.tv.level[b]);
             logw = log(w);
             for (int i = 0; i < a.power; ++i) wpow *= w;
@@ -639,8 +660,8 @@ static void launch_tc(Fmm &f, const Tree &t, double2 *mp, double2 *lc, int b0, c
     PHS_REQUIRE(lay.total <= 232448, PHS_ERR_INVALID_ARG, "tensor-core M2L: shared memory layout too large");
     TcArgs a;
     a.tv = tree_view(t);
-    a.b0 = b0;
-    a.nbox = t.nbox;
+    a.tgt = f.tc_tgt.get();
+    a.ntgt = t.nbox - b0;
     a.v_off = t.v_off.get();
     a.v_src = t.v_src.get();
     a.v_cls = t.v_cls.get();
@@ -659,10 +680,35 @@ static void launch_tc(Fmm &f, const Tree &t, double2 *mp, double2 *lc, int b0, c
     a.err = f.tc_err.get();
     a.wait_ns = f.tc_wait_ns > 0 ? f.tc_wait_ns : TC_TIMEOUT_NS;
     a.probe = f.tc_probe;
-    const int nb = t.nbox - b0;
-    const unsigned grid = (unsigned)((nb + TcLayout<ND>::TPB - 1) / TcLayout<ND>::TPB);
+    const unsigned grid = (unsigned)((a.ntgt + TcLayout<ND>::TPB - 1) / TcLayout<ND>::TPB);
     m2l_tc_kernel<ND><<<grid, tc_threads<ND>(), lay.total, s>>>(a);
     PHS_LAUNCH_CHECK();
+}
+
+// Tile order of the M2L targets (the boxes of levels >= 2): by level, then by the box's
+// position within its parent (the low two bits of its Morton key), then by box index.
+// The V list of a box is the children of its parent's neighbours that are not its own
+// neighbours, so in a refined neighbourhood its offset classes depend only on that
+// position: 16 targets of one position share one class set (27 classes) where 16
+// consecutive boxes (all four positions) span the union of 40, and each tile step
+// stages and multiplies rows of every target in the tile.
+__global__ void tc_tgt_keys(const int *level, const uint64_t *key, int b0, int nbox, uint64_t *k, int *v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbox - b0) return;
+    const int b = b0 + i;
+    k[i] = ((uint64_t)level[b] << 33) | ((key[b] & 3ull) << 31) | (uint64_t)b;
+    v[i] = b;
+}
+static void tc_build_targets(Fmm &f, const Tree &t, int b0, bool force, cudaStream_t s) {
+    if (!force && f.tc_tgt_nbox == t.nbox) return;
+    const int n = t.nbox - b0;
+    f.tc_tgt.alloc(std::max(n, 1));
+    DBuf<uint64_t> k(std::max(n, 1));
+    tc_tgt_keys<<<blocks_for(n, 256), 256, 0, s>>>(t.level.get(), t.key.get(), b0, t.nbox, k.get(), f.tc_tgt.get());
+    PHS_LAUNCH_CHECK();
+    radix_sort_pairs(k.get(), f.tc_tgt.get(), n, 38, s);
+    PHS_CUDA(cudaStreamSynchronize(s));
+    f.tc_tgt_nbox = t.nbox;
 }
 
 void m2l_tc_pass(Fmm &f, const Tree &t, double2 *mp, double2 *lc, cudaStream_t s) {
@@ -670,6 +716,7 @@ void m2l_tc_pass(Fmm &f, const Tree &t, double2 *mp, double2 *lc, cudaStream_t s
     const size_t esz = (size_t)f.nd * f.P * sizeof(double2);
     if (b0 > 0) PHS_CUDA(cudaMemsetAsync(lc, 0, (size_t)b0 * esz, s));
     if (b0 >= t.nbox) return;
+    tc_build_targets(f, t, b0, false, s);  // built by m2l_tc_count for each new tree
     if (f.tc_mexp.n < (size_t)t.nbox) f.tc_mexp.alloc(t.nbox);
     tc_fixed_kernel<<<blocks_for(t.nbox, 8), 256, 0, s>>>(mp, t.nbox, f.nd, f.P, f.tc_mexp.get());
     PHS_LAUNCH_CHECK();
@@ -677,18 +724,21 @@ void m2l_tc_pass(Fmm &f, const Tree &t, double2 *mp, double2 *lc, cudaStream_t s
     else launch_tc<9>(f, t, mp, lc, b0, s);
 }
 
-// classes present per tile of TPB consecutive boxes (the steps the pass will take)
-__global__ void tc_count_kernel(const int *v_off, const unsigned char *v_cls, int b0, int nbox, int tpb,
+// classes present per tile (the steps the pass will take)
+__global__ void tc_count_kernel(const int *v_off, const unsigned char *v_cls, const int *tgt, int ntgt, int tpb,
                                 unsigned long long *steps) {
     const int tile = blockIdx.x * blockDim.x + threadIdx.x;
-    const int tb0 = b0 + tile * tpb;
-    if (tb0 >= nbox) return;
+    const int tb0 = tile * tpb;
+    if (tb0 >= ntgt) return;
     unsigned long long m = 0;
-    for (int b = tb0; b < min(tb0 + tpb, nbox); ++b)
+    for (int i = tb0; i < min(tb0 + tpb, ntgt); ++i) {
+        const int b = tgt[i];
         for (int v = v_off[b]; v < v_off[b + 1]; ++v) m |= 1ull << v_cls[v];
+    }
     atomicAdd(steps, (unsigned long long)__popcll(m));
 }
 
+// digit-plane products of 128 x npad x 16 per step (plane pairs i + j <= 5, three K slices)
 int m2l_tc_mmas_per_step() { return (TC_KC / 16) * TC_NPL * (TC_NPL + 1) / 2; }
 
 void m2l_tc_count(Fmm &f, const Tree &t, cudaStream_t s) {
@@ -698,9 +748,11 @@ void m2l_tc_count(Fmm &f, const Tree &t, cudaStream_t s) {
     const int tpb = f.nd == 4 ? TcLayout<4>::TPB : TcLayout<9>::TPB;
     const int ntile = (t.nbox - b0 + tpb - 1) / tpb;
     if (ntile <= 0) return;
+    tc_build_targets(f, t, b0, true, s);
     DBuf<unsigned long long> cnt(1);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(unsigned long long), s));
-    tc_count_kernel<<<blocks_for(ntile, 128), 128, 0, s>>>(t.v_off.get(), t.v_cls.get(), b0, t.nbox, tpb, cnt.get());
+    tc_count_kernel<<<blocks_for(ntile, 128), 128, 0, s>>>(t.v_off.get(), t.v_cls.get(), f.tc_tgt.get(), t.nbox - b0,
+                                                           tpb, cnt.get());
     PHS_LAUNCH_CHECK();
     unsigned long long h = 0;
     PHS_CUDA(cudaMemcpyAsync(&h, cnt.get(), sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -265,6 +265,8 @@ struct Fmm {
     DBuf<int> tc_gexp;                   // log2 bound of the frame-change row growth [49][nd]
     DBuf<int2> tc_off;                   // nd = 4: class offsets (ox, oy)
     DBuf<int> tc_mexp;                   // per-box exponent bound of the multipoles
+    DBuf<int> tc_tgt;                    // M2L targets (levels >= 2) by (level, child position, box)
+    int tc_tgt_nbox = -1;                // box count of the tree tc_tgt was built for
     DBuf<int> tc_err;                    // device status (nonzero: a bounded wait expired)
     uint64_t tc_wait_ns = 0;             // main-loop wait limit of the pass (0: the 2 s default)
     int tc_probe = 0;                    // test hook: make the pass's first wait expire
