@@ -275,7 +275,18 @@ __global__ void a_centre_d2(const double2 *xs, int64_t n, const HParams *prm, do
     const double2 c = make_double2(__dadd_rn(h.xmin, 0.5 * h.E), __dadd_rn(h.ymin, 0.5 * h.E));
     const double d = a_d2(xs[p], c);
     d2[p] = d;
-    atomicMin(&st->root_d2, a_bits(d));
+    // one atomic per full warp: the warp's smallest distance (bits of a non-negative
+    // double order like the values)
+    unsigned long long m = a_bits(d);
+    if (__activemask() == 0xffffffffu) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long q = __shfl_xor_sync(0xffffffffu, m, o);
+            m = q < m ? q : m;
+        }
+        if ((threadIdx.x & 31) == 0) atomicMin(&st->root_d2, m);
+    } else {
+        atomicMin(&st->root_d2, m);
+    }
 }
 __global__ void a_centre_arg(const int *idx, const double *d2, int64_t n, AStat *st) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,7 +324,17 @@ __global__ void a_seg_keys(const uint64_t *key, const int *flag, const int *segx
     if (p < n && flag[p]) segkey[segx[p]] = key[p] >> shift;
 }
 // segment ids of the 5 x 5 block of level-L cells around each segment (-1: empty/outside)
-__global__ void a_seg_nbrs(const uint64_t *segkey, int nseg, int L, int *nb) {
+// Finer levels: the cells of one coarse cell (level Lc, key >> cs) are a contiguous run of
+// the sorted cell keys, which dir[coarse] = (first, end) delimits; each lookup searches
+// that run only.
+__global__ void a_seg_dir(const uint64_t *segkey, int nseg, int cs, int2 *dir) {
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg >= nseg) return;
+    const uint64_t c = segkey[sg] >> cs;
+    if (sg == 0 || (segkey[sg - 1] >> cs) != c) dir[c].x = sg;
+    if (sg == nseg - 1 || (segkey[sg + 1] >> cs) != c) dir[c].y = sg + 1;
+}
+__global__ void a_seg_nbrs(const uint64_t *segkey, int nseg, int L, const int2 *dir, int cs, int *nb) {
     const int sg = blockIdx.x * blockDim.x + threadIdx.x;
     if (sg >= nseg) return;
     const uint64_t pre = segkey[sg];
@@ -325,7 +346,8 @@ __global__ void a_seg_nbrs(const uint64_t *segkey, int nseg, int L, int *nb) {
             int found = -1;
             if (qx >= 0 && qy >= 0 && qx < side && qy < side) {
                 const uint64_t q = morton((uint32_t)qx, (uint32_t)qy);
-                int lo = 0, hi = nseg;  // first segkey >= q
+                const int2 r = dir[q >> cs];
+                int lo = r.x, hi = r.y;  // first segkey >= q within the coarse cell's run
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if (segkey[mid] < q) lo = mid + 1;
@@ -335,6 +357,36 @@ __global__ void a_seg_nbrs(const uint64_t *segkey, int nseg, int L, int *nb) {
             }
             nb[(int64_t)sg * 25 + (dy + 2) * 5 + (dx + 2)] = found;
         }
+}
+// the same 5 x 5 block through a dense table of the level's cells (tab[cell] = segment
+// or -1), for levels whose grid is small enough to tabulate
+__global__ void a_seg_table(const uint64_t *segkey, int nseg, int *tab) {
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg < nseg) tab[segkey[sg]] = sg;
+}
+__global__ void a_seg_nbrs_tab(const uint64_t *segkey, int nseg, int L, const int *tab, int *nb) {
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg >= nseg) return;
+    const uint64_t pre = segkey[sg];
+    const int cx = (int)compact_bits(pre), cy = (int)compact_bits(pre >> 1);
+    const int side = 1 << L;
+    for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+            const int qx = cx + dx, qy = cy + dy;
+            const bool in = qx >= 0 && qy >= 0 && qx < side && qy < side;
+            nb[(int64_t)sg * 25 + (dy + 2) * 5 + (dx + 2)] = in ? tab[morton((uint32_t)qx, (uint32_t)qy)] : -1;
+        }
+}
+// cells with a point accepted in the pass within their 5 x 5 block
+__global__ void a_near_acc(int nseg, const int *nb, const signed char *status, unsigned char *nacc) {
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg >= nseg) return;
+    unsigned char any = 0;
+    for (int k = 0; k < 25; ++k) {
+        const int t = nb[(int64_t)sg * 25 + k];
+        if (t >= 0 && status[t] == 2) any = 1;
+    }
+    nacc[sg] = any;
 }
 __global__ void a_pass_reset(int nseg, unsigned long long *segbest, int *segarg) {
     const int sg = blockIdx.x * blockDim.x + threadIdx.x;
@@ -347,11 +399,29 @@ __device__ __forceinline__ int a_seg(const int *segx, const int *flag, int64_t p
 __global__ void a_cand(const double *l2, const unsigned char *taken, const int *segx, const int *flag, int64_t n,
                        double c2, unsigned long long *segbest, AStat *st) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     bool c = false;
-    if (p < n && !taken[p] && l2[p] >= c2) {
-        c = true;
-        atomicMax(&segbest[a_seg(segx, flag, p)], a_bits(l2[p]));
+    int sg = -1;
+    unsigned long long v = 0;  // l2 bits of a candidate (positive), 0 otherwise
+    if (p < n) {
+        sg = a_seg(segx, flag, p);
+        if (!taken[p] && l2[p] >= c2) {
+            c = true;
+            v = a_bits(l2[p]);
+        }
     }
+    // A cell's points are consecutive positions, so the lanes of one cell form a run of
+    // the warp: a segmented max over each run, then one atomic per cell and warp from the
+    // run's first lane.  After the step with offset o a lane holds the maximum over the
+    // next 2o lanes of its run.
+    const unsigned grp = __match_any_sync(0xffffffffu, sg);
+    const int last = 31 - __clz(grp);
+    unsigned long long mx = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long q = __shfl_down_sync(0xffffffffu, mx, o);
+        if (lane + o <= last) mx = q > mx ? q : mx;
+    }
+    if (mx != 0 && lane == __ffs(grp) - 1) atomicMax(&segbest[sg], mx);
     a_warp_count(&st->cand, c);
 }
 __global__ void a_cand_arg(const double *l2, const unsigned char *taken, const int *segx, const int *flag,
@@ -416,10 +486,12 @@ __global__ void a_accept(int nseg, const int *elig, const signed char *status, c
 }
 // lower l2 of untaken points by the points accepted in the pass (5 x 5 cells)
 __global__ void a_update(const double2 *xs, const unsigned char *taken, const int *segx, const int *flag, int64_t n,
-                         const int *nb, const int *elig, const signed char *status, double *l2) {
+                         const int *nb, const int *elig, const signed char *status, const unsigned char *nacc,
+                         double *l2) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n || taken[p]) return;
+    if (p >= n) return;
     const int sg = a_seg(segx, flag, p);
+    if (!nacc[sg] || taken[p]) return;
     const double2 xp = xs[p];
     double best = l2[p];
     const int *row = nb + (int64_t)sg * 25;
@@ -485,10 +557,18 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
     PHS_CUDA(cudaMemcpyAsync(&h, prm.get(), sizeof(HParams), cudaMemcpyDeviceToHost, s));
     PHS_CUDA(cudaStreamSynchronize(s));
 
-    DBuf<uint64_t> segkey;
-    DBuf<unsigned long long> segbest;
-    DBuf<int> segarg, elig, nbr;
-    DBuf<signed char> status;
+    // per-cell buffers (a level has at most n cells), stream-ordered scratch sized once
+    SBuf<uint64_t> segkey(n, s);
+    SBuf<unsigned long long> segbest(n, s);
+    SBuf<int> segarg(n, s), elig(n, s), nbr((size_t)n * 25, s);
+    SBuf<signed char> status(n, s);
+    // levels whose 4^L cells number at most max(16 n, 4^8), and at most 4^11, look their
+    // neighbour cells up in a dense table; finer levels search the sorted cell keys within
+    // the run of one coarse cell (stream-ordered scratch, sized once)
+    const int64_t tab_cap = std::min<int64_t>(1ll << 22, std::max<int64_t>(16 * n, 1ll << 16));
+    SBuf<int> celltab(tab_cap, s);
+    SBuf<int2> dirtab(tab_cap, s);
+    SBuf<unsigned char> nacc(n, s);
     uint64_t pass = 0;
     auto read_stat = [&]() {
         PHS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(AStat), cudaMemcpyDeviceToHost, s));
@@ -515,18 +595,26 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
         h_flags<<<nb256, 256, 0, s>>>(key.get(), n, shift, flag.get());
         PHS_LAUNCH_CHECK();
         const int nseg = (int)exclusive_scan_i32(flag.get(), segx.get(), n, s);
-        if (segkey.n < (size_t)nseg) {
-            segkey.alloc(nseg);
-            segbest.alloc(nseg);
-            segarg.alloc(nseg);
-            elig.alloc(nseg);
-            status.alloc(nseg);
-            nbr.alloc((size_t)nseg * 25);
-        }
         const unsigned sb = blocks_for(nseg, 256);
         a_seg_keys<<<nb256, 256, 0, s>>>(key.get(), flag.get(), segx.get(), n, shift, segkey.get());
         PHS_LAUNCH_CHECK();
-        a_seg_nbrs<<<sb, 256, 0, s>>>(segkey.get(), nseg, L, nbr.get());
+        const int64_t ncell = 1ll << (2 * L);
+        if (ncell <= tab_cap) {
+            PHS_CUDA(cudaMemsetAsync(celltab.get(), 0xFF, (size_t)ncell * sizeof(int), s));
+            a_seg_table<<<sb, 256, 0, s>>>(segkey.get(), nseg, celltab.get());
+            PHS_LAUNCH_CHECK();
+            a_seg_nbrs_tab<<<sb, 256, 0, s>>>(segkey.get(), nseg, L, celltab.get(), nbr.get());
+        } else {
+            // coarse directory at the finest tabulated level
+            int Lc = 0;
+            while (Lc < L && (1ll << (2 * (Lc + 1))) <= tab_cap) ++Lc;
+            const int cs = 2 * (L - Lc);
+            const int64_t ncoarse = 1ll << (2 * Lc);
+            PHS_CUDA(cudaMemsetAsync(dirtab.get(), 0, (size_t)ncoarse * sizeof(int2), s));  // empty runs
+            a_seg_dir<<<sb, 256, 0, s>>>(segkey.get(), nseg, cs, dirtab.get());
+            PHS_LAUNCH_CHECK();
+            a_seg_nbrs<<<sb, 256, 0, s>>>(segkey.get(), nseg, L, dirtab.get(), cs, nbr.get());
+        }
         PHS_LAUNCH_CHECK();
         for (;;) {
             // a pass: candidates, one eligible point per cell, then rounds of the parallel
@@ -564,8 +652,10 @@ void amaxmin_order_dev(const double2 *x, int64_t n, int *order_out, cudaStream_t
             a_accept<<<sb, 256, 0, s>>>(nseg, elig.get(), status.get(), l2.get(), c2, pass, taken.get(),
                                         keysel.get());
             PHS_LAUNCH_CHECK();
+            a_near_acc<<<sb, 256, 0, s>>>(nseg, nbr.get(), status.get(), nacc.get());
+            PHS_LAUNCH_CHECK();
             a_update<<<nb256, 256, 0, s>>>(xs.get(), taken.get(), segx.get(), flag.get(), n, nbr.get(), elig.get(),
-                                           status.get(), l2.get());
+                                           status.get(), nacc.get(), l2.get());
             PHS_LAUNCH_CHECK();
         }
     }
