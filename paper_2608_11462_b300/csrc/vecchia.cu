@@ -197,8 +197,9 @@ struct WarpTopM {
 // Warp per rank r: the min(m, r) nearest points of smaller rank, by (d2, rank).  Small
 // ranks scan all previous points; the others walk square rings of grid cells around
 // the query until the held need-th distance is below the distance to the ring's outside.
-// A ring's new cells are at most two ranges per grid row; 32 ranges at a time are
-// concatenated by a warp scan of their lengths so that every distance batch is full.
+// Points sit in cells sorted by rank, so each of a ring's cells contributes the prefix of
+// its range below r (a binary search); 32 such ranges at a time are concatenated by a
+// warp scan of their lengths so that every distance batch is full of admissible points.
 __global__ void knn_kernel(const double2 *x_by_rank, int64_t n, int m, int brute, const Grid *gp, const int *cstart,
                            const double2 *xc, const int *rc, const int *order, int *nbr_ell) {
     const unsigned full = 0xffffffffu;
@@ -221,30 +222,40 @@ __global__ void knn_kernel(const double2 *x_by_rank, int64_t n, int m, int brute
         const int cx0 = grid_coord(p.x, g.x0, g), cy0 = grid_coord(p.y, g.y0, g);
         for (int k = 0;; ++k) {
             const int xa = cx0 - k, xb = cx0 + k, ya = cy0 - k, yb = cy0 + k;
-            const int cxa = max(xa, 0), cxb = min(xb, g.G - 1), rya = max(ya, 0), ryb = min(yb, g.G - 1);
-            // range j: row rya + j / 2; edge rows: part 0 = cells cxa..cxb; other rows:
-            // part 0 = cell xa, part 1 = cell xb (when inside the grid)
-            const int nr = 2 * (ryb - rya + 1);
+            // cell j of ring k (8k cells; 1 for k = 0): the top row, the bottom row, then
+            // the two ends of each row between.  A cell's points are sorted by rank, so
+            // those before r (the only admissible ones) are a prefix of its range.
+            const int nr = k == 0 ? 1 : 8 * k;
             for (int g0 = 0; g0 < nr; g0 += 32) {
                 int st = 0, len = 0;
                 const int j = g0 + lane;
                 if (j < nr) {
-                    const int cy = rya + (j >> 1), part = j & 1;
-                    const bool edge = cy == ya || cy == yb;
-                    int c0 = -1, c1 = -1;
-                    if (edge) {
-                        if (part == 0) {
-                            c0 = cxa;
-                            c1 = cxb;
+                    int dx = 0, dy = 0;
+                    if (k > 0) {
+                        if (j < 2 * k + 1) {
+                            dy = -k;
+                            dx = j - k;
+                        } else if (j < 4 * k + 2) {
+                            dy = k;
+                            dx = j - (3 * k + 1);
+                        } else {
+                            const int t2 = j - (4 * k + 2);
+                            dy = 1 - k + (t2 >> 1);
+                            dx = (t2 & 1) ? k : -k;
                         }
-                    } else if (part == 0) {
-                        if (xa >= 0) c0 = c1 = xa;
-                    } else if (xb < g.G) {
-                        c0 = c1 = xb;
                     }
-                    if (c0 >= 0) {
-                        st = cstart[cy * g.G + c0];
-                        len = cstart[cy * g.G + c1 + 1] - st;
+                    const int cx = cx0 + dx, cy = cy0 + dy;
+                    if (cx >= 0 && cx < g.G && cy >= 0 && cy < g.G) {
+                        const int c = cy * g.G + cx;
+                        const int a0 = cstart[c];
+                        int lo = a0, hi = cstart[c + 1];
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (rc[mid] < r) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        st = a0;
+                        len = lo - a0;
                     }
                 }
                 int off = len;  // inclusive scan of the range lengths
