@@ -493,6 +493,23 @@ __device__ __forceinline__ double recip_nr(double d) {
     return fma(r, fma(-d, r, 1.0), r);
 }
 
+// Triangular numbering e = a (a + 1) / 2 + c (c <= a) of the lower triangle, tabulated per
+// block in shared memory after the warps' regions: the same table serves the entry loop
+// (all pairs b <= a) and every trailing update (the triangle of rows and columns j+1..s
+// numbered from j + 1), so no lane derives its (row, column) by search.
+__device__ __forceinline__ const uchar2 *tri_table(double *fsm, int per, int m) {
+    uchar2 *tri = reinterpret_cast<uchar2 *>(fsm + (size_t)(blockDim.x >> 5) * per);
+    const int T = (m + 1) * (m + 2) / 2;
+    for (int e = threadIdx.x; e < T; e += blockDim.x) {
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 > e) --a;
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        tri[e] = make_uchar2((unsigned char)a, (unsigned char)(e - a * (a + 1) / 2));
+    }
+    __syncthreads();
+    return tri;
+}
+
 // Warp per point i with conditioning set sigma (s = |sigma| points): LDL' of the
 // (s+1) x (s+1) covariance of (X_sigma, x_i), the point itself last (Eq. 2.19).  With
 // K = [K_ss k; k' 1] = L D L' (L unit lower), row s of L is (D^-1 L_ss^-1 k)' and its
@@ -512,6 +529,7 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
     double *W = A + (m + 1) * ld;  // column j before scaling by 1/d_j
     double *X = W + (m + 1);
     double *Y = X + (m + 1);
+    const uchar2 *tri = tri_table(fsm, per, m);
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (i >= n) return;
     const unsigned full = 0xffffffffu;
@@ -528,10 +546,8 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
     for (int t = 0; t <= 7 && !ok; ++t) {
         const double jit = t == 0 ? 0.0 : 1e-12 * pow(10.0, (double)(t - 1));
         for (int idx = lane; idx < ntri; idx += 32) {
-            int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-            while (a * (a + 1) / 2 > idx) --a;
-            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-            const int b = idx - a * (a + 1) / 2;
+            const uchar2 tb = tri[idx];
+            const int a = tb.x, b = tb.y;
             double v;
             if (b == a) {
                 v = a < s ? 1.0 + jit : 1.0;  // jitter on K_ss only
@@ -554,21 +570,12 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
                 A[a * ld + j] = w * r;
             }
             __syncwarp();
-            // entry t = a'(a'+1)/2 + c', c' <= a', of the trailing block (rows and columns j+1..s)
+            // entry e = a'(a'+1)/2 + c', c' <= a', of the trailing block (rows and columns j+1..s)
             const int mm = s - j, ntr = mm * (mm + 1) / 2;
-            int ap = 0, cp = lane;
-            while (cp > ap) {
-                cp -= ap + 1;
-                ++ap;
-            }
             for (int e = lane; e < ntr; e += 32) {
-                const int a = j + 1 + ap, c = j + 1 + cp;
+                const uchar2 tb = tri[e];
+                const int a = j + 1 + tb.x, c = j + 1 + tb.y;
                 A[a * ld + c] = fma(-A[a * ld + j], W[c], A[a * ld + c]);
-                cp += 32;
-                while (cp > ap) {
-                    cp -= ap + 1;
-                    ++ap;
-                }
             }
             __syncwarp();
         }
@@ -616,6 +623,7 @@ __global__ void factor_kernel_ff(const double2 *x, int64_t n, const int *rank, c
     float2 *W = A + (m + 1) * ld;
     float2 *X = W + (m + 1);  // scaled coordinates, hi + lo
     float2 *Y = X + (m + 1);
+    const uchar2 *tri = tri_table(fsm, per, m);
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (i >= n) return;
     const unsigned full = 0xffffffffu;
@@ -633,10 +641,8 @@ __global__ void factor_kernel_ff(const double2 *x, int64_t n, const int *rank, c
     for (int t = 0; t <= 7 && !ok; ++t) {
         const double jit = t == 0 ? 0.0 : 1e-12 * pow(10.0, (double)(t - 1));
         for (int idx = lane; idx < ntri; idx += 32) {
-            int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-            while (a * (a + 1) / 2 > idx) --a;
-            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-            const int b = idx - a * (a + 1) / 2;
+            const uchar2 tb = tri[idx];
+            const int a = tb.x, b = tb.y;
             F2 vf;
             if (b == a) {
                 vf = ffa::split_d(a < s ? 1.0 + jit : 1.0);  // jitter on K_ss only
@@ -666,21 +672,12 @@ __global__ void factor_kernel_ff(const double2 *x, int64_t n, const int *rank, c
             }
             __syncwarp();
             const int mm = s - j, ntr = mm * (mm + 1) / 2;
-            int ap = 0, cp = lane;
-            while (cp > ap) {
-                cp -= ap + 1;
-                ++ap;
-            }
             for (int e2 = lane; e2 < ntr; e2 += 32) {
-                const int a = j + 1 + ap, c = j + 1 + cp;
+                const uchar2 tb = tri[e2];
+                const int a = j + 1 + tb.x, c = j + 1 + tb.y;
                 const float2 la = A[a * ld + j], wc = W[c], ac = A[a * ld + c];
                 const F2 u = ffa::ff_add(F2{ac.x, ac.y}, ffa::ff_neg(ffa::ff_mul(F2{la.x, la.y}, F2{wc.x, wc.y})));
                 A[a * ld + c] = make_float2(u.h, u.l);
-                cp += 32;
-                while (cp > ap) {
-                    cp -= ap + 1;
-                    ++ap;
-                }
             }
             __syncwarp();
         }
@@ -1020,7 +1017,8 @@ int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const i
     const int ld = (m + 1) | 1;  // odd row stride: rows of consecutive lanes fall in different banks
     const size_t per = (size_t)((m + 1) * ld + 3 * (m + 1)) * sizeof(double);
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
-    const size_t smem = per * wpb;
+    const size_t tri_bytes = ((size_t)(m + 1) * (m + 2) / 2 * sizeof(uchar2) + 7) & ~(size_t)7;
+    const size_t smem = per * wpb + tri_bytes;
     SBuf<unsigned long long> cnt(2, s);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, 2 * sizeof(unsigned long long), s));
     const int nuc = nu == 0.5 ? 0 : (nu == 1.0 ? 1 : (nu == 1.5 ? 2 : (nu == 2.0 ? 3 : 4)));
