@@ -40,11 +40,8 @@ constexpr int CHEB_T = 256;
 namespace {
 
 __device__ __forceinline__ void box_center_h(const TreeView &tv, int b, double &cx, double &cy, double &h) {
-    int ix, iy;
-    demorton(tv.key[b], ix, iy);
-    const double w = box_width(tv.R, tv.level[b]);
-    cx = -tv.R + (ix + 0.5) * w;
-    cy = -tv.R + (iy + 0.5) * w;
+    double w;
+    box_geom(tv, b, cx, cy, w);
     h = 0.5 * w;
 }
 

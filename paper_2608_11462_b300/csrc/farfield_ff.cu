@@ -41,9 +41,8 @@ __global__ void __launch_bounds__(PF_T) p2m_ff_kernel(TreeView tv, const int *le
     float4 *zs = pw + (size_t)64 * P;                                // [64] scaled coordinates
     float2 *qs = reinterpret_cast<float2 *>(zs + 64);                // [64][ND] charges
     const int b = leaf_box[blockIdx.x];
-    double cx, cy, w;
-    box_geom(tv, b, cx, cy, w);
-    const double iw = 1.0 / w;
+    double cx, cy, w, iw;
+    box_geom_iw(tv, b, cx, cy, w, iw);
     const int s = tv.start[b], e = tv.end[b];
     const int nout = ND * P;
     const int Q = (P + 3) / 4;
@@ -127,9 +126,8 @@ __global__ void __launch_bounds__(LF_T) l2p_ff_kernel(TreeView tv, const int *le
     const int nout = ND * P;
     for (int i = threadIdx.x; i < nout; i += LF_T) lf_sm[i] = c4_pack(c4_of(lc[(size_t)b * nout + i]));
     __syncthreads();
-    double cx, cy, w;
-    box_geom(tv, b, cx, cy, w);
-    const double iw = 1.0 / w;
+    double cx, cy, w, iw;
+    box_geom_iw(tv, b, cx, cy, w, iw);
     const int s = tv.start[b], e = tv.end[b];
     for (int j = s + threadIdx.x; j < e; j += LF_T) {
         const double2 xj = xs[j];

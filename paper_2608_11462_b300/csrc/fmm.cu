@@ -110,9 +110,8 @@ __global__ void p2m_kernel(TreeView tv, const int *leaf_box, const double2 *xs, 
     C *pw = reinterpret_cast<C *>(smem_raw);        // [32][P]
     T *qs = reinterpret_cast<T *>(pw + 32 * P);     // [32][nd]
     const int b = leaf_box[blockIdx.x];
-    double cx, cy, w;
-    box_geom(tv, b, cx, cy, w);
-    const double iw = 1.0 / w;
+    double cx, cy, w, iw;
+    box_geom_iw(tv, b, cx, cy, w, iw);
     const int s = tv.start[b], e = tv.end[b];
     C acc[OUT_PER_T];
 #pragma unroll
@@ -353,9 +352,8 @@ __global__ void l2p_kernel(TreeView tv, const int *leaf_box, const double2 *xs, 
     const int nout = nd * P;
     for (int i = threadIdx.x; i < nout; i += blockDim.x) sm[i] = lc[(size_t)b * nout + i];
     __syncthreads();
-    double cx, cy, w;
-    box_geom(tv, b, cx, cy, w);
-    const double iw = 1.0 / w;
+    double cx, cy, w, iw;
+    box_geom_iw(tv, b, cx, cy, w, iw);
     for (int j = tv.start[b] + threadIdx.x; j < tv.end[b]; j += blockDim.x) {
         const double2 xj = xs[j];
         C v;
@@ -383,6 +381,7 @@ __global__ void l2p_kernel(TreeView tv, const int *leaf_box, const double2 *xs, 
 // thread of a block has work, dependent chains are short, and the children of a parent
 // are processed together (two block barriers instead of twelve).
 constexpr int UD_T = 256;
+__device__ double g_neg_inv_k[kMaxP];  // -1/k for 1 <= k < kMaxP (host division, correctly rounded)
 
 // P2M: chunks of 64 points; four threads per point build the powers zeta^k, each a
 // quarter of k from its own starting power; then one thread per output (d, k) sums the
@@ -395,9 +394,8 @@ __global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *lea
     double2 *pw = p2m_sm;                                 // [64][P]
     double *qs = reinterpret_cast<double *>(pw + 64 * P);  // [64][nd]
     const int b = leaf_box[blockIdx.x];
-    double cx, cy, w;
-    box_geom(tv, b, cx, cy, w);
-    const double iw = 1.0 / w;
+    double cx, cy, w, iw;
+    box_geom_iw(tv, b, cx, cy, w, iw);
     const int s = tv.start[b], e = tv.end[b];
     const int nout = nd * P;
     const int Q = (P + 3) / 4;
@@ -454,7 +452,7 @@ __global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *lea
             const int d = o / P, k = o - d * P;
             double2 a = acc[i];
             if (k > 0) {
-                const double sc = -1.0 / k;
+                const double sc = g_neg_inv_k[k];  // -1/k, correctly rounded (no FP64 division)
                 a.x *= sc;
                 a.y *= sc;
             }
@@ -610,9 +608,8 @@ __global__ void __launch_bounds__(L2P_T) l2p64_kernel(TreeView tv, const int *le
     const int nout = ND * P;
     for (int i = threadIdx.x; i < nout; i += L2P_T) l2p_sm[i] = lc[(size_t)b * nout + i];
     __syncthreads();
-    double cx, cy, w;
-    box_geom(tv, b, cx, cy, w);
-    const double iw = 1.0 / w;
+    double cx, cy, w, iw;
+    box_geom_iw(tv, b, cx, cy, w, iw);
     const int s = tv.start[b], e = tv.end[b];
     for (int j = s + threadIdx.x; j < e; j += L2P_T) {
         const double2 xj = xs[j];
@@ -1253,6 +1250,9 @@ static void upload_log_tables() {
     for (int i = 0; i < kExpTab; ++i) el[i] = (double)((long double)(kExpLo + i - 1023) * std::log(2.0L));
     PHS_CUDA(cudaMemcpyToSymbol(g_logtab, tab.data(), kLogTab * sizeof(double2)));
     PHS_CUDA(cudaMemcpyToSymbol(g_eln2, el.data(), kExpTab * sizeof(double)));
+    std::vector<double> ik(kMaxP, 0.0);
+    for (int k = 1; k < (int)ik.size(); ++k) ik[k] = -1.0 / k;
+    PHS_CUDA(cudaMemcpyToSymbol(g_neg_inv_k, ik.data(), ik.size() * sizeof(double)));
 }
 template <int K>
 static void p2p_sym_launch(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_sorted, double *y,

@@ -1,6 +1,7 @@
 // geom.cuh -- quadtree geometry helpers shared by the tree, FMM and evaluation kernels.
 #pragma once
 #include <stdint.h>
+#include <cmath>
 
 #include "phs_internal.cuh"
 
@@ -39,16 +40,40 @@ __host__ __device__ __forceinline__ void demorton(uint64_t key, int &ix, int &iy
     iy = (int)compact_bits(key >> 1);
 }
 
-// box of level l in the root [-R, R]^2: width 2R/2^l, centre -R + (i + 1/2) * width
-__host__ __device__ __forceinline__ double box_width(double R, int l) { return 2.0 * R / (double)(1ll << l); }
+// x 2^e for positive normal x and a normal result: exact, by the exponent field alone
+// (no FP64 arithmetic on the device)
+__host__ __device__ __forceinline__ double pow2_scaled(double x, int e) {
+#ifdef __CUDA_ARCH__
+    return __hiloint2double(__double2hiint(x) + (e << 20), __double2loint(x));
+#else
+    return std::ldexp(x, e);
+#endif
+}
 
-// centre (cx, cy) and width w of box b
+// box of level l in the root [-R, R]^2: width 2R/2^l, centre -R + (i + 1/2) * width.
+// Dividing by a power of two is exact, so the scaled forms equal the quotients.
+__host__ __device__ __forceinline__ double box_width(double R, int l) { return pow2_scaled(2.0 * R, -l); }
+__host__ __device__ __forceinline__ double box_centre(double R, double w, int i) { return -R + (i + 0.5) * w; }
+
+// centre (cx, cy) and width w of box b; centres from the tree's table when it has one
 __device__ __forceinline__ void box_geom(const TreeView &tv, int b, double &cx, double &cy, double &w) {
-    int ix, iy;
-    demorton(tv.key[b], ix, iy);
     w = box_width(tv.R, tv.level[b]);
-    cx = -tv.R + (ix + 0.5) * w;
-    cy = -tv.R + (iy + 0.5) * w;
+    if (tv.ctr) {
+        const double2 c = tv.ctr[b];
+        cx = c.x;
+        cy = c.y;
+    } else {
+        int ix, iy;
+        demorton(tv.key[b], ix, iy);
+        cx = box_centre(tv.R, w, ix);
+        cy = box_centre(tv.R, w, iy);
+    }
+}
+// the same and 1 / w = (1 / 2R) 2^l, the correctly rounded quotient 1.0 / w
+__device__ __forceinline__ void box_geom_iw(const TreeView &tv, int b, double &cx, double &cy, double &w,
+                                            double &iw) {
+    box_geom(tv, b, cx, cy, w);
+    iw = pow2_scaled(tv.rinv2, tv.level[b]);
 }
 
 // index of the box at (l, ix, iy), or -1 if it does not exist

@@ -309,15 +309,20 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
                     }
                     continue;
                 }
-                // sources come to the finest row scale of the target (one rounding shift), mix
-                // exactly in integers, and each row rounds once to its own exponent
+                // nd = 4: the sources (|X| <= 2^53) mix exactly at their own scale (row sums
+                // of |S| are at most 1 + 6 + 6 + 18 = 31, so |y| < 2^58) and each row rounds
+                // once, by the shift to the target's finest scale plus its own.  nd = 9 (row
+                // sums up to 2^10): the sources first come to the finest row scale (one
+                // rounding shift), then mix, then each row rounds to its own exponent.
+                constexpr bool kOneShift = ND == 4;
                 const int emin = kPrefetch ? emin_r : Et[TPB * ND + ti];
                 const int sh2 = vsh[ti * TC_NCLS + c];
+                const int s0 = kOneShift ? sh2 : 0;  // shift still owed to the finest row scale
                 long long xr[ND], xi[ND];
 #pragma unroll
                 for (int b = 0; b < ND; ++b) {
-                    xr[b] = rshift_round(m[b].x, sh2);
-                    xi[b] = rshift_round(m[b].y, sh2);
+                    xr[b] = kOneShift ? m[b].x : rshift_round(m[b].x, sh2);
+                    xi[b] = kOneShift ? m[b].y : rshift_round(m[b].y, sh2);
                 }
                 long long yrs[ND], yis[ND];
                 if constexpr (ND == 4) {
@@ -352,9 +357,11 @@ __global__ void __launch_bounds__(tc_threads<ND>(), 1) m2l_tc_kernel(TcArgs a) {
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
                     const int dsh = kPrefetch ? dsh_r[d] : Et[ti * ND + d] - emin;
-                    if (k == 0) lsum[ti * ND + d] += dsh > 0 ? rshift_round(yrs[d], dsh) : yrs[d];
-                    const long long yr = rshift_round(yrs[d], TC_GB + dsh);
-                    const long long yi = rshift_round(yis[d], TC_GB + dsh);
+                    // shifts of 63 round |y| < 2^58 to 0, as every larger one would
+                    if (k == 0) lsum[ti * ND + d] += s0 + dsh > 0 ? rshift_round(yrs[d], min(s0 + dsh, 63)) : yrs[d];
+                    const int s1 = min(s0 + TC_GB + dsh, 63);
+                    const long long yr = rshift_round(yrs[d], s1);
+                    const long long yi = rshift_round(yis[d], s1);
                     float dr[TC_NPL], di[TC_NPL];
                     digits_f(yr, dr);
                     digits_f(yi, di);

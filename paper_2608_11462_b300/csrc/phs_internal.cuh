@@ -178,6 +178,7 @@ struct Tree {
     DBuf<int> lvl_dev;               // device copy of lvl_off
     DBuf<int> start, end, parent, child, nchild, level;
     DBuf<uint64_t> key;              // Morton key of the box at its own level
+    DBuf<double2> ctr;               // box centres
     DBuf<int> leaf_box;              // leaf list
     DBuf<int> point_leaf;            // leaf index of each (sorted) point
     DBuf<int> v_off, v_src;          // V (M2L) lists per box (CSR)
@@ -214,8 +215,10 @@ struct TreeView {
     const int *start, *end, *parent, *child, *nchild, *level;
     const uint64_t *key;
     const int *lvl_off;  // device copy
+    const double2 *ctr;  // box centres (null while the tree is being built)
     int depth;
     double R;
+    double rinv2;        // 1 / (2R), correctly rounded
 };
 TreeView tree_view(const Tree &t);
 

@@ -287,8 +287,19 @@ TreeView tree_view(const Tree &t) {
     TreeView v;
     v.start = t.start.get(); v.end = t.end.get(); v.parent = t.parent.get(); v.child = t.child.get();
     v.nchild = t.nchild.get(); v.level = t.level.get(); v.key = t.key.get(); v.lvl_off = t.lvl_dev.get();
+    v.ctr = t.ctr.get();
     v.depth = t.depth; v.R = t.R;
+    v.rinv2 = 1.0 / (2.0 * t.R);
     return v;
+}
+
+__global__ void box_centres_kernel(TreeView tv, int nbox, double2 *ctr) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int ix, iy;
+    demorton(tv.key[b], ix, iy);
+    const double w = box_width(tv.R, tv.level[b]);
+    ctr[b] = make_double2(box_centre(tv.R, w, ix), box_centre(tv.R, w, iy));
 }
 
 void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, int leaf_cap, PointSet &ps,
@@ -407,6 +418,9 @@ void build_points_and_tree(const double *pts_dev, int64_t n, double halfwidth, i
     tree.lvl_dev.alloc(tree.lvl_off.size());
     PHS_CUDA(cudaMemcpyAsync(tree.lvl_dev.get(), tree.lvl_off.data(), tree.lvl_off.size() * sizeof(int),
                              cudaMemcpyHostToDevice, s));
+    tree.ctr.alloc(tree.nbox);
+    box_centres_kernel<<<blocks_for(tree.nbox, 256), 256, 0, s>>>(tree_view(tree), tree.nbox, tree.ctr.get());
+    PHS_LAUNCH_CHECK();
     TreeView tv = tree_view(tree);
     {
         SBuf<int> cnt(tree.nbox, s);
