@@ -40,10 +40,10 @@ TUNE_SEED = 2002
 # profiles/p2p_sym_kernel_tps_262k.md and profiles/m2l_tc_kernel_tps_262k.md, taken on the
 # n = 262144 case of this workload at leaf capacity 96 and scaled to the bench size: the
 # tensor-core M2L by its tile count (408 tiles there), the near field by the point count.
-M2L_DRAM_BYTES_PER_TILE = (21.427712e6 + 21.76e3) / 408
-P2P_DRAM_BYTES_PER_POINT = (6.951936e6 + 512) / 262144
+M2L_DRAM_BYTES_PER_TILE = (21.455872e6 + 7424) / 408
+P2P_DRAM_BYTES_PER_POINT = (6.971136e6 + 768) / 262144
 # the float-float near field (precision 4): profiles/p2p_sym_ff_kernel_tps_262k.md
-P2P_FF_DRAM_BYTES_PER_POINT = (6.909696e6 + 256) / 262144
+P2P_FF_DRAM_BYTES_PER_POINT = (6.929152e6 + 512) / 262144
 
 
 def workload_config(args, n, m_t, fmm_order, world):
