@@ -380,10 +380,22 @@ __global__ void l2p_kernel(TreeView tv, const int *leaf_box, const double2 *xs, 
 // The same arithmetic as the templated kernels above, arranged for the FP64 pipe: every
 // thread of a block has work, dependent chains are short, and the children of a parent
 // are processed together (two block barriers instead of twelve).
-constexpr int UD_T = 256;
+constexpr int UD_T = 256;    // P2M threads at most
+constexpr int UD_MAX = 1024;  // M2M / L2L threads at most
+// Block sizes that leave no lane idle where the work is (a warp instruction on the FP64
+// pipe costs the same with one lane as with 32): the fewest rounds of at most `cap`
+// threads over `items`, each round rounded up to whole warps.
+static int even_threads(int items, int cap) {
+    const int rounds = (items + cap - 1) / cap;
+    return std::max(32, ((items + rounds - 1) / rounds + 31) / 32 * 32);
+}
+// P2M: one thread per output (nd P of them, at most three rounds) and four per point of
+// a chunk of blockDim / 4 points; M2M / L2L: one thread per (child, density, row pair)
+static int p2m_threads(int nd, int P) { return even_threads(nd * P, UD_T); }
+static int shift_threads(int nd, int P) { return even_threads(4 * nd * ((P + 1) / 2), UD_MAX); }
 __device__ double g_neg_inv_k[kMaxP];  // -1/k for 1 <= k < kMaxP (host division, correctly rounded)
 
-// P2M: chunks of 64 points; four threads per point build the powers zeta^k, each a
+// P2M: chunks of blockDim / 4 points (at most 64); four threads per point build the powers zeta^k, each a
 // quarter of k from its own starting power; then one thread per output (d, k) sums the
 // chunk.  a_0 = sum q, a_k = -sum q zeta^k / k (box-width scaled, fmm.cu header).
 template <int ND>  // density count (static, so the Hadamard factors stay in registers)
@@ -402,8 +414,9 @@ __global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *lea
     double2 acc[OUT_PER_T];
 #pragma unroll
     for (int i = 0; i < OUT_PER_T; ++i) acc[i] = make_double2(0.0, 0.0);
-    for (int j0 = s; j0 < e; j0 += 64) {
-        const int jn = min(64, e - j0);
+    const int CH = blockDim.x >> 2;  // points per chunk (at most 64)
+    for (int j0 = s; j0 < e; j0 += CH) {
+        const int jn = min(CH, e - j0);
         {
             const int jp = threadIdx.x >> 2, q = threadIdx.x & 3;
             if (jp < jn) {
@@ -430,7 +443,7 @@ __global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *lea
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < OUT_PER_T; ++i) {
-            const int o = threadIdx.x + i * UD_T;
+            const int o = threadIdx.x + i * (int)blockDim.x;
             if (o < nout) {
                 const int d = o / P, k = o - d * P;
                 double2 a = acc[i];
@@ -447,7 +460,7 @@ __global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *lea
     }
 #pragma unroll
     for (int i = 0; i < OUT_PER_T; ++i) {
-        const int o = threadIdx.x + i * UD_T;
+        const int o = threadIdx.x + i * (int)blockDim.x;
         if (o < nout) {
             const int d = o / P, k = o - d * P;
             double2 a = acc[i];
@@ -466,7 +479,7 @@ __global__ void __launch_bounds__(UD_T) p2m64_kernel(TreeView tv, const int *lea
 // core R common to the four quadrants, so the O(P^2) part is real x complex (2 FMA per
 // entry instead of 4).  Each thread takes row pairs (l, P-1-l) to balance the triangle;
 // then the parent sums the children through the frame changes Rv (mix slots 49 + q).
-__global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd, int P, const double *R,
+__global__ void __launch_bounds__(UD_MAX) m2m64_kernel(TreeView tv, int b0, int nd, int P, const double *R,
                                                     const double2 *ph, const double *mix, double2 *mp) {
     extern __shared__ double2 m2m_sm[];
     const int b = b0 + blockIdx.x;
@@ -474,14 +487,14 @@ __global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd
     if (nc == 0) return;
     const int nout = nd * P, c0 = tv.child[b];
     double2 *ch = m2m_sm, *sh = m2m_sm + 4 * nout;
-    for (int i = threadIdx.x; i < nc * nout; i += UD_T) {
+    for (int i = threadIdx.x; i < nc * nout; i += (int)blockDim.x) {
         const int c = i / nout, k = (i - c * nout) % P;
         const double2 a = mp[(size_t)c0 * nout + i], e = ph[(size_t)(tv.key[c0 + c] & 3) * P + k];
         ch[i] = make_double2(fma(a.x, e.x, a.y * e.y), fma(a.y, e.x, -a.x * e.y));  // a e^{-i th k}
     }
     __syncthreads();
     const int half = (P + 1) / 2;
-    for (int it = threadIdx.x; it < nc * nd * half; it += UD_T) {
+    for (int it = threadIdx.x; it < nc * nd * half; it += (int)blockDim.x) {
         const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
         const double2 *ephq = ph + (size_t)(tv.key[c0 + c] & 3) * P;
         const double2 *src = ch + c * nout + d * P;
@@ -511,7 +524,7 @@ __global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd
         }
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < nout; o += UD_T) {
+    for (int o = threadIdx.x; o < nout; o += (int)blockDim.x) {
         const int d = o / P, l = o - d * P;
         double ax = 0.0, ay = 0.0;
         for (int c = 0; c < nc; ++c) {
@@ -533,7 +546,7 @@ __global__ void __launch_bounds__(UD_T) m2m64_kernel(TreeView tv, int b0, int nd
 // child's phase e^{i th_q l}, shifts through the real upper-triangular core (rows m
 // paired with P-1-m: sum over l >= m), takes e^{-i th_q m}, and mixes through Ru (mix
 // slots 53 + q) into the child's local expansion.
-__global__ void __launch_bounds__(UD_T) l2l64_kernel(TreeView tv, int b0, int nd, int P, const double *R,
+__global__ void __launch_bounds__(UD_MAX) l2l64_kernel(TreeView tv, int b0, int nd, int P, const double *R,
                                                     const double2 *ph, const double *mix, double2 *lc) {
     extern __shared__ double2 l2l_sm[];
     const int b = b0 + blockIdx.x;
@@ -541,14 +554,14 @@ __global__ void __launch_bounds__(UD_T) l2l64_kernel(TreeView tv, int b0, int nd
     if (nc == 0) return;
     const int nout = nd * P, c0 = tv.child[b];
     double2 *y = l2l_sm, *sh = l2l_sm + 4 * nout;
-    for (int i = threadIdx.x; i < nc * nout; i += UD_T) {
+    for (int i = threadIdx.x; i < nc * nout; i += (int)blockDim.x) {
         const int c = i / nout, o = i - c * nout, l = o % P;
         const double2 v = lc[(size_t)b * nout + o], e = ph[(size_t)(tv.key[c0 + c] & 3) * P + l];
         y[i] = make_double2(fma(v.x, e.x, -v.y * e.y), fma(v.x, e.y, v.y * e.x));  // b e^{i th l}
     }
     __syncthreads();
     const int half = (P + 1) / 2;
-    for (int it = threadIdx.x; it < nc * nd * half; it += UD_T) {
+    for (int it = threadIdx.x; it < nc * nd * half; it += (int)blockDim.x) {
         const int c = it / (nd * half), r = it - c * nd * half, d = r / half, p = r - d * half;
         const double2 *ephq = ph + (size_t)(tv.key[c0 + c] & 3) * P;
         const double2 *src = y + c * nout + d * P;
@@ -578,7 +591,7 @@ __global__ void __launch_bounds__(UD_T) l2l64_kernel(TreeView tv, int b0, int nd
         }
     }
     __syncthreads();
-    for (int it = threadIdx.x; it < nc * nout; it += UD_T) {
+    for (int it = threadIdx.x; it < nc * nout; it += (int)blockDim.x) {
         const int c = it / nout, o = it - c * nout, a_ = o / P, m = o - a_ * P;
         const double *Ru = mix + (size_t)(53 + (tv.key[c0 + c] & 3)) * nd * nd;
         double2 acc = lc[(size_t)(c0 + c) * nout + o];
@@ -1107,15 +1120,15 @@ static void upward(Fmm &f, const Tree &t, const PointSet &ps, const double *tv_s
         set_pass_smem_limits();
         const size_t sm = (size_t)64 * P * sizeof(double2) + (size_t)64 * nd * sizeof(double);
         if (ff) p2m_ff_launch(f, t, ps, tv_sorted, mp, s);
-        else if (nd == 4) p2m64_kernel<4><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
-        else if (nd == 9) p2m64_kernel<9><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
-        else p2m64_kernel<1><<<t.nleaf, UD_T, sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
+        else if (nd == 4) p2m64_kernel<4><<<t.nleaf, p2m_threads(nd, P), sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
+        else if (nd == 9) p2m64_kernel<9><<<t.nleaf, p2m_threads(nd, P), sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
+        else p2m64_kernel<1><<<t.nleaf, p2m_threads(nd, P), sm, s>>>(tv, t.leaf_box.get(), ps.xs.get(), tv_sorted, f.power, P, mp);
         PHS_LAUNCH_CHECK();
         for (int l = t.depth - 1; l >= 0; --l) {
             const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
             if (nb > 0 && ff) m2m_ff_launch(f, t, b0, nb, mp, s);
             else if (nb > 0)
-                m2m64_kernel<<<nb, UD_T, 8 * esz, s>>>(tv, b0, nd, P, f.shift_r.get(), f.shift_ph.get(), mix_buf<T>(f),
+                m2m64_kernel<<<nb, shift_threads(nd, P), 8 * esz, s>>>(tv, b0, nd, P, f.shift_r.get(), f.shift_ph.get(), mix_buf<T>(f),
                                                        mp);
             PHS_LAUNCH_CHECK();
         }
@@ -1162,7 +1175,7 @@ static void downward(Fmm &f, const Tree &t, typename C2T<T>::type *lc, const typ
             const int b0 = t.lvl_off[l], nb = t.lvl_off[l + 1] - b0;
             if (nb > 0 && ff) l2l_ff_launch(f, t, b0, nb, lc, s);
             else if (nb > 0)
-                l2l64_kernel<<<nb, UD_T, 8 * esz, s>>>(tree_view(t), b0, f.nd, P, f.shift_r.get() + (size_t)P * P,
+                l2l64_kernel<<<nb, shift_threads(f.nd, P), 8 * esz, s>>>(tree_view(t), b0, f.nd, P, f.shift_r.get() + (size_t)P * P,
                                                        f.shift_ph.get(), mix_buf<T>(f), lc);
             PHS_LAUNCH_CHECK();
         }
