@@ -522,87 +522,120 @@ __device__ __forceinline__ const uchar2 *tri_table(double *fsm, int per, int m) 
 template <int NUC>
 __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, const int *nbr_ell, int m, int ld,
                               double halpha, double *val_ell, unsigned long long *njit) {
+    // Two points per warp, sixteen lanes each: the FP64 pipe is charged per warp
+    // instruction, so the steps that every lane of a point repeats (the pivot reciprocal,
+    // the column scaling, the back solve) and the narrow late trailing updates serve two
+    // points at once.  Loops run to the larger size of the pair with per-half predicates,
+    // so every __syncwarp and shuffle is reached by all 32 lanes.
     extern __shared__ double fsm[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, half = lane >> 4, hl = lane & 15;
     const int per = (m + 1) * ld + 3 * (m + 1);
-    double *A = fsm + (size_t)wib * per;
+    const uchar2 *tri = tri_table(fsm, 2 * per, m);
+    double *A = fsm + ((size_t)wib * 2 + half) * per;
     double *W = A + (m + 1) * ld;  // column j before scaling by 1/d_j
     double *X = W + (m + 1);
     double *Y = X + (m + 1);
-    const uchar2 *tri = tri_table(fsm, per, m);
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    if (i >= n) return;
-    const unsigned full = 0xffffffffu;
-    const int s = min(m, rank[i]);
-    for (int a = lane; a <= s; a += 32) {
+    const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * 2 + half;
+    const bool valid = i < n;
+    const int s = valid ? min(m, rank[i]) : -1;
+    const int smax = max(s, __shfl_xor_sync(full, s, 16));
+    if (smax < 0) return;  // no point in either half (warp-uniform)
+    for (int a = hl; a <= s; a += 16) {
         const double2 p = a < s ? x[nbr_ell[(int64_t)a * n + i]] : x[i];
         X[a] = p.x * halpha;
         Y[a] = p.y * halpha;
     }
     __syncwarp();
-    const int nn = s + 1, ntri = nn * (nn + 1) / 2;
-    bool ok = false;
+    const int ntri = (s + 1) * (s + 2) / 2, ntri_max = (smax + 1) * (smax + 2) / 2;
+    bool ok = !valid;  // a half without a point counts as done
     int tries = 0;
-    for (int t = 0; t <= 7 && !ok; ++t) {
+    for (int t = 0; t <= 7; ++t) {
+        if (__all_sync(full, ok)) break;
+        const bool work = !ok;
         const double jit = t == 0 ? 0.0 : 1e-12 * pow(10.0, (double)(t - 1));
-        for (int idx = lane; idx < ntri; idx += 32) {
-            const uchar2 tb = tri[idx];
-            const int a = tb.x, b = tb.y;
-            double v;
-            if (b == a) {
-                v = a < s ? 1.0 + jit : 1.0;  // jitter on K_ss only
-            } else {
-                const double dx = X[a] - X[b], dy = Y[a] - Y[b];
-                const double q = fma(dx, dx, dy * dy);
-                v = __double2hiint(q) > 0 ? matern_q<NUC>(q) : 1.0;
+        for (int idx = hl; idx < ntri_max; idx += 16) {
+            if (work && idx < ntri) {
+                const uchar2 tb = tri[idx];
+                const int a = tb.x, b = tb.y;
+                double v;
+                if (b == a) {
+                    v = a < s ? 1.0 + jit : 1.0;  // jitter on K_ss only
+                } else {
+                    const double dx = X[a] - X[b], dy = Y[a] - Y[b];
+                    const double q = fma(dx, dx, dy * dy);
+                    v = __double2hiint(q) > 0 ? matern_q<NUC>(q) : 1.0;
+                }
+                A[a * ld + b] = v;
             }
-            A[a * ld + b] = v;
         }
         __syncwarp();
-        ok = true;
-        for (int j = 0; j < s; ++j) {
-            const double d = A[j * ld + j];  // same value in every lane: the branch is uniform
-            if (!(d >= 2.2250738585072014e-308)) { ok = false; break; }
-            const double r = recip_nr(d);
-            for (int a = j + 1 + lane; a <= s; a += 32) {
-                const double w = A[a * ld + j];
-                W[a] = w;
-                A[a * ld + j] = w * r;
+        bool good = work;  // no non-positive pivot met in this round
+        for (int j = 0; j < smax; ++j) {
+            double r = 0.0;
+            if (good && j < s) {
+                const double d = A[j * ld + j];  // the same value in the half's lanes
+                if (!(d >= 2.2250738585072014e-308)) good = false;
+                else r = recip_nr(d);
+            }
+            const bool act = good && j < s;
+            for (int a = j + 1 + hl; a <= smax; a += 16) {
+                if (act && a <= s) {
+                    const double w = A[a * ld + j];
+                    W[a] = w;
+                    A[a * ld + j] = w * r;
+                }
             }
             __syncwarp();
             // entry e = a'(a'+1)/2 + c', c' <= a', of the trailing block (rows and columns j+1..s)
-            const int mm = s - j, ntr = mm * (mm + 1) / 2;
-            for (int e = lane; e < ntr; e += 32) {
-                const uchar2 tb = tri[e];
-                const int a = j + 1 + tb.x, c = j + 1 + tb.y;
-                A[a * ld + c] = fma(-A[a * ld + j], W[c], A[a * ld + c]);
+            const int mm = s - j, ntr = act ? mm * (mm + 1) / 2 : 0;
+            const int mmx = smax - j, ntr_max = mmx * (mmx + 1) / 2;
+            for (int e = hl; e < ntr_max; e += 16) {
+                if (e < ntr) {
+                    const uchar2 tb = tri[e];
+                    const int a = j + 1 + tb.x, c = j + 1 + tb.y;
+                    A[a * ld + c] = fma(-A[a * ld + j], W[c], A[a * ld + c]);
+                }
             }
             __syncwarp();
         }
-        __syncwarp();
-        if (!ok) ++tries;
+        if (work) {
+            if (good) ok = true;
+            else ++tries;
+        }
     }
-    const double cc = ok ? A[s * ld + s] : 0.0;
-    if (!ok || !(cc > 0.0)) {
+    const double cc = (valid && ok) ? A[s * ld + s] : 0.0;
+    const bool fin = valid && ok && cc > 0.0;
+    // L_ss' lambda = (row s of L)': entries hl + 16 r of the half in its lanes' registers
+    double l[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) l[r] = (fin && hl + 16 * r < s) ? A[s * ld + hl + 16 * r] : 0.0;
+    for (int c = smax - 1; c >= 0; --c) {
+        const int rc = c >> 4;
+        const double src = rc == 0 ? l[0] : (rc == 1 ? l[1] : (rc == 2 ? l[2] : l[3]));
+        const double lc = __shfl_sync(full, src, (half << 4) | (c & 15));
+        if (fin && c < s) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (16 * r < c && hl + 16 * r < c) l[r] = fma(-A[c * ld + hl + 16 * r], lc, l[r]);
+        }
+    }
+    if (!valid) return;
+    if (!fin) {
         // indefinite after the largest jitter, or no positive conditional variance:
         // empty conditioning set for this point
-        if (lane == 0 && (!ok || tries == 0)) atomicAdd(njit, 1ull);
-        for (int q = lane; q <= m; q += 32) val_ell[(int64_t)q * n + i] = q == 0 ? 1.0 : 0.0;
+        if (hl == 0 && (!ok || tries == 0)) atomicAdd(njit, 1ull);
+        for (int q = hl; q <= m; q += 16) val_ell[(int64_t)q * n + i] = q == 0 ? 1.0 : 0.0;
         return;
     }
-    if (tries > 0 && lane == 0) atomicAdd(njit, 1ull);
-    // L_ss' lambda = (row s of L)'; entries a and a + 32 in the lanes' registers
-    double l0 = lane < s ? A[s * ld + lane] : 0.0;
-    double l1 = lane + 32 < s ? A[s * ld + lane + 32] : 0.0;
-    for (int c = s - 1; c >= 0; --c) {
-        const double lc = __shfl_sync(full, c >= 32 ? l1 : l0, c & 31);
-        if (lane < c) l0 = fma(-A[c * ld + lane], lc, l0);
-        if (s > 32 && lane + 32 < c) l1 = fma(-A[c * ld + lane + 32], lc, l1);
-    }
+    if (tries > 0 && hl == 0) atomicAdd(njit, 1ull);
     const double ic = rsqrt(cc);
-    if (lane == 0) val_ell[i] = ic;
-    if (lane < m) val_ell[(int64_t)(1 + lane) * n + i] = lane < s ? -l0 * ic : 0.0;
-    if (lane + 32 < m) val_ell[(int64_t)(33 + lane) * n + i] = lane + 32 < s ? -l1 * ic : 0.0;
+    if (hl == 0) val_ell[i] = ic;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int q = hl + 16 * r;
+        if (q < m) val_ell[(int64_t)(1 + q) * n + i] = q < s ? -l[r] * ic : 0.0;
+    }
 }
 
 // The same factorisation with the elimination, pivots and back solve in float-float on the
@@ -1016,15 +1049,18 @@ int64_t vecchia_factor_dev(const double2 *x, int64_t n, const int *rank, const i
     once_per_device(3, upload_bessel_tables);
     const int ld = (m + 1) | 1;  // odd row stride: rows of consecutive lanes fall in different banks
     const size_t per = (size_t)((m + 1) * ld + 3 * (m + 1)) * sizeof(double);
-    int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
+    // points per warp: two in FP64 (factor_kernel), one in float-float (factor_kernel_ff)
+    const int ppw = ff ? 1 : 2;
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (ff ? 96 * 1024 : 110 * 1024) / (ppw * per)));
     const size_t tri_bytes = ((size_t)(m + 1) * (m + 2) / 2 * sizeof(uchar2) + 7) & ~(size_t)7;
-    const size_t smem = per * wpb + tri_bytes;
+    const size_t smem = per * ppw * wpb + tri_bytes;
     SBuf<unsigned long long> cnt(2, s);
     PHS_CUDA(cudaMemsetAsync(cnt.get(), 0, 2 * sizeof(unsigned long long), s));
     const int nuc = nu == 0.5 ? 0 : (nu == 1.0 ? 1 : (nu == 1.5 ? 2 : (nu == 2.0 ? 3 : 4)));
     auto launch = [&](auto kern) {
         PHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<blocks_for(n, wpb), 32 * wpb, smem, s>>>(x, n, rank, nbr_ell, m, ld, 0.5 * alpha, val_ell, cnt.get());
+        kern<<<blocks_for(n, (int64_t)ppw * wpb), 32 * wpb, smem, s>>>(x, n, rank, nbr_ell, m, ld, 0.5 * alpha, val_ell,
+                                                                      cnt.get());
     };
     if (ff) {
         switch (nuc) {
