@@ -639,8 +639,10 @@ __global__ void factor_kernel(const double2 *x, int64_t n, const int *rank, cons
 }
 
 // The same factorisation with the elimination, pivots and back solve in float-float on the
-// FP32 pipe (precision-4 plans): the Matern entries stay FP64 (then split), the stored
-// factor is FP64.  The factor only shapes the preconditioner: any U gives a symmetric
+// FP32 pipe (precision-4 plans), one point per warp (this kernel is bound by instruction
+// issue, not by the FP64 pipe: two points per warp, with half the warps in flight, was
+// measured slower): the Matern entries of nu = 1 and 2 come from the float-float series
+// (matern_ff; other nu in FP64, then split), the stored factor is FP64.  The factor only shapes the preconditioner: any U gives a symmetric
 // U U' applied in FP64, so float-float's rounding (about 2^-46 per operation, times the
 // local condition number) moves the iteration count, not the fit's accuracy.  A pivot
 // below the smallest normal float counts as non-positive (next rung of the jitter ladder).
