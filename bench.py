@@ -36,6 +36,13 @@ WORKLOAD = "tps_1m"
 # iterations for no alpha of the search (0.035 to 3.5).
 NU, ALPHA = 1.0, 0.011
 TUNE_SEED = 2002
+# k = 3 (cubic workload and the serving stream's k = 3 requests): phs_tune_alpha on another
+# draw of the cubic recipe (seed 2003, all 100,000 points) found alpha = 1.005 (40 PCG
+# iterations on the bench's own draw against 63 at the library's 0.35), and on held-out
+# serving requests (seed 2005, eight k = 3 requests of 48k-495k points) 1.0 took the fewest
+# iterations of {0.1, 0.35, 1, 2, 4}; for k = 1 and 2 the library's 0.35 was already best
+# there (within 5%), so those keep it.
+K3_ALPHA = 1.0
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/p2p_sym_kernel_tps_262k.md and profiles/m2l_tc_kernel_tps_262k.md, taken on the
 # n = 262144 case of this workload at leaf capacity 96 and scaled to the bench size: the
@@ -92,7 +99,7 @@ def parse():
                     help="step: the bench (plan + fit + evaluation, the JSON contract line); plan / "
                          "matvec / precond: one piece of it repeated --steps times on one plan, for "
                          "profiling; cubic: the cubic-PHS workload (n = 100,000 from 20 clusters, "
-                         "k = 3, m = 20, library defaults, tol 1e-8) timed like a step; serving: the "
+                         "k = 3, m = 20, alpha K3_ALPHA, tol 1e-8) timed like a step; serving: the "
                          "serving engine on a stream of requests with Poisson arrivals (n log-uniform in "
                          "[1000, --n-max], k in 1..3) against the same stream served one job at a time "
                          "(each of these prints its own short line); tune: phs_tune_alpha on the bench "
@@ -217,7 +224,8 @@ def serve_stream(phs, reqs, arrivals, max_active, threads=4):
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
-        ids.append(sv.submit(r["points"], r["f"], r["targets"], r["k"], vecchia_m=30, opts=phs.options(r["k"])))
+        o = phs.options(r["k"], alpha=K3_ALPHA) if r["k"] == 3 else phs.options(r["k"])
+        ids.append(sv.submit(r["points"], r["f"], r["targets"], r["k"], vecchia_m=30, opts=o))
     res = [sv.wait(i, allow_not_converged=True) for i in ids]
     st = sv.stats()
     sv.close()
@@ -387,7 +395,7 @@ def main():
     if args.case == "cubic":
         wc = synth.workload("cubic_mix")
         pc, fc, tc = (torch.tensor(wc[key], device=dev) for key in ("points", "f", "targets"))
-        copts = phs.options(3, tol=1e-8, maxiter=400, precision=args.precision)
+        copts = phs.options(3, tol=1e-8, maxiter=400, precision=args.precision, alpha=K3_ALPHA)
         res = []
         # the timed steps run as a user would (near field beside the far field); one more
         # step with phase timing (near field serialised) gives the breakdown
