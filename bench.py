@@ -306,7 +306,8 @@ def serving_case(args, phs):
            "requests": len(reqs), "n_range": [1000, args.n_max],
            "points_total": int(sum(len(r["f"]) for r in reqs)),
            "k_mix": {str(k): sum(r["k"] == k for r in reqs) for k in (1, 2, 3)},
-           "max_active": args.max_active, "rates": {}}
+           "max_active": args.max_active,
+           "alpha_by_k": {str(k): (K3_ALPHA if k == 3 else phs.options(k).alpha) for k in (1, 2, 3)}, "rates": {}}
     # Sequential arm: one job at a time (max_active = 1 admits the next job only when the
     # last is done), so under any arrival times its latencies follow from each job's own
     # service time by the FIFO single-server recursion start_i = max(a_i, done_{i-1}).  It
@@ -420,6 +421,7 @@ def main():
             t = float(np.mean([r[0] for r in res]))
             info = res[-1][1]
             print(json.dumps({"case": "cubic", "workload": "cubic_mix", "n": len(wc["f"]), "k": 3, "vecchia_m": 20,
+                              "alpha": K3_ALPHA,
                               "precision": args.precision, "value_s": t, "steps": args.steps, "iters": info["iters"],
                               "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"],
                               "ms_fit": info["ms_fit"], "ms_matvec_avg": info["ms_matvec_avg"],
