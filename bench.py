@@ -41,9 +41,9 @@ TUNE_SEED = 2002
 # iterations on the bench's own draw against 63 at the library's 0.35), and on held-out
 # serving requests (seed 2005, eight k = 3 requests of 48k-495k points) 1.0 took the fewest
 # iterations of {0.1, 0.35, 1, 2, 4}; for k = 1 and 2 the library's 0.35 was already best
-# there (within 5%), so those keep it.  The cubic case takes the search's value itself
-# (1.0 there: 47 iterations), the serving stream the sweep's.
-CUBIC_ALPHA = 1.005
+# there (within 5%), so those keep it.  The count is sensitive near there on the cubic
+# draw (47 iterations at 1.0, 53 at 1.005, 40 at the search's unrounded 1.00524): the
+# cubic case and the serving stream both take the round 1.0.
 K3_ALPHA = 1.0
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/p2p_sym_kernel_tps_262k.md and profiles/m2l_tc_kernel_tps_262k.md, taken on the
@@ -101,7 +101,7 @@ def parse():
                     help="step: the bench (plan + fit + evaluation, the JSON contract line); plan / "
                          "matvec / precond: one piece of it repeated --steps times on one plan, for "
                          "profiling; cubic: the cubic-PHS workload (n = 100,000 from 20 clusters, "
-                         "k = 3, m = 20, alpha CUBIC_ALPHA, tol 1e-8) timed like a step; serving: the "
+                         "k = 3, m = 20, alpha K3_ALPHA, tol 1e-8) timed like a step; serving: the "
                          "serving engine on a stream of requests with Poisson arrivals (n log-uniform in "
                          "[1000, --n-max], k in 1..3) against the same stream served one job at a time "
                          "(each of these prints its own short line); tune: phs_tune_alpha on the bench "
@@ -398,7 +398,7 @@ def main():
     if args.case == "cubic":
         wc = synth.workload("cubic_mix")
         pc, fc, tc = (torch.tensor(wc[key], device=dev) for key in ("points", "f", "targets"))
-        copts = phs.options(3, tol=1e-8, maxiter=400, precision=args.precision, alpha=CUBIC_ALPHA)
+        copts = phs.options(3, tol=1e-8, maxiter=400, precision=args.precision, alpha=K3_ALPHA)
         res = []
         # the timed steps run as a user would (near field beside the far field); one more
         # step with phase timing (near field serialised) gives the breakdown
@@ -423,7 +423,7 @@ def main():
             t = float(np.mean([r[0] for r in res]))
             info = res[-1][1]
             print(json.dumps({"case": "cubic", "workload": "cubic_mix", "n": len(wc["f"]), "k": 3, "vecchia_m": 20,
-                              "alpha": CUBIC_ALPHA,
+                              "alpha": K3_ALPHA,
                               "precision": args.precision, "value_s": t, "steps": args.steps, "iters": info["iters"],
                               "rel_res_true": info["rel_res_true"], "ms_plan": info["ms_plan"],
                               "ms_fit": info["ms_fit"], "ms_matvec_avg": info["ms_matvec_avg"],
