@@ -302,6 +302,12 @@ __global__ void zero_k(double *y, int64_t n) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) y[j] = 0.0;
 }
+// flag[0] = 1 if a and b differ in any bit (flag zeroed by the caller)
+__global__ void differ_k(const double *a, const double *b, int64_t n, int *flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool d = i < n && __double_as_longlong(a[i]) != __double_as_longlong(b[i]);
+    if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) *flag = 1;
+}
 __global__ void sub_k(double *out, const double *a, const double *b, int64_t n) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) out[j] = a[j] - b[j];
@@ -615,6 +621,28 @@ void matvec_norm(phs_plan *pl, const double *t, double *y, int precision, cudaSt
     fmm_apply(pl->fmm, pl->tree, pl->ps, t, y, precision, s, &pl->tm);
 }
 
+// The expansion buffers now hold the FP64 far field of the caller-order coefficients w
+// (scaled and sorted as phs_eval does); keep a copy of w to recognise it.
+void remember_far_field(phs_plan *pl, const double *w_dev, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    if (pl->fmm.far_w.n != (size_t)n) pl->fmm.far_w.alloc(n);
+    PHS_CUDA(cudaMemcpyAsync(pl->fmm.far_w.get(), w_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    pl->fmm.far_valid = true;
+}
+// whether the expansion buffers hold the FP64 far field of w (bitwise the same w)
+static bool far_field_of(phs_plan *pl, const double *w_dev, cudaStream_t s) {
+    const int64_t n = pl->ps.n;
+    if (!pl->fmm.far_valid || pl->fmm.far_w.n != (size_t)n) return false;
+    int *flag = reinterpret_cast<int *>(pl->scal.get() + 63);
+    PHS_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    differ_k<<<blocks_for(n, 256), 256, 0, s>>>(w_dev, pl->fmm.far_w.get(), n, flag);
+    PHS_LAUNCH_CHECK();
+    int h = 1;
+    PHS_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PHS_CUDA(cudaStreamSynchronize(s));
+    return h == 0;
+}
+
 double read_scalar(phs_plan *pl, const double *dev, cudaStream_t s) {
     PHS_CUDA(cudaMemcpyAsync(pl->hscal, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     PHS_CUDA(cudaStreamSynchronize(s));
@@ -869,6 +897,7 @@ static int pcg(phs_plan *pl, const double *rhs, double *x, double tol_abs, int m
 // rounding (f in span(B)) the solution is w = 0 and x (work vector 9) is zeroed.
 FitStart fit_begin(phs_plan *pl, const double *f_dev, cudaStream_t s) {
     const int64_t n = pl->ps.n;
+    pl->fmm.far_valid = false;  // the fit's applies (some replayed from graphs) overwrite the expansions
     const phs_options &o = pl->opt;
     double *fs = W(pl, 7), *rhs = W(pl, 8), *x = W(pl, 9);
     double *sc = pl->scal.get();
@@ -947,6 +976,9 @@ double fit_end(phs_plan *pl, double *w_dev, double *beta_dev, cudaStream_t s, bo
     scatter_scaled<<<blocks_for(n, 256), 256, 0, s>>>(x, pl->ps.perm.get(), n, std::pow(pl->ps.frame.rho, (double)pl->k),
                                                        w_dev);
     PHS_LAUNCH_CHECK();
+    // the last apply of every fit path is the FP64 operator on x (above, or the refinement
+    // step whose product this reuses): the expansion buffers hold the far field of this w
+    remember_far_field(pl, w_dev, s);
     PHS_CUDA(cudaStreamSynchronize(s));
     return rr_true;
 }
@@ -1226,7 +1258,11 @@ phs_status phs_eval(phs_plan_t pl, const double *w_dev, const double *beta_dev, 
     const Frame &fr = pl->ps.frame;
     norm_targets<<<blocks_for(m, 256), 256, 0, s>>>(tgt_dev, m, fr.cx, fr.cy, fr.rho, yn.get());
     PHS_LAUNCH_CHECK();
-    fmm_eval64(pl->fmm, pl->tree, pl->ps, ws, yn.get(), m, out_dev, s, &pl->tm);
+    // the far field of this w may be in place already (the end of its fit, or an earlier
+    // evaluation of it): then only the evaluation at the targets runs
+    const bool ready = far_field_of(pl, w_dev, s);
+    fmm_eval64(pl->fmm, pl->tree, pl->ps, ws, yn.get(), m, out_dev, s, &pl->tm, ready);
+    if (!ready) remember_far_field(pl, w_dev, s);
     add_poly<<<blocks_for(m, 256), 256, 0, s>>>(yn.get(), m, pl->deg, pl->S, beta_dev, out_dev);
     PHS_LAUNCH_CHECK();
     PHS_CUDA(cudaStreamSynchronize(s));

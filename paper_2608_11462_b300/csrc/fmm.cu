@@ -1371,6 +1371,7 @@ static void p2p_prepare(Fmm &f, const Tree &t) {
 void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y, int mode, cudaStream_t s,
                Timers *tm) {
     PHS_REQUIRE(mode >= 0 && mode <= 4, PHS_ERR_INVALID_ARG, "precision mode must be 0..4");
+    f.far_valid = false;  // the expansion buffers are about to hold this apply's far field
     PHS_REQUIRE(f.log_core || mode == 0 || mode == 4, PHS_ERR_INVALID_ARG, "odd spline orders run in precision 0 or 4");
     // near field on the side stream (it writes y; the far field's L2P adds to y after the
     // join).  With phase timing on it stays on s, so each phase's events time that phase
@@ -1716,9 +1717,11 @@ static void eval_launch(Fmm &f, const Tree &t, const PointSet &ps, const double 
 }
 
 void fmm_eval64(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted, const double2 *tgt, int64_t m,
-                double *out, cudaStream_t s, Timers *tm) {
-    if (f.log_core) far_field<double>(f, t, ps, w_sorted, s, nullptr);
-    else cheb_far_field(f, t, ps, w_sorted, s, nullptr);
+                double *out, cudaStream_t s, Timers *tm, bool far_ready) {
+    if (!far_ready) {
+        if (f.log_core) far_field<double>(f, t, ps, w_sorted, s, nullptr);
+        else cheb_far_field(f, t, ps, w_sorted, s, nullptr);
+    }
     if (tm) tm->begin(s);
     switch (f.k) {
         case 1: eval_launch<1>(f, t, ps, w_sorted, tgt, m, out, s); break;

@@ -269,6 +269,11 @@ struct Fmm {
     DBuf<int2> tc_off;                   // nd = 4: class offsets (ox, oy)
     DBuf<int> tc_mexp;                   // per-box exponent bound of the multipoles
     DBuf<int> tc_tgt;                    // M2L targets (levels >= 2) by (level, child position, box)
+    // The FP64 far field held in the expansion buffers is that of the caller-order
+    // coefficients far_w (set by the end of a fit, whose last apply is the FP64 operator on
+    // the solution, and by an evaluation); any FMM apply clears it
+    bool far_valid = false;
+    DBuf<double> far_w;
     int tc_tgt_nbox = -1;                // box count of the tree tc_tgt was built for
     DBuf<int> tc_err;                    // device status (nonzero: a bounded wait expired)
     uint64_t tc_wait_ns = 0;             // main-loop wait limit of the pass (0: the 2 s default)
@@ -344,9 +349,11 @@ void l2l_ff_launch(const Fmm &f, const Tree &t, int b0, int nb, double2 *lc, cud
 void fmm_apply(Fmm &f, const Tree &t, const PointSet &ps, const double *t_sorted, double *y_sorted, int mode,
                cudaStream_t s, struct Timers *tm);
 // evaluate sum_j w_j phi(|x_j - y|) at normalised targets (after an FMM upward/downward
-// pass on w), out written (overwritten) for m targets
+// pass on w, skipped when far_ready: the expansion buffers already hold w's FP64 far
+// field), out written (overwritten) for m targets
 void fmm_eval64(Fmm &f, const Tree &t, const PointSet &ps, const double *w_sorted,
-                const double2 *tgt_norm, int64_t m, double *out, cudaStream_t s, struct Timers *tm);
+                const double2 *tgt_norm, int64_t m, double *out, cudaStream_t s, struct Timers *tm,
+                bool far_ready = false);
 // exact all-pairs product out = M t (points in any order, FP64)
 void dense_matvec64(const double2 *x, int64_t n, int k, const double *t, double *out, cudaStream_t s);
 

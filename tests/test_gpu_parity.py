@@ -596,6 +596,48 @@ def test_fit_uniform_tps_matches_dense_solve(phs, precision):
     assert np.max(np.abs(at_nodes - w_["f"])) <= 1e-8 * np.max(np.abs(w_["f"]))
 
 
+@pytest.mark.parametrize("k,precision", [(2, 0), (2, 4), (3, 0)])
+def test_eval_reuses_the_fits_far_field(phs, k, precision):
+    """phs_eval right after phs_fit takes the far field of the fit's last FP64 apply (on
+    the same w) instead of recomputing it: the predictions agree with an evaluation whose
+    far field is recomputed (an intervening matvec clears the record) to rounding (the fit
+    applied the operator to w before its caller-order rescaling by rho^k), and a second
+    evaluation of the same w reuses its own far field bit for bit; a different w is
+    recomputed."""
+    rng = np.random.default_rng(41 + k)
+    # tight clusters for k = 2; the cubic system on them is beyond this preconditioner's
+    # reach at these settings, so uniform points there
+    pts = _clustered(20_000, 43 + k) if k == 2 else rng.random((20_000, 2))
+    f = np.sin(3 * pts[:, 0]) * np.cos(2 * pts[:, 1]) + 0.1 * rng.standard_normal(len(pts))
+    tg = rng.random((2_000, 2))
+    # the reduced-precision operator stalls short of 1e-8 on clustered points: 1e-6 there
+    tol = 1e-8 if precision == 0 else 1e-6
+    plan = phs.Plan(_t(pts), k, fmm_order=0, vecchia_m=30,
+                    opts=phs.options(k, tol=tol, maxiter=400, precision=precision))
+    w, beta, info = plan.fit(_t(f))
+    assert info["converged"] == 1
+    p_reuse = plan.eval(w, beta, _t(tg)).cpu().numpy()
+    plan.matvec(w)
+    p_fresh = plan.eval(w, beta, _t(tg)).cpu().numpy()
+    p_again = plan.eval(w, beta, _t(tg)).cpu().numpy()
+    # the two far fields come from w at the last bit (the fit's own vector, or w scaled back
+    # and forth by rho^k); the sums they feed cancel, so the bound is rounding of the sum of
+    # magnitudes sum_j |w_j phi(|t - x_j|)| at each target, not of the prediction
+    wn = w.cpu().numpy()
+    d = np.sqrt(((tg[:, None, :] - pts[None, :, :]) ** 2).sum(-1))
+    phi = d ** k * (np.log(np.maximum(d, 1e-300)) if k % 2 == 0 else 1.0)
+    mag = np.abs(phi) @ np.abs(wn)
+    diff = np.abs(p_reuse - p_fresh)
+    assert np.all(diff <= 1000 * np.finfo(float).eps * mag), np.max(diff / mag)
+    assert np.array_equal(p_again, p_fresh)
+    # another w: its own far field (not the cached one)
+    w2 = w * 1.5
+    p2 = plan.eval(w2, beta, _t(tg)).cpu().numpy()
+    plan.matvec(w2)
+    p2_fresh = plan.eval(w2, beta, _t(tg)).cpu().numpy()
+    assert np.array_equal(p2, p2_fresh)
+
+
 def test_lowrank_precond_fit_same_solution_fewer_iterations(phs):
     """Clustered TPS workload (n = 40,000): with the low-rank term the PCG needs no
     more iterations than the plain preconditioner, and both reach the same true
