@@ -775,6 +775,7 @@ void m2l_tc_check(Fmm &f, cudaStream_t s) {
     PHS_CUDA(cudaStreamSynchronize(s));
     if (h) {
         PHS_CUDA(cudaMemsetAsync(f.tc_err.get(), 0, sizeof(int), s));
+        f.far_valid = false;  // the expansions of that apply are incomplete: no evaluation reuses them
         throw Error{PHS_ERR_TIMEOUT, "tensor-core M2L: a bounded wait expired"};
     }
 }
