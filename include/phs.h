@@ -183,7 +183,14 @@ phs_status phs_fit(phs_plan_t plan, const double *f_dev, double *w_dev, double *
 
 /* Evaluate the interpolant (Eq. 1.1) at m targets (m x 2 device array, caller
  * frame) with the FMM for the kernel part; w_dev/beta_dev as returned by
- * phs_fit.  out_dev: m values. */
+ * phs_fit.  out_dev: m values.  The plan keeps a device copy of the w whose FP64
+ * far field (multipole and local expansions) it last built, at the end of
+ * phs_fit or in an earlier phs_eval; when w_dev equals it bit for bit the
+ * upward pass, M2L and downward pass are skipped and only the target-side
+ * evaluation runs.  The result then agrees with a recomputed far field to
+ * rounding (the fit built it from its own scaling of the same weights).
+ * phs_matvec, a new fit or a tensor-core wait timeout clears the record.
+ * Synchronises `stream`. */
 phs_status phs_eval(phs_plan_t plan, const double *w_dev, const double *beta_dev,
                     const double *tgt_dev, int64_t m, double *out_dev, phs_stream_t stream);
 
