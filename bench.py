@@ -299,6 +299,19 @@ def batch_case(args, phs):
     print(json.dumps(out))
 
 
+def fifo_latencies(arrivals, service):
+    """Latencies of requests served one at a time in arrival order (a single FIFO
+    server): request i starts at max(a_i, end of request i-1) and ends s_i later; its
+    latency is end_i - a_i.  Arrivals must be non-decreasing."""
+    import numpy as np
+
+    done, lat = 0.0, []
+    for a_, s_ in zip(arrivals, service):
+        done = max(float(a_), done) + float(s_)
+        lat.append(done - float(a_))
+    return np.asarray(lat)
+
+
 def serving_case(args, phs):
     import numpy as np
 
@@ -320,11 +333,8 @@ def serving_case(args, phs):
     svc = seq.pop("_service_s")
 
     def fifo(arr, svc_):
-        done, lat = 0.0, []
-        for a_, s_ in zip(arr, svc_):
-            done = max(a_, done) + s_
-            lat.append(done - a_)
-        lat = np.asarray(lat)
+        lat = fifo_latencies(arr, svc_)
+        done = float(arr[-1]) + float(lat[-1])
         return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "mean_s": float(lat.mean()), "solves_per_s": len(arr) / (done - float(np.min(arr))),
                 "simulated": True}

@@ -60,3 +60,44 @@ def test_default_fmm_order_rule():
     assert bench.default_fmm_order(0.9) == 4 and bench.default_fmm_order(1e-40) == 60
     src = open(os.path.join(ROOT, "paper_2608_11462_b300", "csrc", "abi.cu")).read()
     assert "std::log(o.fmm_eps) / std::log(0.55)" in src and "std::max(4, std::min(p, 60))" in src
+
+
+def test_fifo_latencies_of_the_sequential_serving_arm():
+    """The serving case's one-at-a-time latencies at Poisson rates come from the single
+    FIFO server recursion over measured service times.  Checked on a hand-worked case, on
+    simultaneous arrivals (latency i = s_0 + ... + s_i), and against a discrete-event
+    simulation that tracks the server's state between events."""
+    import heapq
+
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    # a = 0, 1, 1.5, 10 with s = 2, 2, 1, 1: ends 2, 4, 5, 11
+    lat = bench.fifo_latencies([0.0, 1.0, 1.5, 10.0], [2.0, 2.0, 1.0, 1.0])
+    assert np.array_equal(lat, [2.0, 3.0, 3.5, 1.0])
+    svc = np.array([0.5, 0.25, 2.0, 1.0])
+    assert np.allclose(bench.fifo_latencies(np.zeros(4), svc), np.cumsum(svc), rtol=0, atol=1e-15)
+
+    def simulate(arr, svc_):
+        # events (time, kind, request): kind 0 = a request ends, kind 1 = a request arrives
+        ev = [(a_, 1, i) for i, a_ in enumerate(arr)]
+        heapq.heapify(ev)
+        queue, busy, end = [], False, [0.0] * len(arr)
+        while ev:
+            t, kind, i = heapq.heappop(ev)
+            if kind == 0:
+                end[i] = t
+                busy = False
+            else:
+                queue.append(i)
+            if not busy and queue:
+                j = queue.pop(0)
+                busy = True
+                heapq.heappush(ev, (t + svc_[j], 0, j))
+        return np.asarray(end) - np.asarray(arr)
+
+    rng = np.random.default_rng(5)
+    for rate in (0.5, 2.0, 8.0):
+        arr = np.cumsum(rng.exponential(1.0 / rate, 300))
+        s_ = rng.lognormal(-1.0, 1.0, 300)
+        assert np.allclose(bench.fifo_latencies(arr, s_), simulate(arr, s_), rtol=1e-12, atol=1e-12)
