@@ -43,7 +43,7 @@ TUNE_SEED = 2002
 # iterations of {0.1, 0.35, 1, 2, 4}; for k = 1 and 2 the library's 0.35 was already best
 # there (within 5%), so those keep it.  The count is sensitive near there on the cubic
 # draw (47 iterations at 1.0, 53 at 1.005, 40 at the search's unrounded 1.00524): the
-# cubic case and the serving stream both take the round 1.0.
+# cubic case and the serving stream both take the whole number 1.0.
 K3_ALPHA = 1.0
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/p2p_sym_kernel_tps_262k.md and profiles/m2l_tc_kernel_tps_262k.md, taken on the

@@ -36,7 +36,7 @@ struct phs_plan {
 
 namespace phs {
 
-// 64 pinned host doubles from a process-wide pool (never returned to the driver, so a
+// 64 pinned host doubles from a process-wide pool (never returned to the CUDA driver, so a
 // plan's destruction does not synchronise the device through cudaFreeHost)
 double *pinned_block();
 void pinned_release(double *b);
